@@ -1,0 +1,152 @@
+/*
+ * evo.h -- C ABI of the GB300 (sm_103a) Evoformer block library (libevo.so).
+ *
+ * The operation is one AlphaFold2 Evoformer block, the unit that HelixFold
+ * (arXiv 2207.05477) optimises: MSA row attention with pair bias, MSA column
+ * attention, MSA transition, outer product mean, triangle multiplication
+ * (outgoing, incoming), triangle attention (starting, ending node) and pair
+ * transition, in that order (paper Sec. 3.1 and Fig. 1-2 name the modules;
+ * the arithmetic is that of AlphaFold2's published Evoformer, Algorithms 6-15
+ * and 19 of its supplement).  Forward and backward; the backward recomputes
+ * the forward of the block from its inputs (per-block recompute, Sec. 3.4.1).
+ *
+ * Conventions for every entry point:
+ *  - Every pointer argument named *_in/*_out, m, z, masks, params, dparams,
+ *    workspace is a DEVICE pointer owned by the caller.  The library never
+ *    allocates or frees device memory and never synchronises the stream,
+ *    except evo_get_error which reads the device error word.
+ *  - Tensors are dense, row-major, channel innermost:
+ *      m        [n_seq, n_res, c_m]     activation dtype (act_dtype)
+ *      z        [n_res, n_res, c_z]     activation dtype
+ *      msa_mask [n_seq, n_res]          fp32, 1 = valid, 0 = padded
+ *      pair_mask[n_res, n_res]          fp32, 1 = valid, 0 = padded
+ *    A masked key is excluded from its softmax exactly; a query with no valid
+ *    key receives an attention output of 0 (its update is the output bias).
+ *  - params is the flat fp32 parameter buffer of one block (evo_param_layout
+ *    lists each tensor; each starts on a 256-byte boundary, the alignment of
+ *    the paper's fused parameter tensors, Sec. 3.2 "Tensor Fusion").
+ *  - params_bf16 is evo_params_to_bf16's copy of params (same offsets); it is
+ *    required when act_dtype == EVO_BF16 and ignored for EVO_F32.
+ *  - Every call returns 0 (EVO_OK) or a negative EVO_ERR_* code.  Calls never
+ *    abort and never print.  Launch errors are reported as EVO_ERR_CUDA.
+ *  - The stream argument is a cudaStream_t (0 = legacy default stream).
+ */
+#ifndef EVO_H
+#define EVO_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *evo_stream_t; /* same type as cudaStream_t */
+
+enum {
+  EVO_OK = 0,
+  EVO_ERR_INVALID_ARG = -1,  /* null pointer, non-positive size, bad enum   */
+  EVO_ERR_UNSUPPORTED = -2,  /* dims the kernels do not implement           */
+  EVO_ERR_ALIGNMENT = -3,    /* device pointer not 256-byte aligned         */
+  EVO_ERR_WORKSPACE = -4,    /* ws_bytes below evo_workspace_size           */
+  EVO_ERR_CUDA = -5,         /* a CUDA runtime call or launch failed        */
+  EVO_ERR_TIMEOUT = -6       /* a bounded device wait gave up (error word)  */
+};
+
+enum { EVO_F32 = 0, EVO_BF16 = 1 };           /* act_dtype */
+enum { EVO_COL_ATTENTION = 0, EVO_COL_GLOBAL = 1 }; /* msa_col_mode */
+enum { EVO_MODE_FWD = 0, EVO_MODE_BWD = 1 };  /* workspace query mode */
+
+/* Sizes of one block.  Defaults of the paper's Evoformer (Table "model
+ * settings", Table "FastFold vs PPFold": C_m=256, C_z=128, 8 heads):
+ * c_m 256, c_z 128, h_msa 8, c_msa 32, h_tri 4, c_tri 32, c_mul 128,
+ * c_opm 32, trans_n 4.  The extra-MSA block uses c_m 64, c_msa 8 and
+ * msa_col_mode EVO_COL_GLOBAL. */
+typedef struct evo_dims {
+  int32_t n_seq, n_res, c_m, c_z;
+  int32_t h_msa, c_msa, h_tri, c_tri;
+  int32_t c_mul, c_opm, trans_n;
+  int32_t msa_col_mode; /* EVO_COL_ATTENTION | EVO_COL_GLOBAL */
+  int32_t act_dtype;    /* EVO_F32 | EVO_BF16: storage of m, z, intermediates */
+} evo_dims;
+
+typedef struct evo_param_entry {
+  char name[48];     /* e.g. "row.w_qkvg"                                    */
+  int64_t offset;    /* in floats from the start of params                  */
+  int32_t ndim;      /* 1 or 2                                              */
+  int64_t shape[4];  /* weights are [out, in]                               */
+} evo_param_entry;
+
+/* Number of fp32 scalars in one block's flat parameter buffer, padding
+ * included (1,829,952 at the paper's Evoformer dims).  0 on bad dims. */
+size_t evo_param_count(const evo_dims *d);
+
+/* Fills up to cap entries of the parameter table (Sec. 3.2 flat buffer) and
+ * returns the total number of entries, or a negative error.  Host only. */
+int evo_param_layout(const evo_dims *d, evo_param_entry *out, int cap);
+
+/* Bytes of the BF16 parameter copy (evo_param_count * 2). */
+int evo_params_bf16_size(const evo_dims *d, size_t *bytes);
+
+/* Rounds params (fp32, device) to bfloat16 (round to nearest even) into
+ * params_bf16 (device, evo_params_bf16_size bytes). */
+int evo_params_to_bf16(const evo_dims *d, const float *params, void *params_bf16,
+                       evo_stream_t stream);
+
+/* Workspace bytes for evo_block_fwd (mode EVO_MODE_FWD) or evo_block_bwd
+ * (EVO_MODE_BWD).  The workspace is scratch owned by the caller; its
+ * content on entry is irrelevant and on exit undefined. */
+int evo_workspace_size(const evo_dims *d, int mode, size_t *bytes);
+
+/* Forward of one block: (m_out, z_out) = Evoformer(m_in, z_in).
+ * m_out may equal m_in and z_out may equal z_in (in-place update).
+ * All device pointers must be 256-byte aligned. */
+int evo_block_fwd(const evo_dims *d, const float *params, const void *params_bf16,
+                  const void *m_in, const void *z_in, void *m_out, void *z_out,
+                  const float *msa_mask, const float *pair_mask,
+                  void *workspace, size_t ws_bytes, evo_stream_t stream);
+
+/* Backward of one block with per-block recompute (Sec. 3.4.1): recomputes
+ * the forward from (m_in, z_in) inside the workspace, then propagates the
+ * cotangents dm_out [n_seq,n_res,c_m] and dz_out [n_res,n_res,c_z]
+ * (activation dtype) back to dm_in, dz_in (activation dtype, overwritten)
+ * and ADDS the parameter gradient to dparams (fp32, evo_param_count). */
+int evo_block_bwd(const evo_dims *d, const float *params, const void *params_bf16,
+                  const void *m_in, const void *z_in,
+                  const float *msa_mask, const float *pair_mask,
+                  const void *dm_out, const void *dz_out,
+                  void *dm_in, void *dz_in, float *dparams,
+                  void *workspace, size_t ws_bytes, evo_stream_t stream);
+
+/* Forward through n_blocks consecutive blocks (the EvoformerStack, Fig. 1),
+ * updating m and z in place.  Block b reads params + b*param_stride and
+ * params_bf16 + b*param_stride (bf16 elements).  Workspace as for
+ * EVO_MODE_FWD. */
+int evo_stack_fwd(const evo_dims *d, int n_blocks, const float *params,
+                  const void *params_bf16, size_t param_stride,
+                  void *m, void *z, const float *msa_mask, const float *pair_mask,
+                  void *workspace, size_t ws_bytes, evo_stream_t stream);
+
+/* Waits for the stream, then returns and clears the device error word:
+ * EVO_OK, or EVO_ERR_TIMEOUT if a bounded in-kernel wait gave up since the
+ * last call. */
+int evo_get_error(evo_stream_t stream);
+
+/* Diagnostics for failure detection: launches one CTA whose bounded
+ * mbarrier wait is never satisfied and gives up after limit_ns (at most 5 s),
+ * recording EVO_ERR_TIMEOUT in the device error word exactly as a timed-out
+ * wait inside a GEMM would.  The GPU context stays usable; evo_get_error
+ * then returns EVO_ERR_TIMEOUT.  The paper has no counterpart (it describes
+ * no failure detection). */
+int evo_debug_wait_timeout(long long limit_ns, evo_stream_t stream);
+
+/* Static description of an EVO_* code. */
+const char *evo_strerror(int code);
+
+/* Library build id (sm target and version), static string. */
+const char *evo_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* EVO_H */

@@ -1,0 +1,611 @@
+// Evoformer block drivers: the AlphaFold2 Algorithm 6 order of sub-modules,
+// each a short chain of libevo kernels, forward (optionally keeping every
+// intermediate for the backward) and backward with per-block recompute
+// (HelixFold keeps only block inputs and recomputes the rest, Sec. 3.4.1).
+//
+// One driver serves both storage types: act_dtype EVO_BF16 runs the tcgen05
+// GEMMs and tensor-core attention, EVO_F32 the plain SIMT kernels.  Weights
+// enter the GEMMs straight from the flat parameter buffer (or its BF16 copy):
+// a forward projection uses W [out,in] as a K-major operand and the backward
+// dX = dY W uses the same buffer as an MN-major operand, so no transposed
+// copies exist.  Residual-stream gradients accumulate in FP32.
+#include <cmath>
+#include <algorithm>
+#include <map>
+
+#include "block.h"
+
+namespace evo {
+
+// ------------------------------------------------------------ param table
+int64_t build_param_table(const evo_dims &d, std::vector<PEntry> &out) {
+  out.clear();
+  int64_t off = 0;
+  auto add = [&](const std::string &name, std::initializer_list<int64_t> shape) {
+    PEntry e;
+    e.name = name;
+    e.offset = off;
+    e.ndim = (int)shape.size();
+    int64_t n = 1;
+    int k = 0;
+    for (int64_t v : shape) {
+      e.shape[k++] = v;
+      n *= v;
+    }
+    for (; k < 4; ++k) e.shape[k] = 0;
+    out.push_back(e);
+    off += (n + 63) / 64 * 64;
+  };
+  auto ln = [&](const std::string &p, int64_t c) {
+    add(p + ".gamma", {c});
+    add(p + ".beta", {c});
+  };
+  const int64_t C = d.c_m, Z = d.c_z, hm = d.h_msa, cm = d.c_msa, ht = d.h_tri, ct = d.c_tri;
+  ln("row.ln_m", C);
+  ln("row.ln_z", Z);
+  add("row.w_b", {hm, Z});
+  add("row.w_qkvg", {4 * hm * cm, C});
+  add("row.b_g", {hm * cm});
+  add("row.w_o", {C, hm * cm});
+  add("row.b_o", {C});
+  ln("col.ln", C);
+  if (d.msa_col_mode == EVO_COL_ATTENTION) add("col.w_qkvg", {4 * hm * cm, C});
+  else add("col.w_qkvg", {2 * hm * cm + 2 * cm, C});
+  add("col.b_g", {hm * cm});
+  add("col.w_o", {C, hm * cm});
+  add("col.b_o", {C});
+  ln("msa_trans.ln", C);
+  add("msa_trans.w1", {d.trans_n * C, C});
+  add("msa_trans.b1", {d.trans_n * C});
+  add("msa_trans.w2", {C, d.trans_n * C});
+  add("msa_trans.b2", {C});
+  ln("opm.ln", C);
+  add("opm.w_ab", {2 * d.c_opm, C});
+  add("opm.b_ab", {2 * d.c_opm});
+  add("opm.w_o", {Z, (int64_t)d.c_opm * d.c_opm});
+  add("opm.b_o", {Z});
+  for (const char *t : {"tri_out", "tri_in"}) {
+    const std::string p(t);
+    ln(p + ".ln_in", Z);
+    add(p + ".w_abg", {4 * d.c_mul + Z, Z});
+    add(p + ".b_abg", {4 * d.c_mul + Z});
+    ln(p + ".ln_out", d.c_mul);
+    add(p + ".w_o", {Z, d.c_mul});
+    add(p + ".b_o", {Z});
+  }
+  for (const char *t : {"att_start", "att_end"}) {
+    const std::string p(t);
+    ln(p + ".ln", Z);
+    add(p + ".w_b", {ht, Z});
+    add(p + ".w_qkvg", {4 * ht * ct, Z});
+    add(p + ".b_g", {ht * ct});
+    add(p + ".w_o", {Z, ht * ct});
+    add(p + ".b_o", {Z});
+  }
+  ln("pair_trans.ln", Z);
+  add("pair_trans.w1", {d.trans_n * Z, Z});
+  add("pair_trans.b1", {d.trans_n * Z});
+  add("pair_trans.w2", {Z, d.trans_n * Z});
+  add("pair_trans.b2", {Z});
+  return off;
+}
+
+int validate_dims(const evo_dims *d) {
+  if (!d) return EVO_ERR_INVALID_ARG;
+  if (d->n_seq <= 0 || d->n_res <= 0 || d->c_m <= 0 || d->c_z <= 0 || d->h_msa <= 0 || d->c_msa <= 0 ||
+      d->h_tri <= 0 || d->c_tri <= 0 || d->c_mul <= 0 || d->c_opm <= 0 || d->trans_n <= 0)
+    return EVO_ERR_INVALID_ARG;
+  if (d->act_dtype != EVO_F32 && d->act_dtype != EVO_BF16) return EVO_ERR_INVALID_ARG;
+  if (d->msa_col_mode != EVO_COL_ATTENTION && d->msa_col_mode != EVO_COL_GLOBAL) return EVO_ERR_INVALID_ARG;
+  // kernels: channel dims multiples of 8 (16-byte rows), heads <= 8, head dim <= 32
+  if (d->c_m % 8 || d->c_z % 8 || d->c_mul % 8 || d->c_opm % 8 || d->c_msa % 8 || d->c_tri % 8) return EVO_ERR_UNSUPPORTED;
+  if (d->h_msa > 8 || d->h_tri > 8 || d->c_msa > 32 || d->c_tri > 32) return EVO_ERR_UNSUPPORTED;
+  if (d->c_m > 1024 || d->c_z > 1024 || d->c_mul > 256) return EVO_ERR_UNSUPPORTED;
+  if (d->msa_col_mode == EVO_COL_GLOBAL) return EVO_ERR_UNSUPPORTED;
+  return EVO_OK;
+}
+
+// ------------------------------------------------------------ workspace plan
+namespace {
+
+constexpr int MAXSPLIT = 32;
+
+struct TriBufs {
+  size_t xz, abg, A, B, X, xo, y, zout;
+};
+struct AttBufs {
+  size_t xz, bias, qkvg, oatt, og, lse, zout;
+};
+
+struct Plan {
+  size_t xm1, xz1, bias1, qkvg1, oatt1, og1, lse1, m1;
+  size_t xm2, qkvg2, oatt2, og2, lse2, m2;
+  size_t xm3, h3, m3;
+  size_t xm4, ab4, O4, inv4, z1;
+  TriBufs tri[2];
+  AttBufs att[2];
+  size_t xz9, h9, z6;
+  size_t dm_acc, dmT, dz_acc, dzT, G1, G2, G3, dO4, dA, dB, dX, dq_acc, dbias, Dsum, dab4, split, cpart, lpart, hpart;
+  size_t total;
+};
+
+struct Dims2 {
+  int64_t S, R, Cm, Cz, Hm, cm, Ht, ct, cmul, co, n, Mm, Mz, Rp, HCm, HCt, QKm, QKc, ABG;
+  explicit Dims2(const evo_dims &d) {
+    S = d.n_seq, R = d.n_res, Cm = d.c_m, Cz = d.c_z, Hm = d.h_msa, cm = d.c_msa, Ht = d.h_tri, ct = d.c_tri;
+    cmul = d.c_mul, co = d.c_opm, n = d.trans_n;
+    Mm = S * R, Mz = R * R, Rp = (R + 7) / 8 * 8;
+    HCm = Hm * cm, HCt = Ht * ct;
+    QKm = 4 * HCm;
+    QKc = d.msa_col_mode == EVO_COL_ATTENTION ? 4 * HCm : 2 * HCm + 2 * cm;
+    ABG = 4 * cmul + Cz;
+  }
+};
+
+size_t make_plan(const evo_dims &d, int mode, Plan &p) {
+  const Dims2 k(d);
+  const size_t ts = d.act_dtype == EVO_BF16 ? 2 : 4;
+  size_t off = 0;
+  auto T = [&](int64_t elems) {
+    size_t o = off;
+    off += ((size_t)elems * ts + 255) / 256 * 256;
+    return o;
+  };
+  auto F = [&](int64_t elems) {
+    size_t o = off;
+    off += ((size_t)elems * 4 + 255) / 256 * 256;
+    return o;
+  };
+  p.xm1 = T(k.Mm * k.Cm), p.xz1 = T(k.Mz * k.Cz), p.bias1 = F(k.Hm * k.Mz), p.qkvg1 = T(k.Mm * k.QKm);
+  p.oatt1 = T(k.Mm * k.HCm), p.og1 = T(k.Mm * k.HCm), p.lse1 = F(k.S * k.Hm * k.R), p.m1 = T(k.Mm * k.Cm);
+  p.xm2 = T(k.Mm * k.Cm), p.qkvg2 = T(k.Mm * k.QKc), p.oatt2 = T(k.Mm * k.HCm), p.og2 = T(k.Mm * k.HCm);
+  p.lse2 = F(k.R * k.Hm * k.S), p.m2 = T(k.Mm * k.Cm);
+  p.xm3 = T(k.Mm * k.Cm), p.h3 = T(k.Mm * k.n * k.Cm), p.m3 = T(k.Mm * k.Cm);
+  p.xm4 = T(k.Mm * k.Cm), p.ab4 = T(2 * k.Mm * k.co), p.O4 = T(k.Mz * k.co * k.co), p.inv4 = F(k.Mz);
+  p.z1 = T(k.Mz * k.Cz);
+  for (int t = 0; t < 2; ++t) {
+    TriBufs &b = p.tri[t];
+    b.xz = T(k.Mz * k.Cz), b.abg = T(k.Mz * k.ABG), b.A = T(k.cmul * k.R * k.Rp), b.B = T(k.cmul * k.R * k.Rp);
+    b.X = T(k.cmul * k.R * k.Rp), b.xo = T(k.Mz * k.cmul), b.y = T(k.Mz * k.Cz), b.zout = T(k.Mz * k.Cz);
+  }
+  for (int t = 0; t < 2; ++t) {
+    AttBufs &b = p.att[t];
+    b.xz = T(k.Mz * k.Cz), b.bias = F(k.Ht * k.Mz), b.qkvg = T(k.Mz * 4 * k.HCt), b.oatt = T(k.Mz * k.HCt);
+    b.og = T(k.Mz * k.HCt), b.lse = F(k.R * k.Ht * k.R), b.zout = T(k.Mz * k.Cz);
+  }
+  p.xz9 = T(k.Mz * k.Cz), p.h9 = T(k.Mz * k.n * k.Cz), p.z6 = T(k.Mz * k.Cz);
+  if (mode == EVO_MODE_BWD) {
+    p.dm_acc = F(k.Mm * k.Cm), p.dmT = T(k.Mm * k.Cm), p.dz_acc = F(k.Mz * k.Cz), p.dzT = T(k.Mz * k.Cz);
+    int64_t g1 = std::max<int64_t>({k.Mm * k.n * k.Cm, k.Mz * k.n * k.Cz, k.Mm * k.QKm, k.Mm * k.QKc, k.Mz * 4 * k.HCt,
+                           k.Mz * k.ABG});
+    int64_t g2 = std::max<int64_t>({k.Mm * k.Cm, k.Mz * k.Cz, k.Mm * k.HCm, k.Mz * k.HCt, k.Mm * 2 * k.co});
+    int64_t g3 = std::max<int64_t>({k.Mm * k.HCm, k.Mz * k.HCt, k.Mz * k.cmul, k.Mz * k.Cz});
+    p.G1 = T(g1), p.G2 = T(g2), p.G3 = T(g3);
+    p.dO4 = T(k.Mz * k.co * k.co);
+    p.dA = T(k.cmul * k.R * k.Rp), p.dB = T(k.cmul * k.R * k.Rp), p.dX = T(k.cmul * k.R * k.Rp);
+    p.dq_acc = F(std::max(k.Mm * k.HCm, k.Mz * k.HCt));
+    p.dbias = F(std::max(k.Hm, k.Ht) * k.Mz);
+    p.Dsum = F(std::max(k.S * k.Hm * k.R, k.R * k.Ht * k.R));
+    p.dab4 = T(k.Mm * 2 * k.co);
+    int64_t wmax = std::max<int64_t>({k.QKm * k.Cm, k.QKc * k.Cm, k.n * k.Cm * k.Cm, k.n * k.Cz * k.Cz, k.ABG * k.Cz,
+                             4 * k.HCt * k.Cz, k.Cz * k.co * k.co, k.Cm * k.HCm, 2 * k.co * k.Cm,
+                             k.Cz * k.cmul, k.Cz * k.HCt});
+    p.split = F(MAXSPLIT * wmax);
+    int64_t nmax = std::max<int64_t>({k.QKm, k.QKc, k.n * k.Cm, k.n * k.Cz, k.ABG, 4 * k.HCt, k.Cm, k.Cz});
+    p.cpart = F(512 * nmax);
+    int64_t lmax = std::max<int64_t>(1024 * 2 * std::max(k.Cm, k.Cz),
+                                     (int64_t)ln_bwd_cm_blocks((int)k.R) * 2 * k.cmul);
+    p.lpart = F(lmax);
+    p.hpart = F(1024 * std::max(k.Hm, k.Ht) * k.Cz);
+  }
+  p.total = off;
+  return off;
+}
+
+inline GemmOp mk(int64_t M, int64_t N, int64_t K, const void *A, int64_t lda, int amn, const void *B, int64_t ldb,
+                 int bmn, void *C, int64_t ldc) {
+  GemmOp g{};
+  g.M = (int)M, g.N = (int)N, g.K = (int)K, g.batch = 1;
+  g.A = A, g.lda = lda, g.a_mn = amn;
+  g.B = B, g.ldb = ldb, g.b_mn = bmn;
+  g.splits = 1;
+  g.e.C = C;
+  g.e.map = rowmajor_map(ldc);
+  g.e.alpha = 1.f;
+  g.e.act = ACT_NONE;
+  return g;
+}
+
+struct Drv {
+  const evo_dims &d;
+  Dims2 k;
+  int bf;
+  size_t ts;
+  cudaStream_t s;
+  const float *p32;
+  const bf16 *p16;
+  std::map<std::string, int64_t> off;
+  char *ws;
+  Plan pl;
+  float *dparams = nullptr;
+  cudaError_t err = cudaSuccess;
+
+  Drv(const evo_dims &d_, const float *p32_, const bf16 *p16_, void *ws_, int mode, cudaStream_t s_)
+      : d(d_), k(d_), bf(d_.act_dtype == EVO_BF16), ts(bf ? 2 : 4), s(s_), p32(p32_), p16(p16_), ws((char *)ws_) {
+    std::vector<PEntry> t;
+    build_param_table(d, t);
+    for (auto &e : t) off[e.name] = e.offset;
+    make_plan(d, mode, pl);
+  }
+  void ck(cudaError_t e) {
+    if (err == cudaSuccess && e != cudaSuccess) err = e;
+  }
+  void *B(size_t o) { return ws + o; }
+  float *Bf(size_t o) { return (float *)(ws + o); }
+  void *at(const void *base, int64_t elems) { return (char *)base + elems * (int64_t)ts; }
+  const float *P(const std::string &n) { return p32 + off.at(n); }
+  const void *W(const std::string &n) {
+    return bf ? (const void *)(p16 + off.at(n)) : (const void *)(p32 + off.at(n));
+  }
+  float *D(const std::string &n) { return dparams + off.at(n); }
+
+  void gemm(GemmOp g) {
+    g.e.M = g.M;
+    g.e.N = g.N;
+    ck(bf ? gemm_tc_bf16(g, s) : gemm_simt_f32(g, s));
+  }
+  void ln(const void *x, const std::string &pre, void *y, int64_t M, int C) {
+    ck(ln_fwd(x, P(pre + ".gamma"), P(pre + ".beta"), y, M, C, bf, s));
+  }
+
+  // ---------------- backward helpers (parameter gradients accumulate into dparams)
+  void dW(const void *dY, int64_t ldY, int64_t Nout, const void *X, int64_t ldX, int64_t Kin, int64_t rows,
+          const std::string &w) {
+    GemmOp g = mk(Nout, Kin, rows, dY, ldY, 1, X, ldX, 1, nullptr, 0);
+    const int64_t tile = bf ? 128 : 64;
+    const int64_t tiles = ((Nout + tile - 1) / tile) * ((Kin + tile - 1) / tile);
+    int64_t sp = (2 * 152 + tiles - 1) / tiles;
+    sp = std::min<int64_t>(sp, std::max<int64_t>(1, rows / 256));
+    sp = std::max<int64_t>(1, std::min<int64_t>(sp, MAXSPLIT));
+    g.splits = (int)sp;
+    g.e.partial = Bf(pl.split);
+    gemm(g);
+    ck(reduce_splits(Bf(pl.split), (int)sp, Nout * Kin, D(w), s));
+  }
+  void db(const void *dY, int64_t ldY, int64_t rows, int64_t N, const std::string &b) {
+    ck(colsum(dY, ldY, rows, (int)N, Bf(pl.cpart), bf, s));
+    ck(reduce_partials(Bf(pl.cpart), colsum_blocks(rows), (int)N, D(b), s));
+  }
+  void lnb(const void *dy, const void *x, const std::string &pre, float *dacc, void *dcopy, void *dx_out, int64_t M,
+           int C) {
+    ck(ln_bwd(dy, x, P(pre + ".gamma"), dacc, dcopy, dx_out, Bf(pl.lpart), M, C, bf, s));
+    const int nb = ln_bwd_blocks(M);
+    ck(reduce_partials_ld(Bf(pl.lpart), nb, 2 * C, C, D(pre + ".gamma"), s));
+    ck(reduce_partials_ld(Bf(pl.lpart) + C, nb, 2 * C, C, D(pre + ".beta"), s));
+  }
+
+  // ---------------- attention argument sets
+  // kind 0: MSA row (batch s, query i, key j), 1: MSA column (batch i, query s, key t),
+  //      2: triangle start (batch i, query j, key k), 3: triangle end (batch j, query i, key k)
+  AttnArgs attn_args(int kind, void *qkvg, void *oatt, void *og, float *lse, float *bias, const float *mask) {
+    AttnArgs a{};
+    const bool msa = kind < 2;
+    const int64_t H = msa ? k.Hm : k.Ht, c = msa ? k.cm : k.ct, HC = H * c, QK = 4 * HC;
+    const int64_t R = k.R, S = k.S;
+    a.q = qkvg, a.k = at(qkvg, HC), a.v = at(qkvg, 2 * HC), a.g = at(qkvg, 3 * HC);
+    a.H = (int)H, a.c = (int)c;
+    a.o_att = oatt, a.o_gate = og, a.lse2 = lse;
+    a.scale = 1.f / std::sqrt((float)c);
+    a.bias = bias;
+    a.sBh = k.Mz, a.sBx = R;
+    a.mask = mask;
+    switch (kind) {
+      case 0:
+        a.B1 = (int)S, a.X = (int)R, a.Y = (int)R;
+        a.sQb = R * QK, a.sQx = QK, a.sKb = R * QK, a.sKy = QK;
+        a.sMb = R, a.sMy = 1;
+        a.sOb = R * HC, a.sOx = HC;
+        break;
+      case 1:
+        a.B1 = (int)R, a.X = (int)S, a.Y = (int)S;
+        a.sQb = QK, a.sQx = R * QK, a.sKb = QK, a.sKy = R * QK;
+        a.sMb = 1, a.sMy = R;
+        a.sOb = HC, a.sOx = R * HC;
+        break;
+      case 2:
+        a.B1 = (int)R, a.X = (int)R, a.Y = (int)R;
+        a.sQb = R * QK, a.sQx = QK, a.sKb = R * QK, a.sKy = QK;
+        a.sMb = R, a.sMy = 1;
+        a.sOb = R * HC, a.sOx = HC;
+        break;
+      default:
+        a.B1 = (int)R, a.X = (int)R, a.Y = (int)R;
+        a.sQb = QK, a.sQx = R * QK, a.sKb = QK, a.sKy = R * QK;
+        a.sMb = 1, a.sMy = R;
+        a.sOb = HC, a.sOx = R * HC;
+        break;
+    }
+    return a;
+  }
+
+  // ================================================================ forward
+  void forward(const void *m0, const void *z0, void *m_out, void *z_out, const float *mm, const float *pm) {
+    const int64_t S = k.S, R = k.R, Cm = k.Cm, Cz = k.Cz, Mm = k.Mm, Mz = k.Mz, HCm = k.HCm, HCt = k.HCt;
+    // 1. MSA row attention with pair bias (AF2 Alg. 7)
+    ln(m0, "row.ln_m", B(pl.xm1), Mm, (int)Cm);
+    ln(z0, "row.ln_z", B(pl.xz1), Mz, (int)Cz);
+    ck(head_proj_fwd(B(pl.xz1), P("row.w_b"), Bf(pl.bias1), (int)R, (int)Cz, (int)k.Hm, 0, bf, s));
+    {
+      GemmOp g = mk(Mm, k.QKm, Cm, B(pl.xm1), Cm, 0, W("row.w_qkvg"), Cm, 0, B(pl.qkvg1), k.QKm);
+      g.e.bias = P("row.b_g"), g.e.bias_n0 = (int)(3 * HCm), g.e.act = ACT_SIGMOID, g.e.act_n0 = (int)(3 * HCm);
+      gemm(g);
+      AttnArgs a = attn_args(0, B(pl.qkvg1), B(pl.oatt1), B(pl.og1), Bf(pl.lse1), Bf(pl.bias1), mm);
+      ck(attn_fwd(a, bf, s));
+      GemmOp o = mk(Mm, Cm, HCm, B(pl.og1), HCm, 0, W("row.w_o"), HCm, 0, B(pl.m1), Cm);
+      o.e.bias = P("row.b_o"), o.e.residual = m0;
+      gemm(o);
+    }
+    // 2. MSA column attention (AF2 Alg. 8)
+    ln(B(pl.m1), "col.ln", B(pl.xm2), Mm, (int)Cm);
+    {
+      GemmOp g = mk(Mm, k.QKc, Cm, B(pl.xm2), Cm, 0, W("col.w_qkvg"), Cm, 0, B(pl.qkvg2), k.QKc);
+      g.e.bias = P("col.b_g"), g.e.bias_n0 = (int)(3 * HCm), g.e.act = ACT_SIGMOID, g.e.act_n0 = (int)(3 * HCm);
+      gemm(g);
+      AttnArgs a = attn_args(1, B(pl.qkvg2), B(pl.oatt2), B(pl.og2), Bf(pl.lse2), nullptr, mm);
+      ck(attn_fwd(a, bf, s));
+      GemmOp o = mk(Mm, Cm, HCm, B(pl.og2), HCm, 0, W("col.w_o"), HCm, 0, B(pl.m2), Cm);
+      o.e.bias = P("col.b_o"), o.e.residual = B(pl.m1);
+      gemm(o);
+    }
+    // 3. MSA transition (AF2 Alg. 9)
+    void *m3 = m_out ? m_out : B(pl.m3);
+    transition_fwd("msa_trans", B(pl.m2), B(pl.xm3), B(pl.h3), m3, Mm, Cm);
+    // 4. outer product mean (AF2 Alg. 10)
+    ln(m3, "opm.ln", B(pl.xm4), Mm, (int)Cm);
+    {
+      const int64_t co = k.co;
+      GemmOp g = mk(Mm, 2 * co, Cm, B(pl.xm4), Cm, 0, W("opm.w_ab"), Cm, 0, B(pl.ab4), 0);
+      g.e.map = OutMap{1ll << 40, 0, co, co, Mm * co, 1};  // a -> [s][i][c], b -> [s][j][d]
+      g.e.bias = P("opm.b_ab"), g.e.row_scale = mm;
+      gemm(g);
+      ck(opm_inv_norm(mm, Bf(pl.inv4), (int)S, (int)R, 1e-3f, s));
+      GemmOp o = mk(R * co, R * co, S, B(pl.ab4), R * co, 1, at(B(pl.ab4), Mm * co), R * co, 1, B(pl.O4), 0);
+      o.e.map = OutMap{co, R * co * co, co, co, co * co, 1};  // O[i][j][c*co + d]
+      gemm(o);
+      GemmOp p = mk(Mz, Cz, co * co, B(pl.O4), co * co, 0, W("opm.w_o"), co * co, 0, B(pl.z1), Cz);
+      p.e.bias = P("opm.b_o"), p.e.row_scale = Bf(pl.inv4), p.e.residual = z0;
+      gemm(p);
+    }
+    // 5, 6. triangle multiplication outgoing / incoming (AF2 Alg. 11, 12)
+    trimul_fwd(0, B(pl.z1), pm);
+    trimul_fwd(1, B(pl.tri[0].zout), pm);
+    // 7, 8. triangle attention starting / ending node (AF2 Alg. 13, 14)
+    triatt_fwd(0, B(pl.tri[1].zout), pm);
+    triatt_fwd(1, B(pl.att[0].zout), pm);
+    // 9. pair transition (AF2 Alg. 15)
+    void *z6 = z_out ? z_out : B(pl.z6);
+    transition_fwd("pair_trans", B(pl.att[1].zout), B(pl.xz9), B(pl.h9), z6, Mz, Cz);
+    (void)HCt;
+  }
+
+  void transition_fwd(const std::string &pre, const void *x, void *xn, void *h, void *out, int64_t M, int64_t C) {
+    ln(x, pre + ".ln", xn, M, (int)C);
+    const int64_t nC = k.n * C;
+    GemmOp g = mk(M, nC, C, xn, C, 0, W(pre + ".w1"), C, 0, h, nC);
+    g.e.bias = P(pre + ".b1"), g.e.act = ACT_RELU;
+    gemm(g);
+    GemmOp o = mk(M, C, nC, h, nC, 0, W(pre + ".w2"), nC, 0, out, C);
+    o.e.bias = P(pre + ".b2"), o.e.residual = x;
+    gemm(o);
+  }
+
+  void trimul_fwd(int t, const void *zin, const float *pm) {
+    const std::string pre = t == 0 ? "tri_out" : "tri_in";
+    const TriBufs &b = pl.tri[t];
+    const int64_t R = k.R, Rp = k.Rp, Cz = k.Cz, Mz = k.Mz, cmul = k.cmul, ABG = k.ABG;
+    ln(zin, pre + ".ln_in", B(b.xz), Mz, (int)Cz);
+    GemmOp g = mk(Mz, ABG, Cz, B(b.xz), Cz, 0, W(pre + ".w_abg"), Cz, 0, B(b.abg), ABG);
+    g.e.bias = P(pre + ".b_abg");
+    gemm(g);
+    ck(trimul_gate_fwd(B(b.abg), ABG, pm, B(b.A), B(b.B), Rp, (int)R, (int)cmul, (int)Cz, t, bf, s));
+    // X_c = A_c B_c^T per channel c (incoming stores A, B transposed, so the product is the same)
+    GemmOp x = mk(R, R, R, B(b.A), Rp, 0, B(b.B), Rp, 0, B(b.X), Rp);
+    x.batch = (int)cmul, x.a_bs = R * Rp, x.b_bs = R * Rp, x.e.c_bstride = R * Rp;
+    gemm(x);
+    ck(ln_fwd_cm(B(b.X), Rp, P(pre + ".ln_out.gamma"), P(pre + ".ln_out.beta"), B(b.xo), (int)R, (int)cmul, bf, s));
+    GemmOp o = mk(Mz, Cz, cmul, B(b.xo), cmul, 0, W(pre + ".w_o"), cmul, 0, B(b.zout), Cz);
+    o.e.bias = P(pre + ".b_o"), o.e.aux = B(b.y), o.e.aux_ld = Cz;
+    o.e.gate = at(B(b.abg), 4 * cmul), o.e.gate_ld = ABG, o.e.residual = zin;
+    gemm(o);
+  }
+
+  void triatt_fwd(int t, const void *zin, const float *pm) {
+    const std::string pre = t == 0 ? "att_start" : "att_end";
+    const AttBufs &b = pl.att[t];
+    const int64_t R = k.R, Cz = k.Cz, Mz = k.Mz, HCt = k.HCt;
+    ln(zin, pre + ".ln", B(b.xz), Mz, (int)Cz);
+    ck(head_proj_fwd(B(b.xz), P(pre + ".w_b"), Bf(b.bias), (int)R, (int)Cz, (int)k.Ht, t, bf, s));
+    GemmOp g = mk(Mz, 4 * HCt, Cz, B(b.xz), Cz, 0, W(pre + ".w_qkvg"), Cz, 0, B(b.qkvg), 4 * HCt);
+    g.e.bias = P(pre + ".b_g"), g.e.bias_n0 = (int)(3 * HCt), g.e.act = ACT_SIGMOID, g.e.act_n0 = (int)(3 * HCt);
+    gemm(g);
+    AttnArgs a = attn_args(2 + t, B(b.qkvg), B(b.oatt), B(b.og), Bf(b.lse), Bf(b.bias), pm);
+    ck(attn_fwd(a, bf, s));
+    GemmOp o = mk(Mz, Cz, HCt, B(b.og), HCt, 0, W(pre + ".w_o"), HCt, 0, B(b.zout), Cz);
+    o.e.bias = P(pre + ".b_o"), o.e.residual = zin;
+    gemm(o);
+  }
+
+  // ================================================================ backward
+  // dacc/dT: FP32 running gradient of the residual stream and its storage-type copy.
+  void transition_bwd(const std::string &pre, const void *x, const void *xn, const void *h, float *dacc, void *dT,
+                      int64_t M, int64_t C) {
+    const int64_t nC = k.n * C;
+    dW(dT, C, C, h, nC, nC, M, pre + ".w2");
+    db(dT, C, M, C, pre + ".b2");
+    GemmOp g = mk(M, nC, C, dT, C, 0, W(pre + ".w2"), nC, 1, B(pl.G1), nC);
+    g.e.relu_ref = h, g.e.relu_ld = nC;
+    gemm(g);
+    dW(B(pl.G1), nC, nC, xn, C, C, M, pre + ".w1");
+    db(B(pl.G1), nC, M, nC, pre + ".b1");
+    GemmOp o = mk(M, C, nC, B(pl.G1), nC, 0, W(pre + ".w1"), C, 1, B(pl.G2), C);
+    gemm(o);
+    lnb(B(pl.G2), x, pre + ".ln", dacc, dT, nullptr, M, (int)C);
+  }
+
+  // Gated attention backward down to d(LN input) in G2 (not yet through LayerNorm).
+  // Leaves dqkvg in G1 and the pair-bias gradient in dbias (when bias != null).
+  void attention_bwd(int kind, const std::string &pre, const void *xn, void *qkvg, void *oatt, void *og, float *lse,
+                     float *bias, const float *mask, const void *dT, int64_t M, int64_t Cin) {
+    const bool msa = kind < 2;
+    const int64_t HC = msa ? k.HCm : k.HCt, QK = 4 * HC;
+    dW(dT, Cin, Cin, og, HC, HC, M, pre + ".w_o");
+    db(dT, Cin, M, Cin, pre + ".b_o");
+    GemmOp g = mk(M, HC, Cin, dT, Cin, 0, W(pre + ".w_o"), HC, 1, B(pl.G2), HC);
+    gemm(g);
+    AttnArgs a = attn_args(kind, qkvg, oatt, og, lse, bias, mask);
+    a.do_att = B(pl.G3);
+    a.Dsum = Bf(pl.Dsum);
+    a.dq_acc = Bf(pl.dq_acc);
+    a.dk = at(B(pl.G1), HC);
+    a.dv = at(B(pl.G1), 2 * HC);
+    a.dbias = bias ? Bf(pl.dbias) : nullptr;
+    ck(attn_gate_bwd(a, B(pl.G2), at(B(pl.G1), 3 * HC), a.sQb, a.sQx, B(pl.G3), Bf(pl.Dsum), bf, s));
+    ck(cudaMemsetAsync(Bf(pl.dq_acc), 0, (size_t)M * HC * 4, s));
+    if (bias) ck(cudaMemsetAsync(Bf(pl.dbias), 0, (size_t)a.H * k.Mz * 4, s));
+    ck(attn_bwd(a, bf, s));
+    ck(attn_dq_store(a, B(pl.G1), bf, s));
+    dW(B(pl.G1), QK, QK, xn, Cin, Cin, M, pre + ".w_qkvg");
+    db(at(B(pl.G1), 3 * HC), QK, M, HC, pre + ".b_g");
+    GemmOp x = mk(M, Cin, QK, B(pl.G1), QK, 0, W(pre + ".w_qkvg"), Cin, 1, B(pl.G2), Cin);
+    gemm(x);
+  }
+
+  void pair_bias_bwd(const std::string &wname, const void *xn, int H, int transpose, int accumulate) {
+    ck(head_proj_bwd(Bf(pl.dbias), xn, P(wname), B(pl.G2), accumulate, Bf(pl.hpart), (int)k.R, (int)k.Cz, H,
+                     transpose, bf, s));
+    ck(reduce_partials(Bf(pl.hpart), head_proj_blocks((int)k.R), H * (int)k.Cz, D(wname), s));
+  }
+
+  void trimul_bwd(int t, const void *zin, const float *pm, float *dacc, void *dT) {
+    const std::string pre = t == 0 ? "tri_out" : "tri_in";
+    const TriBufs &b = pl.tri[t];
+    const int64_t R = k.R, Rp = k.Rp, Cz = k.Cz, Mz = k.Mz, cmul = k.cmul, ABG = k.ABG;
+    ck(gate_out_bwd(dT, at(B(b.abg), 4 * cmul), ABG, B(b.y), B(pl.G2), at(B(pl.G1), 4 * cmul), ABG, Mz, (int)Cz, bf, s));
+    dW(B(pl.G2), Cz, Cz, B(b.xo), cmul, cmul, Mz, pre + ".w_o");
+    db(B(pl.G2), Cz, Mz, Cz, pre + ".b_o");
+    GemmOp g = mk(Mz, cmul, Cz, B(pl.G2), Cz, 0, W(pre + ".w_o"), cmul, 1, B(pl.G3), cmul);
+    gemm(g);
+    ck(ln_bwd_cm(B(pl.G3), B(b.X), Rp, P(pre + ".ln_out.gamma"), B(pl.dX), Bf(pl.lpart), (int)R, (int)cmul, bf, s));
+    {
+      const int nb = ln_bwd_cm_blocks((int)R);
+      ck(reduce_partials_ld(Bf(pl.lpart), nb, 2 * cmul, (int)cmul, D(pre + ".ln_out.gamma"), s));
+      ck(reduce_partials_ld(Bf(pl.lpart) + cmul, nb, 2 * cmul, (int)cmul, D(pre + ".ln_out.beta"), s));
+    }
+    // dA_c = dX_c B_c ; dB_c = dX_c^T A_c
+    GemmOp ga = mk(R, R, R, B(pl.dX), Rp, 0, B(b.B), Rp, 1, B(pl.dA), Rp);
+    ga.batch = (int)cmul, ga.a_bs = R * Rp, ga.b_bs = R * Rp, ga.e.c_bstride = R * Rp;
+    gemm(ga);
+    GemmOp gb = mk(R, R, R, B(pl.dX), Rp, 1, B(b.A), Rp, 1, B(pl.dB), Rp);
+    gb.batch = (int)cmul, gb.a_bs = R * Rp, gb.b_bs = R * Rp, gb.e.c_bstride = R * Rp;
+    gemm(gb);
+    ck(trimul_gate_bwd(B(pl.dA), B(pl.dB), Rp, B(b.abg), ABG, pm, B(pl.G1), (int)R, (int)cmul, t, bf, s));
+    dW(B(pl.G1), ABG, ABG, B(b.xz), Cz, Cz, Mz, pre + ".w_abg");
+    db(B(pl.G1), ABG, Mz, ABG, pre + ".b_abg");
+    GemmOp x = mk(Mz, Cz, ABG, B(pl.G1), ABG, 0, W(pre + ".w_abg"), Cz, 1, B(pl.G2), Cz);
+    gemm(x);
+    lnb(B(pl.G2), zin, pre + ".ln_in", dacc, dT, nullptr, Mz, (int)Cz);
+  }
+
+  void backward(const void *m0, const void *z0, const float *mm, const float *pm, const void *dm_out,
+                const void *dz_out, void *dm_in, void *dz_in) {
+    const int64_t S = k.S, R = k.R, Cm = k.Cm, Cz = k.Cz, Mm = k.Mm, Mz = k.Mz, co = k.co;
+    float *dm = Bf(pl.dm_acc), *dz = Bf(pl.dz_acc);
+    void *dmT = B(pl.dmT), *dzT = B(pl.dzT);
+    ck(to_f32(dm_out, dm, Mm * Cm, bf, s));
+    ck(to_f32(dz_out, dz, Mz * Cz, bf, s));
+    ck(cudaMemcpyAsync(dmT, dm_out, (size_t)Mm * Cm * ts, cudaMemcpyDeviceToDevice, s));
+    ck(cudaMemcpyAsync(dzT, dz_out, (size_t)Mz * Cz * ts, cudaMemcpyDeviceToDevice, s));
+
+    // 9. pair transition
+    transition_bwd("pair_trans", B(pl.att[1].zout), B(pl.xz9), B(pl.h9), dz, dzT, Mz, Cz);
+    // 8, 7. triangle attention ending / starting node
+    for (int t = 1; t >= 0; --t) {
+      const AttBufs &b = pl.att[t];
+      const std::string pre = t == 0 ? "att_start" : "att_end";
+      const void *zin = t == 0 ? B(pl.tri[1].zout) : B(pl.att[0].zout);
+      attention_bwd(2 + t, pre, B(b.xz), B(b.qkvg), B(b.oatt), B(b.og), Bf(b.lse), Bf(b.bias), pm, dzT, Mz, Cz);
+      pair_bias_bwd(pre + ".w_b", B(b.xz), (int)k.Ht, t, 1);
+      lnb(B(pl.G2), zin, pre + ".ln", dz, dzT, nullptr, Mz, (int)Cz);
+    }
+    // 6, 5. triangle multiplication incoming / outgoing
+    trimul_bwd(1, B(pl.tri[0].zout), pm, dz, dzT);
+    trimul_bwd(0, B(pl.z1), pm, dz, dzT);
+    // 4. outer product mean
+    {
+      ck(row_scale(dzT, Bf(pl.inv4), B(pl.G2), Mz, (int)Cz, bf, s));
+      dW(B(pl.G2), Cz, Cz, B(pl.O4), co * co, co * co, Mz, "opm.w_o");
+      db(B(pl.G2), Cz, Mz, Cz, "opm.b_o");
+      // dO laid out [i][c][j][d] so both contractions below read it as a plain matrix
+      GemmOp g = mk(Mz, co * co, Cz, B(pl.G2), Cz, 0, W("opm.w_o"), co * co, 1, B(pl.dO4), 0);
+      g.e.map = OutMap{R, co * R * co, co, co, R * co, 1};
+      gemm(g);
+      // da[s][(i,c)] = sum_(j,d) b[s][(j,d)] dO[(i,c)][(j,d)]
+      GemmOp ga = mk(S, R * co, R * co, at(B(pl.ab4), Mm * co), R * co, 0, B(pl.dO4), R * co, 0, B(pl.dab4), 0);
+      ga.e.map = OutMap{1ll << 40, 0, R * 2 * co, co, 2 * co, 1};
+      gemm(ga);
+      // db[s][(j,d)] = sum_(i,c) a[s][(i,c)] dO[(i,c)][(j,d)]
+      GemmOp gb = mk(S, R * co, R * co, B(pl.ab4), R * co, 0, B(pl.dO4), R * co, 1, at(B(pl.dab4), co), 0);
+      gb.e.map = OutMap{1ll << 40, 0, R * 2 * co, co, 2 * co, 1};
+      gemm(gb);
+      ck(row_scale(B(pl.dab4), mm, B(pl.dab4), Mm, (int)(2 * co), bf, s));
+      dW(B(pl.dab4), 2 * co, 2 * co, B(pl.xm4), Cm, Cm, Mm, "opm.w_ab");
+      db(B(pl.dab4), 2 * co, Mm, 2 * co, "opm.b_ab");
+      GemmOp x = mk(Mm, Cm, 2 * co, B(pl.dab4), 2 * co, 0, W("opm.w_ab"), Cm, 1, B(pl.G2), Cm);
+      gemm(x);
+      lnb(B(pl.G2), B(pl.m3), "opm.ln", dm, dmT, nullptr, Mm, (int)Cm);
+    }
+    // 3. MSA transition
+    transition_bwd("msa_trans", B(pl.m2), B(pl.xm3), B(pl.h3), dm, dmT, Mm, Cm);
+    // 2. MSA column attention
+    attention_bwd(1, "col", B(pl.xm2), B(pl.qkvg2), B(pl.oatt2), B(pl.og2), Bf(pl.lse2), nullptr, mm, dmT, Mm, Cm);
+    lnb(B(pl.G2), B(pl.m1), "col.ln", dm, dmT, nullptr, Mm, (int)Cm);
+    // 1. MSA row attention with pair bias
+    attention_bwd(0, "row", B(pl.xm1), B(pl.qkvg1), B(pl.oatt1), B(pl.og1), Bf(pl.lse1), Bf(pl.bias1), mm, dmT, Mm,
+                  Cm);
+    lnb(B(pl.G2), m0, "row.ln_m", dm, nullptr, nullptr, Mm, (int)Cm);
+    pair_bias_bwd("row.w_b", B(pl.xz1), (int)k.Hm, 0, 0);
+    lnb(B(pl.G2), z0, "row.ln_z", dz, nullptr, nullptr, Mz, (int)Cz);
+
+    ck(from_f32(dm, dm_in, Mm * Cm, bf, s));
+    ck(from_f32(dz, dz_in, Mz * Cz, bf, s));
+  }
+};
+
+}  // namespace
+
+size_t workspace_bytes(const evo_dims &d, int mode) {
+  Plan p;
+  return make_plan(d, mode, p);
+}
+
+int block_forward(const evo_dims &d, const float *p32, const bf16 *p16, const void *m_in, const void *z_in,
+                  void *m_out, void *z_out, const float *msa_mask, const float *pair_mask, void *ws, size_t ws_bytes,
+                  cudaStream_t s) {
+  Drv drv(d, p32, p16, ws, EVO_MODE_FWD, s);
+  if (ws_bytes < drv.pl.total) return EVO_ERR_WORKSPACE;
+  drv.forward(m_in, z_in, m_out, z_out, msa_mask, pair_mask);
+  return drv.err == cudaSuccess ? EVO_OK : EVO_ERR_CUDA;
+}
+
+int block_backward(const evo_dims &d, const float *p32, const bf16 *p16, const void *m_in, const void *z_in,
+                   const float *msa_mask, const float *pair_mask, const void *dm_out, const void *dz_out, void *dm_in,
+                   void *dz_in, float *dparams, void *ws, size_t ws_bytes, cudaStream_t s) {
+  Drv drv(d, p32, p16, ws, EVO_MODE_BWD, s);
+  if (ws_bytes < drv.pl.total) return EVO_ERR_WORKSPACE;
+  drv.dparams = dparams;
+  drv.forward(m_in, z_in, nullptr, nullptr, msa_mask, pair_mask);
+  drv.backward(m_in, z_in, msa_mask, pair_mask, dm_out, dz_out, dm_in, dz_in);
+  return drv.err == cudaSuccess ? EVO_OK : EVO_ERR_CUDA;
+}
+
+}  // namespace evo

@@ -1,0 +1,36 @@
+// Internal: parameter table, workspace plan and block drivers of libevo.
+#pragma once
+#include <string>
+#include <vector>
+
+#include "evo.h"
+#include "kernels.h"
+
+namespace evo {
+
+struct PEntry {
+  std::string name;
+  int64_t offset;  // floats
+  int ndim;
+  int64_t shape[4];
+};
+
+// The flat parameter buffer of one block (256-byte aligned tensors). Returns
+// the padded total in floats.
+int64_t build_param_table(const evo_dims &d, std::vector<PEntry> &out);
+
+// 0 if the dims are implemented, else an EVO_ERR_* code.
+int validate_dims(const evo_dims *d);
+
+// Workspace bytes of forward (save_for_bwd = 0) or backward.
+size_t workspace_bytes(const evo_dims &d, int mode);
+
+int block_forward(const evo_dims &d, const float *p32, const bf16 *p16, const void *m_in, const void *z_in,
+                  void *m_out, void *z_out, const float *msa_mask, const float *pair_mask, void *ws, size_t ws_bytes,
+                  cudaStream_t s);
+
+int block_backward(const evo_dims &d, const float *p32, const bf16 *p16, const void *m_in, const void *z_in,
+                   const float *msa_mask, const float *pair_mask, const void *dm_out, const void *dz_out, void *dm_in,
+                   void *dz_in, float *dparams, void *ws, size_t ws_bytes, cudaStream_t s);
+
+}  // namespace evo

@@ -1,0 +1,147 @@
+// Internal launch interface of libevo's kernels (host side).
+#pragma once
+#include "common.cuh"
+
+namespace evo {
+
+// C = epilogue( sum_k A(m,k) B(n,k) ), batched over blockIdx.z.
+//   A(m,k) = A[b*a_bs + m*lda + k]   (a_mn = 0, "K-major")
+//          = A[b*a_bs + k*lda + m]   (a_mn = 1, "MN-major")
+//   B(n,k) likewise with ldb, b_bs, b_mn.
+// With splits > 1 (batch must be 1) each split writes e.partial and the caller
+// reduces the partials (reduce_splits).
+struct GemmOp {
+  int M, N, K, batch;
+  const void *A;
+  int64_t lda, a_bs;
+  int a_mn;
+  const void *B;
+  int64_t ldb, b_bs;
+  int b_mn;
+  Epi e;
+  int splits;
+};
+
+// SIMT FP32 GEMM (the plain path; no tensor cores).
+cudaError_t gemm_simt_f32(const GemmOp &g, cudaStream_t s);
+// tcgen05 + TMA BF16 GEMM (FP32 accumulation in tensor memory).
+cudaError_t gemm_tc_bf16(const GemmOp &g, cudaStream_t s);
+// Query whether gemm_tc_bf16 accepts the operand strides/alignment.
+bool gemm_tc_supported(const GemmOp &g);
+// Reads and clears the device error word (EVO_OK or EVO_ERR_TIMEOUT); synchronous.
+cudaError_t error_word_read_clear(int *out);
+// Launches one CTA whose bounded mbarrier wait is made to run out after limit_ns.
+cudaError_t debug_wait(int64_t limit_ns, cudaStream_t s);
+
+// Attention over one axis with optional pair bias, key mask and sigmoid gate.
+// Batch b in [0,B1), head h, query x in [0,X), key y in [0,Y), head dim c.
+//   q(b,x,h,:) = q[b*sQb + x*sQx + h*c + :]   g shares q's strides
+//   k(b,y,h,:) = k[b*sKb + y*sKy + h*c + :]   v shares k's strides
+//   bias(h,x,y) = bias[h*sBh + x*sBx + y]     (fp32, may be null)
+//   key valid   = mask[b*sMb + y*sMy] != 0    (fp32, may be null)
+//   o(b,x,h,:) at o_att/o_gate[b*sOb + x*sOx + h*c + :]
+//   lse2[(b*H + h)*X + x] = log2 of the softmax normaliser (+inf: no valid key)
+struct AttnArgs {
+  const void *q, *k, *v, *g;
+  int64_t sQb, sQx, sKb, sKy;
+  int B1, H, X, Y, c;
+  const float *bias;
+  int64_t sBh, sBx;
+  const float *mask;
+  int64_t sMb, sMy;
+  void *o_att, *o_gate;
+  int64_t sOb, sOx;
+  float *lse2;
+  float scale;
+  // backward
+  const void *do_att;    // grad of the ungated output, o_att's strides
+  const float *Dsum;     // [(b*H+h)*X + x] = sum_d do_att * o_att
+  float *dq_acc;         // fp32 [b*sOb + x*sOx + h*c + d] accumulated (unscaled)
+  void *dk, *dv;         // k/v strides
+  float *dbias;          // fp32 [h*sBh + x*sBx + y] accumulated
+};
+cudaError_t attn_fwd(const AttnArgs &a, int use_bf16, cudaStream_t s);
+cudaError_t attn_bwd(const AttnArgs &a, int use_bf16, cudaStream_t s);
+
+// Global column attention (extra-MSA stack): single-head k, v.
+struct GlobalAttnArgs {
+  const void *qkvg;  // rows (s,i) of width ld: [q (H*c) | k (c) | v (c) | g (H*c)]
+  int64_t ld;
+  int S, R, H, c;
+  const float *mask;  // [S,R]
+  void *o_att_bar;    // [R, H*c] fp32 attention output per column (before gate)
+  float *qbar;        // [R, H*c] fp32
+  float *lse2;        // [R, H]
+  void *o_gate;       // [S,R,H*c]
+  float scale;
+};
+cudaError_t global_attn_fwd(const GlobalAttnArgs &a, int use_bf16, cudaStream_t s);
+// backward: dog [S,R,H*c] grad of gated output -> dqkvg rows (same layout as qkvg)
+cudaError_t global_attn_bwd(const GlobalAttnArgs &a, const void *dog, void *dqkvg, float *scratch,
+                            int use_bf16, cudaStream_t s);
+
+// LayerNorm over channels of rows x[M, C] (eps 1e-5, biased variance).
+cudaError_t ln_fwd(const void *x, const float *gamma, const float *beta, void *y, int64_t M, int C,
+                   int use_bf16, cudaStream_t s);
+// LayerNorm of a channel-major tensor x[C][R][pitch] (position p = (i,j) at i*pitch+j)
+// written row-major y[R*R, C].
+cudaError_t ln_fwd_cm(const void *x, int64_t pitch, const float *gamma, const float *beta, void *y,
+                      int R, int C, int use_bf16, cudaStream_t s);
+// dx = LN backward of dy (rows x[M,C]); dacc (fp32) += dx if dacc else dx_out = dx;
+// dcopy (activation type, may be null) = updated dacc; partial sums of dgamma, dbeta
+// go to part[blk][2C] (blocks = ln_bwd_blocks(M)).
+int ln_bwd_blocks(int64_t M);
+cudaError_t ln_bwd(const void *dy, const void *x, const float *gamma, float *dacc, void *dcopy,
+                   void *dx_out, float *part, int64_t M, int C, int use_bf16, cudaStream_t s);
+// LayerNorm backward for the channel-major input of ln_fwd_cm: dy row-major [R*R, C],
+// dx channel-major [C][R][pitch].
+int ln_bwd_cm_blocks(int R);
+cudaError_t ln_bwd_cm(const void *dy, const void *x, int64_t pitch, const float *gamma, void *dx,
+                      float *part, int R, int C, int use_bf16, cudaStream_t s);
+
+// Sum of partial rows: out[n] += sum_b part[b*N + n], n < N.
+cudaError_t reduce_partials(const float *part, int nblk, int N, float *out, cudaStream_t s);
+// out[n] += sum_b part[b*ld + n]
+cudaError_t reduce_partials_ld(const float *part, int nblk, int64_t ld, int N, float *out, cudaStream_t s);
+// Column sums of x[M, N] (leading dim ld, activation type) into part[blk][N].
+int colsum_blocks(int64_t M);
+cudaError_t colsum(const void *x, int64_t ld, int64_t M, int N, float *part, int use_bf16, cudaStream_t s);
+// out[i] += sum_s part[s*n + i]
+cudaError_t reduce_splits(const float *part, int splits, int64_t n, float *out, cudaStream_t s);
+
+// Pair-bias projection: out[h][pos'] = x[pos] . w[h], pos = (p0,p1) in [R,R];
+// pos' = p0*R+p1, or p1*R+p0 with transpose.
+cudaError_t head_proj_fwd(const void *x, const float *w, float *out, int R, int C, int H, int transpose,
+                          int use_bf16, cudaStream_t s);
+// dx[pos] (+)= sum_h dbias[h][pos'] w[h]; dw partials part[blk][H*C].
+int head_proj_blocks(int R);
+cudaError_t head_proj_bwd(const float *dbias, const void *x, const float *w, void *dx, int accumulate,
+                          float *part, int R, int C, int H, int transpose, int use_bf16, cudaStream_t s);
+
+// Triangle multiplication gating: abg[P, ld] raw projections [ap|ag|bp|bg|g];
+// a,b written channel-major [c][R][pitch] (incoming: transposed positions);
+// g columns replaced by sigmoid(g) in place.
+cudaError_t trimul_gate_fwd(void *abg, int64_t ld, const float *mask, void *A, void *B, int64_t pitch,
+                            int R, int cm, int cz, int incoming, int use_bf16, cudaStream_t s);
+cudaError_t trimul_gate_bwd(const void *dA, const void *dB, int64_t pitch, const void *abg, int64_t ld,
+                            const float *mask, void *dabg, int R, int cm, int incoming, int use_bf16,
+                            cudaStream_t s);
+// Output gate backward: dy = dz * g; dgpre = dz * y * g (1 - g).
+cudaError_t gate_out_bwd(const void *dz, const void *g, int64_t g_ld, const void *y, void *dy,
+                         void *dgpre, int64_t dg_ld, int64_t P, int C, int use_bf16, cudaStream_t s);
+// Attention gate backward: do_att = dog * g; dgpre = dog * o_att * g (1-g);
+// D[(b*H+h)*X+x] = sum_d do_att * o_att.  Rows follow AttnArgs strides.
+cudaError_t attn_gate_bwd(const AttnArgs &a, const void *dog, void *dgpre, int64_t sGb_d, int64_t sGx_d,
+                          void *do_att, float *D, int use_bf16, cudaStream_t s);
+// dq (activation type, q strides of dst) = scale * dq_acc
+cudaError_t attn_dq_store(const AttnArgs &a, void *dq, int use_bf16, cudaStream_t s);
+// inv_norm[i*R+j] = 1 / (eps + sum_s mask[s,i] mask[s,j])
+cudaError_t opm_inv_norm(const float *mask, float *inv_norm, int S, int R, float eps, cudaStream_t s);
+// y[m, :] = x[m, :] * scale[m]   (x, y activation type; rows of width C)
+cudaError_t row_scale(const void *x, const float *scale, void *y, int64_t M, int C, int use_bf16, cudaStream_t s);
+// dst = (float) src  and  dst = (T) src conversions; fill.
+cudaError_t to_f32(const void *src, float *dst, int64_t n, int use_bf16, cudaStream_t s);
+cudaError_t from_f32(const float *src, void *dst, int64_t n, int use_bf16, cudaStream_t s);
+cudaError_t f32_to_bf16(const float *src, bf16 *dst, int64_t n, cudaStream_t s);
+
+}  // namespace evo

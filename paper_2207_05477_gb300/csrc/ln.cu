@@ -1,0 +1,271 @@
+// LayerNorm over the channel axis (AlphaFold2 LayerNorm: biased variance,
+// eps 1e-5), FP32 statistics, warp-shuffle reductions: one warp per row.
+// The channel-major variants serve the triangle-multiplication output, whose
+// per-channel batched product is laid out [c][i][j].
+#include "kernels.h"
+
+namespace evo {
+namespace {
+
+constexpr float LN_EPS = 1e-5f;
+
+template <typename T, int CPL>
+__global__ void __launch_bounds__(256) ln_fwd_rows(const T *x, const float *gamma, const float *beta, T *y,
+                                                   int64_t M, int C) {
+  const int lane = threadIdx.x & 31;
+  const int64_t row = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+  if (row >= M) return;
+  const T *xr = x + row * C;
+  float v[CPL > 0 ? CPL : 1];
+  float s = 0.f;
+  if (CPL > 0) {
+#pragma unroll
+    for (int j = 0; j < CPL; ++j) {
+      v[j] = ldf(xr + lane + 32 * j);
+      s += v[j];
+    }
+    const float mu = warp_sum(s) / C;
+    float q = 0.f;
+#pragma unroll
+    for (int j = 0; j < CPL; ++j) q += (v[j] - mu) * (v[j] - mu);
+    const float rstd = rsqrtf(warp_sum(q) / C + LN_EPS);
+#pragma unroll
+    for (int j = 0; j < CPL; ++j) {
+      const int cc = lane + 32 * j;
+      stf(y + row * C + cc, (v[j] - mu) * rstd * gamma[cc] + beta[cc]);
+    }
+  } else {
+    for (int cc = lane; cc < C; cc += 32) s += ldf(xr + cc);
+    const float mu = warp_sum(s) / C;
+    float q = 0.f;
+    for (int cc = lane; cc < C; cc += 32) {
+      const float d = ldf(xr + cc) - mu;
+      q += d * d;
+    }
+    const float rstd = rsqrtf(warp_sum(q) / C + LN_EPS);
+    for (int cc = lane; cc < C; cc += 32) stf(y + row * C + cc, (ldf(xr + cc) - mu) * rstd * gamma[cc] + beta[cc]);
+  }
+}
+
+// dx = rstd * (gdy - mean(gdy) - xhat * mean(gdy * xhat)), gdy = gamma * dy.
+template <typename T>
+__global__ void __launch_bounds__(256) ln_bwd_rows(const T *dy, const T *x, const float *gamma, float *dacc, T *dcopy,
+                                                   T *dx_out, float *part, int64_t M, int C, int64_t rows_per_blk) {
+  extern __shared__ float sh[];  // [8][2C]
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  float *mine = sh + warp * 2 * C;
+  for (int cc = lane; cc < 2 * C; cc += 32) mine[cc] = 0.f;
+  const int64_t r0 = (int64_t)blockIdx.x * rows_per_blk;
+  const int64_t r1 = min(M, r0 + rows_per_blk);
+  for (int64_t row = r0 + warp; row < r1; row += 8) {
+    const T *xr = x + row * C;
+    const T *dyr = dy + row * C;
+    float s = 0.f;
+    for (int cc = lane; cc < C; cc += 32) s += ldf(xr + cc);
+    const float mu = warp_sum(s) / C;
+    float q = 0.f;
+    for (int cc = lane; cc < C; cc += 32) {
+      const float d = ldf(xr + cc) - mu;
+      q += d * d;
+    }
+    const float rstd = rsqrtf(warp_sum(q) / C + LN_EPS);
+    float a1 = 0.f, a2 = 0.f;
+    for (int cc = lane; cc < C; cc += 32) {
+      const float xh = (ldf(xr + cc) - mu) * rstd;
+      const float g = ldf(dyr + cc);
+      const float gd = g * gamma[cc];
+      a1 += gd;
+      a2 += gd * xh;
+      mine[cc] += g * xh;
+      mine[C + cc] += g;
+    }
+    a1 = warp_sum(a1) / C;
+    a2 = warp_sum(a2) / C;
+    for (int cc = lane; cc < C; cc += 32) {
+      const float xh = (ldf(xr + cc) - mu) * rstd;
+      const float gd = ldf(dyr + cc) * gamma[cc];
+      const float dx = rstd * (gd - a1 - xh * a2);
+      if (dacc) {
+        const float nv = dacc[row * C + cc] + dx;
+        dacc[row * C + cc] = nv;
+        if (dcopy) stf(dcopy + row * C + cc, nv);
+      } else {
+        stf(dx_out + row * C + cc, dx);
+      }
+    }
+  }
+  __syncthreads();
+  for (int cc = threadIdx.x; cc < 2 * C; cc += blockDim.x) {
+    float t = 0.f;
+    for (int w = 0; w < 8; ++w) t += sh[w * 2 * C + cc];
+    part[(int64_t)blockIdx.x * 2 * C + cc] = t;
+  }
+}
+
+// Channel-major input: block = 32 consecutive j of one row i.
+template <typename T>
+__global__ void __launch_bounds__(256) ln_fwd_cm_k(const T *x, int64_t pitch, const float *gamma, const float *beta,
+                                                   T *y, int R, int C) {
+  extern __shared__ float tile[];  // [C][33]
+  const int i = blockIdx.y, j0 = blockIdx.x * 32;
+  const int64_t plane = (int64_t)R * pitch;
+  for (int idx = threadIdx.x; idx < C * 32; idx += blockDim.x) {
+    const int cc = idx >> 5, jj = idx & 31;
+    tile[cc * 33 + jj] = (j0 + jj < R) ? ldf(x + cc * plane + (int64_t)i * pitch + j0 + jj) : 0.f;
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int jj = warp; jj < 32; jj += 8) {
+    if (j0 + jj >= R) break;
+    float s = 0.f;
+    for (int cc = lane; cc < C; cc += 32) s += tile[cc * 33 + jj];
+    const float mu = warp_sum(s) / C;
+    float q = 0.f;
+    for (int cc = lane; cc < C; cc += 32) {
+      const float d = tile[cc * 33 + jj] - mu;
+      q += d * d;
+    }
+    const float rstd = rsqrtf(warp_sum(q) / C + LN_EPS);
+    const int64_t p = (int64_t)i * R + j0 + jj;
+    for (int cc = lane; cc < C; cc += 32)
+      stf(y + p * C + cc, (tile[cc * 33 + jj] - mu) * rstd * gamma[cc] + beta[cc]);
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) ln_bwd_cm_k(const T *dy, const T *x, int64_t pitch, const float *gamma, T *dx,
+                                                   float *part, int R, int C) {
+  extern __shared__ float sm[];  // xt [C][33], dxt [C][33], acc [8][2C]
+  float *xt = sm;
+  float *dxt = sm + C * 33;
+  float *acc = sm + 2 * C * 33;
+  const int i = blockIdx.y, j0 = blockIdx.x * 32;
+  const int64_t plane = (int64_t)R * pitch;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int idx = threadIdx.x; idx < C * 32; idx += blockDim.x) {
+    const int cc = idx >> 5, jj = idx & 31;
+    xt[cc * 33 + jj] = (j0 + jj < R) ? ldf(x + cc * plane + (int64_t)i * pitch + j0 + jj) : 0.f;
+  }
+  float *mine = acc + warp * 2 * C;
+  for (int cc = lane; cc < 2 * C; cc += 32) mine[cc] = 0.f;
+  __syncthreads();
+  for (int jj = warp; jj < 32; jj += 8) {
+    if (j0 + jj >= R) {
+      for (int cc = lane; cc < C; cc += 32) dxt[cc * 33 + jj] = 0.f;
+      continue;
+    }
+    float s = 0.f;
+    for (int cc = lane; cc < C; cc += 32) s += xt[cc * 33 + jj];
+    const float mu = warp_sum(s) / C;
+    float q = 0.f;
+    for (int cc = lane; cc < C; cc += 32) {
+      const float d = xt[cc * 33 + jj] - mu;
+      q += d * d;
+    }
+    const float rstd = rsqrtf(warp_sum(q) / C + LN_EPS);
+    const int64_t p = (int64_t)i * R + j0 + jj;
+    float a1 = 0.f, a2 = 0.f;
+    for (int cc = lane; cc < C; cc += 32) {
+      const float xh = (xt[cc * 33 + jj] - mu) * rstd;
+      const float g = ldf(dy + p * C + cc);
+      const float gd = g * gamma[cc];
+      a1 += gd;
+      a2 += gd * xh;
+      mine[cc] += g * xh;
+      mine[C + cc] += g;
+    }
+    a1 = warp_sum(a1) / C;
+    a2 = warp_sum(a2) / C;
+    for (int cc = lane; cc < C; cc += 32) {
+      const float xh = (xt[cc * 33 + jj] - mu) * rstd;
+      const float gd = ldf(dy + p * C + cc) * gamma[cc];
+      dxt[cc * 33 + jj] = rstd * (gd - a1 - xh * a2);
+    }
+  }
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < C * 32; idx += blockDim.x) {
+    const int cc = idx >> 5, jj = idx & 31;
+    if (j0 + jj < R) stf(dx + cc * plane + (int64_t)i * pitch + j0 + jj, dxt[cc * 33 + jj]);
+  }
+  const int64_t blk = (int64_t)blockIdx.y * gridDim.x + blockIdx.x;
+  for (int cc = threadIdx.x; cc < 2 * C; cc += blockDim.x) {
+    float t = 0.f;
+    for (int w = 0; w < 8; ++w) t += acc[w * 2 * C + cc];
+    part[blk * 2 * C + cc] = t;
+  }
+}
+
+template <typename T>
+cudaError_t ln_fwd_t(const void *x, const float *gamma, const float *beta, void *y, int64_t M, int C, cudaStream_t s) {
+  const dim3 grid((unsigned)((M + 7) / 8));
+  const T *xx = (const T *)x;
+  T *yy = (T *)y;
+  switch (C) {
+    case 64: ln_fwd_rows<T, 2><<<grid, 256, 0, s>>>(xx, gamma, beta, yy, M, C); break;
+    case 128: ln_fwd_rows<T, 4><<<grid, 256, 0, s>>>(xx, gamma, beta, yy, M, C); break;
+    case 256: ln_fwd_rows<T, 8><<<grid, 256, 0, s>>>(xx, gamma, beta, yy, M, C); break;
+    default: ln_fwd_rows<T, 0><<<grid, 256, 0, s>>>(xx, gamma, beta, yy, M, C); break;
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+int ln_bwd_blocks(int64_t M) {
+  int64_t b = (M + 63) / 64;
+  return (int)(b < 1024 ? (b < 1 ? 1 : b) : 1024);
+}
+int ln_bwd_cm_blocks(int R) { return R * ((R + 31) / 32); }
+
+cudaError_t ln_fwd(const void *x, const float *gamma, const float *beta, void *y, int64_t M, int C, int use_bf16,
+                   cudaStream_t s) {
+  if (M <= 0) return cudaSuccess;
+  return use_bf16 ? ln_fwd_t<bf16>(x, gamma, beta, y, M, C, s) : ln_fwd_t<float>(x, gamma, beta, y, M, C, s);
+}
+
+cudaError_t ln_fwd_cm(const void *x, int64_t pitch, const float *gamma, const float *beta, void *y, int R, int C,
+                      int use_bf16, cudaStream_t s) {
+  if (R <= 0) return cudaSuccess;
+  dim3 grid((R + 31) / 32, R);
+  const size_t sm = (size_t)C * 33 * sizeof(float);
+  if (use_bf16)
+    ln_fwd_cm_k<bf16><<<grid, 256, sm, s>>>((const bf16 *)x, pitch, gamma, beta, (bf16 *)y, R, C);
+  else
+    ln_fwd_cm_k<float><<<grid, 256, sm, s>>>((const float *)x, pitch, gamma, beta, (float *)y, R, C);
+  return cudaGetLastError();
+}
+
+cudaError_t ln_bwd(const void *dy, const void *x, const float *gamma, float *dacc, void *dcopy, void *dx_out,
+                   float *part, int64_t M, int C, int use_bf16, cudaStream_t s) {
+  if (M <= 0) return cudaSuccess;
+  const int nb = ln_bwd_blocks(M);
+  const int64_t rpb = (M + nb - 1) / nb;
+  const size_t sm = (size_t)8 * 2 * C * sizeof(float);
+  if (use_bf16)
+    ln_bwd_rows<bf16><<<nb, 256, sm, s>>>((const bf16 *)dy, (const bf16 *)x, gamma, dacc, (bf16 *)dcopy,
+                                          (bf16 *)dx_out, part, M, C, rpb);
+  else
+    ln_bwd_rows<float><<<nb, 256, sm, s>>>((const float *)dy, (const float *)x, gamma, dacc, (float *)dcopy,
+                                           (float *)dx_out, part, M, C, rpb);
+  return cudaGetLastError();
+}
+
+cudaError_t ln_bwd_cm(const void *dy, const void *x, int64_t pitch, const float *gamma, void *dx, float *part, int R,
+                      int C, int use_bf16, cudaStream_t s) {
+  if (R <= 0) return cudaSuccess;
+  dim3 grid((R + 31) / 32, R);
+  const size_t sm = ((size_t)2 * C * 33 + (size_t)8 * 2 * C) * sizeof(float);
+  if (sm > 48 * 1024) {
+    cudaError_t e = use_bf16 ? cudaFuncSetAttribute(ln_bwd_cm_k<bf16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)
+                         : cudaFuncSetAttribute(ln_bwd_cm_k<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+  }
+  if (use_bf16)
+    ln_bwd_cm_k<bf16><<<grid, 256, sm, s>>>((const bf16 *)dy, (const bf16 *)x, pitch, gamma, (bf16 *)dx, part, R, C);
+  else
+    ln_bwd_cm_k<float><<<grid, 256, sm, s>>>((const float *)dy, (const float *)x, pitch, gamma, (float *)dx, part, R,
+                                             C);
+  return cudaGetLastError();
+}
+
+}  // namespace evo

@@ -1,0 +1,410 @@
+// Bandwidth-bound helpers of the Evoformer block: pair-bias projection,
+// triangle-multiplication gating (with the [c][i][k] relayout the per-channel
+// product needs), gate backwards, outer-product-mean normaliser, column sums
+// and partial reductions, dtype conversions.
+#include "kernels.h"
+
+namespace evo {
+namespace {
+
+// ------------------------------------------------------------- reductions
+__global__ void reduce_partials_k(const float *part, int nblk, int64_t ld, int N, float *out) {
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= N) return;
+  float t = 0.f;
+  for (int b = 0; b < nblk; ++b) t += part[(int64_t)b * ld + n];
+  out[n] += t;
+}
+
+template <typename T>
+__global__ void colsum_k(const T *x, int64_t ld, int64_t M, int N, float *part, int64_t rows_per_blk) {
+  const int64_t r0 = (int64_t)blockIdx.x * rows_per_blk;
+  const int64_t r1 = min(M, r0 + rows_per_blk);
+  for (int n = threadIdx.x; n < N; n += blockDim.x) {
+    float t = 0.f;
+    for (int64_t r = r0; r < r1; ++r) t += ldf(x + r * ld + n);
+    part[(int64_t)blockIdx.x * N + n] = t;
+  }
+}
+
+__global__ void reduce_splits_k(const float *part, int splits, int64_t n, float *out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  float t = 0.f;
+  for (int s = 0; s < splits; ++s) t += part[(int64_t)s * n + i];
+  out[i] += t;
+}
+
+// ------------------------------------------------------------- pair bias
+template <typename T>
+__global__ void head_proj_fwd_k(const T *x, const float *w, float *out, int R, int C, int H, int transpose) {
+  const int lane = threadIdx.x & 31;
+  const int64_t p = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+  const int64_t P = (int64_t)R * R;
+  if (p >= P) return;
+  float acc[8];
+#pragma unroll
+  for (int h = 0; h < 8; ++h) acc[h] = 0.f;
+  for (int cc = lane; cc < C; cc += 32) {
+    const float xv = ldf(x + p * C + cc);
+#pragma unroll
+    for (int h = 0; h < 8; ++h)
+      if (h < H) acc[h] = fmaf(xv, w[h * C + cc], acc[h]);
+  }
+  const int64_t i = p / R, j = p % R;
+  const int64_t pp = transpose ? j * R + i : p;
+#pragma unroll
+  for (int h = 0; h < 8; ++h) {
+    if (h >= H) break;
+    const float v = warp_sum(acc[h]);
+    if (lane == 0) out[h * P + pp] = v;
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) head_proj_bwd_k(const float *dbias, const T *x, const float *w, T *dx,
+                                                       int accumulate, float *part, int R, int C, int H, int transpose,
+                                                       int64_t pos_per_blk) {
+  extern __shared__ float acc[];  // [8 warps][H*C]
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  float *mine = acc + warp * H * C;
+  for (int k = lane; k < H * C; k += 32) mine[k] = 0.f;
+  const int64_t P = (int64_t)R * R;
+  const int64_t p0 = (int64_t)blockIdx.x * pos_per_blk;
+  const int64_t p1 = min(P, p0 + pos_per_blk);
+  for (int64_t p = p0 + warp; p < p1; p += 8) {
+    const int64_t i = p / R, j = p % R;
+    const int64_t pp = transpose ? j * R + i : p;
+    float g[8];
+#pragma unroll
+    for (int h = 0; h < 8; ++h) g[h] = h < H ? dbias[h * P + pp] : 0.f;
+    for (int cc = lane; cc < C; cc += 32) {
+      float d = 0.f;
+      const float xv = ldf(x + p * C + cc);
+#pragma unroll
+      for (int h = 0; h < 8; ++h) {
+        if (h < H) {
+          d = fmaf(g[h], w[h * C + cc], d);
+          mine[h * C + cc] += g[h] * xv;
+        }
+      }
+      T *dp = dx + p * C + cc;
+      stf(dp, accumulate ? ldf(dp) + d : d);
+    }
+  }
+  __syncthreads();
+  for (int k = threadIdx.x; k < H * C; k += blockDim.x) {
+    float t = 0.f;
+    for (int ww = 0; ww < 8; ++ww) t += acc[ww * H * C + k];
+    part[(int64_t)blockIdx.x * H * C + k] = t;
+  }
+}
+
+// ---------------------------------------------------- triangle multiplication
+// Tile of 32 (orow) x 32 (ocol) positions, 4 channels. Outgoing: position
+// (p0,p1) = (orow, ocol); incoming: (p0,p1) = (ocol, orow). Channel-major
+// element (c, orow, ocol) sits at c*R*pitch + orow*pitch + ocol.
+template <typename T>
+__global__ void __launch_bounds__(256) trimul_gate_fwd_k(const T *abg, int64_t ld, const float *mask, T *A, T *B,
+                                                         int64_t pitch, int R, int cm, int incoming) {
+  __shared__ float as[4][32][33], bs[4][32][33];
+  const int q0 = blockIdx.x * 32, r0 = blockIdx.y * 32, c0 = blockIdx.z * 4;
+  for (int idx = threadIdx.x; idx < 32 * 32 * 4; idx += blockDim.x) {
+    const int cc = idx & 3, ocl = (idx >> 2) & 31, orl = idx >> 7;
+    const int orow = r0 + orl, ocol = q0 + ocl, c = c0 + cc;
+    float av = 0.f, bv = 0.f;
+    if (orow < R && ocol < R && c < cm) {
+      const int64_t p = incoming ? (int64_t)ocol * R + orow : (int64_t)orow * R + ocol;
+      const T *row = abg + p * ld;
+      const float mk = mask[p];
+      const float ap = ldf(row + c), ag = ldf(row + cm + c), bp = ldf(row + 2 * cm + c), bg = ldf(row + 3 * cm + c);
+      av = mk * sigmoidf_(ag) * ap;
+      bv = mk * sigmoidf_(bg) * bp;
+    }
+    as[cc][orl][ocl] = av;
+    bs[cc][orl][ocl] = bv;
+  }
+  __syncthreads();
+  const int64_t plane = (int64_t)R * pitch;
+  for (int idx = threadIdx.x; idx < 32 * 32 * 4; idx += blockDim.x) {
+    const int ocl = idx & 31, orl = (idx >> 5) & 31, cc = idx >> 10;
+    const int orow = r0 + orl, ocol = q0 + ocl, c = c0 + cc;
+    if (orow < R && ocol < R && c < cm) {
+      const int64_t o = (int64_t)c * plane + (int64_t)orow * pitch + ocol;
+      stf(A + o, as[cc][orl][ocl]);
+      stf(B + o, bs[cc][orl][ocl]);
+    }
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) trimul_gate_bwd_k(const T *dA, const T *dB, int64_t pitch, const T *abg,
+                                                         int64_t ld, const float *mask, T *dabg, int R, int cm,
+                                                         int incoming) {
+  __shared__ float as[4][32][33], bs[4][32][33];
+  const int q0 = blockIdx.x * 32, r0 = blockIdx.y * 32, c0 = blockIdx.z * 4;
+  const int64_t plane = (int64_t)R * pitch;
+  for (int idx = threadIdx.x; idx < 32 * 32 * 4; idx += blockDim.x) {
+    const int ocl = idx & 31, orl = (idx >> 5) & 31, cc = idx >> 10;
+    const int orow = r0 + orl, ocol = q0 + ocl, c = c0 + cc;
+    float av = 0.f, bv = 0.f;
+    if (orow < R && ocol < R && c < cm) {
+      const int64_t o = (int64_t)c * plane + (int64_t)orow * pitch + ocol;
+      av = ldf(dA + o);
+      bv = ldf(dB + o);
+    }
+    as[cc][orl][ocl] = av;
+    bs[cc][orl][ocl] = bv;
+  }
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < 32 * 32 * 4; idx += blockDim.x) {
+    const int cc = idx & 3, ocl = (idx >> 2) & 31, orl = idx >> 7;
+    const int orow = r0 + orl, ocol = q0 + ocl, c = c0 + cc;
+    if (orow < R && ocol < R && c < cm) {
+      const int64_t p = incoming ? (int64_t)ocol * R + orow : (int64_t)orow * R + ocol;
+      const T *row = abg + p * ld;
+      T *drow = dabg + p * ld;
+      const float mk = mask[p];
+      const float ap = ldf(row + c), ag = ldf(row + cm + c), bp = ldf(row + 2 * cm + c), bg = ldf(row + 3 * cm + c);
+      const float sa = sigmoidf_(ag), sb = sigmoidf_(bg);
+      const float da = as[cc][orl][ocl] * mk, db = bs[cc][orl][ocl] * mk;
+      stf(drow + c, da * sa);
+      stf(drow + cm + c, da * ap * sa * (1.f - sa));
+      stf(drow + 2 * cm + c, db * sb);
+      stf(drow + 3 * cm + c, db * bp * sb * (1.f - sb));
+    }
+  }
+}
+
+template <typename T>
+__global__ void sigmoid_cols_k(T *x, int64_t ld, int col0, int ncols, int64_t P) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= P * ncols) return;
+  const int64_t p = i / ncols;
+  const int c = (int)(i % ncols);
+  T *e = x + p * ld + col0 + c;
+  stf(e, sigmoidf_(ldf(e)));
+}
+
+template <typename T>
+__global__ void gate_out_bwd_k(const T *dz, const T *g, int64_t g_ld, const T *y, T *dy, T *dgpre, int64_t dg_ld,
+                               int64_t P, int C) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= P * C) return;
+  const int64_t p = i / C;
+  const int c = (int)(i % C);
+  const float d = ldf(dz + i), gv = ldf(g + p * g_ld + c), yv = ldf(y + i);
+  stf(dy + i, d * gv);
+  stf(dgpre + p * dg_ld + c, d * yv * gv * (1.f - gv));
+}
+
+// ------------------------------------------------------------ attention gate
+template <typename T>
+__global__ void attn_gate_bwd_k(AttnArgs a, const T *dog, T *dgpre, int64_t sGb_d, int64_t sGx_d, T *do_att,
+                                float *D) {
+  const int lane = threadIdx.x & 31;
+  const int64_t row = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+  if (row >= (int64_t)a.B1 * a.X) return;
+  const int64_t b = row / a.X, x = row % a.X;
+  const int64_t ob = b * a.sOb + x * a.sOx;
+  const int64_t gb = b * a.sQb + x * a.sQx;
+  const int64_t db = b * sGb_d + x * sGx_d;
+  for (int h = 0; h < a.H; ++h) {
+    float s = 0.f;
+    for (int d = lane; d < a.c; d += 32) {
+      const int64_t k = h * a.c + d;
+      const float dg = ldf(dog + ob + k), gv = ldf((const T *)a.g + gb + k), ov = ldf((const T *)a.o_att + ob + k);
+      const float doa = dg * gv;
+      stf(do_att + ob + k, doa);
+      stf(dgpre + db + k, dg * ov * gv * (1.f - gv));
+      s += doa * ov;
+    }
+    s = warp_sum(s);
+    if (lane == 0) D[(b * a.H + h) * a.X + x] = s;
+  }
+}
+
+template <typename T>
+__global__ void attn_dq_store_k(AttnArgs a, T *dq) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int hc = a.H * a.c;
+  if (i >= (int64_t)a.B1 * a.X * hc) return;
+  const int64_t row = i / hc;
+  const int k = (int)(i % hc);
+  const int64_t b = row / a.X, x = row % a.X;
+  stf(dq + b * a.sQb + x * a.sQx + k, a.scale * a.dq_acc[b * a.sOb + x * a.sOx + k]);
+}
+
+// ------------------------------------------------------------ OPM, scaling
+__global__ void opm_inv_norm_k(const float *mask, float *inv, int S, int R, float eps) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (int64_t)R * R) return;
+  const int i = (int)(idx / R), j = (int)(idx % R);
+  float n = 0.f;
+  for (int s = 0; s < S; ++s) n += mask[(int64_t)s * R + i] * mask[(int64_t)s * R + j];
+  inv[idx] = 1.f / (eps + n);
+}
+
+template <typename T>
+__global__ void row_scale_k(const T *x, const float *scale, T *y, int64_t M, int C) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= M * C) return;
+  stf(y + i, ldf(x + i) * scale[i / C]);
+}
+
+template <typename T>
+__global__ void to_f32_k(const T *src, float *dst, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) dst[i] = ldf(src + i);
+}
+template <typename T>
+__global__ void from_f32_k(const float *src, T *dst, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) stf(dst + i, src[i]);
+}
+
+inline unsigned nblk(int64_t n, int t = 256) { return (unsigned)((n + t - 1) / t); }
+
+}  // namespace
+
+cudaError_t reduce_partials(const float *part, int nb, int N, float *out, cudaStream_t s) {
+  reduce_partials_k<<<nblk(N), 256, 0, s>>>(part, nb, N, N, out);
+  return cudaGetLastError();
+}
+// Variant with a leading dimension (LayerNorm partials hold gamma and beta sums).
+cudaError_t reduce_partials_ld(const float *part, int nb, int64_t ld, int N, float *out, cudaStream_t s) {
+  reduce_partials_k<<<nblk(N), 256, 0, s>>>(part, nb, ld, N, out);
+  return cudaGetLastError();
+}
+
+int colsum_blocks(int64_t M) {
+  int64_t b = (M + 127) / 128;
+  return (int)(b < 512 ? (b < 1 ? 1 : b) : 512);
+}
+cudaError_t colsum(const void *x, int64_t ld, int64_t M, int N, float *part, int use_bf16, cudaStream_t s) {
+  const int nb = colsum_blocks(M);
+  const int64_t rpb = (M + nb - 1) / nb;
+  if (use_bf16) colsum_k<bf16><<<nb, 256, 0, s>>>((const bf16 *)x, ld, M, N, part, rpb);
+  else colsum_k<float><<<nb, 256, 0, s>>>((const float *)x, ld, M, N, part, rpb);
+  return cudaGetLastError();
+}
+
+cudaError_t reduce_splits(const float *part, int splits, int64_t n, float *out, cudaStream_t s) {
+  reduce_splits_k<<<nblk(n), 256, 0, s>>>(part, splits, n, out);
+  return cudaGetLastError();
+}
+
+cudaError_t head_proj_fwd(const void *x, const float *w, float *out, int R, int C, int H, int transpose, int use_bf16,
+                          cudaStream_t s) {
+  if (H > 8) return cudaErrorInvalidValue;
+  const int64_t P = (int64_t)R * R;
+  if (use_bf16) head_proj_fwd_k<bf16><<<nblk(P, 8), 256, 0, s>>>((const bf16 *)x, w, out, R, C, H, transpose);
+  else head_proj_fwd_k<float><<<nblk(P, 8), 256, 0, s>>>((const float *)x, w, out, R, C, H, transpose);
+  return cudaGetLastError();
+}
+
+int head_proj_blocks(int R) {
+  int64_t b = ((int64_t)R * R + 63) / 64;
+  return (int)(b < 1024 ? (b < 1 ? 1 : b) : 1024);
+}
+cudaError_t head_proj_bwd(const float *dbias, const void *x, const float *w, void *dx, int accumulate, float *part,
+                          int R, int C, int H, int transpose, int use_bf16, cudaStream_t s) {
+  if (H > 8) return cudaErrorInvalidValue;
+  const int nb = head_proj_blocks(R);
+  const int64_t ppb = ((int64_t)R * R + nb - 1) / nb;
+  const size_t sm = (size_t)8 * H * C * sizeof(float);
+  if (sm > 48 * 1024) return cudaErrorInvalidValue;
+  if (use_bf16)
+    head_proj_bwd_k<bf16><<<nb, 256, sm, s>>>(dbias, (const bf16 *)x, w, (bf16 *)dx, accumulate, part, R, C, H,
+                                              transpose, ppb);
+  else
+    head_proj_bwd_k<float><<<nb, 256, sm, s>>>(dbias, (const float *)x, w, (float *)dx, accumulate, part, R, C, H,
+                                               transpose, ppb);
+  return cudaGetLastError();
+}
+
+cudaError_t trimul_gate_fwd(void *abg, int64_t ld, const float *mask, void *A, void *B, int64_t pitch, int R, int cm,
+                            int cz, int incoming, int use_bf16, cudaStream_t s) {
+  dim3 grid((R + 31) / 32, (R + 31) / 32, (cm + 3) / 4);
+  const int64_t P = (int64_t)R * R;
+  if (use_bf16) {
+    trimul_gate_fwd_k<bf16><<<grid, 256, 0, s>>>((const bf16 *)abg, ld, mask, (bf16 *)A, (bf16 *)B, pitch, R, cm,
+                                                 incoming);
+    sigmoid_cols_k<bf16><<<nblk(P * cz), 256, 0, s>>>((bf16 *)abg, ld, 4 * cm, cz, P);
+  } else {
+    trimul_gate_fwd_k<float><<<grid, 256, 0, s>>>((const float *)abg, ld, mask, (float *)A, (float *)B, pitch, R,
+                                                  cm, incoming);
+    sigmoid_cols_k<float><<<nblk(P * cz), 256, 0, s>>>((float *)abg, ld, 4 * cm, cz, P);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t trimul_gate_bwd(const void *dA, const void *dB, int64_t pitch, const void *abg, int64_t ld,
+                            const float *mask, void *dabg, int R, int cm, int incoming, int use_bf16, cudaStream_t s) {
+  dim3 grid((R + 31) / 32, (R + 31) / 32, (cm + 3) / 4);
+  if (use_bf16)
+    trimul_gate_bwd_k<bf16><<<grid, 256, 0, s>>>((const bf16 *)dA, (const bf16 *)dB, pitch, (const bf16 *)abg, ld,
+                                                 mask, (bf16 *)dabg, R, cm, incoming);
+  else
+    trimul_gate_bwd_k<float><<<grid, 256, 0, s>>>((const float *)dA, (const float *)dB, pitch, (const float *)abg, ld,
+                                                  mask, (float *)dabg, R, cm, incoming);
+  return cudaGetLastError();
+}
+
+cudaError_t gate_out_bwd(const void *dz, const void *g, int64_t g_ld, const void *y, void *dy, void *dgpre,
+                         int64_t dg_ld, int64_t P, int C, int use_bf16, cudaStream_t s) {
+  if (use_bf16)
+    gate_out_bwd_k<bf16><<<nblk(P * C), 256, 0, s>>>((const bf16 *)dz, (const bf16 *)g, g_ld, (const bf16 *)y,
+                                                     (bf16 *)dy, (bf16 *)dgpre, dg_ld, P, C);
+  else
+    gate_out_bwd_k<float><<<nblk(P * C), 256, 0, s>>>((const float *)dz, (const float *)g, g_ld, (const float *)y,
+                                                      (float *)dy, (float *)dgpre, dg_ld, P, C);
+  return cudaGetLastError();
+}
+
+cudaError_t attn_gate_bwd(const AttnArgs &a, const void *dog, void *dgpre, int64_t sGb_d, int64_t sGx_d, void *do_att,
+                          float *D, int use_bf16, cudaStream_t s) {
+  const int64_t rows = (int64_t)a.B1 * a.X;
+  if (use_bf16)
+    attn_gate_bwd_k<bf16><<<nblk(rows, 8), 256, 0, s>>>(a, (const bf16 *)dog, (bf16 *)dgpre, sGb_d, sGx_d,
+                                                        (bf16 *)do_att, D);
+  else
+    attn_gate_bwd_k<float><<<nblk(rows, 8), 256, 0, s>>>(a, (const float *)dog, (float *)dgpre, sGb_d, sGx_d,
+                                                         (float *)do_att, D);
+  return cudaGetLastError();
+}
+
+cudaError_t attn_dq_store(const AttnArgs &a, void *dq, int use_bf16, cudaStream_t s) {
+  const int64_t n = (int64_t)a.B1 * a.X * a.H * a.c;
+  if (use_bf16) attn_dq_store_k<bf16><<<nblk(n), 256, 0, s>>>(a, (bf16 *)dq);
+  else attn_dq_store_k<float><<<nblk(n), 256, 0, s>>>(a, (float *)dq);
+  return cudaGetLastError();
+}
+
+cudaError_t opm_inv_norm(const float *mask, float *inv, int S, int R, float eps, cudaStream_t s) {
+  opm_inv_norm_k<<<nblk((int64_t)R * R), 256, 0, s>>>(mask, inv, S, R, eps);
+  return cudaGetLastError();
+}
+
+cudaError_t row_scale(const void *x, const float *scale, void *y, int64_t M, int C, int use_bf16, cudaStream_t s) {
+  if (use_bf16) row_scale_k<bf16><<<nblk(M * C), 256, 0, s>>>((const bf16 *)x, scale, (bf16 *)y, M, C);
+  else row_scale_k<float><<<nblk(M * C), 256, 0, s>>>((const float *)x, scale, (float *)y, M, C);
+  return cudaGetLastError();
+}
+
+cudaError_t to_f32(const void *src, float *dst, int64_t n, int use_bf16, cudaStream_t s) {
+  if (use_bf16) to_f32_k<bf16><<<nblk(n), 256, 0, s>>>((const bf16 *)src, dst, n);
+  else to_f32_k<float><<<nblk(n), 256, 0, s>>>((const float *)src, dst, n);
+  return cudaGetLastError();
+}
+cudaError_t from_f32(const float *src, void *dst, int64_t n, int use_bf16, cudaStream_t s) {
+  if (use_bf16) from_f32_k<bf16><<<nblk(n), 256, 0, s>>>(src, (bf16 *)dst, n);
+  else from_f32_k<float><<<nblk(n), 256, 0, s>>>(src, (float *)dst, n);
+  return cudaGetLastError();
+}
+cudaError_t f32_to_bf16(const float *src, bf16 *dst, int64_t n, cudaStream_t s) {
+  from_f32_k<bf16><<<nblk(n), 256, 0, s>>>(src, dst, n);
+  return cudaGetLastError();
+}
+
+}  // namespace evo

@@ -1,0 +1,232 @@
+"""Thin Python binding of libevo.so (the C ABI in include/evo.h).
+
+Only argument marshalling lives here: every step of the Evoformer block runs
+in the library's CUDA kernels.  PyTorch supplies device memory and streams.
+The library must have been built (``paper_2207_05477_gb300.build.build()``);
+there is no fallback of any kind when it is missing.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(PKG)
+LIB_PATH = os.path.join(PKG, "libevo.so")
+HEADER = os.path.join(ROOT, "include", "evo.h")
+
+EVO_OK, EVO_ERR_INVALID_ARG, EVO_ERR_UNSUPPORTED, EVO_ERR_ALIGNMENT = 0, -1, -2, -3
+EVO_ERR_WORKSPACE, EVO_ERR_CUDA, EVO_ERR_TIMEOUT = -4, -5, -6
+EVO_F32, EVO_BF16 = 0, 1
+EVO_COL_ATTENTION, EVO_COL_GLOBAL = 0, 1
+EVO_MODE_FWD, EVO_MODE_BWD = 0, 1
+
+
+class EvoError(RuntimeError):
+    def __init__(self, code, where):
+        self.code = code
+        super().__init__(f"{where}: {code} ({strerror(code)})")
+
+
+class CDims(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int32) for n in (
+        "n_seq", "n_res", "c_m", "c_z", "h_msa", "c_msa", "h_tri", "c_tri",
+        "c_mul", "c_opm", "trans_n", "msa_col_mode", "act_dtype")]
+
+
+class CParamEntry(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 48), ("offset", ctypes.c_int64), ("ndim", ctypes.c_int32),
+                ("shape", ctypes.c_int64 * 4)]
+
+
+_lib = None
+_vp, _sz = ctypes.c_void_p, ctypes.c_size_t
+
+
+def lib():
+    """The loaded libevo.so; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_2207_05477_gb300.build.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        P = ctypes.POINTER
+        L.evo_param_count.argtypes = [P(CDims)]
+        L.evo_param_count.restype = _sz
+        L.evo_param_layout.argtypes = [P(CDims), P(CParamEntry), ctypes.c_int]
+        L.evo_params_bf16_size.argtypes = [P(CDims), P(_sz)]
+        L.evo_params_to_bf16.argtypes = [P(CDims), _vp, _vp, _vp]
+        L.evo_workspace_size.argtypes = [P(CDims), ctypes.c_int, P(_sz)]
+        L.evo_block_fwd.argtypes = [P(CDims), _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _sz, _vp]
+        L.evo_block_bwd.argtypes = [P(CDims), _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _sz,
+                                    _vp]
+        L.evo_stack_fwd.argtypes = [P(CDims), ctypes.c_int, _vp, _vp, _sz, _vp, _vp, _vp, _vp, _vp, _sz, _vp]
+        L.evo_get_error.argtypes = [_vp]
+        L.evo_debug_wait_timeout.argtypes = [ctypes.c_longlong, _vp]
+        L.evo_strerror.argtypes = [ctypes.c_int]
+        L.evo_strerror.restype = ctypes.c_char_p
+        L.evo_version.restype = ctypes.c_char_p
+        _lib = L
+    return _lib
+
+
+def header_functions():
+    """Names of the functions include/evo.h declares."""
+    txt = open(HEADER).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(evo_[a-z0-9_]+)\s*\(", txt)))
+
+
+def strerror(code):
+    try:
+        return lib().evo_strerror(int(code)).decode()
+    except Exception:  # during import errors
+        return "?"
+
+
+def _check(code, where):
+    if code != EVO_OK:
+        raise EvoError(code, where)
+
+
+def cdims(d, act_dtype):
+    """ctypes evo_dims from a synth.Dims-like object."""
+    return CDims(d.n_seq, d.n_res, d.c_m, d.c_z, d.h_msa, d.c_msa, d.h_tri, d.c_tri, d.c_mul, d.c_opm,
+                 d.trans_n, d.msa_col_mode, act_dtype)
+
+
+def param_count(cd):
+    return int(lib().evo_param_count(ctypes.byref(cd)))
+
+
+def param_layout(cd):
+    n = lib().evo_param_layout(ctypes.byref(cd), None, 0)
+    if n < 0:
+        raise EvoError(n, "evo_param_layout")
+    arr = (CParamEntry * n)()
+    lib().evo_param_layout(ctypes.byref(cd), arr, n)
+    return [(e.name.decode(), int(e.offset), tuple(int(e.shape[k]) for k in range(e.ndim))) for e in arr]
+
+
+def workspace_size(cd, mode):
+    out = _sz(0)
+    _check(lib().evo_workspace_size(ctypes.byref(cd), mode, ctypes.byref(out)), "evo_workspace_size")
+    return int(out.value)
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def params_to_bf16(cd, p32, p16, stream=None):
+    _check(lib().evo_params_to_bf16(ctypes.byref(cd), _ptr(p32), _ptr(p16), _stream(stream)),
+           "evo_params_to_bf16")
+
+
+def block_fwd(cd, params, params_bf16, m, z, m_out, z_out, msa_mask, pair_mask, ws, stream=None):
+    _check(lib().evo_block_fwd(ctypes.byref(cd), _ptr(params), _ptr(params_bf16), _ptr(m), _ptr(z), _ptr(m_out),
+                               _ptr(z_out), _ptr(msa_mask), _ptr(pair_mask), _ptr(ws), ws.numel() * ws.element_size(),
+                               _stream(stream)), "evo_block_fwd")
+
+
+def block_bwd(cd, params, params_bf16, m, z, msa_mask, pair_mask, dm_out, dz_out, dm_in, dz_in, dparams, ws,
+              stream=None):
+    _check(lib().evo_block_bwd(ctypes.byref(cd), _ptr(params), _ptr(params_bf16), _ptr(m), _ptr(z), _ptr(msa_mask),
+                               _ptr(pair_mask), _ptr(dm_out), _ptr(dz_out), _ptr(dm_in), _ptr(dz_in), _ptr(dparams),
+                               _ptr(ws), ws.numel() * ws.element_size(), _stream(stream)), "evo_block_bwd")
+
+
+def stack_fwd(cd, n_blocks, params, params_bf16, param_stride, m, z, msa_mask, pair_mask, ws, stream=None):
+    _check(lib().evo_stack_fwd(ctypes.byref(cd), n_blocks, _ptr(params), _ptr(params_bf16), param_stride, _ptr(m),
+                               _ptr(z), _ptr(msa_mask), _ptr(pair_mask), _ptr(ws), ws.numel() * ws.element_size(),
+                               _stream(stream)), "evo_stack_fwd")
+
+
+def get_error(stream=None):
+    return int(lib().evo_get_error(_stream(stream)))
+
+
+def debug_wait_timeout(limit_ns, stream=None):
+    _check(lib().evo_debug_wait_timeout(int(limit_ns), _stream(stream)), "evo_debug_wait_timeout")
+
+
+# ------------------------------------------------------------- torch glue
+
+def _torch_dtype(act_dtype):
+    import torch
+    return torch.bfloat16 if act_dtype == EVO_BF16 else torch.float32
+
+
+def workspace(cd, mode, device):
+    import torch
+    return torch.empty(workspace_size(cd, mode), dtype=torch.uint8, device=device)
+
+
+def bf16_params(cd, params):
+    """BF16 copy of the flat parameter buffer (None for the FP32 path)."""
+    import torch
+    if cd.act_dtype != EVO_BF16:
+        return None
+    p16 = torch.empty(param_count(cd), dtype=torch.bfloat16, device=params.device)
+    params_to_bf16(cd, params, p16)
+    return p16
+
+
+def _autograd_fn():
+    import torch
+
+    class EvoBlockFn(torch.autograd.Function):
+        """One Evoformer block; backward recomputes the block (only m, z saved)."""
+
+        @staticmethod
+        def forward(ctx, m, z, params, msa_mask, pair_mask, cd):
+            m, z = m.contiguous(), z.contiguous()
+            p16 = bf16_params(cd, params)
+            m_out, z_out = torch.empty_like(m), torch.empty_like(z)
+            ws = workspace(cd, EVO_MODE_FWD, m.device)
+            block_fwd(cd, params, p16, m, z, m_out, z_out, msa_mask, pair_mask, ws)
+            ctx.save_for_backward(m, z, params, msa_mask, pair_mask)
+            ctx.cd = cd
+            ctx.mark_non_differentiable(msa_mask, pair_mask)
+            return m_out, z_out
+
+        @staticmethod
+        def backward(ctx, dm, dz):
+            m, z, params, msa_mask, pair_mask = ctx.saved_tensors
+            cd = ctx.cd
+            dt = _torch_dtype(cd.act_dtype)
+            dm = torch.zeros_like(m) if dm is None else dm.to(dt).contiguous()
+            dz = torch.zeros_like(z) if dz is None else dz.to(dt).contiguous()
+            p16 = bf16_params(cd, params)
+            dm_in, dz_in = torch.empty_like(m), torch.empty_like(z)
+            dparams = torch.zeros_like(params)
+            ws = workspace(cd, EVO_MODE_BWD, m.device)
+            block_bwd(cd, params, p16, m, z, msa_mask, pair_mask, dm, dz, dm_in, dz_in, dparams, ws)
+            return dm_in, dz_in, dparams, None, None, None
+
+    return EvoBlockFn
+
+
+_EvoBlockFn = None
+
+
+def evoformer_block(m, z, params, msa_mask, pair_mask, cd):
+    """Differentiable Evoformer block through libevo (forward and backward kernels)."""
+    global _EvoBlockFn
+    if _EvoBlockFn is None:
+        _EvoBlockFn = _autograd_fn()
+    return _EvoBlockFn.apply(m, z, params, msa_mask, pair_mask, cd)
+
+
+def evoformer_stack(m, z, params_list, msa_mask, pair_mask, cd):
+    """Stack of blocks; each block recomputes itself in backward (per-block recompute)."""
+    for p in params_list:
+        m, z = evoformer_block(m, z, p, msa_mask, pair_mask, cd)
+    return m, z

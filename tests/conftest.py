@@ -14,7 +14,8 @@ def pytest_configure(config):
 
 
 @pytest.fixture(scope="session")
-def torch64():
-    import torch
-    torch.set_default_dtype(torch.float64)
-    return torch
+def built_lib():
+    """libevo.so, built in-tree first if missing or stale."""
+    from paper_2207_05477_gb300 import build, evo
+    build.build()
+    return evo.lib()

@@ -1,0 +1,81 @@
+"""Shared helpers of the parity tests: run the library and the oracle on the same seeded inputs."""
+import functools
+
+import numpy as np
+import torch
+
+from oracle import evoformer as O
+from paper_2207_05477_gb300 import evo, synth
+
+
+def rel_l2(x, ref, mask=None):
+    x = torch.as_tensor(x).double().cpu()
+    ref = torch.as_tensor(ref).double().cpu()
+    if mask is not None:
+        m = torch.as_tensor(mask).bool().cpu()
+        while m.dim() < x.dim():
+            m = m[..., None]
+        m = m.expand_as(x)
+        x, ref = x[m], ref[m]
+    den = ref.norm().item()
+    return (x - ref).norm().item() / (den if den > 0 else 1.0)
+
+
+@functools.lru_cache(maxsize=4)
+def problem(d, seed=32, pad_frac=0.0, trailing=False):
+    return synth.make_problem(d, seed, pad_frac, trailing)
+
+
+@functools.lru_cache(maxsize=3)
+def oracle_fwd_bwd(d, seed=32, pad_frac=0.0, trailing=False):
+    prob = problem(d, seed, pad_frac, trailing)
+    p = synth.unpack_params(d, prob["params"])
+    mo, zo, dm, dz, dp = O.block_forward_backward(prob["m"], prob["z"], prob["msa_mask"], prob["pair_mask"], p, d,
+                                                  prob["gm"], prob["gz"])
+    return mo, zo, dm, dz, dp
+
+
+@functools.lru_cache(maxsize=3)
+def oracle_fwd(d, seed=32, pad_frac=0.0, trailing=False):
+    prob = problem(d, seed, pad_frac, trailing)
+    p = synth.unpack_params(d, prob["params"])
+    return O.block_forward(prob["m"], prob["z"], prob["msa_mask"], prob["pair_mask"], p, d)
+
+
+def gpu_run(d, act_dtype, seed=32, pad_frac=0.0, trailing=False, backward=True):
+    """Block forward (and backward) through the C ABI on cuda:0; results on the CPU in fp64."""
+    prob = problem(d, seed, pad_frac, trailing)
+    dev = torch.device("cuda:0")
+    dt = torch.bfloat16 if act_dtype == evo.EVO_BF16 else torch.float32
+    cd = evo.cdims(d, act_dtype)
+    params = torch.tensor(prob["params"], device=dev)
+    p16 = evo.bf16_params(cd, params)
+    m = torch.tensor(prob["m"], device=dev).to(dt)
+    z = torch.tensor(prob["z"], device=dev).to(dt)
+    mm = torch.tensor(prob["msa_mask"], device=dev)
+    pm = torch.tensor(prob["pair_mask"], device=dev)
+    m_out, z_out = torch.empty_like(m), torch.empty_like(z)
+    ws = evo.workspace(cd, evo.EVO_MODE_FWD, dev)
+    evo.block_fwd(cd, params, p16, m, z, m_out, z_out, mm, pm, ws)
+    out = {"m": m_out.double().cpu(), "z": z_out.double().cpu()}
+    if backward:
+        gm = torch.tensor(prob["gm"], device=dev).to(dt)
+        gz = torch.tensor(prob["gz"], device=dev).to(dt)
+        dm, dz = torch.empty_like(m), torch.empty_like(z)
+        dp = torch.zeros_like(params)
+        wsb = evo.workspace(cd, evo.EVO_MODE_BWD, dev)
+        evo.block_bwd(cd, params, p16, m, z, mm, pm, gm, gz, dm, dz, dp, wsb)
+        out.update(dm=dm.double().cpu(), dz=dz.double().cpu(), dparams=dp.double().cpu())
+    torch.cuda.synchronize()
+    assert evo.get_error() == evo.EVO_OK
+    return out
+
+
+def param_grad_errors(d, gpu_dparams, oracle_dp):
+    lay, _ = synth.param_layout(d)
+    errs = {}
+    for name, off, shape, _ in lay:
+        n = int(np.prod(shape))
+        g = gpu_dparams[off:off + n].reshape(shape)
+        errs[name] = rel_l2(g, oracle_dp[name])
+    return errs

@@ -1,0 +1,63 @@
+"""The C-ABI library builds for sm_103a, loads, and exports what include/evo.h declares.
+
+Host-only entry points are exercised here; nothing touches a GPU.
+"""
+import ctypes
+
+import pytest
+
+from paper_2207_05477_gb300 import evo, synth
+
+
+def test_every_declared_symbol_is_exported(built_lib):
+    names = evo.header_functions()
+    assert len(names) >= 10
+    for n in names:
+        assert hasattr(built_lib, n), n
+
+
+@pytest.mark.parametrize("d", [synth.DIMS_TRAIN_CROP, synth.DIMS_SMALL_FP32, synth.DIMS_EXTRA_MSA])
+def test_param_layout_matches_generator_table(built_lib, d):
+    cd = evo.cdims(d, evo.EVO_BF16)
+    lay = evo.param_layout(cd)
+    ref, total = synth.param_layout(d)
+    assert [(n, o, s) for n, o, s, _ in ref] == lay
+    assert evo.param_count(cd) == total
+    assert all(o % 64 == 0 for _, o, _ in lay)  # 256-byte aligned tensors
+
+
+def test_param_count_at_paper_dims(built_lib):
+    assert evo.param_count(evo.cdims(synth.DIMS_TRAIN_CROP, evo.EVO_BF16)) == 1829952
+
+
+def test_workspace_queries_and_errors(built_lib):
+    cd = evo.cdims(synth.DIMS_TRAIN_CROP, evo.EVO_BF16)
+    fwd = evo.workspace_size(cd, evo.EVO_MODE_FWD)
+    bwd = evo.workspace_size(cd, evo.EVO_MODE_BWD)
+    assert 0 < fwd < bwd < 4 * 2 ** 30
+    bad = evo.cdims(synth.DIMS_TRAIN_CROP.replace(c_m=100), evo.EVO_BF16)
+    with pytest.raises(evo.EvoError) as e:
+        evo.workspace_size(bad, evo.EVO_MODE_FWD)
+    assert e.value.code == evo.EVO_ERR_UNSUPPORTED
+    neg = evo.cdims(synth.DIMS_TRAIN_CROP.replace(n_res=0), evo.EVO_BF16)
+    with pytest.raises(evo.EvoError) as e:
+        evo.workspace_size(neg, evo.EVO_MODE_FWD)
+    assert e.value.code == evo.EVO_ERR_INVALID_ARG
+    with pytest.raises(evo.EvoError):
+        evo.workspace_size(cd, 7)
+
+
+def test_null_and_misaligned_pointers_are_rejected_before_any_launch(built_lib):
+    cd = evo.cdims(synth.DIMS_SMALL_FP32, evo.EVO_F32)
+    L = built_lib
+    null = ctypes.c_void_p(0)
+    r = L.evo_block_fwd(ctypes.byref(cd), null, null, null, null, null, null, null, null, null, 0, null)
+    assert r == evo.EVO_ERR_INVALID_ARG
+    odd = ctypes.c_void_p(0x1000 + 8)
+    r = L.evo_block_fwd(ctypes.byref(cd), odd, null, odd, odd, odd, odd, odd, odd, odd, 1 << 30, null)
+    assert r == evo.EVO_ERR_ALIGNMENT
+
+
+def test_strerror_and_version(built_lib):
+    assert evo.strerror(evo.EVO_ERR_TIMEOUT) == "bounded device wait timed out"
+    assert b"sm_103a" in built_lib.evo_version()

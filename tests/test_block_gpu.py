@@ -1,0 +1,82 @@
+"""Parity of the CUDA Evoformer block (through the C ABI) with the FP64 oracle.
+
+Tolerances (relative L2 over all positions): FP32 plain path 1e-4 on m, z and
+on every gradient; BF16 path 2e-2 on m, z and 5e-2 on dm, dz and each
+parameter tensor's gradient.
+"""
+import pytest
+
+from helpers import gpu_run, oracle_fwd, oracle_fwd_bwd, param_grad_errors, rel_l2
+from paper_2207_05477_gb300 import evo, synth
+
+pytestmark = pytest.mark.gpu
+
+FP32_TOL = 1e-4
+BF16_TOL = 2e-2
+BF16_GRAD_TOL = 5e-2
+
+RAGGED = synth.Dims(n_seq=5, n_res=37)  # ragged against every 64/128-wide tile
+
+
+def _check(out, ref, tol, gtol, d):
+    mo, zo, dm, dz, dp = ref
+    errs = {"m": rel_l2(out["m"], mo), "z": rel_l2(out["z"], zo)}
+    assert errs["m"] <= tol and errs["z"] <= tol, errs
+    if "dm" in out:
+        g = {"dm": rel_l2(out["dm"], dm), "dz": rel_l2(out["dz"], dz)}
+        g.update(param_grad_errors(d, out["dparams"], dp))
+        bad = {k: v for k, v in g.items() if not v <= gtol}
+        assert not bad, bad
+
+
+def test_fp32_forward_small_config(built_lib):
+    d = synth.DIMS_SMALL_FP32
+    out = gpu_run(d, evo.EVO_F32, backward=False)
+    mo, zo = oracle_fwd(d)
+    assert rel_l2(out["m"], mo) <= FP32_TOL
+    assert rel_l2(out["z"], zo) <= FP32_TOL
+
+
+def test_fp32_fwd_bwd_ragged_padded(built_lib):
+    out = gpu_run(RAGGED, evo.EVO_F32, pad_frac=0.1)
+    _check(out, oracle_fwd_bwd(RAGGED, pad_frac=0.1), FP32_TOL, FP32_TOL, RAGGED)
+
+
+def test_bf16_fwd_bwd_ragged_padded(built_lib):
+    out = gpu_run(RAGGED, evo.EVO_BF16, pad_frac=0.1)
+    _check(out, oracle_fwd_bwd(RAGGED, pad_frac=0.1), BF16_TOL, BF16_GRAD_TOL, RAGGED)
+
+
+def test_bf16_forward_small_config(built_lib):
+    d = synth.DIMS_SMALL_FP32
+    out = gpu_run(d, evo.EVO_BF16, backward=False)
+    mo, zo = oracle_fwd(d)
+    assert rel_l2(out["m"], mo) <= BF16_TOL
+    assert rel_l2(out["z"], zo) <= BF16_TOL
+
+
+@pytest.mark.parametrize("d", [synth.Dims(n_seq=1, n_res=8), synth.Dims(n_seq=3, n_res=1)])
+def test_bf16_degenerate_sizes(built_lib, d):
+    out = gpu_run(d, evo.EVO_BF16)
+    _check(out, oracle_fwd_bwd(d), BF16_TOL, BF16_GRAD_TOL, d)
+
+
+def test_bf16_trailing_padding_and_single_valid_residue(built_lib):
+    d = synth.Dims(n_seq=4, n_res=20)
+    out = gpu_run(d, evo.EVO_BF16, pad_frac=0.95, trailing=True)
+    _check(out, oracle_fwd_bwd(d, pad_frac=0.95, trailing=True), BF16_TOL, BF16_GRAD_TOL, d)
+
+
+@pytest.mark.slow
+def test_bf16_fwd_bwd_training_crop(built_lib):
+    """The paper's initial-training crop: N_seq=128, N_res=256, 5% padded residues."""
+    d = synth.DIMS_TRAIN_CROP
+    out = gpu_run(d, evo.EVO_BF16, pad_frac=0.05)
+    _check(out, oracle_fwd_bwd(d, pad_frac=0.05), BF16_TOL, BF16_GRAD_TOL, d)
+
+
+@pytest.mark.slow
+def test_fp32_fwd_bwd_training_crop(built_lib):
+    d = synth.DIMS_TRAIN_CROP
+    out = gpu_run(d, evo.EVO_F32, pad_frac=0.05)
+    _check(out, oracle_fwd_bwd(d, pad_frac=0.05), FP32_TOL, FP32_TOL, d)
