@@ -140,6 +140,22 @@ int evo_get_error(evo_stream_t stream);
  * no failure detection). */
 int evo_debug_wait_timeout(long long limit_ns, evo_stream_t stream);
 
+/* Per-kernel timing.  evo_profile_begin starts recording a CUDA event pair
+ * around every kernel launch of the library (on the launch stream), with the
+ * launch's algorithmic flops and DRAM bytes; evo_profile_end waits for the
+ * stream, stops recording and aggregates by kernel name into out (up to cap
+ * entries), returning the number of distinct names. */
+typedef struct evo_profile_entry {
+  char name[32];
+  int32_t calls;     /* launch sites that ran                           */
+  int32_t launches;  /* kernel launches                                 */
+  double total_ms;   /* summed event time                               */
+  double flops;      /* algorithmic flops of those launches             */
+  double bytes;      /* algorithmic DRAM bytes (inputs read + outputs)  */
+} evo_profile_entry;
+int evo_profile_begin(void);
+int evo_profile_end(evo_stream_t stream, evo_profile_entry *out, int cap);
+
 /* Static description of an EVO_* code. */
 const char *evo_strerror(int code);
 

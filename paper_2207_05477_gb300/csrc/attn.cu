@@ -614,6 +614,11 @@ bool mma_ok(const AttnArgs &a) {
 
 cudaError_t attn_fwd(const AttnArgs &a, int use_bf16, cudaStream_t s) {
   if (a.B1 <= 0 || a.X <= 0 || a.H <= 0) return cudaSuccess;
+  const double inner = (double)a.B1 * a.H * a.X * (double)a.Y * a.c;
+  const double ts = use_bf16 ? 2.0 : 4.0;
+  const double io = (double)a.B1 * a.H * a.c * ((double)a.X * 4 + (double)a.Y * 2) * ts +
+                    (a.bias ? 4.0 * a.H * (double)a.X * a.Y : 0.0);
+  Prof p(use_bf16 ? "attn_fwd_mma" : "attn_fwd_simt", s, 4.0 * inner, io);
   if (use_bf16) {
     if (!mma_ok(a)) return cudaErrorInvalidValue;
     dim3 grid((a.X + 63) / 64, a.H, a.B1);
@@ -630,6 +635,11 @@ cudaError_t attn_fwd(const AttnArgs &a, int use_bf16, cudaStream_t s) {
 
 cudaError_t attn_bwd(const AttnArgs &a, int use_bf16, cudaStream_t s) {
   if (a.B1 <= 0 || a.X <= 0 || a.H <= 0) return cudaSuccess;
+  const double inner = (double)a.B1 * a.H * a.X * (double)a.Y * a.c;
+  const double ts = use_bf16 ? 2.0 : 4.0;
+  const double io = (double)a.B1 * a.H * a.c * ((double)a.X * (2 * ts + 4) + (double)a.Y * 4 * ts) +
+                    (a.bias ? 8.0 * a.H * (double)a.X * a.Y : 0.0);
+  Prof p(use_bf16 ? "attn_bwd_mma" : "attn_bwd_simt", s, 10.0 * inner, io, use_bf16 ? 1 : 2);
   if (use_bf16) {
     if (!mma_ok(a)) return cudaErrorInvalidValue;
     dim3 grid((a.Y + 63) / 64, a.H, a.B1);

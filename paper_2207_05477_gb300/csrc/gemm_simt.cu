@@ -74,6 +74,8 @@ __global__ void __launch_bounds__(256) gemm_simt_kernel(GemmOp g) {
 cudaError_t gemm_simt_f32(const GemmOp &g, cudaStream_t s) {
   if (g.M <= 0 || g.N <= 0 || g.batch <= 0) return cudaSuccess;
   dim3 grid((g.N + BN - 1) / BN, (g.M + BM - 1) / BM, g.batch * g.splits);
+  Prof p("gemm_simt", s, 2.0 * g.M * g.N * (double)g.K * g.batch,
+         4.0 * g.batch * ((double)g.M * g.K + (double)g.N * g.K + (double)g.M * g.N));
   gemm_simt_kernel<float><<<grid, 256, 0, s>>>(g);
   return cudaGetLastError();
 }

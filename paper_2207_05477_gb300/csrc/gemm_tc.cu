@@ -334,6 +334,9 @@ cudaError_t launch_tc(const GemmOp &g, cudaStream_t s) {
     attr_set = true;
   }
   dim3 grid((g.N + BN - 1) / BN, (g.M + BM - 1) / BM, g.batch * g.splits);
+  const double cbytes = g.e.partial ? 4.0 * g.splits : (g.e.c_f32 ? 4.0 : 2.0);
+  Prof p("gemm_tc", s, 2.0 * g.M * g.N * (double)g.K * g.batch,
+         g.batch * (2.0 * ((double)g.M * g.K + (double)g.N * g.K) + cbytes * g.M * g.N));
   gemm_tc_kernel<BN, STAGES, AMN, BMN><<<grid, 128, C::SMEM, s>>>(ta, tb, g);
   return cudaGetLastError();
 }
@@ -373,6 +376,7 @@ cudaError_t error_word_read_clear(int *out) {
 }
 
 cudaError_t debug_wait(int64_t limit_ns, cudaStream_t s) {
+  Prof p("debug_wait", s);
   debug_wait_kernel<<<1, 32, 0, s>>>(limit_ns);
   return cudaGetLastError();
 }

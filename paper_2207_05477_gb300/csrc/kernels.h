@@ -1,6 +1,7 @@
 // Internal launch interface of libevo's kernels (host side).
 #pragma once
 #include "common.cuh"
+#include "prof.h"
 
 namespace evo {
 

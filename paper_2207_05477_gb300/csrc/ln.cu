@@ -220,12 +220,14 @@ int ln_bwd_cm_blocks(int R) { return R * ((R + 31) / 32); }
 cudaError_t ln_fwd(const void *x, const float *gamma, const float *beta, void *y, int64_t M, int C, int use_bf16,
                    cudaStream_t s) {
   if (M <= 0) return cudaSuccess;
+  Prof p("ln_fwd", s, 0, (use_bf16 ? 4.0 : 8.0) * M * C);
   return use_bf16 ? ln_fwd_t<bf16>(x, gamma, beta, y, M, C, s) : ln_fwd_t<float>(x, gamma, beta, y, M, C, s);
 }
 
 cudaError_t ln_fwd_cm(const void *x, int64_t pitch, const float *gamma, const float *beta, void *y, int R, int C,
                       int use_bf16, cudaStream_t s) {
   if (R <= 0) return cudaSuccess;
+  Prof p("ln_fwd_cm", s, 0, (use_bf16 ? 4.0 : 8.0) * R * (double)R * C);
   dim3 grid((R + 31) / 32, R);
   const size_t sm = (size_t)C * 33 * sizeof(float);
   if (use_bf16)
@@ -238,6 +240,7 @@ cudaError_t ln_fwd_cm(const void *x, int64_t pitch, const float *gamma, const fl
 cudaError_t ln_bwd(const void *dy, const void *x, const float *gamma, float *dacc, void *dcopy, void *dx_out,
                    float *part, int64_t M, int C, int use_bf16, cudaStream_t s) {
   if (M <= 0) return cudaSuccess;
+  Prof p("ln_bwd", s, 0, (use_bf16 ? 2.0 : 4.0) * M * C * (dcopy ? 3 : 2) + (dacc ? 8.0 * M * C : 0.0));
   const int nb = ln_bwd_blocks(M);
   const int64_t rpb = (M + nb - 1) / nb;
   const size_t sm = (size_t)8 * 2 * C * sizeof(float);
@@ -253,6 +256,7 @@ cudaError_t ln_bwd(const void *dy, const void *x, const float *gamma, float *dac
 cudaError_t ln_bwd_cm(const void *dy, const void *x, int64_t pitch, const float *gamma, void *dx, float *part, int R,
                       int C, int use_bf16, cudaStream_t s) {
   if (R <= 0) return cudaSuccess;
+  Prof p("ln_bwd_cm", s, 0, (use_bf16 ? 6.0 : 12.0) * R * (double)R * C);
   dim3 grid((R + 31) / 32, R);
   const size_t sm = ((size_t)2 * C * 33 + (size_t)8 * 2 * C) * sizeof(float);
   if (sm > 48 * 1024) {

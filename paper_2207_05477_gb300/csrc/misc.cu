@@ -268,11 +268,13 @@ inline unsigned nblk(int64_t n, int t = 256) { return (unsigned)((n + t - 1) / t
 }  // namespace
 
 cudaError_t reduce_partials(const float *part, int nb, int N, float *out, cudaStream_t s) {
+  Prof prof("reduce_partials", s, 0, 4.0 * nb * (double)N, 1);
   reduce_partials_k<<<nblk(N), 256, 0, s>>>(part, nb, N, N, out);
   return cudaGetLastError();
 }
 // Variant with a leading dimension (LayerNorm partials hold gamma and beta sums).
 cudaError_t reduce_partials_ld(const float *part, int nb, int64_t ld, int N, float *out, cudaStream_t s) {
+  Prof prof("reduce_partials", s, 0, 4.0 * nb * (double)N, 1);
   reduce_partials_k<<<nblk(N), 256, 0, s>>>(part, nb, ld, N, out);
   return cudaGetLastError();
 }
@@ -282,6 +284,7 @@ int colsum_blocks(int64_t M) {
   return (int)(b < 512 ? (b < 1 ? 1 : b) : 512);
 }
 cudaError_t colsum(const void *x, int64_t ld, int64_t M, int N, float *part, int use_bf16, cudaStream_t s) {
+  Prof prof("colsum", s, 0, (use_bf16 ? 2.0 : 4.0) * M * (double)N, 1);
   const int nb = colsum_blocks(M);
   const int64_t rpb = (M + nb - 1) / nb;
   if (use_bf16) colsum_k<bf16><<<nb, 256, 0, s>>>((const bf16 *)x, ld, M, N, part, rpb);
@@ -290,12 +293,14 @@ cudaError_t colsum(const void *x, int64_t ld, int64_t M, int N, float *part, int
 }
 
 cudaError_t reduce_splits(const float *part, int splits, int64_t n, float *out, cudaStream_t s) {
+  Prof prof("reduce_splits", s, 0, 4.0 * (splits + 2) * (double)n, 1);
   reduce_splits_k<<<nblk(n), 256, 0, s>>>(part, splits, n, out);
   return cudaGetLastError();
 }
 
 cudaError_t head_proj_fwd(const void *x, const float *w, float *out, int R, int C, int H, int transpose, int use_bf16,
                           cudaStream_t s) {
+  Prof prof("head_proj_fwd", s, 2.0 * R * (double)R * C * H, (use_bf16 ? 2.0 : 4.0) * R * (double)R * C + 4.0 * H * R * (double)R, 1);
   if (H > 8) return cudaErrorInvalidValue;
   const int64_t P = (int64_t)R * R;
   if (use_bf16) head_proj_fwd_k<bf16><<<nblk(P, 8), 256, 0, s>>>((const bf16 *)x, w, out, R, C, H, transpose);
@@ -309,6 +314,7 @@ int head_proj_blocks(int R) {
 }
 cudaError_t head_proj_bwd(const float *dbias, const void *x, const float *w, void *dx, int accumulate, float *part,
                           int R, int C, int H, int transpose, int use_bf16, cudaStream_t s) {
+  Prof prof("head_proj_bwd", s, 4.0 * R * (double)R * C * H, (use_bf16 ? 2.0 : 4.0) * R * (double)R * C * (accumulate ? 3 : 2) + 4.0 * H * R * (double)R, 1);
   if (H > 8) return cudaErrorInvalidValue;
   const int nb = head_proj_blocks(R);
   const int64_t ppb = ((int64_t)R * R + nb - 1) / nb;
@@ -325,6 +331,7 @@ cudaError_t head_proj_bwd(const float *dbias, const void *x, const float *w, voi
 
 cudaError_t trimul_gate_fwd(void *abg, int64_t ld, const float *mask, void *A, void *B, int64_t pitch, int R, int cm,
                             int cz, int incoming, int use_bf16, cudaStream_t s) {
+  Prof prof("trimul_gate_fwd", s, 0, (use_bf16 ? 2.0 : 4.0) * R * (double)R * (6.0 * cm + 2.0 * cz), 2);
   dim3 grid((R + 31) / 32, (R + 31) / 32, (cm + 3) / 4);
   const int64_t P = (int64_t)R * R;
   if (use_bf16) {
@@ -341,6 +348,7 @@ cudaError_t trimul_gate_fwd(void *abg, int64_t ld, const float *mask, void *A, v
 
 cudaError_t trimul_gate_bwd(const void *dA, const void *dB, int64_t pitch, const void *abg, int64_t ld,
                             const float *mask, void *dabg, int R, int cm, int incoming, int use_bf16, cudaStream_t s) {
+  Prof prof("trimul_gate_bwd", s, 0, (use_bf16 ? 2.0 : 4.0) * R * (double)R * 10.0 * cm, 1);
   dim3 grid((R + 31) / 32, (R + 31) / 32, (cm + 3) / 4);
   if (use_bf16)
     trimul_gate_bwd_k<bf16><<<grid, 256, 0, s>>>((const bf16 *)dA, (const bf16 *)dB, pitch, (const bf16 *)abg, ld,
@@ -353,6 +361,7 @@ cudaError_t trimul_gate_bwd(const void *dA, const void *dB, int64_t pitch, const
 
 cudaError_t gate_out_bwd(const void *dz, const void *g, int64_t g_ld, const void *y, void *dy, void *dgpre,
                          int64_t dg_ld, int64_t P, int C, int use_bf16, cudaStream_t s) {
+  Prof prof("gate_out_bwd", s, 0, (use_bf16 ? 2.0 : 4.0) * (double)P * C * 5, 1);
   if (use_bf16)
     gate_out_bwd_k<bf16><<<nblk(P * C), 256, 0, s>>>((const bf16 *)dz, (const bf16 *)g, g_ld, (const bf16 *)y,
                                                      (bf16 *)dy, (bf16 *)dgpre, dg_ld, P, C);
@@ -364,6 +373,7 @@ cudaError_t gate_out_bwd(const void *dz, const void *g, int64_t g_ld, const void
 
 cudaError_t attn_gate_bwd(const AttnArgs &a, const void *dog, void *dgpre, int64_t sGb_d, int64_t sGx_d, void *do_att,
                           float *D, int use_bf16, cudaStream_t s) {
+  Prof prof("attn_gate_bwd", s, 0, (use_bf16 ? 2.0 : 4.0) * (double)a.B1 * a.X * a.H * a.c * 5, 1);
   const int64_t rows = (int64_t)a.B1 * a.X;
   if (use_bf16)
     attn_gate_bwd_k<bf16><<<nblk(rows, 8), 256, 0, s>>>(a, (const bf16 *)dog, (bf16 *)dgpre, sGb_d, sGx_d,
@@ -375,6 +385,7 @@ cudaError_t attn_gate_bwd(const AttnArgs &a, const void *dog, void *dgpre, int64
 }
 
 cudaError_t attn_dq_store(const AttnArgs &a, void *dq, int use_bf16, cudaStream_t s) {
+  Prof prof("attn_dq_store", s, 0, (use_bf16 ? 6.0 : 8.0) * (double)a.B1 * a.X * a.H * a.c, 1);
   const int64_t n = (int64_t)a.B1 * a.X * a.H * a.c;
   if (use_bf16) attn_dq_store_k<bf16><<<nblk(n), 256, 0, s>>>(a, (bf16 *)dq);
   else attn_dq_store_k<float><<<nblk(n), 256, 0, s>>>(a, (float *)dq);
@@ -382,27 +393,32 @@ cudaError_t attn_dq_store(const AttnArgs &a, void *dq, int use_bf16, cudaStream_
 }
 
 cudaError_t opm_inv_norm(const float *mask, float *inv, int S, int R, float eps, cudaStream_t s) {
+  Prof prof("opm_inv_norm", s, 0, 8.0 * S * (double)R + 4.0 * R * (double)R, 1);
   opm_inv_norm_k<<<nblk((int64_t)R * R), 256, 0, s>>>(mask, inv, S, R, eps);
   return cudaGetLastError();
 }
 
 cudaError_t row_scale(const void *x, const float *scale, void *y, int64_t M, int C, int use_bf16, cudaStream_t s) {
+  Prof prof("row_scale", s, 0, (use_bf16 ? 4.0 : 8.0) * M * (double)C, 1);
   if (use_bf16) row_scale_k<bf16><<<nblk(M * C), 256, 0, s>>>((const bf16 *)x, scale, (bf16 *)y, M, C);
   else row_scale_k<float><<<nblk(M * C), 256, 0, s>>>((const float *)x, scale, (float *)y, M, C);
   return cudaGetLastError();
 }
 
 cudaError_t to_f32(const void *src, float *dst, int64_t n, int use_bf16, cudaStream_t s) {
+  Prof prof("convert", s, 0, (use_bf16 ? 6.0 : 8.0) * n, 1);
   if (use_bf16) to_f32_k<bf16><<<nblk(n), 256, 0, s>>>((const bf16 *)src, dst, n);
   else to_f32_k<float><<<nblk(n), 256, 0, s>>>((const float *)src, dst, n);
   return cudaGetLastError();
 }
 cudaError_t from_f32(const float *src, void *dst, int64_t n, int use_bf16, cudaStream_t s) {
+  Prof prof("convert", s, 0, (use_bf16 ? 6.0 : 8.0) * n, 1);
   if (use_bf16) from_f32_k<bf16><<<nblk(n), 256, 0, s>>>(src, (bf16 *)dst, n);
   else from_f32_k<float><<<nblk(n), 256, 0, s>>>(src, (float *)dst, n);
   return cudaGetLastError();
 }
 cudaError_t f32_to_bf16(const float *src, bf16 *dst, int64_t n, cudaStream_t s) {
+  Prof prof("convert", s, 0, 6.0 * n, 1);
   from_f32_k<bf16><<<nblk(n), 256, 0, s>>>(src, dst, n);
   return cudaGetLastError();
 }

@@ -1,0 +1,36 @@
+// Per-kernel CUDA-event timing of libevo launches (off unless evo_profile_begin
+// was called).  Each host launch function opens one Prof scope naming its
+// kernel, how many kernels it launches, and the algorithmic flops and bytes of
+// the launch; the scope records an event pair on the launch stream.
+#pragma once
+#include <cuda_runtime.h>
+
+namespace evo {
+
+bool prof_on();
+void prof_record(const char *name, int launches, double flops, double bytes, cudaEvent_t a, cudaEvent_t b);
+cudaEvent_t prof_event();
+
+struct Prof {
+  const char *name;
+  int launches;
+  double flops, bytes;
+  cudaStream_t s;
+  cudaEvent_t a = nullptr, b = nullptr;
+  Prof(const char *n, cudaStream_t st, double f = 0, double by = 0, int nl = 1)
+      : name(n), launches(nl), flops(f), bytes(by), s(st) {
+    if (prof_on()) {
+      a = prof_event();
+      b = prof_event();
+      if (a) cudaEventRecord(a, s);
+    }
+  }
+  ~Prof() {
+    if (a && b) {
+      cudaEventRecord(b, s);
+      prof_record(name, launches, flops, bytes, a, b);
+    }
+  }
+};
+
+}  // namespace evo

@@ -35,6 +35,11 @@ class CDims(ctypes.Structure):
         "c_mul", "c_opm", "trans_n", "msa_col_mode", "act_dtype")]
 
 
+class CProfileEntry(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 32), ("calls", ctypes.c_int32), ("launches", ctypes.c_int32),
+                ("total_ms", ctypes.c_double), ("flops", ctypes.c_double), ("bytes", ctypes.c_double)]
+
+
 class CParamEntry(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 48), ("offset", ctypes.c_int64), ("ndim", ctypes.c_int32),
                 ("shape", ctypes.c_int64 * 4)]
@@ -64,6 +69,8 @@ def lib():
         L.evo_stack_fwd.argtypes = [P(CDims), ctypes.c_int, _vp, _vp, _sz, _vp, _vp, _vp, _vp, _vp, _sz, _vp]
         L.evo_get_error.argtypes = [_vp]
         L.evo_debug_wait_timeout.argtypes = [ctypes.c_longlong, _vp]
+        L.evo_profile_begin.argtypes = []
+        L.evo_profile_end.argtypes = [_vp, P(CProfileEntry), ctypes.c_int]
         L.evo_strerror.argtypes = [ctypes.c_int]
         L.evo_strerror.restype = ctypes.c_char_p
         L.evo_version.restype = ctypes.c_char_p
@@ -155,6 +162,20 @@ def get_error(stream=None):
 
 def debug_wait_timeout(limit_ns, stream=None):
     _check(lib().evo_debug_wait_timeout(int(limit_ns), _stream(stream)), "evo_debug_wait_timeout")
+
+
+def profile_begin():
+    _check(lib().evo_profile_begin(), "evo_profile_begin")
+
+
+def profile_end(stream=None, cap=256):
+    """{kernel name: dict(calls, launches, ms, flops, bytes)} recorded since profile_begin."""
+    arr = (CProfileEntry * cap)()
+    n = lib().evo_profile_end(_stream(stream), arr, cap)
+    if n < 0:
+        raise EvoError(n, "evo_profile_end")
+    return {arr[i].name.decode(): dict(calls=arr[i].calls, launches=arr[i].launches, ms=arr[i].total_ms,
+                                       flops=arr[i].flops, bytes=arr[i].bytes) for i in range(min(n, cap))}
 
 
 # ------------------------------------------------------------- torch glue

@@ -99,3 +99,14 @@ def test_elementwise_fd_on_a_small_tensor():
         mn[idx] -= h
         fd = (_loss(d, *args(mp, z)) - _loss(d, *args(mn, z))) / (2 * h)
         assert abs(fd - float(dm[idx])) <= 1e-6 * max(1.0, abs(fd))
+
+
+def test_pair_bias_layernorm_shift_has_zero_gradient():
+    """beta of the pair-bias LayerNorm adds beta.W_b^h to every logit of head h;
+    softmax is shift-invariant, so its gradient vanishes while gamma's does not."""
+    d = synth.DIMS_TINY
+    prob, mm, pm, gm, gz = _problem(d)
+    params = synth.unpack_params(d, prob["params"])
+    _, _, _, _, dp = O.block_forward_backward(prob["m"], prob["z"], mm, pm, params, d, gm, gz)
+    assert dp["row.ln_z.beta"].abs().max().item() < 1e-12
+    assert dp["row.ln_z.gamma"].abs().max().item() > 1e-3
