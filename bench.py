@@ -1,0 +1,379 @@
+#!/usr/bin/env python
+"""Benchmark of one Evoformer block forward + backward on GB300.
+
+Workload: the paper's initial-training crop (Table "model settings":
+N_seq=128, N_res=256; C_m=256, C_z=128, 8 MSA heads as in the per-layer
+timing table), BF16 activations with FP32 accumulation, 5% padded residues,
+seeded synthetic inputs.  One step = BF16 copy of the parameters, block
+forward, block backward (which recomputes the forward: per-block recompute)
+through the C ABI of libevo.so.
+
+Metric: algorithmic TFLOP/s = 3 x (forward contraction flops) / time, the
+backward counted as twice the forward and the recompute not counted.
+
+Prints ONE JSON line (rank 0).  ``--impl reference`` times the FP64 CPU oracle
+instead (on host cores, rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Evoformer block fwd+bwd ms & TFLOP/s, BF16 vs FP32, GB300, N_res=256 N_seq=128"
+L2_BYTES = 129 * 2 ** 20
+
+
+def block_fwd_flops(d) -> float:
+    """Algorithmic forward flops of one block (2 flops per multiply-add of every contraction)."""
+    S, R, Cm, Cz = d.n_seq, d.n_res, d.c_m, d.c_z
+    Mm, Mz = S * R, R * R
+    HCm, HCt = d.h_msa * d.c_msa, d.h_tri * d.c_tri
+    f = 0.0
+    # MSA row attention with pair bias
+    f += 2 * Mm * Cm * 4 * HCm + 2 * Mz * Cz * d.h_msa + 4 * S * d.h_msa * R * R * d.c_msa + 2 * Mm * HCm * Cm
+    # MSA column attention
+    f += 2 * Mm * Cm * 4 * HCm + 4 * R * d.h_msa * S * S * d.c_msa + 2 * Mm * HCm * Cm
+    # MSA transition
+    f += 2 * 2 * Mm * Cm * d.trans_n * Cm
+    # outer product mean
+    co = d.c_opm
+    f += 2 * Mm * Cm * 2 * co + 2 * (R * co) ** 2 * S + 2 * Mz * co * co * Cz
+    # triangle multiplication x2
+    f += 2 * (2 * Mz * Cz * (4 * d.c_mul + Cz) + 2 * d.c_mul * R ** 3 + 2 * Mz * d.c_mul * Cz)
+    # triangle attention x2
+    f += 2 * (2 * Mz * Cz * d.h_tri + 2 * Mz * Cz * 4 * HCt + 4 * R * d.h_tri * R * R * d.c_tri + 2 * Mz * HCt * Cz)
+    # pair transition
+    f += 2 * 2 * Mz * Cz * d.trans_n * Cz
+    return float(f)
+
+
+def step_flops(d) -> float:
+    return 3.0 * block_fwd_flops(d)
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            j = json.load(f)
+        return dict(hbm=j["hbm_gbs"], bf16=j["bf16_tflops"], bf16_sus=j["bf16_tflops_sustained"], src="measured")
+    return dict(hbm=6800.0, bf16=1900.0, bf16_sus=1700.0, src="fallback")
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        self.f.seek(0)
+        rows = [r.split(",") for r in self.f.read().strip().splitlines() if r.strip()]
+        os.unlink(self.f.name)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].strip().replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if len(r) > 5 + k and "Active" in r[5 + k]
+                          and "Not" not in r[5 + k]})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def run_oracle_step(d, prob):
+    from oracle import evoformer as O
+    from paper_2207_05477_gb300 import synth
+    p = synth.unpack_params(d, prob["params"])
+    t0 = time.perf_counter()
+    O.block_forward_backward(prob["m"], prob["z"], prob["msa_mask"], prob["pair_mask"], p, d, prob["gm"], prob["gz"])
+    return time.perf_counter() - t0
+
+
+def cpu_baseline(d, seed):
+    """The FP64 oracle timed once on the host cores: one full block fwd+bwd of the workload."""
+    import torch
+    from paper_2207_05477_gb300 import synth
+    prob = synth.make_problem(d, seed, pad_frac=0.05)
+    t = run_oracle_step(d, prob)
+    return {"value": step_flops(d) / t / 1e12, "unit": "TFLOP/s", "cores": torch.get_num_threads(), "kind": "oracle",
+            "sample": f"one FP64 block fwd+bwd at N_seq={d.n_seq} N_res={d.n_res} (the full step), {t:.1f} s",
+            "seconds": t}
+
+
+# ---------------------------------------------------------------- reference arm
+def reference_arm(args):
+    world, rank, _ = dist_setup()
+    if rank != 0:
+        return 0
+    import torch
+    from paper_2207_05477_gb300 import synth
+    full = synth.Dims(n_seq=args.n_seq, n_res=args.n_res)
+    # a bounded sample of the workload per step: the same block on a 128-residue crop
+    d = full.replace(n_res=min(128, args.n_res))
+    prob = synth.make_problem(d, 32, pad_frac=0.05)
+    for _ in range(args.warmup):
+        run_oracle_step(d, prob)
+    ts = [run_oracle_step(d, prob) for _ in range(args.steps)]
+    tot = sum(ts)
+    v = step_flops(d) * args.steps / tot / 1e12
+    sample = f"one FP64 block fwd+bwd per step on an N_seq={d.n_seq}, N_res={d.n_res} crop of the workload"
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "TFLOP/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"Evoformer block fwd+bwd, N_seq={full.n_seq} N_res={full.n_res}, c_m=256 c_z=128",
+                       "sample": sample},
+            "cpu_baseline": {"value": v, "unit": "TFLOP/s", "cores": torch.get_num_threads(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": v, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------- our arm
+def ours_arm(args):
+    import torch
+    from paper_2207_05477_gb300 import evo, synth
+    world, rank, local = dist_setup()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    evo.lib()
+
+    d = synth.Dims(n_seq=args.n_seq, n_res=args.n_res)
+    act = evo.EVO_BF16 if args.dtype == "bf16" else evo.EVO_F32
+    tdt = torch.bfloat16 if act == evo.EVO_BF16 else torch.float32
+    cd = evo.cdims(d, act)
+    seed = 32 + rank
+    prob = synth.make_problem(d, seed, pad_frac=0.05)
+
+    # device-resident inputs
+    params = torch.tensor(prob["params"], device=dev)
+    p16 = torch.empty(evo.param_count(cd), dtype=torch.bfloat16, device=dev) if act == evo.EVO_BF16 else None
+    m = torch.tensor(prob["m"], device=dev).to(tdt)
+    z = torch.tensor(prob["z"], device=dev).to(tdt)
+    mm = torch.tensor(prob["msa_mask"], device=dev)
+    pm = torch.tensor(prob["pair_mask"], device=dev)
+    gm = torch.tensor(prob["gm"], device=dev).to(tdt)
+    gz = torch.tensor(prob["gz"], device=dev).to(tdt)
+    m_out, z_out = torch.empty_like(m), torch.empty_like(z)
+    dm, dz = torch.empty_like(m), torch.empty_like(z)
+    dparams = torch.zeros_like(params)
+    ws_f = evo.workspace(cd, evo.EVO_MODE_FWD, dev)
+    ws_b = evo.workspace(cd, evo.EVO_MODE_BWD, dev)
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step(mi, zi, mmi, pmi, gmi, gzi, prm):
+        if p16 is not None:
+            evo.params_to_bf16(cd, prm, p16)
+        evo.block_fwd(cd, prm, p16, mi, zi, m_out, z_out, mmi, pmi, ws_f)
+        evo.block_bwd(cd, prm, p16, mi, zi, mmi, pmi, gmi, gzi, dm, dz, dparams, ws_b)
+
+    for _ in range(args.warmup):
+        step(m, z, mm, pm, gm, gz, params)
+    torch.cuda.synchronize()
+    if evo.get_error() != evo.EVO_OK:
+        raise RuntimeError("device error word set during warm-up")
+
+    # ---- timed region: K steps, L2 flushed between steps (outside each step's events)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    evo.profile_begin()
+    for i in range(args.steps):
+        flush.fill_(float(i))
+        ev[i][0].record(stream)
+        step(m, z, mm, pm, gm, gz, params)
+        ev[i][1].record(stream)
+    prof = evo.profile_end()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    dev_ms = sum(a.elapsed_time(b) for a, b in ev)
+    if evo.get_error() != evo.EVO_OK:
+        raise RuntimeError("device error word set during the timed steps")
+    t = torch.tensor([dev_ms], device=dev, dtype=torch.float64)
+    if world > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    max_ms = float(t.item())
+    value = world * step_flops(d) * args.steps / (max_ms / 1e3) / 1e12
+
+    # ---- end to end through the C ABI with host buffers: H2D of the step's inputs, D2H of its results
+    host = {k: torch.tensor(prob[k]).to(tdt if k in ("m", "z", "gm", "gz") else torch.float32).pin_memory()
+            for k in ("m", "z", "msa_mask", "pair_mask", "gm", "gz", "params")}
+    out_host = {k: torch.empty(v.shape, dtype=v.dtype).pin_memory() for k, v in
+                (("dm", dm), ("dz", dz), ("dparams", dparams))}
+    h2d = sum(v.numel() * v.element_size() for v in host.values())
+    d2h = sum(v.numel() * v.element_size() for v in out_host.values())
+    dbuf = {k: torch.empty(v.shape, dtype=v.dtype, device=dev) for k, v in host.items()}
+    e2e_steps = max(1, min(args.steps, 50))
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(e2e_steps):
+        for k in host:
+            dbuf[k].copy_(host[k], non_blocking=True)
+        step(dbuf["m"], dbuf["z"], dbuf["msa_mask"], dbuf["pair_mask"], dbuf["gm"], dbuf["gz"], dbuf["params"])
+        out_host["dm"].copy_(dm, non_blocking=True)
+        out_host["dz"].copy_(dz, non_blocking=True)
+        out_host["dparams"].copy_(dparams, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1) / e2e_steps
+    te = torch.tensor([e2e_ms], device=dev, dtype=torch.float64)
+    if world > 1:
+        torch.distributed.all_reduce(te, op=torch.distributed.ReduceOp.MAX)
+    e2e_value = world * step_flops(d) / (float(te.item()) / 1e3) / 1e12
+
+    # ---- plain FP32 path, same workload (the comparison the target names)
+    fp32 = None
+    if act == evo.EVO_BF16 and not args.no_fp32:
+        cd32 = evo.cdims(d, evo.EVO_F32)
+        m32, z32 = torch.tensor(prob["m"], device=dev), torch.tensor(prob["z"], device=dev)
+        g32m, g32z = torch.tensor(prob["gm"], device=dev), torch.tensor(prob["gz"], device=dev)
+        mo32, zo32, dm32, dz32 = (torch.empty_like(x) for x in (m32, z32, m32, z32))
+        w32f, w32b = evo.workspace(cd32, evo.EVO_MODE_FWD, dev), evo.workspace(cd32, evo.EVO_MODE_BWD, dev)
+        dp32 = torch.zeros_like(params)
+
+        def step32():
+            evo.block_fwd(cd32, params, None, m32, z32, mo32, zo32, mm, pm, w32f)
+            evo.block_bwd(cd32, params, None, m32, z32, mm, pm, g32m, g32z, dm32, dz32, dp32, w32b)
+
+        step32()
+        torch.cuda.synchronize()
+        n32 = 3
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(n32):
+            step32()
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms32 = a.elapsed_time(b) / n32
+        fp32 = {"ms_per_step": ms32, "tflops": step_flops(d) / (ms32 / 1e3) / 1e12,
+                "bf16_speedup": ms32 / (max_ms / args.steps)}
+        del w32f, w32b
+
+    # ---- roofline of the dominant kernel class of the timed steps
+    peaks = load_peaks()
+    launches = int(sum(v["launches"] for v in prof.values()))
+    dom_name, dom = max(prof.items(), key=lambda kv: kv[1]["ms"])
+    dom_ms_per_launch = dom["ms"] / max(dom["launches"], 1)
+    tensor_kernels = ("gemm_tc", "attn_fwd_mma", "attn_bwd_mma")
+    if dom_name in tensor_kernels:
+        achieved = dom["flops"] / (dom["ms"] / 1e3) / 1e12
+        roof = {"kernel": dom_name, "bound": "tensor", "achieved": achieved, "peak": peaks["bf16_sus"],
+                "unit": "TFLOP/s", "frac": achieved / peaks["bf16_sus"],
+                "peak_kind": f"bf16 dense sustained, {peaks['src']}"}
+    else:
+        achieved = dom["bytes"] / (dom["ms"] / 1e3) / 1e9
+        roof = {"kernel": dom_name, "bound": "hbm", "achieved": achieved, "peak": peaks["hbm"], "unit": "GB/s",
+                "frac": achieved / peaks["hbm"], "peak_kind": f"HBM copy, {peaks['src']}"}
+    roof["ms_per_launch"] = dom_ms_per_launch
+    roof["share_of_step"] = dom["ms"] / max(sum(v["ms"] for v in prof.values()), 1e-9)
+    roof["traffic"] = None
+    tfile = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    if os.path.exists(tfile):
+        with open(tfile) as f:
+            tr = json.load(f)
+        if dom_name in tr and tr[dom_name].get("valid", False):
+            roof["traffic"] = tr[dom_name]["bytes_per_launch"]
+
+    kernels = {k: {"ms_per_step": v["ms"] / args.steps, "launches_per_step": v["launches"] / args.steps,
+                   "share": v["ms"] / max(sum(x["ms"] for x in prof.values()), 1e-9),
+                   "tflops": (v["flops"] / (v["ms"] / 1e3) / 1e12) if v["flops"] else None,
+                   "gbs": (v["bytes"] / (v["ms"] / 1e3) / 1e9) if v["bytes"] else None}
+               for k, v in sorted(prof.items(), key=lambda kv: -kv[1]["ms"])}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(d, 32)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": max_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": args.dtype, "data": "synthetic",
+            "config": {"workload": f"Evoformer block fwd+bwd (per-block recompute), N_seq={d.n_seq} N_res={d.n_res}, "
+                                   f"c_m=256 c_z=128, 5% padded residues",
+                       "n_seq": d.n_seq, "n_res": d.n_res, "flops_per_step": step_flops(d),
+                       "l2": "flushed between timed steps (258 MB write outside the step events)",
+                       "parallelism": f"replicas x{world}"},
+            "clocks": clk, "gpu_launches": launches,
+            "e2e": {"value": e2e_value, "unit": "TFLOP/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                    "ms_per_step": float(te.item())},
+            "roofline": roof, "cpu_baseline": cpu, "fp32_plain": fp32, "kernels": kernels,
+            "paper_context": {"ms_per_layer_fwd_bwd": 32.47, "hardware": "A100 40G, FP16, PPFold DAP=1 BP=1"},
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--dtype", default="bf16", choices=["bf16", "fp32"])
+    ap.add_argument("--n-seq", type=int, default=128)
+    ap.add_argument("--n-res", type=int, default=256)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp32", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        args.warmup = 3
+    if args.impl == "reference":
+        return reference_arm(args)
+    return ours_arm(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())
