@@ -40,11 +40,21 @@ __device__ __forceinline__ uint64_t globaltimer_ns() {
 
 // Output index map of GEMM epilogues:
 // offset(m, n) = (m / mdiv) * s_m1 + (m % mdiv) * s_m0 + (n / ndiv) * s_n1 + (n % ndiv) * s_n0
+// A divisor of 2^31 or more means "no split" along that index; splits use
+// 32-bit division (row and column indices are below 2^31).
 struct OutMap {
   int64_t mdiv, s_m1, s_m0, ndiv, s_n1, s_n0;
-  __host__ __device__ __forceinline__ int64_t operator()(int64_t m, int64_t n) const {
-    return (m / mdiv) * s_m1 + (m % mdiv) * s_m0 + (n / ndiv) * s_n1 + (n % ndiv) * s_n0;
+  __host__ __device__ __forceinline__ int64_t row(int m) const {
+    if (mdiv >= (1ll << 31)) return (int64_t)m * s_m0;
+    const int d = (int)mdiv, q = m / d;
+    return (int64_t)q * s_m1 + (int64_t)(m - q * d) * s_m0;
   }
+  __host__ __device__ __forceinline__ int64_t col(int n) const {
+    if (ndiv >= (1ll << 31)) return (int64_t)n * s_n0;
+    const int d = (int)ndiv, q = n / d;
+    return (int64_t)q * s_n1 + (int64_t)(n - q * d) * s_n0;
+  }
+  __host__ __device__ __forceinline__ int64_t operator()(int m, int n) const { return row(m) + col(n); }
 };
 
 inline OutMap rowmajor_map(int64_t ld) { return OutMap{1ll << 40, 0, ld, 1ll << 40, 0, 1}; }
@@ -78,12 +88,9 @@ struct Epi {
   int M, N;
 };
 
+// Epilogue chain up to (not including) the residual add.
 template <typename T>
-__device__ __forceinline__ void epi_store(const Epi &e, int b, int split, int m, int n, float acc) {
-  if (e.partial) {
-    e.partial[((int64_t)split * e.M + m) * e.N + n] = acc;
-    return;
-  }
+__device__ __forceinline__ float epi_value(const Epi &e, int m, int n, float acc) {
   float v = e.alpha * acc;
   if (e.bias && n >= e.bias_n0) v += e.bias[n - e.bias_n0];
   if (e.row_scale) v *= e.row_scale[m];
@@ -92,6 +99,16 @@ __device__ __forceinline__ void epi_store(const Epi &e, int b, int split, int m,
   else if (e.act == ACT_SIGMOID && n >= e.act_n0) v = 1.f / (1.f + __expf(-v));
   if (e.aux) stf((T *)e.aux + (int64_t)m * e.aux_ld + n, v);
   if (e.gate) v *= ldf((const T *)e.gate + (int64_t)m * e.gate_ld + n);
+  return v;
+}
+
+template <typename T>
+__device__ __forceinline__ void epi_store(const Epi &e, int b, int split, int m, int n, float acc) {
+  if (e.partial) {
+    e.partial[((int64_t)split * e.M + m) * e.N + n] = acc;
+    return;
+  }
+  float v = epi_value<T>(e, m, n, acc);
   const int64_t off = (int64_t)b * e.c_bstride + e.map(m, n);
   if (e.residual) v += ldf((const T *)e.residual + off);
   if (e.c_f32) {
@@ -99,6 +116,62 @@ __device__ __forceinline__ void epi_store(const Epi &e, int b, int split, int m,
     if (e.accumulate) *c += v; else *c = v;
   } else {
     stf((T *)e.C + off, v);
+  }
+}
+
+// Columns n and n+1 (n even) of row m: one 2-element vector load/store where
+// the two outputs are adjacent and aligned, else two scalar ones.
+template <typename T>
+__device__ __forceinline__ void epi_pair(const Epi &e, int b, int split, int m, int n, int64_t rowoff, float a0,
+                                         float a1) {
+  const bool two = n + 1 < e.N;
+  if (!two) {
+    epi_store<T>(e, b, split, m, n, a0);
+    return;
+  }
+  if (e.partial) {
+    float *p = e.partial + ((int64_t)split * e.M + m) * e.N + n;
+    if (((uintptr_t)p & 7u) == 0) *reinterpret_cast<float2 *>(p) = make_float2(a0, a1);
+    else { p[0] = a0; p[1] = a1; }
+    return;
+  }
+  float v0 = epi_value<T>(e, m, n, a0);
+  float v1 = epi_value<T>(e, m, n + 1, a1);
+  const int64_t off0 = rowoff + e.map.col(n);
+  const int64_t off1 = rowoff + e.map.col(n + 1);
+  const bool vec = off1 == off0 + 1 && (off0 & 1) == 0;
+  if (e.residual) {
+    const T *r = (const T *)e.residual;
+    if (vec && is_bf16<T>::value) {
+      const __nv_bfloat162 rr = *reinterpret_cast<const __nv_bfloat162 *>(r + off0);
+      v0 += __low2float(rr);
+      v1 += __high2float(rr);
+    } else {
+      v0 += ldf(r + off0);
+      v1 += ldf(r + off1);
+    }
+  }
+  if (e.c_f32) {
+    float *c = (float *)e.C;
+    if (e.accumulate) {
+      c[off0] += v0;
+      c[off1] += v1;
+    } else if (vec) {
+      *reinterpret_cast<float2 *>(c + off0) = make_float2(v0, v1);
+    } else {
+      c[off0] = v0;
+      c[off1] = v1;
+    }
+  } else {
+    T *c = (T *)e.C;
+    if (vec && is_bf16<T>::value) {
+      *reinterpret_cast<__nv_bfloat162 *>(c + off0) = __floats2bfloat162_rn(v0, v1);
+    } else if (vec) {
+      *reinterpret_cast<float2 *>(c + off0) = make_float2(v0, v1);
+    } else {
+      stf(c + off0, v0);
+      stf(c + off1, v1);
+    }
   }
 }
 

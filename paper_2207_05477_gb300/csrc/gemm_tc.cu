@@ -4,9 +4,9 @@
 // in tensor memory, and the four warps drain TMEM with tcgen05.ld through the
 // shared epilogue (bias, scales, gates, residual, layout-changing stores).
 //
-// Warp roles (128 threads): warp 0 allocates TMEM, lane 0 of warp 0 is the TMA
-// producer, lane 0 of warp 1 issues the MMAs, all four warps run the epilogue
-// (warp w owns TMEM lanes / tile rows 32w..32w+31).
+// Warp roles (256 threads): warp 0 allocates TMEM, lane 0 of warp 0 is the TMA
+// producer, lane 0 of warp 1 issues the MMAs, all eight warps run the epilogue
+// (warps w and w+4 read TMEM lanes / tile rows 32w..32w+31, half the columns each).
 //
 // Operands may be K-major or MN-major (the transpose bits of the instruction
 // descriptor); backward GEMMs (dX = dY W, dW = dY^T X) use MN-major views of
@@ -144,10 +144,12 @@ struct TcCfg {
   // At most 512 TMEM columns per SM across the CTAs that fit by shared memory.
   static_assert((233472 / (SMEM + 1024)) * TMEM_COLS <= 512, "TMEM oversubscription");
   static_assert(BN % 16 == 0 && BN >= 16 && BN <= 256, "UMMA N");
+  // the epilogue stages 8 warps x 32 rows x (64 + 1) floats in the stage buffers
+  static_assert(8 * 32 * ((BN < 64 ? BN : 64) + 1) * 4 <= STAGES * STAGE_BYTES, "epilogue staging");
 };
 
 template <int BN, int STAGES, bool AMN, bool BMN>
-__global__ void __launch_bounds__(128, 1)
+__global__ void __launch_bounds__(256, 2)
     gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, GemmOp g) {
   using C = TcCfg<BN, STAGES, AMN, BMN>;
   extern __shared__ uint8_t dsmem[];
@@ -244,27 +246,91 @@ __global__ void __launch_bounds__(128, 1)
   }
   __syncwarp();
 
-  // ---------------- epilogue
+  // ---------------- epilogue: TMEM -> shared (64-column chunks, in the idle
+  // stage buffers) -> stores with lanes along columns, so every output map
+  // used by the block is written in contiguous runs.  Warps w and w+4 share
+  // TMEM lane quarter w and split the tile's columns.
   bool have = nk > 0;
   if (have) have = mbar_wait(&done_bar, 0, &s_abort);
+  have = __all_sync(0xffffffffu, have);
   tc_fence_after();
-  const int row = warp * 32 + lane;
-  const int m = m0 + row;
-  for (int c0 = 0; c0 < BN; c0 += 16) {
-    if (n0 + c0 >= g.N) break;
-    uint32_t r[16];
-    if (have) {
-      tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, r);
-    } else {
+  const int quarter = warp & 3, half = warp >> 2;
+  constexpr int CH = BN < 64 ? BN : 64;
+  constexpr int LDS = CH + 1;
+  constexpr int NCH = BN / CH;
+  constexpr int CH_PER_HALF = NCH > 1 ? NCH / 2 : 1;
+  if (have || (nk == 0 && !s_abort)) {
+    float *mine = reinterpret_cast<float *>(dsmem + (sbase - raw)) + warp * 32 * LDS;
+    const Epi &e = g.e;
+    const bool fast = !e.partial && !e.c_f32 && !e.relu_ref && !e.aux && !e.gate && e.map.mdiv >= (1ll << 31) &&
+                      e.map.ndiv >= (1ll << 31) && e.map.s_n0 == 1 && (e.map.s_m0 & 1) == 0 &&
+                      (e.c_bstride & 1) == 0;
+    for (int ci = 0; ci < CH_PER_HALF; ++ci) {
+      const int cidx = NCH > 1 ? half * CH_PER_HALF + ci : ci;
+      if (NCH == 1 && half == 1) break;  // a single chunk is drained by warps 0-3
+      const int c0 = cidx * CH;
+      if (n0 + c0 >= g.N) break;
+      if (have) {
 #pragma unroll
-      for (int j = 0; j < 16; ++j) r[j] = 0u;
-    }
-    if (m < g.M && !s_abort) {
+        for (int q = 0; q < CH; q += 16) {
+          uint32_t r[16];
+          tmem_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(c0 + q), r);
 #pragma unroll
-      for (int j = 0; j < 16; ++j) {
-        const int n = n0 + c0 + j;
-        if (n < g.N) epi_store<bf16>(g.e, b, split, m, n, __uint_as_float(r[j]));
+          for (int j = 0; j < 16; ++j) mine[lane * LDS + q + j] = __uint_as_float(r[j]);
+        }
+      } else {
+        for (int j = 0; j < CH; ++j) mine[lane * LDS + j] = 0.f;
       }
+      __syncwarp();
+      const int cc = 2 * lane;
+      const int n = n0 + c0 + cc;
+      if (fast && cc < CH) {
+        // row-major output: bias / activation decisions per lane, one bf16x2 per row
+        const bool ok0 = n < g.N, ok1 = n + 1 < g.N;
+        const float b0 = (e.bias && ok0 && n >= e.bias_n0) ? e.bias[n - e.bias_n0] : 0.f;
+        const float b1 = (e.bias && ok1 && n + 1 >= e.bias_n0) ? e.bias[n + 1 - e.bias_n0] : 0.f;
+        const bool s0 = e.act == ACT_SIGMOID && n >= e.act_n0, s1 = e.act == ACT_SIGMOID && n + 1 >= e.act_n0;
+        const bool relu = e.act == ACT_RELU;
+        bf16 *cb = (bf16 *)e.C + (int64_t)b * e.c_bstride + n;
+        const bf16 *rb = e.residual ? (const bf16 *)e.residual + (int64_t)b * e.c_bstride + n : nullptr;
+        for (int rr = 0; rr < 32; ++rr) {
+          const int m = m0 + quarter * 32 + rr;
+          if (m >= g.M || !ok0) break;
+          float v0 = mine[rr * LDS + cc] * e.alpha + b0;
+          float v1 = mine[rr * LDS + cc + 1] * e.alpha + b1;
+          if (e.row_scale) {
+            const float rs = e.row_scale[m];
+            v0 *= rs;
+            v1 *= rs;
+          }
+          if (relu) {
+            v0 = fmaxf(v0, 0.f);
+            v1 = fmaxf(v1, 0.f);
+          }
+          if (s0) v0 = 1.f / (1.f + __expf(-v0));
+          if (s1) v1 = 1.f / (1.f + __expf(-v1));
+          const int64_t ro = (int64_t)m * e.map.s_m0;
+          if (ok1) {
+            if (rb) {
+              const __nv_bfloat162 r2 = *reinterpret_cast<const __nv_bfloat162 *>(rb + ro);
+              v0 += __low2float(r2);
+              v1 += __high2float(r2);
+            }
+            *reinterpret_cast<__nv_bfloat162 *>(cb + ro) = __floats2bfloat162_rn(v0, v1);
+          } else {
+            if (rb) v0 += __bfloat162float(rb[ro]);
+            cb[ro] = __float2bfloat16_rn(v0);
+          }
+        }
+      } else if (cc < CH) {
+        for (int rr = 0; rr < 32; ++rr) {
+          const int m = m0 + quarter * 32 + rr;
+          if (m >= g.M) break;
+          const int64_t rowoff = (int64_t)b * e.c_bstride + e.map.row(m);
+          if (n < g.N) epi_pair<bf16>(e, b, split, m, n, rowoff, mine[rr * LDS + cc], mine[rr * LDS + cc + 1]);
+        }
+      }
+      __syncwarp();
     }
   }
   if (s_abort && nk > 0 && threadIdx.x == 0) {
@@ -337,7 +403,7 @@ cudaError_t launch_tc(const GemmOp &g, cudaStream_t s) {
   const double cbytes = g.e.partial ? 4.0 * g.splits : (g.e.c_f32 ? 4.0 : 2.0);
   Prof p("gemm_tc", s, 2.0 * g.M * g.N * (double)g.K * g.batch,
          g.batch * (2.0 * ((double)g.M * g.K + (double)g.N * g.K) + cbytes * g.M * g.N));
-  gemm_tc_kernel<BN, STAGES, AMN, BMN><<<grid, 128, C::SMEM, s>>>(ta, tb, g);
+  gemm_tc_kernel<BN, STAGES, AMN, BMN><<<grid, 256, C::SMEM, s>>>(ta, tb, g);
   return cudaGetLastError();
 }
 
@@ -393,8 +459,9 @@ bool gemm_tc_supported(const GemmOp &g) {
 
 cudaError_t gemm_tc_bf16(const GemmOp &g, cudaStream_t s) {
   if (!gemm_tc_supported(g)) return cudaErrorInvalidValue;
-  if (g.N > 128 && g.N % 256 == 0) return dispatch_major<256, 3>(g, s);
-  if (g.N > 64) return dispatch_major<128, 4>(g, s);
+  // stage counts keep two CTAs resident per SM (shared memory and 512 TMEM columns)
+  if (g.N > 128 && g.N % 256 == 0) return dispatch_major<256, 2>(g, s);
+  if (g.N > 64) return dispatch_major<128, 3>(g, s);
   return dispatch_major<64, 4>(g, s);
 }
 

@@ -213,7 +213,7 @@ cudaError_t ln_fwd_t(const void *x, const float *gamma, const float *beta, void 
 
 int ln_bwd_blocks(int64_t M) {
   int64_t b = (M + 63) / 64;
-  return (int)(b < 1024 ? (b < 1 ? 1 : b) : 1024);
+  return (int)(b < 296 ? (b < 1 ? 1 : b) : 296);
 }
 int ln_bwd_cm_blocks(int R) { return R * ((R + 31) / 32); }
 

@@ -7,23 +7,61 @@
 namespace evo {
 namespace {
 
-// ------------------------------------------------------------- reductions
-__global__ void reduce_partials_k(const float *part, int nblk, int64_t ld, int N, float *out) {
-  const int n = blockIdx.x * blockDim.x + threadIdx.x;
-  if (n >= N) return;
-  float t = 0.f;
-  for (int b = 0; b < nblk; ++b) t += part[(int64_t)b * ld + n];
-  out[n] += t;
+// q = i / d, r = i % d with 32-bit division when i fits.
+__device__ __forceinline__ void divmod(int64_t i, int d, int64_t &q, int &r) {
+  if (i < (1ll << 31)) {
+    const int ii = (int)i, qq = ii / d;
+    q = qq;
+    r = ii - qq * d;
+  } else {
+    q = i / d;
+    r = (int)(i - q * d);
+  }
 }
 
+// ------------------------------------------------------------- reductions
+// 32 columns per block; the 8 warps split the partial rows, then combine.
+__global__ void __launch_bounds__(256) reduce_partials_k(const float *part, int nblk, int64_t ld, int N, float *out) {
+  __shared__ float s[8][33];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int n = blockIdx.x * 32 + lane;
+  float t = 0.f;
+  if (n < N)
+    for (int b = w; b < nblk; b += 8) t += part[(int64_t)b * ld + n];
+  s[w][lane] = t;
+  __syncthreads();
+  if (w == 0 && n < N) {
+    float tot = 0.f;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) tot += s[k][lane];
+    out[n] += tot;
+  }
+}
+
+// Column sums: block (64 columns, a range of rows); each lane owns two
+// adjacent columns, the 8 warps split the rows, then combine.
 template <typename T>
-__global__ void colsum_k(const T *x, int64_t ld, int64_t M, int N, float *part, int64_t rows_per_blk) {
-  const int64_t r0 = (int64_t)blockIdx.x * rows_per_blk;
+__global__ void __launch_bounds__(256) colsum_k(const T *x, int64_t ld, int64_t M, int N, float *part,
+                                                int64_t rows_per_blk) {
+  __shared__ float s[8][64];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int n = blockIdx.x * 64 + 2 * lane;
+  const int64_t r0 = (int64_t)blockIdx.y * rows_per_blk;
   const int64_t r1 = min(M, r0 + rows_per_blk);
-  for (int n = threadIdx.x; n < N; n += blockDim.x) {
-    float t = 0.f;
-    for (int64_t r = r0; r < r1; ++r) t += ldf(x + r * ld + n);
-    part[(int64_t)blockIdx.x * N + n] = t;
+  float t0 = 0.f, t1 = 0.f;
+  for (int64_t r = r0 + w; r < r1; r += 8) {
+    if (n < N) t0 += ldf(x + r * ld + n);
+    if (n + 1 < N) t1 += ldf(x + r * ld + n + 1);
+  }
+  s[w][2 * lane] = t0;
+  s[w][2 * lane + 1] = t1;
+  __syncthreads();
+  if (threadIdx.x < 64) {
+    const int nn = blockIdx.x * 64 + threadIdx.x;
+    float tot = 0.f;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) tot += s[k][threadIdx.x];
+    if (nn < N) part[(int64_t)blockIdx.y * N + nn] = tot;
   }
 }
 
@@ -51,8 +89,10 @@ __global__ void head_proj_fwd_k(const T *x, const float *w, float *out, int R, i
     for (int h = 0; h < 8; ++h)
       if (h < H) acc[h] = fmaf(xv, w[h * C + cc], acc[h]);
   }
-  const int64_t i = p / R, j = p % R;
-  const int64_t pp = transpose ? j * R + i : p;
+  int64_t i;
+  int j;
+  divmod(p, R, i, j);
+  const int64_t pp = transpose ? (int64_t)j * R + i : p;
 #pragma unroll
   for (int h = 0; h < 8; ++h) {
     if (h >= H) break;
@@ -73,8 +113,10 @@ __global__ void __launch_bounds__(256) head_proj_bwd_k(const float *dbias, const
   const int64_t p0 = (int64_t)blockIdx.x * pos_per_blk;
   const int64_t p1 = min(P, p0 + pos_per_blk);
   for (int64_t p = p0 + warp; p < p1; p += 8) {
-    const int64_t i = p / R, j = p % R;
-    const int64_t pp = transpose ? j * R + i : p;
+    int64_t i;
+    int j;
+    divmod(p, R, i, j);
+    const int64_t pp = transpose ? (int64_t)j * R + i : p;
     float g[8];
 #pragma unroll
     for (int h = 0; h < 8; ++h) g[h] = h < H ? dbias[h * P + pp] : 0.f;
@@ -180,8 +222,9 @@ template <typename T>
 __global__ void sigmoid_cols_k(T *x, int64_t ld, int col0, int ncols, int64_t P) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= P * ncols) return;
-  const int64_t p = i / ncols;
-  const int c = (int)(i % ncols);
+  int64_t p;
+  int c;
+  divmod(i, ncols, p, c);
   T *e = x + p * ld + col0 + c;
   stf(e, sigmoidf_(ldf(e)));
 }
@@ -191,8 +234,9 @@ __global__ void gate_out_bwd_k(const T *dz, const T *g, int64_t g_ld, const T *y
                                int64_t P, int C) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= P * C) return;
-  const int64_t p = i / C;
-  const int c = (int)(i % C);
+  int64_t p;
+  int c;
+  divmod(i, C, p, c);
   const float d = ldf(dz + i), gv = ldf(g + p * g_ld + c), yv = ldf(y + i);
   stf(dy + i, d * gv);
   stf(dgpre + p * dg_ld + c, d * yv * gv * (1.f - gv));
@@ -205,7 +249,9 @@ __global__ void attn_gate_bwd_k(AttnArgs a, const T *dog, T *dgpre, int64_t sGb_
   const int lane = threadIdx.x & 31;
   const int64_t row = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
   if (row >= (int64_t)a.B1 * a.X) return;
-  const int64_t b = row / a.X, x = row % a.X;
+  int64_t b;
+  int x;
+  divmod(row, a.X, b, x);
   const int64_t ob = b * a.sOb + x * a.sOx;
   const int64_t gb = b * a.sQb + x * a.sQx;
   const int64_t db = b * sGb_d + x * sGx_d;
@@ -229,9 +275,10 @@ __global__ void attn_dq_store_k(AttnArgs a, T *dq) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int hc = a.H * a.c;
   if (i >= (int64_t)a.B1 * a.X * hc) return;
-  const int64_t row = i / hc;
-  const int k = (int)(i % hc);
-  const int64_t b = row / a.X, x = row % a.X;
+  int64_t row, b;
+  int k, x;
+  divmod(i, hc, row, k);
+  divmod(row, a.X, b, x);
   stf(dq + b * a.sQb + x * a.sQx + k, a.scale * a.dq_acc[b * a.sOb + x * a.sOx + k]);
 }
 
@@ -239,7 +286,10 @@ __global__ void attn_dq_store_k(AttnArgs a, T *dq) {
 __global__ void opm_inv_norm_k(const float *mask, float *inv, int S, int R, float eps) {
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= (int64_t)R * R) return;
-  const int i = (int)(idx / R), j = (int)(idx % R);
+  int64_t i64;
+  int j;
+  divmod(idx, R, i64, j);
+  const int i = (int)i64;
   float n = 0.f;
   for (int s = 0; s < S; ++s) n += mask[(int64_t)s * R + i] * mask[(int64_t)s * R + j];
   inv[idx] = 1.f / (eps + n);
@@ -249,7 +299,10 @@ template <typename T>
 __global__ void row_scale_k(const T *x, const float *scale, T *y, int64_t M, int C) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= M * C) return;
-  stf(y + i, ldf(x + i) * scale[i / C]);
+  int64_t r;
+  int c;
+  divmod(i, C, r, c);
+  stf(y + i, ldf(x + i) * scale[r]);
 }
 
 template <typename T>
@@ -269,26 +322,27 @@ inline unsigned nblk(int64_t n, int t = 256) { return (unsigned)((n + t - 1) / t
 
 cudaError_t reduce_partials(const float *part, int nb, int N, float *out, cudaStream_t s) {
   Prof prof("reduce_partials", s, 0, 4.0 * nb * (double)N, 1);
-  reduce_partials_k<<<nblk(N), 256, 0, s>>>(part, nb, N, N, out);
+  reduce_partials_k<<<(N + 31) / 32, 256, 0, s>>>(part, nb, N, N, out);
   return cudaGetLastError();
 }
 // Variant with a leading dimension (LayerNorm partials hold gamma and beta sums).
 cudaError_t reduce_partials_ld(const float *part, int nb, int64_t ld, int N, float *out, cudaStream_t s) {
   Prof prof("reduce_partials", s, 0, 4.0 * nb * (double)N, 1);
-  reduce_partials_k<<<nblk(N), 256, 0, s>>>(part, nb, ld, N, out);
+  reduce_partials_k<<<(N + 31) / 32, 256, 0, s>>>(part, nb, ld, N, out);
   return cudaGetLastError();
 }
 
 int colsum_blocks(int64_t M) {
-  int64_t b = (M + 127) / 128;
-  return (int)(b < 512 ? (b < 1 ? 1 : b) : 512);
+  int64_t b = (M + 255) / 256;
+  return (int)(b < 296 ? (b < 1 ? 1 : b) : 296);
 }
 cudaError_t colsum(const void *x, int64_t ld, int64_t M, int N, float *part, int use_bf16, cudaStream_t s) {
   Prof prof("colsum", s, 0, (use_bf16 ? 2.0 : 4.0) * M * (double)N, 1);
   const int nb = colsum_blocks(M);
   const int64_t rpb = (M + nb - 1) / nb;
-  if (use_bf16) colsum_k<bf16><<<nb, 256, 0, s>>>((const bf16 *)x, ld, M, N, part, rpb);
-  else colsum_k<float><<<nb, 256, 0, s>>>((const float *)x, ld, M, N, part, rpb);
+  const dim3 grid((N + 63) / 64, nb);
+  if (use_bf16) colsum_k<bf16><<<grid, 256, 0, s>>>((const bf16 *)x, ld, M, N, part, rpb);
+  else colsum_k<float><<<grid, 256, 0, s>>>((const float *)x, ld, M, N, part, rpb);
   return cudaGetLastError();
 }
 
@@ -310,7 +364,7 @@ cudaError_t head_proj_fwd(const void *x, const float *w, float *out, int R, int 
 
 int head_proj_blocks(int R) {
   int64_t b = ((int64_t)R * R + 63) / 64;
-  return (int)(b < 1024 ? (b < 1 ? 1 : b) : 1024);
+  return (int)(b < 296 ? (b < 1 ? 1 : b) : 296);
 }
 cudaError_t head_proj_bwd(const float *dbias, const void *x, const float *w, void *dx, int accumulate, float *part,
                           int R, int C, int H, int transpose, int use_bf16, cudaStream_t s) {
