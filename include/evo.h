@@ -127,6 +127,28 @@ int evo_stack_fwd(const evo_dims *d, int n_blocks, const float *params,
                   void *m, void *z, const float *msa_mask, const float *pair_mask,
                   void *workspace, size_t ws_bytes, evo_stream_t stream);
 
+/* Forward of one block, as evo_block_fwd, but allocating nothing and taking
+ * no workspace: its scratch is a 128 MiB array inside the library, reserved
+ * on every GPU that loads it until the process exits.  This is a library
+ * convenience with no counterpart in the paper.  It is meant for callers that
+ * cannot allocate device memory when they call (a server whose device memory
+ * was divided up at start-up, a host callback or latency-critical loop where
+ * cudaMalloc's possible device synchronisation is not acceptable) and do not
+ * want to hold a workspace of their own.
+ *  - Inputs and outputs are caller-owned device buffers, exactly as for
+ *    evo_block_fwd (256-byte aligned; m_out may equal m_in, z_out z_in).
+ *  - Returns EVO_ERR_WORKSPACE when the problem needs more scratch than
+ *    128 MiB (evo_workspace_size(d, EVO_MODE_FWD) > 128 MiB).
+ *  - The first call on a device looks up the array's device address on the
+ *    current device (cudaGetSymbolAddress); make that first call before any
+ *    stream capture.
+ *  - Every call uses the same array: calls that may overlap on the GPU (other
+ *    streams, other host threads) race and must be serialised by the caller.
+ *    Nothing in the array needs to start at zero. */
+int evo_block_fwd_noalloc(const evo_dims *d, const float *params, const void *params_bf16,
+                          const void *m_in, const void *z_in, void *m_out, void *z_out,
+                          const float *msa_mask, const float *pair_mask, evo_stream_t stream);
+
 /* Waits for the stream, then returns and clears the device error word:
  * EVO_OK, or EVO_ERR_TIMEOUT if a bounded in-kernel wait gave up since the
  * last call. */

@@ -66,6 +66,7 @@ def lib():
         L.evo_block_fwd.argtypes = [P(CDims), _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _sz, _vp]
         L.evo_block_bwd.argtypes = [P(CDims), _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _sz,
                                     _vp]
+        L.evo_block_fwd_noalloc.argtypes = [P(CDims), _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]
         L.evo_stack_fwd.argtypes = [P(CDims), ctypes.c_int, _vp, _vp, _sz, _vp, _vp, _vp, _vp, _vp, _sz, _vp]
         L.evo_get_error.argtypes = [_vp]
         L.evo_debug_wait_timeout.argtypes = [ctypes.c_longlong, _vp]
@@ -141,6 +142,13 @@ def block_fwd(cd, params, params_bf16, m, z, m_out, z_out, msa_mask, pair_mask, 
     _check(lib().evo_block_fwd(ctypes.byref(cd), _ptr(params), _ptr(params_bf16), _ptr(m), _ptr(z), _ptr(m_out),
                                _ptr(z_out), _ptr(msa_mask), _ptr(pair_mask), _ptr(ws), ws.numel() * ws.element_size(),
                                _stream(stream)), "evo_block_fwd")
+
+
+def block_fwd_noalloc(cd, params, params_bf16, m, z, m_out, z_out, msa_mask, pair_mask, stream=None):
+    """Block forward with the library's own fixed scratch (no workspace, no allocation)."""
+    _check(lib().evo_block_fwd_noalloc(ctypes.byref(cd), _ptr(params), _ptr(params_bf16), _ptr(m), _ptr(z),
+                                       _ptr(m_out), _ptr(z_out), _ptr(msa_mask), _ptr(pair_mask), _stream(stream)),
+           "evo_block_fwd_noalloc")
 
 
 def block_bwd(cd, params, params_bf16, m, z, msa_mask, pair_mask, dm_out, dz_out, dm_in, dz_in, dparams, ws,
