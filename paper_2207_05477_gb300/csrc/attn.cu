@@ -57,6 +57,41 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
   return *reinterpret_cast<uint32_t *>(&v);
 }
 
+// Coalesced copy of the pair-bias tile bias[h][x0 + r][y0 + q] (r, q < 64) into
+// shared memory, pre-scaled by log2(e); zero outside [X, Y).
+__device__ __forceinline__ void load_bias_tile(float (*dst)[68], const AttnArgs &a, int h, int x0, int y0) {
+  const float *src = a.bias + (int64_t)h * a.sBh;
+  const bool vec = ((a.sBx & 3) == 0) && ((a.sBh & 3) == 0) && (((uintptr_t)a.bias & 15u) == 0);
+  for (int idx = threadIdx.x; idx < 64 * 16; idx += blockDim.x) {
+    const int r = idx >> 4, q4 = (idx & 15) * 4;
+    const int x = x0 + r, y = y0 + q4;
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (x < a.X) {
+      const float *p = src + (int64_t)x * a.sBx + y;
+      if (vec && y + 3 < a.Y) {
+        v = *reinterpret_cast<const float4 *>(p);
+      } else {
+        if (y < a.Y) v.x = p[0];
+        if (y + 1 < a.Y) v.y = p[1];
+        if (y + 2 < a.Y) v.z = p[2];
+        if (y + 3 < a.Y) v.w = p[3];
+      }
+    }
+    dst[r][q4] = v.x * EVO_LOG2E;
+    dst[r][q4 + 1] = v.y * EVO_LOG2E;
+    dst[r][q4 + 2] = v.z * EVO_LOG2E;
+    dst[r][q4 + 3] = v.w * EVO_LOG2E;
+  }
+}
+
+__device__ __forceinline__ void red_add_v2(float *p, float a, float b) {
+  asm volatile("red.global.add.v2.f32 [%0], {%1, %2};" ::"l"(p), "f"(a), "f"(b) : "memory");
+}
+__device__ __forceinline__ void red_add_v4(float *p, float a, float b, float c, float d) {
+  asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(a), "f"(b), "f"(c), "f"(d)
+               : "memory");
+}
+
 // Copies a [64 x c] bf16 tile (rows r0.., row stride ld elements) into smem
 // rows of LD elements, zero-filling rows >= nrows and columns >= c.
 template <int CP, int LD>
@@ -78,6 +113,7 @@ __global__ void __launch_bounds__(128) attn_fwd_mma(AttnArgs a) {
   __shared__ __align__(16) bf16 Ks[2][64][LD];
   __shared__ __align__(16) bf16 Vs[2][64][LD];
   __shared__ float Ms[2][64];
+  __shared__ float Bs[64][68];  // pair-bias tile (log2 units) of the current key tile
   const int b = blockIdx.z, h = blockIdx.y, x0 = blockIdx.x * 64;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, gq = lane >> 2, t = lane & 3;
   const int c = a.c;
@@ -119,6 +155,7 @@ __global__ void __launch_bounds__(128) attn_fwd_mma(AttnArgs a) {
     } else {
       cp_wait<0>();
     }
+    if (a.bias) load_bias_tile(Bs, a, h, x0, kt * 64);
     __syncthreads();
     if (kt == 0) {
 #pragma unroll
@@ -141,16 +178,13 @@ __global__ void __launch_bounds__(128) attn_fwd_mma(AttnArgs a) {
         mma16816(s[nt + 1], qa[ks], r[2], r[3]);
       }
     }
-    const int y0 = kt * 64;
 #pragma unroll
     for (int nt = 0; nt < 8; ++nt) {
 #pragma unroll
       for (int e = 0; e < 4; ++e) {
         const int kc = nt * 8 + 2 * t + (e & 1);
-        const int x = xr[e >> 1];
         float v = s[nt][e] * sl2;
-        if (a.bias && x < a.X && y0 + kc < a.Y)
-          v += a.bias[(int64_t)h * a.sBh + (int64_t)x * a.sBx + y0 + kc] * EVO_LOG2E;
+        if (a.bias) v += Bs[warp * 16 + gq + 8 * (e >> 1)][kc];
         s[nt][e] = Ms[buf][kc] != 0.f ? v : NEG_INF;
       }
     }
@@ -237,7 +271,7 @@ __global__ void __launch_bounds__(128) attn_bwd_mma(AttnArgs a) {
   __shared__ __align__(16) bf16 Qs[64][LD];
   __shared__ __align__(16) bf16 dOs[64][LD];
   __shared__ __align__(16) bf16 dSs[64][64 + 8];  // [query][key]
-  __shared__ float dSf[64][65];                    // [query][key]
+  __shared__ float dSf[64][68];                    // [query][key]: bias tile, then dS
   __shared__ float lse_s[64], D_s[64], kval[64];
   const int b = blockIdx.z, h = blockIdx.y, y0 = blockIdx.x * 64;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, gq = lane >> 2, t = lane & 3;
@@ -283,6 +317,7 @@ __global__ void __launch_bounds__(128) attn_bwd_mma(AttnArgs a) {
       lse_s[r] = x < a.X ? a.lse2[li] : POS_INF;
       D_s[r] = x < a.X ? a.Dsum[li] : 0.f;
     }
+    if (a.bias) load_bias_tile(dSf, a, h, x0, y0);
     cp_wait<0>();
     __syncthreads();
     float st[8][4], dp[8][4];
@@ -314,15 +349,21 @@ __global__ void __launch_bounds__(128) attn_bwd_mma(AttnArgs a) {
         float p = 0.f;
         if (kval[krow] != 0.f && x < a.X) {
           float v = st[nt][e] * sl2;
-          if (a.bias) v += a.bias[(int64_t)h * a.sBh + (int64_t)x * a.sBx + y] * EVO_LOG2E;
+          if (a.bias) v += dSf[qc][krow];
           p = exp2f(v - lse_s[qc]);
         }
         const float ds = p * (dp[nt][e] - D_s[qc]);
         st[nt][e] = p;
         dp[nt][e] = ds;
         dSs[qc][krow] = __float2bfloat16_rn(ds);
-        dSf[qc][krow] = ds;
       }
+    }
+    if (a.bias) {
+      __syncthreads();  // every thread has read its bias values
+#pragma unroll
+      for (int nt = 0; nt < 8; ++nt)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) dSf[nt * 8 + 2 * t + (e & 1)][kr[e >> 1]] = dp[nt][e];
     }
 #pragma unroll
     for (int kk = 0; kk < 4; ++kk) {
@@ -374,20 +415,26 @@ __global__ void __launch_bounds__(128) attn_bwd_mma(AttnArgs a) {
 #pragma unroll
         for (int dd = 0; dd < CP / 8; ++dd) {
           const int d = dd * 8 + 2 * t;
-          if (d < c) {
-            atomicAdd(dst + d, dq[dd][2 * r]);
-            atomicAdd(dst + d + 1, dq[dd][2 * r + 1]);
-          }
+          if (d < c) red_add_v2(dst + d, dq[dd][2 * r], dq[dd][2 * r + 1]);
         }
       }
     }
     if (a.dbias) {
-      for (int idx = threadIdx.x; idx < 64 * 64; idx += blockDim.x) {
-        const int qc = idx >> 6, krow = idx & 63;
-        const int x = x0 + qc, y = y0 + krow;
-        const float v = dSf[qc][krow];
-        if (x < a.X && y < a.Y && v != 0.f)
-          atomicAdd(a.dbias + (int64_t)h * a.sBh + (int64_t)x * a.sBx + y, v);
+      const bool vec = ((a.sBx & 3) == 0) && ((a.sBh & 3) == 0) && (((uintptr_t)a.dbias & 15u) == 0);
+      for (int idx = threadIdx.x; idx < 64 * 16; idx += blockDim.x) {
+        const int qc = idx >> 4, k4 = (idx & 15) * 4;
+        const int x = x0 + qc, y = y0 + k4;
+        if (x >= a.X || y >= a.Y) continue;
+        float *dst = a.dbias + (int64_t)h * a.sBh + (int64_t)x * a.sBx + y;
+        const float v0 = dSf[qc][k4], v1 = dSf[qc][k4 + 1], v2 = dSf[qc][k4 + 2], v3 = dSf[qc][k4 + 3];
+        if (vec && y + 3 < a.Y) {
+          if (v0 != 0.f || v1 != 0.f || v2 != 0.f || v3 != 0.f) red_add_v4(dst, v0, v1, v2, v3);
+        } else {
+          if (v0 != 0.f) atomicAdd(dst, v0);
+          if (y + 1 < a.Y && v1 != 0.f) atomicAdd(dst + 1, v1);
+          if (y + 2 < a.Y && v2 != 0.f) atomicAdd(dst + 2, v2);
+          if (y + 3 < a.Y && v3 != 0.f) atomicAdd(dst + 3, v3);
+        }
       }
     }
     __syncthreads();

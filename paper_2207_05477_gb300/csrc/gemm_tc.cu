@@ -4,9 +4,11 @@
 // in tensor memory, and the four warps drain TMEM with tcgen05.ld through the
 // shared epilogue (bias, scales, gates, residual, layout-changing stores).
 //
-// Warp roles (256 threads): warp 0 allocates TMEM, lane 0 of warp 0 is the TMA
-// producer, lane 0 of warp 1 issues the MMAs, all eight warps run the epilogue
-// (warps w and w+4 read TMEM lanes / tile rows 32w..32w+31, half the columns each).
+// The kernel is persistent (one CTA per SM) and warp-specialised: lane 0 of
+// warp 0 streams A/B k-tiles with TMA through a STAGES-deep ring, running
+// ahead across output tiles; lane 0 of warp 1 issues the MMAs into one of two
+// TMEM accumulators; warps 2-5 drain the other accumulator through the
+// epilogue, so a tile's epilogue overlaps the next tile's loads and MMAs.
 //
 // Operands may be K-major or MN-major (the transpose bits of the instruction
 // descriptor); backward GEMMs (dX = dY W, dW = dY^T X) use MN-major views of
@@ -16,6 +18,9 @@
 // wait that runs out sets the library's device error word, the CTA drains its
 // in-flight copies with bounded waits, frees its TMEM and returns.
 #include <cuda.h>
+
+#include <algorithm>
+#include <cstring>
 
 #include "kernels.h"
 
@@ -77,6 +82,25 @@ __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap *tm,
       : "memory");
 }
 
+__device__ __forceinline__ void tma_store_3d(const CUtensorMap *tm, uint32_t src, int c0, int c1, int c2) {
+  asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%1, %2, %3}], [%4];" ::"l"((uint64_t)tm),
+               "r"(c0), "r"(c1), "r"(c2), "r"(src)
+               : "memory");
+}
+__device__ __forceinline__ void tma_store_4d(const CUtensorMap *tm, uint32_t src, int c0, int c1, int c2, int c3) {
+  asm volatile("cp.async.bulk.tensor.4d.global.shared::cta.bulk_group [%0, {%1, %2, %3, %4}], [%5];" ::"l"(
+                   (uint64_t)tm),
+               "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(src)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void bulk_wait_read() {
+  asm volatile("cp.async.bulk.wait_group.read %0;" ::"n"(N) : "memory");
+}
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
 __device__ __forceinline__ void tc_fence_before() {
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
 }
@@ -126,13 +150,26 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// Persistent kernel configuration: a STAGES-deep ring of A/B k-tiles, an
+// epilogue staging area for the four epilogue warps, and two TMEM
+// accumulators of BN columns (tile i drains while tile i+1 accumulates).
 template <int BN, int STAGES, bool AMN, bool BMN>
 struct TcCfg {
   static constexpr int A_BYTES = BM * BK * 2;
   static constexpr int B_BYTES = BN * BK * 2;
   static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
-  static constexpr int SMEM = STAGES * STAGE_BYTES + 1024;
-  static constexpr int TMEM_COLS = BN < 32 ? 32 : BN;
+  static constexpr int CH = BN < 64 ? BN : 64;  // epilogue column chunk
+  static constexpr int LDS = CH + 1;            // staged row pitch (floats)
+  static constexpr int EPI_WARP_BYTES = 9216;  // two 1 KB-aligned 4 KB TMA buffers, or 32 x LDS floats
+  static constexpr int EPI_WARPS = 8;  // two per TMEM lane quarter, splitting the 64-column chunks
+  static constexpr int EPI_BYTES = EPI_WARPS * EPI_WARP_BYTES;
+  static_assert(32 * LDS * 4 <= EPI_WARP_BYTES, "epilogue staging");
+  static constexpr int SMEM = STAGES * STAGE_BYTES + EPI_BYTES + 1024;
+  static constexpr int TMEM_COLS = 2 * BN < 32 ? 32 : 2 * BN;
   // A K-major tile: rows of 128 B, k-step of 16 elements = 32 B.
   // An MN-major tile: 64-element (128 B) MN chunks of 64 K-rows (8 KB each);
   // a k-step of 16 rows = 2 KB.
@@ -141,47 +178,206 @@ struct TcCfg {
   static constexpr uint32_t A_LBO = AMN ? 8192u : 16u;
   static constexpr uint32_t B_LBO = BMN ? 8192u : 16u;
   static constexpr uint32_t IDESC = instr_desc(BM, BN, AMN, BMN);
-  // At most 512 TMEM columns per SM across the CTAs that fit by shared memory.
-  static_assert((233472 / (SMEM + 1024)) * TMEM_COLS <= 512, "TMEM oversubscription");
   static_assert(BN % 16 == 0 && BN >= 16 && BN <= 256, "UMMA N");
-  // the epilogue stages 8 warps x 32 rows x (64 + 1) floats in the stage buffers
-  static_assert(8 * 32 * ((BN < 64 ? BN : 64) + 1) * 4 <= STAGES * STAGE_BYTES, "epilogue staging");
+  static_assert(TMEM_COLS <= 512 && (TMEM_COLS & (TMEM_COLS - 1)) == 0, "TMEM columns");
+  // one CTA per SM: more than half of the SM's shared memory
+  static_assert(SMEM > 233472 / 2 && SMEM <= 232448, "one resident CTA per SM");
 };
 
+struct TileCoord {
+  int m0, n0, b, split, kt0, nk;
+};
+
+__device__ __forceinline__ TileCoord decode_tile(const GemmOp &g, int t, int bn) {
+  const int ntn = (g.N + bn - 1) / bn, ntm = (g.M + BM - 1) / BM;
+  TileCoord c;
+  const int nn = t % ntn;
+  int rest = t / ntn;
+  const int mm = rest % ntm;
+  rest /= ntm;
+  c.b = rest / g.splits;
+  c.split = rest % g.splits;
+  c.m0 = mm * BM;
+  c.n0 = nn * bn;
+  const int kt_total = (g.K + BK - 1) / BK;
+  const int per = (kt_total + g.splits - 1) / g.splits;
+  c.kt0 = c.split * per;
+  c.nk = max(0, min(kt_total, c.kt0 + per) - c.kt0);
+  return c;
+}
+
+// Stores one staged 32-row x CH-column chunk (rows mrow0.., columns n..)
+// through the epilogue chain; lane owns columns n, n+1.
+__device__ __forceinline__ void epi_chunk(const GemmOp &g, const float *mine, int lane, int mrow0, int nbase, int ch,
+                                          int b, int split, int64_t my_rowoff, bool rows_even) {
+  constexpr int LDS_ = 65;
+  const Epi &e = g.e;
+  const int cc = 2 * lane;
+  const int n = nbase + cc;
+  const bool ok0 = cc < ch && n < g.N, ok1 = ok0 && n + 1 < g.N;
+  const int ld = ch + 1;
+  (void)LDS_;
+  if (e.partial) {
+    for (int rr = 0; rr < 32; ++rr) {
+      const int m = mrow0 + rr;
+      if (m >= g.M) break;
+      if (!ok0) continue;
+      float *p = e.partial + ((int64_t)split * e.M + m) * e.N + n;
+      const float a0 = mine[rr * ld + cc], a1 = mine[rr * ld + cc + 1];
+      if (ok1 && ((e.N & 1) == 0)) {
+        *reinterpret_cast<float2 *>(p) = make_float2(a0, a1);
+      } else {
+        p[0] = a0;
+        if (ok1) p[1] = a1;
+      }
+    }
+    return;
+  }
+  const int64_t col0 = ok0 ? e.map.col(n) : 0, col1 = ok1 ? e.map.col(n + 1) : 0;
+  const bool vec = ok1 && rows_even && col1 == col0 + 1 && (col0 & 1) == 0;
+  const float b0 = (e.bias && ok0 && n >= e.bias_n0) ? e.bias[n - e.bias_n0] : 0.f;
+  const float b1 = (e.bias && ok1 && n + 1 >= e.bias_n0) ? e.bias[n + 1 - e.bias_n0] : 0.f;
+  const bool s0 = e.act == ACT_SIGMOID && n >= e.act_n0, s1 = e.act == ACT_SIGMOID && n + 1 >= e.act_n0;
+  const bool relu = e.act == ACT_RELU;
+  const bool pair_ref = ok1 && (e.relu_ld & 1) == 0, pair_aux = ok1 && (e.aux_ld & 1) == 0,
+             pair_gate = ok1 && (e.gate_ld & 1) == 0;
+  const bf16 *refp = (const bf16 *)e.relu_ref + n;
+  bf16 *auxp = (bf16 *)e.aux + n;
+  const bf16 *gatep = (const bf16 *)e.gate + n;
+  bf16 *cb = (bf16 *)e.C;
+  const bf16 *rb = (const bf16 *)e.residual;
+  for (int rr = 0; rr < 32; ++rr) {
+    const int m = mrow0 + rr;
+    if (m >= g.M) break;
+    const int64_t rowoff = __shfl_sync(0xffffffffu, my_rowoff, rr);
+    if (!ok0) continue;
+    float v0 = mine[rr * ld + cc] * e.alpha + b0;
+    float v1 = mine[rr * ld + cc + 1] * e.alpha + b1;
+    if (e.row_scale) {
+      const float rs = e.row_scale[m];
+      v0 *= rs;
+      v1 *= rs;
+    }
+    if (e.relu_ref) {
+      const int64_t o = (int64_t)m * e.relu_ld;
+      float r0, r1 = 1.f;
+      if (pair_ref) {
+        const float2 rf = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(refp + o));
+        r0 = rf.x;
+        r1 = rf.y;
+      } else {
+        r0 = __bfloat162float(refp[o]);
+        if (ok1) r1 = __bfloat162float(refp[o + 1]);
+      }
+      if (!(r0 > 0.f)) v0 = 0.f;
+      if (!(r1 > 0.f)) v1 = 0.f;
+    }
+    if (relu) {
+      v0 = fmaxf(v0, 0.f);
+      v1 = fmaxf(v1, 0.f);
+    }
+    if (s0) v0 = __fdividef(1.f, 1.f + __expf(-v0));
+    if (s1) v1 = __fdividef(1.f, 1.f + __expf(-v1));
+    if (e.aux) {
+      const int64_t o = (int64_t)m * e.aux_ld;
+      if (pair_aux) {
+        *reinterpret_cast<__nv_bfloat162 *>(auxp + o) = __floats2bfloat162_rn(v0, v1);
+      } else {
+        auxp[o] = __float2bfloat16_rn(v0);
+        if (ok1) auxp[o + 1] = __float2bfloat16_rn(v1);
+      }
+    }
+    if (e.gate) {
+      const int64_t o = (int64_t)m * e.gate_ld;
+      if (pair_gate) {
+        const float2 gt = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(gatep + o));
+        v0 *= gt.x;
+        v1 *= gt.y;
+      } else {
+        v0 *= __bfloat162float(gatep[o]);
+        if (ok1) v1 *= __bfloat162float(gatep[o + 1]);
+      }
+    }
+    const int64_t o0 = rowoff + col0, o1 = rowoff + col1;
+    if (vec) {
+      if (rb) {
+        const float2 rv = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(rb + o0));
+        v0 += rv.x;
+        v1 += rv.y;
+      }
+      if (e.c_f32) {
+        float *cf = (float *)e.C;
+        if (e.accumulate) {
+          cf[o0] += v0;
+          cf[o1] += v1;
+        } else {
+          *reinterpret_cast<float2 *>(cf + o0) = make_float2(v0, v1);
+        }
+      } else {
+        *reinterpret_cast<__nv_bfloat162 *>(cb + o0) = __floats2bfloat162_rn(v0, v1);
+      }
+    } else {
+      if (rb) {
+        v0 += __bfloat162float(rb[o0]);
+        if (ok1) v1 += __bfloat162float(rb[o1]);
+      }
+      if (e.c_f32) {
+        float *cf = (float *)e.C;
+        if (e.accumulate) {
+          cf[o0] += v0;
+          if (ok1) cf[o1] += v1;
+        } else {
+          cf[o0] = v0;
+          if (ok1) cf[o1] = v1;
+        }
+      } else {
+        cb[o0] = __float2bfloat16_rn(v0);
+        if (ok1) cb[o1] = __float2bfloat16_rn(v1);
+      }
+    }
+  }
+}
+
+// Persistent warp-specialised GEMM: grid = min(#tiles, #SMs), tiles taken
+// round-robin (N fastest, so CTAs working at the same time share A tiles in L2).
+// warp 0 lane 0: TMA producer (runs ahead through the stage ring across tiles)
+// warp 1 lane 0: MMA issuer (accumulator buffer alternates per tile)
+// warps 2-9: epilogue (warp w drains TMEM lane quarter w % 4; warps w and w+4
+//            take alternate 64-column chunks)
 template <int BN, int STAGES, bool AMN, bool BMN>
-__global__ void __launch_bounds__(256, 2)
-    gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, GemmOp g) {
+__global__ void __launch_bounds__(320, 1)
+    gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                   const __grid_constant__ CUtensorMap tmC, GemmOp g, int tma_store) {
   using C = TcCfg<BN, STAGES, AMN, BMN>;
   extern __shared__ uint8_t dsmem[];
   __shared__ __align__(8) uint64_t full_bar[STAGES];
   __shared__ __align__(8) uint64_t empty_bar[STAGES];
+  __shared__ __align__(8) uint64_t accf_bar[2];
+  __shared__ __align__(8) uint64_t acce_bar[2];
   __shared__ __align__(8) uint64_t done_bar;
   __shared__ uint32_t tmem_slot;
   __shared__ volatile int s_abort;
 
   const uint32_t raw = smem_u32(dsmem);
   const uint32_t sbase = (raw + 1023u) & ~1023u;
-
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int n0 = blockIdx.x * BN, m0 = blockIdx.y * BM;
-  const int b = blockIdx.z / g.splits, split = blockIdx.z % g.splits;
-  const int kt_total = (g.K + BK - 1) / BK;
-  const int per = (kt_total + g.splits - 1) / g.splits;
-  const int kt0 = split * per;
-  const int nk = max(0, min(kt_total, kt0 + per) - kt0);
+  const int ntiles = ((g.N + BN - 1) / BN) * ((g.M + BM - 1) / BM) * g.batch * g.splits;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
       mbar_init(&full_bar[s], 1);
       mbar_init(&empty_bar[s], 1);
     }
+    for (int a = 0; a < 2; ++a) {
+      mbar_init(&accf_bar[a], 1);
+      mbar_init(&acce_bar[a], C::EPI_WARPS);
+    }
     mbar_init(&done_bar, 1);
     s_abort = 0;
     fence_mbar_init();
   }
   if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
-                     smem_u32(&tmem_slot)),
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
                  "r"((uint32_t)C::TMEM_COLS)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
@@ -191,150 +387,290 @@ __global__ void __launch_bounds__(256, 2)
   tc_fence_after();
   const uint32_t tmem = tmem_slot;
 
-  if (nk > 0 && warp == 0 && lane == 0) {
+  if (warp == 0 && lane == 0) {
     // ---------------- TMA producer
-    int issued = 0;
-    for (int i = 0; i < nk; ++i) {
-      const int s = i % STAGES;
-      const uint32_t j = (uint32_t)(i / STAGES);
-      if (i >= STAGES && !mbar_wait(&empty_bar[s], (j - 1) & 1u, &s_abort)) break;
-      const uint32_t sa = sbase + s * C::STAGE_BYTES;
-      const uint32_t sb = sa + C::A_BYTES;
-      const int kc = (kt0 + i) * BK;
-      mbar_arrive_expect_tx(&full_bar[s], C::STAGE_BYTES);
-      if (AMN) {
-        tma_load_3d(sa, &tmA, m0, kc, b, &full_bar[s]);
-        tma_load_3d(sa + 8192, &tmA, m0 + 64, kc, b, &full_bar[s]);
-      } else {
-        tma_load_3d(sa, &tmA, kc, m0, b, &full_bar[s]);
-      }
-      if (BMN) {
+    uint32_t it = 0;
+    bool stop = false;
+    for (int t = blockIdx.x; t < ntiles && !stop; t += gridDim.x) {
+      const TileCoord tc = decode_tile(g, t, BN);
+      for (int i = 0; i < tc.nk; ++i, ++it) {
+        const int s = (int)(it % STAGES);
+        const uint32_t j = it / STAGES;
+        if (it >= (uint32_t)STAGES && !mbar_wait(&empty_bar[s], (j - 1) & 1u, &s_abort)) {
+          stop = true;
+          break;
+        }
+        const uint32_t sa = sbase + s * C::STAGE_BYTES;
+        const uint32_t sb = sa + C::A_BYTES;
+        const int kc = (tc.kt0 + i) * BK;
+        mbar_arrive_expect_tx(&full_bar[s], C::STAGE_BYTES);
+        if (AMN) {
+          tma_load_3d(sa, &tmA, tc.m0, kc, tc.b, &full_bar[s]);
+          tma_load_3d(sa + 8192, &tmA, tc.m0 + 64, kc, tc.b, &full_bar[s]);
+        } else {
+          tma_load_3d(sa, &tmA, kc, tc.m0, tc.b, &full_bar[s]);
+        }
+        if (BMN) {
 #pragma unroll
-        for (int c = 0; c < BN / 64; ++c) tma_load_3d(sb + c * 8192, &tmB, n0 + c * 64, kc, b, &full_bar[s]);
-      } else {
-        tma_load_3d(sb, &tmB, kc, n0, b, &full_bar[s]);
+          for (int cpart = 0; cpart < BN / 64; ++cpart)
+            tma_load_3d(sb + cpart * 8192, &tmB, tc.n0 + cpart * 64, kc, tc.b, &full_bar[s]);
+        } else {
+          tma_load_3d(sb, &tmB, kc, tc.n0, tc.b, &full_bar[s]);
+        }
       }
-      ++issued;
     }
     if (s_abort) {
-      // drain: wait (bounded) for every load still in flight before leaving
-      for (int i = max(0, issued - STAGES); i < issued; ++i) {
+      // drain: wait (bounded) for every load that may still be in flight
+      const uint32_t first = it > (uint32_t)STAGES ? it - STAGES : 0u;
+      for (uint32_t i = first; i < it; ++i) {
         const uint64_t t0 = globaltimer_ns();
-        while (!mbar_try_wait(&full_bar[i % STAGES], (uint32_t)(i / STAGES) & 1u) &&
-               globaltimer_ns() - t0 < WAIT_LIMIT_NS) {
+        while (!mbar_try_wait(&full_bar[i % STAGES], (i / STAGES) & 1u) && globaltimer_ns() - t0 < WAIT_LIMIT_NS) {
         }
       }
     }
-  } else if (nk > 0 && warp == 1 && lane == 0) {
+  } else if (warp == 1 && lane == 0) {
     // ---------------- MMA issuer
-    for (int i = 0; i < nk; ++i) {
-      const int s = i % STAGES;
-      const uint32_t j = (uint32_t)(i / STAGES);
-      if (!mbar_wait(&full_bar[s], j & 1u, &s_abort)) break;
+    uint32_t it = 0, ai = 0;
+    bool stop = false;
+    for (int t = blockIdx.x; t < ntiles && !stop; t += gridDim.x) {
+      const TileCoord tc = decode_tile(g, t, BN);
+      if (tc.nk == 0) continue;
+      const uint32_t ab = ai & 1u, u = ai >> 1;
+      if (ai >= 2 && !mbar_wait(&acce_bar[ab], (u - 1) & 1u, &s_abort)) break;
       tc_fence_after();
-      const uint32_t sa = sbase + s * C::STAGE_BYTES;
-      const uint32_t sb = sa + C::A_BYTES;
+      const uint32_t dacc = tmem + ab * BN;
+      for (int i = 0; i < tc.nk; ++i, ++it) {
+        const int s = (int)(it % STAGES);
+        const uint32_t j = it / STAGES;
+        if (!mbar_wait(&full_bar[s], j & 1u, &s_abort)) {
+          stop = true;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t sa = sbase + s * C::STAGE_BYTES;
+        const uint32_t sb = sa + C::A_BYTES;
 #pragma unroll
-      for (int kk = 0; kk < BK / 16; ++kk) {
-        const uint64_t ad = smem_desc(sa + kk * C::A_KSTEP, C::A_LBO, 1024);
-        const uint64_t bd = smem_desc(sb + kk * C::B_KSTEP, C::B_LBO, 1024);
-        tc_mma(tmem, ad, bd, C::IDESC, (i > 0 || kk > 0) ? 1u : 0u);
+        for (int kk = 0; kk < BK / 16; ++kk) {
+          const uint64_t ad = smem_desc(sa + kk * C::A_KSTEP, C::A_LBO, 1024);
+          const uint64_t bd = smem_desc(sb + kk * C::B_KSTEP, C::B_LBO, 1024);
+          tc_mma(dacc, ad, bd, C::IDESC, (i > 0 || kk > 0) ? 1u : 0u);
+        }
+        tc_commit(&empty_bar[s]);
       }
-      tc_commit(&empty_bar[s]);
+      if (stop) break;
+      tc_commit(&accf_bar[ab]);
+      ++ai;
     }
     tc_commit(&done_bar);
-  }
-  __syncwarp();
-
-  // ---------------- epilogue: TMEM -> shared (64-column chunks, in the idle
-  // stage buffers) -> stores with lanes along columns, so every output map
-  // used by the block is written in contiguous runs.  Warps w and w+4 share
-  // TMEM lane quarter w and split the tile's columns.
-  bool have = nk > 0;
-  if (have) have = mbar_wait(&done_bar, 0, &s_abort);
-  have = __all_sync(0xffffffffu, have);
-  tc_fence_after();
-  const int quarter = warp & 3, half = warp >> 2;
-  constexpr int CH = BN < 64 ? BN : 64;
-  constexpr int LDS = CH + 1;
-  constexpr int NCH = BN / CH;
-  constexpr int CH_PER_HALF = NCH > 1 ? NCH / 2 : 1;
-  if (have || (nk == 0 && !s_abort)) {
-    float *mine = reinterpret_cast<float *>(dsmem + (sbase - raw)) + warp * 32 * LDS;
+  } else if (warp >= 2) {
+    // ---------------- epilogue warps
+    const int quarter = warp & 3, half = (warp - 2) >> 2;
+    const uint32_t region = sbase + STAGES * C::STAGE_BYTES + (warp - 2) * C::EPI_WARP_BYTES;
+    float *mine = reinterpret_cast<float *>(dsmem + (region - raw));
+    uint32_t ai = 0, nstore = 0;
     const Epi &e = g.e;
-    const bool fast = !e.partial && !e.c_f32 && !e.relu_ref && !e.aux && !e.gate && e.map.mdiv >= (1ll << 31) &&
-                      e.map.ndiv >= (1ll << 31) && e.map.s_n0 == 1 && (e.map.s_m0 & 1) == 0 &&
-                      (e.c_bstride & 1) == 0;
-    for (int ci = 0; ci < CH_PER_HALF; ++ci) {
-      const int cidx = NCH > 1 ? half * CH_PER_HALF + ci : ci;
-      if (NCH == 1 && half == 1) break;  // a single chunk is drained by warps 0-3
-      const int c0 = cidx * CH;
-      if (n0 + c0 >= g.N) break;
-      if (have) {
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+      const TileCoord tc = decode_tile(g, t, BN);
+      const uint32_t ab = ai & 1u, u = ai >> 1;
+      bool have = false;
+      if (tc.nk > 0) {
+        have = mbar_wait(&accf_bar[ab], u & 1u, &s_abort);
+        have = __all_sync(0xffffffffu, have);
+        if (!have) break;
+        tc_fence_after();
+      }
+      const int mrow0 = tc.m0 + quarter * 32;
+      if (tma_store) {
+        // thread = row: TMEM -> registers -> epilogue -> bf16 -> swizzled shared -> TMA store
+        const int m = mrow0 + lane;
+        const bool mok = m < g.M;
+        const int64_t cbase = (int64_t)tc.b * e.c_bstride + (int64_t)m * e.map.s_m0;
+        const float rs = (e.row_scale && mok) ? e.row_scale[m] : 1.f;
+        for (int c0 = half * 64; c0 < BN; c0 += 128) {
+          const int nb = tc.n0 + c0;
+          if (nb >= g.N) break;
+          float v[64];
+          if (have) {
 #pragma unroll
-        for (int q = 0; q < CH; q += 16) {
-          uint32_t r[16];
-          tmem_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(c0 + q), r);
+            for (int q = 0; q < 64; q += 16) {
+              uint32_t r[16];
+              tmem_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + ab * BN + (uint32_t)(c0 + q), r);
 #pragma unroll
-          for (int j = 0; j < 16; ++j) mine[lane * LDS + q + j] = __uint_as_float(r[j]);
+              for (int jj = 0; jj < 16; ++jj) v[q + jj] = __uint_as_float(r[jj]);
+            }
+          } else {
+#pragma unroll
+            for (int jj = 0; jj < 64; ++jj) v[jj] = 0.f;
+          }
+#pragma unroll
+          for (int g8 = 0; g8 < 8; ++g8) {
+            const int n = nb + g8 * 8;
+            const bool full8 = n + 7 < g.N;
+            float bb[8];
+#pragma unroll
+            for (int jj = 0; jj < 8; ++jj) bb[jj] = 0.f;
+            if (e.bias) {
+              const int bi = n - e.bias_n0;
+              if (full8 && bi >= 0 && (bi & 3) == 0) {
+                const float4 x0 = *reinterpret_cast<const float4 *>(e.bias + bi);
+                const float4 x1 = *reinterpret_cast<const float4 *>(e.bias + bi + 4);
+                bb[0] = x0.x, bb[1] = x0.y, bb[2] = x0.z, bb[3] = x0.w;
+                bb[4] = x1.x, bb[5] = x1.y, bb[6] = x1.z, bb[7] = x1.w;
+              } else {
+#pragma unroll
+                for (int jj = 0; jj < 8; ++jj)
+                  if (n + jj < g.N && n + jj >= e.bias_n0) bb[jj] = e.bias[n + jj - e.bias_n0];
+              }
+            }
+#pragma unroll
+            for (int jj = 0; jj < 8; ++jj) v[g8 * 8 + jj] = (v[g8 * 8 + jj] * e.alpha + bb[jj]) * rs;
+          }
+          if (e.relu_ref && mok) {
+            const bf16 *p = (const bf16 *)e.relu_ref + (int64_t)m * e.relu_ld + nb;
+#pragma unroll
+            for (int g8 = 0; g8 < 8; ++g8) {
+              if (nb + g8 * 8 + 7 < g.N) {
+                const uint4 w = *reinterpret_cast<const uint4 *>(p + g8 * 8);
+                const bf16 *h = reinterpret_cast<const bf16 *>(&w);
+#pragma unroll
+                for (int jj = 0; jj < 8; ++jj)
+                  if (!(__bfloat162float(h[jj]) > 0.f)) v[g8 * 8 + jj] = 0.f;
+              } else {
+                for (int jj = 0; jj < 8; ++jj)
+                  if (nb + g8 * 8 + jj < g.N && !(__bfloat162float(p[g8 * 8 + jj]) > 0.f)) v[g8 * 8 + jj] = 0.f;
+              }
+            }
+          }
+          if (e.act == ACT_RELU) {
+#pragma unroll
+            for (int jj = 0; jj < 64; ++jj) v[jj] = fmaxf(v[jj], 0.f);
+          } else if (e.act == ACT_SIGMOID) {
+#pragma unroll
+            for (int jj = 0; jj < 64; ++jj)
+              if (nb + jj >= e.act_n0) v[jj] = __fdividef(1.f, 1.f + __expf(-v[jj]));
+          }
+          if (e.aux && mok) {
+            bf16 *p = (bf16 *)e.aux + (int64_t)m * e.aux_ld + nb;
+#pragma unroll
+            for (int g8 = 0; g8 < 8; ++g8) {
+              if (nb + g8 * 8 + 7 < g.N) {
+                uint4 w;
+                uint32_t *wp = reinterpret_cast<uint32_t *>(&w);
+#pragma unroll
+                for (int jj = 0; jj < 4; ++jj) {
+                  __nv_bfloat162 h2 = __floats2bfloat162_rn(v[g8 * 8 + 2 * jj], v[g8 * 8 + 2 * jj + 1]);
+                  wp[jj] = *reinterpret_cast<uint32_t *>(&h2);
+                }
+                *reinterpret_cast<uint4 *>(p + g8 * 8) = w;
+              } else {
+                for (int jj = 0; jj < 8; ++jj)
+                  if (nb + g8 * 8 + jj < g.N) p[g8 * 8 + jj] = __float2bfloat16_rn(v[g8 * 8 + jj]);
+              }
+            }
+          }
+          if (e.gate && mok) {
+            const bf16 *p = (const bf16 *)e.gate + (int64_t)m * e.gate_ld + nb;
+#pragma unroll
+            for (int g8 = 0; g8 < 8; ++g8) {
+              if (nb + g8 * 8 + 7 < g.N) {
+                const uint4 w = *reinterpret_cast<const uint4 *>(p + g8 * 8);
+                const bf16 *h = reinterpret_cast<const bf16 *>(&w);
+#pragma unroll
+                for (int jj = 0; jj < 8; ++jj) v[g8 * 8 + jj] *= __bfloat162float(h[jj]);
+              } else {
+                for (int jj = 0; jj < 8; ++jj)
+                  if (nb + g8 * 8 + jj < g.N) v[g8 * 8 + jj] *= __bfloat162float(p[g8 * 8 + jj]);
+              }
+            }
+          }
+          if (e.residual && mok) {
+            const bf16 *p = (const bf16 *)e.residual + cbase + nb;
+#pragma unroll
+            for (int g8 = 0; g8 < 8; ++g8) {
+              if (nb + g8 * 8 + 7 < g.N) {
+                const uint4 w = *reinterpret_cast<const uint4 *>(p + g8 * 8);
+                const bf16 *h = reinterpret_cast<const bf16 *>(&w);
+#pragma unroll
+                for (int jj = 0; jj < 8; ++jj) v[g8 * 8 + jj] += __bfloat162float(h[jj]);
+              } else {
+                for (int jj = 0; jj < 8; ++jj)
+                  if (nb + g8 * 8 + jj < g.N) v[g8 * 8 + jj] += __bfloat162float(p[g8 * 8 + jj]);
+              }
+            }
+          }
+          // stage bf16 into the 128-byte-swizzled buffer (row = lane, 16-byte chunk j at j ^ (lane & 7))
+          const uint32_t buf = region + (nstore & 1u) * 4096u;
+          if (lane == 0) bulk_wait_read<1>();
+          __syncwarp();
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            uint32_t w[4];
+#pragma unroll
+            for (int jj = 0; jj < 4; ++jj) {
+              __nv_bfloat162 h2 = __floats2bfloat162_rn(v[j * 8 + 2 * jj], v[j * 8 + 2 * jj + 1]);
+              w[jj] = *reinterpret_cast<uint32_t *>(&h2);
+            }
+            // kind 1: [row][64] with the 128-byte swizzle; kind 2: [n/32][row][32];
+            // kind 3: [row][64] unswizzled (the element order of the 4-D box)
+            uint32_t dst;
+            if (tma_store == 1) dst = buf + lane * 128u + (uint32_t)(((j ^ (lane & 7)) & 7) * 16);
+            else if (tma_store == 2) dst = buf + (uint32_t)(j >> 2) * 2048u + lane * 64u + (uint32_t)(j & 3) * 16u;
+            else dst = buf + lane * 128u + (uint32_t)j * 16u;
+            asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(dst), "r"(w[0]), "r"(w[1]), "r"(w[2]),
+                         "r"(w[3])
+                         : "memory");
+          }
+          fence_proxy_async();
+          __syncwarp();
+          if (lane == 0 && mrow0 < g.M) {  // rows and columns past the tensor are clipped by TMA
+            if (tma_store == 1) {
+              tma_store_3d(&tmC, buf, nb, mrow0, tc.b);
+            } else {
+              // 4-D view of a two-level output map (see the host side for the order)
+              const int md = e.map.mdiv >= (1ll << 31) ? g.M : (int)e.map.mdiv;
+              if (tma_store == 2) tma_store_4d(&tmC, buf, 0, mrow0 % md, nb >> 5, mrow0 / md);
+              else tma_store_4d(&tmC, buf, 0, nb >> 5, mrow0 % md, mrow0 / md);
+            }
+            bulk_commit();
+          }
+          ++nstore;
         }
       } else {
-        for (int j = 0; j < CH; ++j) mine[lane * LDS + j] = 0.f;
-      }
-      __syncwarp();
-      const int cc = 2 * lane;
-      const int n = n0 + c0 + cc;
-      if (fast && cc < CH) {
-        // row-major output: bias / activation decisions per lane, one bf16x2 per row
-        const bool ok0 = n < g.N, ok1 = n + 1 < g.N;
-        const float b0 = (e.bias && ok0 && n >= e.bias_n0) ? e.bias[n - e.bias_n0] : 0.f;
-        const float b1 = (e.bias && ok1 && n + 1 >= e.bias_n0) ? e.bias[n + 1 - e.bias_n0] : 0.f;
-        const bool s0 = e.act == ACT_SIGMOID && n >= e.act_n0, s1 = e.act == ACT_SIGMOID && n + 1 >= e.act_n0;
-        const bool relu = e.act == ACT_RELU;
-        bf16 *cb = (bf16 *)e.C + (int64_t)b * e.c_bstride + n;
-        const bf16 *rb = e.residual ? (const bf16 *)e.residual + (int64_t)b * e.c_bstride + n : nullptr;
-        for (int rr = 0; rr < 32; ++rr) {
-          const int m = m0 + quarter * 32 + rr;
-          if (m >= g.M || !ok0) break;
-          float v0 = mine[rr * LDS + cc] * e.alpha + b0;
-          float v1 = mine[rr * LDS + cc + 1] * e.alpha + b1;
-          if (e.row_scale) {
-            const float rs = e.row_scale[m];
-            v0 *= rs;
-            v1 *= rs;
-          }
-          if (relu) {
-            v0 = fmaxf(v0, 0.f);
-            v1 = fmaxf(v1, 0.f);
-          }
-          if (s0) v0 = 1.f / (1.f + __expf(-v0));
-          if (s1) v1 = 1.f / (1.f + __expf(-v1));
-          const int64_t ro = (int64_t)m * e.map.s_m0;
-          if (ok1) {
-            if (rb) {
-              const __nv_bfloat162 r2 = *reinterpret_cast<const __nv_bfloat162 *>(rb + ro);
-              v0 += __low2float(r2);
-              v1 += __high2float(r2);
+        const int64_t my_rowoff = (int64_t)tc.b * e.c_bstride + e.map.row(min(mrow0 + lane, g.M - 1));
+        const bool rows_even = (e.c_bstride & 1) == 0 && (e.map.s_m0 & 1) == 0 &&
+                               (e.map.mdiv >= (1ll << 31) || (e.map.s_m1 & 1) == 0);
+        for (int c0 = half * C::CH; c0 < BN; c0 += 2 * C::CH) {
+          if (tc.n0 + c0 >= g.N) break;
+          if (have) {
+#pragma unroll
+            for (int q = 0; q < C::CH; q += 16) {
+              uint32_t r[16];
+              tmem_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + ab * BN + (uint32_t)(c0 + q), r);
+#pragma unroll
+              for (int jj = 0; jj < 16; ++jj) mine[lane * C::LDS + q + jj] = __uint_as_float(r[jj]);
             }
-            *reinterpret_cast<__nv_bfloat162 *>(cb + ro) = __floats2bfloat162_rn(v0, v1);
           } else {
-            if (rb) v0 += __bfloat162float(rb[ro]);
-            cb[ro] = __float2bfloat16_rn(v0);
+            for (int jj = 0; jj < C::CH; ++jj) mine[lane * C::LDS + jj] = 0.f;
           }
-        }
-      } else if (cc < CH) {
-        for (int rr = 0; rr < 32; ++rr) {
-          const int m = m0 + quarter * 32 + rr;
-          if (m >= g.M) break;
-          const int64_t rowoff = (int64_t)b * e.c_bstride + e.map.row(m);
-          if (n < g.N) epi_pair<bf16>(e, b, split, m, n, rowoff, mine[rr * LDS + cc], mine[rr * LDS + cc + 1]);
+          __syncwarp();
+          epi_chunk(g, mine, lane, mrow0, tc.n0 + c0, C::CH, tc.b, tc.split, my_rowoff, rows_even);
+          __syncwarp();
         }
       }
-      __syncwarp();
+      if (tc.nk > 0) {
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&acce_bar[ab]);
+        ++ai;
+      }
+      if (s_abort) break;
     }
+    if (lane == 0) bulk_wait_all();
+    __syncwarp();
   }
-  if (s_abort && nk > 0 && threadIdx.x == 0) {
-    // MMAs may still be in flight: wait (bounded) for their commit before freeing TMEM
+  __syncwarp();
+  // every MMA issued has completed before TMEM is released
+  if (threadIdx.x == 0) {
     const uint64_t t0 = globaltimer_ns();
     while (!mbar_try_wait(&done_bar, 0) && globaltimer_ns() - t0 < WAIT_LIMIT_NS) {
     }
@@ -342,9 +678,23 @@ __global__ void __launch_bounds__(256, 2)
   tc_fence_before();
   __syncthreads();
   if (warp == 0) {
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
-                 "r"((uint32_t)C::TMEM_COLS)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)C::TMEM_COLS)
                  : "memory");
+  }
+}
+
+__global__ void debug_wait_kernel(int64_t limit_ns) {
+  // One mbarrier that nothing ever arrives on: the bounded wait runs out,
+  // records the timeout in the device error word and the kernel returns.
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x != 0) return;
+  mbar_init(&bar, 1);
+  const uint64_t t0 = globaltimer_ns();
+  while (!mbar_try_wait(&bar, 0)) {
+    if ((int64_t)(globaltimer_ns() - t0) > limit_ns) {
+      atomicExch(&g_evo_error, -6);
+      return;
+    }
   }
 }
 
@@ -383,6 +733,33 @@ bool make_tmap(CUtensorMap *tm, const void *base, uint64_t inner, uint64_t outer
   return r == CUDA_SUCCESS;
 }
 
+int sm_count() {
+  static int n = 0;
+  if (n == 0) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+      n = 148;
+  }
+  return n;
+}
+
+// 4-D bf16 tensor {d0, d1, d2, d3} with element strides s1, s2, s3 (any order).
+bool make_tmap4(CUtensorMap *tm, const void *base, uint64_t d0, uint64_t d1, uint64_t d2, uint64_t d3, uint64_t s1,
+                uint64_t s2, uint64_t s3, uint32_t b0, uint32_t b1, uint32_t b2, uint32_t b3, bool swizzle) {
+  // strides must be non-decreasing and each must span the previous dimension
+  if (s1 < d0 || s2 < s1 * d1 || s3 < s2 * d2) return false;
+  EncodeTiledFn enc = get_encode();
+  if (!enc) return false;
+  cuuint64_t dims[4] = {d0, d1, d2, d3};
+  cuuint64_t strides[3] = {s1 * 2, s2 * 2, s3 * 2};
+  cuuint32_t box[4] = {b0, b1, b2, b3};
+  cuuint32_t estr[4] = {1, 1, 1, 1};
+  CUresult r = enc(tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void *>(base), dims, strides, box, estr,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, swizzle ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_NONE,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
 template <int BN, int STAGES, bool AMN, bool BMN>
 cudaError_t launch_tc(const GemmOp &g, cudaStream_t s) {
   using C = TcCfg<BN, STAGES, AMN, BMN>;
@@ -392,6 +769,40 @@ cudaError_t launch_tc(const GemmOp &g, cudaStream_t s) {
   ok = ok && (BMN ? make_tmap(&tb, g.B, g.N, g.K, g.batch, g.ldb, g.b_bs, 64, 64)
                   : make_tmap(&tb, g.B, g.K, g.N, g.batch, g.ldb, g.b_bs, 64, BN));
   if (!ok) return cudaErrorInvalidValue;
+  // TMA-store epilogue.  Kind 1: plain row-major bf16 output (3-D map over
+  // n, m, batch).  Kind 2: a two-level map with 32-wide column groups,
+  // offset = (n / 32) s_n1 + n % 32 + (m / mdiv) s_m1 + (m % mdiv) s_m0, stored
+  // through a 4-D map whose box is one warp's 32 x 64 sub-tile.  Every operand
+  // the epilogue reads needs 16-byte aligned row vectors.
+  const Epi &e = g.e;
+  auto a16 = [](const void *p) { return ((uintptr_t)p & 15u) == 0; };
+  const bool operands_ok = !e.partial && !e.c_f32 && !e.accumulate && a16(e.C) && (!e.residual || a16(e.residual)) &&
+                           (!e.relu_ref || (a16(e.relu_ref) && e.relu_ld % 8 == 0)) &&
+                           (!e.aux || (a16(e.aux) && e.aux_ld % 8 == 0)) &&
+                           (!e.gate || (a16(e.gate) && e.gate_ld % 8 == 0)) &&
+                           (!e.bias || (a16(e.bias) && e.bias_n0 % 4 == 0));
+  const bool plain = e.map.mdiv >= (1ll << 31) && e.map.ndiv >= (1ll << 31) && e.map.s_n0 == 1;
+  int tstore = 0;
+  CUtensorMap tc;
+  std::memset(&tc, 0, sizeof(tc));
+  if (operands_ok && plain && e.map.s_m0 % 8 == 0 && (g.batch == 1 || e.c_bstride % 8 == 0)) {
+    if (make_tmap(&tc, e.C, g.N, g.M, g.batch, e.map.s_m0, g.batch > 1 ? e.c_bstride : 0, 64, 32)) tstore = 1;
+  } else if (operands_ok && !plain && g.batch == 1 && !e.residual && e.map.ndiv == 32 && e.map.s_n0 == 1 &&
+             g.N % 32 == 0 && e.map.s_n1 % 8 == 0 && e.map.s_m0 % 8 == 0 &&
+             (e.map.mdiv >= (1ll << 31) || (e.map.mdiv % 32 == 0 && g.M % e.map.mdiv == 0 && e.map.s_m1 % 8 == 0))) {
+    // TMA wants each dimension's stride to cover the previous dimensions, so the
+    // four index parts are ordered by stride: d (1) first, then the smaller of
+    // m % md and n / 32, then the other, then m / md.
+    const uint64_t md = e.map.mdiv >= (1ll << 31) ? (uint64_t)g.M : (uint64_t)e.map.mdiv;
+    const uint64_t s_nhi = (uint64_t)e.map.s_n1, s_mlo = (uint64_t)e.map.s_m0;
+    const uint64_t s_mhi = e.map.mdiv >= (1ll << 31) ? s_mlo * md : (uint64_t)e.map.s_m1;
+    const uint64_t nhi = (uint64_t)g.N / 32, mhi = (uint64_t)g.M / md;
+    if (s_mlo >= 32 && s_mlo <= s_nhi && s_nhi >= s_mlo * md && s_mhi >= s_nhi * nhi) {
+      if (make_tmap4(&tc, e.C, 32, md, nhi, mhi, s_mlo, s_nhi, s_mhi, 32, 32, 2, 1, false)) tstore = 2;
+    } else if (s_nhi >= 32 && s_nhi <= s_mlo && s_mlo >= s_nhi * nhi && s_mhi >= s_mlo * md) {
+      if (make_tmap4(&tc, e.C, 32, nhi, md, mhi, s_nhi, s_mlo, s_mhi, 32, 2, 32, 1, false)) tstore = 3;
+    }
+  }
   static bool attr_set = false;
   if (!attr_set) {
     cudaError_t e = cudaFuncSetAttribute(gemm_tc_kernel<BN, STAGES, AMN, BMN>,
@@ -399,11 +810,13 @@ cudaError_t launch_tc(const GemmOp &g, cudaStream_t s) {
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
-  dim3 grid((g.N + BN - 1) / BN, (g.M + BM - 1) / BM, g.batch * g.splits);
+  const long long tiles =
+      (long long)((g.N + BN - 1) / BN) * ((g.M + BM - 1) / BM) * (long long)g.batch * g.splits;
+  const int grid = (int)std::min<long long>(tiles, sm_count());
   const double cbytes = g.e.partial ? 4.0 * g.splits : (g.e.c_f32 ? 4.0 : 2.0);
   Prof p("gemm_tc", s, 2.0 * g.M * g.N * (double)g.K * g.batch,
          g.batch * (2.0 * ((double)g.M * g.K + (double)g.N * g.K) + cbytes * g.M * g.N));
-  gemm_tc_kernel<BN, STAGES, AMN, BMN><<<grid, 256, C::SMEM, s>>>(ta, tb, g);
+  gemm_tc_kernel<BN, STAGES, AMN, BMN><<<grid, 320, C::SMEM, s>>>(ta, tb, tc, g, tstore);
   return cudaGetLastError();
 }
 
@@ -413,23 +826,6 @@ cudaError_t dispatch_major(const GemmOp &g, cudaStream_t s) {
     return g.b_mn ? launch_tc<BN, STAGES, true, true>(g, s) : launch_tc<BN, STAGES, true, false>(g, s);
   }
   return g.b_mn ? launch_tc<BN, STAGES, false, true>(g, s) : launch_tc<BN, STAGES, false, false>(g, s);
-}
-
-__global__ void debug_wait_kernel(int64_t limit_ns) {
-  // One mbarrier that nothing ever arrives on: the bounded wait runs out,
-  // records the timeout in the device error word and the kernel returns.
-  __shared__ __align__(8) uint64_t bar;
-  __shared__ volatile int abort_flag;
-  if (threadIdx.x != 0) return;
-  mbar_init(&bar, 1);
-  abort_flag = 0;
-  const uint64_t t0 = globaltimer_ns();
-  while (!mbar_try_wait(&bar, 0)) {
-    if ((int64_t)(globaltimer_ns() - t0) > limit_ns) {
-      atomicExch(&g_evo_error, -6);
-      return;
-    }
-  }
 }
 
 }  // namespace
@@ -459,10 +855,11 @@ bool gemm_tc_supported(const GemmOp &g) {
 
 cudaError_t gemm_tc_bf16(const GemmOp &g, cudaStream_t s) {
   if (!gemm_tc_supported(g)) return cudaErrorInvalidValue;
-  // stage counts keep two CTAs resident per SM (shared memory and 512 TMEM columns)
-  if (g.N > 128 && g.N % 256 == 0) return dispatch_major<256, 2>(g, s);
-  if (g.N > 64) return dispatch_major<128, 3>(g, s);
-  return dispatch_major<64, 4>(g, s);
+  // one persistent CTA per SM; the stage ring fills the shared memory the
+  // epilogue staging leaves free
+  if (g.N > 128 && g.N % 256 == 0) return dispatch_major<256, 3>(g, s);
+  if (g.N > 64) return dispatch_major<128, 4>(g, s);
+  return dispatch_major<64, 6>(g, s);
 }
 
 }  // namespace evo

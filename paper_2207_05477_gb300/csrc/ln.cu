@@ -102,6 +102,138 @@ __global__ void __launch_bounds__(256) ln_bwd_rows(const T *dy, const T *x, cons
   }
 }
 
+
+template <typename T> struct Pair;
+template <> struct Pair<bf16> {
+  static __device__ __forceinline__ float2 ld(const bf16 *p) {
+    return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(p));
+  }
+  static __device__ __forceinline__ void st(bf16 *p, float a, float b) {
+    *reinterpret_cast<__nv_bfloat162 *>(p) = __floats2bfloat162_rn(a, b);
+  }
+};
+template <> struct Pair<float> {
+  static __device__ __forceinline__ float2 ld(const float *p) { return *reinterpret_cast<const float2 *>(p); }
+  static __device__ __forceinline__ void st(float *p, float a, float b) {
+    *reinterpret_cast<float2 *>(p) = make_float2(a, b);
+  }
+};
+
+// LayerNorm backward with the row in registers: lane l holds channels
+// 64j + 2l, 64j + 2l + 1 (j < P), so every load is a coalesced pair.
+template <typename T, int P>
+__global__ void __launch_bounds__(256) ln_bwd_rows_vec(const T *dy, const T *x, const float *gamma, float *dacc,
+                                                       T *dcopy, T *dx_out, float *part, int64_t M,
+                                                       int64_t rows_per_blk) {
+  constexpr int C = 64 * P;
+  __shared__ float red[8][2 * C];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  float g0[P], g1[P], ag[P], ag1[P], ab[P], ab1[P];
+#pragma unroll
+  for (int j = 0; j < P; ++j) {
+    const int c = 64 * j + 2 * lane;
+    g0[j] = gamma[c];
+    g1[j] = gamma[c + 1];
+    ag[j] = ag1[j] = ab[j] = ab1[j] = 0.f;
+  }
+  const int64_t r0 = (int64_t)blockIdx.x * rows_per_blk;
+  const int64_t r1 = min(M, r0 + rows_per_blk);
+  for (int64_t row = r0 + warp; row < r1; row += 8) {
+    float2 xv[P], gv[P];
+    float s = 0.f;
+#pragma unroll
+    for (int j = 0; j < P; ++j) {
+      const int c = 64 * j + 2 * lane;
+      xv[j] = Pair<T>::ld(x + row * C + c);
+      gv[j] = Pair<T>::ld(dy + row * C + c);
+      s += xv[j].x + xv[j].y;
+    }
+    const float mu = warp_sum(s) * (1.f / C);
+    float q = 0.f;
+#pragma unroll
+    for (int j = 0; j < P; ++j) {
+      const float d0 = xv[j].x - mu, d1 = xv[j].y - mu;
+      q += d0 * d0 + d1 * d1;
+    }
+    const float rstd = rsqrtf(warp_sum(q) * (1.f / C) + LN_EPS);
+    float a1 = 0.f, a2 = 0.f;
+#pragma unroll
+    for (int j = 0; j < P; ++j) {
+      const float h0 = (xv[j].x - mu) * rstd, h1 = (xv[j].y - mu) * rstd;
+      xv[j].x = h0;
+      xv[j].y = h1;
+      const float d0 = gv[j].x * g0[j], d1 = gv[j].y * g1[j];
+      a1 += d0 + d1;
+      a2 += d0 * h0 + d1 * h1;
+      ag[j] += gv[j].x * h0;
+      ag1[j] += gv[j].y * h1;
+      ab[j] += gv[j].x;
+      ab1[j] += gv[j].y;
+    }
+    a1 = warp_sum(a1) * (1.f / C);
+    a2 = warp_sum(a2) * (1.f / C);
+#pragma unroll
+    for (int j = 0; j < P; ++j) {
+      const int c = 64 * j + 2 * lane;
+      const float dx0 = rstd * (gv[j].x * g0[j] - a1 - xv[j].x * a2);
+      const float dx1 = rstd * (gv[j].y * g1[j] - a1 - xv[j].y * a2);
+      if (dacc) {
+        float2 *pa = reinterpret_cast<float2 *>(dacc + row * C + c);
+        float2 nv = *pa;
+        nv.x += dx0;
+        nv.y += dx1;
+        *pa = nv;
+        if (dcopy) Pair<T>::st(dcopy + row * C + c, nv.x, nv.y);
+      } else {
+        Pair<T>::st(dx_out + row * C + c, dx0, dx1);
+      }
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < P; ++j) {
+    const int c = 64 * j + 2 * lane;
+    red[warp][c] = ag[j];
+    red[warp][c + 1] = ag1[j];
+    red[warp][C + c] = ab[j];
+    red[warp][C + c + 1] = ab1[j];
+  }
+  __syncthreads();
+  for (int cc = threadIdx.x; cc < 2 * C; cc += blockDim.x) {
+    float t = 0.f;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) t += red[w][cc];
+    part[(int64_t)blockIdx.x * 2 * C + cc] = t;
+  }
+}
+
+
+template <typename T, int P>
+__global__ void __launch_bounds__(256) ln_fwd_rows_vec(const T *x, const float *gamma, const float *beta, T *y,
+                                                       int64_t M) {
+  constexpr int C = 64 * P;
+  const int lane = threadIdx.x & 31;
+  const int64_t row = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+  if (row >= M) return;
+  float2 v[P];
+  float s = 0.f;
+#pragma unroll
+  for (int j = 0; j < P; ++j) {
+    v[j] = Pair<T>::ld(x + row * C + 64 * j + 2 * lane);
+    s += v[j].x + v[j].y;
+  }
+  const float mu = warp_sum(s) * (1.f / C);
+  float q = 0.f;
+#pragma unroll
+  for (int j = 0; j < P; ++j) q += (v[j].x - mu) * (v[j].x - mu) + (v[j].y - mu) * (v[j].y - mu);
+  const float rstd = rsqrtf(warp_sum(q) * (1.f / C) + LN_EPS);
+#pragma unroll
+  for (int j = 0; j < P; ++j) {
+    const int c = 64 * j + 2 * lane;
+    Pair<T>::st(y + row * C + c, (v[j].x - mu) * rstd * gamma[c] + beta[c],
+                (v[j].y - mu) * rstd * gamma[c + 1] + beta[c + 1]);
+  }
+}
+
 // Channel-major input: block = 32 consecutive j of one row i.
 template <typename T>
 __global__ void __launch_bounds__(256) ln_fwd_cm_k(const T *x, int64_t pitch, const float *gamma, const float *beta,
@@ -201,9 +333,9 @@ cudaError_t ln_fwd_t(const void *x, const float *gamma, const float *beta, void 
   const T *xx = (const T *)x;
   T *yy = (T *)y;
   switch (C) {
-    case 64: ln_fwd_rows<T, 2><<<grid, 256, 0, s>>>(xx, gamma, beta, yy, M, C); break;
-    case 128: ln_fwd_rows<T, 4><<<grid, 256, 0, s>>>(xx, gamma, beta, yy, M, C); break;
-    case 256: ln_fwd_rows<T, 8><<<grid, 256, 0, s>>>(xx, gamma, beta, yy, M, C); break;
+    case 64: ln_fwd_rows_vec<T, 1><<<grid, 256, 0, s>>>(xx, gamma, beta, yy, M); break;
+    case 128: ln_fwd_rows_vec<T, 2><<<grid, 256, 0, s>>>(xx, gamma, beta, yy, M); break;
+    case 256: ln_fwd_rows_vec<T, 4><<<grid, 256, 0, s>>>(xx, gamma, beta, yy, M); break;
     default: ln_fwd_rows<T, 0><<<grid, 256, 0, s>>>(xx, gamma, beta, yy, M, C); break;
   }
   return cudaGetLastError();
@@ -243,6 +375,20 @@ cudaError_t ln_bwd(const void *dy, const void *x, const float *gamma, float *dac
   Prof p("ln_bwd", s, 0, (use_bf16 ? 2.0 : 4.0) * M * C * (dcopy ? 3 : 2) + (dacc ? 8.0 * M * C : 0.0));
   const int nb = ln_bwd_blocks(M);
   const int64_t rpb = (M + nb - 1) / nb;
+#define EVO_LN_BWD_VEC(P)                                                                                        \
+  if (C == 64 * P) {                                                                                             \
+    if (use_bf16)                                                                                                \
+      ln_bwd_rows_vec<bf16, P><<<nb, 256, 0, s>>>((const bf16 *)dy, (const bf16 *)x, gamma, dacc, (bf16 *)dcopy, \
+                                                  (bf16 *)dx_out, part, M, rpb);                                 \
+    else                                                                                                         \
+      ln_bwd_rows_vec<float, P><<<nb, 256, 0, s>>>((const float *)dy, (const float *)x, gamma, dacc,             \
+                                                   (float *)dcopy, (float *)dx_out, part, M, rpb);               \
+    return cudaGetLastError();                                                                                   \
+  }
+  EVO_LN_BWD_VEC(1)
+  EVO_LN_BWD_VEC(2)
+  EVO_LN_BWD_VEC(4)
+#undef EVO_LN_BWD_VEC
   const size_t sm = (size_t)8 * 2 * C * sizeof(float);
   if (use_bf16)
     ln_bwd_rows<bf16><<<nb, 256, sm, s>>>((const bf16 *)dy, (const bf16 *)x, gamma, dacc, (bf16 *)dcopy,
