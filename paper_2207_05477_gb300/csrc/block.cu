@@ -101,7 +101,9 @@ int validate_dims(const evo_dims *d) {
   if (d->c_m % 8 || d->c_z % 8 || d->c_mul % 8 || d->c_opm % 8 || d->c_msa % 8 || d->c_tri % 8) return EVO_ERR_UNSUPPORTED;
   if (d->h_msa > 8 || d->h_tri > 8 || d->c_msa > 32 || d->c_tri > 32) return EVO_ERR_UNSUPPORTED;
   if (d->c_m > 1024 || d->c_z > 1024 || d->c_mul > 256) return EVO_ERR_UNSUPPORTED;
-  if (d->msa_col_mode == EVO_COL_GLOBAL) return EVO_ERR_UNSUPPORTED;
+  if (d->msa_col_mode == EVO_COL_GLOBAL &&
+      (!global_attn_supported(d->h_msa, d->c_msa) || (int64_t)d->n_seq * d->h_msa * 4 > 200 * 1024))
+    return EVO_ERR_UNSUPPORTED;
   return EVO_OK;
 }
 
@@ -120,6 +122,7 @@ struct AttBufs {
 struct Plan {
   size_t xm1, xz1, bias1, qkvg1, oatt1, og1, lse1, m1;
   size_t xm2, qkvg2, oatt2, og2, lse2, m2;
+  size_t gq, gob, gst;  // global column attention: masked-mean query, output, softmax stats
   size_t xm3, h3, m3;
   size_t xm4, ab4, O4, inv4, z1;
   TriBufs tri[2];
@@ -160,6 +163,7 @@ size_t make_plan(const evo_dims &d, int mode, Plan &p) {
   p.oatt1 = T(k.Mm * k.HCm), p.og1 = T(k.Mm * k.HCm), p.lse1 = F(k.S * k.Hm * k.R), p.m1 = T(k.Mm * k.Cm);
   p.xm2 = T(k.Mm * k.Cm), p.qkvg2 = T(k.Mm * k.QKc), p.oatt2 = T(k.Mm * k.HCm), p.og2 = T(k.Mm * k.HCm);
   p.lse2 = F(k.R * k.Hm * k.S), p.m2 = T(k.Mm * k.Cm);
+  p.gq = F(k.R * k.HCm), p.gob = F(k.R * k.HCm), p.gst = F(k.R * k.Hm * 2);
   p.xm3 = T(k.Mm * k.Cm), p.h3 = T(k.Mm * k.n * k.Cm), p.m3 = T(k.Mm * k.Cm);
   p.xm4 = T(k.Mm * k.Cm), p.ab4 = T(2 * k.Mm * k.co), p.O4 = T(k.Mz * k.co * k.co), p.inv4 = F(k.Mz);
   p.z1 = T(k.Mz * k.Cz);
@@ -328,8 +332,19 @@ struct Drv {
     return a;
   }
 
+  GlobalAttnArgs global_args() {
+    GlobalAttnArgs a{};
+    a.qkvg = B(pl.qkvg2), a.ld = k.QKc, a.S = (int)k.S, a.R = (int)k.R, a.H = (int)k.Hm, a.c = (int)k.cm;
+    a.mask = msa_mask_, a.o_att_bar = Bf(pl.gob), a.qbar = Bf(pl.gq), a.lse2 = Bf(pl.gst), a.o_gate = B(pl.og2);
+    a.scale = 1.f / std::sqrt((float)k.cm);
+    return a;
+  }
+
   // ================================================================ forward
+  const float *msa_mask_ = nullptr;
+
   void forward(const void *m0, const void *z0, void *m_out, void *z_out, const float *mm, const float *pm) {
+    msa_mask_ = mm;
     const int64_t S = k.S, R = k.R, Cm = k.Cm, Cz = k.Cz, Mm = k.Mm, Mz = k.Mz, HCm = k.HCm, HCt = k.HCt;
     // 1. MSA row attention with pair bias (AF2 Alg. 7)
     ln(m0, "row.ln_m", B(pl.xm1), Mm, (int)Cm);
@@ -345,14 +360,19 @@ struct Drv {
       o.e.bias = P("row.b_o"), o.e.residual = m0;
       gemm(o);
     }
-    // 2. MSA column attention (AF2 Alg. 8)
+    // 2. MSA column attention (AF2 Alg. 8), or global column attention (AF2 Alg. 19)
     ln(B(pl.m1), "col.ln", B(pl.xm2), Mm, (int)Cm);
     {
+      const int64_t g0 = d.msa_col_mode == EVO_COL_GLOBAL ? HCm + 2 * k.cm : 3 * HCm;
       GemmOp g = mk(Mm, k.QKc, Cm, B(pl.xm2), Cm, 0, W("col.w_qkvg"), Cm, 0, B(pl.qkvg2), k.QKc);
-      g.e.bias = P("col.b_g"), g.e.bias_n0 = (int)(3 * HCm), g.e.act = ACT_SIGMOID, g.e.act_n0 = (int)(3 * HCm);
+      g.e.bias = P("col.b_g"), g.e.bias_n0 = (int)g0, g.e.act = ACT_SIGMOID, g.e.act_n0 = (int)g0;
       gemm(g);
-      AttnArgs a = attn_args(1, B(pl.qkvg2), B(pl.oatt2), B(pl.og2), Bf(pl.lse2), nullptr, mm);
-      ck(attn_fwd(a, bf, s));
+      if (d.msa_col_mode == EVO_COL_GLOBAL) {
+        ck(global_attn_fwd(global_args(), bf, s));
+      } else {
+        AttnArgs a = attn_args(1, B(pl.qkvg2), B(pl.oatt2), B(pl.og2), Bf(pl.lse2), nullptr, mm);
+        ck(attn_fwd(a, bf, s));
+      }
       GemmOp o = mk(Mm, Cm, HCm, B(pl.og2), HCm, 0, W("col.w_o"), HCm, 0, B(pl.m2), Cm);
       o.e.bias = P("col.b_o"), o.e.residual = B(pl.m1);
       gemm(o);
@@ -566,8 +586,21 @@ struct Drv {
     }
     // 3. MSA transition
     transition_bwd("msa_trans", B(pl.m2), B(pl.xm3), B(pl.h3), dm, dmT, Mm, Cm);
-    // 2. MSA column attention
-    attention_bwd(1, "col", B(pl.xm2), B(pl.qkvg2), B(pl.oatt2), B(pl.og2), Bf(pl.lse2), nullptr, mm, dmT, Mm, Cm);
+    // 2. MSA column attention (or global column attention)
+    if (d.msa_col_mode == EVO_COL_GLOBAL) {
+      const int64_t HC = k.HCm, QK = k.QKc;
+      dW(dmT, Cm, Cm, B(pl.og2), HC, HC, Mm, "col.w_o");
+      db(dmT, Cm, Mm, Cm, "col.b_o");
+      GemmOp g = mk(Mm, HC, Cm, dmT, Cm, 0, W("col.w_o"), HC, 1, B(pl.G2), HC);
+      gemm(g);
+      ck(global_attn_bwd(global_args(), B(pl.G2), B(pl.G1), nullptr, bf, s));
+      dW(B(pl.G1), QK, QK, B(pl.xm2), Cm, Cm, Mm, "col.w_qkvg");
+      db(at(B(pl.G1), HC + 2 * k.cm), QK, Mm, HC, "col.b_g");
+      GemmOp x = mk(Mm, Cm, QK, B(pl.G1), QK, 0, W("col.w_qkvg"), Cm, 1, B(pl.G2), Cm);
+      gemm(x);
+    } else {
+      attention_bwd(1, "col", B(pl.xm2), B(pl.qkvg2), B(pl.oatt2), B(pl.og2), Bf(pl.lse2), nullptr, mm, dmT, Mm, Cm);
+    }
     lnb(B(pl.G2), B(pl.m1), "col.ln", dm, dmT, nullptr, Mm, (int)Cm);
     // 1. MSA row attention with pair bias
     attention_bwd(0, "row", B(pl.xm1), B(pl.qkvg1), B(pl.oatt1), B(pl.og1), Bf(pl.lse1), Bf(pl.bias1), mm, dmT, Mm,

@@ -71,11 +71,12 @@ struct GlobalAttnArgs {
   int S, R, H, c;
   const float *mask;  // [S,R]
   void *o_att_bar;    // [R, H*c] fp32 attention output per column (before gate)
-  float *qbar;        // [R, H*c] fp32
-  float *lse2;        // [R, H]
+  float *qbar;        // [R, H*c] fp32 masked mean of q
+  float *lse2;        // [R, H, 2] fp32 softmax max (log2 units) and sum
   void *o_gate;       // [S,R,H*c]
   float scale;
 };
+bool global_attn_supported(int H, int c);
 cudaError_t global_attn_fwd(const GlobalAttnArgs &a, int use_bf16, cudaStream_t s);
 // backward: dog [S,R,H*c] grad of gated output -> dqkvg rows (same layout as qkvg)
 cudaError_t global_attn_bwd(const GlobalAttnArgs &a, const void *dog, void *dqkvg, float *scratch,

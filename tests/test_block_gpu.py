@@ -104,3 +104,26 @@ def test_fp32_fwd_bwd_training_crop(built_lib):
     d = synth.DIMS_TRAIN_CROP
     out = gpu_run(d, evo.EVO_F32, pad_frac=0.05)
     _check(out, oracle_fwd_bwd(d, pad_frac=0.05), FP32_TOL, FP32_GRAD_TOL, d)
+
+
+# ------------------------------------------------- extra-MSA block (global column attention)
+EXTRA_SMALL = synth.DIMS_EXTRA_MSA.replace(n_seq=64, n_res=40)
+EXTRA_MID = synth.DIMS_EXTRA_MSA.replace(n_seq=512, n_res=96)
+
+
+def test_extra_msa_fp32_fwd_bwd(built_lib):
+    out = gpu_run(EXTRA_SMALL, evo.EVO_F32, pad_frac=0.1)
+    _check(out, oracle_fwd_bwd(EXTRA_SMALL, pad_frac=0.1), FP32_TOL, FP32_GRAD_TOL, EXTRA_SMALL)
+
+
+def test_extra_msa_bf16_fwd_bwd(built_lib):
+    out = gpu_run(EXTRA_MID, evo.EVO_BF16, pad_frac=0.05)
+    _check(out, oracle_fwd_bwd(EXTRA_MID, pad_frac=0.05), BF16_TOL, BF16_GRAD_TOL, EXTRA_MID, RELU_MASKED_TOL)
+
+
+@pytest.mark.slow
+def test_extra_msa_bf16_full_size(built_lib):
+    """The paper's initial-training extra-MSA block: N_extra_seq=1024, N_res=256, c_e=64."""
+    d = synth.DIMS_EXTRA_MSA
+    out = gpu_run(d, evo.EVO_BF16, pad_frac=0.05)
+    _check(out, oracle_fwd_bwd(d, pad_frac=0.05), BF16_TOL, BF16_GRAD_TOL, d, RELU_MASKED_TOL)
