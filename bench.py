@@ -41,8 +41,11 @@ def block_fwd_flops(d) -> float:
     f = 0.0
     # MSA row attention with pair bias
     f += 2 * Mm * Cm * 4 * HCm + 2 * Mz * Cz * d.h_msa + 4 * S * d.h_msa * R * R * d.c_msa + 2 * Mm * HCm * Cm
-    # MSA column attention
-    f += 2 * Mm * Cm * 4 * HCm + 4 * R * d.h_msa * S * S * d.c_msa + 2 * Mm * HCm * Cm
+    # MSA column attention (global column attention in the extra-MSA block)
+    if d.msa_col_mode == 0:
+        f += 2 * Mm * Cm * 4 * HCm + 4 * R * d.h_msa * S * S * d.c_msa + 2 * Mm * HCm * Cm
+    else:
+        f += 2 * Mm * Cm * (2 * HCm + 2 * d.c_msa) + 4 * S * R * HCm + 2 * Mm * HCm * Cm
     # MSA transition
     f += 2 * 2 * Mm * Cm * d.trans_n * Cm
     # outer product mean
@@ -217,6 +220,20 @@ def ours_arm(args):
     if evo.get_error() != evo.EVO_OK:
         raise RuntimeError("device error word set during warm-up")
 
+    graph = None
+    if args.graph:
+        # the whole step (parameter copy, forward, backward) as one CUDA graph; the
+        # library's per-kernel event records are captured with it and hold the
+        # times of the last replay
+        gstream = torch.cuda.Stream()
+        gstream.wait_stream(stream)
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph, stream=gstream):
+            step(m, z, mm, pm, gm, gz, params)
+        stream.wait_stream(gstream)
+        graph.replay()
+        torch.cuda.synchronize()
+
     # ---- timed region: K steps, L2 flushed between steps (outside each step's events)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     clocks = ClockSampler(local)
@@ -224,13 +241,26 @@ def ours_arm(args):
         torch.distributed.barrier()
     torch.cuda.synchronize()
     clocks.start()
-    evo.profile_begin()
+    if graph is None:
+        evo.profile_begin()
     for i in range(args.steps):
         flush.fill_(float(i))
         ev[i][0].record(stream)
-        step(m, z, mm, pm, gm, gz, params)
+        if graph is None:
+            step(m, z, mm, pm, gm, gz, params)
+        else:
+            graph.replay()
         ev[i][1].record(stream)
-    prof = evo.profile_end()
+    if graph is None:
+        prof = evo.profile_end()
+    else:
+        # event pairs captured inside a graph cannot be timed: the per-kernel
+        # profile comes from one eager step after the timed region
+        torch.cuda.synchronize()
+        evo.profile_begin()
+        step(m, z, mm, pm, gm, gz, params)
+        prof = evo.profile_end()
+    prof_steps = 1 if graph is not None else args.steps
     torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
@@ -256,10 +286,15 @@ def ours_arm(args):
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
+    if graph is not None:  # the graph reads the step's fixed device buffers
+        dbuf = {"m": m, "z": z, "msa_mask": mm, "pair_mask": pm, "gm": gm, "gz": gz, "params": params}
     for _ in range(e2e_steps):
         for k in host:
             dbuf[k].copy_(host[k], non_blocking=True)
-        step(dbuf["m"], dbuf["z"], dbuf["msa_mask"], dbuf["pair_mask"], dbuf["gm"], dbuf["gz"], dbuf["params"])
+        if graph is None:
+            step(dbuf["m"], dbuf["z"], dbuf["msa_mask"], dbuf["pair_mask"], dbuf["gm"], dbuf["gz"], dbuf["params"])
+        else:
+            graph.replay()
         out_host["dm"].copy_(dm, non_blocking=True)
         out_host["dz"].copy_(dz, non_blocking=True)
         out_host["dparams"].copy_(dparams, non_blocking=True)
@@ -301,7 +336,7 @@ def ours_arm(args):
 
     # ---- roofline of the dominant kernel class of the timed steps
     peaks = load_peaks()
-    launches = int(sum(v["launches"] for v in prof.values()))
+    launches = int(sum(v["launches"] for v in prof.values())) * (args.steps // prof_steps)
     dom_name, dom = max(prof.items(), key=lambda kv: kv[1]["ms"])
     dom_ms_per_launch = dom["ms"] / max(dom["launches"], 1)
     tensor_kernels = ("gemm_tc", "attn_fwd_mma", "attn_bwd_mma")
@@ -324,7 +359,7 @@ def ours_arm(args):
         if dom_name in tr and tr[dom_name].get("valid", False):
             roof["traffic"] = tr[dom_name]["bytes_per_launch"]
 
-    kernels = {k: {"ms_per_step": v["ms"] / args.steps, "launches_per_step": v["launches"] / args.steps,
+    kernels = {k: {"ms_per_step": v["ms"] / prof_steps, "launches_per_step": v["launches"] / prof_steps,
                    "share": v["ms"] / max(sum(x["ms"] for x in prof.values()), 1e-9),
                    "tflops": (v["flops"] / (v["ms"] / 1e3) / 1e12) if v["flops"] else None,
                    "gbs": (v["bytes"] / (v["ms"] / 1e3) / 1e9) if v["bytes"] else None}
@@ -343,7 +378,7 @@ def ours_arm(args):
                                    f"c_m=256 c_z=128, 5% padded residues",
                        "n_seq": d.n_seq, "n_res": d.n_res, "flops_per_step": step_flops(d),
                        "l2": "flushed between timed steps (258 MB write outside the step events)",
-                       "parallelism": f"replicas x{world}"},
+                       "parallelism": f"replicas x{world}", "cuda_graph": bool(args.graph)},
             "clocks": clk, "gpu_launches": launches,
             "e2e": {"value": e2e_value, "unit": "TFLOP/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "ms_per_step": float(te.item())},
@@ -353,6 +388,152 @@ def ours_arm(args):
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
+    return 0
+
+
+# ---------------------------------------------------------------- other workloads
+def other_workload(args):
+    """The paper's other shapes, one JSON line each (not the headline):
+    small_fp32_fwd  one block forward, plain FP32 path, N_seq=16 N_res=64
+    extra_msa       extra-MSA block fwd+bwd (global column attention), N_extra=1024 N_res=256 c_e=64
+    stack48         48-block stack fwd+bwd, N_seq=512 N_res=384, per-block recompute (block inputs kept)
+    long2048        one block forward at N_res=2048, N_seq=128
+    batch16         16 proteins (N_res ~ U[64,1024], N_seq ~ U[32,512], seeded), 48-block forward each
+    """
+    import numpy as np
+    import torch
+    from paper_2207_05477_gb300 import evo, synth
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    evo.lib()
+    stream = torch.cuda.current_stream()
+    peaks = load_peaks()
+
+    def buffers(d, act, seed, n_params=1):
+        cd = evo.cdims(d, act)
+        tdt = torch.bfloat16 if act == evo.EVO_BF16 else torch.float32
+        prob = synth.make_problem(d, seed, pad_frac=0.05)
+        n = evo.param_count(cd)
+        stride = (n + 127) // 128 * 128  # per-block sets start 256-byte aligned in both copies
+        if n_params == 1:
+            params = torch.tensor(prob["params"], device=dev)
+        else:
+            params = torch.zeros(n_params * stride, device=dev)
+            for b in range(n_params):
+                params[b * stride:b * stride + n] = torch.tensor(synth.make_params(d, seed + 1000 + b), device=dev)
+        p16 = None
+        if act == evo.EVO_BF16:
+            p16 = torch.empty(params.numel(), dtype=torch.bfloat16, device=dev)
+            for b in range(n_params):
+                evo.params_to_bf16(cd, params[b * stride:b * stride + n], p16[b * stride:b * stride + n])
+        return dict(cd=cd, stride=stride, params=params, p16=p16,
+                    m=torch.tensor(prob["m"], device=dev).to(tdt), z=torch.tensor(prob["z"], device=dev).to(tdt),
+                    mm=torch.tensor(prob["msa_mask"], device=dev), pm=torch.tensor(prob["pair_mask"], device=dev),
+                    gm=torch.tensor(prob["gm"], device=dev).to(tdt), gz=torch.tensor(prob["gz"], device=dev).to(tdt))
+
+    def timed(fn, steps, warmup):
+        for _ in range(warmup):
+            fn()
+        torch.cuda.synchronize()
+        clocks = ClockSampler(0)
+        clocks.start()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(steps):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        if evo.get_error() != evo.EVO_OK:
+            raise RuntimeError("device error word set")
+        return a.elapsed_time(b) / steps, clocks.stop()
+
+    torch.cuda.reset_peak_memory_stats()
+    w = args.workload
+    extra = {}
+    if w in ("small_fp32_fwd", "long2048", "extra_msa"):
+        if w == "small_fp32_fwd":
+            d, act, bwd = synth.DIMS_SMALL_FP32, evo.EVO_F32, False
+        elif w == "long2048":
+            d, act, bwd = synth.Dims(n_seq=128, n_res=2048), evo.EVO_BF16, False
+        else:
+            d, act, bwd = synth.DIMS_EXTRA_MSA, evo.EVO_BF16, True
+        B = buffers(d, act, 32)
+        cd = B["cd"]
+        mo, zo = torch.empty_like(B["m"]), torch.empty_like(B["z"])
+        wsf = evo.workspace(cd, evo.EVO_MODE_FWD, dev)
+        wsb = evo.workspace(cd, evo.EVO_MODE_BWD, dev) if bwd else None
+        dm, dz, dp = torch.empty_like(B["m"]), torch.empty_like(B["z"]), torch.zeros_like(B["params"])
+
+        def fn():
+            evo.block_fwd(cd, B["params"], B["p16"], B["m"], B["z"], mo, zo, B["mm"], B["pm"], wsf)
+            if bwd:
+                evo.block_bwd(cd, B["params"], B["p16"], B["m"], B["z"], B["mm"], B["pm"], B["gm"], B["gz"], dm, dz,
+                              dp, wsb)
+
+        ms, clk = timed(fn, args.steps, max(3, args.warmup))
+        flops = step_flops(d) if bwd else block_fwd_flops(d)
+        desc = f"N_seq={d.n_seq} N_res={d.n_res} c_m={d.c_m} {'fwd+bwd' if bwd else 'fwd'} " \
+               f"{'BF16' if act else 'FP32 plain'}{' global column attention' if d.msa_col_mode else ''}"
+    elif w == "stack48":
+        d = synth.Dims(n_seq=512, n_res=384)
+        nb = 48
+        B = buffers(d, evo.EVO_BF16, 32, n_params=nb)
+        cd, stride = B["cd"], B["stride"]
+        wsf = evo.workspace(cd, evo.EVO_MODE_FWD, dev)
+        wsb = evo.workspace(cd, evo.EVO_MODE_BWD, dev)
+        ms_in = [torch.empty_like(B["m"]) for _ in range(nb + 1)]  # block inputs: the only saved activations
+        zs_in = [torch.empty_like(B["z"]) for _ in range(nb + 1)]
+        dm, dz = B["gm"].clone(), B["gz"].clone()
+        dm2, dz2 = torch.empty_like(dm), torch.empty_like(dz)
+        dp = torch.zeros_like(B["params"])
+
+        def fn():
+            ms_in[0].copy_(B["m"])
+            zs_in[0].copy_(B["z"])
+            for b in range(nb):
+                p = B["params"][b * stride:(b + 1) * stride]
+                p16 = B["p16"][b * stride:(b + 1) * stride]
+                evo.block_fwd(cd, p, p16, ms_in[b], zs_in[b], ms_in[b + 1], zs_in[b + 1], B["mm"], B["pm"], wsf)
+            g_m, g_z, o_m, o_z = B["gm"], B["gz"], dm, dz
+            for b in reversed(range(nb)):
+                p = B["params"][b * stride:(b + 1) * stride]
+                p16 = B["p16"][b * stride:(b + 1) * stride]
+                evo.block_bwd(cd, p, p16, ms_in[b], zs_in[b], B["mm"], B["pm"], g_m, g_z, o_m, o_z,
+                              dp[b * stride:(b + 1) * stride], wsb)
+                g_m, g_z, o_m, o_z = o_m, o_z, (dm2 if o_m is dm else dm), (dz2 if o_z is dz else dz)
+
+        ms, clk = timed(fn, args.steps, 1)
+        flops = nb * step_flops(d)
+        desc = f"48-block stack fwd+bwd, N_seq=512 N_res=384, BF16, per-block recompute"
+        extra["saved_block_inputs_gb"] = sum(t.numel() * t.element_size() for t in ms_in + zs_in) / 1e9
+    else:  # batch16
+        rng = np.random.default_rng(32)
+        prot = [(int(rng.integers(32, 513)), int(rng.integers(64, 1025))) for _ in range(16)]
+        nb = 48
+        flops = 0.0
+        jobs = []
+        for i, (S, R) in enumerate(prot):
+            d = synth.Dims(n_seq=S, n_res=R)
+            B = buffers(d, evo.EVO_BF16, 100 + i, n_params=1)
+            jobs.append((d, B))
+            flops += nb * block_fwd_flops(d)
+        maxws = max(evo.workspace_size(B["cd"], evo.EVO_MODE_FWD) for _, B in jobs)
+        wsf = torch.empty(maxws, dtype=torch.uint8, device=dev)
+
+        def fn():
+            for d, B in jobs:
+                m, z = B["m"].clone(), B["z"].clone()
+                for _ in range(nb):
+                    evo.block_fwd(B["cd"], B["params"], B["p16"], m, z, m, z, B["mm"], B["pm"], wsf)
+
+        ms, clk = timed(fn, args.steps, 1)
+        desc = "16 proteins (seeded N_res~U[64,1024], N_seq~U[32,512]), 48-block forward each, BF16, in sequence"
+        extra["proteins"] = prot
+    line = {"workload": w, "metric": desc, "value": flops / (ms / 1e3) / 1e12, "unit": "TFLOP/s", "ms_per_step": ms,
+            "steps": args.steps, "flops_per_step": flops, "frac_of_bf16_peak": flops / (ms / 1e3) / 1e12 / peaks["bf16_sus"],
+            "peak_mem_gb": torch.cuda.max_memory_allocated() / 1e9, "clocks": clk, "data": "synthetic"}
+    line.update(extra)
+    print(json.dumps(line), flush=True)
     return 0
 
 
@@ -367,11 +548,16 @@ def main():
     ap.add_argument("--n-res", type=int, default=256)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp32", action="store_true")
+    ap.add_argument("--graph", action="store_true", help="replay the step as one captured CUDA graph")
+    ap.add_argument("--workload", default="train_crop",
+                    choices=["train_crop", "small_fp32_fwd", "extra_msa", "stack48", "long2048", "batch16"])
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
     if args.impl == "reference":
         return reference_arm(args)
+    if args.workload != "train_crop":
+        return other_workload(args)
     return ours_arm(args)
 
 
