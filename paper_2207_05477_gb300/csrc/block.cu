@@ -128,7 +128,7 @@ struct Plan {
   TriBufs tri[2];
   AttBufs att[2];
   size_t xz9, h9, z6;
-  size_t dm_acc, dmT, dz_acc, dzT, G1, G2, G3, dO4, dA, dB, dX, dq_acc, dbias, Dsum, dab4, split, cpart, lpart, hpart;
+  size_t dm_acc, dmT, dz_acc, dzT, G1, G2, G3, dO4, dA, dB, dX, dq_acc, dbias, Dsum, dab4, split;
   size_t total;
 };
 
@@ -195,12 +195,6 @@ size_t make_plan(const evo_dims &d, int mode, Plan &p) {
                              4 * k.HCt * k.Cz, k.Cz * k.co * k.co, k.Cm * k.HCm, 2 * k.co * k.Cm,
                              k.Cz * k.cmul, k.Cz * k.HCt});
     p.split = F(MAXSPLIT * wmax);
-    int64_t nmax = std::max<int64_t>({k.QKm, k.QKc, k.n * k.Cm, k.n * k.Cz, k.ABG, 4 * k.HCt, k.Cm, k.Cz});
-    p.cpart = F(512 * nmax);
-    int64_t lmax = std::max<int64_t>(1024 * 2 * std::max(k.Cm, k.Cz),
-                                     (int64_t)ln_bwd_cm_blocks((int)k.R) * 2 * k.cmul);
-    p.lpart = F(lmax);
-    p.hpart = F(1024 * std::max(k.Hm, k.Ht) * k.Cz);
   }
   p.total = off;
   return off;
@@ -277,15 +271,11 @@ struct Drv {
     ck(reduce_splits(Bf(pl.split), (int)sp, Nout * Kin, D(w), s));
   }
   void db(const void *dY, int64_t ldY, int64_t rows, int64_t N, const std::string &b) {
-    ck(colsum(dY, ldY, rows, (int)N, Bf(pl.cpart), bf, s));
-    ck(reduce_partials(Bf(pl.cpart), colsum_blocks(rows), (int)N, D(b), s));
+    ck(colsum(dY, ldY, rows, (int)N, bf, s, D(b)));
   }
   void lnb(const void *dy, const void *x, const std::string &pre, float *dacc, void *dcopy, void *dx_out, int64_t M,
            int C) {
-    ck(ln_bwd(dy, x, P(pre + ".gamma"), dacc, dcopy, dx_out, Bf(pl.lpart), M, C, bf, s));
-    const int nb = ln_bwd_blocks(M);
-    ck(reduce_partials_ld(Bf(pl.lpart), nb, 2 * C, C, D(pre + ".gamma"), s));
-    ck(reduce_partials_ld(Bf(pl.lpart) + C, nb, 2 * C, C, D(pre + ".beta"), s));
+    ck(ln_bwd(dy, x, P(pre + ".gamma"), dacc, dcopy, dx_out, M, C, bf, s, D(pre + ".gamma"), D(pre + ".beta")));
   }
 
   // ---------------- attention argument sets
@@ -501,9 +491,8 @@ struct Drv {
   }
 
   void pair_bias_bwd(const std::string &wname, const void *xn, int H, int transpose, int accumulate) {
-    ck(head_proj_bwd(Bf(pl.dbias), xn, P(wname), B(pl.G2), accumulate, Bf(pl.hpart), (int)k.R, (int)k.Cz, H,
-                     transpose, bf, s));
-    ck(reduce_partials(Bf(pl.hpart), head_proj_blocks((int)k.R), H * (int)k.Cz, D(wname), s));
+    ck(head_proj_bwd(Bf(pl.dbias), xn, P(wname), B(pl.G2), accumulate, (int)k.R, (int)k.Cz, H, transpose, bf, s,
+                     D(wname)));
   }
 
   void trimul_bwd(int t, const void *zin, const float *pm, float *dacc, void *dT) {
@@ -515,12 +504,8 @@ struct Drv {
     db(B(pl.G2), Cz, Mz, Cz, pre + ".b_o");
     GemmOp g = mk(Mz, cmul, Cz, B(pl.G2), Cz, 0, W(pre + ".w_o"), cmul, 1, B(pl.G3), cmul);
     gemm(g);
-    ck(ln_bwd_cm(B(pl.G3), B(b.X), Rp, P(pre + ".ln_out.gamma"), B(pl.dX), Bf(pl.lpart), (int)R, (int)cmul, bf, s));
-    {
-      const int nb = ln_bwd_cm_blocks((int)R);
-      ck(reduce_partials_ld(Bf(pl.lpart), nb, 2 * cmul, (int)cmul, D(pre + ".ln_out.gamma"), s));
-      ck(reduce_partials_ld(Bf(pl.lpart) + cmul, nb, 2 * cmul, (int)cmul, D(pre + ".ln_out.beta"), s));
-    }
+    ck(ln_bwd_cm(B(pl.G3), B(b.X), Rp, P(pre + ".ln_out.gamma"), B(pl.dX), (int)R, (int)cmul, bf, s,
+                 D(pre + ".ln_out.gamma"), D(pre + ".ln_out.beta")));
     // dA_c = dX_c B_c ; dB_c = dX_c^T A_c
     GemmOp ga = mk(R, R, R, B(pl.dX), Rp, 0, B(b.B), Rp, 1, B(pl.dA), Rp);
     ga.batch = (int)cmul, ga.a_bs = R * Rp, ga.b_bs = R * Rp, ga.e.c_bstride = R * Rp;

@@ -90,24 +90,23 @@ cudaError_t ln_fwd(const void *x, const float *gamma, const float *beta, void *y
 cudaError_t ln_fwd_cm(const void *x, int64_t pitch, const float *gamma, const float *beta, void *y,
                       int R, int C, int use_bf16, cudaStream_t s);
 // dx = LN backward of dy (rows x[M,C]); dacc (fp32) += dx if dacc else dx_out = dx;
-// dcopy (activation type, may be null) = updated dacc; partial sums of dgamma, dbeta
-// go to part[blk][2C] (blocks = ln_bwd_blocks(M)).
-int ln_bwd_blocks(int64_t M);
+// dcopy (activation type, may be null) = updated dacc.  Each block adds its sums
+// of the gamma/beta gradients to dgamma, dbeta with fp32 atomics.
 cudaError_t ln_bwd(const void *dy, const void *x, const float *gamma, float *dacc, void *dcopy,
-                   void *dx_out, float *part, int64_t M, int C, int use_bf16, cudaStream_t s);
+                   void *dx_out, int64_t M, int C, int use_bf16, cudaStream_t s, float *dgamma,
+                   float *dbeta);
 // LayerNorm backward for the channel-major input of ln_fwd_cm: dy row-major [R*R, C],
-// dx channel-major [C][R][pitch].
-int ln_bwd_cm_blocks(int R);
+// dx channel-major [C][R][pitch]; dgamma, dbeta accumulated with fp32 atomics.
 cudaError_t ln_bwd_cm(const void *dy, const void *x, int64_t pitch, const float *gamma, void *dx,
-                      float *part, int R, int C, int use_bf16, cudaStream_t s);
+                      int R, int C, int use_bf16, cudaStream_t s, float *dgamma, float *dbeta);
 
 // Sum of partial rows: out[n] += sum_b part[b*N + n], n < N.
 cudaError_t reduce_partials(const float *part, int nblk, int N, float *out, cudaStream_t s);
 // out[n] += sum_b part[b*ld + n]
 cudaError_t reduce_partials_ld(const float *part, int nblk, int64_t ld, int N, float *out, cudaStream_t s);
-// Column sums of x[M, N] (leading dim ld, activation type) into part[blk][N].
-int colsum_blocks(int64_t M);
-cudaError_t colsum(const void *x, int64_t ld, int64_t M, int N, float *part, int use_bf16, cudaStream_t s);
+// out[n] += sum_m x[m, n] (leading dim ld, activation type); each block adds its
+// column sums over a range of rows with fp32 atomics.
+cudaError_t colsum(const void *x, int64_t ld, int64_t M, int N, int use_bf16, cudaStream_t s, float *out);
 // out[i] += sum_s part[s*n + i]
 cudaError_t reduce_splits(const float *part, int splits, int64_t n, float *out, cudaStream_t s);
 
@@ -115,10 +114,10 @@ cudaError_t reduce_splits(const float *part, int splits, int64_t n, float *out, 
 // pos' = p0*R+p1, or p1*R+p0 with transpose.
 cudaError_t head_proj_fwd(const void *x, const float *w, float *out, int R, int C, int H, int transpose,
                           int use_bf16, cudaStream_t s);
-// dx[pos] (+)= sum_h dbias[h][pos'] w[h]; dw partials part[blk][H*C].
-int head_proj_blocks(int R);
+// dx[pos] (+)= sum_h dbias[h][pos'] w[h]; dw += sum_pos dbias x (each block adds
+// its sum over a range of positions with fp32 atomics).
 cudaError_t head_proj_bwd(const float *dbias, const void *x, const float *w, void *dx, int accumulate,
-                          float *part, int R, int C, int H, int transpose, int use_bf16, cudaStream_t s);
+                          int R, int C, int H, int transpose, int use_bf16, cudaStream_t s, float *dw);
 
 // Triangle multiplication gating: abg[P, ld] raw projections [ap|ag|bp|bg|g];
 // a,b written channel-major [c][R][pitch] (incoming: transposed positions);

@@ -50,7 +50,8 @@ __global__ void __launch_bounds__(256) ln_fwd_rows(const T *x, const float *gamm
 // dx = rstd * (gdy - mean(gdy) - xhat * mean(gdy * xhat)), gdy = gamma * dy.
 template <typename T>
 __global__ void __launch_bounds__(256) ln_bwd_rows(const T *dy, const T *x, const float *gamma, float *dacc, T *dcopy,
-                                                   T *dx_out, float *part, int64_t M, int C, int64_t rows_per_blk) {
+                                                   T *dx_out, int64_t M, int C, int64_t rows_per_blk,
+                                                   float *dgamma, float *dbeta) {
   extern __shared__ float sh[];  // [8][2C]
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   float *mine = sh + warp * 2 * C;
@@ -98,7 +99,7 @@ __global__ void __launch_bounds__(256) ln_bwd_rows(const T *dy, const T *x, cons
   for (int cc = threadIdx.x; cc < 2 * C; cc += blockDim.x) {
     float t = 0.f;
     for (int w = 0; w < 8; ++w) t += sh[w * 2 * C + cc];
-    part[(int64_t)blockIdx.x * 2 * C + cc] = t;
+    atomicAdd(cc < C ? dgamma + cc : dbeta + cc - C, t);
   }
 }
 
@@ -123,8 +124,8 @@ template <> struct Pair<float> {
 // 64j + 2l, 64j + 2l + 1 (j < P), so every load is a coalesced pair.
 template <typename T, int P>
 __global__ void __launch_bounds__(256) ln_bwd_rows_vec(const T *dy, const T *x, const float *gamma, float *dacc,
-                                                       T *dcopy, T *dx_out, float *part, int64_t M,
-                                                       int64_t rows_per_blk) {
+                                                       T *dcopy, T *dx_out, int64_t M,
+                                                       int64_t rows_per_blk, float *dgamma, float *dbeta) {
   constexpr int C = 64 * P;
   __shared__ float red[8][2 * C];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -202,7 +203,7 @@ __global__ void __launch_bounds__(256) ln_bwd_rows_vec(const T *dy, const T *x, 
     float t = 0.f;
 #pragma unroll
     for (int w = 0; w < 8; ++w) t += red[w][cc];
-    part[(int64_t)blockIdx.x * 2 * C + cc] = t;
+    atomicAdd(cc < C ? dgamma + cc : dbeta + cc - C, t);
   }
 }
 
@@ -266,7 +267,7 @@ __global__ void __launch_bounds__(256) ln_fwd_cm_k(const T *x, int64_t pitch, co
 
 template <typename T>
 __global__ void __launch_bounds__(256) ln_bwd_cm_k(const T *dy, const T *x, int64_t pitch, const float *gamma, T *dx,
-                                                   float *part, int R, int C) {
+                                                   int R, int C, float *dgamma, float *dbeta) {
   extern __shared__ float sm[];  // xt [C][33], dxt [C][33], acc [8][2C]
   float *xt = sm;
   float *dxt = sm + C * 33;
@@ -319,11 +320,10 @@ __global__ void __launch_bounds__(256) ln_bwd_cm_k(const T *dy, const T *x, int6
     const int cc = idx >> 5, jj = idx & 31;
     if (j0 + jj < R) stf(dx + cc * plane + (int64_t)i * pitch + j0 + jj, dxt[cc * 33 + jj]);
   }
-  const int64_t blk = (int64_t)blockIdx.y * gridDim.x + blockIdx.x;
   for (int cc = threadIdx.x; cc < 2 * C; cc += blockDim.x) {
     float t = 0.f;
     for (int w = 0; w < 8; ++w) t += acc[w * 2 * C + cc];
-    part[blk * 2 * C + cc] = t;
+    atomicAdd(cc < C ? dgamma + cc : dbeta + cc - C, t);
   }
 }
 
@@ -347,7 +347,6 @@ int ln_bwd_blocks(int64_t M) {
   int64_t b = (M + 63) / 64;
   return (int)(b < 296 ? (b < 1 ? 1 : b) : 296);
 }
-int ln_bwd_cm_blocks(int R) { return R * ((R + 31) / 32); }
 
 cudaError_t ln_fwd(const void *x, const float *gamma, const float *beta, void *y, int64_t M, int C, int use_bf16,
                    cudaStream_t s) {
@@ -370,7 +369,7 @@ cudaError_t ln_fwd_cm(const void *x, int64_t pitch, const float *gamma, const fl
 }
 
 cudaError_t ln_bwd(const void *dy, const void *x, const float *gamma, float *dacc, void *dcopy, void *dx_out,
-                   float *part, int64_t M, int C, int use_bf16, cudaStream_t s) {
+                   int64_t M, int C, int use_bf16, cudaStream_t s, float *dgamma, float *dbeta) {
   if (M <= 0) return cudaSuccess;
   Prof p("ln_bwd", s, 0, (use_bf16 ? 2.0 : 4.0) * M * C * (dcopy ? 3 : 2) + (dacc ? 8.0 * M * C : 0.0));
   const int nb = ln_bwd_blocks(M);
@@ -379,10 +378,10 @@ cudaError_t ln_bwd(const void *dy, const void *x, const float *gamma, float *dac
   if (C == 64 * P) {                                                                                             \
     if (use_bf16)                                                                                                \
       ln_bwd_rows_vec<bf16, P><<<nb, 256, 0, s>>>((const bf16 *)dy, (const bf16 *)x, gamma, dacc, (bf16 *)dcopy, \
-                                                  (bf16 *)dx_out, part, M, rpb);                                 \
+                                                  (bf16 *)dx_out, M, rpb, dgamma, dbeta);         \
     else                                                                                                         \
       ln_bwd_rows_vec<float, P><<<nb, 256, 0, s>>>((const float *)dy, (const float *)x, gamma, dacc,             \
-                                                   (float *)dcopy, (float *)dx_out, part, M, rpb);               \
+                                                   (float *)dcopy, (float *)dx_out, M, rpb, dgamma, dbeta);                                                     \
     return cudaGetLastError();                                                                                   \
   }
   EVO_LN_BWD_VEC(1)
@@ -392,15 +391,15 @@ cudaError_t ln_bwd(const void *dy, const void *x, const float *gamma, float *dac
   const size_t sm = (size_t)8 * 2 * C * sizeof(float);
   if (use_bf16)
     ln_bwd_rows<bf16><<<nb, 256, sm, s>>>((const bf16 *)dy, (const bf16 *)x, gamma, dacc, (bf16 *)dcopy,
-                                          (bf16 *)dx_out, part, M, C, rpb);
+                                          (bf16 *)dx_out, M, C, rpb, dgamma, dbeta);
   else
     ln_bwd_rows<float><<<nb, 256, sm, s>>>((const float *)dy, (const float *)x, gamma, dacc, (float *)dcopy,
-                                           (float *)dx_out, part, M, C, rpb);
+                                           (float *)dx_out, M, C, rpb, dgamma, dbeta);
   return cudaGetLastError();
 }
 
-cudaError_t ln_bwd_cm(const void *dy, const void *x, int64_t pitch, const float *gamma, void *dx, float *part, int R,
-                      int C, int use_bf16, cudaStream_t s) {
+cudaError_t ln_bwd_cm(const void *dy, const void *x, int64_t pitch, const float *gamma, void *dx, int R,
+                      int C, int use_bf16, cudaStream_t s, float *dgamma, float *dbeta) {
   if (R <= 0) return cudaSuccess;
   Prof p("ln_bwd_cm", s, 0, (use_bf16 ? 6.0 : 12.0) * R * (double)R * C);
   dim3 grid((R + 31) / 32, R);
@@ -411,10 +410,11 @@ cudaError_t ln_bwd_cm(const void *dy, const void *x, int64_t pitch, const float 
     if (e != cudaSuccess) return e;
   }
   if (use_bf16)
-    ln_bwd_cm_k<bf16><<<grid, 256, sm, s>>>((const bf16 *)dy, (const bf16 *)x, pitch, gamma, (bf16 *)dx, part, R, C);
+    ln_bwd_cm_k<bf16><<<grid, 256, sm, s>>>((const bf16 *)dy, (const bf16 *)x, pitch, gamma, (bf16 *)dx, R, C,
+                                            dgamma, dbeta);
   else
-    ln_bwd_cm_k<float><<<grid, 256, sm, s>>>((const float *)dy, (const float *)x, pitch, gamma, (float *)dx, part, R,
-                                             C);
+    ln_bwd_cm_k<float><<<grid, 256, sm, s>>>((const float *)dy, (const float *)x, pitch, gamma, (float *)dx, R,
+                                             C, dgamma, dbeta);
   return cudaGetLastError();
 }
 

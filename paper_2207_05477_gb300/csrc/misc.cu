@@ -19,6 +19,24 @@ __device__ __forceinline__ void divmod(int64_t i, int d, int64_t &q, int &r) {
   }
 }
 
+__device__ __forceinline__ void ld8(const bf16 *p, float (&v)[8]) {
+  const uint4 w = *reinterpret_cast<const uint4 *>(p);
+  const __nv_bfloat162 *h = reinterpret_cast<const __nv_bfloat162 *>(&w);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const float2 f = __bfloat1622float2(h[k]);
+    v[2 * k] = f.x;
+    v[2 * k + 1] = f.y;
+  }
+}
+__device__ __forceinline__ void st8(bf16 *p, const float (&v)[8]) {
+  uint4 w;
+  __nv_bfloat162 *h = reinterpret_cast<__nv_bfloat162 *>(&w);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) h[k] = __floats2bfloat162_rn(v[2 * k], v[2 * k + 1]);
+  *reinterpret_cast<uint4 *>(p) = w;
+}
+
 // ------------------------------------------------------------- reductions
 // 32 columns per block; the 8 warps split the partial rows, then combine.
 __global__ void __launch_bounds__(256) reduce_partials_k(const float *part, int nblk, int64_t ld, int N, float *out) {
@@ -41,8 +59,8 @@ __global__ void __launch_bounds__(256) reduce_partials_k(const float *part, int 
 // Column sums: block (64 columns, a range of rows); each lane owns two
 // adjacent columns, the 8 warps split the rows, then combine.
 template <typename T>
-__global__ void __launch_bounds__(256) colsum_k(const T *x, int64_t ld, int64_t M, int N, float *part,
-                                                int64_t rows_per_blk) {
+__global__ void __launch_bounds__(256) colsum_k(const T *x, int64_t ld, int64_t M, int N,
+                                                int64_t rows_per_blk, float *out) {
   __shared__ float s[8][64];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int n = blockIdx.x * 64 + 2 * lane;
@@ -61,7 +79,7 @@ __global__ void __launch_bounds__(256) colsum_k(const T *x, int64_t ld, int64_t 
     float tot = 0.f;
 #pragma unroll
     for (int k = 0; k < 8; ++k) tot += s[k][threadIdx.x];
-    if (nn < N) part[(int64_t)blockIdx.y * N + nn] = tot;
+    if (nn < N) atomicAdd(out + nn, tot);
   }
 }
 
@@ -103,8 +121,8 @@ __global__ void head_proj_fwd_k(const T *x, const float *w, float *out, int R, i
 
 template <typename T>
 __global__ void __launch_bounds__(256) head_proj_bwd_k(const float *dbias, const T *x, const float *w, T *dx,
-                                                       int accumulate, float *part, int R, int C, int H, int transpose,
-                                                       int64_t pos_per_blk) {
+                                                       int accumulate, int R, int C, int H, int transpose,
+                                                       int64_t pos_per_blk, float *dw) {
   extern __shared__ float acc[];  // [8 warps][H*C]
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   float *mine = acc + warp * H * C;
@@ -138,7 +156,106 @@ __global__ void __launch_bounds__(256) head_proj_bwd_k(const float *dbias, const
   for (int k = threadIdx.x; k < H * C; k += blockDim.x) {
     float t = 0.f;
     for (int ww = 0; ww < 8; ++ww) t += acc[ww * H * C + k];
-    part[(int64_t)blockIdx.x * H * C + k] = t;
+    atomicAdd(dw + k, t);
+  }
+}
+
+
+// Pair-bias projection, BF16 fast path: one thread per position, the
+// position's C channels read as 16-byte vectors, w staged in shared memory.
+template <int H>
+__global__ void __launch_bounds__(128) head_proj_fwd_v8(const bf16 *x, const float *w, float *out, int R, int C,
+                                                        int transpose) {
+  extern __shared__ float ws[];  // [H][C]
+  for (int k = threadIdx.x; k < H * C; k += blockDim.x) ws[k] = w[k];
+  __syncthreads();
+  const int64_t P = (int64_t)R * R;
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= P) return;
+  float acc[H];
+#pragma unroll
+  for (int h = 0; h < H; ++h) acc[h] = 0.f;
+  const bf16 *row = x + p * C;
+  for (int c0 = 0; c0 < C; c0 += 8) {
+    float v[8];
+    ld8(row + c0, v);
+#pragma unroll
+    for (int h = 0; h < H; ++h)
+#pragma unroll
+      for (int k = 0; k < 8; ++k) acc[h] = fmaf(v[k], ws[h * C + c0 + k], acc[h]);
+  }
+  int64_t i;
+  int j;
+  divmod(p, R, i, j);
+  const int64_t pp = transpose ? (int64_t)j * R + i : p;
+#pragma unroll
+  for (int h = 0; h < H; ++h) out[h * P + pp] = acc[h];
+}
+
+// Backward, BF16 fast path: warp per position, lane owns channel pairs
+// 64j + 2*lane (+1); the weight gradient accumulates in registers.
+template <int H, int PJ>
+__global__ void __launch_bounds__(256) head_proj_bwd_v8(const float *dbias, const bf16 *x, const float *w, bf16 *dx,
+                                                        int accumulate, int R, int transpose,
+                                                        int64_t pos_per_blk, float *dw) {
+  constexpr int C = 64 * PJ;
+  __shared__ float red[8][H * C];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  float acc[H][2 * PJ];
+  float wl[H][2 * PJ];
+#pragma unroll
+  for (int h = 0; h < H; ++h)
+#pragma unroll
+    for (int j = 0; j < PJ; ++j) {
+      acc[h][2 * j] = acc[h][2 * j + 1] = 0.f;
+      wl[h][2 * j] = w[h * C + 64 * j + 2 * lane];
+      wl[h][2 * j + 1] = w[h * C + 64 * j + 2 * lane + 1];
+    }
+  const int64_t P = (int64_t)R * R;
+  const int64_t p0 = (int64_t)blockIdx.x * pos_per_blk;
+  const int64_t p1 = min(P, p0 + pos_per_blk);
+  for (int64_t p = p0 + warp; p < p1; p += 8) {
+    int64_t i;
+    int jj;
+    divmod(p, R, i, jj);
+    const int64_t pp = transpose ? (int64_t)jj * R + i : p;
+    float g[H];
+#pragma unroll
+    for (int h = 0; h < H; ++h) g[h] = dbias[h * P + pp];
+#pragma unroll
+    for (int j = 0; j < PJ; ++j) {
+      const int c = 64 * j + 2 * lane;
+      const float2 xv = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(x + p * C + c));
+      float d0 = 0.f, d1 = 0.f;
+#pragma unroll
+      for (int h = 0; h < H; ++h) {
+        d0 = fmaf(g[h], wl[h][2 * j], d0);
+        d1 = fmaf(g[h], wl[h][2 * j + 1], d1);
+        acc[h][2 * j] = fmaf(g[h], xv.x, acc[h][2 * j]);
+        acc[h][2 * j + 1] = fmaf(g[h], xv.y, acc[h][2 * j + 1]);
+      }
+      __nv_bfloat162 *dp = reinterpret_cast<__nv_bfloat162 *>(dx + p * C + c);
+      if (accumulate) {
+        const float2 old = __bfloat1622float2(*dp);
+        d0 += old.x;
+        d1 += old.y;
+      }
+      *dp = __floats2bfloat162_rn(d0, d1);
+    }
+  }
+#pragma unroll
+  for (int h = 0; h < H; ++h)
+#pragma unroll
+    for (int j = 0; j < PJ; ++j) {
+      red[warp][h * C + 64 * j + 2 * lane] = acc[h][2 * j];
+      red[warp][h * C + 64 * j + 2 * lane + 1] = acc[h][2 * j + 1];
+    }
+  __syncthreads();
+  for (int k = threadIdx.x; k < H * C; k += blockDim.x) {
+    float t = 0.f;
+#pragma unroll
+    for (int ww = 0; ww < 8; ++ww) t += red[ww][k];
+    atomicAdd(dw + k, t);
   }
 }
 
@@ -215,6 +332,121 @@ __global__ void __launch_bounds__(256) trimul_gate_bwd_k(const T *dA, const T *d
       stf(drow + 2 * cm + c, db * sb);
       stf(drow + 3 * cm + c, db * bp * sb * (1.f - sb));
     }
+  }
+}
+
+
+// BF16 fast path of the gating relayout: a block owns 32 x 32 positions and
+// 8 channels; each position's 8 channels of a_proj, a_gate, b_proj, b_gate
+// arrive as four 16-byte loads; the sigmoid of the g columns is folded in
+// (block z handles g columns z*8.., z*8 + 8).
+__global__ void __launch_bounds__(256) trimul_gate_fwd_v8(bf16 *abg, int64_t ld, const float *mask, bf16 *A, bf16 *B,
+                                                          int64_t pitch, int R, int cm, int cz, int incoming) {
+  __shared__ bf16 as[8][32][34], bs[8][32][34];
+  const int q0 = blockIdx.x * 32, r0 = blockIdx.y * 32, c0 = blockIdx.z * 8;
+  for (int idx = threadIdx.x; idx < 32 * 32; idx += blockDim.x) {
+    const int ocl = idx & 31, orl = idx >> 5;
+    const int orow = r0 + orl, ocol = q0 + ocl;
+    float av[8] = {}, bv[8] = {};
+    if (orow < R && ocol < R) {
+      const int64_t p = incoming ? (int64_t)ocol * R + orow : (int64_t)orow * R + ocol;
+      bf16 *row = abg + p * ld;
+      const float mk = mask[p];
+      float ap[8], ag[8], bp[8], bg[8];
+      ld8(row + c0, ap);
+      ld8(row + cm + c0, ag);
+      ld8(row + 2 * cm + c0, bp);
+      ld8(row + 3 * cm + c0, bg);
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        av[k] = mk * __fdividef(ap[k], 1.f + __expf(-ag[k]));
+        bv[k] = mk * __fdividef(bp[k], 1.f + __expf(-bg[k]));
+      }
+      for (int gc = c0; gc < cz; gc += gridDim.z * 8) {  // sigmoid of this block's share of the g columns
+        float g[8];
+        ld8(row + 4 * cm + gc, g);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) g[k] = __fdividef(1.f, 1.f + __expf(-g[k]));
+        st8(row + 4 * cm + gc, g);
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      as[k][orl][ocl] = __float2bfloat16_rn(av[k]);
+      bs[k][orl][ocl] = __float2bfloat16_rn(bv[k]);
+    }
+  }
+  __syncthreads();
+  const int64_t plane = (int64_t)R * pitch;
+  for (int idx = threadIdx.x; idx < 8 * 32 * 16; idx += blockDim.x) {  // pairs of columns
+    const int oc2 = (idx & 15) * 2, orl = (idx >> 4) & 31, k = idx >> 9;
+    const int orow = r0 + orl, ocol = q0 + oc2, c = c0 + k;
+    if (orow >= R || c >= cm) continue;
+    const int64_t o = (int64_t)c * plane + (int64_t)orow * pitch + ocol;
+    if (ocol + 1 < R && (o & 1) == 0) {
+      __nv_bfloat162 a2, b2;
+      a2.x = as[k][orl][oc2], a2.y = as[k][orl][oc2 + 1];
+      b2.x = bs[k][orl][oc2], b2.y = bs[k][orl][oc2 + 1];
+      *reinterpret_cast<__nv_bfloat162 *>(A + o) = a2;
+      *reinterpret_cast<__nv_bfloat162 *>(B + o) = b2;
+    } else {
+      if (ocol < R) {
+        A[o] = as[k][orl][oc2];
+        B[o] = bs[k][orl][oc2];
+      }
+      if (ocol + 1 < R) {
+        A[o + 1] = as[k][orl][oc2 + 1];
+        B[o + 1] = bs[k][orl][oc2 + 1];
+      }
+    }
+  }
+}
+
+__global__ void __launch_bounds__(256) trimul_gate_bwd_v8(const bf16 *dA, const bf16 *dB, int64_t pitch,
+                                                          const bf16 *abg, int64_t ld, const float *mask, bf16 *dabg,
+                                                          int R, int cm, int incoming) {
+  __shared__ bf16 as[8][32][34], bs[8][32][34];
+  const int q0 = blockIdx.x * 32, r0 = blockIdx.y * 32, c0 = blockIdx.z * 8;
+  const int64_t plane = (int64_t)R * pitch;
+  for (int idx = threadIdx.x; idx < 8 * 32 * 32; idx += blockDim.x) {
+    const int ocl = idx & 31, orl = (idx >> 5) & 31, k = idx >> 10;
+    const int orow = r0 + orl, ocol = q0 + ocl, c = c0 + k;
+    bf16 av = __float2bfloat16_rn(0.f), bv = av;
+    if (orow < R && ocol < R && c < cm) {
+      const int64_t o = (int64_t)c * plane + (int64_t)orow * pitch + ocol;
+      av = dA[o];
+      bv = dB[o];
+    }
+    as[k][orl][ocl] = av;
+    bs[k][orl][ocl] = bv;
+  }
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < 32 * 32; idx += blockDim.x) {
+    const int ocl = idx & 31, orl = idx >> 5;
+    const int orow = r0 + orl, ocol = q0 + ocl;
+    if (orow >= R || ocol >= R) continue;
+    const int64_t p = incoming ? (int64_t)ocol * R + orow : (int64_t)orow * R + ocol;
+    const bf16 *row = abg + p * ld;
+    bf16 *drow = dabg + p * ld;
+    const float mk = mask[p];
+    float ap[8], ag[8], bp[8], bg[8], dap[8], dag[8], dbp[8], dbg[8];
+    ld8(row + c0, ap);
+    ld8(row + cm + c0, ag);
+    ld8(row + 2 * cm + c0, bp);
+    ld8(row + 3 * cm + c0, bg);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const float sa = __fdividef(1.f, 1.f + __expf(-ag[k])), sb = __fdividef(1.f, 1.f + __expf(-bg[k]));
+      const float da = __bfloat162float(as[k][orl][ocl]) * mk, db = __bfloat162float(bs[k][orl][ocl]) * mk;
+      dap[k] = da * sa;
+      dag[k] = da * ap[k] * sa * (1.f - sa);
+      dbp[k] = db * sb;
+      dbg[k] = db * bp[k] * sb * (1.f - sb);
+    }
+    st8(drow + c0, dap);
+    st8(drow + cm + c0, dag);
+    st8(drow + 2 * cm + c0, dbp);
+    st8(drow + 3 * cm + c0, dbg);
   }
 }
 
@@ -336,13 +568,13 @@ int colsum_blocks(int64_t M) {
   int64_t b = (M + 255) / 256;
   return (int)(b < 296 ? (b < 1 ? 1 : b) : 296);
 }
-cudaError_t colsum(const void *x, int64_t ld, int64_t M, int N, float *part, int use_bf16, cudaStream_t s) {
+cudaError_t colsum(const void *x, int64_t ld, int64_t M, int N, int use_bf16, cudaStream_t s, float *out) {
   Prof prof("colsum", s, 0, (use_bf16 ? 2.0 : 4.0) * M * (double)N, 1);
   const int nb = colsum_blocks(M);
   const int64_t rpb = (M + nb - 1) / nb;
   const dim3 grid((N + 63) / 64, nb);
-  if (use_bf16) colsum_k<bf16><<<grid, 256, 0, s>>>((const bf16 *)x, ld, M, N, part, rpb);
-  else colsum_k<float><<<grid, 256, 0, s>>>((const float *)x, ld, M, N, part, rpb);
+  if (use_bf16) colsum_k<bf16><<<grid, 256, 0, s>>>((const bf16 *)x, ld, M, N, rpb, out);
+  else colsum_k<float><<<grid, 256, 0, s>>>((const float *)x, ld, M, N, rpb, out);
   return cudaGetLastError();
 }
 
@@ -357,7 +589,11 @@ cudaError_t head_proj_fwd(const void *x, const float *w, float *out, int R, int 
   Prof prof("head_proj_fwd", s, 2.0 * R * (double)R * C * H, (use_bf16 ? 2.0 : 4.0) * R * (double)R * C + 4.0 * H * R * (double)R, 1);
   if (H > 8) return cudaErrorInvalidValue;
   const int64_t P = (int64_t)R * R;
-  if (use_bf16) head_proj_fwd_k<bf16><<<nblk(P, 8), 256, 0, s>>>((const bf16 *)x, w, out, R, C, H, transpose);
+  if (use_bf16 && C % 8 == 0 && (((uintptr_t)x) & 15u) == 0 && (H == 4 || H == 8)) {
+    const size_t sm = (size_t)H * C * sizeof(float);
+    if (H == 4) head_proj_fwd_v8<4><<<nblk(P, 128), 128, sm, s>>>((const bf16 *)x, w, out, R, C, transpose);
+    else head_proj_fwd_v8<8><<<nblk(P, 128), 128, sm, s>>>((const bf16 *)x, w, out, R, C, transpose);
+  } else if (use_bf16) head_proj_fwd_k<bf16><<<nblk(P, 8), 256, 0, s>>>((const bf16 *)x, w, out, R, C, H, transpose);
   else head_proj_fwd_k<float><<<nblk(P, 8), 256, 0, s>>>((const float *)x, w, out, R, C, H, transpose);
   return cudaGetLastError();
 }
@@ -366,29 +602,39 @@ int head_proj_blocks(int R) {
   int64_t b = ((int64_t)R * R + 63) / 64;
   return (int)(b < 296 ? (b < 1 ? 1 : b) : 296);
 }
-cudaError_t head_proj_bwd(const float *dbias, const void *x, const float *w, void *dx, int accumulate, float *part,
-                          int R, int C, int H, int transpose, int use_bf16, cudaStream_t s) {
+cudaError_t head_proj_bwd(const float *dbias, const void *x, const float *w, void *dx, int accumulate, int R, int C, int H, int transpose, int use_bf16, cudaStream_t s, float *dw) {
   Prof prof("head_proj_bwd", s, 4.0 * R * (double)R * C * H, (use_bf16 ? 2.0 : 4.0) * R * (double)R * C * (accumulate ? 3 : 2) + 4.0 * H * R * (double)R, 1);
   if (H > 8) return cudaErrorInvalidValue;
   const int nb = head_proj_blocks(R);
   const int64_t ppb = ((int64_t)R * R + nb - 1) / nb;
   const size_t sm = (size_t)8 * H * C * sizeof(float);
   if (sm > 48 * 1024) return cudaErrorInvalidValue;
-  if (use_bf16)
-    head_proj_bwd_k<bf16><<<nb, 256, sm, s>>>(dbias, (const bf16 *)x, w, (bf16 *)dx, accumulate, part, R, C, H,
-                                              transpose, ppb);
+  if (use_bf16 && C == 128 && (H == 4 || H == 8) && (((uintptr_t)x) & 3u) == 0 && (((uintptr_t)dx) & 3u) == 0) {
+    if (H == 4)
+      head_proj_bwd_v8<4, 2><<<nb, 256, 0, s>>>(dbias, (const bf16 *)x, w, (bf16 *)dx, accumulate, R, transpose,
+                                                ppb, dw);
+    else
+      head_proj_bwd_v8<8, 2><<<nb, 256, 0, s>>>(dbias, (const bf16 *)x, w, (bf16 *)dx, accumulate, R, transpose,
+                                                ppb, dw);
+  } else if (use_bf16)
+    head_proj_bwd_k<bf16><<<nb, 256, sm, s>>>(dbias, (const bf16 *)x, w, (bf16 *)dx, accumulate, R, C, H,
+                                              transpose, ppb, dw);
   else
-    head_proj_bwd_k<float><<<nb, 256, sm, s>>>(dbias, (const float *)x, w, (float *)dx, accumulate, part, R, C, H,
-                                               transpose, ppb);
+    head_proj_bwd_k<float><<<nb, 256, sm, s>>>(dbias, (const float *)x, w, (float *)dx, accumulate, R, C, H,
+                                               transpose, ppb, dw);
   return cudaGetLastError();
 }
 
 cudaError_t trimul_gate_fwd(void *abg, int64_t ld, const float *mask, void *A, void *B, int64_t pitch, int R, int cm,
                             int cz, int incoming, int use_bf16, cudaStream_t s) {
-  Prof prof("trimul_gate_fwd", s, 0, (use_bf16 ? 2.0 : 4.0) * R * (double)R * (6.0 * cm + 2.0 * cz), 2);
+  Prof prof("trimul_gate_fwd", s, 0, (use_bf16 ? 2.0 : 4.0) * R * (double)R * (6.0 * cm + 2.0 * cz), use_bf16 ? 1 : 2);
   dim3 grid((R + 31) / 32, (R + 31) / 32, (cm + 3) / 4);
   const int64_t P = (int64_t)R * R;
-  if (use_bf16) {
+  const bool v8 = cm % 8 == 0 && cz % 8 == 0 && ld % 8 == 0 && (((uintptr_t)abg) & 15u) == 0;
+  if (use_bf16 && v8) {
+    dim3 g8((R + 31) / 32, (R + 31) / 32, cm / 8);
+    trimul_gate_fwd_v8<<<g8, 256, 0, s>>>((bf16 *)abg, ld, mask, (bf16 *)A, (bf16 *)B, pitch, R, cm, cz, incoming);
+  } else if (use_bf16) {
     trimul_gate_fwd_k<bf16><<<grid, 256, 0, s>>>((const bf16 *)abg, ld, mask, (bf16 *)A, (bf16 *)B, pitch, R, cm,
                                                  incoming);
     sigmoid_cols_k<bf16><<<nblk(P * cz), 256, 0, s>>>((bf16 *)abg, ld, 4 * cm, cz, P);
@@ -404,7 +650,12 @@ cudaError_t trimul_gate_bwd(const void *dA, const void *dB, int64_t pitch, const
                             const float *mask, void *dabg, int R, int cm, int incoming, int use_bf16, cudaStream_t s) {
   Prof prof("trimul_gate_bwd", s, 0, (use_bf16 ? 2.0 : 4.0) * R * (double)R * 10.0 * cm, 1);
   dim3 grid((R + 31) / 32, (R + 31) / 32, (cm + 3) / 4);
-  if (use_bf16)
+  const bool v8 = cm % 8 == 0 && ld % 8 == 0 && (((uintptr_t)abg) & 15u) == 0 && (((uintptr_t)dabg) & 15u) == 0;
+  if (use_bf16 && v8) {
+    dim3 g8((R + 31) / 32, (R + 31) / 32, cm / 8);
+    trimul_gate_bwd_v8<<<g8, 256, 0, s>>>((const bf16 *)dA, (const bf16 *)dB, pitch, (const bf16 *)abg, ld, mask,
+                                          (bf16 *)dabg, R, cm, incoming);
+  } else if (use_bf16)
     trimul_gate_bwd_k<bf16><<<grid, 256, 0, s>>>((const bf16 *)dA, (const bf16 *)dB, pitch, (const bf16 *)abg, ld,
                                                  mask, (bf16 *)dabg, R, cm, incoming);
   else

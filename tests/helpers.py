@@ -42,6 +42,33 @@ def oracle_fwd(d, seed=32, pad_frac=0.0, trailing=False):
     return O.block_forward(prob["m"], prob["z"], prob["msa_mask"], prob["pair_mask"], p, d)
 
 
+def _to_bf16_grid(x):
+    """x rounded to the nearest BF16 value (round-to-nearest-even), back in fp64."""
+    return torch.as_tensor(np.asarray(x)).float().bfloat16().double().numpy()
+
+
+@functools.lru_cache(maxsize=3)
+def oracle_bf16_floor(d, seed=32, pad_frac=0.0, trailing=False):
+    """Relative L2 change of each oracle output when only the block's inputs
+    (m, z, every parameter and the cotangents gm, gz) are rounded to BF16 and
+    everything else stays FP64.  A BF16 path must round these inputs, so no
+    BF16 result can be expected closer to the FP64 oracle than this floor.
+    Returns {"dm": .., "dz": .., <parameter name>: ..}."""
+    prob = problem(d, seed, pad_frac, trailing)
+    p = synth.unpack_params(d, _to_bf16_grid(prob["params"]))
+    _, _, dm, dz, dp = O.block_forward_backward(_to_bf16_grid(prob["m"]), _to_bf16_grid(prob["z"]), prob["msa_mask"],
+                                                prob["pair_mask"], p, d, _to_bf16_grid(prob["gm"]),
+                                                _to_bf16_grid(prob["gz"]))
+    ref = oracle_fwd_bwd(d, seed, pad_frac, trailing)
+    lay, _ = synth.param_layout(d)
+    packed = np.zeros(max(o + int(np.prod(s)) for _, o, s, _ in lay))
+    for name, off, shape, _ in lay:
+        packed[off:off + int(np.prod(shape))] = dp[name].detach().numpy().ravel()
+    errs = {"dm": rel_l2(dm, ref[2]), "dz": rel_l2(dz, ref[3])}
+    errs.update(param_grad_errors(d, packed, ref[4]))
+    return errs
+
+
 def gpu_run(d, act_dtype, seed=32, pad_frac=0.0, trailing=False, backward=True):
     """Block forward (and backward) through the C ABI on cuda:0; results on the CPU in fp64."""
     prob = problem(d, seed, pad_frac, trailing)

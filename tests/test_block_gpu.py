@@ -12,10 +12,19 @@ where those cannot hold, from the arithmetic:
     gradient passes through that ReLU mask (LayerNorm gamma/beta, w1, b1):
     BF16 forward error ~4e-3 puts ~0.3% of pre-activations on the other side
     of zero, an expected relative error of ~sqrt(0.3%) = 5.5%; bound 1e-1.
+  * Small BF16 problems (a few MSA rows): every tensor upstream of a
+    transition inherits part of that ReLU-flip noise, with too few positions
+    to average it out.  There the bound of each tensor is also at least twice
+    the oracle's own BF16 floor: the change of that tensor when the oracle's
+    inputs alone are rounded to BF16 (``oracle_bf16_floor``).  The kernels
+    round the activations again at every stored intermediate (about 16
+    roundings of the same size between the block input and a ReLU);
+    independent roundings add in quadrature (amplitude x4) and the flip error
+    grows as the square root of the amplitude: x2.
 """
 import pytest
 
-from helpers import gpu_run, oracle_fwd, oracle_fwd_bwd, param_grad_errors, rel_l2
+from helpers import gpu_run, oracle_bf16_floor, oracle_fwd, oracle_fwd_bwd, param_grad_errors, rel_l2
 from paper_2207_05477_gb300 import evo, synth
 
 pytestmark = pytest.mark.gpu
@@ -25,12 +34,13 @@ FP32_GRAD_TOL = 1e-3
 BF16_TOL = 2e-2
 BF16_GRAD_TOL = 5e-2
 RELU_MASKED_TOL = 1e-1
+BF16_FLOOR_FACTOR = 2.0
 RELU_MASKED = {p + "." + t for p in ("msa_trans", "pair_trans") for t in ("ln.gamma", "ln.beta", "w1", "b1")}
 
 RAGGED = synth.Dims(n_seq=5, n_res=37)  # ragged against every 64/128-wide tile
 
 
-def _check(out, ref, tol, gtol, d, relu_tol=None):
+def _check(out, ref, tol, gtol, d, relu_tol=None, floor=None):
     mo, zo, dm, dz, dp = ref
     errs = {"m": rel_l2(out["m"], mo), "z": rel_l2(out["z"], zo)}
     assert errs["m"] <= tol and errs["z"] <= tol, errs
@@ -38,6 +48,8 @@ def _check(out, ref, tol, gtol, d, relu_tol=None):
         g = {"dm": rel_l2(out["dm"], dm), "dz": rel_l2(out["dz"], dz)}
         g.update(param_grad_errors(d, out["dparams"], dp))
         lim = {k: (relu_tol if relu_tol is not None and k in RELU_MASKED else gtol) for k in g}
+        if floor is not None:
+            lim = {k: max(v, BF16_FLOOR_FACTOR * floor[k]) for k, v in lim.items()}
         bad = {k: v for k, v in g.items() if not v <= lim[k]}
         assert not bad, bad
 
@@ -57,7 +69,8 @@ def test_fp32_fwd_bwd_ragged_padded(built_lib):
 
 def test_bf16_fwd_bwd_ragged_padded(built_lib):
     out = gpu_run(RAGGED, evo.EVO_BF16, pad_frac=0.1)
-    _check(out, oracle_fwd_bwd(RAGGED, pad_frac=0.1), BF16_TOL, BF16_GRAD_TOL, RAGGED, RELU_MASKED_TOL)
+    _check(out, oracle_fwd_bwd(RAGGED, pad_frac=0.1), BF16_TOL, BF16_GRAD_TOL, RAGGED, RELU_MASKED_TOL,
+           oracle_bf16_floor(RAGGED, pad_frac=0.1))
 
 
 def test_bf16_forward_small_config(built_lib):
