@@ -166,7 +166,13 @@ int evo_debug_wait_timeout(long long limit_ns, evo_stream_t stream);
  * around every kernel launch of the library (on the launch stream), with the
  * launch's algorithmic flops and DRAM bytes; evo_profile_end waits for the
  * stream, stops recording and aggregates by kernel name into out (up to cap
- * entries), returning the number of distinct names. */
+ * entries), returning the number of distinct names.  evo_profile_only
+ * (called before evo_profile_begin) restricts the next recording to the
+ * launches of one kernel name, so that timing a single kernel class adds one
+ * event pair per launch of that class and nothing elsewhere; NULL or "" means
+ * every kernel.  With EVO_PROFILE_DETAIL=1 in the environment at
+ * evo_profile_begin, GEMM entries are named by shape and tile
+ * ("g<M>x<N>x<K>*<batch>s<splits>n<BN>..."). */
 typedef struct evo_profile_entry {
   char name[32];
   int32_t calls;     /* launch sites that ran                           */
@@ -175,6 +181,7 @@ typedef struct evo_profile_entry {
   double flops;      /* algorithmic flops of those launches             */
   double bytes;      /* algorithmic DRAM bytes (inputs read + outputs)  */
 } evo_profile_entry;
+int evo_profile_only(const char *kernel_name);
 int evo_profile_begin(void);
 int evo_profile_end(evo_stream_t stream, evo_profile_entry *out, int cap);
 

@@ -129,6 +129,7 @@ struct Plan {
   AttBufs att[2];
   size_t xz9, h9, z6;
   size_t dm_acc, dmT, dz_acc, dzT, G1, G2, G3, dO4, dA, dB, dX, dq_acc, dbias, Dsum, dab4, split;
+  int64_t wmax = 0;  // split holds MAXSPLIT * wmax floats
   size_t total;
 };
 
@@ -195,6 +196,7 @@ size_t make_plan(const evo_dims &d, int mode, Plan &p) {
                              4 * k.HCt * k.Cz, k.Cz * k.co * k.co, k.Cm * k.HCm, 2 * k.co * k.Cm,
                              k.Cz * k.cmul, k.Cz * k.HCt});
     p.split = F(MAXSPLIT * wmax);
+    p.wmax = wmax;
   }
   p.total = off;
   return off;
@@ -250,7 +252,32 @@ struct Drv {
   void gemm(GemmOp g) {
     g.e.M = g.M;
     g.e.N = g.N;
+    if (bf && splitk_wanted(g)) {
+      // too few output tiles to fill the GPU and a long K: fp32 partial sums
+      // per K range, then one reduction writes the bf16 output through the map
+      const int64_t tiles = ((g.M + 127) / 128) * ((g.N + 255) / 256);
+      int64_t sp = std::min<int64_t>((152 + tiles - 1) / tiles, g.K / 1024);
+      sp = std::min<int64_t>(sp, (int64_t)MAXSPLIT * pl.wmax / ((int64_t)g.M * g.N));
+      if (sp >= 2) {
+        const OutMap map = g.e.map;
+        void *out = g.e.C;
+        g.splits = (int)sp;
+        g.e.partial = Bf(pl.split);
+        g.e.C = nullptr;
+        ck(gemm_tc_bf16(g, s));
+        ck(reduce_splits_map(Bf(pl.split), (int)sp, g.M, g.N, map, out, s));
+        return;
+      }
+    }
     ck(bf ? gemm_tc_bf16(g, s) : gemm_simt_f32(g, s));
+  }
+  // A plain product (no epilogue but the output map) whose tiles cannot fill the GPU.
+  static bool splitk_wanted(const GemmOp &g) {
+    const Epi &e = g.e;
+    const int64_t tiles = ((g.M + 127) / 128) * ((g.N + 255) / 256) * g.batch;
+    return g.batch == 1 && g.splits == 1 && !e.partial && tiles * 2 <= 152 && g.K >= 2048 && g.N % 2 == 0 &&
+           e.alpha == 1.f && !e.bias && !e.row_scale && !e.relu_ref && e.act == ACT_NONE && !e.aux && !e.gate &&
+           !e.residual && !e.c_f32 && !e.accumulate;
   }
   void ln(const void *x, const std::string &pre, void *y, int64_t M, int C) {
     ck(ln_fwd(x, P(pre + ".gamma"), P(pre + ".beta"), y, M, C, bf, s));

@@ -1,14 +1,19 @@
 // BF16 GEMM on the 5th-generation tensor cores (sm_103a): TMA loads 128x64 /
 // BNx64 operand tiles (128-byte swizzle) into a STAGES-deep shared-memory ring,
 // one elected thread issues tcgen05.mma (M=128, N=BN, K=16) accumulating FP32
-// in tensor memory, and the four warps drain TMEM with tcgen05.ld through the
-// shared epilogue (bias, scales, gates, residual, layout-changing stores).
+// in tensor memory, and sixteen epilogue warps drain TMEM with tcgen05.ld
+// through the shared epilogue (bias, scales, gates, residual, layout-changing
+// stores).
 //
 // The kernel is persistent (one CTA per SM) and warp-specialised: lane 0 of
 // warp 0 streams A/B k-tiles with TMA through a STAGES-deep ring, running
 // ahead across output tiles; lane 0 of warp 1 issues the MMAs into one of two
-// TMEM accumulators; warps 2-5 drain the other accumulator through the
+// TMEM accumulators; warps 2-17 drain the other accumulator through the
 // epilogue, so a tile's epilogue overlaps the next tile's loads and MMAs.
+// The epilogue is latency-bound (few instructions per byte, each waiting on
+// TMEM or global loads), hence four warps per TMEM lane quarter, each on
+// 32-column chunks, with the row operands of a chunk (gate, residual, ReLU
+// reference) requested before the accumulator wait.
 //
 // Operands may be K-major or MN-major (the transpose bits of the instruction
 // descriptor); backward GEMMs (dX = dY W, dW = dY^T X) use MN-major views of
@@ -150,6 +155,18 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
 __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
@@ -162,10 +179,11 @@ struct TcCfg {
   static constexpr int A_BYTES = BM * BK * 2;
   static constexpr int B_BYTES = BN * BK * 2;
   static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
-  static constexpr int CH = BN < 64 ? BN : 64;  // epilogue column chunk
-  static constexpr int LDS = CH + 1;            // staged row pitch (floats)
-  static constexpr int EPI_WARP_BYTES = 9216;  // two 1 KB-aligned 4 KB TMA buffers, or 32 x LDS floats
-  static constexpr int EPI_WARPS = 8;  // two per TMEM lane quarter, splitting the 64-column chunks
+  static constexpr int CH = 32;   // epilogue column chunk (one warp-iteration)
+  static constexpr int LDS = CH + 1;  // staged row pitch of the general path (floats)
+  // per epilogue warp: two 2 KB TMA-store buffers (1 KB aligned), or 32 x LDS floats
+  static constexpr int EPI_WARP_BYTES = 5120;
+  static constexpr int EPI_WARPS = 16;  // four per TMEM lane quarter, 32-column slots at a 128-column stride
   static constexpr int EPI_BYTES = EPI_WARPS * EPI_WARP_BYTES;
   static_assert(32 * LDS * 4 <= EPI_WARP_BYTES, "epilogue staging");
   static constexpr int SMEM = STAGES * STAGE_BYTES + EPI_BYTES + 1024;
@@ -206,146 +224,51 @@ __device__ __forceinline__ TileCoord decode_tile(const GemmOp &g, int t, int bn)
   return c;
 }
 
-// Stores one staged 32-row x CH-column chunk (rows mrow0.., columns n..)
-// through the epilogue chain; lane owns columns n, n+1.
-__device__ __forceinline__ void epi_chunk(const GemmOp &g, const float *mine, int lane, int mrow0, int nbase, int ch,
-                                          int b, int split, int64_t my_rowoff, bool rows_even) {
-  constexpr int LDS_ = 65;
+// General epilogue of one staged 32-row x 32-column chunk (rows mrow0..,
+// columns nbase..): lane = column, rows in turn (split-K partials are plain
+// coalesced fp32 rows; everything else goes through epi_store).
+__device__ __forceinline__ void epi_chunk(const GemmOp &g, const float *mine, int lane, int mrow0, int nbase, int b,
+                                          int split) {
   const Epi &e = g.e;
-  const int cc = 2 * lane;
-  const int n = nbase + cc;
-  const bool ok0 = cc < ch && n < g.N, ok1 = ok0 && n + 1 < g.N;
-  const int ld = ch + 1;
-  (void)LDS_;
-  if (e.partial) {
-    for (int rr = 0; rr < 32; ++rr) {
-      const int m = mrow0 + rr;
-      if (m >= g.M) break;
-      if (!ok0) continue;
-      float *p = e.partial + ((int64_t)split * e.M + m) * e.N + n;
-      const float a0 = mine[rr * ld + cc], a1 = mine[rr * ld + cc + 1];
-      if (ok1 && ((e.N & 1) == 0)) {
-        *reinterpret_cast<float2 *>(p) = make_float2(a0, a1);
-      } else {
-        p[0] = a0;
-        if (ok1) p[1] = a1;
-      }
-    }
-    return;
-  }
-  const int64_t col0 = ok0 ? e.map.col(n) : 0, col1 = ok1 ? e.map.col(n + 1) : 0;
-  const bool vec = ok1 && rows_even && col1 == col0 + 1 && (col0 & 1) == 0;
-  const float b0 = (e.bias && ok0 && n >= e.bias_n0) ? e.bias[n - e.bias_n0] : 0.f;
-  const float b1 = (e.bias && ok1 && n + 1 >= e.bias_n0) ? e.bias[n + 1 - e.bias_n0] : 0.f;
-  const bool s0 = e.act == ACT_SIGMOID && n >= e.act_n0, s1 = e.act == ACT_SIGMOID && n + 1 >= e.act_n0;
-  const bool relu = e.act == ACT_RELU;
-  const bool pair_ref = ok1 && (e.relu_ld & 1) == 0, pair_aux = ok1 && (e.aux_ld & 1) == 0,
-             pair_gate = ok1 && (e.gate_ld & 1) == 0;
-  const bf16 *refp = (const bf16 *)e.relu_ref + n;
-  bf16 *auxp = (bf16 *)e.aux + n;
-  const bf16 *gatep = (const bf16 *)e.gate + n;
-  bf16 *cb = (bf16 *)e.C;
-  const bf16 *rb = (const bf16 *)e.residual;
+  const int n = nbase + lane;
+  if (n >= g.N) return;
   for (int rr = 0; rr < 32; ++rr) {
     const int m = mrow0 + rr;
     if (m >= g.M) break;
-    const int64_t rowoff = __shfl_sync(0xffffffffu, my_rowoff, rr);
-    if (!ok0) continue;
-    float v0 = mine[rr * ld + cc] * e.alpha + b0;
-    float v1 = mine[rr * ld + cc + 1] * e.alpha + b1;
-    if (e.row_scale) {
-      const float rs = e.row_scale[m];
-      v0 *= rs;
-      v1 *= rs;
-    }
-    if (e.relu_ref) {
-      const int64_t o = (int64_t)m * e.relu_ld;
-      float r0, r1 = 1.f;
-      if (pair_ref) {
-        const float2 rf = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(refp + o));
-        r0 = rf.x;
-        r1 = rf.y;
-      } else {
-        r0 = __bfloat162float(refp[o]);
-        if (ok1) r1 = __bfloat162float(refp[o + 1]);
-      }
-      if (!(r0 > 0.f)) v0 = 0.f;
-      if (!(r1 > 0.f)) v1 = 0.f;
-    }
-    if (relu) {
-      v0 = fmaxf(v0, 0.f);
-      v1 = fmaxf(v1, 0.f);
-    }
-    if (s0) v0 = __fdividef(1.f, 1.f + __expf(-v0));
-    if (s1) v1 = __fdividef(1.f, 1.f + __expf(-v1));
-    if (e.aux) {
-      const int64_t o = (int64_t)m * e.aux_ld;
-      if (pair_aux) {
-        *reinterpret_cast<__nv_bfloat162 *>(auxp + o) = __floats2bfloat162_rn(v0, v1);
-      } else {
-        auxp[o] = __float2bfloat16_rn(v0);
-        if (ok1) auxp[o + 1] = __float2bfloat16_rn(v1);
-      }
-    }
-    if (e.gate) {
-      const int64_t o = (int64_t)m * e.gate_ld;
-      if (pair_gate) {
-        const float2 gt = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(gatep + o));
-        v0 *= gt.x;
-        v1 *= gt.y;
-      } else {
-        v0 *= __bfloat162float(gatep[o]);
-        if (ok1) v1 *= __bfloat162float(gatep[o + 1]);
-      }
-    }
-    const int64_t o0 = rowoff + col0, o1 = rowoff + col1;
-    if (vec) {
-      if (rb) {
-        const float2 rv = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(rb + o0));
-        v0 += rv.x;
-        v1 += rv.y;
-      }
-      if (e.c_f32) {
-        float *cf = (float *)e.C;
-        if (e.accumulate) {
-          cf[o0] += v0;
-          cf[o1] += v1;
-        } else {
-          *reinterpret_cast<float2 *>(cf + o0) = make_float2(v0, v1);
-        }
-      } else {
-        *reinterpret_cast<__nv_bfloat162 *>(cb + o0) = __floats2bfloat162_rn(v0, v1);
-      }
+    const float acc = mine[rr * 33 + lane];
+    if (e.partial) e.partial[((int64_t)split * e.M + m) * e.N + n] = acc;
+    else epi_store<bf16>(e, b, split, m, n, acc);
+  }
+}
+
+// Four 16-byte vectors of row m, columns nb..nb+31 of a bf16 matrix (zero
+// past column N or row M).
+__device__ __forceinline__ void ld_row32(const void *base, int64_t ld, int m, bool mok, int nb, int N, uint4 (&o)[4]) {
+  const bf16 *p = (const bf16 *)base + (int64_t)m * ld + nb;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    if (mok && nb + j * 8 + 7 < N) {
+      o[j] = *reinterpret_cast<const uint4 *>(p + j * 8);
     } else {
-      if (rb) {
-        v0 += __bfloat162float(rb[o0]);
-        if (ok1) v1 += __bfloat162float(rb[o1]);
-      }
-      if (e.c_f32) {
-        float *cf = (float *)e.C;
-        if (e.accumulate) {
-          cf[o0] += v0;
-          if (ok1) cf[o1] += v1;
-        } else {
-          cf[o0] = v0;
-          if (ok1) cf[o1] = v1;
-        }
-      } else {
-        cb[o0] = __float2bfloat16_rn(v0);
-        if (ok1) cb[o1] = __float2bfloat16_rn(v1);
-      }
+      bf16 *h = reinterpret_cast<bf16 *>(&o[j]);
+#pragma unroll
+      for (int jj = 0; jj < 8; ++jj) h[jj] = (mok && nb + j * 8 + jj < N) ? p[j * 8 + jj] : __float2bfloat16_rn(0.f);
     }
   }
+}
+
+__device__ __forceinline__ float bf_at(const uint4 (&o)[4], int k) {
+  return __bfloat162float(reinterpret_cast<const bf16 *>(&o[k >> 3])[k & 7]);
 }
 
 // Persistent warp-specialised GEMM: grid = min(#tiles, #SMs), tiles taken
 // round-robin (N fastest, so CTAs working at the same time share A tiles in L2).
 // warp 0 lane 0: TMA producer (runs ahead through the stage ring across tiles)
 // warp 1 lane 0: MMA issuer (accumulator buffer alternates per tile)
-// warps 2-9: epilogue (warp w drains TMEM lane quarter w % 4; warps w and w+4
-//            take alternate 64-column chunks)
+// warps 2-17: epilogue (warp w drains TMEM lane quarter w % 4 and takes the
+//             32-column slot (w - 2) / 4 of every 128 columns)
 template <int BN, int STAGES, bool AMN, bool BMN>
-__global__ void __launch_bounds__(320, 1)
+__global__ void __launch_bounds__(576, 1)
     gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                    const __grid_constant__ CUtensorMap tmC, GemmOp g, int tma_store) {
   using C = TcCfg<BN, STAGES, AMN, BMN>;
@@ -464,14 +387,32 @@ __global__ void __launch_bounds__(320, 1)
     tc_commit(&done_bar);
   } else if (warp >= 2) {
     // ---------------- epilogue warps
-    const int quarter = warp & 3, half = (warp - 2) >> 2;
-    const uint32_t region = sbase + STAGES * C::STAGE_BYTES + (warp - 2) * C::EPI_WARP_BYTES;
+    // warp w drains TMEM lane quarter w % 4 (the lanes tcgen05.ld lets it
+    // reach); the four warps of a quarter take 32-column slots 0..3 of every
+    // 128 columns of the tile.
+    const int ew = warp - 2;
+    const int quarter = warp & 3, slot = ew >> 2;
+    const uint32_t region = sbase + STAGES * C::STAGE_BYTES + ew * C::EPI_WARP_BYTES;
     float *mine = reinterpret_cast<float *>(dsmem + (region - raw));
     uint32_t ai = 0, nstore = 0;
     const Epi &e = g.e;
+    // gate and relu_ref (never both present) share one operand register set
+    const void *opa = e.gate ? e.gate : e.relu_ref;
+    const int64_t opa_ld = e.gate ? e.gate_ld : e.relu_ld;
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
       const TileCoord tc = decode_tile(g, t, BN);
       const uint32_t ab = ai & 1u, u = ai >> 1;
+      const int mrow0 = tc.m0 + quarter * 32;
+      const int m = mrow0 + lane;
+      const bool mok = m < g.M;
+      const bool rows = mrow0 < g.M;  // warp-uniform: any row of this quarter in range
+      const bf16 *resid = e.residual ? (const bf16 *)e.residual + (int64_t)tc.b * e.c_bstride : nullptr;
+      // row operands of the first chunk are fetched while the accumulator fills
+      uint4 va[4], vr[4];
+      if (tma_store && rows && slot * 32 < BN && tc.n0 + slot * 32 < g.N) {
+        if (opa) ld_row32(opa, opa_ld, m, mok, tc.n0 + slot * 32, g.N, va);
+        if (resid) ld_row32(resid, e.map.s_m0, m, mok, tc.n0 + slot * 32, g.N, vr);
+      }
       bool have = false;
       if (tc.nk > 0) {
         have = mbar_wait(&accf_bar[ab], u & 1u, &s_abort);
@@ -479,150 +420,106 @@ __global__ void __launch_bounds__(320, 1)
         if (!have) break;
         tc_fence_after();
       }
-      const int mrow0 = tc.m0 + quarter * 32;
       if (tma_store) {
         // thread = row: TMEM -> registers -> epilogue -> bf16 -> swizzled shared -> TMA store
-        const int m = mrow0 + lane;
-        const bool mok = m < g.M;
-        const int64_t cbase = (int64_t)tc.b * e.c_bstride + (int64_t)m * e.map.s_m0;
         const float rs = (e.row_scale && mok) ? e.row_scale[m] : 1.f;
-        for (int c0 = half * 64; c0 < BN; c0 += 128) {
+        for (int c0 = slot * 32; rows && c0 < BN; c0 += 128) {
           const int nb = tc.n0 + c0;
           if (nb >= g.N) break;
-          float v[64];
+          if (c0 != slot * 32) {
+            if (opa) ld_row32(opa, opa_ld, m, mok, nb, g.N, va);
+            if (resid) ld_row32(resid, e.map.s_m0, m, mok, nb, g.N, vr);
+          }
+          float v[32];
           if (have) {
+            uint32_t r[32];
+            tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + ab * BN + (uint32_t)c0, r);
 #pragma unroll
-            for (int q = 0; q < 64; q += 16) {
-              uint32_t r[16];
-              tmem_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + ab * BN + (uint32_t)(c0 + q), r);
-#pragma unroll
-              for (int jj = 0; jj < 16; ++jj) v[q + jj] = __uint_as_float(r[jj]);
-            }
+            for (int jj = 0; jj < 32; ++jj) v[jj] = __uint_as_float(r[jj]) * e.alpha;
           } else {
 #pragma unroll
-            for (int jj = 0; jj < 64; ++jj) v[jj] = 0.f;
+            for (int jj = 0; jj < 32; ++jj) v[jj] = 0.f;
           }
+          if (e.bias) {
 #pragma unroll
-          for (int g8 = 0; g8 < 8; ++g8) {
-            const int n = nb + g8 * 8;
-            const bool full8 = n + 7 < g.N;
-            float bb[8];
-#pragma unroll
-            for (int jj = 0; jj < 8; ++jj) bb[jj] = 0.f;
-            if (e.bias) {
-              const int bi = n - e.bias_n0;
-              if (full8 && bi >= 0 && (bi & 3) == 0) {
-                const float4 x0 = *reinterpret_cast<const float4 *>(e.bias + bi);
-                const float4 x1 = *reinterpret_cast<const float4 *>(e.bias + bi + 4);
-                bb[0] = x0.x, bb[1] = x0.y, bb[2] = x0.z, bb[3] = x0.w;
-                bb[4] = x1.x, bb[5] = x1.y, bb[6] = x1.z, bb[7] = x1.w;
-              } else {
-#pragma unroll
-                for (int jj = 0; jj < 8; ++jj)
-                  if (n + jj < g.N && n + jj >= e.bias_n0) bb[jj] = e.bias[n + jj - e.bias_n0];
+            for (int q = 0; q < 8; ++q) {
+              const int n = nb + 4 * q;
+              if (n >= e.bias_n0) {  // bias_n0 % 4 == 0: a group is all biased or all not
+                if (n + 3 < g.N) {
+                  const float4 x = *reinterpret_cast<const float4 *>(e.bias + (n - e.bias_n0));
+                  v[4 * q] += x.x, v[4 * q + 1] += x.y, v[4 * q + 2] += x.z, v[4 * q + 3] += x.w;
+                } else {
+                  for (int jj = 0; jj < 4; ++jj)
+                    if (n + jj < g.N) v[4 * q + jj] += e.bias[n + jj - e.bias_n0];
+                }
               }
             }
-#pragma unroll
-            for (int jj = 0; jj < 8; ++jj) v[g8 * 8 + jj] = (v[g8 * 8 + jj] * e.alpha + bb[jj]) * rs;
           }
-          if (e.relu_ref && mok) {
-            const bf16 *p = (const bf16 *)e.relu_ref + (int64_t)m * e.relu_ld + nb;
+          if (e.row_scale) {
 #pragma unroll
-            for (int g8 = 0; g8 < 8; ++g8) {
-              if (nb + g8 * 8 + 7 < g.N) {
-                const uint4 w = *reinterpret_cast<const uint4 *>(p + g8 * 8);
-                const bf16 *h = reinterpret_cast<const bf16 *>(&w);
+            for (int jj = 0; jj < 32; ++jj) v[jj] *= rs;
+          }
+          if (e.relu_ref) {
 #pragma unroll
-                for (int jj = 0; jj < 8; ++jj)
-                  if (!(__bfloat162float(h[jj]) > 0.f)) v[g8 * 8 + jj] = 0.f;
-              } else {
-                for (int jj = 0; jj < 8; ++jj)
-                  if (nb + g8 * 8 + jj < g.N && !(__bfloat162float(p[g8 * 8 + jj]) > 0.f)) v[g8 * 8 + jj] = 0.f;
-              }
-            }
+            for (int jj = 0; jj < 32; ++jj)
+              if (!(bf_at(va, jj) > 0.f)) v[jj] = 0.f;
           }
           if (e.act == ACT_RELU) {
 #pragma unroll
-            for (int jj = 0; jj < 64; ++jj) v[jj] = fmaxf(v[jj], 0.f);
+            for (int jj = 0; jj < 32; ++jj) v[jj] = fmaxf(v[jj], 0.f);
           } else if (e.act == ACT_SIGMOID) {
 #pragma unroll
-            for (int jj = 0; jj < 64; ++jj)
+            for (int jj = 0; jj < 32; ++jj)
               if (nb + jj >= e.act_n0) v[jj] = __fdividef(1.f, 1.f + __expf(-v[jj]));
           }
           if (e.aux && mok) {
             bf16 *p = (bf16 *)e.aux + (int64_t)m * e.aux_ld + nb;
 #pragma unroll
-            for (int g8 = 0; g8 < 8; ++g8) {
-              if (nb + g8 * 8 + 7 < g.N) {
+            for (int j = 0; j < 4; ++j) {
+              if (nb + j * 8 + 7 < g.N) {
                 uint4 w;
                 uint32_t *wp = reinterpret_cast<uint32_t *>(&w);
 #pragma unroll
                 for (int jj = 0; jj < 4; ++jj) {
-                  __nv_bfloat162 h2 = __floats2bfloat162_rn(v[g8 * 8 + 2 * jj], v[g8 * 8 + 2 * jj + 1]);
+                  __nv_bfloat162 h2 = __floats2bfloat162_rn(v[j * 8 + 2 * jj], v[j * 8 + 2 * jj + 1]);
                   wp[jj] = *reinterpret_cast<uint32_t *>(&h2);
                 }
-                *reinterpret_cast<uint4 *>(p + g8 * 8) = w;
+                *reinterpret_cast<uint4 *>(p + j * 8) = w;
               } else {
                 for (int jj = 0; jj < 8; ++jj)
-                  if (nb + g8 * 8 + jj < g.N) p[g8 * 8 + jj] = __float2bfloat16_rn(v[g8 * 8 + jj]);
+                  if (nb + j * 8 + jj < g.N) p[j * 8 + jj] = __float2bfloat16_rn(v[j * 8 + jj]);
               }
             }
           }
-          if (e.gate && mok) {
-            const bf16 *p = (const bf16 *)e.gate + (int64_t)m * e.gate_ld + nb;
+          if (e.gate) {
 #pragma unroll
-            for (int g8 = 0; g8 < 8; ++g8) {
-              if (nb + g8 * 8 + 7 < g.N) {
-                const uint4 w = *reinterpret_cast<const uint4 *>(p + g8 * 8);
-                const bf16 *h = reinterpret_cast<const bf16 *>(&w);
-#pragma unroll
-                for (int jj = 0; jj < 8; ++jj) v[g8 * 8 + jj] *= __bfloat162float(h[jj]);
-              } else {
-                for (int jj = 0; jj < 8; ++jj)
-                  if (nb + g8 * 8 + jj < g.N) v[g8 * 8 + jj] *= __bfloat162float(p[g8 * 8 + jj]);
-              }
-            }
+            for (int jj = 0; jj < 32; ++jj) v[jj] *= bf_at(va, jj);
           }
-          if (e.residual && mok) {
-            const bf16 *p = (const bf16 *)e.residual + cbase + nb;
+          if (resid) {
 #pragma unroll
-            for (int g8 = 0; g8 < 8; ++g8) {
-              if (nb + g8 * 8 + 7 < g.N) {
-                const uint4 w = *reinterpret_cast<const uint4 *>(p + g8 * 8);
-                const bf16 *h = reinterpret_cast<const bf16 *>(&w);
-#pragma unroll
-                for (int jj = 0; jj < 8; ++jj) v[g8 * 8 + jj] += __bfloat162float(h[jj]);
-              } else {
-                for (int jj = 0; jj < 8; ++jj)
-                  if (nb + g8 * 8 + jj < g.N) v[g8 * 8 + jj] += __bfloat162float(p[g8 * 8 + jj]);
-              }
-            }
+            for (int jj = 0; jj < 32; ++jj) v[jj] += bf_at(vr, jj);
           }
-          // stage bf16 into the 128-byte-swizzled buffer (row = lane, 16-byte chunk j at j ^ (lane & 7))
-          const uint32_t buf = region + (nstore & 1u) * 4096u;
+          // stage bf16 rows of 64 B with the 64-byte swizzle (16-byte chunk j of
+          // row r at j ^ ((r >> 1) & 3)), the layout the TMA store reads
+          const uint32_t buf = region + (nstore & 1u) * 2048u;
           if (lane == 0) bulk_wait_read<1>();
           __syncwarp();
 #pragma unroll
-          for (int j = 0; j < 8; ++j) {
+          for (int j = 0; j < 4; ++j) {
             uint32_t w[4];
 #pragma unroll
             for (int jj = 0; jj < 4; ++jj) {
               __nv_bfloat162 h2 = __floats2bfloat162_rn(v[j * 8 + 2 * jj], v[j * 8 + 2 * jj + 1]);
               w[jj] = *reinterpret_cast<uint32_t *>(&h2);
             }
-            // kind 1: [row][64] with the 128-byte swizzle; kind 2: [n/32][row][32];
-            // kind 3: [row][64] unswizzled (the element order of the 4-D box)
-            uint32_t dst;
-            if (tma_store == 1) dst = buf + lane * 128u + (uint32_t)(((j ^ (lane & 7)) & 7) * 16);
-            else if (tma_store == 2) dst = buf + (uint32_t)(j >> 2) * 2048u + lane * 64u + (uint32_t)(j & 3) * 16u;
-            else dst = buf + lane * 128u + (uint32_t)j * 16u;
+            const uint32_t dst = buf + lane * 64u + (uint32_t)((j ^ ((lane >> 1) & 3)) * 16);
             asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(dst), "r"(w[0]), "r"(w[1]), "r"(w[2]),
                          "r"(w[3])
                          : "memory");
           }
           fence_proxy_async();
           __syncwarp();
-          if (lane == 0 && mrow0 < g.M) {  // rows and columns past the tensor are clipped by TMA
+          if (lane == 0) {  // rows and columns past the tensor are clipped by TMA
             if (tma_store == 1) {
               tma_store_3d(&tmC, buf, nb, mrow0, tc.b);
             } else {
@@ -636,24 +533,18 @@ __global__ void __launch_bounds__(320, 1)
           ++nstore;
         }
       } else {
-        const int64_t my_rowoff = (int64_t)tc.b * e.c_bstride + e.map.row(min(mrow0 + lane, g.M - 1));
-        const bool rows_even = (e.c_bstride & 1) == 0 && (e.map.s_m0 & 1) == 0 &&
-                               (e.map.mdiv >= (1ll << 31) || (e.map.s_m1 & 1) == 0);
-        for (int c0 = half * C::CH; c0 < BN; c0 += 2 * C::CH) {
+        for (int c0 = slot * 32; rows && c0 < BN; c0 += 128) {
           if (tc.n0 + c0 >= g.N) break;
           if (have) {
+            uint32_t r[32];
+            tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + ab * BN + (uint32_t)c0, r);
 #pragma unroll
-            for (int q = 0; q < C::CH; q += 16) {
-              uint32_t r[16];
-              tmem_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + ab * BN + (uint32_t)(c0 + q), r);
-#pragma unroll
-              for (int jj = 0; jj < 16; ++jj) mine[lane * C::LDS + q + jj] = __uint_as_float(r[jj]);
-            }
+            for (int jj = 0; jj < 32; ++jj) mine[lane * C::LDS + jj] = __uint_as_float(r[jj]);
           } else {
-            for (int jj = 0; jj < C::CH; ++jj) mine[lane * C::LDS + jj] = 0.f;
+            for (int jj = 0; jj < 32; ++jj) mine[lane * C::LDS + jj] = 0.f;
           }
           __syncwarp();
-          epi_chunk(g, mine, lane, mrow0, tc.n0 + c0, C::CH, tc.b, tc.split, my_rowoff, rows_even);
+          epi_chunk(g, mine, lane, mrow0, tc.n0 + c0, tc.b, tc.split);
           __syncwarp();
         }
       }
@@ -719,7 +610,8 @@ EncodeTiledFn get_encode() {
 
 // 3-D bf16 tensor {inner, outer, batch} with strides ld, bs (elements).
 bool make_tmap(CUtensorMap *tm, const void *base, uint64_t inner, uint64_t outer, uint64_t batch, uint64_t ld,
-               uint64_t bs, uint32_t box_inner, uint32_t box_outer) {
+               uint64_t bs, uint32_t box_inner, uint32_t box_outer,
+               CUtensorMapSwizzle swz = CU_TENSOR_MAP_SWIZZLE_128B) {
   EncodeTiledFn enc = get_encode();
   if (!enc) return false;
   if (batch <= 1) bs = ld * outer;
@@ -728,7 +620,7 @@ bool make_tmap(CUtensorMap *tm, const void *base, uint64_t inner, uint64_t outer
   cuuint32_t box[3] = {box_inner, box_outer, 1};
   cuuint32_t estr[3] = {1, 1, 1};
   CUresult r = enc(tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void *>(base), dims, strides, box, estr,
-                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, swz, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS;
 }
@@ -745,7 +637,7 @@ int sm_count() {
 
 // 4-D bf16 tensor {d0, d1, d2, d3} with element strides s1, s2, s3 (any order).
 bool make_tmap4(CUtensorMap *tm, const void *base, uint64_t d0, uint64_t d1, uint64_t d2, uint64_t d3, uint64_t s1,
-                uint64_t s2, uint64_t s3, uint32_t b0, uint32_t b1, uint32_t b2, uint32_t b3, bool swizzle) {
+                uint64_t s2, uint64_t s3, uint32_t b0, uint32_t b1, uint32_t b2, uint32_t b3, CUtensorMapSwizzle swz) {
   // strides must be non-decreasing and each must span the previous dimension
   if (s1 < d0 || s2 < s1 * d1 || s3 < s2 * d2) return false;
   EncodeTiledFn enc = get_encode();
@@ -755,7 +647,7 @@ bool make_tmap4(CUtensorMap *tm, const void *base, uint64_t d0, uint64_t d1, uin
   cuuint32_t box[4] = {b0, b1, b2, b3};
   cuuint32_t estr[4] = {1, 1, 1, 1};
   CUresult r = enc(tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void *>(base), dims, strides, box, estr,
-                   CU_TENSOR_MAP_INTERLEAVE_NONE, swizzle ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_NONE,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, swz,
                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS;
 }
@@ -772,11 +664,12 @@ cudaError_t launch_tc(const GemmOp &g, cudaStream_t s) {
   // TMA-store epilogue.  Kind 1: plain row-major bf16 output (3-D map over
   // n, m, batch).  Kind 2: a two-level map with 32-wide column groups,
   // offset = (n / 32) s_n1 + n % 32 + (m / mdiv) s_m1 + (m % mdiv) s_m0, stored
-  // through a 4-D map whose box is one warp's 32 x 64 sub-tile.  Every operand
+  // through a 4-D map whose box is one warp's 32 x 32 sub-tile.  Every operand
   // the epilogue reads needs 16-byte aligned row vectors.
   const Epi &e = g.e;
   auto a16 = [](const void *p) { return ((uintptr_t)p & 15u) == 0; };
-  const bool operands_ok = !e.partial && !e.c_f32 && !e.accumulate && a16(e.C) && (!e.residual || a16(e.residual)) &&
+  const bool operands_ok = !e.partial && !e.c_f32 && !e.accumulate && !(e.gate && e.relu_ref) && a16(e.C) &&
+                           (!e.residual || a16(e.residual)) &&
                            (!e.relu_ref || (a16(e.relu_ref) && e.relu_ld % 8 == 0)) &&
                            (!e.aux || (a16(e.aux) && e.aux_ld % 8 == 0)) &&
                            (!e.gate || (a16(e.gate) && e.gate_ld % 8 == 0)) &&
@@ -786,7 +679,9 @@ cudaError_t launch_tc(const GemmOp &g, cudaStream_t s) {
   CUtensorMap tc;
   std::memset(&tc, 0, sizeof(tc));
   if (operands_ok && plain && e.map.s_m0 % 8 == 0 && (g.batch == 1 || e.c_bstride % 8 == 0)) {
-    if (make_tmap(&tc, e.C, g.N, g.M, g.batch, e.map.s_m0, g.batch > 1 ? e.c_bstride : 0, 64, 32)) tstore = 1;
+    if (make_tmap(&tc, e.C, g.N, g.M, g.batch, e.map.s_m0, g.batch > 1 ? e.c_bstride : 0, 32, 32,
+                  CU_TENSOR_MAP_SWIZZLE_64B))
+      tstore = 1;
   } else if (operands_ok && !plain && g.batch == 1 && !e.residual && e.map.ndiv == 32 && e.map.s_n0 == 1 &&
              g.N % 32 == 0 && e.map.s_n1 % 8 == 0 && e.map.s_m0 % 8 == 0 &&
              (e.map.mdiv >= (1ll << 31) || (e.map.mdiv % 32 == 0 && g.M % e.map.mdiv == 0 && e.map.s_m1 % 8 == 0))) {
@@ -798,9 +693,11 @@ cudaError_t launch_tc(const GemmOp &g, cudaStream_t s) {
     const uint64_t s_mhi = e.map.mdiv >= (1ll << 31) ? s_mlo * md : (uint64_t)e.map.s_m1;
     const uint64_t nhi = (uint64_t)g.N / 32, mhi = (uint64_t)g.M / md;
     if (s_mlo >= 32 && s_mlo <= s_nhi && s_nhi >= s_mlo * md && s_mhi >= s_nhi * nhi) {
-      if (make_tmap4(&tc, e.C, 32, md, nhi, mhi, s_mlo, s_nhi, s_mhi, 32, 32, 2, 1, false)) tstore = 2;
+      if (make_tmap4(&tc, e.C, 32, md, nhi, mhi, s_mlo, s_nhi, s_mhi, 32, 32, 1, 1, CU_TENSOR_MAP_SWIZZLE_64B))
+        tstore = 2;
     } else if (s_nhi >= 32 && s_nhi <= s_mlo && s_mlo >= s_nhi * nhi && s_mhi >= s_mlo * md) {
-      if (make_tmap4(&tc, e.C, 32, nhi, md, mhi, s_nhi, s_mlo, s_mhi, 32, 2, 32, 1, false)) tstore = 3;
+      if (make_tmap4(&tc, e.C, 32, nhi, md, mhi, s_nhi, s_mlo, s_mhi, 32, 1, 32, 1, CU_TENSOR_MAP_SWIZZLE_64B))
+        tstore = 3;
     }
   }
   static bool attr_set = false;
@@ -813,10 +710,16 @@ cudaError_t launch_tc(const GemmOp &g, cudaStream_t s) {
   const long long tiles =
       (long long)((g.N + BN - 1) / BN) * ((g.M + BM - 1) / BM) * (long long)g.batch * g.splits;
   const int grid = (int)std::min<long long>(tiles, sm_count());
-  const double cbytes = g.e.partial ? 4.0 * g.splits : (g.e.c_f32 ? 4.0 : 2.0);
-  Prof p("gemm_tc", s, 2.0 * g.M * g.N * (double)g.K * g.batch,
+  // algorithmic bytes: operands once, the output once, and every epilogue
+  // operand (residual, gate, ReLU reference, aux copy) once
+  double cbytes = g.e.partial ? 4.0 * g.splits : (g.e.c_f32 ? (g.e.accumulate ? 8.0 : 4.0) : 2.0);
+  cbytes += 2.0 * ((g.e.residual ? 1 : 0) + (g.e.gate ? 1 : 0) + (g.e.relu_ref ? 1 : 0) + (g.e.aux ? 1 : 0));
+  Prof p(prof_detail() ? prof_name("g%dx%dx%d*%ds%dn%d%s%se%d", (int)g.M, (int)g.N, (int)g.K, (int)g.batch, g.splits,
+                                    BN, AMN ? "T" : "", BMN ? "t" : "", tstore)
+                      : "gemm_tc",
+         s, 2.0 * g.M * g.N * (double)g.K * g.batch,
          g.batch * (2.0 * ((double)g.M * g.K + (double)g.N * g.K) + cbytes * g.M * g.N));
-  gemm_tc_kernel<BN, STAGES, AMN, BMN><<<grid, 320, C::SMEM, s>>>(ta, tb, tc, g, tstore);
+  gemm_tc_kernel<BN, STAGES, AMN, BMN><<<grid, 576, C::SMEM, s>>>(ta, tb, tc, g, tstore);
   return cudaGetLastError();
 }
 

@@ -109,6 +109,9 @@ cudaError_t reduce_partials_ld(const float *part, int nblk, int64_t ld, int N, f
 cudaError_t colsum(const void *x, int64_t ld, int64_t M, int N, int use_bf16, cudaStream_t s, float *out);
 // out[i] += sum_s part[s*n + i]
 cudaError_t reduce_splits(const float *part, int splits, int64_t n, float *out, cudaStream_t s);
+// bf16 out[map(m, n)] = sum_s part[(s*M + m)*N + n]  (N even)
+cudaError_t reduce_splits_map(const float *part, int splits, int M, int N, const OutMap &map, void *out,
+                              cudaStream_t s);
 
 // Pair-bias projection: out[h][pos'] = x[pos] . w[h], pos = (p0,p1) in [R,R];
 // pos' = p0*R+p1, or p1*R+p0 with transpose.

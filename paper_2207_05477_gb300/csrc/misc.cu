@@ -91,6 +91,27 @@ __global__ void reduce_splits_k(const float *part, int splits, int64_t n, float 
   out[i] += t;
 }
 
+// out(m, n) = sum_s part[(s*M + m)*N + n] in bf16 at offset map(m, n); a
+// thread owns two adjacent columns (N even).
+__global__ void reduce_splits_map_k(const float *part, int splits, int M, int N, OutMap map, bf16 *out) {
+  const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 2;
+  if (i >= (int64_t)M * N) return;
+  const int m = (int)(i / N), n = (int)(i - (int64_t)m * N);
+  float t0 = 0.f, t1 = 0.f;
+  for (int s = 0; s < splits; ++s) {
+    const float2 v = *reinterpret_cast<const float2 *>(part + (int64_t)s * M * N + i);
+    t0 += v.x;
+    t1 += v.y;
+  }
+  const int64_t o0 = map.row(m) + map.col(n), o1 = map.row(m) + map.col(n + 1);
+  if (o1 == o0 + 1 && (o0 & 1) == 0) {
+    *reinterpret_cast<__nv_bfloat162 *>(out + o0) = __floats2bfloat162_rn(t0, t1);
+  } else {
+    out[o0] = __float2bfloat16_rn(t0);
+    out[o1] = __float2bfloat16_rn(t1);
+  }
+}
+
 // ------------------------------------------------------------- pair bias
 template <typename T>
 __global__ void head_proj_fwd_k(const T *x, const float *w, float *out, int R, int C, int H, int transpose) {
@@ -581,6 +602,15 @@ cudaError_t colsum(const void *x, int64_t ld, int64_t M, int N, int use_bf16, cu
 cudaError_t reduce_splits(const float *part, int splits, int64_t n, float *out, cudaStream_t s) {
   Prof prof("reduce_splits", s, 0, 4.0 * (splits + 2) * (double)n, 1);
   reduce_splits_k<<<nblk(n), 256, 0, s>>>(part, splits, n, out);
+  return cudaGetLastError();
+}
+
+cudaError_t reduce_splits_map(const float *part, int splits, int M, int N, const OutMap &map, void *out,
+                              cudaStream_t s) {
+  if (N % 2) return cudaErrorInvalidValue;
+  Prof prof("reduce_splits", s, 0, (4.0 * splits + 2.0) * (double)M * N, 1);
+  const int64_t pairs = (int64_t)M * N / 2;
+  reduce_splits_map_k<<<nblk(pairs), 256, 0, s>>>(part, splits, M, N, map, (bf16 *)out);
   return cudaGetLastError();
 }
 

@@ -1,6 +1,10 @@
 // Launch profiling of libevo (see prof.h) and its C entry points.
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
+#include <set>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -20,6 +24,9 @@ struct Rec {
 
 std::mutex g_mu;
 bool g_on = false;
+bool g_detail = false;
+std::string g_only;  // record only this kernel name ("" = all)
+std::set<std::string> g_names;
 std::vector<Rec> g_recs;
 std::vector<cudaEvent_t> g_pool;  // events handed out since the last begin
 size_t g_next = 0;
@@ -27,6 +34,22 @@ size_t g_next = 0;
 }  // namespace
 
 bool prof_on() { return g_on; }
+bool prof_wants(const char *name) {
+  if (!g_on) return false;
+  std::lock_guard<std::mutex> lk(g_mu);
+  return g_only.empty() || g_only == name;
+}
+bool prof_detail() { return g_on && g_detail; }
+
+const char *prof_name(const char *fmt, ...) {
+  char buf[64];
+  va_list ap;
+  va_start(ap, fmt);
+  std::vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  std::lock_guard<std::mutex> lk(g_mu);
+  return g_names.insert(std::string(buf)).first->c_str();
+}
 
 cudaEvent_t prof_event() {
   std::lock_guard<std::mutex> lk(g_mu);
@@ -49,10 +72,18 @@ using namespace evo;
 
 extern "C" {
 
+int evo_profile_only(const char *kernel_name) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  g_only = kernel_name ? kernel_name : "";
+  return EVO_OK;
+}
+
 int evo_profile_begin(void) {
   std::lock_guard<std::mutex> lk(g_mu);
   g_recs.clear();
   g_next = 0;
+  const char *d = std::getenv("EVO_PROFILE_DETAIL");
+  g_detail = d && d[0] == '1';
   g_on = true;
   return EVO_OK;
 }
@@ -61,6 +92,7 @@ int evo_profile_end(evo_stream_t stream, evo_profile_entry *out, int cap) {
   if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) return EVO_ERR_CUDA;
   std::lock_guard<std::mutex> lk(g_mu);
   g_on = false;
+  g_only.clear();
   std::map<std::string, evo_profile_entry> agg;
   std::vector<std::string> order;
   for (const Rec &r : g_recs) {

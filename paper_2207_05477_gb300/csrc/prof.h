@@ -8,6 +8,13 @@
 namespace evo {
 
 bool prof_on();
+// True while recording and name passes the evo_profile_only selection.
+bool prof_wants(const char *name);
+// True while profiling with per-shape names (EVO_PROFILE_DETAIL=1 in the
+// environment at evo_profile_begin).
+bool prof_detail();
+// A stable copy of a printf-formatted name (lives until the process exits).
+const char *prof_name(const char *fmt, ...);
 void prof_record(const char *name, int launches, double flops, double bytes, cudaEvent_t a, cudaEvent_t b);
 cudaEvent_t prof_event();
 
@@ -19,7 +26,7 @@ struct Prof {
   cudaEvent_t a = nullptr, b = nullptr;
   Prof(const char *n, cudaStream_t st, double f = 0, double by = 0, int nl = 1)
       : name(n), launches(nl), flops(f), bytes(by), s(st) {
-    if (prof_on()) {
+    if (prof_wants(n)) {
       a = prof_event();
       b = prof_event();
       if (a) cudaEventRecord(a, s);

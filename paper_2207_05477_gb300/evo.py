@@ -70,6 +70,7 @@ def lib():
         L.evo_stack_fwd.argtypes = [P(CDims), ctypes.c_int, _vp, _vp, _sz, _vp, _vp, _vp, _vp, _vp, _sz, _vp]
         L.evo_get_error.argtypes = [_vp]
         L.evo_debug_wait_timeout.argtypes = [ctypes.c_longlong, _vp]
+        L.evo_profile_only.argtypes = [ctypes.c_char_p]
         L.evo_profile_begin.argtypes = []
         L.evo_profile_end.argtypes = [_vp, P(CProfileEntry), ctypes.c_int]
         L.evo_strerror.argtypes = [ctypes.c_int]
@@ -170,6 +171,11 @@ def get_error(stream=None):
 
 def debug_wait_timeout(limit_ns, stream=None):
     _check(lib().evo_debug_wait_timeout(int(limit_ns), _stream(stream)), "evo_debug_wait_timeout")
+
+
+def profile_only(kernel_name=None):
+    """Restrict the next profile recording to one kernel name (None: all)."""
+    _check(lib().evo_profile_only(kernel_name.encode() if kernel_name else None), "evo_profile_only")
 
 
 def profile_begin():
