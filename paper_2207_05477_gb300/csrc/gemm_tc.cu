@@ -63,12 +63,25 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
+// try_wait that may suspend the thread until the phase completes or about
+// hint_ns pass (so waiting warps do not spin on the issue slots).
+__device__ __forceinline__ bool mbar_try_wait_hint(uint64_t *bar, uint32_t parity, uint32_t hint_ns) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity), "r"(hint_ns)
+      : "memory");
+  return ok != 0;
+}
 // Bounded wait; gives up when the CTA abort flag is raised or the limit passes.
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort_flag) {
   if (mbar_try_wait(bar, parity)) return true;
   const uint64_t t0 = globaltimer_ns();
   while (true) {
-    if (mbar_try_wait(bar, parity)) return true;
+    if (mbar_try_wait_hint(bar, parity, 100000u)) return true;
     if (*abort_flag) return false;
     if (globaltimer_ns() - t0 > WAIT_LIMIT_NS) {
       *abort_flag = 1;
@@ -171,22 +184,20 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
-// Persistent kernel configuration: a STAGES-deep ring of A/B k-tiles, an
-// epilogue staging area for the four epilogue warps, and two TMEM
-// accumulators of BN columns (tile i drains while tile i+1 accumulates).
-template <int BN, int STAGES, bool AMN, bool BMN>
+// Persistent kernel configuration: a ring of A/B k-tiles, sixteen epilogue
+// warps with a small shared-memory region each, and two TMEM accumulators of
+// BN columns (tile i drains while tile i+1 accumulates).  The depth of the
+// k-tile ring is chosen at launch: whatever shared memory the epilogue
+// regions leave.
+constexpr int EPI_WARPS = 16;  // four per TMEM lane quarter, 32-column slots at a 128-column stride
+constexpr int MAX_STAGES = 6;
+constexpr int SMEM_LIMIT = 232448;  // bytes of dynamic shared memory one CTA may use
+
+template <int BN, bool AMN, bool BMN>
 struct TcCfg {
   static constexpr int A_BYTES = BM * BK * 2;
   static constexpr int B_BYTES = BN * BK * 2;
   static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
-  static constexpr int CH = 32;   // epilogue column chunk (one warp-iteration)
-  static constexpr int LDS = CH + 1;  // staged row pitch of the general path (floats)
-  // per epilogue warp: two 2 KB TMA-store buffers (1 KB aligned), or 32 x LDS floats
-  static constexpr int EPI_WARP_BYTES = 5120;
-  static constexpr int EPI_WARPS = 16;  // four per TMEM lane quarter, 32-column slots at a 128-column stride
-  static constexpr int EPI_BYTES = EPI_WARPS * EPI_WARP_BYTES;
-  static_assert(32 * LDS * 4 <= EPI_WARP_BYTES, "epilogue staging");
-  static constexpr int SMEM = STAGES * STAGE_BYTES + EPI_BYTES + 1024;
   static constexpr int TMEM_COLS = 2 * BN < 32 ? 32 : 2 * BN;
   // A K-major tile: rows of 128 B, k-step of 16 elements = 32 B.
   // An MN-major tile: 64-element (128 B) MN chunks of 64 K-rows (8 KB each);
@@ -198,8 +209,24 @@ struct TcCfg {
   static constexpr uint32_t IDESC = instr_desc(BM, BN, AMN, BMN);
   static_assert(BN % 16 == 0 && BN >= 16 && BN <= 256, "UMMA N");
   static_assert(TMEM_COLS <= 512 && (TMEM_COLS & (TMEM_COLS - 1)) == 0, "TMEM columns");
-  // one CTA per SM: more than half of the SM's shared memory
-  static_assert(SMEM > 233472 / 2 && SMEM <= 232448, "one resident CTA per SM");
+};
+
+// Epilogue region of one warp (1 KB aligned):
+//   [0, 4 KB)    two 2 KB slots: the chunk's residual tile, loaded by TMA and
+//                overwritten in place by the bf16 result the TMA store reads
+//                (the output staging when there is no residual);
+//   [4 KB, 8 KB) two 2 KB slots for the gate or ReLU-reference tile (only
+//                when the epilogue has one);
+//   the general path instead stages 32 x 33 floats from offset 0.
+// Tiles are 32 rows x 64 B with the 64-byte swizzle.
+__host__ __device__ constexpr int epi_warp_bytes(bool has_opa) { return has_opa ? 8192 : 5120; }
+
+struct TcLaunch {
+  int stages;     // depth of the k-tile ring
+  int epi_bytes;  // per epilogue warp
+  int tma_store;  // 0: general epilogue; 1: 3-D row-major map; 2, 3: 4-D two-level maps
+  int has_opa;    // gate or ReLU reference tile loaded by TMA
+  int has_res;    // residual tile loaded by TMA
 };
 
 struct TileCoord {
@@ -267,16 +294,18 @@ __device__ __forceinline__ float bf_at(const uint4 (&o)[4], int k) {
 // warp 1 lane 0: MMA issuer (accumulator buffer alternates per tile)
 // warps 2-17: epilogue (warp w drains TMEM lane quarter w % 4 and takes the
 //             32-column slot (w - 2) / 4 of every 128 columns)
-template <int BN, int STAGES, bool AMN, bool BMN>
+template <int BN, bool AMN, bool BMN>
 __global__ void __launch_bounds__(576, 1)
     gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-                   const __grid_constant__ CUtensorMap tmC, GemmOp g, int tma_store) {
-  using C = TcCfg<BN, STAGES, AMN, BMN>;
+                   const __grid_constant__ CUtensorMap tmC, const __grid_constant__ CUtensorMap tmOpA,
+                   const __grid_constant__ CUtensorMap tmRes, GemmOp g, TcLaunch L) {
+  using C = TcCfg<BN, AMN, BMN>;
   extern __shared__ uint8_t dsmem[];
-  __shared__ __align__(8) uint64_t full_bar[STAGES];
-  __shared__ __align__(8) uint64_t empty_bar[STAGES];
+  __shared__ __align__(8) uint64_t full_bar[MAX_STAGES];
+  __shared__ __align__(8) uint64_t empty_bar[MAX_STAGES];
   __shared__ __align__(8) uint64_t accf_bar[2];
   __shared__ __align__(8) uint64_t acce_bar[2];
+  __shared__ __align__(8) uint64_t op_bar[EPI_WARPS][2];
   __shared__ __align__(8) uint64_t done_bar;
   __shared__ uint32_t tmem_slot;
   __shared__ volatile int s_abort;
@@ -285,15 +314,20 @@ __global__ void __launch_bounds__(576, 1)
   const uint32_t sbase = (raw + 1023u) & ~1023u;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int ntiles = ((g.N + BN - 1) / BN) * ((g.M + BM - 1) / BM) * g.batch * g.splits;
+  const int stages = L.stages;
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < STAGES; ++s) {
+    for (int s = 0; s < stages; ++s) {
       mbar_init(&full_bar[s], 1);
       mbar_init(&empty_bar[s], 1);
     }
     for (int a = 0; a < 2; ++a) {
       mbar_init(&accf_bar[a], 1);
-      mbar_init(&acce_bar[a], C::EPI_WARPS);
+      mbar_init(&acce_bar[a], EPI_WARPS);
+    }
+    for (int w = 0; w < EPI_WARPS; ++w) {
+      mbar_init(&op_bar[w][0], 1);
+      mbar_init(&op_bar[w][1], 1);
     }
     mbar_init(&done_bar, 1);
     s_abort = 0;
@@ -312,48 +346,47 @@ __global__ void __launch_bounds__(576, 1)
 
   if (warp == 0 && lane == 0) {
     // ---------------- TMA producer
-    uint32_t it = 0;
+    uint32_t it = 0, stage = 0, phase = 0;
     bool stop = false;
     for (int t = blockIdx.x; t < ntiles && !stop; t += gridDim.x) {
       const TileCoord tc = decode_tile(g, t, BN);
       for (int i = 0; i < tc.nk; ++i, ++it) {
-        const int s = (int)(it % STAGES);
-        const uint32_t j = it / STAGES;
-        if (it >= (uint32_t)STAGES && !mbar_wait(&empty_bar[s], (j - 1) & 1u, &s_abort)) {
+        if (it >= (uint32_t)stages && !mbar_wait(&empty_bar[stage], phase ^ 1u, &s_abort)) {
           stop = true;
           break;
         }
-        const uint32_t sa = sbase + s * C::STAGE_BYTES;
+        const uint32_t sa = sbase + stage * C::STAGE_BYTES;
         const uint32_t sb = sa + C::A_BYTES;
         const int kc = (tc.kt0 + i) * BK;
-        mbar_arrive_expect_tx(&full_bar[s], C::STAGE_BYTES);
+        mbar_arrive_expect_tx(&full_bar[stage], C::STAGE_BYTES);
         if (AMN) {
-          tma_load_3d(sa, &tmA, tc.m0, kc, tc.b, &full_bar[s]);
-          tma_load_3d(sa + 8192, &tmA, tc.m0 + 64, kc, tc.b, &full_bar[s]);
+          tma_load_3d(sa, &tmA, tc.m0, kc, tc.b, &full_bar[stage]);
+          tma_load_3d(sa + 8192, &tmA, tc.m0 + 64, kc, tc.b, &full_bar[stage]);
         } else {
-          tma_load_3d(sa, &tmA, kc, tc.m0, tc.b, &full_bar[s]);
+          tma_load_3d(sa, &tmA, kc, tc.m0, tc.b, &full_bar[stage]);
         }
         if (BMN) {
 #pragma unroll
           for (int cpart = 0; cpart < BN / 64; ++cpart)
-            tma_load_3d(sb + cpart * 8192, &tmB, tc.n0 + cpart * 64, kc, tc.b, &full_bar[s]);
+            tma_load_3d(sb + cpart * 8192, &tmB, tc.n0 + cpart * 64, kc, tc.b, &full_bar[stage]);
         } else {
-          tma_load_3d(sb, &tmB, kc, tc.n0, tc.b, &full_bar[s]);
+          tma_load_3d(sb, &tmB, kc, tc.n0, tc.b, &full_bar[stage]);
         }
+        if (++stage == (uint32_t)stages) stage = 0, phase ^= 1u;
       }
     }
     if (s_abort) {
       // drain: wait (bounded) for every load that may still be in flight
-      const uint32_t first = it > (uint32_t)STAGES ? it - STAGES : 0u;
+      const uint32_t first = it > (uint32_t)stages ? it - stages : 0u;
       for (uint32_t i = first; i < it; ++i) {
         const uint64_t t0 = globaltimer_ns();
-        while (!mbar_try_wait(&full_bar[i % STAGES], (i / STAGES) & 1u) && globaltimer_ns() - t0 < WAIT_LIMIT_NS) {
+        while (!mbar_try_wait(&full_bar[i % stages], (i / stages) & 1u) && globaltimer_ns() - t0 < WAIT_LIMIT_NS) {
         }
       }
     }
   } else if (warp == 1 && lane == 0) {
     // ---------------- MMA issuer
-    uint32_t it = 0, ai = 0;
+    uint32_t stage = 0, phase = 0, ai = 0;
     bool stop = false;
     for (int t = blockIdx.x; t < ntiles && !stop; t += gridDim.x) {
       const TileCoord tc = decode_tile(g, t, BN);
@@ -362,15 +395,13 @@ __global__ void __launch_bounds__(576, 1)
       if (ai >= 2 && !mbar_wait(&acce_bar[ab], (u - 1) & 1u, &s_abort)) break;
       tc_fence_after();
       const uint32_t dacc = tmem + ab * BN;
-      for (int i = 0; i < tc.nk; ++i, ++it) {
-        const int s = (int)(it % STAGES);
-        const uint32_t j = it / STAGES;
-        if (!mbar_wait(&full_bar[s], j & 1u, &s_abort)) {
+      for (int i = 0; i < tc.nk; ++i) {
+        if (!mbar_wait(&full_bar[stage], phase, &s_abort)) {
           stop = true;
           break;
         }
         tc_fence_after();
-        const uint32_t sa = sbase + s * C::STAGE_BYTES;
+        const uint32_t sa = sbase + stage * C::STAGE_BYTES;
         const uint32_t sb = sa + C::A_BYTES;
 #pragma unroll
         for (int kk = 0; kk < BK / 16; ++kk) {
@@ -378,7 +409,8 @@ __global__ void __launch_bounds__(576, 1)
           const uint64_t bd = smem_desc(sb + kk * C::B_KSTEP, C::B_LBO, 1024);
           tc_mma(dacc, ad, bd, C::IDESC, (i > 0 || kk > 0) ? 1u : 0u);
         }
-        tc_commit(&empty_bar[s]);
+        tc_commit(&empty_bar[stage]);
+        if (++stage == (uint32_t)stages) stage = 0, phase ^= 1u;
       }
       if (stop) break;
       tc_commit(&accf_bar[ab]);
@@ -392,85 +424,133 @@ __global__ void __launch_bounds__(576, 1)
     // 128 columns of the tile.
     const int ew = warp - 2;
     const int quarter = warp & 3, slot = ew >> 2;
-    const uint32_t region = sbase + STAGES * C::STAGE_BYTES + ew * C::EPI_WARP_BYTES;
+    const uint32_t region = sbase + stages * C::STAGE_BYTES + ew * L.epi_bytes;
     float *mine = reinterpret_cast<float *>(dsmem + (region - raw));
-    uint32_t ai = 0, nstore = 0;
     const Epi &e = g.e;
-    // gate and relu_ref (never both present) share one operand register set
-    const void *opa = e.gate ? e.gate : e.relu_ref;
-    const int64_t opa_ld = e.gate ? e.gate_ld : e.relu_ld;
-    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
-      const TileCoord tc = decode_tile(g, t, BN);
-      const uint32_t ab = ai & 1u, u = ai >> 1;
-      const int mrow0 = tc.m0 + quarter * 32;
-      const int m = mrow0 + lane;
-      const bool mok = m < g.M;
-      const bool rows = mrow0 < g.M;  // warp-uniform: any row of this quarter in range
-      const bf16 *resid = e.residual ? (const bf16 *)e.residual + (int64_t)tc.b * e.c_bstride : nullptr;
-      // row operands of the first chunk are fetched while the accumulator fills
-      uint4 va[4], vr[4];
-      if (tma_store && rows && slot * 32 < BN && tc.n0 + slot * 32 < g.N) {
-        if (opa) ld_row32(opa, opa_ld, m, mok, tc.n0 + slot * 32, g.N, va);
-        if (resid) ld_row32(resid, e.map.s_m0, m, mok, tc.n0 + slot * 32, g.N, vr);
-      }
-      bool have = false;
-      if (tc.nk > 0) {
-        have = mbar_wait(&accf_bar[ab], u & 1u, &s_abort);
-        have = __all_sync(0xffffffffu, have);
-        if (!have) break;
-        tc_fence_after();
-      }
-      if (tma_store) {
-        // thread = row: TMEM -> registers -> epilogue -> bf16 -> swizzled shared -> TMA store
+    uint32_t ai = 0;
+    if (L.tma_store) {
+      // Chunk k of this warp (k counts the warp's chunks over all its tiles)
+      // uses slot k & 1.  Its operand tiles are requested by TMA at the end
+      // of chunk k - 1 (the first one before the loop), after the store that
+      // last read that slot (chunk k - 2) has finished reading.
+      const uint32_t op_bytes = (L.has_opa ? 2048u : 0u) + (L.has_res ? 2048u : 0u);
+      int nt = blockIdx.x, nc = slot * 32;  // the next chunk whose operands are requested
+      // the chunks of a tile are columns slot*32 + 128 i below BN and N, rows
+      // of the warp's quarter below M; advance() moves (nt, nc) to the next
+      // one in the order the loop below visits them (nt >= ntiles: none left)
+      auto advance = [&]() {
+        nc += 128;
+        while (nt < ntiles) {
+          const TileCoord q = decode_tile(g, nt, BN);
+          if (nc < BN && q.n0 + nc < g.N && q.m0 + quarter * 32 < g.M) return;
+          nt += gridDim.x;
+          nc = slot * 32;
+        }
+      };
+      uint32_t requested = 0;  // chunks whose operand tiles have been requested
+      auto request = [&](uint32_t k) {  // lane 0: operand tiles of chunk (nt, nc) into slot k & 1
+        if (nt >= ntiles || op_bytes == 0) return;
+        requested = k + 1;
+        const TileCoord q = decode_tile(g, nt, BN);
+        const uint32_t sl = k & 1u;
+        mbar_arrive_expect_tx(&op_bar[ew][sl], op_bytes);
+        const int n = q.n0 + nc, mq = q.m0 + quarter * 32;
+        if (L.has_res) tma_load_3d(region + sl * 2048u, &tmRes, n, mq, q.b, &op_bar[ew][sl]);
+        if (L.has_opa) tma_load_3d(region + 4096u + sl * 2048u, &tmOpA, n, mq, 0, &op_bar[ew][sl]);
+      };
+      nc -= 128;
+      advance();
+      if (lane == 0) request(0);
+      uint32_t k = 0;
+      for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const TileCoord tc = decode_tile(g, t, BN);
+        const uint32_t ab = ai & 1u, u = ai >> 1;
+        const int mrow0 = tc.m0 + quarter * 32;
+        const int m = mrow0 + lane;
+        const bool mok = m < g.M;
+        bool have = false;
+        if (tc.nk > 0) {
+          have = mbar_wait(&accf_bar[ab], u & 1u, &s_abort);
+          have = __all_sync(0xffffffffu, have);
+          if (!have) break;
+          tc_fence_after();
+        }
         const float rs = (e.row_scale && mok) ? e.row_scale[m] : 1.f;
-        for (int c0 = slot * 32; rows && c0 < BN; c0 += 128) {
+        bool ok = true;
+        for (int c0 = slot * 32; c0 < BN && mrow0 < g.M; c0 += 128) {
           const int nb = tc.n0 + c0;
           if (nb >= g.N) break;
-          if (c0 != slot * 32) {
-            if (opa) ld_row32(opa, opa_ld, m, mok, nb, g.N, va);
-            if (resid) ld_row32(resid, e.map.s_m0, m, mok, nb, g.N, vr);
-          }
+          const uint32_t sl = k & 1u;
+          const uint32_t obuf = region + sl * 2048u, abuf = region + 4096u + sl * 2048u;
+          // this thread's 64-byte row of a swizzled 32 x 32 bf16 tile: 16-byte
+          // chunk j at j ^ ((row >> 1) & 3)
+          const uint32_t rowoff = lane * 64u;
+          const uint32_t swz = (uint32_t)((lane >> 1) & 3);
           float v[32];
           if (have) {
             uint32_t r[32];
             tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + ab * BN + (uint32_t)c0, r);
 #pragma unroll
-            for (int jj = 0; jj < 32; ++jj) v[jj] = __uint_as_float(r[jj]) * e.alpha;
+            for (int jj = 0; jj < 32; ++jj) v[jj] = __uint_as_float(r[jj]);
+            if (e.alpha != 1.f) {
+#pragma unroll
+              for (int jj = 0; jj < 32; ++jj) v[jj] *= e.alpha;
+            }
           } else {
 #pragma unroll
             for (int jj = 0; jj < 32; ++jj) v[jj] = 0.f;
           }
-          if (e.bias) {
+          // column conditions are decided per chunk where the whole chunk agrees
+          if (e.bias && nb >= e.bias_n0 && nb + 31 < g.N) {
+            const float4 *bp = reinterpret_cast<const float4 *>(e.bias + (nb - e.bias_n0));
 #pragma unroll
             for (int q = 0; q < 8; ++q) {
-              const int n = nb + 4 * q;
-              if (n >= e.bias_n0) {  // bias_n0 % 4 == 0: a group is all biased or all not
-                if (n + 3 < g.N) {
-                  const float4 x = *reinterpret_cast<const float4 *>(e.bias + (n - e.bias_n0));
-                  v[4 * q] += x.x, v[4 * q + 1] += x.y, v[4 * q + 2] += x.z, v[4 * q + 3] += x.w;
-                } else {
-                  for (int jj = 0; jj < 4; ++jj)
-                    if (n + jj < g.N) v[4 * q + jj] += e.bias[n + jj - e.bias_n0];
-                }
-              }
+              const float4 x = bp[q];
+              v[4 * q] += x.x, v[4 * q + 1] += x.y, v[4 * q + 2] += x.z, v[4 * q + 3] += x.w;
+            }
+          } else if (e.bias && nb + 31 >= e.bias_n0) {
+            // boundary chunk: columns past N are clipped by the store, so their
+            // (clamped) bias index only has to stay inside the bias vector
+#pragma unroll
+            for (int jj = 0; jj < 32; ++jj) {
+              const int n = min(nb + jj, g.N - 1);
+              const float b = e.bias[max(n - e.bias_n0, 0)];
+              v[jj] += nb + jj >= e.bias_n0 ? b : 0.f;
             }
           }
           if (e.row_scale) {
 #pragma unroll
             for (int jj = 0; jj < 32; ++jj) v[jj] *= rs;
           }
+          if (L.has_opa || L.has_res) {
+            if (!mbar_wait(&op_bar[ew][sl], (k >> 1) & 1u, &s_abort)) ok = false;
+            if (!__all_sync(0xffffffffu, ok)) break;
+          }
           if (e.relu_ref) {
 #pragma unroll
-            for (int jj = 0; jj < 32; ++jj)
-              if (!(bf_at(va, jj) > 0.f)) v[jj] = 0.f;
+            for (int j = 0; j < 4; ++j) {
+              uint4 w;
+              asm volatile("ld.shared.v4.b32 {%0, %1, %2, %3}, [%4];"
+                           : "=r"(w.x), "=r"(w.y), "=r"(w.z), "=r"(w.w)
+                           : "r"(abuf + rowoff + ((j ^ swz) << 4)));
+              const bf16 *h = reinterpret_cast<const bf16 *>(&w);
+#pragma unroll
+              for (int jj = 0; jj < 8; ++jj)
+                if (!(__bfloat162float(h[jj]) > 0.f)) v[j * 8 + jj] = 0.f;
+            }
           }
           if (e.act == ACT_RELU) {
 #pragma unroll
             for (int jj = 0; jj < 32; ++jj) v[jj] = fmaxf(v[jj], 0.f);
-          } else if (e.act == ACT_SIGMOID) {
+          } else if (e.act == ACT_SIGMOID && nb >= e.act_n0) {
 #pragma unroll
-            for (int jj = 0; jj < 32; ++jj)
-              if (nb + jj >= e.act_n0) v[jj] = __fdividef(1.f, 1.f + __expf(-v[jj]));
+            for (int jj = 0; jj < 32; ++jj) v[jj] = __fdividef(1.f, 1.f + __expf(-v[jj]));
+          } else if (e.act == ACT_SIGMOID && nb + 31 >= e.act_n0) {
+#pragma unroll
+            for (int jj = 0; jj < 32; ++jj) {
+              const float sg = __fdividef(1.f, 1.f + __expf(-v[jj]));
+              v[jj] = nb + jj >= e.act_n0 ? sg : v[jj];
+            }
           }
           if (e.aux && mok) {
             bf16 *p = (bf16 *)e.aux + (int64_t)m * e.aux_ld + nb;
@@ -491,70 +571,117 @@ __global__ void __launch_bounds__(576, 1)
               }
             }
           }
-          if (e.gate) {
-#pragma unroll
-            for (int jj = 0; jj < 32; ++jj) v[jj] *= bf_at(va, jj);
+          if (!L.has_res) {
+            // the output slot was last read by the store of chunk k - 2
+            if (lane == 0) bulk_wait_read<1>();
+            __syncwarp();
           }
-          if (resid) {
-#pragma unroll
-            for (int jj = 0; jj < 32; ++jj) v[jj] += bf_at(vr, jj);
-          }
-          // stage bf16 rows of 64 B with the 64-byte swizzle (16-byte chunk j of
-          // row r at j ^ ((r >> 1) & 3)), the layout the TMA store reads
-          const uint32_t buf = region + (nstore & 1u) * 2048u;
-          if (lane == 0) bulk_wait_read<1>();
-          __syncwarp();
 #pragma unroll
           for (int j = 0; j < 4; ++j) {
+            const uint32_t off = rowoff + ((j ^ swz) << 4);
+            if (e.gate) {
+              uint4 w;
+              asm volatile("ld.shared.v4.b32 {%0, %1, %2, %3}, [%4];"
+                           : "=r"(w.x), "=r"(w.y), "=r"(w.z), "=r"(w.w)
+                           : "r"(abuf + off));
+              const bf16 *h = reinterpret_cast<const bf16 *>(&w);
+#pragma unroll
+              for (int jj = 0; jj < 8; ++jj) v[j * 8 + jj] *= __bfloat162float(h[jj]);
+            }
+            if (L.has_res) {
+              uint4 w;
+              asm volatile("ld.shared.v4.b32 {%0, %1, %2, %3}, [%4];"
+                           : "=r"(w.x), "=r"(w.y), "=r"(w.z), "=r"(w.w)
+                           : "r"(obuf + off));
+              const bf16 *h = reinterpret_cast<const bf16 *>(&w);
+#pragma unroll
+              for (int jj = 0; jj < 8; ++jj) v[j * 8 + jj] += __bfloat162float(h[jj]);
+            }
             uint32_t w[4];
 #pragma unroll
             for (int jj = 0; jj < 4; ++jj) {
               __nv_bfloat162 h2 = __floats2bfloat162_rn(v[j * 8 + 2 * jj], v[j * 8 + 2 * jj + 1]);
               w[jj] = *reinterpret_cast<uint32_t *>(&h2);
             }
-            const uint32_t dst = buf + lane * 64u + (uint32_t)((j ^ ((lane >> 1) & 3)) * 16);
-            asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(dst), "r"(w[0]), "r"(w[1]), "r"(w[2]),
-                         "r"(w[3])
+            asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(obuf + off), "r"(w[0]), "r"(w[1]),
+                         "r"(w[2]), "r"(w[3])
                          : "memory");
           }
           fence_proxy_async();
           __syncwarp();
           if (lane == 0) {  // rows and columns past the tensor are clipped by TMA
-            if (tma_store == 1) {
-              tma_store_3d(&tmC, buf, nb, mrow0, tc.b);
+            if (L.tma_store == 1) {
+              tma_store_3d(&tmC, obuf, nb, mrow0, tc.b);
             } else {
               // 4-D view of a two-level output map (see the host side for the order)
               const int md = e.map.mdiv >= (1ll << 31) ? g.M : (int)e.map.mdiv;
-              if (tma_store == 2) tma_store_4d(&tmC, buf, 0, mrow0 % md, nb >> 5, mrow0 / md);
-              else tma_store_4d(&tmC, buf, 0, nb >> 5, mrow0 % md, mrow0 / md);
+              if (L.tma_store == 2) tma_store_4d(&tmC, obuf, 0, mrow0 % md, nb >> 5, mrow0 / md);
+              else tma_store_4d(&tmC, obuf, 0, nb >> 5, mrow0 % md, mrow0 / md);
             }
             bulk_commit();
           }
-          ++nstore;
+          if (op_bytes) {
+            // operands of the next chunk into the other slot, once the store
+            // of chunk k - 1 (the slot's last reader) has read it
+            advance();
+            if (lane == 0) {
+              bulk_wait_read<1>();
+              request(k + 1);
+            }
+          }
+          ++k;
         }
-      } else {
-        for (int c0 = slot * 32; rows && c0 < BN; c0 += 128) {
+        if (!ok) break;
+        if (tc.nk > 0) {
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&acce_bar[ab]);
+          ++ai;
+        }
+        if (s_abort) break;
+      }
+      if (lane == 0) {
+        // drain (after an abort): operand tiles requested but not consumed
+        for (uint32_t kk = k; kk < requested; ++kk) {
+          const uint64_t t0 = globaltimer_ns();
+          while (!mbar_try_wait(&op_bar[ew][kk & 1u], (kk >> 1) & 1u) && globaltimer_ns() - t0 < WAIT_LIMIT_NS) {
+          }
+        }
+      }
+    } else {
+      for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const TileCoord tc = decode_tile(g, t, BN);
+        const uint32_t ab = ai & 1u, u = ai >> 1;
+        const int mrow0 = tc.m0 + quarter * 32;
+        bool have = false;
+        if (tc.nk > 0) {
+          have = mbar_wait(&accf_bar[ab], u & 1u, &s_abort);
+          have = __all_sync(0xffffffffu, have);
+          if (!have) break;
+          tc_fence_after();
+        }
+        for (int c0 = slot * 32; c0 < BN && mrow0 < g.M; c0 += 128) {
           if (tc.n0 + c0 >= g.N) break;
           if (have) {
             uint32_t r[32];
             tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + ab * BN + (uint32_t)c0, r);
 #pragma unroll
-            for (int jj = 0; jj < 32; ++jj) mine[lane * C::LDS + jj] = __uint_as_float(r[jj]);
+            for (int jj = 0; jj < 32; ++jj) mine[lane * 33 + jj] = __uint_as_float(r[jj]);
           } else {
-            for (int jj = 0; jj < 32; ++jj) mine[lane * C::LDS + jj] = 0.f;
+            for (int jj = 0; jj < 32; ++jj) mine[lane * 33 + jj] = 0.f;
           }
           __syncwarp();
           epi_chunk(g, mine, lane, mrow0, tc.n0 + c0, tc.b, tc.split);
           __syncwarp();
         }
+        if (tc.nk > 0) {
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&acce_bar[ab]);
+          ++ai;
+        }
+        if (s_abort) break;
       }
-      if (tc.nk > 0) {
-        tc_fence_before();
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&acce_bar[ab]);
-        ++ai;
-      }
-      if (s_abort) break;
     }
     if (lane == 0) bulk_wait_all();
     __syncwarp();
@@ -652,9 +779,9 @@ bool make_tmap4(CUtensorMap *tm, const void *base, uint64_t d0, uint64_t d1, uin
   return r == CUDA_SUCCESS;
 }
 
-template <int BN, int STAGES, bool AMN, bool BMN>
+template <int BN, bool AMN, bool BMN>
 cudaError_t launch_tc(const GemmOp &g, cudaStream_t s) {
-  using C = TcCfg<BN, STAGES, AMN, BMN>;
+  using C = TcCfg<BN, AMN, BMN>;
   CUtensorMap ta, tb;
   bool ok = AMN ? make_tmap(&ta, g.A, g.M, g.K, g.batch, g.lda, g.a_bs, 64, 64)
                 : make_tmap(&ta, g.A, g.K, g.M, g.batch, g.lda, g.a_bs, 64, BM);
@@ -664,8 +791,9 @@ cudaError_t launch_tc(const GemmOp &g, cudaStream_t s) {
   // TMA-store epilogue.  Kind 1: plain row-major bf16 output (3-D map over
   // n, m, batch).  Kind 2: a two-level map with 32-wide column groups,
   // offset = (n / 32) s_n1 + n % 32 + (m / mdiv) s_m1 + (m % mdiv) s_m0, stored
-  // through a 4-D map whose box is one warp's 32 x 32 sub-tile.  Every operand
-  // the epilogue reads needs 16-byte aligned row vectors.
+  // through a 4-D map whose box is one warp's 32 x 32 sub-tile.  The row
+  // operands (residual, gate or ReLU reference) arrive by TMA as 32 x 32
+  // tiles too, so they need 16-byte aligned bases and row strides.
   const Epi &e = g.e;
   auto a16 = [](const void *p) { return ((uintptr_t)p & 15u) == 0; };
   const bool operands_ok = !e.partial && !e.c_f32 && !e.accumulate && !(e.gate && e.relu_ref) && a16(e.C) &&
@@ -675,13 +803,15 @@ cudaError_t launch_tc(const GemmOp &g, cudaStream_t s) {
                            (!e.gate || (a16(e.gate) && e.gate_ld % 8 == 0)) &&
                            (!e.bias || (a16(e.bias) && e.bias_n0 % 4 == 0));
   const bool plain = e.map.mdiv >= (1ll << 31) && e.map.ndiv >= (1ll << 31) && e.map.s_n0 == 1;
-  int tstore = 0;
-  CUtensorMap tc;
+  TcLaunch L{};
+  CUtensorMap tc, topa, tres;
   std::memset(&tc, 0, sizeof(tc));
+  std::memset(&topa, 0, sizeof(topa));
+  std::memset(&tres, 0, sizeof(tres));
   if (operands_ok && plain && e.map.s_m0 % 8 == 0 && (g.batch == 1 || e.c_bstride % 8 == 0)) {
     if (make_tmap(&tc, e.C, g.N, g.M, g.batch, e.map.s_m0, g.batch > 1 ? e.c_bstride : 0, 32, 32,
                   CU_TENSOR_MAP_SWIZZLE_64B))
-      tstore = 1;
+      L.tma_store = 1;
   } else if (operands_ok && !plain && g.batch == 1 && !e.residual && e.map.ndiv == 32 && e.map.s_n0 == 1 &&
              g.N % 32 == 0 && e.map.s_n1 % 8 == 0 && e.map.s_m0 % 8 == 0 &&
              (e.map.mdiv >= (1ll << 31) || (e.map.mdiv % 32 == 0 && g.M % e.map.mdiv == 0 && e.map.s_m1 % 8 == 0))) {
@@ -694,17 +824,40 @@ cudaError_t launch_tc(const GemmOp &g, cudaStream_t s) {
     const uint64_t nhi = (uint64_t)g.N / 32, mhi = (uint64_t)g.M / md;
     if (s_mlo >= 32 && s_mlo <= s_nhi && s_nhi >= s_mlo * md && s_mhi >= s_nhi * nhi) {
       if (make_tmap4(&tc, e.C, 32, md, nhi, mhi, s_mlo, s_nhi, s_mhi, 32, 32, 1, 1, CU_TENSOR_MAP_SWIZZLE_64B))
-        tstore = 2;
+        L.tma_store = 2;
     } else if (s_nhi >= 32 && s_nhi <= s_mlo && s_mlo >= s_nhi * nhi && s_mhi >= s_mlo * md) {
       if (make_tmap4(&tc, e.C, 32, nhi, md, mhi, s_nhi, s_mlo, s_mhi, 32, 1, 32, 1, CU_TENSOR_MAP_SWIZZLE_64B))
-        tstore = 3;
+        L.tma_store = 3;
     }
   }
+  if (L.tma_store) {
+    const void *opa = e.gate ? e.gate : e.relu_ref;
+    const int64_t opa_ld = e.gate ? e.gate_ld : e.relu_ld;
+    bool ops = true;
+    if (opa) {
+      ops = make_tmap(&topa, opa, g.N, g.M, 1, opa_ld, 0, 32, 32, CU_TENSOR_MAP_SWIZZLE_64B);
+      L.has_opa = 1;
+    }
+    if (ops && e.residual) {
+      ops = make_tmap(&tres, e.residual, g.N, g.M, g.batch, e.map.s_m0, g.batch > 1 ? e.c_bstride : 0, 32, 32,
+                      CU_TENSOR_MAP_SWIZZLE_64B);
+      L.has_res = 1;
+    }
+    if (!ops) L.tma_store = L.has_opa = L.has_res = 0;
+  }
+  L.epi_bytes = epi_warp_bytes(L.has_opa);
+  L.stages = std::min(MAX_STAGES, (SMEM_LIMIT - 2048 - EPI_WARPS * L.epi_bytes) / C::STAGE_BYTES);
+  if (L.stages < 2) return cudaErrorInvalidValue;
+  const int smem = L.stages * C::STAGE_BYTES + EPI_WARPS * L.epi_bytes + 1024;
+  // more than half of the SM's shared memory: one resident CTA per SM, so a
+  // CTA's TMEM allocation never waits on another CTA's
+  if (smem <= SMEM_LIMIT / 2 + 1024 || smem > SMEM_LIMIT - 2048) return cudaErrorInvalidValue;
   static bool attr_set = false;
   if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(gemm_tc_kernel<BN, STAGES, AMN, BMN>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
-    if (e != cudaSuccess) return e;
+    // the opt-in limit covers static shared memory (the barriers) as well
+    cudaError_t err = cudaFuncSetAttribute(gemm_tc_kernel<BN, AMN, BMN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           SMEM_LIMIT - 2048);
+    if (err != cudaSuccess) return err;
     attr_set = true;
   }
   const long long tiles =
@@ -715,20 +868,20 @@ cudaError_t launch_tc(const GemmOp &g, cudaStream_t s) {
   double cbytes = g.e.partial ? 4.0 * g.splits : (g.e.c_f32 ? (g.e.accumulate ? 8.0 : 4.0) : 2.0);
   cbytes += 2.0 * ((g.e.residual ? 1 : 0) + (g.e.gate ? 1 : 0) + (g.e.relu_ref ? 1 : 0) + (g.e.aux ? 1 : 0));
   Prof p(prof_detail() ? prof_name("g%dx%dx%d*%ds%dn%d%s%se%d", (int)g.M, (int)g.N, (int)g.K, (int)g.batch, g.splits,
-                                    BN, AMN ? "T" : "", BMN ? "t" : "", tstore)
+                                    BN, AMN ? "T" : "", BMN ? "t" : "", L.tma_store)
                       : "gemm_tc",
          s, 2.0 * g.M * g.N * (double)g.K * g.batch,
          g.batch * (2.0 * ((double)g.M * g.K + (double)g.N * g.K) + cbytes * g.M * g.N));
-  gemm_tc_kernel<BN, STAGES, AMN, BMN><<<grid, 576, C::SMEM, s>>>(ta, tb, tc, g, tstore);
+  gemm_tc_kernel<BN, AMN, BMN><<<grid, 32 * (2 + EPI_WARPS), smem, s>>>(ta, tb, tc, topa, tres, g, L);
   return cudaGetLastError();
 }
 
-template <int BN, int STAGES>
+template <int BN>
 cudaError_t dispatch_major(const GemmOp &g, cudaStream_t s) {
   if (g.a_mn) {
-    return g.b_mn ? launch_tc<BN, STAGES, true, true>(g, s) : launch_tc<BN, STAGES, true, false>(g, s);
+    return g.b_mn ? launch_tc<BN, true, true>(g, s) : launch_tc<BN, true, false>(g, s);
   }
-  return g.b_mn ? launch_tc<BN, STAGES, false, true>(g, s) : launch_tc<BN, STAGES, false, false>(g, s);
+  return g.b_mn ? launch_tc<BN, false, true>(g, s) : launch_tc<BN, false, false>(g, s);
 }
 
 }  // namespace
@@ -758,11 +911,10 @@ bool gemm_tc_supported(const GemmOp &g) {
 
 cudaError_t gemm_tc_bf16(const GemmOp &g, cudaStream_t s) {
   if (!gemm_tc_supported(g)) return cudaErrorInvalidValue;
-  // one persistent CTA per SM; the stage ring fills the shared memory the
-  // epilogue staging leaves free
-  if (g.N > 128 && g.N % 256 == 0) return dispatch_major<256, 3>(g, s);
-  if (g.N > 64) return dispatch_major<128, 4>(g, s);
-  return dispatch_major<64, 6>(g, s);
+  // one persistent CTA per SM
+  if (g.N > 128 && g.N % 256 == 0) return dispatch_major<256>(g, s);
+  if (g.N > 64) return dispatch_major<128>(g, s);
+  return dispatch_major<64>(g, s);
 }
 
 }  // namespace evo
