@@ -665,6 +665,10 @@ cudaError_t attn_fwd(const AttnArgs &a, int use_bf16, cudaStream_t s) {
   const double ts = use_bf16 ? 2.0 : 4.0;
   const double io = (double)a.B1 * a.H * a.c * ((double)a.X * 4 + (double)a.Y * 2) * ts +
                     (a.bias ? 4.0 * a.H * (double)a.X * a.Y : 0.0);
+  if (use_bf16 && attn_tc_supported(a)) {
+    const cudaError_t e = attn_fwd_tc_launch(a, s, 4.0 * inner, io);
+    if (e != cudaErrorNotSupported) return e;
+  }
   Prof p(use_bf16 ? "attn_fwd_mma" : "attn_fwd_simt", s, 4.0 * inner, io);
   if (use_bf16) {
     if (!mma_ok(a)) return cudaErrorInvalidValue;

@@ -62,6 +62,12 @@ struct AttnArgs {
   float *dbias;          // fp32 [h*sBh + x*sBx + y] accumulated
 };
 cudaError_t attn_fwd(const AttnArgs &a, int use_bf16, cudaStream_t s);
+// tcgen05 forward (bf16, head dim 32, at most 256 keys, 16-byte aligned rows);
+// cudaErrorNotSupported (nothing launched) when TMA cannot describe the views.
+bool attn_tc_supported(const AttnArgs &a);
+cudaError_t attn_fwd_tc_launch(const AttnArgs &a, cudaStream_t s, double flops, double bytes);
+// Reads and clears the error word of the tcgen05 attention kernels; synchronous.
+cudaError_t attn_tc_error_read_clear(int *out);
 cudaError_t attn_bwd(const AttnArgs &a, int use_bf16, cudaStream_t s);
 
 // Global column attention (extra-MSA stack): single-head k, v.
