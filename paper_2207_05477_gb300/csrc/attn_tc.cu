@@ -3,15 +3,19 @@
 // attentions of the Evoformer block at training-crop sizes (AF2 Alg. 7, 8,
 // 13, 14; the fused operator of Sec. 3.1).
 //
-// One CTA of four warps per (128 queries, head, batch item):
-//   * TMA brings Q [128 x 32], K and V [Ypad x 32] (64-byte swizzle) and the
-//     pair-bias tile in 32-key chunks (fp32, 128-byte swizzle, two buffers);
+// One CTA of eight warps per (128 queries, head, batch item):
+//   * TMA brings Q [128 x 32], K and V [Ypad x 32] (64-byte swizzle); each
+//     warp streams its 32 rows of the pair-bias tile in 32-key chunks (fp32,
+//     128-byte swizzle) through a ring of its own, so the softmax warps never
+//     wait for one another;
 //   * one tcgen05.mma pair computes S = Q K^T (M 128, N Ypad, K 32) into
 //     TMEM columns [0, Ypad);
-//   * thread = query row (warp w reads TMEM lanes 32w..): pass 1 turns S into
-//     log2-domain logits (scale, pair bias, key mask) stored back in place and
-//     takes the row max; pass 2 writes P = 2^(logit - max) as bf16 pairs into
-//     TMEM columns [0, Ypad / 2) (over logits already consumed) and sums it;
+//   * thread = query row (warps w and w + 4 read TMEM lanes 32(w % 4).. and
+//     take half of the key chunks each): pass 1 turns S into log2-domain
+//     logits (scale, pair bias, key mask) stored back in place and takes the
+//     row max; pass 2 writes P = 2^(logit - max) as bf16 pairs into TMEM
+//     columns [0, Ypad / 2) (over logits every warp has consumed) and sums
+//     it; partial maxima and sums meet in shared memory;
 //   * tcgen05.mma with A = P from TMEM and B = V from shared memory
 //     accumulates O = P V (M 128, N 32, K Ypad) in TMEM columns [128, 160);
 //   * the epilogue divides by the row sum, writes the attention output and its
@@ -66,16 +70,28 @@ constexpr int AT_C = 32;
 constexpr int AT_MAXKEYS = 256;
 constexpr int AT_TMEM_COLS = 256;
 constexpr int AT_O_COL = 128;  // O accumulator columns [128, 160)
+constexpr int AT_WARPS = 8;    // two per TMEM lane quarter, splitting the key chunks
 // dynamic shared memory (offsets from a 1 KB aligned base)
 constexpr int AT_Q_OFF = 0;                               // 128 x 64 B
 constexpr int AT_K_OFF = AT_Q_OFF + AT_QROWS * 64;        // 256 x 64 B
 constexpr int AT_V_OFF = AT_K_OFF + AT_MAXKEYS * 64;      // 256 x 64 B
-constexpr int AT_B_OFF = AT_V_OFF + AT_MAXKEYS * 64;      // 2 x 128 x 128 B (fp32 bias chunks)
-constexpr int AT_M_OFF = AT_B_OFF + 2 * AT_QROWS * 128;   // 256 floats: additive key mask
+// pair bias: per warp a ring of AT_BRING [32 rows x 32 keys] fp32 chunks (4 KB each)
+constexpr int AT_BRING = 2;
+constexpr int AT_B_OFF = AT_V_OFF + AT_MAXKEYS * 64;
+constexpr int AT_R_OFF = AT_B_OFF + AT_WARPS * AT_BRING * 4096;  // [2][128] row max, [2][128] row sum
+constexpr int AT_M_OFF = AT_R_OFF + 4 * AT_QROWS * 4;            // 256 floats: additive key mask
 constexpr int AT_SMEM = AT_M_OFF + AT_MAXKEYS * 4 + 1024;
 
 constexpr float NEG_INF_F = -__builtin_huge_valf();
 constexpr float POS_INF_F = __builtin_huge_valf();
+
+// 2^x on the SFU (ex2.approx: relative error about 2^-22, far below the bf16
+// rounding P receives next)
+__device__ __forceinline__ float ex2(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
 
 // Coordinates of a q/k/v tile in its 4-D map (d, then h / row / batch ordered by stride).
 struct QkvPos {
@@ -96,12 +112,12 @@ __device__ __forceinline__ void tile_coords(const QkvPos &p, int row, int h, int
   c[p.b] = b;
 }
 
-__global__ void __launch_bounds__(128) attn_fwd_tc(const __grid_constant__ CUtensorMap tmQ,
-                                                   const __grid_constant__ CUtensorMap tmK,
-                                                   const __grid_constant__ CUtensorMap tmV,
-                                                   const __grid_constant__ CUtensorMap tmB, AttnTcArgs A) {
+__global__ void __launch_bounds__(AT_WARPS * 32) attn_fwd_tc(const __grid_constant__ CUtensorMap tmQ,
+                                                             const __grid_constant__ CUtensorMap tmK,
+                                                             const __grid_constant__ CUtensorMap tmV,
+                                                             const __grid_constant__ CUtensorMap tmB, AttnTcArgs A) {
   extern __shared__ uint8_t dsm[];
-  __shared__ __align__(8) uint64_t bar_qk, bar_v, bar_s, bar_o, bar_b[2];
+  __shared__ __align__(8) uint64_t bar_qk, bar_v, bar_s, bar_o, bar_b[AT_WARPS][AT_BRING];
   __shared__ uint32_t tmem_slot;
   __shared__ volatile int s_abort;
   const AttnArgs &a = A.a;
@@ -109,17 +125,22 @@ __global__ void __launch_bounds__(128) attn_fwd_tc(const __grid_constant__ CUten
   const uint32_t base = (raw + 1023u) & ~1023u;
   uint8_t *gbase = dsm + (base - raw);
   float *maskadd = reinterpret_cast<float *>(gbase + AT_M_OFF);
+  float *red = reinterpret_cast<float *>(gbase + AT_R_OFF);  // [0..255] max, [256..511] sum
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, tid = threadIdx.x;
+  const int quarter = warp & 3, half = warp >> 2;
   const int x0 = blockIdx.x * AT_QROWS, h = blockIdx.y, b = blockIdx.z;
   const int ypad = A.ypad, nch = ypad / 32;
+  // this warp's key chunks [c_lo, c_hi)
+  const int c_mid = (nch + 1) / 2;
+  const int c_lo = half ? c_mid : 0, c_hi = half ? nch : c_mid;
 
   if (tid == 0) {
     mbar_init(&bar_qk, 1);
     mbar_init(&bar_v, 1);
     mbar_init(&bar_s, 1);
     mbar_init(&bar_o, 1);
-    mbar_init(&bar_b[0], 1);
-    mbar_init(&bar_b[1], 1);
+    for (int w = 0; w < AT_WARPS; ++w)
+      for (int k = 0; k < AT_BRING; ++k) mbar_init(&bar_b[w][k], 1);
     s_abort = 0;
     fence_mbar_init();
   }
@@ -129,19 +150,23 @@ __global__ void __launch_bounds__(128) attn_fwd_tc(const __grid_constant__ CUten
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
-  // additive key mask: 0 for a valid key, -inf for a masked or padding key
-  for (int y = tid; y < ypad; y += blockDim.x) {
-    bool ok = y < a.Y;
-    if (ok && a.mask) ok = a.mask[(int64_t)b * a.sMb + (int64_t)y * a.sMy] != 0.f;
-    maskadd[y] = ok ? 0.f : NEG_INF_F;
-  }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = tmem_slot;
-  // thread 0's record of what it put in flight (drained after an abort)
-  int bias_issued = 0;
+  // what this thread put in flight (drained after an abort): lane 0 of each
+  // warp streams the pair bias of its rows and chunks; thread 0 issues the rest
+  int bias_issued = 0, bias_done = 0;
   bool s_issued = false, o_issued = false;
+  const uint32_t bring = base + AT_B_OFF + (uint32_t)warp * AT_BRING * 4096u;
+  auto bias_chunk = [&](int j) {  // lane 0: chunk j (keys 32j..) of this warp's rows, slot (j - c_lo) % ring
+    const int k = (j - c_lo) % AT_BRING;
+    mbar_arrive_expect_tx(&bar_b[warp][k], 4096);
+    tma_load_3d(bring + k * 4096u, &tmB, j * 32, x0 + quarter * 32, h, &bar_b[warp][k]);
+    ++bias_issued;
+  };
+  if (A.has_bias && lane == 0)
+    for (int j = c_lo; j < c_hi && j < c_lo + AT_BRING; ++j) bias_chunk(j);
 
   if (tid == 0) {
     int c[4];
@@ -152,13 +177,16 @@ __global__ void __launch_bounds__(128) attn_fwd_tc(const __grid_constant__ CUten
     tma_load_4d(base + AT_K_OFF, &tmK, c[0], c[1], c[2], c[3], &bar_qk);
     mbar_arrive_expect_tx(&bar_v, (uint32_t)(ypad * 64));
     tma_load_4d(base + AT_V_OFF, &tmV, c[0], c[1], c[2], c[3], &bar_v);
-    if (A.has_bias) {
-      for (int j = 0; j < 2 && j < nch; ++j) {
-        mbar_arrive_expect_tx(&bar_b[j], AT_QROWS * 128);
-        tma_load_3d(base + AT_B_OFF + j * AT_QROWS * 128, &tmB, j * 32, x0, h, &bar_b[j]);
-        ++bias_issued;
-      }
-    }
+  }
+  // additive key mask (0 for a valid key, -inf for a masked or padding key),
+  // read while the copies are in flight
+  for (int y = tid; y < ypad; y += blockDim.x) {
+    bool valid = y < a.Y;
+    if (valid && a.mask) valid = a.mask[(int64_t)b * a.sMb + (int64_t)y * a.sMy] != 0.f;
+    maskadd[y] = valid ? 0.f : NEG_INF_F;
+  }
+  __syncthreads();
+  if (tid == 0) {
     // S = Q K^T
     if (mbar_wait(&bar_qk, 0, &s_abort)) {
       tc_fence_after();
@@ -173,21 +201,22 @@ __global__ void __launch_bounds__(128) attn_fwd_tc(const __grid_constant__ CUten
       s_issued = true;
     }
   }
-  const int row = warp * 32 + lane;  // query row within the tile (TMEM lane)
-  const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
+  const int row = quarter * 32 + lane;  // query row within the tile (TMEM lane)
+  const uint32_t lane_base = tmem + ((uint32_t)(quarter * 32) << 16);
   const float sl2 = a.scale * EVO_LOG2E;
   // tcgen05.ld / st are warp-collective: every decision that guards them is
   // made uniform across the warp
   bool ok = __all_sync(0xffffffffu, mbar_wait(&bar_s, 0, &s_abort));
   tc_fence_after();
 
-  // pass 1: logits (log2 domain) in place, row max.  The loop runs the same
-  // number of times in every thread (it holds block barriers); a thread whose
-  // wait gave up skips the arithmetic.
+  // pass 1 over this warp's chunks: logits (log2 domain) in place, partial row max
   float mx = NEG_INF_F;
-  for (int j = 0; j < nch; ++j) {
-    const int sl = j & 1;
-    if (A.has_bias) ok = __all_sync(0xffffffffu, ok && mbar_wait(&bar_b[sl], (uint32_t)((j >> 1) & 1), &s_abort));
+  for (int j = c_lo; j < c_hi; ++j) {
+    const int sl = (j - c_lo) % AT_BRING;
+    if (A.has_bias)
+      ok = __all_sync(0xffffffffu,
+                      ok && mbar_wait(&bar_b[warp][sl], (uint32_t)(((j - c_lo) / AT_BRING) & 1), &s_abort));
+    if (ok) bias_done = j - c_lo + 1;
     if (ok) {
       uint32_t r[32];
       tmem_ld32(lane_base + (uint32_t)(j * 32), r);
@@ -202,18 +231,18 @@ __global__ void __launch_bounds__(128) attn_fwd_tc(const __grid_constant__ CUten
         v[4 * q + 3] = __uint_as_float(r[4 * q + 3]) * sl2 + mv.w;
       }
       if (A.has_bias) {
-        // row `row` of the 128-byte-swizzled chunk: 16-byte piece k at k ^ (row & 7)
-        const uint32_t rb = base + AT_B_OFF + sl * AT_QROWS * 128 + row * 128;
+        // this lane's row of the warp's 128-byte-swizzled chunk: 16-byte piece k at k ^ (lane & 7)
+        const uint32_t rb = bring + sl * 4096u + lane * 128u;
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
           float4 bv;
           asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
                        : "=f"(bv.x), "=f"(bv.y), "=f"(bv.z), "=f"(bv.w)
-                       : "r"(rb + (uint32_t)((k ^ (row & 7)) << 4)));
-          v[4 * k] += bv.x * EVO_LOG2E;
-          v[4 * k + 1] += bv.y * EVO_LOG2E;
-          v[4 * k + 2] += bv.z * EVO_LOG2E;
-          v[4 * k + 3] += bv.w * EVO_LOG2E;
+                       : "r"(rb + (uint32_t)((k ^ (lane & 7)) << 4)));
+          v[4 * k] = fmaf(bv.x, EVO_LOG2E, v[4 * k]);
+          v[4 * k + 1] = fmaf(bv.y, EVO_LOG2E, v[4 * k + 1]);
+          v[4 * k + 2] = fmaf(bv.z, EVO_LOG2E, v[4 * k + 2]);
+          v[4 * k + 3] = fmaf(bv.w, EVO_LOG2E, v[4 * k + 3]);
         }
       }
 #pragma unroll
@@ -224,34 +253,48 @@ __global__ void __launch_bounds__(128) attn_fwd_tc(const __grid_constant__ CUten
       tmem_st32(lane_base + (uint32_t)(j * 32), r);
     }
     if (A.has_bias) {
-      // the buffer is refilled with chunk j + 2 once every row has read it
-      __syncthreads();
-      if (tid == 0 && !s_abort && j + 2 < nch) {
-        mbar_arrive_expect_tx(&bar_b[sl], AT_QROWS * 128);
-        tma_load_3d(base + AT_B_OFF + sl * AT_QROWS * 128, &tmB, (j + 2) * 32, x0, h, &bar_b[sl]);
-        ++bias_issued;
+      // the slot is refilled once the warp has read it
+      __syncwarp();
+      if (lane == 0 && ok && j + AT_BRING < c_hi) bias_chunk(j + AT_BRING);
+    }
+  }
+  red[half * AT_QROWS + row] = mx;
+  tmem_wait_st();
+  __syncthreads();
+  mx = fmaxf(red[row], red[AT_QROWS + row]);
+
+  // pass 2: P = 2^(logit - max) of this warp's chunks, held as bf16 pairs
+  // until every warp has read its logits (P for chunk j lands in columns
+  // [16j, 16j + 16), over logits of chunk j / 2, which may be the other warp's)
+  const float muse = mx == NEG_INF_F ? 0.f : mx;
+  float l = 0.f;
+  uint32_t pk[4][16];
+#pragma unroll
+  for (int t = 0; t < 4; ++t) {
+    const int j = c_lo + t;
+    if (ok && j < c_hi) {
+      uint32_t r[32];
+      tmem_ld32(lane_base + (uint32_t)(j * 32), r);
+#pragma unroll
+      for (int i = 0; i < 16; ++i) {
+        const float p0 = ex2(__uint_as_float(r[2 * i]) - muse);
+        const float p1 = ex2(__uint_as_float(r[2 * i + 1]) - muse);
+        l += p0 + p1;
+        __nv_bfloat162 hv = __floats2bfloat162_rn(p0, p1);
+        pk[t][i] = *reinterpret_cast<uint32_t *>(&hv);
       }
     }
   }
-  tmem_wait_st();
-
-  // pass 2: P = 2^(logit - max) as bf16 pairs into columns [0, ypad / 2), row sum
-  const float muse = mx == NEG_INF_F ? 0.f : mx;
-  float l = 0.f;
-  for (int j = 0; j < nch && ok; ++j) {
-    uint32_t r[32];
-    tmem_ld32(lane_base + (uint32_t)(j * 32), r);
-    uint32_t pk[16];
+  red[2 * AT_QROWS + half * AT_QROWS + row] = l;
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
 #pragma unroll
-    for (int i = 0; i < 16; ++i) {
-      const float p0 = exp2f(__uint_as_float(r[2 * i]) - muse);
-      const float p1 = exp2f(__uint_as_float(r[2 * i + 1]) - muse);
-      l += p0 + p1;
-      __nv_bfloat162 hv = __floats2bfloat162_rn(p0, p1);
-      pk[i] = *reinterpret_cast<uint32_t *>(&hv);
-    }
-    tmem_st16(lane_base + (uint32_t)(j * 16), pk);
+  for (int t = 0; t < 4; ++t) {
+    const int j = c_lo + t;
+    if (ok && j < c_hi) tmem_st16(lane_base + (uint32_t)(j * 16), pk[t]);
   }
+  l = red[2 * AT_QROWS + row] + red[3 * AT_QROWS + row];
   tmem_wait_st();
   tc_fence_before();
   __syncthreads();
@@ -269,44 +312,57 @@ __global__ void __launch_bounds__(128) attn_fwd_tc(const __grid_constant__ CUten
       o_issued = true;
     }
   }
+  // epilogue: the two warps of a quarter take 16 output channels each; the
+  // gate row is requested before the wait for O
+  const int x = x0 + row;
+  const int d0 = half * 16;
+  uint4 gwv[2] = {make_uint4(0, 0, 0, 0), make_uint4(0, 0, 0, 0)};
+  if (x < a.X) {
+    const bf16 *gp = (const bf16 *)a.g + (int64_t)b * a.sQb + (int64_t)x * a.sQx + h * AT_C + d0;
+    gwv[0] = *reinterpret_cast<const uint4 *>(gp);
+    gwv[1] = *reinterpret_cast<const uint4 *>(gp + 8);
+  }
   __syncthreads();
   ok = __all_sync(0xffffffffu, ok && !s_abort && mbar_wait(&bar_o, 0, &s_abort));
   tc_fence_after();
-
-  const int x = x0 + row;
-  uint32_t r[32];
-  if (ok) tmem_ld32(lane_base + AT_O_COL, r);
+  uint32_t r[16];
+  if (ok) tmem_ld16(lane_base + AT_O_COL + (uint32_t)d0, r);
   if (ok && x < a.X) {
     const float inv = l > 0.f ? 1.f / l : 0.f;
-    const bf16 *gp = (const bf16 *)a.g + (int64_t)b * a.sQb + (int64_t)x * a.sQx + h * AT_C;
-    bf16 *op = (bf16 *)a.o_att + (int64_t)b * a.sOb + (int64_t)x * a.sOx + h * AT_C;
-    bf16 *gop = (bf16 *)a.o_gate + (int64_t)b * a.sOb + (int64_t)x * a.sOx + h * AT_C;
+    bf16 *op = (bf16 *)a.o_att + (int64_t)b * a.sOb + (int64_t)x * a.sOx + h * AT_C + d0;
+    bf16 *gop = (bf16 *)a.o_gate + (int64_t)b * a.sOb + (int64_t)x * a.sOx + h * AT_C + d0;
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const uint4 gw = *reinterpret_cast<const uint4 *>(gp + q * 8);
+    for (int q = 0; q < 2; ++q) {
+      const uint4 gw = gwv[q];
       const bf16 *gh = reinterpret_cast<const bf16 *>(&gw);
       uint4 ow, gow;
       uint32_t *o32 = reinterpret_cast<uint32_t *>(&ow), *g32 = reinterpret_cast<uint32_t *>(&gow);
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
-        const float v0 = __uint_as_float(r[q * 8 + 2 * i]) * inv, v1 = __uint_as_float(r[q * 8 + 2 * i + 1]) * inv;
+        const float v0 = __uint_as_float(r[q * 8 + 2 * i]) * inv;
+        const float v1 = __uint_as_float(r[q * 8 + 2 * i + 1]) * inv;
         __nv_bfloat162 o2 = __floats2bfloat162_rn(v0, v1);
-        __nv_bfloat162 g2 = __floats2bfloat162_rn(v0 * __bfloat162float(gh[2 * i]), v1 * __bfloat162float(gh[2 * i + 1]));
+        __nv_bfloat162 g2 =
+            __floats2bfloat162_rn(v0 * __bfloat162float(gh[2 * i]), v1 * __bfloat162float(gh[2 * i + 1]));
         o32[i] = *reinterpret_cast<uint32_t *>(&o2);
         g32[i] = *reinterpret_cast<uint32_t *>(&g2);
       }
       *reinterpret_cast<uint4 *>(op + q * 8) = ow;
       *reinterpret_cast<uint4 *>(gop + q * 8) = gow;
     }
-    a.lse2[((int64_t)b * a.H + h) * a.X + x] = l > 0.f ? muse + log2f(l) : POS_INF_F;
+    if (half == 0) a.lse2[((int64_t)b * a.H + h) * a.X + x] = l > 0.f ? muse + log2f(l) : POS_INF_F;
   }
   // drain (after an abort) anything still in flight before the CTA exits
-  if (tid == 0 && s_abort) {
-    mbar_drain(&bar_qk, 0);
-    mbar_drain(&bar_v, 0);
-    for (int j = 0; j < bias_issued; ++j) mbar_drain(&bar_b[j & 1], (uint32_t)((j >> 1) & 1));
-    if (s_issued) mbar_drain(&bar_s, 0);
-    if (o_issued) mbar_drain(&bar_o, 0);
+  if (s_abort) {
+    if (tid == 0) {
+      mbar_drain(&bar_qk, 0);
+      mbar_drain(&bar_v, 0);
+      if (s_issued) mbar_drain(&bar_s, 0);
+      if (o_issued) mbar_drain(&bar_o, 0);
+    }
+    if (lane == 0)
+      for (int j = bias_done; j < bias_issued; ++j)
+        mbar_drain(&bar_b[warp][j % AT_BRING], (uint32_t)((j / AT_BRING) & 1));
   }
   tc_fence_before();
   __syncthreads();
@@ -375,7 +431,7 @@ cudaError_t attn_fwd_tc_launch(const AttnArgs &a, cudaStream_t s, double flops, 
   if (a.bias) {
     const uint64_t dims[3] = {(uint64_t)a.Y, (uint64_t)a.X, (uint64_t)a.H};
     const uint64_t st[2] = {(uint64_t)a.sBx * 4, (uint64_t)a.sBh * 4};
-    const uint32_t box[3] = {32, AT_QROWS, 1};
+    const uint32_t box[3] = {32, 32, 1};
     if (!make_tmap_nd(&tb, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, a.bias, dims, st, box, CU_TENSOR_MAP_SWIZZLE_128B))
       return cudaErrorNotSupported;
   }
@@ -387,7 +443,7 @@ cudaError_t attn_fwd_tc_launch(const AttnArgs &a, cudaStream_t s, double flops, 
   }
   dim3 grid((a.X + AT_QROWS - 1) / AT_QROWS, a.H, a.B1);
   Prof p("attn_fwd_tc", s, flops, bytes);
-  attn_fwd_tc<<<grid, 128, AT_SMEM, s>>>(tq, tk, tv, tb, A);
+  attn_fwd_tc<<<grid, AT_WARPS * 32, AT_SMEM, s>>>(tq, tk, tv, tb, A);
   return cudaGetLastError();
 }
 
