@@ -684,31 +684,47 @@ cudaError_t attn_fwd(const AttnArgs &a, int use_bf16, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+// mma.sync (bf16) or SIMT (fp32) backward: dq accumulates, unscaled, in fp32
+// with atomics and is then scaled into its destination.
+static cudaError_t attn_bwd_accumulating(const AttnArgs &a, int use_bf16, cudaStream_t s, double flops, double io) {
+  cudaError_t e = cudaMemsetAsync(a.dq_acc, 0, (size_t)a.B1 * a.X * a.H * a.c * sizeof(float), s);
+  if (e != cudaSuccess) return e;
+  {
+    Prof p(use_bf16 ? "attn_bwd_mma" : "attn_bwd_simt", s, flops, io, use_bf16 ? 1 : 2);
+    if (use_bf16) {
+      if (!mma_ok(a)) return cudaErrorInvalidValue;
+      dim3 grid((a.Y + 63) / 64, a.H, a.B1);
+      if (a.c <= 16) attn_bwd_mma<16><<<grid, 128, 0, s>>>(a);
+      else attn_bwd_mma<32><<<grid, 128, 0, s>>>(a);
+    } else {
+      dim3 gq((a.X + 127) / 128, a.H, a.B1), gk((a.Y + 127) / 128, a.H, a.B1);
+      if (a.c <= 8) {
+        attn_bwd_dq_simt<8><<<gq, 128, 0, s>>>(a);
+        attn_bwd_dkv_simt<8><<<gk, 128, 0, s>>>(a);
+      } else if (a.c <= 32) {
+        attn_bwd_dq_simt<32><<<gq, 128, 0, s>>>(a);
+        attn_bwd_dkv_simt<32><<<gk, 128, 0, s>>>(a);
+      } else {
+        return cudaErrorInvalidValue;
+      }
+    }
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return attn_dq_store(a, a.dq, use_bf16, s);
+}
+
 cudaError_t attn_bwd(const AttnArgs &a, int use_bf16, cudaStream_t s) {
   if (a.B1 <= 0 || a.X <= 0 || a.H <= 0) return cudaSuccess;
   const double inner = (double)a.B1 * a.H * a.X * (double)a.Y * a.c;
   const double ts = use_bf16 ? 2.0 : 4.0;
   const double io = (double)a.B1 * a.H * a.c * ((double)a.X * (2 * ts + 4) + (double)a.Y * 4 * ts) +
                     (a.bias ? 8.0 * a.H * (double)a.X * a.Y : 0.0);
-  Prof p(use_bf16 ? "attn_bwd_mma" : "attn_bwd_simt", s, 10.0 * inner, io, use_bf16 ? 1 : 2);
-  if (use_bf16) {
-    if (!mma_ok(a)) return cudaErrorInvalidValue;
-    dim3 grid((a.Y + 63) / 64, a.H, a.B1);
-    if (a.c <= 16) attn_bwd_mma<16><<<grid, 128, 0, s>>>(a);
-    else attn_bwd_mma<32><<<grid, 128, 0, s>>>(a);
-  } else {
-    dim3 gq((a.X + 127) / 128, a.H, a.B1), gk((a.Y + 127) / 128, a.H, a.B1);
-    if (a.c <= 8) {
-      attn_bwd_dq_simt<8><<<gq, 128, 0, s>>>(a);
-      attn_bwd_dkv_simt<8><<<gk, 128, 0, s>>>(a);
-    } else if (a.c <= 32) {
-      attn_bwd_dq_simt<32><<<gq, 128, 0, s>>>(a);
-      attn_bwd_dkv_simt<32><<<gk, 128, 0, s>>>(a);
-    } else {
-      return cudaErrorInvalidValue;
-    }
+  if (use_bf16 && attn_bwd_tc_supported(a)) {
+    const cudaError_t e = attn_bwd_tc_launch(a, s, 10.0 * inner, io);
+    if (e != cudaErrorNotSupported) return e;
   }
-  return cudaGetLastError();
+  return attn_bwd_accumulating(a, use_bf16, s, 10.0 * inner, io);
 }
 
 }  // namespace evo

@@ -372,6 +372,341 @@ __global__ void __launch_bounds__(AT_WARPS * 32) attn_fwd_tc(const __grid_consta
   }
 }
 
+// ------------------------------------------------------------------ backward
+// One CTA of eight warps per (head, batch item), all X <= 256 queries and
+// Y <= 256 keys.  Query tiles of 128 (qt) and key halves of 128 (kh):
+//   for kh: for qt:
+//     S = Q_qt K_kh^T, dP = dO_qt V_kh^T                     (TMEM [0,128), [128,256))
+//     P = 2^(logit - lse2), dS = P (dP - D)     thread = query row, two warps
+//                                                per TMEM lane quarter on 64 keys each
+//     P, dS (bf16) -> shared memory as the MN-major A operands of
+//       dV_kh += P^T dO_qt, dK_kh += dS^T Q_qt                (TMEM [256,288), [288,320))
+//     dS (bf16 pairs) -> TMEM [128,192) as the A operand of
+//       dQ_qt += dS K_kh                                      (TMEM [320 + 32 qt, ...))
+//     dbias[h][x][y] += dS (fp32 vector atomics, one warp per query row, read
+//       back from the shared dS copy so that a warp covers 128 contiguous keys)
+//   dK_kh, dV_kh -> k/v gradient rows (bf16); finally dQ -> q gradient rows.
+// Logit scale: S holds raw q.k; dQ and dK carry the softmax scale.
+constexpr int BT_TMEM_COLS = 512;
+constexpr int BT_S_COL = 0, BT_DP_COL = 128, BT_DK_COL = 256, BT_DV_COL = 288, BT_DQ_COL = 320;
+// dynamic shared memory (1 KB aligned base)
+constexpr int BT_Q_OFF = 0;                      // 2 x [128 q][64 B]
+constexpr int BT_DO_OFF = BT_Q_OFF + 2 * 8192;   // 2 x [128 q][64 B]
+constexpr int BT_K_OFF = BT_DO_OFF + 2 * 8192;   // 2 x [128 keys][64 B]
+constexpr int BT_V_OFF = BT_K_OFF + 2 * 8192;    // 2 x [128 keys][64 B]
+constexpr int BT_P_OFF = BT_V_OFF + 2 * 8192;    // [2 kb][2 mc][64 q][128 B]  (P^T operand)
+constexpr int BT_DS_OFF = BT_P_OFF + 32768;      // same layout (dS^T operand)
+constexpr int BT_B_OFF = BT_DS_OFF + 32768;      // per warp 2 x [32 rows][32 keys] fp32
+constexpr int BT_L_OFF = BT_B_OFF + AT_WARPS * 2 * 4096;  // lse2 [256], D [256], maskadd [256]
+constexpr int BT_SMEM = BT_L_OFF + 3 * 256 * 4 + 1024;
+
+struct AttnTcBwdArgs {
+  AttnArgs a;
+  QkvPos pq, pk, po;  // q / k, v / dO map dimension positions
+  int nq, nkh;        // query tiles of 128, key halves of 128
+  int has_bias;
+};
+
+// Byte offset of element (mn, k) in a [2 kb][2 mc][64 k][64 mn] bf16 tile
+// with the 128-byte swizzle (the MN-major operand layout, K = 128, MN = 128).
+__device__ __forceinline__ uint32_t mn_major_off(int mn, int k) {
+  const int kb = k >> 6, kr = k & 63, mc = mn >> 6, m = mn & 63;
+  return (uint32_t)(kb * 16384 + mc * 8192 + kr * 128 + ((((m >> 3) ^ (kr & 7)) & 7) << 4) + (m & 7) * 2);
+}
+
+__global__ void __launch_bounds__(AT_WARPS * 32, 1) attn_bwd_tc(const __grid_constant__ CUtensorMap tmQ,
+                                                                const __grid_constant__ CUtensorMap tmK,
+                                                                const __grid_constant__ CUtensorMap tmV,
+                                                                const __grid_constant__ CUtensorMap tmO,
+                                                                const __grid_constant__ CUtensorMap tmB,
+                                                                AttnTcBwdArgs A) {
+  extern __shared__ uint8_t dsm[];
+  __shared__ __align__(8) uint64_t bar_in, bar_sd, bar_mm, bar_b[AT_WARPS][2];
+  __shared__ uint32_t tmem_slot;
+  __shared__ volatile int s_abort;
+  const AttnArgs &a = A.a;
+  const uint32_t raw = smem_u32(dsm);
+  const uint32_t base = (raw + 1023u) & ~1023u;
+  uint8_t *gbase = dsm + (base - raw);
+  float *lse_s = reinterpret_cast<float *>(gbase + BT_L_OFF);
+  float *d_s = lse_s + 256;
+  float *maskadd = lse_s + 512;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, tid = threadIdx.x;
+  const int quarter = warp & 3, half = warp >> 2;
+  const int h = blockIdx.x, b = blockIdx.y;
+  const int nq = A.nq, nkh = A.nkh;
+
+  if (tid == 0) {
+    mbar_init(&bar_in, 1);
+    mbar_init(&bar_sd, 1);
+    mbar_init(&bar_mm, 1);
+    for (int w = 0; w < AT_WARPS; ++w) mbar_init(&bar_b[w][0], 1), mbar_init(&bar_b[w][1], 1);
+    s_abort = 0;
+    fence_mbar_init();
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                 "r"((uint32_t)BT_TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_slot;
+  bool in_issued = false;
+  int nsd = 0, nmm = 0;  // commits issued on bar_sd / bar_mm (thread 0)
+  if (tid == 0) {
+    int c[4];
+    mbar_arrive_expect_tx(&bar_in, (uint32_t)(nq * 2 * 8192 + nkh * 2 * 8192));
+    for (int qt = 0; qt < nq; ++qt) {
+      tile_coords(A.pq, qt * 128, h, b, c);
+      tma_load_4d(base + BT_Q_OFF + qt * 8192, &tmQ, c[0], c[1], c[2], c[3], &bar_in);
+      tile_coords(A.po, qt * 128, h, b, c);
+      tma_load_4d(base + BT_DO_OFF + qt * 8192, &tmO, c[0], c[1], c[2], c[3], &bar_in);
+    }
+    for (int kh = 0; kh < nkh; ++kh) {
+      tile_coords(A.pk, kh * 128, h, b, c);
+      tma_load_4d(base + BT_K_OFF + kh * 8192, &tmK, c[0], c[1], c[2], c[3], &bar_in);
+      tma_load_4d(base + BT_V_OFF + kh * 8192, &tmV, c[0], c[1], c[2], c[3], &bar_in);
+    }
+    in_issued = true;
+  }
+  // row statistics of the forward (padding rows get lse2 = +inf: P = 0) and the key mask
+  for (int i = tid; i < 256; i += blockDim.x) {
+    const bool xin = i < a.X;
+    lse_s[i] = xin ? a.lse2[((int64_t)b * a.H + h) * a.X + i] : POS_INF_F;
+    d_s[i] = xin ? a.Dsum[((int64_t)b * a.H + h) * a.X + i] : 0.f;
+    bool valid = i < a.Y;
+    if (valid && a.mask) valid = a.mask[(int64_t)b * a.sMb + (int64_t)i * a.sMy] != 0.f;
+    maskadd[i] = valid ? 0.f : NEG_INF_F;
+  }
+  __syncthreads();
+  bool ok = __all_sync(0xffffffffu, mbar_wait(&bar_in, 0, &s_abort));
+  const float sl2 = a.scale * EVO_LOG2E;
+  const uint32_t lane_base = tmem + ((uint32_t)(quarter * 32) << 16);
+  const uint32_t bring = base + BT_B_OFF + (uint32_t)warp * 2 * 4096u;
+  int bias_issued = 0, bias_done = 0;
+
+  for (int kh = 0; kh < nkh; ++kh) {
+    for (int qt = 0; qt < nq; ++qt) {
+      const int it = kh * nq + qt;  // sub-tile counter (barrier phases)
+      // this warp's pair-bias chunks: rows qt*128 + 32 quarter.., keys kh*128 + 64 half + 32 t
+      if (a.bias && lane == 0 && ok) {
+        for (int t = 0; t < 2; ++t) {
+          mbar_arrive_expect_tx(&bar_b[warp][t], 4096);
+          tma_load_3d(bring + t * 4096u, &tmB, kh * 128 + half * 64 + t * 32, qt * 128 + quarter * 32, h,
+                      &bar_b[warp][t]);
+          ++bias_issued;
+        }
+      }
+      if (tid == 0 && ok && !s_abort) {
+        tc_fence_after();
+        const uint32_t idesc = instr_desc(128, 128, false, false);
+#pragma unroll
+        for (int ks = 0; ks < AT_C / 16; ++ks) {
+          const uint64_t qd = smem_desc(base + BT_Q_OFF + qt * 8192 + ks * 32, 16, 512, 4);
+          const uint64_t kd = smem_desc(base + BT_K_OFF + kh * 8192 + ks * 32, 16, 512, 4);
+          mma_ss(tmem + BT_S_COL, qd, kd, idesc, ks > 0 ? 1u : 0u);
+        }
+#pragma unroll
+        for (int ks = 0; ks < AT_C / 16; ++ks) {
+          const uint64_t od = smem_desc(base + BT_DO_OFF + qt * 8192 + ks * 32, 16, 512, 4);
+          const uint64_t vd = smem_desc(base + BT_V_OFF + kh * 8192 + ks * 32, 16, 512, 4);
+          mma_ss(tmem + BT_DP_COL, od, vd, idesc, ks > 0 ? 1u : 0u);
+        }
+        mma_commit(&bar_sd);
+        ++nsd;
+      }
+      ok = __all_sync(0xffffffffu, ok && mbar_wait(&bar_sd, (uint32_t)(it & 1), &s_abort));
+      tc_fence_after();
+      const int row = quarter * 32 + lane;  // query row in the tile
+      const int xq = qt * 128 + row;
+      const float lse = lse_s[xq < 256 ? xq : 255], dd = d_s[xq < 256 ? xq : 255];
+      uint32_t pk[2][16];
+#pragma unroll
+      for (int t = 0; t < 2; ++t) {
+        const int cl = half * 2 + t;           // 32-key chunk within the key half
+        const int y0 = kh * 128 + cl * 32;     // first key of the chunk
+        if (a.bias) ok = __all_sync(0xffffffffu, ok && mbar_wait(&bar_b[warp][t], (uint32_t)((it)&1), &s_abort));
+        if (ok && a.bias) bias_done = 2 * it + t + 1;
+        if (ok) {
+          uint32_t sr[32], pr[32];
+          tmem_ld32(lane_base + BT_S_COL + (uint32_t)(cl * 32), sr);
+          tmem_ld32(lane_base + BT_DP_COL + (uint32_t)(cl * 32), pr);
+          float bv[32];
+          if (a.bias) {
+            const uint32_t rb = bring + t * 4096u + lane * 128u;
+#pragma unroll
+            for (int k = 0; k < 8; ++k)
+              asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+                           : "=f"(bv[4 * k]), "=f"(bv[4 * k + 1]), "=f"(bv[4 * k + 2]), "=f"(bv[4 * k + 3])
+                           : "r"(rb + (uint32_t)((k ^ (lane & 7)) << 4)));
+          } else {
+#pragma unroll
+            for (int k = 0; k < 32; ++k) bv[k] = 0.f;
+          }
+          float p[32], ds[32];
+#pragma unroll
+          for (int k = 0; k < 32; ++k) {
+            const float lg = fmaf(__uint_as_float(sr[k]), sl2, fmaf(bv[k], EVO_LOG2E, maskadd[y0 + k]));
+            p[k] = ex2(lg - lse);
+            ds[k] = p[k] * (__uint_as_float(pr[k]) - dd);
+          }
+          // P and dS into the MN-major operand tiles (element (key, query) at mn_major_off)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            uint32_t wp[4], wd[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+              __nv_bfloat162 a2 = __floats2bfloat162_rn(p[8 * j + 2 * i], p[8 * j + 2 * i + 1]);
+              __nv_bfloat162 d2 = __floats2bfloat162_rn(ds[8 * j + 2 * i], ds[8 * j + 2 * i + 1]);
+              wp[i] = *reinterpret_cast<uint32_t *>(&a2);
+              wd[i] = *reinterpret_cast<uint32_t *>(&d2);
+            }
+            const uint32_t off = mn_major_off(cl * 32 + 8 * j, row);
+            asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(base + BT_P_OFF + off), "r"(wp[0]),
+                         "r"(wp[1]), "r"(wp[2]), "r"(wp[3])
+                         : "memory");
+            asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(base + BT_DS_OFF + off), "r"(wd[0]),
+                         "r"(wd[1]), "r"(wd[2]), "r"(wd[3])
+                         : "memory");
+          }
+#pragma unroll
+          for (int i = 0; i < 16; ++i) {
+            __nv_bfloat162 d2 = __floats2bfloat162_rn(ds[2 * i], ds[2 * i + 1]);
+            pk[t][i] = *reinterpret_cast<uint32_t *>(&d2);
+          }
+        }
+      }
+      // every warp has read its dP columns: dS pairs may now land over them
+      tc_fence_before();
+      __syncthreads();
+      tc_fence_after();
+      if (ok) {
+        tmem_st16(lane_base + BT_DP_COL + (uint32_t)((half * 2) * 16), pk[0]);
+        tmem_st16(lane_base + BT_DP_COL + (uint32_t)((half * 2 + 1) * 16), pk[1]);
+      }
+      tmem_wait_st();
+      fence_proxy_async();
+      tc_fence_before();
+      __syncthreads();
+      if (tid == 0 && ok && !s_abort) {
+        tc_fence_after();
+        const uint32_t id_kv = instr_desc(128, AT_C, true, true);   // A = P^T / dS^T (MN-major), B = dO / Q (MN-major)
+        const uint32_t id_q = instr_desc(128, AT_C, false, true);   // A = dS (TMEM), B = K (MN-major)
+        for (int ks = 0; ks < 8; ++ks) {
+          const uint32_t aoff = (uint32_t)((ks >> 2) * 16384 + (ks & 3) * 2048);
+          const uint64_t pd = smem_desc(base + BT_P_OFF + aoff, 8192, 1024, 2);
+          const uint64_t dsd = smem_desc(base + BT_DS_OFF + aoff, 8192, 1024, 2);
+          const uint64_t od = smem_desc(base + BT_DO_OFF + qt * 8192 + ks * 1024, 16384, 512, 4);
+          const uint64_t qd = smem_desc(base + BT_Q_OFF + qt * 8192 + ks * 1024, 16384, 512, 4);
+          const uint64_t kd = smem_desc(base + BT_K_OFF + kh * 8192 + ks * 1024, 16384, 512, 4);
+          const uint32_t acc_kv = (qt > 0 || ks > 0) ? 1u : 0u;
+          mma_ss(tmem + BT_DV_COL, pd, od, id_kv, acc_kv);
+          mma_ss(tmem + BT_DK_COL, dsd, qd, id_kv, acc_kv);
+          mma_ts(tmem + BT_DQ_COL + (uint32_t)(qt * 32), tmem + BT_DP_COL + (uint32_t)(ks * 8), kd, id_q,
+                 (kh > 0 || ks > 0) ? 1u : 0u);
+        }
+        mma_commit(&bar_mm);
+        ++nmm;
+      }
+      // pair-bias gradient from the shared dS copy: warp w takes query rows w, w + 8, ..
+      if (a.dbias && ok) {
+        for (int r = warp; r < 128; r += AT_WARPS) {
+          const int x = qt * 128 + r;
+          const int y = kh * 128 + lane * 4;
+          if (x >= a.X || y >= a.Y) continue;
+          const uint32_t off = mn_major_off(lane * 4, r);
+          uint32_t w0, w1;
+          asm volatile("ld.shared.v2.b32 {%0, %1}, [%2];" : "=r"(w0), "=r"(w1) : "r"(base + BT_DS_OFF + off));
+          const float2 f0 = __bfloat1622float2(*reinterpret_cast<__nv_bfloat162 *>(&w0));
+          const float2 f1 = __bfloat1622float2(*reinterpret_cast<__nv_bfloat162 *>(&w1));
+          float *dst = a.dbias + (int64_t)h * a.sBh + (int64_t)x * a.sBx + y;
+          asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(dst), "f"(f0.x), "f"(f0.y), "f"(f1.x),
+                       "f"(f1.y)
+                       : "memory");
+        }
+      }
+      ok = __all_sync(0xffffffffu, ok && mbar_wait(&bar_mm, (uint32_t)(it & 1), &s_abort));
+      // every warp is done with this sub-tile's shared P / dS copies and TMEM
+      // columns before the next sub-tile rewrites them
+      tc_fence_before();
+      __syncthreads();
+      tc_fence_after();
+    }
+    // dK, dV of this key half: thread = key row, the two warps of a quarter take 16 channels each
+    {
+      const int y = kh * 128 + quarter * 32 + lane;
+      uint32_t rk[16], rv[16];
+      if (ok) {
+        tmem_ld16(lane_base + BT_DK_COL + (uint32_t)(half * 16), rk);
+        tmem_ld16(lane_base + BT_DV_COL + (uint32_t)(half * 16), rv);
+      }
+      if (ok && y < a.Y) {
+        bf16 *dk = (bf16 *)a.dk + (int64_t)b * a.sKb + (int64_t)y * a.sKy + h * AT_C + half * 16;
+        bf16 *dv = (bf16 *)a.dv + (int64_t)b * a.sKb + (int64_t)y * a.sKy + h * AT_C + half * 16;
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+          uint4 wk, wv;
+          uint32_t *k32 = reinterpret_cast<uint32_t *>(&wk), *v32 = reinterpret_cast<uint32_t *>(&wv);
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            __nv_bfloat162 k2 = __floats2bfloat162_rn(__uint_as_float(rk[8 * q + 2 * i]) * a.scale,
+                                                      __uint_as_float(rk[8 * q + 2 * i + 1]) * a.scale);
+            __nv_bfloat162 v2 =
+                __floats2bfloat162_rn(__uint_as_float(rv[8 * q + 2 * i]), __uint_as_float(rv[8 * q + 2 * i + 1]));
+            k32[i] = *reinterpret_cast<uint32_t *>(&k2);
+            v32[i] = *reinterpret_cast<uint32_t *>(&v2);
+          }
+          *reinterpret_cast<uint4 *>(dk + 8 * q) = wk;
+          *reinterpret_cast<uint4 *>(dv + 8 * q) = wv;
+        }
+      }
+      tc_fence_before();
+      __syncthreads();  // the next key half restarts the dK / dV accumulators
+      tc_fence_after();
+    }
+  }
+  // dQ of every query tile
+  for (int qt = 0; qt < nq; ++qt) {
+    const int x = qt * 128 + quarter * 32 + lane;
+    uint32_t rq[16];
+    if (ok) tmem_ld16(lane_base + BT_DQ_COL + (uint32_t)(qt * 32 + half * 16), rq);
+    if (ok && x < a.X) {
+      bf16 *dq = (bf16 *)a.dq + (int64_t)b * a.sQb + (int64_t)x * a.sQx + h * AT_C + half * 16;
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        uint4 w;
+        uint32_t *w32 = reinterpret_cast<uint32_t *>(&w);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          __nv_bfloat162 q2 = __floats2bfloat162_rn(__uint_as_float(rq[8 * q + 2 * i]) * a.scale,
+                                                    __uint_as_float(rq[8 * q + 2 * i + 1]) * a.scale);
+          w32[i] = *reinterpret_cast<uint32_t *>(&q2);
+        }
+        *reinterpret_cast<uint4 *>(dq + 8 * q) = w;
+      }
+    }
+  }
+  // drain (after an abort) anything still in flight before the CTA exits
+  if (s_abort) {
+    if (tid == 0) {
+      if (in_issued) mbar_drain(&bar_in, 0);
+      for (int i = 0; i < nsd; ++i) mbar_drain(&bar_sd, (uint32_t)(i & 1));
+      for (int i = 0; i < nmm; ++i) mbar_drain(&bar_mm, (uint32_t)(i & 1));
+    }
+    if (lane == 0)
+      for (int j = bias_done; j < bias_issued; ++j) mbar_drain(&bar_b[warp][j & 1], (uint32_t)((j >> 1) & 1));
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)BT_TMEM_COLS)
+                 : "memory");
+  }
+}
+
 // 4-D map of a q/k/v view: element (d, h, row, b) at base + b*s_b + row*s_row + h*c + d,
 // outer dimensions ordered by stride (TMA takes them in any order; ascending
 // strides keep every dimension's span inside the next stride).
@@ -444,6 +779,46 @@ cudaError_t attn_fwd_tc_launch(const AttnArgs &a, cudaStream_t s, double flops, 
   dim3 grid((a.X + AT_QROWS - 1) / AT_QROWS, a.H, a.B1);
   Prof p("attn_fwd_tc", s, flops, bytes);
   attn_fwd_tc<<<grid, AT_WARPS * 32, AT_SMEM, s>>>(tq, tk, tv, tb, A);
+  return cudaGetLastError();
+}
+
+bool attn_bwd_tc_supported(const AttnArgs &a) {
+  auto a16 = [](const void *p) { return ((uintptr_t)p & 15u) == 0; };
+  if (!attn_tc_supported(a) || a.X > 256 || !a.dq || !a.do_att || !a.dk || !a.dv || !a.Dsum) return false;
+  if (!a16(a.dq) || !a16(a.dk) || !a16(a.dv) || !a16(a.do_att) || a.sKy % 8 || a.sKb % 8) return false;
+  if (a.bias && (!a.dbias || !a16(a.dbias) || a.Y % 4)) return false;
+  return true;
+}
+
+cudaError_t attn_bwd_tc_launch(const AttnArgs &a, cudaStream_t s, double flops, double bytes) {
+  AttnTcBwdArgs A{};
+  A.a = a;
+  A.nq = (a.X + 127) / 128;
+  A.nkh = (a.Y + 127) / 128;
+  A.has_bias = a.bias != nullptr;
+  CUtensorMap tq, tk, tv, to, tb;
+  std::memset(&tb, 0, sizeof(tb));
+  QkvPos pv;
+  if (!qkv_map(&tq, a.q, a.H, a.X, a.B1, a.sQx, a.sQb, 128, &A.pq)) return cudaErrorNotSupported;
+  if (!qkv_map(&tk, a.k, a.H, a.Y, a.B1, a.sKy, a.sKb, 128, &A.pk)) return cudaErrorNotSupported;
+  if (!qkv_map(&tv, a.v, a.H, a.Y, a.B1, a.sKy, a.sKb, 128, &pv)) return cudaErrorNotSupported;
+  if (!qkv_map(&to, a.do_att, a.H, a.X, a.B1, a.sOx, a.sOb, 128, &A.po)) return cudaErrorNotSupported;
+  if (a.bias) {
+    const uint64_t dims[3] = {(uint64_t)a.Y, (uint64_t)a.X, (uint64_t)a.H};
+    const uint64_t st[2] = {(uint64_t)a.sBx * 4, (uint64_t)a.sBh * 4};
+    const uint32_t box[3] = {32, 32, 1};
+    if (!make_tmap_nd(&tb, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, a.bias, dims, st, box, CU_TENSOR_MAP_SWIZZLE_128B))
+      return cudaErrorNotSupported;
+  }
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(attn_bwd_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, BT_SMEM);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  dim3 grid(a.H, a.B1);
+  Prof p("attn_bwd_tc", s, flops, bytes);
+  attn_bwd_tc<<<grid, AT_WARPS * 32, BT_SMEM, s>>>(tq, tk, tv, to, tb, A);
   return cudaGetLastError();
 }
 

@@ -506,11 +506,10 @@ struct Drv {
     a.dk = at(B(pl.G1), HC);
     a.dv = at(B(pl.G1), 2 * HC);
     a.dbias = bias ? Bf(pl.dbias) : nullptr;
+    a.dq = B(pl.G1);
     ck(attn_gate_bwd(a, B(pl.G2), at(B(pl.G1), 3 * HC), a.sQb, a.sQx, B(pl.G3), Bf(pl.Dsum), bf, s));
-    ck(cudaMemsetAsync(Bf(pl.dq_acc), 0, (size_t)M * HC * 4, s));
     if (bias) ck(cudaMemsetAsync(Bf(pl.dbias), 0, (size_t)a.H * k.Mz * 4, s));
     ck(attn_bwd(a, bf, s));
-    ck(attn_dq_store(a, B(pl.G1), bf, s));
     dW(B(pl.G1), QK, QK, xn, Cin, Cin, M, pre + ".w_qkvg");
     db(at(B(pl.G1), 3 * HC), QK, M, HC, pre + ".b_g");
     GemmOp x = mk(M, Cin, QK, B(pl.G1), QK, 0, W(pre + ".w_qkvg"), Cin, 1, B(pl.G2), Cin);

@@ -60,12 +60,17 @@ struct AttnArgs {
   float *dq_acc;         // fp32 [b*sOb + x*sOx + h*c + d] accumulated (unscaled)
   void *dk, *dv;         // k/v strides
   float *dbias;          // fp32 [h*sBh + x*sBx + y] accumulated
+  void *dq;              // q strides: the scaled query gradient (activation type)
 };
 cudaError_t attn_fwd(const AttnArgs &a, int use_bf16, cudaStream_t s);
 // tcgen05 forward (bf16, head dim 32, at most 256 keys, 16-byte aligned rows);
 // cudaErrorNotSupported (nothing launched) when TMA cannot describe the views.
 bool attn_tc_supported(const AttnArgs &a);
 cudaError_t attn_fwd_tc_launch(const AttnArgs &a, cudaStream_t s, double flops, double bytes);
+// tcgen05 backward (as the forward, and X <= 256): writes dq, dk, dv and adds
+// the pair-bias gradient; cudaErrorNotSupported (nothing launched) as above.
+bool attn_bwd_tc_supported(const AttnArgs &a);
+cudaError_t attn_bwd_tc_launch(const AttnArgs &a, cudaStream_t s, double flops, double bytes);
 // Reads and clears the error word of the tcgen05 attention kernels; synchronous.
 cudaError_t attn_tc_error_read_clear(int *out);
 cudaError_t attn_bwd(const AttnArgs &a, int use_bf16, cudaStream_t s);
