@@ -293,9 +293,15 @@ struct Drv {
     sp = std::min<int64_t>(sp, std::max<int64_t>(1, rows / 256));
     sp = std::max<int64_t>(1, std::min<int64_t>(sp, MAXSPLIT));
     g.splits = (int)sp;
-    g.e.partial = Bf(pl.split);
-    gemm(g);
-    ck(reduce_splits(Bf(pl.split), (int)sp, Nout * Kin, D(w), s));
+    if (bf) {
+      // each K range adds its partial product straight into the fp32 gradient
+      g.e.C = D(w), g.e.c_f32 = 1, g.e.atomic = 1, g.e.map = rowmajor_map(Kin);
+      gemm(g);
+    } else {
+      g.e.partial = Bf(pl.split);
+      gemm(g);
+      ck(reduce_splits(Bf(pl.split), (int)sp, Nout * Kin, D(w), s));
+    }
   }
   void db(const void *dY, int64_t ldY, int64_t rows, int64_t N, const std::string &b) {
     ck(colsum(dY, ldY, rows, (int)N, bf, s, D(b)));

@@ -72,6 +72,7 @@ struct Epi {
   OutMap map;
   int c_f32;        // C is fp32 (else the activation type)
   int accumulate;   // fp32 C += v
+  int atomic;       // fp32 C += v with atomics (split-K; no other epilogue step)
   float alpha;
   const float *bias;
   int bias_n0;

@@ -264,6 +264,7 @@ __device__ __forceinline__ void epi_chunk(const GemmOp &g, const float *mine, in
     if (m >= g.M) break;
     const float acc = mine[rr * 33 + lane];
     if (e.partial) e.partial[((int64_t)split * e.M + m) * e.N + n] = acc;
+    else if (e.atomic) atomicAdd((float *)e.C + (int64_t)b * e.c_bstride + e.map(m, n), acc * e.alpha);
     else epi_store<bf16>(e, b, split, m, n, acc);
   }
 }
@@ -796,7 +797,7 @@ cudaError_t launch_tc(const GemmOp &g, cudaStream_t s) {
   // tiles too, so they need 16-byte aligned bases and row strides.
   const Epi &e = g.e;
   auto a16 = [](const void *p) { return ((uintptr_t)p & 15u) == 0; };
-  const bool operands_ok = !e.partial && !e.c_f32 && !e.accumulate && !(e.gate && e.relu_ref) && a16(e.C) &&
+  const bool operands_ok = !e.partial && !e.atomic && !e.c_f32 && !e.accumulate && !(e.gate && e.relu_ref) && a16(e.C) &&
                            (!e.residual || a16(e.residual)) &&
                            (!e.relu_ref || (a16(e.relu_ref) && e.relu_ld % 8 == 0)) &&
                            (!e.aux || (a16(e.aux) && e.aux_ld % 8 == 0)) &&
@@ -904,7 +905,7 @@ bool gemm_tc_supported(const GemmOp &g) {
   if (!al16(g.A) || !al16(g.B)) return false;
   if ((g.lda * 2) % 16 || (g.ldb * 2) % 16) return false;
   if (g.batch > 1 && ((g.a_bs * 2) % 16 || (g.b_bs * 2) % 16)) return false;
-  if (g.splits > 1 && (g.batch != 1 || !g.e.partial)) return false;
+  if (g.splits > 1 && (g.batch != 1 || !(g.e.partial || g.e.atomic))) return false;
   if (g.M <= 0 || g.N <= 0 || g.K <= 0) return false;
   return true;
 }

@@ -471,6 +471,143 @@ __global__ void __launch_bounds__(256) trimul_gate_bwd_v8(const bf16 *dA, const 
   }
 }
 
+// Triangle-multiplication gates, tiled for bf16 with cm a multiple of 64:
+// block = 2 rows x 64 columns of the (row, col) output grid and 64 of the cm
+// channels (blockIdx.z).  A warp reads one position's 64-channel segments of
+// ap | ag | bp | bg (4 x 128 B: lanes 0-7, 8-15, 16-23, 24-31), exchanges the
+// gate halves by shuffles, and the channel-major A, B rows leave as 128-byte
+// rows through a shared-memory transposition ([row][col][channel] with an odd
+// channel pitch, so both the channel-wise and the column-wise accesses are
+// free of bank conflicts).  Position of (row, col): row * R + col (outgoing)
+// or col * R + row (incoming).
+constexpr int TG_ROWS = 2, TG_COLS = 64, TG_CH = 64, TG_LDC = TG_CH + 1;
+
+__device__ __forceinline__ float sigm(float x) { return __fdividef(1.f, 1.f + __expf(-x)); }
+
+__global__ void __launch_bounds__(256) trimul_gate_fwd_t(bf16 *abg, int64_t ld, const float *mask, bf16 *A, bf16 *B,
+                                                         int64_t pitch, int R, int cm, int cz, int incoming) {
+  __shared__ bf16 as[TG_ROWS][TG_COLS][TG_LDC];
+  __shared__ bf16 bs[TG_ROWS][TG_COLS][TG_LDC];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int q0 = blockIdx.x * TG_COLS, r0 = blockIdx.y * TG_ROWS, c0 = blockIdx.z * TG_CH;
+  const int seg = lane >> 3, sub = lane & 7;  // segment (ap, ag, bp, bg) and its 8-channel piece
+  const int gz = (cz + TG_CH - 1) / TG_CH;    // z-blocks that also take a share of the g columns
+  for (int pi = warp; pi < TG_ROWS * TG_COLS; pi += 8) {
+    const int orl = pi / TG_COLS, ocl = pi % TG_COLS;
+    const int orow = r0 + orl, ocol = q0 + ocl;
+    float v[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    float mk = 0.f;
+    int64_t p = 0;
+    const bool in = orow < R && ocol < R;
+    if (in) {
+      p = incoming ? (int64_t)ocol * R + orow : (int64_t)orow * R + ocol;
+      mk = mask[p];
+      ld8(abg + p * ld + seg * cm + c0 + sub * 8, v);
+    }
+    // lanes 0-7 (ap) take ag from lanes 8-15; lanes 16-23 (bp) take bg from 24-31
+    float gv[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) gv[k] = __shfl_down_sync(0xffffffffu, v[k], 8);
+    if ((seg & 1) == 0) {
+      bf16 *dst = seg == 0 ? &as[orl][ocl][sub * 8] : &bs[orl][ocl][sub * 8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) dst[k] = __float2bfloat16_rn(mk * v[k] * sigm(gv[k]));
+    }
+    // sigmoid of this block's share of the output-gate columns, in place
+    if (in && blockIdx.z < gz && lane < 8) {
+      const int gc = blockIdx.z * TG_CH + sub * 8;
+      if (gc < cz) {
+        float g[8];
+        bf16 *gp = abg + p * ld + 4 * cm + gc;
+        ld8(gp, g);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) g[k] = sigm(g[k]);
+        st8(gp, g);
+      }
+    }
+  }
+  __syncthreads();
+  // channel-major rows: A[c][orow][q0 ..] (64 bf16 = 128 B per warp instruction)
+  const int64_t plane = (int64_t)R * pitch;
+  for (int t = warp; t < 2 * TG_CH * TG_ROWS; t += 8) {
+    const int which = t / (TG_CH * TG_ROWS), rem = t % (TG_CH * TG_ROWS);
+    const int ch = rem / TG_ROWS, orl = rem % TG_ROWS;
+    const int c = c0 + ch, orow = r0 + orl, ocol = q0 + 2 * lane;
+    if (c >= cm || orow >= R || ocol >= R) continue;
+    const bf16 (*src)[TG_COLS][TG_LDC] = which ? bs : as;
+    const bf16 v0 = src[orl][2 * lane][ch], v1 = src[orl][2 * lane + 1][ch];
+    bf16 *dst = (which ? B : A) + (int64_t)c * plane + (int64_t)orow * pitch + ocol;
+    if (ocol + 1 < R && ((((uintptr_t)dst) & 3u) == 0)) {
+      __nv_bfloat162 w;
+      w.x = v0, w.y = v1;
+      *reinterpret_cast<__nv_bfloat162 *>(dst) = w;
+    } else {
+      dst[0] = v0;
+      if (ocol + 1 < R) dst[1] = v1;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(256) trimul_gate_bwd_t(const bf16 *dA, const bf16 *dB, int64_t pitch,
+                                                         const bf16 *abg, int64_t ld, const float *mask, bf16 *dabg,
+                                                         int R, int cm, int incoming) {
+  __shared__ bf16 as[TG_ROWS][TG_COLS][TG_LDC];
+  __shared__ bf16 bs[TG_ROWS][TG_COLS][TG_LDC];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int q0 = blockIdx.x * TG_COLS, r0 = blockIdx.y * TG_ROWS, c0 = blockIdx.z * TG_CH;
+  const int64_t plane = (int64_t)R * pitch;
+  // channel-major gradient rows in (128 B per warp instruction)
+  for (int t = warp; t < 2 * TG_CH * TG_ROWS; t += 8) {
+    const int which = t / (TG_CH * TG_ROWS), rem = t % (TG_CH * TG_ROWS);
+    const int ch = rem / TG_ROWS, orl = rem % TG_ROWS;
+    const int c = c0 + ch, orow = r0 + orl, ocol = q0 + 2 * lane;
+    bf16 (*dst)[TG_COLS][TG_LDC] = which ? bs : as;
+    bf16 v0 = __float2bfloat16_rn(0.f), v1 = v0;
+    if (c < cm && orow < R && ocol < R) {
+      const bf16 *src = (which ? dB : dA) + (int64_t)c * plane + (int64_t)orow * pitch + ocol;
+      if (ocol + 1 < R && ((((uintptr_t)src) & 3u) == 0)) {
+        const __nv_bfloat162 w = *reinterpret_cast<const __nv_bfloat162 *>(src);
+        v0 = w.x, v1 = w.y;
+      } else {
+        v0 = src[0];
+        if (ocol + 1 < R) v1 = src[1];
+      }
+    }
+    dst[orl][2 * lane][ch] = v0;
+    dst[orl][2 * lane + 1][ch] = v1;
+  }
+  __syncthreads();
+  const int seg = lane >> 3, sub = lane & 7;
+  for (int pi = warp; pi < TG_ROWS * TG_COLS; pi += 8) {
+    const int orl = pi / TG_COLS, ocl = pi % TG_COLS;
+    const int orow = r0 + orl, ocol = q0 + ocl;
+    if (orow >= R || ocol >= R) continue;  // warp-uniform
+    const int64_t p = incoming ? (int64_t)ocol * R + orow : (int64_t)orow * R + ocol;
+    const float mk = mask[p];
+    float v[8];
+    ld8(abg + p * ld + seg * cm + c0 + sub * 8, v);
+    float gv[8], pv[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      gv[k] = __shfl_down_sync(0xffffffffu, v[k], 8);  // the gate pre-activation, for lanes of ap / bp
+      pv[k] = __shfl_up_sync(0xffffffffu, v[k], 8);    // the projection, for lanes of ag / bg
+    }
+    const bf16 *src = seg < 2 ? &as[orl][ocl][sub * 8] : &bs[orl][ocl][sub * 8];
+    float out[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const float d = __bfloat162float(src[k]) * mk;
+      if ((seg & 1) == 0) {
+        out[k] = d * sigm(gv[k]);  // d proj = d * sigmoid(gate)
+      } else {
+        const float sg = sigm(v[k]);
+        out[k] = d * pv[k] * sg * (1.f - sg);  // d gate = d * proj * sigmoid'(gate)
+      }
+    }
+    st8(dabg + p * ld + seg * cm + c0 + sub * 8, out);
+  }
+}
+
 template <typename T>
 __global__ void sigmoid_cols_k(T *x, int64_t ld, int col0, int ncols, int64_t P) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -661,7 +798,10 @@ cudaError_t trimul_gate_fwd(void *abg, int64_t ld, const float *mask, void *A, v
   dim3 grid((R + 31) / 32, (R + 31) / 32, (cm + 3) / 4);
   const int64_t P = (int64_t)R * R;
   const bool v8 = cm % 8 == 0 && cz % 8 == 0 && ld % 8 == 0 && (((uintptr_t)abg) & 15u) == 0;
-  if (use_bf16 && v8) {
+  if (use_bf16 && v8 && cm % TG_CH == 0 && (cz + TG_CH - 1) / TG_CH <= cm / TG_CH) {
+    dim3 gt((R + TG_COLS - 1) / TG_COLS, (R + TG_ROWS - 1) / TG_ROWS, cm / TG_CH);
+    trimul_gate_fwd_t<<<gt, 256, 0, s>>>((bf16 *)abg, ld, mask, (bf16 *)A, (bf16 *)B, pitch, R, cm, cz, incoming);
+  } else if (use_bf16 && v8) {
     dim3 g8((R + 31) / 32, (R + 31) / 32, cm / 8);
     trimul_gate_fwd_v8<<<g8, 256, 0, s>>>((bf16 *)abg, ld, mask, (bf16 *)A, (bf16 *)B, pitch, R, cm, cz, incoming);
   } else if (use_bf16) {
@@ -681,7 +821,11 @@ cudaError_t trimul_gate_bwd(const void *dA, const void *dB, int64_t pitch, const
   Prof prof("trimul_gate_bwd", s, 0, (use_bf16 ? 2.0 : 4.0) * R * (double)R * 10.0 * cm, 1);
   dim3 grid((R + 31) / 32, (R + 31) / 32, (cm + 3) / 4);
   const bool v8 = cm % 8 == 0 && ld % 8 == 0 && (((uintptr_t)abg) & 15u) == 0 && (((uintptr_t)dabg) & 15u) == 0;
-  if (use_bf16 && v8) {
+  if (use_bf16 && v8 && cm % TG_CH == 0) {
+    dim3 gt((R + TG_COLS - 1) / TG_COLS, (R + TG_ROWS - 1) / TG_ROWS, cm / TG_CH);
+    trimul_gate_bwd_t<<<gt, 256, 0, s>>>((const bf16 *)dA, (const bf16 *)dB, pitch, (const bf16 *)abg, ld, mask,
+                                         (bf16 *)dabg, R, cm, incoming);
+  } else if (use_bf16 && v8) {
     dim3 g8((R + 31) / 32, (R + 31) / 32, cm / 8);
     trimul_gate_bwd_v8<<<g8, 256, 0, s>>>((const bf16 *)dA, (const bf16 *)dB, pitch, (const bf16 *)abg, ld, mask,
                                           (bf16 *)dabg, R, cm, incoming);
