@@ -121,8 +121,10 @@ template <> struct Pair<float> {
 };
 
 // LayerNorm backward with the row in registers: lane l holds channels
-// 64j + 2l, 64j + 2l + 1 (j < P), so every load is a coalesced pair.
-template <typename T, int P>
+// 64j + 2l, 64j + 2l + 1 (j < P), so every load is a coalesced pair.  A warp
+// takes NR rows at a time (all their loads issued before any reduction) so
+// that the latency of one row overlaps the others.
+template <typename T, int P, int NR>
 __global__ void __launch_bounds__(256) ln_bwd_rows_vec(const T *dy, const T *x, const float *gamma, float *dacc,
                                                        T *dcopy, T *dx_out, int64_t M,
                                                        int64_t rows_per_blk, float *dgamma, float *dbeta) {
@@ -139,54 +141,66 @@ __global__ void __launch_bounds__(256) ln_bwd_rows_vec(const T *dy, const T *x, 
   }
   const int64_t r0 = (int64_t)blockIdx.x * rows_per_blk;
   const int64_t r1 = min(M, r0 + rows_per_blk);
-  for (int64_t row = r0 + warp; row < r1; row += 8) {
-    float2 xv[P], gv[P];
-    float s = 0.f;
+  for (int64_t rb = r0 + (int64_t)warp * NR; rb < r1; rb += 8 * NR) {
+    float2 xv[NR][P], gv[NR][P], av[NR][P];
 #pragma unroll
-    for (int j = 0; j < P; ++j) {
-      const int c = 64 * j + 2 * lane;
-      xv[j] = Pair<T>::ld(x + row * C + c);
-      gv[j] = Pair<T>::ld(dy + row * C + c);
-      s += xv[j].x + xv[j].y;
+    for (int i = 0; i < NR; ++i) {
+      const int64_t row = rb + i;
+#pragma unroll
+      for (int j = 0; j < P; ++j) {
+        const int c = 64 * j + 2 * lane;
+        if (row < r1) {
+          xv[i][j] = Pair<T>::ld(x + row * C + c);
+          gv[i][j] = Pair<T>::ld(dy + row * C + c);
+          av[i][j] = dacc ? *reinterpret_cast<const float2 *>(dacc + row * C + c) : make_float2(0.f, 0.f);
+        } else {
+          xv[i][j] = gv[i][j] = av[i][j] = make_float2(0.f, 0.f);
+        }
+      }
     }
-    const float mu = warp_sum(s) * (1.f / C);
-    float q = 0.f;
 #pragma unroll
-    for (int j = 0; j < P; ++j) {
-      const float d0 = xv[j].x - mu, d1 = xv[j].y - mu;
-      q += d0 * d0 + d1 * d1;
-    }
-    const float rstd = rsqrtf(warp_sum(q) * (1.f / C) + LN_EPS);
-    float a1 = 0.f, a2 = 0.f;
+    for (int i = 0; i < NR; ++i) {
+      const int64_t row = rb + i;
+      float s = 0.f;
 #pragma unroll
-    for (int j = 0; j < P; ++j) {
-      const float h0 = (xv[j].x - mu) * rstd, h1 = (xv[j].y - mu) * rstd;
-      xv[j].x = h0;
-      xv[j].y = h1;
-      const float d0 = gv[j].x * g0[j], d1 = gv[j].y * g1[j];
-      a1 += d0 + d1;
-      a2 += d0 * h0 + d1 * h1;
-      ag[j] += gv[j].x * h0;
-      ag1[j] += gv[j].y * h1;
-      ab[j] += gv[j].x;
-      ab1[j] += gv[j].y;
-    }
-    a1 = warp_sum(a1) * (1.f / C);
-    a2 = warp_sum(a2) * (1.f / C);
+      for (int j = 0; j < P; ++j) s += xv[i][j].x + xv[i][j].y;
+      const float mu = warp_sum(s) * (1.f / C);
+      float q = 0.f;
 #pragma unroll
-    for (int j = 0; j < P; ++j) {
-      const int c = 64 * j + 2 * lane;
-      const float dx0 = rstd * (gv[j].x * g0[j] - a1 - xv[j].x * a2);
-      const float dx1 = rstd * (gv[j].y * g1[j] - a1 - xv[j].y * a2);
-      if (dacc) {
-        float2 *pa = reinterpret_cast<float2 *>(dacc + row * C + c);
-        float2 nv = *pa;
-        nv.x += dx0;
-        nv.y += dx1;
-        *pa = nv;
-        if (dcopy) Pair<T>::st(dcopy + row * C + c, nv.x, nv.y);
-      } else {
-        Pair<T>::st(dx_out + row * C + c, dx0, dx1);
+      for (int j = 0; j < P; ++j) {
+        const float d0 = xv[i][j].x - mu, d1 = xv[i][j].y - mu;
+        q += d0 * d0 + d1 * d1;
+      }
+      const float rstd = rsqrtf(warp_sum(q) * (1.f / C) + LN_EPS);
+      float a1 = 0.f, a2 = 0.f;
+#pragma unroll
+      for (int j = 0; j < P; ++j) {
+        const float h0 = (xv[i][j].x - mu) * rstd, h1 = (xv[i][j].y - mu) * rstd;
+        xv[i][j].x = h0;
+        xv[i][j].y = h1;
+        const float d0 = gv[i][j].x * g0[j], d1 = gv[i][j].y * g1[j];
+        a1 += d0 + d1;
+        a2 += d0 * h0 + d1 * h1;
+        ag[j] += gv[i][j].x * h0;
+        ag1[j] += gv[i][j].y * h1;
+        ab[j] += gv[i][j].x;
+        ab1[j] += gv[i][j].y;
+      }
+      a1 = warp_sum(a1) * (1.f / C);
+      a2 = warp_sum(a2) * (1.f / C);
+      if (row >= r1) continue;  // warp-uniform
+#pragma unroll
+      for (int j = 0; j < P; ++j) {
+        const int c = 64 * j + 2 * lane;
+        const float dx0 = rstd * (gv[i][j].x * g0[j] - a1 - xv[i][j].x * a2);
+        const float dx1 = rstd * (gv[i][j].y * g1[j] - a1 - xv[i][j].y * a2);
+        if (dacc) {
+          const float2 nv = make_float2(av[i][j].x + dx0, av[i][j].y + dx1);
+          *reinterpret_cast<float2 *>(dacc + row * C + c) = nv;
+          if (dcopy) Pair<T>::st(dcopy + row * C + c, nv.x, nv.y);
+        } else {
+          Pair<T>::st(dx_out + row * C + c, dx0, dx1);
+        }
       }
     }
   }
@@ -344,8 +358,9 @@ cudaError_t ln_fwd_t(const void *x, const float *gamma, const float *beta, void 
 }  // namespace
 
 int ln_bwd_blocks(int64_t M) {
+  // four blocks per SM (each adds its gamma / beta partial sums with atomics)
   int64_t b = (M + 63) / 64;
-  return (int)(b < 296 ? (b < 1 ? 1 : b) : 296);
+  return (int)(b < 608 ? (b < 1 ? 1 : b) : 608);
 }
 
 cudaError_t ln_fwd(const void *x, const float *gamma, const float *beta, void *y, int64_t M, int C, int use_bf16,
@@ -374,19 +389,19 @@ cudaError_t ln_bwd(const void *dy, const void *x, const float *gamma, float *dac
   Prof p("ln_bwd", s, 0, (use_bf16 ? 2.0 : 4.0) * M * C * (dcopy ? 3 : 2) + (dacc ? 8.0 * M * C : 0.0));
   const int nb = ln_bwd_blocks(M);
   const int64_t rpb = (M + nb - 1) / nb;
-#define EVO_LN_BWD_VEC(P)                                                                                        \
+#define EVO_LN_BWD_VEC(P, NR)                                                                                    \
   if (C == 64 * P) {                                                                                             \
     if (use_bf16)                                                                                                \
-      ln_bwd_rows_vec<bf16, P><<<nb, 256, 0, s>>>((const bf16 *)dy, (const bf16 *)x, gamma, dacc, (bf16 *)dcopy, \
-                                                  (bf16 *)dx_out, M, rpb, dgamma, dbeta);         \
+      ln_bwd_rows_vec<bf16, P, NR><<<nb, 256, 0, s>>>((const bf16 *)dy, (const bf16 *)x, gamma, dacc,           \
+                                                      (bf16 *)dcopy, (bf16 *)dx_out, M, rpb, dgamma, dbeta);     \
     else                                                                                                         \
-      ln_bwd_rows_vec<float, P><<<nb, 256, 0, s>>>((const float *)dy, (const float *)x, gamma, dacc,             \
-                                                   (float *)dcopy, (float *)dx_out, M, rpb, dgamma, dbeta);                                                     \
+      ln_bwd_rows_vec<float, P, NR><<<nb, 256, 0, s>>>((const float *)dy, (const float *)x, gamma, dacc,        \
+                                                       (float *)dcopy, (float *)dx_out, M, rpb, dgamma, dbeta);  \
     return cudaGetLastError();                                                                                   \
   }
-  EVO_LN_BWD_VEC(1)
-  EVO_LN_BWD_VEC(2)
-  EVO_LN_BWD_VEC(4)
+  EVO_LN_BWD_VEC(1, 4)
+  EVO_LN_BWD_VEC(2, 4)
+  EVO_LN_BWD_VEC(4, 2)
 #undef EVO_LN_BWD_VEC
   const size_t sm = (size_t)8 * 2 * C * sizeof(float);
   if (use_bf16)
