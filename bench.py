@@ -173,6 +173,9 @@ def reference_arm(args):
 
 
 # ---------------------------------------------------------------- our arm
+PROFILE_EVERY = 10
+
+
 def ours_arm(args):
     import torch
     from paper_2207_05477_gb300 import evo, synth
@@ -242,9 +245,11 @@ def ours_arm(args):
     dom_name = max(pre.items(), key=lambda kv: kv[1]["ms"])[0]
 
     # ---- timed region: K steps, L2 flushed between steps (outside each step's events).
-    # Eager steps record one event pair around each launch of the dominant
-    # kernel class only (its live per-launch times for the roofline); a graph
-    # replay cannot time launches inside it.
+    # In every PROFILE_EVERY-th eager step one event pair brackets each launch
+    # of the dominant kernel class (its live per-launch times for the
+    # roofline); the other steps run untouched, since an event between two
+    # launches stops the next one from starting early.  A graph replay cannot
+    # time launches inside it.
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     clocks = ClockSampler(local)
     if world > 1:
@@ -254,11 +259,17 @@ def ours_arm(args):
     if graph is None:
         evo.profile_only(dom_name)
         evo.profile_begin()
+        evo.profile_pause(True)
     for i in range(args.steps):
         flush.fill_(float(i))
         ev[i][0].record(stream)
         if graph is None:
+            sampled = i % PROFILE_EVERY == PROFILE_EVERY - 1 or args.steps < PROFILE_EVERY
+            if sampled:
+                evo.profile_pause(False)
             step(m, z, mm, pm, gm, gz, params)
+            if sampled:
+                evo.profile_pause(True)
         else:
             graph.replay()
         ev[i][1].record(stream)
@@ -350,7 +361,8 @@ def ours_arm(args):
     # steps (eager), else of the profiled steps (graph replay)
     peaks = load_peaks()
     dom = (dom_live or prof)[dom_name]
-    dom_src = "timed steps" if dom_live else "eager steps after the timed region"
+    dom_src = (f"every {PROFILE_EVERY}th timed step" if args.steps >= PROFILE_EVERY else "timed steps") if dom_live \
+        else "eager steps after the timed region"
     dom_ms_per_launch = dom["ms"] / max(dom["launches"], 1)
     t_tc = dom["flops"] / (peaks["bf16_sus"] * 1e12) if dom["flops"] else 0.0
     t_hbm = dom["bytes"] / (peaks["hbm"] * 1e9) if dom["bytes"] else 0.0

@@ -182,6 +182,10 @@ typedef struct evo_profile_entry {
   double bytes;      /* algorithmic DRAM bytes (inputs read + outputs)  */
 } evo_profile_entry;
 int evo_profile_only(const char *kernel_name);
+/* Pause (1) or resume (0) the timing of launches inside an open recording
+ * session, without synchronising: the timed launches of a session can be a
+ * sample of the work issued meanwhile. */
+int evo_profile_pause(int paused);
 int evo_profile_begin(void);
 int evo_profile_end(evo_stream_t stream, evo_profile_entry *out, int cap);
 

@@ -108,6 +108,7 @@ __device__ __forceinline__ void load_tile(bf16 (*dst)[LD], const bf16 *src, int6
 // ------------------------------------------------------------------ BF16 fwd
 template <int CP>
 __global__ void __launch_bounds__(128) attn_fwd_mma(AttnArgs a) {
+  pdl_entry();
   constexpr int LD = CP + 8;
   __shared__ __align__(16) bf16 Qs[64][LD];
   __shared__ __align__(16) bf16 Ks[2][64][LD];
@@ -265,6 +266,7 @@ __global__ void __launch_bounds__(128) attn_fwd_mma(AttnArgs a) {
 // memory and atomics; dbias += dS via atomics.
 template <int CP>
 __global__ void __launch_bounds__(128) attn_bwd_mma(AttnArgs a) {
+  pdl_entry();
   constexpr int LD = CP + 8;
   __shared__ __align__(16) bf16 Ks[64][LD];
   __shared__ __align__(16) bf16 Vs[64][LD];
@@ -459,6 +461,7 @@ __global__ void __launch_bounds__(128) attn_bwd_mma(AttnArgs a) {
 // ------------------------------------------------------------------ FP32 plain
 template <int CM>
 __global__ void __launch_bounds__(128) attn_fwd_simt(AttnArgs a) {
+  pdl_entry();
   __shared__ float Ks[32][CM], Vs[32][CM];
   __shared__ float Mk[32];
   const int b = blockIdx.z, h = blockIdx.y;
@@ -524,6 +527,7 @@ __global__ void __launch_bounds__(128) attn_fwd_simt(AttnArgs a) {
 // dq (unscaled, into dq_acc) and dbias: one thread per query.
 template <int CM>
 __global__ void __launch_bounds__(128) attn_bwd_dq_simt(AttnArgs a) {
+  pdl_entry();
   __shared__ float Ks[32][CM], Vs[32][CM];
   __shared__ float Mk[32];
   const int b = blockIdx.z, h = blockIdx.y;
@@ -586,6 +590,7 @@ __global__ void __launch_bounds__(128) attn_bwd_dq_simt(AttnArgs a) {
 // dk, dv: one thread per key.
 template <int CM>
 __global__ void __launch_bounds__(128) attn_bwd_dkv_simt(AttnArgs a) {
+  pdl_entry();
   __shared__ float Qs[32][CM], dOs[32][CM];
   __shared__ float Ls[32], Ds[32];
   const int b = blockIdx.z, h = blockIdx.y;
@@ -673,12 +678,12 @@ cudaError_t attn_fwd(const AttnArgs &a, int use_bf16, cudaStream_t s) {
   if (use_bf16) {
     if (!mma_ok(a)) return cudaErrorInvalidValue;
     dim3 grid((a.X + 63) / 64, a.H, a.B1);
-    if (a.c <= 16) attn_fwd_mma<16><<<grid, 128, 0, s>>>(a);
-    else attn_fwd_mma<32><<<grid, 128, 0, s>>>(a);
+    if (a.c <= 16) launch_k(attn_fwd_mma<16>, grid, 128, 0, s, a);
+    else launch_k(attn_fwd_mma<32>, grid, 128, 0, s, a);
   } else {
     dim3 grid((a.X + 127) / 128, a.H, a.B1);
-    if (a.c <= 8) attn_fwd_simt<8><<<grid, 128, 0, s>>>(a);
-    else if (a.c <= 32) attn_fwd_simt<32><<<grid, 128, 0, s>>>(a);
+    if (a.c <= 8) launch_k(attn_fwd_simt<8>, grid, 128, 0, s, a);
+    else if (a.c <= 32) launch_k(attn_fwd_simt<32>, grid, 128, 0, s, a);
     else return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
@@ -694,16 +699,16 @@ static cudaError_t attn_bwd_accumulating(const AttnArgs &a, int use_bf16, cudaSt
     if (use_bf16) {
       if (!mma_ok(a)) return cudaErrorInvalidValue;
       dim3 grid((a.Y + 63) / 64, a.H, a.B1);
-      if (a.c <= 16) attn_bwd_mma<16><<<grid, 128, 0, s>>>(a);
-      else attn_bwd_mma<32><<<grid, 128, 0, s>>>(a);
+      if (a.c <= 16) launch_k(attn_bwd_mma<16>, grid, 128, 0, s, a);
+      else launch_k(attn_bwd_mma<32>, grid, 128, 0, s, a);
     } else {
       dim3 gq((a.X + 127) / 128, a.H, a.B1), gk((a.Y + 127) / 128, a.H, a.B1);
       if (a.c <= 8) {
-        attn_bwd_dq_simt<8><<<gq, 128, 0, s>>>(a);
-        attn_bwd_dkv_simt<8><<<gk, 128, 0, s>>>(a);
+        launch_k(attn_bwd_dq_simt<8>, gq, 128, 0, s, a);
+        launch_k(attn_bwd_dkv_simt<8>, gk, 128, 0, s, a);
       } else if (a.c <= 32) {
-        attn_bwd_dq_simt<32><<<gq, 128, 0, s>>>(a);
-        attn_bwd_dkv_simt<32><<<gk, 128, 0, s>>>(a);
+        launch_k(attn_bwd_dq_simt<32>, gq, 128, 0, s, a);
+        launch_k(attn_bwd_dkv_simt<32>, gk, 128, 0, s, a);
       } else {
         return cudaErrorInvalidValue;
       }

@@ -116,6 +116,7 @@ __global__ void __launch_bounds__(AT_WARPS * 32) attn_fwd_tc(const __grid_consta
                                                              const __grid_constant__ CUtensorMap tmK,
                                                              const __grid_constant__ CUtensorMap tmV,
                                                              const __grid_constant__ CUtensorMap tmB, AttnTcArgs A) {
+  pdl_entry();
   extern __shared__ uint8_t dsm[];
   __shared__ __align__(8) uint64_t bar_qk, bar_v, bar_s, bar_o, bar_b[AT_WARPS][AT_BRING];
   __shared__ uint32_t tmem_slot;
@@ -420,6 +421,7 @@ __global__ void __launch_bounds__(AT_WARPS * 32, 1) attn_bwd_tc(const __grid_con
                                                                 const __grid_constant__ CUtensorMap tmO,
                                                                 const __grid_constant__ CUtensorMap tmB,
                                                                 AttnTcBwdArgs A) {
+  pdl_entry();
   extern __shared__ uint8_t dsm[];
   __shared__ __align__(8) uint64_t bar_in, bar_sd, bar_mm, bar_b[AT_WARPS][2];
   __shared__ uint32_t tmem_slot;
@@ -778,7 +780,7 @@ cudaError_t attn_fwd_tc_launch(const AttnArgs &a, cudaStream_t s, double flops, 
   }
   dim3 grid((a.X + AT_QROWS - 1) / AT_QROWS, a.H, a.B1);
   Prof p("attn_fwd_tc", s, flops, bytes);
-  attn_fwd_tc<<<grid, AT_WARPS * 32, AT_SMEM, s>>>(tq, tk, tv, tb, A);
+  launch_k(attn_fwd_tc, grid, AT_WARPS * 32, AT_SMEM, s, tq, tk, tv, tb, A);
   return cudaGetLastError();
 }
 
@@ -818,7 +820,7 @@ cudaError_t attn_bwd_tc_launch(const AttnArgs &a, cudaStream_t s, double flops, 
   }
   dim3 grid(a.H, a.B1);
   Prof p("attn_bwd_tc", s, flops, bytes);
-  attn_bwd_tc<<<grid, AT_WARPS * 32, BT_SMEM, s>>>(tq, tk, tv, to, tb, A);
+  launch_k(attn_bwd_tc, grid, AT_WARPS * 32, BT_SMEM, s, tq, tk, tv, to, tb, A);
   return cudaGetLastError();
 }
 

@@ -1,5 +1,6 @@
 // Shared device/host helpers of libevo (internal).
 #pragma once
+#include <utility>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -36,6 +37,38 @@ __device__ __forceinline__ uint64_t globaltimer_ns() {
   uint64_t t;
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
   return t;
+}
+
+// Programmatic dependent launch.  Every kernel of the library starts with
+// pdl_entry(): it waits until the kernels before it in the stream have
+// finished and their writes are visible (griddepcontrol.wait), then lets the
+// next kernel's blocks be scheduled as soon as all of this kernel's blocks
+// have started (griddepcontrol.launch_dependents).  The next kernel's launch
+// and prologue thus overlap this kernel's tail, while no kernel touches
+// memory before its predecessors are done.  Kernels launched without the
+// attribute (pdl_enabled() false) see both instructions as no-ops.
+__device__ __forceinline__ void pdl_entry() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+// Launch attribute switch (on unless EVO_PDL=0 in the environment).
+bool pdl_enabled();
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_k(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                            Args &&...args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = pdl_enabled() ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
 }
 
 // Output index map of GEMM epilogues:

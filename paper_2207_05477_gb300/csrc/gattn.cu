@@ -40,6 +40,7 @@ template <typename T, int H, int CD>
 __global__ void __launch_bounds__(NT) gattn_fwd_k(const T *qkvg, int64_t ld, int S, int R, const float *mask,
                                                   float scale, float *qbar_out, float *obar_out, float *stats,
                                                   T *o_gate) {
+  pdl_entry();
   constexpr int HC = H * CD;
   extern __shared__ float lg[];  // [S][H] logits (log2 units)
   __shared__ float red[NT / 32 * HC];
@@ -148,6 +149,7 @@ template <typename T, int H, int CD>
 __global__ void __launch_bounds__(NT) gattn_bwd_k(const T *qkvg, int64_t ld, int S, int R, const float *mask,
                                                   float scale, const float *qbar_in, const float *obar_in,
                                                   const float *stats, const T *dog, T *dqkvg) {
+  pdl_entry();
   constexpr int HC = H * CD;
   extern __shared__ float lg[];  // [S][H] probabilities
   __shared__ float red[NT / 32 * HC];
@@ -271,7 +273,7 @@ cudaError_t launch_fwd(const GlobalAttnArgs &a, cudaStream_t s) {
   if (sm > 200 * 1024) return cudaErrorInvalidValue;
   if (a.H == 8 && a.c == 8) {
     if (sm > 48 * 1024) cudaFuncSetAttribute(gattn_fwd_k<T, 8, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    gattn_fwd_k<T, 8, 8><<<a.R, NT, sm, s>>>((const T *)a.qkvg, a.ld, a.S, a.R, a.mask, a.scale, a.qbar,
+    launch_k(gattn_fwd_k<T, 8, 8>, a.R, NT, sm, s, (const T *)a.qkvg, a.ld, a.S, a.R, a.mask, a.scale, a.qbar,
                                             (float *)a.o_att_bar, a.lse2, (T *)a.o_gate);
     return cudaGetLastError();
   }
@@ -284,7 +286,7 @@ cudaError_t launch_bwd(const GlobalAttnArgs &a, const void *dog, void *dqkvg, cu
   if (sm > 200 * 1024) return cudaErrorInvalidValue;
   if (a.H == 8 && a.c == 8) {
     if (sm > 48 * 1024) cudaFuncSetAttribute(gattn_bwd_k<T, 8, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    gattn_bwd_k<T, 8, 8><<<a.R, NT, sm, s>>>((const T *)a.qkvg, a.ld, a.S, a.R, a.mask, a.scale, a.qbar,
+    launch_k(gattn_bwd_k<T, 8, 8>, a.R, NT, sm, s, (const T *)a.qkvg, a.ld, a.S, a.R, a.mask, a.scale, a.qbar,
                                             (const float *)a.o_att_bar, a.lse2, (const T *)dog, (T *)dqkvg);
     return cudaGetLastError();
   }

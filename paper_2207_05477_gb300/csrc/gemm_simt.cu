@@ -10,6 +10,7 @@ constexpr int BM = 64, BN = 64, BK = 16;
 
 template <typename T>
 __global__ void __launch_bounds__(256) gemm_simt_kernel(GemmOp g) {
+  pdl_entry();
   __shared__ float As[BK][BM + 4];
   __shared__ float Bs[BK][BN + 4];
   const int tid = threadIdx.x;
@@ -76,7 +77,7 @@ cudaError_t gemm_simt_f32(const GemmOp &g, cudaStream_t s) {
   dim3 grid((g.N + BN - 1) / BN, (g.M + BM - 1) / BM, g.batch * g.splits);
   Prof p("gemm_simt", s, 2.0 * g.M * g.N * (double)g.K * g.batch,
          4.0 * g.batch * ((double)g.M * g.K + (double)g.N * g.K + (double)g.M * g.N));
-  gemm_simt_kernel<float><<<grid, 256, 0, s>>>(g);
+  launch_k(gemm_simt_kernel<float>, grid, 256, 0, s, g);
   return cudaGetLastError();
 }
 

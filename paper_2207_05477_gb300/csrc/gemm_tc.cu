@@ -300,6 +300,7 @@ __global__ void __launch_bounds__(576, 1)
     gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                    const __grid_constant__ CUtensorMap tmC, const __grid_constant__ CUtensorMap tmOpA,
                    const __grid_constant__ CUtensorMap tmRes, GemmOp g, TcLaunch L) {
+  pdl_entry();
   using C = TcCfg<BN, AMN, BMN>;
   extern __shared__ uint8_t dsmem[];
   __shared__ __align__(8) uint64_t full_bar[MAX_STAGES];
@@ -703,6 +704,7 @@ __global__ void __launch_bounds__(576, 1)
 }
 
 __global__ void debug_wait_kernel(int64_t limit_ns) {
+  pdl_entry();
   // One mbarrier that nothing ever arrives on: the bounded wait runs out,
   // records the timeout in the device error word and the kernel returns.
   __shared__ __align__(8) uint64_t bar;
@@ -873,7 +875,7 @@ cudaError_t launch_tc(const GemmOp &g, cudaStream_t s) {
                       : "gemm_tc",
          s, 2.0 * g.M * g.N * (double)g.K * g.batch,
          g.batch * (2.0 * ((double)g.M * g.K + (double)g.N * g.K) + cbytes * g.M * g.N));
-  gemm_tc_kernel<BN, AMN, BMN><<<grid, 32 * (2 + EPI_WARPS), smem, s>>>(ta, tb, tc, topa, tres, g, L);
+  launch_k(gemm_tc_kernel<BN, AMN, BMN>, grid, 32 * (2 + EPI_WARPS), smem, s, ta, tb, tc, topa, tres, g, L);
   return cudaGetLastError();
 }
 
@@ -896,7 +898,7 @@ cudaError_t error_word_read_clear(int *out) {
 
 cudaError_t debug_wait(int64_t limit_ns, cudaStream_t s) {
   Prof p("debug_wait", s);
-  debug_wait_kernel<<<1, 32, 0, s>>>(limit_ns);
+  launch_k(debug_wait_kernel, 1, 32, 0, s, limit_ns);
   return cudaGetLastError();
 }
 

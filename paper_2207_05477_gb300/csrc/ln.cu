@@ -12,6 +12,7 @@ constexpr float LN_EPS = 1e-5f;
 template <typename T, int CPL>
 __global__ void __launch_bounds__(256) ln_fwd_rows(const T *x, const float *gamma, const float *beta, T *y,
                                                    int64_t M, int C) {
+  pdl_entry();
   const int lane = threadIdx.x & 31;
   const int64_t row = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
   if (row >= M) return;
@@ -52,6 +53,7 @@ template <typename T>
 __global__ void __launch_bounds__(256) ln_bwd_rows(const T *dy, const T *x, const float *gamma, float *dacc, T *dcopy,
                                                    T *dx_out, int64_t M, int C, int64_t rows_per_blk,
                                                    float *dgamma, float *dbeta) {
+  pdl_entry();
   extern __shared__ float sh[];  // [8][2C]
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   float *mine = sh + warp * 2 * C;
@@ -128,6 +130,7 @@ template <typename T, int P, int NR>
 __global__ void __launch_bounds__(256) ln_bwd_rows_vec(const T *dy, const T *x, const float *gamma, float *dacc,
                                                        T *dcopy, T *dx_out, int64_t M,
                                                        int64_t rows_per_blk, float *dgamma, float *dbeta) {
+  pdl_entry();
   constexpr int C = 64 * P;
   __shared__ float red[8][2 * C];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -225,6 +228,7 @@ __global__ void __launch_bounds__(256) ln_bwd_rows_vec(const T *dy, const T *x, 
 template <typename T, int P>
 __global__ void __launch_bounds__(256) ln_fwd_rows_vec(const T *x, const float *gamma, const float *beta, T *y,
                                                        int64_t M) {
+  pdl_entry();
   constexpr int C = 64 * P;
   const int lane = threadIdx.x & 31;
   const int64_t row = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
@@ -253,6 +257,7 @@ __global__ void __launch_bounds__(256) ln_fwd_rows_vec(const T *x, const float *
 template <typename T>
 __global__ void __launch_bounds__(256) ln_fwd_cm_k(const T *x, int64_t pitch, const float *gamma, const float *beta,
                                                    T *y, int R, int C) {
+  pdl_entry();
   extern __shared__ float tile[];  // [C][33]
   const int i = blockIdx.y, j0 = blockIdx.x * 32;
   const int64_t plane = (int64_t)R * pitch;
@@ -282,6 +287,7 @@ __global__ void __launch_bounds__(256) ln_fwd_cm_k(const T *x, int64_t pitch, co
 template <typename T>
 __global__ void __launch_bounds__(256) ln_bwd_cm_k(const T *dy, const T *x, int64_t pitch, const float *gamma, T *dx,
                                                    int R, int C, float *dgamma, float *dbeta) {
+  pdl_entry();
   extern __shared__ float sm[];  // xt [C][33], dxt [C][33], acc [8][2C]
   float *xt = sm;
   float *dxt = sm + C * 33;
@@ -347,10 +353,10 @@ cudaError_t ln_fwd_t(const void *x, const float *gamma, const float *beta, void 
   const T *xx = (const T *)x;
   T *yy = (T *)y;
   switch (C) {
-    case 64: ln_fwd_rows_vec<T, 1><<<grid, 256, 0, s>>>(xx, gamma, beta, yy, M); break;
-    case 128: ln_fwd_rows_vec<T, 2><<<grid, 256, 0, s>>>(xx, gamma, beta, yy, M); break;
-    case 256: ln_fwd_rows_vec<T, 4><<<grid, 256, 0, s>>>(xx, gamma, beta, yy, M); break;
-    default: ln_fwd_rows<T, 0><<<grid, 256, 0, s>>>(xx, gamma, beta, yy, M, C); break;
+    case 64: launch_k(ln_fwd_rows_vec<T, 1>, grid, 256, 0, s, xx, gamma, beta, yy, M); break;
+    case 128: launch_k(ln_fwd_rows_vec<T, 2>, grid, 256, 0, s, xx, gamma, beta, yy, M); break;
+    case 256: launch_k(ln_fwd_rows_vec<T, 4>, grid, 256, 0, s, xx, gamma, beta, yy, M); break;
+    default: launch_k(ln_fwd_rows<T, 0>, grid, 256, 0, s, xx, gamma, beta, yy, M, C); break;
   }
   return cudaGetLastError();
 }
@@ -377,9 +383,9 @@ cudaError_t ln_fwd_cm(const void *x, int64_t pitch, const float *gamma, const fl
   dim3 grid((R + 31) / 32, R);
   const size_t sm = (size_t)C * 33 * sizeof(float);
   if (use_bf16)
-    ln_fwd_cm_k<bf16><<<grid, 256, sm, s>>>((const bf16 *)x, pitch, gamma, beta, (bf16 *)y, R, C);
+    launch_k(ln_fwd_cm_k<bf16>, grid, 256, sm, s, (const bf16 *)x, pitch, gamma, beta, (bf16 *)y, R, C);
   else
-    ln_fwd_cm_k<float><<<grid, 256, sm, s>>>((const float *)x, pitch, gamma, beta, (float *)y, R, C);
+    launch_k(ln_fwd_cm_k<float>, grid, 256, sm, s, (const float *)x, pitch, gamma, beta, (float *)y, R, C);
   return cudaGetLastError();
 }
 
@@ -392,10 +398,10 @@ cudaError_t ln_bwd(const void *dy, const void *x, const float *gamma, float *dac
 #define EVO_LN_BWD_VEC(P, NR)                                                                                    \
   if (C == 64 * P) {                                                                                             \
     if (use_bf16)                                                                                                \
-      ln_bwd_rows_vec<bf16, P, NR><<<nb, 256, 0, s>>>((const bf16 *)dy, (const bf16 *)x, gamma, dacc,           \
+      launch_k(ln_bwd_rows_vec<bf16, P, NR>, nb, 256, 0, s, (const bf16 *)dy, (const bf16 *)x, gamma, dacc,           \
                                                       (bf16 *)dcopy, (bf16 *)dx_out, M, rpb, dgamma, dbeta);     \
     else                                                                                                         \
-      ln_bwd_rows_vec<float, P, NR><<<nb, 256, 0, s>>>((const float *)dy, (const float *)x, gamma, dacc,        \
+      launch_k(ln_bwd_rows_vec<float, P, NR>, nb, 256, 0, s, (const float *)dy, (const float *)x, gamma, dacc,        \
                                                        (float *)dcopy, (float *)dx_out, M, rpb, dgamma, dbeta);  \
     return cudaGetLastError();                                                                                   \
   }
@@ -405,10 +411,10 @@ cudaError_t ln_bwd(const void *dy, const void *x, const float *gamma, float *dac
 #undef EVO_LN_BWD_VEC
   const size_t sm = (size_t)8 * 2 * C * sizeof(float);
   if (use_bf16)
-    ln_bwd_rows<bf16><<<nb, 256, sm, s>>>((const bf16 *)dy, (const bf16 *)x, gamma, dacc, (bf16 *)dcopy,
+    launch_k(ln_bwd_rows<bf16>, nb, 256, sm, s, (const bf16 *)dy, (const bf16 *)x, gamma, dacc, (bf16 *)dcopy,
                                           (bf16 *)dx_out, M, C, rpb, dgamma, dbeta);
   else
-    ln_bwd_rows<float><<<nb, 256, sm, s>>>((const float *)dy, (const float *)x, gamma, dacc, (float *)dcopy,
+    launch_k(ln_bwd_rows<float>, nb, 256, sm, s, (const float *)dy, (const float *)x, gamma, dacc, (float *)dcopy,
                                            (float *)dx_out, M, C, rpb, dgamma, dbeta);
   return cudaGetLastError();
 }
@@ -425,10 +431,10 @@ cudaError_t ln_bwd_cm(const void *dy, const void *x, int64_t pitch, const float 
     if (e != cudaSuccess) return e;
   }
   if (use_bf16)
-    ln_bwd_cm_k<bf16><<<grid, 256, sm, s>>>((const bf16 *)dy, (const bf16 *)x, pitch, gamma, (bf16 *)dx, R, C,
+    launch_k(ln_bwd_cm_k<bf16>, grid, 256, sm, s, (const bf16 *)dy, (const bf16 *)x, pitch, gamma, (bf16 *)dx, R, C,
                                             dgamma, dbeta);
   else
-    ln_bwd_cm_k<float><<<grid, 256, sm, s>>>((const float *)dy, (const float *)x, pitch, gamma, (float *)dx, R,
+    launch_k(ln_bwd_cm_k<float>, grid, 256, sm, s, (const float *)dy, (const float *)x, pitch, gamma, (float *)dx, R,
                                              C, dgamma, dbeta);
   return cudaGetLastError();
 }

@@ -40,6 +40,7 @@ __device__ __forceinline__ void st8(bf16 *p, const float (&v)[8]) {
 // ------------------------------------------------------------- reductions
 // 32 columns per block; the 8 warps split the partial rows, then combine.
 __global__ void __launch_bounds__(256) reduce_partials_k(const float *part, int nblk, int64_t ld, int N, float *out) {
+  pdl_entry();
   __shared__ float s[8][33];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int n = blockIdx.x * 32 + lane;
@@ -61,6 +62,7 @@ __global__ void __launch_bounds__(256) reduce_partials_k(const float *part, int 
 template <typename T>
 __global__ void __launch_bounds__(256) colsum_k(const T *x, int64_t ld, int64_t M, int N,
                                                 int64_t rows_per_blk, float *out) {
+  pdl_entry();
   __shared__ float s[8][64];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int n = blockIdx.x * 64 + 2 * lane;
@@ -84,6 +86,7 @@ __global__ void __launch_bounds__(256) colsum_k(const T *x, int64_t ld, int64_t 
 }
 
 __global__ void reduce_splits_k(const float *part, int splits, int64_t n, float *out) {
+  pdl_entry();
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   float t = 0.f;
@@ -94,6 +97,7 @@ __global__ void reduce_splits_k(const float *part, int splits, int64_t n, float 
 // out(m, n) = sum_s part[(s*M + m)*N + n] in bf16 at offset map(m, n); a
 // thread owns two adjacent columns (N even).
 __global__ void reduce_splits_map_k(const float *part, int splits, int M, int N, OutMap map, bf16 *out) {
+  pdl_entry();
   const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 2;
   if (i >= (int64_t)M * N) return;
   const int m = (int)(i / N), n = (int)(i - (int64_t)m * N);
@@ -115,6 +119,7 @@ __global__ void reduce_splits_map_k(const float *part, int splits, int M, int N,
 // ------------------------------------------------------------- pair bias
 template <typename T>
 __global__ void head_proj_fwd_k(const T *x, const float *w, float *out, int R, int C, int H, int transpose) {
+  pdl_entry();
   const int lane = threadIdx.x & 31;
   const int64_t p = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
   const int64_t P = (int64_t)R * R;
@@ -144,6 +149,7 @@ template <typename T>
 __global__ void __launch_bounds__(256) head_proj_bwd_k(const float *dbias, const T *x, const float *w, T *dx,
                                                        int accumulate, int R, int C, int H, int transpose,
                                                        int64_t pos_per_blk, float *dw) {
+  pdl_entry();
   extern __shared__ float acc[];  // [8 warps][H*C]
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   float *mine = acc + warp * H * C;
@@ -187,6 +193,7 @@ __global__ void __launch_bounds__(256) head_proj_bwd_k(const float *dbias, const
 template <int H>
 __global__ void __launch_bounds__(128) head_proj_fwd_v8(const bf16 *x, const float *w, float *out, int R, int C,
                                                         int transpose) {
+  pdl_entry();
   extern __shared__ float ws[];  // [H][C]
   for (int k = threadIdx.x; k < H * C; k += blockDim.x) ws[k] = w[k];
   __syncthreads();
@@ -219,6 +226,7 @@ template <int H, int PJ>
 __global__ void __launch_bounds__(256) head_proj_bwd_v8(const float *dbias, const bf16 *x, const float *w, bf16 *dx,
                                                         int accumulate, int R, int transpose,
                                                         int64_t pos_per_blk, float *dw) {
+  pdl_entry();
   constexpr int C = 64 * PJ;
   __shared__ float red[8][H * C];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -287,6 +295,7 @@ __global__ void __launch_bounds__(256) head_proj_bwd_v8(const float *dbias, cons
 template <typename T>
 __global__ void __launch_bounds__(256) trimul_gate_fwd_k(const T *abg, int64_t ld, const float *mask, T *A, T *B,
                                                          int64_t pitch, int R, int cm, int incoming) {
+  pdl_entry();
   __shared__ float as[4][32][33], bs[4][32][33];
   const int q0 = blockIdx.x * 32, r0 = blockIdx.y * 32, c0 = blockIdx.z * 4;
   for (int idx = threadIdx.x; idx < 32 * 32 * 4; idx += blockDim.x) {
@@ -321,6 +330,7 @@ template <typename T>
 __global__ void __launch_bounds__(256) trimul_gate_bwd_k(const T *dA, const T *dB, int64_t pitch, const T *abg,
                                                          int64_t ld, const float *mask, T *dabg, int R, int cm,
                                                          int incoming) {
+  pdl_entry();
   __shared__ float as[4][32][33], bs[4][32][33];
   const int q0 = blockIdx.x * 32, r0 = blockIdx.y * 32, c0 = blockIdx.z * 4;
   const int64_t plane = (int64_t)R * pitch;
@@ -363,6 +373,7 @@ __global__ void __launch_bounds__(256) trimul_gate_bwd_k(const T *dA, const T *d
 // (block z handles g columns z*8.., z*8 + 8).
 __global__ void __launch_bounds__(256) trimul_gate_fwd_v8(bf16 *abg, int64_t ld, const float *mask, bf16 *A, bf16 *B,
                                                           int64_t pitch, int R, int cm, int cz, int incoming) {
+  pdl_entry();
   __shared__ bf16 as[8][32][34], bs[8][32][34];
   const int q0 = blockIdx.x * 32, r0 = blockIdx.y * 32, c0 = blockIdx.z * 8;
   for (int idx = threadIdx.x; idx < 32 * 32; idx += blockDim.x) {
@@ -426,6 +437,7 @@ __global__ void __launch_bounds__(256) trimul_gate_fwd_v8(bf16 *abg, int64_t ld,
 __global__ void __launch_bounds__(256) trimul_gate_bwd_v8(const bf16 *dA, const bf16 *dB, int64_t pitch,
                                                           const bf16 *abg, int64_t ld, const float *mask, bf16 *dabg,
                                                           int R, int cm, int incoming) {
+  pdl_entry();
   __shared__ bf16 as[8][32][34], bs[8][32][34];
   const int q0 = blockIdx.x * 32, r0 = blockIdx.y * 32, c0 = blockIdx.z * 8;
   const int64_t plane = (int64_t)R * pitch;
@@ -486,6 +498,7 @@ __device__ __forceinline__ float sigm(float x) { return __fdividef(1.f, 1.f + __
 
 __global__ void __launch_bounds__(256) trimul_gate_fwd_t(bf16 *abg, int64_t ld, const float *mask, bf16 *A, bf16 *B,
                                                          int64_t pitch, int R, int cm, int cz, int incoming) {
+  pdl_entry();
   __shared__ bf16 as[TG_ROWS][TG_COLS][TG_LDC];
   __shared__ bf16 bs[TG_ROWS][TG_COLS][TG_LDC];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -551,6 +564,7 @@ __global__ void __launch_bounds__(256) trimul_gate_fwd_t(bf16 *abg, int64_t ld, 
 __global__ void __launch_bounds__(256) trimul_gate_bwd_t(const bf16 *dA, const bf16 *dB, int64_t pitch,
                                                          const bf16 *abg, int64_t ld, const float *mask, bf16 *dabg,
                                                          int R, int cm, int incoming) {
+  pdl_entry();
   __shared__ bf16 as[TG_ROWS][TG_COLS][TG_LDC];
   __shared__ bf16 bs[TG_ROWS][TG_COLS][TG_LDC];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -610,6 +624,7 @@ __global__ void __launch_bounds__(256) trimul_gate_bwd_t(const bf16 *dA, const b
 
 template <typename T>
 __global__ void sigmoid_cols_k(T *x, int64_t ld, int col0, int ncols, int64_t P) {
+  pdl_entry();
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= P * ncols) return;
   int64_t p;
@@ -622,6 +637,7 @@ __global__ void sigmoid_cols_k(T *x, int64_t ld, int col0, int ncols, int64_t P)
 template <typename T>
 __global__ void gate_out_bwd_k(const T *dz, const T *g, int64_t g_ld, const T *y, T *dy, T *dgpre, int64_t dg_ld,
                                int64_t P, int C) {
+  pdl_entry();
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= P * C) return;
   int64_t p;
@@ -636,6 +652,7 @@ __global__ void gate_out_bwd_k(const T *dz, const T *g, int64_t g_ld, const T *y
 template <typename T>
 __global__ void attn_gate_bwd_k(AttnArgs a, const T *dog, T *dgpre, int64_t sGb_d, int64_t sGx_d, T *do_att,
                                 float *D) {
+  pdl_entry();
   const int lane = threadIdx.x & 31;
   const int64_t row = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
   if (row >= (int64_t)a.B1 * a.X) return;
@@ -662,6 +679,7 @@ __global__ void attn_gate_bwd_k(AttnArgs a, const T *dog, T *dgpre, int64_t sGb_
 
 template <typename T>
 __global__ void attn_dq_store_k(AttnArgs a, T *dq) {
+  pdl_entry();
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int hc = a.H * a.c;
   if (i >= (int64_t)a.B1 * a.X * hc) return;
@@ -674,6 +692,7 @@ __global__ void attn_dq_store_k(AttnArgs a, T *dq) {
 
 // ------------------------------------------------------------ OPM, scaling
 __global__ void opm_inv_norm_k(const float *mask, float *inv, int S, int R, float eps) {
+  pdl_entry();
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= (int64_t)R * R) return;
   int64_t i64;
@@ -687,6 +706,7 @@ __global__ void opm_inv_norm_k(const float *mask, float *inv, int S, int R, floa
 
 template <typename T>
 __global__ void row_scale_k(const T *x, const float *scale, T *y, int64_t M, int C) {
+  pdl_entry();
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= M * C) return;
   int64_t r;
@@ -697,11 +717,13 @@ __global__ void row_scale_k(const T *x, const float *scale, T *y, int64_t M, int
 
 template <typename T>
 __global__ void to_f32_k(const T *src, float *dst, int64_t n) {
+  pdl_entry();
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) dst[i] = ldf(src + i);
 }
 template <typename T>
 __global__ void from_f32_k(const float *src, T *dst, int64_t n) {
+  pdl_entry();
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) stf(dst + i, src[i]);
 }
@@ -712,13 +734,13 @@ inline unsigned nblk(int64_t n, int t = 256) { return (unsigned)((n + t - 1) / t
 
 cudaError_t reduce_partials(const float *part, int nb, int N, float *out, cudaStream_t s) {
   Prof prof("reduce_partials", s, 0, 4.0 * nb * (double)N, 1);
-  reduce_partials_k<<<(N + 31) / 32, 256, 0, s>>>(part, nb, N, N, out);
+  launch_k(reduce_partials_k, (N + 31) / 32, 256, 0, s, part, nb, N, N, out);
   return cudaGetLastError();
 }
 // Variant with a leading dimension (LayerNorm partials hold gamma and beta sums).
 cudaError_t reduce_partials_ld(const float *part, int nb, int64_t ld, int N, float *out, cudaStream_t s) {
   Prof prof("reduce_partials", s, 0, 4.0 * nb * (double)N, 1);
-  reduce_partials_k<<<(N + 31) / 32, 256, 0, s>>>(part, nb, ld, N, out);
+  launch_k(reduce_partials_k, (N + 31) / 32, 256, 0, s, part, nb, ld, N, out);
   return cudaGetLastError();
 }
 
@@ -731,14 +753,14 @@ cudaError_t colsum(const void *x, int64_t ld, int64_t M, int N, int use_bf16, cu
   const int nb = colsum_blocks(M);
   const int64_t rpb = (M + nb - 1) / nb;
   const dim3 grid((N + 63) / 64, nb);
-  if (use_bf16) colsum_k<bf16><<<grid, 256, 0, s>>>((const bf16 *)x, ld, M, N, rpb, out);
-  else colsum_k<float><<<grid, 256, 0, s>>>((const float *)x, ld, M, N, rpb, out);
+  if (use_bf16) launch_k(colsum_k<bf16>, grid, 256, 0, s, (const bf16 *)x, ld, M, N, rpb, out);
+  else launch_k(colsum_k<float>, grid, 256, 0, s, (const float *)x, ld, M, N, rpb, out);
   return cudaGetLastError();
 }
 
 cudaError_t reduce_splits(const float *part, int splits, int64_t n, float *out, cudaStream_t s) {
   Prof prof("reduce_splits", s, 0, 4.0 * (splits + 2) * (double)n, 1);
-  reduce_splits_k<<<nblk(n), 256, 0, s>>>(part, splits, n, out);
+  launch_k(reduce_splits_k, nblk(n), 256, 0, s, part, splits, n, out);
   return cudaGetLastError();
 }
 
@@ -747,7 +769,7 @@ cudaError_t reduce_splits_map(const float *part, int splits, int M, int N, const
   if (N % 2) return cudaErrorInvalidValue;
   Prof prof("reduce_splits", s, 0, (4.0 * splits + 2.0) * (double)M * N, 1);
   const int64_t pairs = (int64_t)M * N / 2;
-  reduce_splits_map_k<<<nblk(pairs), 256, 0, s>>>(part, splits, M, N, map, (bf16 *)out);
+  launch_k(reduce_splits_map_k, nblk(pairs), 256, 0, s, part, splits, M, N, map, (bf16 *)out);
   return cudaGetLastError();
 }
 
@@ -758,10 +780,10 @@ cudaError_t head_proj_fwd(const void *x, const float *w, float *out, int R, int 
   const int64_t P = (int64_t)R * R;
   if (use_bf16 && C % 8 == 0 && (((uintptr_t)x) & 15u) == 0 && (H == 4 || H == 8)) {
     const size_t sm = (size_t)H * C * sizeof(float);
-    if (H == 4) head_proj_fwd_v8<4><<<nblk(P, 128), 128, sm, s>>>((const bf16 *)x, w, out, R, C, transpose);
-    else head_proj_fwd_v8<8><<<nblk(P, 128), 128, sm, s>>>((const bf16 *)x, w, out, R, C, transpose);
-  } else if (use_bf16) head_proj_fwd_k<bf16><<<nblk(P, 8), 256, 0, s>>>((const bf16 *)x, w, out, R, C, H, transpose);
-  else head_proj_fwd_k<float><<<nblk(P, 8), 256, 0, s>>>((const float *)x, w, out, R, C, H, transpose);
+    if (H == 4) launch_k(head_proj_fwd_v8<4>, nblk(P, 128), 128, sm, s, (const bf16 *)x, w, out, R, C, transpose);
+    else launch_k(head_proj_fwd_v8<8>, nblk(P, 128), 128, sm, s, (const bf16 *)x, w, out, R, C, transpose);
+  } else if (use_bf16) launch_k(head_proj_fwd_k<bf16>, nblk(P, 8), 256, 0, s, (const bf16 *)x, w, out, R, C, H, transpose);
+  else launch_k(head_proj_fwd_k<float>, nblk(P, 8), 256, 0, s, (const float *)x, w, out, R, C, H, transpose);
   return cudaGetLastError();
 }
 
@@ -778,16 +800,16 @@ cudaError_t head_proj_bwd(const float *dbias, const void *x, const float *w, voi
   if (sm > 48 * 1024) return cudaErrorInvalidValue;
   if (use_bf16 && C == 128 && (H == 4 || H == 8) && (((uintptr_t)x) & 3u) == 0 && (((uintptr_t)dx) & 3u) == 0) {
     if (H == 4)
-      head_proj_bwd_v8<4, 2><<<nb, 256, 0, s>>>(dbias, (const bf16 *)x, w, (bf16 *)dx, accumulate, R, transpose,
+      launch_k(head_proj_bwd_v8<4, 2>, nb, 256, 0, s, dbias, (const bf16 *)x, w, (bf16 *)dx, accumulate, R, transpose,
                                                 ppb, dw);
     else
-      head_proj_bwd_v8<8, 2><<<nb, 256, 0, s>>>(dbias, (const bf16 *)x, w, (bf16 *)dx, accumulate, R, transpose,
+      launch_k(head_proj_bwd_v8<8, 2>, nb, 256, 0, s, dbias, (const bf16 *)x, w, (bf16 *)dx, accumulate, R, transpose,
                                                 ppb, dw);
   } else if (use_bf16)
-    head_proj_bwd_k<bf16><<<nb, 256, sm, s>>>(dbias, (const bf16 *)x, w, (bf16 *)dx, accumulate, R, C, H,
+    launch_k(head_proj_bwd_k<bf16>, nb, 256, sm, s, dbias, (const bf16 *)x, w, (bf16 *)dx, accumulate, R, C, H,
                                               transpose, ppb, dw);
   else
-    head_proj_bwd_k<float><<<nb, 256, sm, s>>>(dbias, (const float *)x, w, (float *)dx, accumulate, R, C, H,
+    launch_k(head_proj_bwd_k<float>, nb, 256, sm, s, dbias, (const float *)x, w, (float *)dx, accumulate, R, C, H,
                                                transpose, ppb, dw);
   return cudaGetLastError();
 }
@@ -800,18 +822,18 @@ cudaError_t trimul_gate_fwd(void *abg, int64_t ld, const float *mask, void *A, v
   const bool v8 = cm % 8 == 0 && cz % 8 == 0 && ld % 8 == 0 && (((uintptr_t)abg) & 15u) == 0;
   if (use_bf16 && v8 && cm % TG_CH == 0 && (cz + TG_CH - 1) / TG_CH <= cm / TG_CH) {
     dim3 gt((R + TG_COLS - 1) / TG_COLS, (R + TG_ROWS - 1) / TG_ROWS, cm / TG_CH);
-    trimul_gate_fwd_t<<<gt, 256, 0, s>>>((bf16 *)abg, ld, mask, (bf16 *)A, (bf16 *)B, pitch, R, cm, cz, incoming);
+    launch_k(trimul_gate_fwd_t, gt, 256, 0, s, (bf16 *)abg, ld, mask, (bf16 *)A, (bf16 *)B, pitch, R, cm, cz, incoming);
   } else if (use_bf16 && v8) {
     dim3 g8((R + 31) / 32, (R + 31) / 32, cm / 8);
-    trimul_gate_fwd_v8<<<g8, 256, 0, s>>>((bf16 *)abg, ld, mask, (bf16 *)A, (bf16 *)B, pitch, R, cm, cz, incoming);
+    launch_k(trimul_gate_fwd_v8, g8, 256, 0, s, (bf16 *)abg, ld, mask, (bf16 *)A, (bf16 *)B, pitch, R, cm, cz, incoming);
   } else if (use_bf16) {
-    trimul_gate_fwd_k<bf16><<<grid, 256, 0, s>>>((const bf16 *)abg, ld, mask, (bf16 *)A, (bf16 *)B, pitch, R, cm,
+    launch_k(trimul_gate_fwd_k<bf16>, grid, 256, 0, s, (const bf16 *)abg, ld, mask, (bf16 *)A, (bf16 *)B, pitch, R, cm,
                                                  incoming);
-    sigmoid_cols_k<bf16><<<nblk(P * cz), 256, 0, s>>>((bf16 *)abg, ld, 4 * cm, cz, P);
+    launch_k(sigmoid_cols_k<bf16>, nblk(P * cz), 256, 0, s, (bf16 *)abg, ld, 4 * cm, cz, P);
   } else {
-    trimul_gate_fwd_k<float><<<grid, 256, 0, s>>>((const float *)abg, ld, mask, (float *)A, (float *)B, pitch, R,
+    launch_k(trimul_gate_fwd_k<float>, grid, 256, 0, s, (const float *)abg, ld, mask, (float *)A, (float *)B, pitch, R,
                                                   cm, incoming);
-    sigmoid_cols_k<float><<<nblk(P * cz), 256, 0, s>>>((float *)abg, ld, 4 * cm, cz, P);
+    launch_k(sigmoid_cols_k<float>, nblk(P * cz), 256, 0, s, (float *)abg, ld, 4 * cm, cz, P);
   }
   return cudaGetLastError();
 }
@@ -823,17 +845,17 @@ cudaError_t trimul_gate_bwd(const void *dA, const void *dB, int64_t pitch, const
   const bool v8 = cm % 8 == 0 && ld % 8 == 0 && (((uintptr_t)abg) & 15u) == 0 && (((uintptr_t)dabg) & 15u) == 0;
   if (use_bf16 && v8 && cm % TG_CH == 0) {
     dim3 gt((R + TG_COLS - 1) / TG_COLS, (R + TG_ROWS - 1) / TG_ROWS, cm / TG_CH);
-    trimul_gate_bwd_t<<<gt, 256, 0, s>>>((const bf16 *)dA, (const bf16 *)dB, pitch, (const bf16 *)abg, ld, mask,
+    launch_k(trimul_gate_bwd_t, gt, 256, 0, s, (const bf16 *)dA, (const bf16 *)dB, pitch, (const bf16 *)abg, ld, mask,
                                          (bf16 *)dabg, R, cm, incoming);
   } else if (use_bf16 && v8) {
     dim3 g8((R + 31) / 32, (R + 31) / 32, cm / 8);
-    trimul_gate_bwd_v8<<<g8, 256, 0, s>>>((const bf16 *)dA, (const bf16 *)dB, pitch, (const bf16 *)abg, ld, mask,
+    launch_k(trimul_gate_bwd_v8, g8, 256, 0, s, (const bf16 *)dA, (const bf16 *)dB, pitch, (const bf16 *)abg, ld, mask,
                                           (bf16 *)dabg, R, cm, incoming);
   } else if (use_bf16)
-    trimul_gate_bwd_k<bf16><<<grid, 256, 0, s>>>((const bf16 *)dA, (const bf16 *)dB, pitch, (const bf16 *)abg, ld,
+    launch_k(trimul_gate_bwd_k<bf16>, grid, 256, 0, s, (const bf16 *)dA, (const bf16 *)dB, pitch, (const bf16 *)abg, ld,
                                                  mask, (bf16 *)dabg, R, cm, incoming);
   else
-    trimul_gate_bwd_k<float><<<grid, 256, 0, s>>>((const float *)dA, (const float *)dB, pitch, (const float *)abg, ld,
+    launch_k(trimul_gate_bwd_k<float>, grid, 256, 0, s, (const float *)dA, (const float *)dB, pitch, (const float *)abg, ld,
                                                   mask, (float *)dabg, R, cm, incoming);
   return cudaGetLastError();
 }
@@ -842,10 +864,10 @@ cudaError_t gate_out_bwd(const void *dz, const void *g, int64_t g_ld, const void
                          int64_t dg_ld, int64_t P, int C, int use_bf16, cudaStream_t s) {
   Prof prof("gate_out_bwd", s, 0, (use_bf16 ? 2.0 : 4.0) * (double)P * C * 5, 1);
   if (use_bf16)
-    gate_out_bwd_k<bf16><<<nblk(P * C), 256, 0, s>>>((const bf16 *)dz, (const bf16 *)g, g_ld, (const bf16 *)y,
+    launch_k(gate_out_bwd_k<bf16>, nblk(P * C), 256, 0, s, (const bf16 *)dz, (const bf16 *)g, g_ld, (const bf16 *)y,
                                                      (bf16 *)dy, (bf16 *)dgpre, dg_ld, P, C);
   else
-    gate_out_bwd_k<float><<<nblk(P * C), 256, 0, s>>>((const float *)dz, (const float *)g, g_ld, (const float *)y,
+    launch_k(gate_out_bwd_k<float>, nblk(P * C), 256, 0, s, (const float *)dz, (const float *)g, g_ld, (const float *)y,
                                                       (float *)dy, (float *)dgpre, dg_ld, P, C);
   return cudaGetLastError();
 }
@@ -855,10 +877,10 @@ cudaError_t attn_gate_bwd(const AttnArgs &a, const void *dog, void *dgpre, int64
   Prof prof("attn_gate_bwd", s, 0, (use_bf16 ? 2.0 : 4.0) * (double)a.B1 * a.X * a.H * a.c * 5, 1);
   const int64_t rows = (int64_t)a.B1 * a.X;
   if (use_bf16)
-    attn_gate_bwd_k<bf16><<<nblk(rows, 8), 256, 0, s>>>(a, (const bf16 *)dog, (bf16 *)dgpre, sGb_d, sGx_d,
+    launch_k(attn_gate_bwd_k<bf16>, nblk(rows, 8), 256, 0, s, a, (const bf16 *)dog, (bf16 *)dgpre, sGb_d, sGx_d,
                                                         (bf16 *)do_att, D);
   else
-    attn_gate_bwd_k<float><<<nblk(rows, 8), 256, 0, s>>>(a, (const float *)dog, (float *)dgpre, sGb_d, sGx_d,
+    launch_k(attn_gate_bwd_k<float>, nblk(rows, 8), 256, 0, s, a, (const float *)dog, (float *)dgpre, sGb_d, sGx_d,
                                                          (float *)do_att, D);
   return cudaGetLastError();
 }
@@ -866,39 +888,39 @@ cudaError_t attn_gate_bwd(const AttnArgs &a, const void *dog, void *dgpre, int64
 cudaError_t attn_dq_store(const AttnArgs &a, void *dq, int use_bf16, cudaStream_t s) {
   Prof prof("attn_dq_store", s, 0, (use_bf16 ? 6.0 : 8.0) * (double)a.B1 * a.X * a.H * a.c, 1);
   const int64_t n = (int64_t)a.B1 * a.X * a.H * a.c;
-  if (use_bf16) attn_dq_store_k<bf16><<<nblk(n), 256, 0, s>>>(a, (bf16 *)dq);
-  else attn_dq_store_k<float><<<nblk(n), 256, 0, s>>>(a, (float *)dq);
+  if (use_bf16) launch_k(attn_dq_store_k<bf16>, nblk(n), 256, 0, s, a, (bf16 *)dq);
+  else launch_k(attn_dq_store_k<float>, nblk(n), 256, 0, s, a, (float *)dq);
   return cudaGetLastError();
 }
 
 cudaError_t opm_inv_norm(const float *mask, float *inv, int S, int R, float eps, cudaStream_t s) {
   Prof prof("opm_inv_norm", s, 0, 8.0 * S * (double)R + 4.0 * R * (double)R, 1);
-  opm_inv_norm_k<<<nblk((int64_t)R * R), 256, 0, s>>>(mask, inv, S, R, eps);
+  launch_k(opm_inv_norm_k, nblk((int64_t)R * R), 256, 0, s, mask, inv, S, R, eps);
   return cudaGetLastError();
 }
 
 cudaError_t row_scale(const void *x, const float *scale, void *y, int64_t M, int C, int use_bf16, cudaStream_t s) {
   Prof prof("row_scale", s, 0, (use_bf16 ? 4.0 : 8.0) * M * (double)C, 1);
-  if (use_bf16) row_scale_k<bf16><<<nblk(M * C), 256, 0, s>>>((const bf16 *)x, scale, (bf16 *)y, M, C);
-  else row_scale_k<float><<<nblk(M * C), 256, 0, s>>>((const float *)x, scale, (float *)y, M, C);
+  if (use_bf16) launch_k(row_scale_k<bf16>, nblk(M * C), 256, 0, s, (const bf16 *)x, scale, (bf16 *)y, M, C);
+  else launch_k(row_scale_k<float>, nblk(M * C), 256, 0, s, (const float *)x, scale, (float *)y, M, C);
   return cudaGetLastError();
 }
 
 cudaError_t to_f32(const void *src, float *dst, int64_t n, int use_bf16, cudaStream_t s) {
   Prof prof("convert", s, 0, (use_bf16 ? 6.0 : 8.0) * n, 1);
-  if (use_bf16) to_f32_k<bf16><<<nblk(n), 256, 0, s>>>((const bf16 *)src, dst, n);
-  else to_f32_k<float><<<nblk(n), 256, 0, s>>>((const float *)src, dst, n);
+  if (use_bf16) launch_k(to_f32_k<bf16>, nblk(n), 256, 0, s, (const bf16 *)src, dst, n);
+  else launch_k(to_f32_k<float>, nblk(n), 256, 0, s, (const float *)src, dst, n);
   return cudaGetLastError();
 }
 cudaError_t from_f32(const float *src, void *dst, int64_t n, int use_bf16, cudaStream_t s) {
   Prof prof("convert", s, 0, (use_bf16 ? 6.0 : 8.0) * n, 1);
-  if (use_bf16) from_f32_k<bf16><<<nblk(n), 256, 0, s>>>(src, (bf16 *)dst, n);
-  else from_f32_k<float><<<nblk(n), 256, 0, s>>>(src, (float *)dst, n);
+  if (use_bf16) launch_k(from_f32_k<bf16>, nblk(n), 256, 0, s, src, (bf16 *)dst, n);
+  else launch_k(from_f32_k<float>, nblk(n), 256, 0, s, src, (float *)dst, n);
   return cudaGetLastError();
 }
 cudaError_t f32_to_bf16(const float *src, bf16 *dst, int64_t n, cudaStream_t s) {
   Prof prof("convert", s, 0, 6.0 * n, 1);
-  from_f32_k<bf16><<<nblk(n), 256, 0, s>>>(src, dst, n);
+  launch_k(from_f32_k<bf16>, nblk(n), 256, 0, s, src, dst, n);
   return cudaGetLastError();
 }
 

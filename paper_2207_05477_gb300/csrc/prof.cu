@@ -25,6 +25,7 @@ struct Rec {
 std::mutex g_mu;
 bool g_on = false;
 bool g_detail = false;
+bool g_paused = false;  // recording session open but launches not timed
 std::string g_only;  // record only this kernel name ("" = all)
 std::set<std::string> g_names;
 std::vector<Rec> g_recs;
@@ -33,9 +34,17 @@ size_t g_next = 0;
 
 }  // namespace
 
-bool prof_on() { return g_on; }
+bool prof_on() { return g_on && !g_paused; }
+
+bool pdl_enabled() {
+  static const bool on = [] {
+    const char *v = std::getenv("EVO_PDL");
+    return !(v && v[0] == '0');
+  }();
+  return on;
+}
 bool prof_wants(const char *name) {
-  if (!g_on) return false;
+  if (!g_on || g_paused) return false;
   std::lock_guard<std::mutex> lk(g_mu);
   return g_only.empty() || g_only == name;
 }
@@ -78,6 +87,12 @@ int evo_profile_only(const char *kernel_name) {
   return EVO_OK;
 }
 
+int evo_profile_pause(int paused) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  g_paused = paused != 0;
+  return EVO_OK;
+}
+
 int evo_profile_begin(void) {
   std::lock_guard<std::mutex> lk(g_mu);
   g_recs.clear();
@@ -92,6 +107,7 @@ int evo_profile_end(evo_stream_t stream, evo_profile_entry *out, int cap) {
   if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) return EVO_ERR_CUDA;
   std::lock_guard<std::mutex> lk(g_mu);
   g_on = false;
+  g_paused = false;
   g_only.clear();
   std::map<std::string, evo_profile_entry> agg;
   std::vector<std::string> order;

@@ -71,6 +71,7 @@ def lib():
         L.evo_get_error.argtypes = [_vp]
         L.evo_debug_wait_timeout.argtypes = [ctypes.c_longlong, _vp]
         L.evo_profile_only.argtypes = [ctypes.c_char_p]
+        L.evo_profile_pause.argtypes = [ctypes.c_int]
         L.evo_profile_begin.argtypes = []
         L.evo_profile_end.argtypes = [_vp, P(CProfileEntry), ctypes.c_int]
         L.evo_strerror.argtypes = [ctypes.c_int]
@@ -176,6 +177,11 @@ def debug_wait_timeout(limit_ns, stream=None):
 def profile_only(kernel_name=None):
     """Restrict the next profile recording to one kernel name (None: all)."""
     _check(lib().evo_profile_only(kernel_name.encode() if kernel_name else None), "evo_profile_only")
+
+
+def profile_pause(paused=True):
+    """Pause or resume launch timing within an open profile session (no synchronisation)."""
+    _check(lib().evo_profile_pause(1 if paused else 0), "evo_profile_pause")
 
 
 def profile_begin():
