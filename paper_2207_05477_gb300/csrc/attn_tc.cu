@@ -116,7 +116,7 @@ __global__ void __launch_bounds__(AT_WARPS * 32) attn_fwd_tc(const __grid_consta
                                                              const __grid_constant__ CUtensorMap tmK,
                                                              const __grid_constant__ CUtensorMap tmV,
                                                              const __grid_constant__ CUtensorMap tmB, AttnTcArgs A) {
-  pdl_entry();
+  pdl_trigger();
   extern __shared__ uint8_t dsm[];
   __shared__ __align__(8) uint64_t bar_qk, bar_v, bar_s, bar_o, bar_b[AT_WARPS][AT_BRING];
   __shared__ uint32_t tmem_slot;
@@ -155,6 +155,8 @@ __global__ void __launch_bounds__(AT_WARPS * 32) attn_fwd_tc(const __grid_consta
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = tmem_slot;
+  // global memory only from here on: wait for the kernels before this one
+  pdl_wait();
   // what this thread put in flight (drained after an abort): lane 0 of each
   // warp streams the pair bias of its rows and chunks; thread 0 issues the rest
   int bias_issued = 0, bias_done = 0;
@@ -421,7 +423,7 @@ __global__ void __launch_bounds__(AT_WARPS * 32, 1) attn_bwd_tc(const __grid_con
                                                                 const __grid_constant__ CUtensorMap tmO,
                                                                 const __grid_constant__ CUtensorMap tmB,
                                                                 AttnTcBwdArgs A) {
-  pdl_entry();
+  pdl_trigger();
   extern __shared__ uint8_t dsm[];
   __shared__ __align__(8) uint64_t bar_in, bar_sd, bar_mm, bar_b[AT_WARPS][2];
   __shared__ uint32_t tmem_slot;
@@ -456,6 +458,8 @@ __global__ void __launch_bounds__(AT_WARPS * 32, 1) attn_bwd_tc(const __grid_con
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = tmem_slot;
+  // global memory only from here on: wait for the kernels before this one
+  pdl_wait();
   bool in_issued = false;
   int nsd = 0, nmm = 0;  // commits issued on bar_sd / bar_mm (thread 0)
   if (tid == 0) {

@@ -287,11 +287,20 @@ struct Drv {
   void dW(const void *dY, int64_t ldY, int64_t Nout, const void *X, int64_t ldX, int64_t Kin, int64_t rows,
           const std::string &w) {
     GemmOp g = mk(Nout, Kin, rows, dY, ldY, 1, X, ldX, 1, nullptr, 0);
-    const int64_t tile = bf ? 128 : 64;
-    const int64_t tiles = ((Nout + tile - 1) / tile) * ((Kin + tile - 1) / tile);
-    int64_t sp = (2 * 152 + tiles - 1) / tiles;
-    sp = std::min<int64_t>(sp, std::max<int64_t>(1, rows / 256));
-    sp = std::max<int64_t>(1, std::min<int64_t>(sp, MAXSPLIT));
+    int64_t sp;
+    if (bf) {
+      // split K until the CTAs fill the SMs once (the tcgen05 GEMM is persistent,
+      // BN = 256 or 128), keeping at least eight 64-deep k-tiles per split; the
+      // partial products meet in the fp32 gradient through atomics
+      const int64_t bn = Kin > 128 && Kin % 256 == 0 ? 256 : 128;
+      const int64_t tiles = ((Nout + 127) / 128) * ((Kin + bn - 1) / bn);
+      sp = std::min<int64_t>((152 + tiles - 1) / tiles, std::max<int64_t>(1, rows / 512));
+    } else {
+      const int64_t tiles = ((Nout + 63) / 64) * ((Kin + 63) / 64);
+      sp = std::min<int64_t>((2 * 152 + tiles - 1) / tiles, std::max<int64_t>(1, rows / 256));
+      sp = std::min<int64_t>(sp, MAXSPLIT);
+    }
+    sp = std::max<int64_t>(1, sp);
     g.splits = (int)sp;
     if (bf) {
       // each K range adds its partial product straight into the fp32 gradient

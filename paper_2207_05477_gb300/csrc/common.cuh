@@ -51,6 +51,10 @@ __device__ __forceinline__ void pdl_entry() {
   asm volatile("griddepcontrol.wait;" ::: "memory");
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
+// The two halves, for kernels with a prologue that touches no global memory
+// (barrier set-up, tensor-memory allocation): trigger first, wait after it.
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
 // Launch attribute switch (on unless EVO_PDL=0 in the environment).
 bool pdl_enabled();

@@ -300,7 +300,7 @@ __global__ void __launch_bounds__(576, 1)
     gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                    const __grid_constant__ CUtensorMap tmC, const __grid_constant__ CUtensorMap tmOpA,
                    const __grid_constant__ CUtensorMap tmRes, GemmOp g, TcLaunch L) {
-  pdl_entry();
+  pdl_trigger();
   using C = TcCfg<BN, AMN, BMN>;
   extern __shared__ uint8_t dsmem[];
   __shared__ __align__(8) uint64_t full_bar[MAX_STAGES];
@@ -345,6 +345,8 @@ __global__ void __launch_bounds__(576, 1)
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = tmem_slot;
+  // global memory only from here on: wait for the kernels before this one
+  pdl_wait();
 
   if (warp == 0 && lane == 0) {
     // ---------------- TMA producer
@@ -823,8 +825,10 @@ cudaError_t launch_tc(const GemmOp &g, cudaStream_t s) {
     // m % md and n / 32, then the other, then m / md.
     const uint64_t md = e.map.mdiv >= (1ll << 31) ? (uint64_t)g.M : (uint64_t)e.map.mdiv;
     const uint64_t s_nhi = (uint64_t)e.map.s_n1, s_mlo = (uint64_t)e.map.s_m0;
-    const uint64_t s_mhi = e.map.mdiv >= (1ll << 31) ? s_mlo * md : (uint64_t)e.map.s_m1;
     const uint64_t nhi = (uint64_t)g.N / 32, mhi = (uint64_t)g.M / md;
+    // a single m / md group never steps its stride: give it one past the others
+    const uint64_t s_mhi = mhi == 1 ? std::max(s_mlo * md, s_nhi * nhi)
+                                    : (e.map.mdiv >= (1ll << 31) ? s_mlo * md : (uint64_t)e.map.s_m1);
     if (s_mlo >= 32 && s_mlo <= s_nhi && s_nhi >= s_mlo * md && s_mhi >= s_nhi * nhi) {
       if (make_tmap4(&tc, e.C, 32, md, nhi, mhi, s_mlo, s_nhi, s_mhi, 32, 32, 1, 1, CU_TENSOR_MAP_SWIZZLE_64B))
         L.tma_store = 2;
