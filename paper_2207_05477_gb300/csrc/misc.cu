@@ -2,6 +2,8 @@
 // triangle-multiplication gating (with the [c][i][k] relayout the per-channel
 // product needs), gate backwards, outer-product-mean normaliser, column sums
 // and partial reductions, dtype conversions.
+#include <algorithm>
+
 #include "kernels.h"
 
 namespace evo {
@@ -82,6 +84,38 @@ __global__ void __launch_bounds__(256) colsum_k(const T *x, int64_t ld, int64_t 
 #pragma unroll
     for (int k = 0; k < 8; ++k) tot += s[k][threadIdx.x];
     if (nn < N) atomicAdd(out + nn, tot);
+  }
+}
+
+// bf16 column sums with 16-byte loads: a thread owns 8 adjacent columns of
+// every (256 / (N / 8))-th row of the block's row range; the rows meet in
+// shared memory and the block adds its N sums with atomics.  N % 8 == 0,
+// N <= 2048, 16-byte aligned rows.
+__global__ void __launch_bounds__(256) colsum_v8_k(const bf16 *x, int64_t ld, int64_t M, int N, int64_t rows_per_blk,
+                                                   float *out) {
+  pdl_entry();
+  extern __shared__ float part[];  // [256 / tpr][N]
+  const int tpr = N / 8;           // threads per row
+  const int rpi = blockDim.x / tpr;  // rows per iteration
+  const int t = threadIdx.x;
+  const int r_in = t / tpr, c8 = (t % tpr) * 8;
+  float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  const int64_t r0 = (int64_t)blockIdx.x * rows_per_blk, r1 = min(M, r0 + rows_per_blk);
+  if (r_in < rpi) {
+    for (int64_t r = r0 + r_in; r < r1; r += rpi) {
+      float v[8];
+      ld8(x + r * ld + c8, v);
+#pragma unroll
+      for (int k = 0; k < 8; ++k) acc[k] += v[k];
+    }
+#pragma unroll
+    for (int k = 0; k < 8; ++k) part[r_in * N + c8 + k] = acc[k];
+  }
+  __syncthreads();
+  for (int c = t; c < N; c += blockDim.x) {
+    float sum = 0.f;
+    for (int i = 0; i < rpi; ++i) sum += part[i * N + c];
+    atomicAdd(out + c, sum);
   }
 }
 
@@ -750,6 +784,14 @@ int colsum_blocks(int64_t M) {
 }
 cudaError_t colsum(const void *x, int64_t ld, int64_t M, int N, int use_bf16, cudaStream_t s, float *out) {
   Prof prof("colsum", s, 0, (use_bf16 ? 2.0 : 4.0) * M * (double)N, 1);
+  if (M <= 0) return cudaSuccess;
+  if (use_bf16 && N % 8 == 0 && N <= 2048 && ld % 8 == 0 && (((uintptr_t)x) & 15u) == 0) {
+    // about four blocks per SM, each over a contiguous row range
+    const int64_t nbv = std::min<int64_t>(608, (M + 63) / 64);
+    const int64_t rpb = (M + nbv - 1) / nbv;
+    const size_t sm = (size_t)(256 / (N / 8)) * N * sizeof(float);
+    return launch_k(colsum_v8_k, (unsigned)nbv, 256, sm, s, (const bf16 *)x, ld, M, N, rpb, out);
+  }
   const int nb = colsum_blocks(M);
   const int64_t rpb = (M + nb - 1) / nb;
   const dim3 grid((N + 63) / 64, nb);
