@@ -233,6 +233,8 @@ struct TileCoord {
   int m0, n0, b, split, kt0, nk;
 };
 
+constexpr int EK_PLAIN = 0, EK_OPS = 1, EK_GENERAL = 2;
+
 __device__ __forceinline__ TileCoord decode_tile(const GemmOp &g, int t, int bn) {
   const int ntn = (g.N + bn - 1) / bn, ntm = (g.M + BM - 1) / BM;
   TileCoord c;
@@ -295,7 +297,12 @@ __device__ __forceinline__ float bf_at(const uint4 (&o)[4], int k) {
 // warp 1 lane 0: MMA issuer (accumulator buffer alternates per tile)
 // warps 2-17: epilogue (warp w drains TMEM lane quarter w % 4 and takes the
 //             32-column slot (w - 2) / 4 of every 128 columns)
-template <int BN, bool AMN, bool BMN>
+// EK selects the epilogue compiled in: EK_PLAIN (TMA store; bias, scales and
+// activation only), EK_OPS (TMA store with row operands: residual, gate,
+// ReLU reference, aux copy) or EK_GENERAL (per-element stores: split-K
+// partials and atomics, fp32 outputs, maps TMA cannot describe).  A smaller
+// epilogue is a smaller, faster-issuing loop.
+template <int BN, bool AMN, bool BMN, int EK>
 __global__ void __launch_bounds__(576, 1)
     gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                    const __grid_constant__ CUtensorMap tmC, const __grid_constant__ CUtensorMap tmOpA,
@@ -432,12 +439,12 @@ __global__ void __launch_bounds__(576, 1)
     float *mine = reinterpret_cast<float *>(dsmem + (region - raw));
     const Epi &e = g.e;
     uint32_t ai = 0;
-    if (L.tma_store) {
+    if constexpr (EK != EK_GENERAL) {
       // Chunk k of this warp (k counts the warp's chunks over all its tiles)
       // uses slot k & 1.  Its operand tiles are requested by TMA at the end
       // of chunk k - 1 (the first one before the loop), after the store that
       // last read that slot (chunk k - 2) has finished reading.
-      const uint32_t op_bytes = (L.has_opa ? 2048u : 0u) + (L.has_res ? 2048u : 0u);
+      const uint32_t op_bytes = EK == EK_OPS ? (L.has_opa ? 2048u : 0u) + (L.has_res ? 2048u : 0u) : 0u;
       int nt = blockIdx.x, nc = slot * 32;  // the next chunk whose operands are requested
       // the chunks of a tile are columns slot*32 + 128 i below BN and N, rows
       // of the warp's quarter below M; advance() moves (nt, nc) to the next
@@ -526,11 +533,11 @@ __global__ void __launch_bounds__(576, 1)
 #pragma unroll
             for (int jj = 0; jj < 32; ++jj) v[jj] *= rs;
           }
-          if (L.has_opa || L.has_res) {
+          if (EK == EK_OPS && (L.has_opa || L.has_res)) {
             if (!mbar_wait(&op_bar[ew][sl], (k >> 1) & 1u, &s_abort)) ok = false;
             if (!__all_sync(0xffffffffu, ok)) break;
           }
-          if (e.relu_ref) {
+          if (EK == EK_OPS && e.relu_ref) {
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
               uint4 w;
@@ -556,7 +563,7 @@ __global__ void __launch_bounds__(576, 1)
               v[jj] = nb + jj >= e.act_n0 ? sg : v[jj];
             }
           }
-          if (e.aux && mok) {
+          if (EK == EK_OPS && e.aux && mok) {
             bf16 *p = (bf16 *)e.aux + (int64_t)m * e.aux_ld + nb;
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
@@ -575,7 +582,7 @@ __global__ void __launch_bounds__(576, 1)
               }
             }
           }
-          if (!L.has_res) {
+          if (EK != EK_OPS || !L.has_res) {
             // the output slot was last read by the store of chunk k - 2
             if (lane == 0) bulk_wait_read<1>();
             __syncwarp();
@@ -583,7 +590,7 @@ __global__ void __launch_bounds__(576, 1)
 #pragma unroll
           for (int j = 0; j < 4; ++j) {
             const uint32_t off = rowoff + ((j ^ swz) << 4);
-            if (e.gate) {
+            if (EK == EK_OPS && e.gate) {
               uint4 w;
               asm volatile("ld.shared.v4.b32 {%0, %1, %2, %3}, [%4];"
                            : "=r"(w.x), "=r"(w.y), "=r"(w.z), "=r"(w.w)
@@ -592,7 +599,7 @@ __global__ void __launch_bounds__(576, 1)
 #pragma unroll
               for (int jj = 0; jj < 8; ++jj) v[j * 8 + jj] *= __bfloat162float(h[jj]);
             }
-            if (L.has_res) {
+            if (EK == EK_OPS && L.has_res) {
               uint4 w;
               asm volatile("ld.shared.v4.b32 {%0, %1, %2, %3}, [%4];"
                            : "=r"(w.x), "=r"(w.y), "=r"(w.z), "=r"(w.w)
@@ -624,7 +631,7 @@ __global__ void __launch_bounds__(576, 1)
             }
             bulk_commit();
           }
-          if (op_bytes) {
+          if (EK == EK_OPS && op_bytes) {
             // operands of the next chunk into the other slot, once the store
             // of chunk k - 1 (the slot's last reader) has read it
             advance();
@@ -644,7 +651,7 @@ __global__ void __launch_bounds__(576, 1)
         }
         if (s_abort) break;
       }
-      if (lane == 0) {
+      if (EK == EK_OPS && lane == 0) {
         // drain (after an abort): operand tiles requested but not consumed
         for (uint32_t kk = k; kk < requested; ++kk) {
           const uint64_t t0 = globaltimer_ns();
@@ -653,6 +660,7 @@ __global__ void __launch_bounds__(576, 1)
         }
       }
     } else {
+      (void)tmC, (void)tmOpA, (void)tmRes;
       for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
         const TileCoord tc = decode_tile(g, t, BN);
         const uint32_t ab = ai & 1u, u = ai >> 1;
@@ -784,6 +792,22 @@ bool make_tmap4(CUtensorMap *tm, const void *base, uint64_t d0, uint64_t d1, uin
   return r == CUDA_SUCCESS;
 }
 
+template <int BN, bool AMN, bool BMN, int EK>
+cudaError_t run_tc(int grid, int smem, cudaStream_t s, const CUtensorMap &ta, const CUtensorMap &tb,
+                   const CUtensorMap &tc, const CUtensorMap &topa, const CUtensorMap &tres, const GemmOp &g,
+                   const TcLaunch &L) {
+  static bool attr_set = false;
+  if (!attr_set) {
+    // the opt-in limit covers static shared memory (the barriers) as well
+    cudaError_t err = cudaFuncSetAttribute(gemm_tc_kernel<BN, AMN, BMN, EK>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_LIMIT - 2048);
+    if (err != cudaSuccess) return err;
+    attr_set = true;
+  }
+  return launch_k(gemm_tc_kernel<BN, AMN, BMN, EK>, grid, 32 * (2 + EPI_WARPS), smem, s, ta, tb, tc, topa, tres, g,
+                  L);
+}
+
 template <int BN, bool AMN, bool BMN>
 cudaError_t launch_tc(const GemmOp &g, cudaStream_t s) {
   using C = TcCfg<BN, AMN, BMN>;
@@ -859,14 +883,7 @@ cudaError_t launch_tc(const GemmOp &g, cudaStream_t s) {
   // more than half of the SM's shared memory: one resident CTA per SM, so a
   // CTA's TMEM allocation never waits on another CTA's
   if (smem <= SMEM_LIMIT / 2 + 1024 || smem > SMEM_LIMIT - 2048) return cudaErrorInvalidValue;
-  static bool attr_set = false;
-  if (!attr_set) {
-    // the opt-in limit covers static shared memory (the barriers) as well
-    cudaError_t err = cudaFuncSetAttribute(gemm_tc_kernel<BN, AMN, BMN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           SMEM_LIMIT - 2048);
-    if (err != cudaSuccess) return err;
-    attr_set = true;
-  }
+
   const long long tiles =
       (long long)((g.N + BN - 1) / BN) * ((g.M + BM - 1) / BM) * (long long)g.batch * g.splits;
   const int grid = (int)std::min<long long>(tiles, sm_count());
@@ -879,8 +896,10 @@ cudaError_t launch_tc(const GemmOp &g, cudaStream_t s) {
                       : "gemm_tc",
          s, 2.0 * g.M * g.N * (double)g.K * g.batch,
          g.batch * (2.0 * ((double)g.M * g.K + (double)g.N * g.K) + cbytes * g.M * g.N));
-  launch_k(gemm_tc_kernel<BN, AMN, BMN>, grid, 32 * (2 + EPI_WARPS), smem, s, ta, tb, tc, topa, tres, g, L);
-  return cudaGetLastError();
+  const int ek = !L.tma_store ? EK_GENERAL : (L.has_opa || L.has_res || e.aux) ? EK_OPS : EK_PLAIN;
+  if (ek == EK_PLAIN) return run_tc<BN, AMN, BMN, EK_PLAIN>(grid, smem, s, ta, tb, tc, topa, tres, g, L);
+  if (ek == EK_OPS) return run_tc<BN, AMN, BMN, EK_OPS>(grid, smem, s, ta, tb, tc, topa, tres, g, L);
+  return run_tc<BN, AMN, BMN, EK_GENERAL>(grid, smem, s, ta, tb, tc, topa, tres, g, L);
 }
 
 template <int BN>
