@@ -316,8 +316,8 @@ struct Drv {
     ck(colsum(dY, ldY, rows, (int)N, bf, s, D(b)));
   }
   void lnb(const void *dy, const void *x, const std::string &pre, float *dacc, void *dcopy, void *dx_out, int64_t M,
-           int C) {
-    ck(ln_bwd(dy, x, P(pre + ".gamma"), dacc, dcopy, dx_out, M, C, bf, s, D(pre + ".gamma"), D(pre + ".beta")));
+           int C, const void *dinit = nullptr) {
+    ck(ln_bwd(dy, x, P(pre + ".gamma"), dacc, dcopy, dx_out, M, C, bf, s, D(pre + ".gamma"), D(pre + ".beta"), dinit));
   }
 
   // ---------------- attention argument sets
@@ -489,8 +489,11 @@ struct Drv {
 
   // ================================================================ backward
   // dacc/dT: FP32 running gradient of the residual stream and its storage-type copy.
-  void transition_bwd(const std::string &pre, const void *x, const void *xn, const void *h, float *dacc, void *dT,
-                      int64_t M, int64_t C) {
+  // dT: the incoming gradient (activation type); dcopy receives the updated
+  // running gradient (dT itself unless the incoming one must stay intact);
+  // dinit: start the fp32 accumulator from this tensor instead of its contents.
+  void transition_bwd(const std::string &pre, const void *x, const void *xn, const void *h, float *dacc,
+                      const void *dT, void *dcopy, int64_t M, int64_t C, const void *dinit = nullptr) {
     const int64_t nC = k.n * C;
     dW(dT, C, C, h, nC, nC, M, pre + ".w2");
     db(dT, C, M, C, pre + ".b2");
@@ -501,7 +504,7 @@ struct Drv {
     db(B(pl.G1), nC, M, nC, pre + ".b1");
     GemmOp o = mk(M, C, nC, B(pl.G1), nC, 0, W(pre + ".w1"), C, 1, B(pl.G2), C);
     gemm(o);
-    lnb(B(pl.G2), x, pre + ".ln", dacc, dT, nullptr, M, (int)C);
+    lnb(B(pl.G2), x, pre + ".ln", dacc, dcopy, nullptr, M, (int)C, dinit);
   }
 
   // Gated attention backward down to d(LN input) in G2 (not yet through LayerNorm).
@@ -565,15 +568,15 @@ struct Drv {
   void backward(const void *m0, const void *z0, const float *mm, const float *pm, const void *dm_out,
                 const void *dz_out, void *dm_in, void *dz_in) {
     const int64_t S = k.S, R = k.R, Cm = k.Cm, Cz = k.Cz, Mm = k.Mm, Mz = k.Mz, co = k.co;
+    // running gradients of the two residual streams: fp32 accumulators dm, dz
+    // and their activation-type copies dmT, dzT.  The first LayerNorm backward
+    // of each stream starts its accumulator from the incoming cotangent, and
+    // the last one writes the outgoing gradient, so no conversion pass exists.
     float *dm = Bf(pl.dm_acc), *dz = Bf(pl.dz_acc);
     void *dmT = B(pl.dmT), *dzT = B(pl.dzT);
-    ck(to_f32(dm_out, dm, Mm * Cm, bf, s));
-    ck(to_f32(dz_out, dz, Mz * Cz, bf, s));
-    ck(cudaMemcpyAsync(dmT, dm_out, (size_t)Mm * Cm * ts, cudaMemcpyDeviceToDevice, s));
-    ck(cudaMemcpyAsync(dzT, dz_out, (size_t)Mz * Cz * ts, cudaMemcpyDeviceToDevice, s));
 
     // 9. pair transition
-    transition_bwd("pair_trans", B(pl.att[1].zout), B(pl.xz9), B(pl.h9), dz, dzT, Mz, Cz);
+    transition_bwd("pair_trans", B(pl.att[1].zout), B(pl.xz9), B(pl.h9), dz, dz_out, dzT, Mz, Cz, dz_out);
     // 8, 7. triangle attention ending / starting node
     for (int t = 1; t >= 0; --t) {
       const AttBufs &b = pl.att[t];
@@ -608,10 +611,10 @@ struct Drv {
       db(B(pl.dab4), 2 * co, Mm, 2 * co, "opm.b_ab");
       GemmOp x = mk(Mm, Cm, 2 * co, B(pl.dab4), 2 * co, 0, W("opm.w_ab"), Cm, 1, B(pl.G2), Cm);
       gemm(x);
-      lnb(B(pl.G2), B(pl.m3), "opm.ln", dm, dmT, nullptr, Mm, (int)Cm);
+      lnb(B(pl.G2), B(pl.m3), "opm.ln", dm, dmT, nullptr, Mm, (int)Cm, dm_out);
     }
     // 3. MSA transition
-    transition_bwd("msa_trans", B(pl.m2), B(pl.xm3), B(pl.h3), dm, dmT, Mm, Cm);
+    transition_bwd("msa_trans", B(pl.m2), B(pl.xm3), B(pl.h3), dm, dmT, dmT, Mm, Cm);
     // 2. MSA column attention (or global column attention)
     if (d.msa_col_mode == EVO_COL_GLOBAL) {
       const int64_t HC = k.HCm, QK = k.QKc;
@@ -631,12 +634,9 @@ struct Drv {
     // 1. MSA row attention with pair bias
     attention_bwd(0, "row", B(pl.xm1), B(pl.qkvg1), B(pl.oatt1), B(pl.og1), Bf(pl.lse1), Bf(pl.bias1), mm, dmT, Mm,
                   Cm);
-    lnb(B(pl.G2), m0, "row.ln_m", dm, nullptr, nullptr, Mm, (int)Cm);
+    lnb(B(pl.G2), m0, "row.ln_m", dm, dm_in, nullptr, Mm, (int)Cm);
     pair_bias_bwd("row.w_b", B(pl.xz1), (int)k.Hm, 0, 0);
-    lnb(B(pl.G2), z0, "row.ln_z", dz, nullptr, nullptr, Mz, (int)Cz);
-
-    ck(from_f32(dm, dm_in, Mm * Cm, bf, s));
-    ck(from_f32(dz, dz_in, Mz * Cz, bf, s));
+    lnb(B(pl.G2), z0, "row.ln_z", dz, dz_in, nullptr, Mz, (int)Cz);
   }
 };
 

@@ -101,11 +101,13 @@ cudaError_t ln_fwd(const void *x, const float *gamma, const float *beta, void *y
 cudaError_t ln_fwd_cm(const void *x, int64_t pitch, const float *gamma, const float *beta, void *y,
                       int R, int C, int use_bf16, cudaStream_t s);
 // dx = LN backward of dy (rows x[M,C]); dacc (fp32) += dx if dacc else dx_out = dx;
-// dcopy (activation type, may be null) = updated dacc.  Each block adds its sums
-// of the gamma/beta gradients to dgamma, dbeta with fp32 atomics.
+// dcopy (activation type, may be null) = updated dacc; with dinit (activation
+// type) the accumulator starts from dinit instead of its old contents (dacc =
+// dinit + dx).  Each block adds its sums of the gamma/beta gradients to
+// dgamma, dbeta with fp32 atomics.
 cudaError_t ln_bwd(const void *dy, const void *x, const float *gamma, float *dacc, void *dcopy,
                    void *dx_out, int64_t M, int C, int use_bf16, cudaStream_t s, float *dgamma,
-                   float *dbeta);
+                   float *dbeta, const void *dinit = nullptr);
 // LayerNorm backward for the channel-major input of ln_fwd_cm: dy row-major [R*R, C],
 // dx channel-major [C][R][pitch]; dgamma, dbeta accumulated with fp32 atomics.
 cudaError_t ln_bwd_cm(const void *dy, const void *x, int64_t pitch, const float *gamma, void *dx,

@@ -51,7 +51,7 @@ __global__ void __launch_bounds__(256) ln_fwd_rows(const T *x, const float *gamm
 // dx = rstd * (gdy - mean(gdy) - xhat * mean(gdy * xhat)), gdy = gamma * dy.
 template <typename T>
 __global__ void __launch_bounds__(256) ln_bwd_rows(const T *dy, const T *x, const float *gamma, float *dacc, T *dcopy,
-                                                   T *dx_out, int64_t M, int C, int64_t rows_per_blk,
+                                                   T *dx_out, const T *dinit, int64_t M, int C, int64_t rows_per_blk,
                                                    float *dgamma, float *dbeta) {
   pdl_entry();
   extern __shared__ float sh[];  // [8][2C]
@@ -89,7 +89,7 @@ __global__ void __launch_bounds__(256) ln_bwd_rows(const T *dy, const T *x, cons
       const float gd = ldf(dyr + cc) * gamma[cc];
       const float dx = rstd * (gd - a1 - xh * a2);
       if (dacc) {
-        const float nv = dacc[row * C + cc] + dx;
+        const float nv = (dinit ? ldf(dinit + row * C + cc) : dacc[row * C + cc]) + dx;
         dacc[row * C + cc] = nv;
         if (dcopy) stf(dcopy + row * C + cc, nv);
       } else {
@@ -128,7 +128,7 @@ template <> struct Pair<float> {
 // that the latency of one row overlaps the others.
 template <typename T, int P, int NR>
 __global__ void __launch_bounds__(256) ln_bwd_rows_vec(const T *dy, const T *x, const float *gamma, float *dacc,
-                                                       T *dcopy, T *dx_out, int64_t M,
+                                                       T *dcopy, T *dx_out, const T *dinit, int64_t M,
                                                        int64_t rows_per_blk, float *dgamma, float *dbeta) {
   pdl_entry();
   constexpr int C = 64 * P;
@@ -155,7 +155,9 @@ __global__ void __launch_bounds__(256) ln_bwd_rows_vec(const T *dy, const T *x, 
         if (row < r1) {
           xv[i][j] = Pair<T>::ld(x + row * C + c);
           gv[i][j] = Pair<T>::ld(dy + row * C + c);
-          av[i][j] = dacc ? *reinterpret_cast<const float2 *>(dacc + row * C + c) : make_float2(0.f, 0.f);
+          av[i][j] = dinit  ? Pair<T>::ld(dinit + row * C + c)
+                     : dacc ? *reinterpret_cast<const float2 *>(dacc + row * C + c)
+                            : make_float2(0.f, 0.f);
         } else {
           xv[i][j] = gv[i][j] = av[i][j] = make_float2(0.f, 0.f);
         }
@@ -390,7 +392,7 @@ cudaError_t ln_fwd_cm(const void *x, int64_t pitch, const float *gamma, const fl
 }
 
 cudaError_t ln_bwd(const void *dy, const void *x, const float *gamma, float *dacc, void *dcopy, void *dx_out,
-                   int64_t M, int C, int use_bf16, cudaStream_t s, float *dgamma, float *dbeta) {
+                   int64_t M, int C, int use_bf16, cudaStream_t s, float *dgamma, float *dbeta, const void *dinit) {
   if (M <= 0) return cudaSuccess;
   Prof p("ln_bwd", s, 0, (use_bf16 ? 2.0 : 4.0) * M * C * (dcopy ? 3 : 2) + (dacc ? 8.0 * M * C : 0.0));
   const int nb = ln_bwd_blocks(M);
@@ -399,10 +401,10 @@ cudaError_t ln_bwd(const void *dy, const void *x, const float *gamma, float *dac
   if (C == 64 * P) {                                                                                             \
     if (use_bf16)                                                                                                \
       launch_k(ln_bwd_rows_vec<bf16, P, NR>, nb, 256, 0, s, (const bf16 *)dy, (const bf16 *)x, gamma, dacc,           \
-                                                      (bf16 *)dcopy, (bf16 *)dx_out, M, rpb, dgamma, dbeta);     \
+                                                      (bf16 *)dcopy, (bf16 *)dx_out, (const bf16 *)dinit, M, rpb, dgamma, dbeta);     \
     else                                                                                                         \
       launch_k(ln_bwd_rows_vec<float, P, NR>, nb, 256, 0, s, (const float *)dy, (const float *)x, gamma, dacc,        \
-                                                       (float *)dcopy, (float *)dx_out, M, rpb, dgamma, dbeta);  \
+                                                       (float *)dcopy, (float *)dx_out, (const float *)dinit, M, rpb, dgamma, dbeta);  \
     return cudaGetLastError();                                                                                   \
   }
   EVO_LN_BWD_VEC(1, 4)
@@ -412,10 +414,10 @@ cudaError_t ln_bwd(const void *dy, const void *x, const float *gamma, float *dac
   const size_t sm = (size_t)8 * 2 * C * sizeof(float);
   if (use_bf16)
     launch_k(ln_bwd_rows<bf16>, nb, 256, sm, s, (const bf16 *)dy, (const bf16 *)x, gamma, dacc, (bf16 *)dcopy,
-                                          (bf16 *)dx_out, M, C, rpb, dgamma, dbeta);
+                                          (bf16 *)dx_out, (const bf16 *)dinit, M, C, rpb, dgamma, dbeta);
   else
     launch_k(ln_bwd_rows<float>, nb, 256, sm, s, (const float *)dy, (const float *)x, gamma, dacc, (float *)dcopy,
-                                           (float *)dx_out, M, C, rpb, dgamma, dbeta);
+                                           (float *)dx_out, (const float *)dinit, M, C, rpb, dgamma, dbeta);
   return cudaGetLastError();
 }
 
