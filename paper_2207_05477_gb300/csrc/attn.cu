@@ -729,6 +729,12 @@ cudaError_t attn_bwd(const AttnArgs &a, int use_bf16, cudaStream_t s) {
     const cudaError_t e = attn_bwd_tc_launch(a, s, 10.0 * inner, io);
     if (e != cudaErrorNotSupported) return e;
   }
+  if (a.dog) {
+    // the other kernels take do_att and D from a separate gate-backward pass
+    const cudaError_t e = attn_gate_bwd(a, a.dog, a.dgpre, a.sQb, a.sQx, const_cast<void *>(a.do_att),
+                                        const_cast<float *>(a.Dsum), use_bf16, s);
+    if (e != cudaSuccess) return e;
+  }
   return attn_bwd_accumulating(a, use_bf16, s, 10.0 * inner, io);
 }
 

@@ -405,9 +405,10 @@ constexpr int BT_SMEM = BT_L_OFF + 3 * 256 * 4 + 1024;
 
 struct AttnTcBwdArgs {
   AttnArgs a;
-  QkvPos pq, pk, po;  // q / k, v / dO map dimension positions
+  QkvPos pq, pk, po;  // q (and g) / k, v / dO (and dog, o) map dimension positions
   int nq, nkh;        // query tiles of 128, key halves of 128
   int has_bias;
+  int fused_gate;     // dO slots hold dog; g and o tiles are loaded too
 };
 
 // Byte offset of element (mn, k) in a [2 kb][2 mc][64 k][64 mn] bf16 tile
@@ -422,6 +423,8 @@ __global__ void __launch_bounds__(AT_WARPS * 32, 1) attn_bwd_tc(const __grid_con
                                                                 const __grid_constant__ CUtensorMap tmV,
                                                                 const __grid_constant__ CUtensorMap tmO,
                                                                 const __grid_constant__ CUtensorMap tmB,
+                                                                const __grid_constant__ CUtensorMap tmG,
+                                                                const __grid_constant__ CUtensorMap tmOa,
                                                                 AttnTcBwdArgs A) {
   pdl_trigger();
   extern __shared__ uint8_t dsm[];
@@ -464,12 +467,16 @@ __global__ void __launch_bounds__(AT_WARPS * 32, 1) attn_bwd_tc(const __grid_con
   int nsd = 0, nmm = 0;  // commits issued on bar_sd / bar_mm (thread 0)
   if (tid == 0) {
     int c[4];
-    mbar_arrive_expect_tx(&bar_in, (uint32_t)(nq * 2 * 8192 + nkh * 2 * 8192));
+    mbar_arrive_expect_tx(&bar_in, (uint32_t)(nq * (A.fused_gate ? 4 : 2) * 8192 + nkh * 2 * 8192));
     for (int qt = 0; qt < nq; ++qt) {
       tile_coords(A.pq, qt * 128, h, b, c);
       tma_load_4d(base + BT_Q_OFF + qt * 8192, &tmQ, c[0], c[1], c[2], c[3], &bar_in);
+      if (A.fused_gate)  // the gate tile (q layout) waits in the P^T buffer
+        tma_load_4d(base + BT_P_OFF + qt * 8192, &tmG, c[0], c[1], c[2], c[3], &bar_in);
       tile_coords(A.po, qt * 128, h, b, c);
       tma_load_4d(base + BT_DO_OFF + qt * 8192, &tmO, c[0], c[1], c[2], c[3], &bar_in);
+      if (A.fused_gate)  // and the attention output tile in the dS^T buffer
+        tma_load_4d(base + BT_DS_OFF + qt * 8192, &tmOa, c[0], c[1], c[2], c[3], &bar_in);
     }
     for (int kh = 0; kh < nkh; ++kh) {
       tile_coords(A.pk, kh * 128, h, b, c);
@@ -482,13 +489,63 @@ __global__ void __launch_bounds__(AT_WARPS * 32, 1) attn_bwd_tc(const __grid_con
   for (int i = tid; i < 256; i += blockDim.x) {
     const bool xin = i < a.X;
     lse_s[i] = xin ? a.lse2[((int64_t)b * a.H + h) * a.X + i] : POS_INF_F;
-    d_s[i] = xin ? a.Dsum[((int64_t)b * a.H + h) * a.X + i] : 0.f;
+    d_s[i] = xin && !A.fused_gate ? a.Dsum[((int64_t)b * a.H + h) * a.X + i] : 0.f;
     bool valid = i < a.Y;
     if (valid && a.mask) valid = a.mask[(int64_t)b * a.sMb + (int64_t)i * a.sMy] != 0.f;
     maskadd[i] = valid ? 0.f : NEG_INF_F;
   }
   __syncthreads();
   bool ok = __all_sync(0xffffffffu, mbar_wait(&bar_in, 0, &s_abort));
+  if (A.fused_gate) {
+    // thread = query row x = tid (X <= 256): do_att = dog * g in place of dog,
+    // D = sum_c do_att * o, dgpre = dog * o * g (1 - g); rows of 64 B with the
+    // 64-byte swizzle (16-byte piece j of row r at j ^ ((r >> 1) & 3))
+    const int qt = tid >> 7, r = tid & 127, x = tid;
+    if (ok && qt < nq) {
+      const uint32_t rowb = (uint32_t)(qt * 8192 + r * 64);
+      float dsum = 0.f;
+      uint4 dgw[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const uint32_t off = rowb + (uint32_t)((j ^ ((r >> 1) & 3)) << 4);
+        uint4 wdog, wg, wo;
+        asm volatile("ld.shared.v4.b32 {%0, %1, %2, %3}, [%4];"
+                     : "=r"(wdog.x), "=r"(wdog.y), "=r"(wdog.z), "=r"(wdog.w) : "r"(base + BT_DO_OFF + off));
+        asm volatile("ld.shared.v4.b32 {%0, %1, %2, %3}, [%4];"
+                     : "=r"(wg.x), "=r"(wg.y), "=r"(wg.z), "=r"(wg.w) : "r"(base + BT_P_OFF + off));
+        asm volatile("ld.shared.v4.b32 {%0, %1, %2, %3}, [%4];"
+                     : "=r"(wo.x), "=r"(wo.y), "=r"(wo.z), "=r"(wo.w) : "r"(base + BT_DS_OFF + off));
+        const bf16 *hd = reinterpret_cast<const bf16 *>(&wdog), *hg = reinterpret_cast<const bf16 *>(&wg),
+                   *ho = reinterpret_cast<const bf16 *>(&wo);
+        uint4 wa;
+        uint32_t *pa = reinterpret_cast<uint32_t *>(&wa), *pg = reinterpret_cast<uint32_t *>(&dgw[j]);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const float d0 = __bfloat162float(hd[2 * i]), d1 = __bfloat162float(hd[2 * i + 1]);
+          const float g0 = __bfloat162float(hg[2 * i]), g1 = __bfloat162float(hg[2 * i + 1]);
+          const float o0 = __bfloat162float(ho[2 * i]), o1 = __bfloat162float(ho[2 * i + 1]);
+          const float a0 = d0 * g0, a1 = d1 * g1;
+          dsum += a0 * o0 + a1 * o1;
+          __nv_bfloat162 va = __floats2bfloat162_rn(a0, a1);
+          __nv_bfloat162 vg = __floats2bfloat162_rn(d0 * o0 * g0 * (1.f - g0), d1 * o1 * g1 * (1.f - g1));
+          pa[i] = *reinterpret_cast<uint32_t *>(&va);
+          pg[i] = *reinterpret_cast<uint32_t *>(&vg);
+        }
+        asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(base + BT_DO_OFF + off), "r"(wa.x), "r"(wa.y),
+                     "r"(wa.z), "r"(wa.w)
+                     : "memory");
+      }
+      if (x < a.X) {
+        d_s[x] = dsum;
+        bf16 *gp = (bf16 *)a.dgpre + (int64_t)b * a.sQb + (int64_t)x * a.sQx + h * AT_C;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) *reinterpret_cast<uint4 *>(gp + 8 * j) = dgw[j];
+      }
+    }
+    // do_att is read by the tensor cores (async proxy) and D by every row below
+    fence_proxy_async();
+    __syncthreads();
+  }
   const float sl2 = a.scale * EVO_LOG2E;
   const uint32_t lane_base = tmem + ((uint32_t)(quarter * 32) << 16);
   const uint32_t bring = base + BT_B_OFF + (uint32_t)warp * 2 * 4096u;
@@ -790,8 +847,9 @@ cudaError_t attn_fwd_tc_launch(const AttnArgs &a, cudaStream_t s, double flops, 
 
 bool attn_bwd_tc_supported(const AttnArgs &a) {
   auto a16 = [](const void *p) { return ((uintptr_t)p & 15u) == 0; };
-  if (!attn_tc_supported(a) || a.X > 256 || !a.dq || !a.do_att || !a.dk || !a.dv || !a.Dsum) return false;
-  if (!a16(a.dq) || !a16(a.dk) || !a16(a.dv) || !a16(a.do_att) || a.sKy % 8 || a.sKb % 8) return false;
+  if (!attn_tc_supported(a) || a.X > 256 || !a.dq || !a.dk || !a.dv) return false;
+  if (!a16(a.dq) || !a16(a.dk) || !a16(a.dv) || a.sKy % 8 || a.sKb % 8) return false;
+  if (a.dog ? (!a.dgpre || !a16(a.dog) || !a16(a.dgpre)) : (!a.do_att || !a.Dsum || !a16(a.do_att))) return false;
   if (a.bias && (!a.dbias || !a16(a.dbias) || a.Y % 4)) return false;
   return true;
 }
@@ -802,13 +860,21 @@ cudaError_t attn_bwd_tc_launch(const AttnArgs &a, cudaStream_t s, double flops, 
   A.nq = (a.X + 127) / 128;
   A.nkh = (a.Y + 127) / 128;
   A.has_bias = a.bias != nullptr;
-  CUtensorMap tq, tk, tv, to, tb;
+  CUtensorMap tq, tk, tv, to, tb, tg, toa;
   std::memset(&tb, 0, sizeof(tb));
-  QkvPos pv;
+  std::memset(&tg, 0, sizeof(tg));
+  std::memset(&toa, 0, sizeof(toa));
+  QkvPos pv, px;
+  A.fused_gate = a.dog != nullptr;
   if (!qkv_map(&tq, a.q, a.H, a.X, a.B1, a.sQx, a.sQb, 128, &A.pq)) return cudaErrorNotSupported;
   if (!qkv_map(&tk, a.k, a.H, a.Y, a.B1, a.sKy, a.sKb, 128, &A.pk)) return cudaErrorNotSupported;
   if (!qkv_map(&tv, a.v, a.H, a.Y, a.B1, a.sKy, a.sKb, 128, &pv)) return cudaErrorNotSupported;
-  if (!qkv_map(&to, a.do_att, a.H, a.X, a.B1, a.sOx, a.sOb, 128, &A.po)) return cudaErrorNotSupported;
+  if (!qkv_map(&to, A.fused_gate ? a.dog : a.do_att, a.H, a.X, a.B1, a.sOx, a.sOb, 128, &A.po))
+    return cudaErrorNotSupported;
+  if (A.fused_gate) {
+    if (!qkv_map(&tg, a.g, a.H, a.X, a.B1, a.sQx, a.sQb, 128, &px)) return cudaErrorNotSupported;
+    if (!qkv_map(&toa, a.o_att, a.H, a.X, a.B1, a.sOx, a.sOb, 128, &px)) return cudaErrorNotSupported;
+  }
   if (a.bias) {
     const uint64_t dims[3] = {(uint64_t)a.Y, (uint64_t)a.X, (uint64_t)a.H};
     const uint64_t st[2] = {(uint64_t)a.sBx * 4, (uint64_t)a.sBh * 4};
@@ -824,7 +890,7 @@ cudaError_t attn_bwd_tc_launch(const AttnArgs &a, cudaStream_t s, double flops, 
   }
   dim3 grid(a.H, a.B1);
   Prof p("attn_bwd_tc", s, flops, bytes);
-  launch_k(attn_bwd_tc, grid, AT_WARPS * 32, BT_SMEM, s, tq, tk, tv, to, tb, A);
+  launch_k(attn_bwd_tc, grid, AT_WARPS * 32, BT_SMEM, s, tq, tk, tv, to, tb, tg, toa, A);
   return cudaGetLastError();
 }
 

@@ -525,7 +525,8 @@ struct Drv {
     a.dv = at(B(pl.G1), 2 * HC);
     a.dbias = bias ? Bf(pl.dbias) : nullptr;
     a.dq = B(pl.G1);
-    ck(attn_gate_bwd(a, B(pl.G2), at(B(pl.G1), 3 * HC), a.sQb, a.sQx, B(pl.G3), Bf(pl.Dsum), bf, s));
+    a.dog = B(pl.G2);                  // gradient of the gated output
+    a.dgpre = at(B(pl.G1), 3 * HC);    // gate pre-activation gradient
     if (bias) ck(cudaMemsetAsync(Bf(pl.dbias), 0, (size_t)a.H * k.Mz * 4, s));
     ck(attn_bwd(a, bf, s));
     dW(B(pl.G1), QK, QK, xn, Cin, Cin, M, pre + ".w_qkvg");

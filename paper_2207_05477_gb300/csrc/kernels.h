@@ -61,6 +61,12 @@ struct AttnArgs {
   void *dk, *dv;         // k/v strides
   float *dbias;          // fp32 [h*sBh + x*sBx + y] accumulated
   void *dq;              // q strides: the scaled query gradient (activation type)
+  // Gate backward in the same pass (tcgen05 path): with dog (grad of the gated
+  // output, o strides) the kernel forms do_att = dog * g and D itself and
+  // writes the gate pre-activation gradient dgpre = dog * o * g (1 - g) (q
+  // strides); do_att and Dsum are then not read.
+  const void *dog;
+  void *dgpre;
 };
 cudaError_t attn_fwd(const AttnArgs &a, int use_bf16, cudaStream_t s);
 // tcgen05 forward (bf16, head dim 32, at most 256 keys, 16-byte aligned rows);
