@@ -58,29 +58,35 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
 }
 
 // Coalesced copy of the pair-bias tile bias[h][x0 + r][y0 + q] (r, q < 64) into
-// shared memory, pre-scaled by log2(e); zero outside [X, Y).
+// shared memory, pre-scaled by log2(e); zero outside [X, Y).  The bias is bf16
+// or fp32 (a.bias_bf16).
 __device__ __forceinline__ void load_bias_tile(float (*dst)[68], const AttnArgs &a, int h, int x0, int y0) {
-  const float *src = a.bias + (int64_t)h * a.sBh;
-  const bool vec = ((a.sBx & 3) == 0) && ((a.sBh & 3) == 0) && (((uintptr_t)a.bias & 15u) == 0);
   for (int idx = threadIdx.x; idx < 64 * 16; idx += blockDim.x) {
     const int r = idx >> 4, q4 = (idx & 15) * 4;
     const int x = x0 + r, y = y0 + q4;
-    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    float v[4] = {0.f, 0.f, 0.f, 0.f};
     if (x < a.X) {
-      const float *p = src + (int64_t)x * a.sBx + y;
-      if (vec && y + 3 < a.Y) {
-        v = *reinterpret_cast<const float4 *>(p);
+      const int64_t o = (int64_t)h * a.sBh + (int64_t)x * a.sBx + y;
+      if (a.bias_bf16) {
+        const bf16 *p = (const bf16 *)a.bias + o;
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+          if (y + k < a.Y) v[k] = __bfloat162float(p[k]);
       } else {
-        if (y < a.Y) v.x = p[0];
-        if (y + 1 < a.Y) v.y = p[1];
-        if (y + 2 < a.Y) v.z = p[2];
-        if (y + 3 < a.Y) v.w = p[3];
+        const float *p = (const float *)a.bias + o;
+        const bool vec = ((a.sBx & 3) == 0) && ((a.sBh & 3) == 0) && (((uintptr_t)a.bias & 15u) == 0);
+        if (vec && y + 3 < a.Y) {
+          const float4 f = *reinterpret_cast<const float4 *>(p);
+          v[0] = f.x, v[1] = f.y, v[2] = f.z, v[3] = f.w;
+        } else {
+#pragma unroll
+          for (int k = 0; k < 4; ++k)
+            if (y + k < a.Y) v[k] = p[k];
+        }
       }
     }
-    dst[r][q4] = v.x * EVO_LOG2E;
-    dst[r][q4 + 1] = v.y * EVO_LOG2E;
-    dst[r][q4 + 2] = v.z * EVO_LOG2E;
-    dst[r][q4 + 3] = v.w * EVO_LOG2E;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) dst[r][q4 + k] = v[k] * EVO_LOG2E;
   }
 }
 
@@ -501,7 +507,7 @@ __global__ void __launch_bounds__(128) attn_fwd_simt(AttnArgs a) {
 #pragma unroll
       for (int d = 0; d < CM; ++d) sdot = fmaf(q[d], Ks[r][d], sdot);
       float s = sdot * sl2;
-      if (a.bias) s += a.bias[(int64_t)h * a.sBh + (int64_t)x * a.sBx + y0 + r] * EVO_LOG2E;
+      if (a.bias) s += ((const float *)a.bias)[(int64_t)h * a.sBh + (int64_t)x * a.sBx + y0 + r] * EVO_LOG2E;
       const float mnew = fmaxf(mrow, s);
       const float alpha = exp2f(mrow - mnew);
       const float p = exp2f(s - mnew);
@@ -574,7 +580,7 @@ __global__ void __launch_bounds__(128) attn_bwd_dq_simt(AttnArgs a) {
         dpv = fmaf(dO[d], Vs[r][d], dpv);
       }
       float s = sdot * sl2;
-      if (a.bias) s += a.bias[(int64_t)h * a.sBh + (int64_t)x * a.sBx + y0 + r] * EVO_LOG2E;
+      if (a.bias) s += ((const float *)a.bias)[(int64_t)h * a.sBh + (int64_t)x * a.sBx + y0 + r] * EVO_LOG2E;
       const float p = exp2f(s - lse);
       const float ds = p * (dpv - Dx);
 #pragma unroll
@@ -635,7 +641,7 @@ __global__ void __launch_bounds__(128) attn_bwd_dkv_simt(AttnArgs a) {
         dpv = fmaf(dOs[r][d], v[d], dpv);
       }
       float s = sdot * sl2;
-      if (a.bias) s += a.bias[(int64_t)h * a.sBh + (int64_t)(x0 + r) * a.sBx + y] * EVO_LOG2E;
+      if (a.bias) s += ((const float *)a.bias)[(int64_t)h * a.sBh + (int64_t)(x0 + r) * a.sBx + y] * EVO_LOG2E;
       const float p = exp2f(s - Ls[r]);
       const float ds = p * (dpv - Ds[r]);
 #pragma unroll

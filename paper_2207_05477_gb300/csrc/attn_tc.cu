@@ -75,7 +75,7 @@ constexpr int AT_WARPS = 8;    // two per TMEM lane quarter, splitting the key c
 constexpr int AT_Q_OFF = 0;                               // 128 x 64 B
 constexpr int AT_K_OFF = AT_Q_OFF + AT_QROWS * 64;        // 256 x 64 B
 constexpr int AT_V_OFF = AT_K_OFF + AT_MAXKEYS * 64;      // 256 x 64 B
-// pair bias: per warp a ring of AT_BRING [32 rows x 32 keys] fp32 chunks (4 KB each)
+// pair bias (bf16): per warp AT_BRING boxes of [32 rows x 64 keys] (4 KB each)
 constexpr int AT_BRING = 2;
 constexpr int AT_B_OFF = AT_V_OFF + AT_MAXKEYS * 64;
 constexpr int AT_R_OFF = AT_B_OFF + AT_WARPS * AT_BRING * 4096;  // [2][128] row max, [2][128] row sum
@@ -161,15 +161,15 @@ __global__ void __launch_bounds__(AT_WARPS * 32) attn_fwd_tc(const __grid_consta
   // warp streams the pair bias of its rows and chunks; thread 0 issues the rest
   int bias_issued = 0, bias_done = 0;
   bool s_issued = false, o_issued = false;
+  // the warp's pair bias (bf16): one [32 rows x 64 keys] box per pair of its
+  // key chunks, all requested at once
   const uint32_t bring = base + AT_B_OFF + (uint32_t)warp * AT_BRING * 4096u;
-  auto bias_chunk = [&](int j) {  // lane 0: chunk j (keys 32j..) of this warp's rows, slot (j - c_lo) % ring
-    const int k = (j - c_lo) % AT_BRING;
-    mbar_arrive_expect_tx(&bar_b[warp][k], 4096);
-    tma_load_3d(bring + k * 4096u, &tmB, j * 32, x0 + quarter * 32, h, &bar_b[warp][k]);
-    ++bias_issued;
-  };
   if (A.has_bias && lane == 0)
-    for (int j = c_lo; j < c_hi && j < c_lo + AT_BRING; ++j) bias_chunk(j);
+    for (int bx = 0; bx < AT_BRING && c_lo + 2 * bx < c_hi; ++bx) {
+      mbar_arrive_expect_tx(&bar_b[warp][bx], 4096);
+      tma_load_3d(bring + bx * 4096u, &tmB, (c_lo + 2 * bx) * 32, x0 + quarter * 32, h, &bar_b[warp][bx]);
+      ++bias_issued;
+    }
 
   if (tid == 0) {
     int c[4];
@@ -215,11 +215,9 @@ __global__ void __launch_bounds__(AT_WARPS * 32) attn_fwd_tc(const __grid_consta
   // pass 1 over this warp's chunks: logits (log2 domain) in place, partial row max
   float mx = NEG_INF_F;
   for (int j = c_lo; j < c_hi; ++j) {
-    const int sl = (j - c_lo) % AT_BRING;
-    if (A.has_bias)
-      ok = __all_sync(0xffffffffu,
-                      ok && mbar_wait(&bar_b[warp][sl], (uint32_t)(((j - c_lo) / AT_BRING) & 1), &s_abort));
-    if (ok) bias_done = j - c_lo + 1;
+    const int bx = (j - c_lo) >> 1, hh = (j - c_lo) & 1;  // box and its half holding chunk j
+    if (A.has_bias) ok = __all_sync(0xffffffffu, ok && mbar_wait(&bar_b[warp][bx], 0, &s_abort));
+    if (ok) bias_done = bx + 1;
     if (ok) {
       uint32_t r[32];
       tmem_ld32(lane_base + (uint32_t)(j * 32), r);
@@ -234,18 +232,18 @@ __global__ void __launch_bounds__(AT_WARPS * 32) attn_fwd_tc(const __grid_consta
         v[4 * q + 3] = __uint_as_float(r[4 * q + 3]) * sl2 + mv.w;
       }
       if (A.has_bias) {
-        // this lane's row of the warp's 128-byte-swizzled chunk: 16-byte piece k at k ^ (lane & 7)
-        const uint32_t rb = bring + sl * 4096u + lane * 128u;
+        // this lane's 128-byte row of the box (64 keys, 128-byte swizzle: 16-byte
+        // piece k at k ^ (lane & 7)); chunk j is pieces 4 hh .. 4 hh + 3
+        const uint32_t rb = bring + bx * 4096u + lane * 128u;
 #pragma unroll
-        for (int k = 0; k < 8; ++k) {
-          float4 bv;
-          asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
-                       : "=f"(bv.x), "=f"(bv.y), "=f"(bv.z), "=f"(bv.w)
-                       : "r"(rb + (uint32_t)((k ^ (lane & 7)) << 4)));
-          v[4 * k] = fmaf(bv.x, EVO_LOG2E, v[4 * k]);
-          v[4 * k + 1] = fmaf(bv.y, EVO_LOG2E, v[4 * k + 1]);
-          v[4 * k + 2] = fmaf(bv.z, EVO_LOG2E, v[4 * k + 2]);
-          v[4 * k + 3] = fmaf(bv.w, EVO_LOG2E, v[4 * k + 3]);
+        for (int k = 0; k < 4; ++k) {
+          uint4 w;
+          asm volatile("ld.shared.v4.b32 {%0, %1, %2, %3}, [%4];"
+                       : "=r"(w.x), "=r"(w.y), "=r"(w.z), "=r"(w.w)
+                       : "r"(rb + (uint32_t)(((4 * hh + k) ^ (lane & 7)) << 4)));
+          const bf16 *hv = reinterpret_cast<const bf16 *>(&w);
+#pragma unroll
+          for (int q = 0; q < 8; ++q) v[8 * k + q] = fmaf(__bfloat162float(hv[q]), EVO_LOG2E, v[8 * k + q]);
         }
       }
 #pragma unroll
@@ -254,11 +252,6 @@ __global__ void __launch_bounds__(AT_WARPS * 32) attn_fwd_tc(const __grid_consta
         r[jj] = __float_as_uint(v[jj]);
       }
       tmem_st32(lane_base + (uint32_t)(j * 32), r);
-    }
-    if (A.has_bias) {
-      // the slot is refilled once the warp has read it
-      __syncwarp();
-      if (lane == 0 && ok && j + AT_BRING < c_hi) bias_chunk(j + AT_BRING);
     }
   }
   red[half * AT_QROWS + row] = mx;
@@ -364,8 +357,7 @@ __global__ void __launch_bounds__(AT_WARPS * 32) attn_fwd_tc(const __grid_consta
       if (o_issued) mbar_drain(&bar_o, 0);
     }
     if (lane == 0)
-      for (int j = bias_done; j < bias_issued; ++j)
-        mbar_drain(&bar_b[warp][j % AT_BRING], (uint32_t)((j / AT_BRING) & 1));
+      for (int bx = bias_done; bx < bias_issued; ++bx) mbar_drain(&bar_b[warp][bx], 0);
   }
   tc_fence_before();
   __syncthreads();
@@ -556,12 +548,10 @@ __global__ void __launch_bounds__(AT_WARPS * 32, 1) attn_bwd_tc(const __grid_con
       const int it = kh * nq + qt;  // sub-tile counter (barrier phases)
       // this warp's pair-bias chunks: rows qt*128 + 32 quarter.., keys kh*128 + 64 half + 32 t
       if (a.bias && lane == 0 && ok) {
-        for (int t = 0; t < 2; ++t) {
-          mbar_arrive_expect_tx(&bar_b[warp][t], 4096);
-          tma_load_3d(bring + t * 4096u, &tmB, kh * 128 + half * 64 + t * 32, qt * 128 + quarter * 32, h,
-                      &bar_b[warp][t]);
-          ++bias_issued;
-        }
+        // one bf16 box: the warp's 32 query rows x its 64 keys
+        mbar_arrive_expect_tx(&bar_b[warp][0], 4096);
+        tma_load_3d(bring, &tmB, kh * 128 + half * 64, qt * 128 + quarter * 32, h, &bar_b[warp][0]);
+        ++bias_issued;
       }
       if (tid == 0 && ok && !s_abort) {
         tc_fence_after();
@@ -591,20 +581,26 @@ __global__ void __launch_bounds__(AT_WARPS * 32, 1) attn_bwd_tc(const __grid_con
       for (int t = 0; t < 2; ++t) {
         const int cl = half * 2 + t;           // 32-key chunk within the key half
         const int y0 = kh * 128 + cl * 32;     // first key of the chunk
-        if (a.bias) ok = __all_sync(0xffffffffu, ok && mbar_wait(&bar_b[warp][t], (uint32_t)((it)&1), &s_abort));
-        if (ok && a.bias) bias_done = 2 * it + t + 1;
+        if (a.bias && t == 0) ok = __all_sync(0xffffffffu, ok && mbar_wait(&bar_b[warp][0], (uint32_t)(it & 1), &s_abort));
+        if (ok && a.bias) bias_done = it + 1;
         if (ok) {
           uint32_t sr[32], pr[32];
           tmem_ld32(lane_base + BT_S_COL + (uint32_t)(cl * 32), sr);
           tmem_ld32(lane_base + BT_DP_COL + (uint32_t)(cl * 32), pr);
           float bv[32];
           if (a.bias) {
-            const uint32_t rb = bring + t * 4096u + lane * 128u;
+            // pieces 4t .. 4t + 3 of this lane's 128-byte (64-key) row, 128-byte swizzle
+            const uint32_t rb = bring + lane * 128u;
 #pragma unroll
-            for (int k = 0; k < 8; ++k)
-              asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
-                           : "=f"(bv[4 * k]), "=f"(bv[4 * k + 1]), "=f"(bv[4 * k + 2]), "=f"(bv[4 * k + 3])
-                           : "r"(rb + (uint32_t)((k ^ (lane & 7)) << 4)));
+            for (int k = 0; k < 4; ++k) {
+              uint4 w;
+              asm volatile("ld.shared.v4.b32 {%0, %1, %2, %3}, [%4];"
+                           : "=r"(w.x), "=r"(w.y), "=r"(w.z), "=r"(w.w)
+                           : "r"(rb + (uint32_t)(((4 * t + k) ^ (lane & 7)) << 4)));
+              const bf16 *hv = reinterpret_cast<const bf16 *>(&w);
+#pragma unroll
+              for (int q = 0; q < 8; ++q) bv[8 * k + q] = __bfloat162float(hv[q]);
+            }
           } else {
 #pragma unroll
             for (int k = 0; k < 32; ++k) bv[k] = 0.f;
@@ -760,7 +756,7 @@ __global__ void __launch_bounds__(AT_WARPS * 32, 1) attn_bwd_tc(const __grid_con
       for (int i = 0; i < nmm; ++i) mbar_drain(&bar_mm, (uint32_t)(i & 1));
     }
     if (lane == 0)
-      for (int j = bias_done; j < bias_issued; ++j) mbar_drain(&bar_b[warp][j & 1], (uint32_t)((j >> 1) & 1));
+      for (int j = bias_done; j < bias_issued; ++j) mbar_drain(&bar_b[warp][0], (uint32_t)(j & 1));
   }
   tc_fence_before();
   __syncthreads();
@@ -809,7 +805,8 @@ bool attn_tc_supported(const AttnArgs &a) {
   if (a.c != AT_C || a.Y <= 0 || a.Y > AT_MAXKEYS || a.X <= 0) return false;
   if (!a16(a.q) || !a16(a.k) || !a16(a.v) || !a16(a.g) || !a16(a.o_att) || !a16(a.o_gate)) return false;
   if (a.sOx % 8 || a.sOb % 8 || a.sQx % 8 || a.sQb % 8) return false;
-  if (a.bias && (!a16(a.bias) || a.sBx % 4 || a.sBh % 4 || a.sBx < a.Y || a.sBh < a.sBx * (int64_t)a.X))
+  if (a.bias && (!a.bias_bf16 || !a16(a.bias) || a.sBx % 8 || a.sBh % 8 || a.sBx < a.Y ||
+                 a.sBh < a.sBx * (int64_t)a.X))
     return false;
   return true;
 }
@@ -828,9 +825,9 @@ cudaError_t attn_fwd_tc_launch(const AttnArgs &a, cudaStream_t s, double flops, 
   if (!qkv_map(&tv, a.v, a.H, a.Y, a.B1, a.sKy, a.sKb, A.ypad, &pv)) return cudaErrorNotSupported;
   if (a.bias) {
     const uint64_t dims[3] = {(uint64_t)a.Y, (uint64_t)a.X, (uint64_t)a.H};
-    const uint64_t st[2] = {(uint64_t)a.sBx * 4, (uint64_t)a.sBh * 4};
-    const uint32_t box[3] = {32, 32, 1};
-    if (!make_tmap_nd(&tb, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, a.bias, dims, st, box, CU_TENSOR_MAP_SWIZZLE_128B))
+    const uint64_t st[2] = {(uint64_t)a.sBx * 2, (uint64_t)a.sBh * 2};
+    const uint32_t box[3] = {64, 32, 1};
+    if (!make_tmap_nd(&tb, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, a.bias, dims, st, box, CU_TENSOR_MAP_SWIZZLE_128B))
       return cudaErrorNotSupported;
   }
   static bool attr = false;
@@ -877,9 +874,9 @@ cudaError_t attn_bwd_tc_launch(const AttnArgs &a, cudaStream_t s, double flops, 
   }
   if (a.bias) {
     const uint64_t dims[3] = {(uint64_t)a.Y, (uint64_t)a.X, (uint64_t)a.H};
-    const uint64_t st[2] = {(uint64_t)a.sBx * 4, (uint64_t)a.sBh * 4};
-    const uint32_t box[3] = {32, 32, 1};
-    if (!make_tmap_nd(&tb, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, a.bias, dims, st, box, CU_TENSOR_MAP_SWIZZLE_128B))
+    const uint64_t st[2] = {(uint64_t)a.sBx * 2, (uint64_t)a.sBh * 2};
+    const uint32_t box[3] = {64, 32, 1};
+    if (!make_tmap_nd(&tb, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, a.bias, dims, st, box, CU_TENSOR_MAP_SWIZZLE_128B))
       return cudaErrorNotSupported;
   }
   static bool attr = false;

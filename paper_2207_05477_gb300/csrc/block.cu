@@ -333,6 +333,7 @@ struct Drv {
     a.o_att = oatt, a.o_gate = og, a.lse2 = lse;
     a.scale = 1.f / std::sqrt((float)c);
     a.bias = bias;
+    a.bias_bf16 = bf;  // the pair bias is an activation: bf16 on the BF16 path
     a.sBh = k.Mz, a.sBx = R;
     a.mask = mask;
     switch (kind) {

@@ -38,7 +38,7 @@ cudaError_t debug_wait(int64_t limit_ns, cudaStream_t s);
 // Batch b in [0,B1), head h, query x in [0,X), key y in [0,Y), head dim c.
 //   q(b,x,h,:) = q[b*sQb + x*sQx + h*c + :]   g shares q's strides
 //   k(b,y,h,:) = k[b*sKb + y*sKy + h*c + :]   v shares k's strides
-//   bias(h,x,y) = bias[h*sBh + x*sBx + y]     (fp32, may be null)
+//   bias(h,x,y) = bias[h*sBh + x*sBx + y]     (bf16 when bias_bf16, else fp32; may be null)
 //   key valid   = mask[b*sMb + y*sMy] != 0    (fp32, may be null)
 //   o(b,x,h,:) at o_att/o_gate[b*sOb + x*sOx + h*c + :]
 //   lse2[(b*H + h)*X + x] = log2 of the softmax normaliser (+inf: no valid key)
@@ -46,8 +46,9 @@ struct AttnArgs {
   const void *q, *k, *v, *g;
   int64_t sQb, sQx, sKb, sKy;
   int B1, H, X, Y, c;
-  const float *bias;
+  const void *bias;
   int64_t sBh, sBx;
+  int bias_bf16;
   const float *mask;
   int64_t sMb, sMy;
   void *o_att, *o_gate;
@@ -133,8 +134,9 @@ cudaError_t reduce_splits_map(const float *part, int splits, int M, int N, const
                               cudaStream_t s);
 
 // Pair-bias projection: out[h][pos'] = x[pos] . w[h], pos = (p0,p1) in [R,R];
-// pos' = p0*R+p1, or p1*R+p0 with transpose.
-cudaError_t head_proj_fwd(const void *x, const float *w, float *out, int R, int C, int H, int transpose,
+// pos' = p0*R+p1, or p1*R+p0 with transpose.  out is bf16 when use_bf16 (the
+// attention kernels read the bias as an activation), else fp32.
+cudaError_t head_proj_fwd(const void *x, const float *w, void *out, int R, int C, int H, int transpose,
                           int use_bf16, cudaStream_t s);
 // dx[pos] (+)= sum_h dbias[h][pos'] w[h]; dw += sum_pos dbias x (each block adds
 // its sum over a range of positions with fp32 atomics).

@@ -151,8 +151,8 @@ __global__ void reduce_splits_map_k(const float *part, int splits, int M, int N,
 }
 
 // ------------------------------------------------------------- pair bias
-template <typename T>
-__global__ void head_proj_fwd_k(const T *x, const float *w, float *out, int R, int C, int H, int transpose) {
+template <typename T, typename OT>
+__global__ void head_proj_fwd_k(const T *x, const float *w, OT *out, int R, int C, int H, int transpose) {
   pdl_entry();
   const int lane = threadIdx.x & 31;
   const int64_t p = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
@@ -175,7 +175,7 @@ __global__ void head_proj_fwd_k(const T *x, const float *w, float *out, int R, i
   for (int h = 0; h < 8; ++h) {
     if (h >= H) break;
     const float v = warp_sum(acc[h]);
-    if (lane == 0) out[h * P + pp] = v;
+    if (lane == 0) stf(out + h * P + pp, v);
   }
 }
 
@@ -224,8 +224,8 @@ __global__ void __launch_bounds__(256) head_proj_bwd_k(const float *dbias, const
 
 // Pair-bias projection, BF16 fast path: one thread per position, the
 // position's C channels read as 16-byte vectors, w staged in shared memory.
-template <int H>
-__global__ void __launch_bounds__(128) head_proj_fwd_v8(const bf16 *x, const float *w, float *out, int R, int C,
+template <int H, typename OT>
+__global__ void __launch_bounds__(128) head_proj_fwd_v8(const bf16 *x, const float *w, OT *out, int R, int C,
                                                         int transpose) {
   pdl_entry();
   extern __shared__ float ws[];  // [H][C]
@@ -251,7 +251,7 @@ __global__ void __launch_bounds__(128) head_proj_fwd_v8(const bf16 *x, const flo
   divmod(p, R, i, j);
   const int64_t pp = transpose ? (int64_t)j * R + i : p;
 #pragma unroll
-  for (int h = 0; h < H; ++h) out[h * P + pp] = acc[h];
+  for (int h = 0; h < H; ++h) stf(out + h * P + pp, acc[h]);
 }
 
 // Backward, BF16 fast path: warp per position, lane owns channel pairs
@@ -815,17 +815,21 @@ cudaError_t reduce_splits_map(const float *part, int splits, int M, int N, const
   return cudaGetLastError();
 }
 
-cudaError_t head_proj_fwd(const void *x, const float *w, float *out, int R, int C, int H, int transpose, int use_bf16,
+cudaError_t head_proj_fwd(const void *x, const float *w, void *out, int R, int C, int H, int transpose, int use_bf16,
                           cudaStream_t s) {
   Prof prof("head_proj_fwd", s, 2.0 * R * (double)R * C * H, (use_bf16 ? 2.0 : 4.0) * R * (double)R * C + 4.0 * H * R * (double)R, 1);
   if (H > 8) return cudaErrorInvalidValue;
   const int64_t P = (int64_t)R * R;
   if (use_bf16 && C % 8 == 0 && (((uintptr_t)x) & 15u) == 0 && (H == 4 || H == 8)) {
     const size_t sm = (size_t)H * C * sizeof(float);
-    if (H == 4) launch_k(head_proj_fwd_v8<4>, nblk(P, 128), 128, sm, s, (const bf16 *)x, w, out, R, C, transpose);
-    else launch_k(head_proj_fwd_v8<8>, nblk(P, 128), 128, sm, s, (const bf16 *)x, w, out, R, C, transpose);
-  } else if (use_bf16) launch_k(head_proj_fwd_k<bf16>, nblk(P, 8), 256, 0, s, (const bf16 *)x, w, out, R, C, H, transpose);
-  else launch_k(head_proj_fwd_k<float>, nblk(P, 8), 256, 0, s, (const float *)x, w, out, R, C, H, transpose);
+    if (H == 4) launch_k(head_proj_fwd_v8<4, bf16>, nblk(P, 128), 128, sm, s, (const bf16 *)x, w, (bf16 *)out, R, C, transpose);
+    else launch_k(head_proj_fwd_v8<8, bf16>, nblk(P, 128), 128, sm, s, (const bf16 *)x, w, (bf16 *)out, R, C, transpose);
+  } else if (use_bf16) {
+    launch_k(head_proj_fwd_k<bf16, bf16>, nblk(P, 8), 256, 0, s, (const bf16 *)x, w, (bf16 *)out, R, C, H, transpose);
+  } else {
+    launch_k(head_proj_fwd_k<float, float>, nblk(P, 8), 256, 0, s, (const float *)x, w, (float *)out, R, C, H,
+             transpose);
+  }
   return cudaGetLastError();
 }
 
