@@ -174,6 +174,24 @@ def reference_arm(args):
 
 # ---------------------------------------------------------------- our arm
 PROFILE_EVERY = 10
+TUNE_PASSES = 12  # at least the largest candidate count of a GEMM shape
+
+
+def autotune(evo, run_once, passes):
+    """GEMM tile autotuning before the warm-up: `passes` untimed runs of the
+    workload cycle every GEMM shape through its candidate tile widths (and
+    split counts); the library keeps the fastest per shape."""
+    import torch
+    torch.cuda.synchronize()
+    evo.tune_begin()
+    for _ in range(passes):
+        run_once()
+    n = evo.tune_end()
+    ents = evo.tune_entries()
+    changed = [f"{e['M']}x{e['N']}x{e['K']}*{e['batch']}: n{e['default_bn']}s{e['default_splits']}"
+               f"->n{e['bn']}s{e['splits']}" for e in ents
+               if (e["bn"], e["splits"]) != (e["default_bn"], e["default_splits"])]
+    return {"shapes": n, "changed": len(changed), "choices": changed}
 
 
 def ours_arm(args):
@@ -217,6 +235,8 @@ def ours_arm(args):
         evo.block_fwd(cd, prm, p16, mi, zi, m_out, z_out, mmi, pmi, ws_f)
         evo.block_bwd(cd, prm, p16, mi, zi, mmi, pmi, gmi, gzi, dm, dz, dparams, ws_b)
 
+    tuned = autotune(evo, lambda: step(m, z, mm, pm, gm, gz, params), TUNE_PASSES) \
+        if act == evo.EVO_BF16 and not args.no_tune else None
     for _ in range(args.warmup):
         step(m, z, mm, pm, gm, gz, params)
     torch.cuda.synchronize()
@@ -408,7 +428,8 @@ def ours_arm(args):
                                    f"c_m=256 c_z=128, 5% padded residues",
                        "n_seq": d.n_seq, "n_res": d.n_res, "flops_per_step": step_flops(d),
                        "l2": "flushed between timed steps (258 MB write outside the step events)",
-                       "parallelism": f"replicas x{world}", "cuda_graph": bool(args.graph)},
+                       "parallelism": f"replicas x{world}", "cuda_graph": bool(args.graph),
+                       "gemm_tiles": ("autotuned before the warm-up: " + json.dumps(tuned)) if tuned else "built-in"},
             "clocks": clk, "gpu_launches": launches,
             "e2e": {"value": e2e_value, "unit": "TFLOP/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "ms_per_step": float(te.item())},
@@ -500,6 +521,8 @@ def other_workload(args):
                 evo.block_bwd(cd, B["params"], B["p16"], B["m"], B["z"], B["mm"], B["pm"], B["gm"], B["gz"], dm, dz,
                               dp, wsb)
 
+        if act == evo.EVO_BF16 and not args.no_tune:
+            extra["gemm_tiles"] = autotune(evo, fn, TUNE_PASSES)
         ms, clk = timed(fn, args.steps, max(3, args.warmup))
         flops = step_flops(d) if bwd else block_fwd_flops(d)
         desc = f"N_seq={d.n_seq} N_res={d.n_res} c_m={d.c_m} {'fwd+bwd' if bwd else 'fwd'} " \
@@ -532,6 +555,8 @@ def other_workload(args):
                               dp[b * stride:(b + 1) * stride], wsb)
                 g_m, g_z, o_m, o_z = o_m, o_z, (dm2 if o_m is dm else dm), (dz2 if o_z is dz else dz)
 
+        if not args.no_tune:  # one pass launches each GEMM shape at least 48 times
+            extra["gemm_tiles"] = autotune(evo, fn, 1)
         ms, clk = timed(fn, args.steps, 1)
         flops = nb * step_flops(d)
         desc = f"48-block stack fwd+bwd, N_seq=512 N_res=384, BF16, per-block recompute"
@@ -547,18 +572,58 @@ def other_workload(args):
             B = buffers(d, evo.EVO_BF16, 100 + i, n_params=1)
             jobs.append((d, B))
             flops += nb * block_fwd_flops(d)
-        maxws = max(evo.workspace_size(B["cd"], evo.EVO_MODE_FWD) for _, B in jobs)
-        wsf = torch.empty(maxws, dtype=torch.uint8, device=dev)
+        # proteins run concurrently on NSTREAMS CUDA streams (largest first onto
+        # the least-loaded stream), each stream with its own workspace, so the
+        # small proteins fill the SMs the large ones leave idle
+        NSTREAMS = max(1, args.streams)
+        order = sorted(range(len(jobs)), key=lambda i: -block_fwd_flops(jobs[i][0]))
+        load = [0.0] * NSTREAMS
+        lanes = [[] for _ in range(NSTREAMS)]
+        for i in order:
+            k = min(range(NSTREAMS), key=lambda q: load[q])
+            lanes[k].append(i)
+            load[k] += block_fwd_flops(jobs[i][0])
+        streams = [torch.cuda.Stream() for _ in range(NSTREAMS)]
+        wss = [torch.empty(max([evo.workspace_size(jobs[i][1]["cd"], evo.EVO_MODE_FWD) for i in lane] or [1]),
+                           dtype=torch.uint8, device=dev) for lane in lanes]
+        work = {i: (jobs[i][1]["m"].clone(), jobs[i][1]["z"].clone()) for i in range(len(jobs))}
 
         def fn():
+            start = torch.cuda.Event()
+            start.record(stream)
+            for k, lane in enumerate(lanes):
+                st = streams[k]
+                st.wait_event(start)
+                with torch.cuda.stream(st):
+                    for i in lane:
+                        d, B = jobs[i]
+                        m, z = work[i]
+                        m.copy_(B["m"])
+                        z.copy_(B["z"])
+                        for _ in range(nb):
+                            evo.block_fwd(B["cd"], B["params"], B["p16"], m, z, m, z, B["mm"], B["pm"], wss[k],
+                                          stream=st)
+            for st in streams:
+                done = torch.cuda.Event()
+                done.record(st)
+                stream.wait_event(done)
+
+        def tune_once():  # each protein's shapes, one protein at a time on one stream
+            wst = torch.empty(max(evo.workspace_size(B["cd"], evo.EVO_MODE_FWD) for _, B in jobs),
+                              dtype=torch.uint8, device=dev)
             for d, B in jobs:
                 m, z = B["m"].clone(), B["z"].clone()
-                for _ in range(nb):
-                    evo.block_fwd(B["cd"], B["params"], B["p16"], m, z, m, z, B["mm"], B["pm"], wsf)
+                for _ in range(TUNE_PASSES):
+                    evo.block_fwd(B["cd"], B["params"], B["p16"], m, z, m, z, B["mm"], B["pm"], wst)
 
+        if not args.no_tune:
+            tuned = autotune(evo, tune_once, 1)
+            extra["gemm_tiles"] = {"shapes": tuned["shapes"], "changed": tuned["changed"]}
         ms, clk = timed(fn, args.steps, 1)
-        desc = "16 proteins (seeded N_res~U[64,1024], N_seq~U[32,512]), 48-block forward each, BF16, in sequence"
+        desc = (f"16 proteins (seeded N_res~U[64,1024], N_seq~U[32,512]), 48-block forward each, BF16, "
+                f"{NSTREAMS} concurrent CUDA streams")
         extra["proteins"] = prot
+        extra["streams"] = NSTREAMS
     line = {"workload": w, "metric": desc, "value": flops / (ms / 1e3) / 1e12, "unit": "TFLOP/s", "ms_per_step": ms,
             "steps": args.steps, "flops_per_step": flops, "frac_of_bf16_peak": flops / (ms / 1e3) / 1e12 / peaks["bf16_sus"],
             "peak_mem_gb": torch.cuda.max_memory_allocated() / 1e9, "clocks": clk, "data": "synthetic"}
@@ -578,6 +643,8 @@ def main():
     ap.add_argument("--n-res", type=int, default=256)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp32", action="store_true")
+    ap.add_argument("--no-tune", action="store_true", help="keep the built-in GEMM tile choice")
+    ap.add_argument("--streams", type=int, default=4, help="concurrent CUDA streams of the 16-protein batch")
     ap.add_argument("--graph", action="store_true", help="replay the step as one captured CUDA graph")
     ap.add_argument("--workload", default="train_crop",
                     choices=["train_crop", "small_fp32_fwd", "extra_msa", "stack48", "long2048", "batch16"])

@@ -189,6 +189,42 @@ int evo_profile_pause(int paused);
 int evo_profile_begin(void);
 int evo_profile_end(evo_stream_t stream, evo_profile_entry *out, int cap);
 
+/* GEMM tile autotuning.  Between evo_tune_begin and evo_tune_end, every
+ * tensor-core GEMM launch of the library is keyed by its shape (M, N, K,
+ * batch, operand majors) and epilogue, and the k-th launch of a key runs the
+ * k-th of that key's candidate launch configurations (cyclically) under a
+ * CUDA event pair: the output tile width BN in {64, 128, 256} and, for the
+ * weight-gradient products that add into fp32 with atomics, the number of K
+ * ranges (the default, twice it, half of it, one).  Every candidate computes
+ * the same product, so the work issued meanwhile stays correct; launches
+ * captured into a CUDA graph are not timed.  evo_tune_end waits for the
+ * stream and the device, then keeps per key the candidate with the lowest mean
+ * time (the default unless every candidate ran at least once) and returns the
+ * number of keys; later launches of a tuned key use its choice.  Run each
+ * workload n times between begin and end, n at least the largest candidate
+ * count (12).  evo_tune_clear drops the table (back to the built-in choice);
+ * evo_tune_entries copies up to cap entries out and returns how many there
+ * are.  This scheduling aid has no counterpart in the paper. */
+typedef struct evo_tune_entry {
+  int64_t M, N, K, batch;
+  int32_t default_bn, default_splits; /* the built-in choice                 */
+  int32_t bn, splits;                 /* the chosen launch configuration     */
+  int32_t candidates;                 /* configurations timed for this key   */
+} evo_tune_entry;
+int evo_tune_begin(void);
+int evo_tune_end(evo_stream_t stream);
+int evo_tune_clear(void);
+int evo_tune_entries(evo_tune_entry *out, int cap);
+/* The tuned table as a text file (one line per shape: its key, the built-in
+ * and the chosen configuration), and back: evo_tune_load replaces the table
+ * (EVO_ERR_INVALID_ARG, table unchanged, for a missing or malformed file or
+ * during a tuning session).  A loaded choice is used only where the tuner
+ * could have offered it for that launch.  With EVO_TUNE_CACHE=<path> in the
+ * environment the file is loaded before the first GEMM launch and written by
+ * every evo_tune_end. */
+int evo_tune_save(const char *path);
+int evo_tune_load(const char *path);
+
 /* Static description of an EVO_* code. */
 const char *evo_strerror(int code);
 

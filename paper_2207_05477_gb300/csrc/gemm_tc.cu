@@ -935,12 +935,19 @@ bool gemm_tc_supported(const GemmOp &g) {
   return true;
 }
 
-cudaError_t gemm_tc_bf16(const GemmOp &g, cudaStream_t s) {
-  if (!gemm_tc_supported(g)) return cudaErrorInvalidValue;
-  // one persistent CTA per SM
-  if (g.N > 128 && g.N % 256 == 0) return dispatch_major<256>(g, s);
-  if (g.N > 64) return dispatch_major<128>(g, s);
-  return dispatch_major<64>(g, s);
+cudaError_t gemm_tc_bf16(const GemmOp &g0, cudaStream_t s) {
+  if (!gemm_tc_supported(g0)) return cudaErrorInvalidValue;
+  // one persistent CTA per SM; the tile width (and, for atomic split-K, the
+  // split count) is the autotuner's once it has timed this shape
+  const int bn0 = g0.N > 128 && g0.N % 256 == 0 ? 256 : g0.N > 64 ? 128 : 64;
+  const TuneChoice c = tune_choose(g0, bn0, s);
+  GemmOp g = g0;
+  g.splits = c.splits;
+  const cudaError_t err = c.bn == 256   ? dispatch_major<256>(g, s)
+                          : c.bn == 128 ? dispatch_major<128>(g, s)
+                                        : dispatch_major<64>(g, s);
+  tune_done(c, s);
+  return err;
 }
 
 }  // namespace evo

@@ -29,6 +29,15 @@ cudaError_t gemm_simt_f32(const GemmOp &g, cudaStream_t s);
 cudaError_t gemm_tc_bf16(const GemmOp &g, cudaStream_t s);
 // Query whether gemm_tc_bf16 accepts the operand strides/alignment.
 bool gemm_tc_supported(const GemmOp &g);
+// Tile width and split count for one GEMM launch (the autotuner's choice, or
+// the defaults passed in); with a and b set the launch is bracketed by that
+// event pair (tune_done records b).
+struct TuneChoice {
+  int bn, splits;
+  cudaEvent_t a, b;
+};
+TuneChoice tune_choose(const GemmOp &g, int default_bn, cudaStream_t s);
+void tune_done(const TuneChoice &c, cudaStream_t s);
 // Reads and clears the device error word (EVO_OK or EVO_ERR_TIMEOUT); synchronous.
 cudaError_t error_word_read_clear(int *out);
 // Launches one CTA whose bounded mbarrier wait is made to run out after limit_ns.

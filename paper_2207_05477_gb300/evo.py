@@ -45,6 +45,12 @@ class CParamEntry(ctypes.Structure):
                 ("shape", ctypes.c_int64 * 4)]
 
 
+class CTuneEntry(ctypes.Structure):
+    _fields_ = [("M", ctypes.c_int64), ("N", ctypes.c_int64), ("K", ctypes.c_int64), ("batch", ctypes.c_int64),
+                ("default_bn", ctypes.c_int32), ("default_splits", ctypes.c_int32), ("bn", ctypes.c_int32),
+                ("splits", ctypes.c_int32), ("candidates", ctypes.c_int32)]
+
+
 _lib = None
 _vp, _sz = ctypes.c_void_p, ctypes.c_size_t
 
@@ -74,6 +80,12 @@ def lib():
         L.evo_profile_pause.argtypes = [ctypes.c_int]
         L.evo_profile_begin.argtypes = []
         L.evo_profile_end.argtypes = [_vp, P(CProfileEntry), ctypes.c_int]
+        L.evo_tune_begin.argtypes = []
+        L.evo_tune_end.argtypes = [_vp]
+        L.evo_tune_clear.argtypes = []
+        L.evo_tune_entries.argtypes = [P(CTuneEntry), ctypes.c_int]
+        L.evo_tune_save.argtypes = [ctypes.c_char_p]
+        L.evo_tune_load.argtypes = [ctypes.c_char_p]
         L.evo_strerror.argtypes = [ctypes.c_int]
         L.evo_strerror.restype = ctypes.c_char_p
         L.evo_version.restype = ctypes.c_char_p
@@ -196,6 +208,41 @@ def profile_end(stream=None, cap=256):
         raise EvoError(n, "evo_profile_end")
     return {arr[i].name.decode(): dict(calls=arr[i].calls, launches=arr[i].launches, ms=arr[i].total_ms,
                                        flops=arr[i].flops, bytes=arr[i].bytes) for i in range(min(n, cap))}
+
+
+def tune_begin():
+    """Start a GEMM tile-tuning session (candidates cycle over the launches of each shape)."""
+    _check(lib().evo_tune_begin(), "evo_tune_begin")
+
+
+def tune_end(stream=None):
+    """Close the session: keep the fastest candidate per GEMM shape; returns the number of shapes."""
+    n = lib().evo_tune_end(_stream(stream))
+    if n < 0:
+        raise EvoError(n, "evo_tune_end")
+    return n
+
+
+def tune_clear():
+    """Drop the tuned table (back to the built-in tile choice)."""
+    _check(lib().evo_tune_clear(), "evo_tune_clear")
+
+
+def tune_save(path):
+    """Write the tuned table to a text file."""
+    _check(lib().evo_tune_save(str(path).encode()), "evo_tune_save")
+
+
+def tune_load(path):
+    """Replace the tuned table with a file written by tune_save."""
+    _check(lib().evo_tune_load(str(path).encode()), "evo_tune_load")
+
+
+def tune_entries(cap=512):
+    """[dict(M, N, K, batch, default_bn, default_splits, bn, splits, candidates)] of the tuned table."""
+    arr = (CTuneEntry * cap)()
+    n = lib().evo_tune_entries(arr, cap)
+    return [{f: getattr(arr[i], f) for f, _ in CTuneEntry._fields_} for i in range(min(n, cap))]
 
 
 # ------------------------------------------------------------- torch glue
