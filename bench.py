@@ -644,7 +644,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp32", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="keep the built-in GEMM tile choice")
-    ap.add_argument("--streams", type=int, default=4, help="concurrent CUDA streams of the 16-protein batch")
+    ap.add_argument("--streams", type=int, default=8, help="concurrent CUDA streams of the 16-protein batch")
     ap.add_argument("--graph", action="store_true", help="replay the step as one captured CUDA graph")
     ap.add_argument("--workload", default="train_crop",
                     choices=["train_crop", "small_fp32_fwd", "extra_msa", "stack48", "long2048", "batch16"])
