@@ -191,18 +191,19 @@ int evo_profile_end(evo_stream_t stream, evo_profile_entry *out, int cap);
 
 /* GEMM tile autotuning.  Between evo_tune_begin and evo_tune_end, every
  * tensor-core GEMM launch of the library is keyed by its shape (M, N, K,
- * batch, operand majors) and epilogue, and the k-th launch of a key runs the
- * k-th of that key's candidate launch configurations (cyclically) under a
- * CUDA event pair: the output tile width BN in {64, 128, 256} and, for the
- * weight-gradient products that add into fp32 with atomics, the number of K
- * ranges (the default, twice it, half of it, one).  Every candidate computes
- * the same product, so the work issued meanwhile stays correct; launches
- * captured into a CUDA graph are not timed.  evo_tune_end waits for the
- * stream and the device, then keeps per key the candidate with the lowest mean
- * time (the default unless every candidate ran at least once) and returns the
- * number of keys; later launches of a tuned key use its choice.  Run each
- * workload n times between begin and end, n at least the largest candidate
- * count (12).  evo_tune_clear drops the table (back to the built-in choice);
+ * batch, operand majors) and epilogue, and each run of n consecutive launches
+ * of a key tries each of its n candidate launch configurations once, in an
+ * order shuffled from run to run, every launch under a CUDA event pair: the
+ * output tile width BN in {64, 128, 256} and, for the weight-gradient
+ * products that add into fp32 with atomics, the number of K ranges (the
+ * default, twice it, half of it, one).  Every candidate computes the same
+ * product, so the work issued meanwhile stays correct; launches captured
+ * into a CUDA graph are not timed.  evo_tune_end waits for the stream and the
+ * device, then keeps per key the candidate with the lowest median time (the
+ * default unless every candidate ran at least once) and returns the number
+ * of keys; later launches of a tuned key use its choice.  Run each workload
+ * n times between begin and end, n at least the largest candidate count
+ * (12).  evo_tune_clear drops the table (back to the built-in choice);
  * evo_tune_entries copies up to cap entries out and returns how many there
  * are.  This scheduling aid has no counterpart in the paper. */
 typedef struct evo_tune_entry {

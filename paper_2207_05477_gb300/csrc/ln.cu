@@ -2,6 +2,8 @@
 // eps 1e-5), FP32 statistics, warp-shuffle reductions: one warp per row.
 // The channel-major variants serve the triangle-multiplication output, whose
 // per-channel batched product is laid out [c][i][j].
+#include <algorithm>
+
 #include "kernels.h"
 
 namespace evo {
@@ -255,6 +257,273 @@ __global__ void __launch_bounds__(256) ln_fwd_rows_vec(const T *x, const float *
   }
 }
 
+// Eight consecutive channels per thread: one 16-byte access for bf16, two for
+// fp32 (rows of C channels start 16-byte aligned).
+__device__ __forceinline__ void ld8(const bf16 *p, float (&v)[8]) {
+  const uint4 w = *reinterpret_cast<const uint4 *>(p);
+  const __nv_bfloat162 *h = reinterpret_cast<const __nv_bfloat162 *>(&w);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const float2 f = __bfloat1622float2(h[k]);
+    v[2 * k] = f.x, v[2 * k + 1] = f.y;
+  }
+}
+__device__ __forceinline__ void ld8(const float *p, float (&v)[8]) {
+  const float4 a = reinterpret_cast<const float4 *>(p)[0], b = reinterpret_cast<const float4 *>(p)[1];
+  v[0] = a.x, v[1] = a.y, v[2] = a.z, v[3] = a.w, v[4] = b.x, v[5] = b.y, v[6] = b.z, v[7] = b.w;
+}
+__device__ __forceinline__ void st8(bf16 *p, const float (&v)[8]) {
+  uint4 w;
+  uint32_t *u = reinterpret_cast<uint32_t *>(&w);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const __nv_bfloat162 h = __floats2bfloat162_rn(v[2 * k], v[2 * k + 1]);
+    u[k] = *reinterpret_cast<const uint32_t *>(&h);
+  }
+  *reinterpret_cast<uint4 *>(p) = w;
+}
+__device__ __forceinline__ void st8(float *p, const float (&v)[8]) {
+  reinterpret_cast<float4 *>(p)[0] = make_float4(v[0], v[1], v[2], v[3]);
+  reinterpret_cast<float4 *>(p)[1] = make_float4(v[4], v[5], v[6], v[7]);
+}
+
+// Row LayerNorm, C in {64, 128, 256}: a row is spread over TPR = C / 8 lanes
+// (eight channels each), so a warp covers 32 / TPR rows per step; each warp
+// keeps U steps of loads in flight before reducing, enough bytes per SM to
+// cover the HBM latency.  Grid-stride over warp-steps.
+template <typename T, int C, int U>
+__global__ void __launch_bounds__(256) ln_fwd_rows_v8(const T *x, const float *gamma, const float *beta, T *y,
+                                                      int64_t M) {
+  pdl_entry();
+  constexpr int TPR = C / 8, RPW = 32 / TPR;
+  const int lane = threadIdx.x & 31;
+  const int sub = lane % TPR, rw = lane / TPR;
+  const int c0 = sub * 8;
+  float g[8], b[8];
+  ld8(gamma + c0, g);
+  ld8(beta + c0, b);
+  const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  const int64_t w0 = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  for (int64_t base = w0 * (RPW * U); base < M; base += nwarps * (RPW * U)) {
+    float v[U][8];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t row = base + u * RPW + rw;
+      if (row < M) {
+        ld8(x + row * C + c0, v[u]);
+      } else {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) v[u][k] = 0.f;
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      float s = 0.f;
+#pragma unroll
+      for (int k = 0; k < 8; ++k) s += v[u][k];
+#pragma unroll
+      for (int o = TPR / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      const float mu = s * (1.f / C);
+      float q = 0.f;
+#pragma unroll
+      for (int k = 0; k < 8; ++k) q += (v[u][k] - mu) * (v[u][k] - mu);
+#pragma unroll
+      for (int o = TPR / 2; o > 0; o >>= 1) q += __shfl_xor_sync(0xffffffffu, q, o);
+      const float rstd = rsqrtf(q * (1.f / C) + LN_EPS);
+      const int64_t row = base + u * RPW + rw;
+      float o8[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) o8[k] = (v[u][k] - mu) * rstd * g[k] + b[k];
+      if (row < M) st8(y + row * C + c0, o8);
+    }
+  }
+}
+
+// Channel-major LayerNorm of the triangle-multiplication output x[c][i][pitch]
+// (pitch a multiple of 8): one block per 32 positions j of a row i.  The
+// C x 32 tile comes in with 16-byte loads (8 positions per thread) into a
+// padded fp32 tile; the per-position statistics are summed by all eight warps
+// over channel slices; the normalised rows are staged [j][C] so that the
+// row-major output leaves in 16-byte stores.
+template <typename T>
+__device__ __forceinline__ void cm_load_tile(const T *x, int64_t pitch, int R, int C, int i, int j0, int nj, float *xt) {
+  const int64_t plane = (int64_t)R * pitch;
+  for (int idx = threadIdx.x; idx < C * 4; idx += blockDim.x) {
+    const int cc = idx >> 2, q = idx & 3;
+    const T *src = x + cc * plane + (int64_t)i * pitch + j0 + q * 8;
+    float v[8];
+    if (q * 8 + 8 <= nj) {
+      ld8(src, v);
+    } else {
+#pragma unroll
+      for (int k = 0; k < 8; ++k) v[k] = q * 8 + k < nj ? ldf(src + k) : 0.f;
+    }
+#pragma unroll
+    for (int k = 0; k < 8; ++k) xt[cc * 33 + q * 8 + k] = v[k];
+  }
+}
+
+// mean and rstd of the 32 positions of an fp32 [C][33] tile into stat[0..31],
+// stat[32..63] (part: [8][32] scratch); ends with the block synchronised
+__device__ __forceinline__ void cm_stats(const float *xt, int C, float *part, float *stat) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  float s = 0.f;
+  for (int cc = warp; cc < C; cc += 8) s += xt[cc * 33 + lane];
+  part[warp * 32 + lane] = s;
+  __syncthreads();
+  if (warp == 0) {
+    float t = 0.f;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) t += part[w * 32 + lane];
+    stat[lane] = t / C;
+  }
+  __syncthreads();
+  const float mu = stat[lane];
+  float q = 0.f;
+  for (int cc = warp; cc < C; cc += 8) {
+    const float d = xt[cc * 33 + lane] - mu;
+    q += d * d;
+  }
+  part[warp * 32 + lane] = q;
+  __syncthreads();
+  if (warp == 0) {
+    float t = 0.f;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) t += part[w * 32 + lane];
+    stat[32 + lane] = rsqrtf(t / C + LN_EPS);
+  }
+  __syncthreads();
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) ln_fwd_cm_v(const T *x, int64_t pitch, const float *gamma, const float *beta,
+                                                   T *y, int R, int C) {
+  pdl_entry();
+  extern __shared__ __align__(16) float smv[];
+  float *xt = smv;              // [C][33]
+  float *part = xt + C * 33;    // [8][32]
+  float *stat = part + 8 * 32;  // mean [32], rstd [32]
+  T *yt = reinterpret_cast<T *>(stat + 64);  // [32][C + 8]
+  const int CP = C + 8;
+  const int i = blockIdx.y, j0 = blockIdx.x * 32, nj = min(32, R - j0);
+  cm_load_tile(x, pitch, R, C, i, j0, nj, xt);
+  __syncthreads();
+  cm_stats(xt, C, part, stat);
+  for (int idx = threadIdx.x; idx < 32 * C; idx += blockDim.x) {
+    const int jj = idx / C, cc = idx - jj * C;
+    const float v = (xt[cc * 33 + jj] - stat[jj]) * stat[32 + jj] * gamma[cc] + beta[cc];
+    if constexpr (sizeof(T) == 2) yt[jj * CP + cc] = __float2bfloat16_rn(v);
+    else yt[jj * CP + cc] = v;
+  }
+  __syncthreads();
+  const int cq = C / 8;
+  for (int idx = threadIdx.x; idx < nj * cq; idx += blockDim.x) {
+    const int jj = idx / cq, q = idx - jj * cq;
+    const T *src = yt + jj * CP + q * 8;
+    T *dst = y + ((int64_t)i * R + j0 + jj) * C + q * 8;
+    if constexpr (sizeof(T) == 2) {
+      *reinterpret_cast<uint4 *>(dst) = *reinterpret_cast<const uint4 *>(src);
+    } else {
+      reinterpret_cast<float4 *>(dst)[0] = reinterpret_cast<const float4 *>(src)[0];
+      reinterpret_cast<float4 *>(dst)[1] = reinterpret_cast<const float4 *>(src)[1];
+    }
+  }
+}
+
+// Backward of ln_fwd_cm_v: dy row-major [R*R][C], dx channel-major like x.
+// The dy rows are staged [j][C + 2] (odd word stride: conflict-free column
+// reads); dx overwrites the x tile in place and leaves in 16-byte stores.
+template <typename T>
+__global__ void __launch_bounds__(256) ln_bwd_cm_v(const T *dy, const T *x, int64_t pitch, const float *gamma, T *dx,
+                                                   int R, int C, float *dgamma, float *dbeta) {
+  pdl_entry();
+  extern __shared__ __align__(16) float smv[];
+  float *xt = smv;              // [C][33]
+  float *part = xt + C * 33;    // [8][32]
+  float *stat = part + 8 * 32;  // mean, rstd, a1, a2 [4][32]
+  float *dyt = stat + 128;      // [32][C + 1] fp32
+  const int DP = C + 1;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int i = blockIdx.y, j0 = blockIdx.x * 32, nj = min(32, R - j0);
+  cm_load_tile(x, pitch, R, C, i, j0, nj, xt);
+  const int cq = C / 8;
+  for (int idx = threadIdx.x; idx < 32 * cq; idx += blockDim.x) {
+    const int jj = idx / cq, q = idx - jj * cq;
+    float v[8];
+    if (jj < nj) {
+      ld8(dy + ((int64_t)i * R + j0 + jj) * C + q * 8, v);
+    } else {
+#pragma unroll
+      for (int k = 0; k < 8; ++k) v[k] = 0.f;
+    }
+#pragma unroll
+    for (int k = 0; k < 8; ++k) dyt[jj * DP + q * 8 + k] = v[k];
+  }
+  __syncthreads();
+  cm_stats(xt, C, part, stat);
+  // a1 = mean_c(dy gamma), a2 = mean_c(dy gamma xhat) per position (lane = j)
+  {
+    const float mu = stat[lane], rs = stat[32 + lane];
+    float a1 = 0.f, a2 = 0.f;
+    for (int cc = warp; cc < C; cc += 8) {
+      const float gd = dyt[lane * DP + cc] * gamma[cc];
+      a1 += gd;
+      a2 += gd * (xt[cc * 33 + lane] - mu) * rs;
+    }
+    part[warp * 32 + lane] = a1;
+    __syncthreads();
+    if (warp == 0) {
+      float t = 0.f;
+#pragma unroll
+      for (int w = 0; w < 8; ++w) t += part[w * 32 + lane];
+      stat[64 + lane] = t / C;
+    }
+    __syncthreads();
+    part[warp * 32 + lane] = a2;
+    __syncthreads();
+    if (warp == 0) {
+      float t = 0.f;
+#pragma unroll
+      for (int w = 0; w < 8; ++w) t += part[w * 32 + lane];
+      stat[96 + lane] = t / C;
+    }
+    __syncthreads();
+  }
+  // gamma / beta gradients: one thread per channel over the block's positions
+  for (int cc = threadIdx.x; cc < C; cc += blockDim.x) {
+    float sg = 0.f, sb = 0.f;
+    for (int jj = 0; jj < nj; ++jj) {
+      const float g = dyt[jj * DP + cc];
+      sg += g * (xt[cc * 33 + jj] - stat[jj]) * stat[32 + jj];
+      sb += g;
+    }
+    atomicAdd(dgamma + cc, sg);
+    atomicAdd(dbeta + cc, sb);
+  }
+  __syncthreads();  // every read of xt above is done before it is overwritten
+  for (int idx = threadIdx.x; idx < 32 * C; idx += blockDim.x) {
+    const int cc = idx >> 5, jj = idx & 31;
+    const float xh = (xt[cc * 33 + jj] - stat[jj]) * stat[32 + jj];
+    xt[cc * 33 + jj] = stat[32 + jj] * (dyt[jj * DP + cc] * gamma[cc] - stat[64 + jj] - xh * stat[96 + jj]);
+  }
+  __syncthreads();
+  const int64_t plane = (int64_t)R * pitch;
+  for (int idx = threadIdx.x; idx < C * 4; idx += blockDim.x) {
+    const int cc = idx >> 2, q = idx & 3;
+    T *dst = dx + cc * plane + (int64_t)i * pitch + j0 + q * 8;
+    float v[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) v[k] = xt[cc * 33 + q * 8 + k];
+    if (q * 8 + 8 <= nj) {
+      st8(dst, v);
+    } else {
+#pragma unroll
+      for (int k = 0; k < 8; ++k)
+        if (q * 8 + k < nj) stf(dst + k, v[k]);
+    }
+  }
+}
+
 // Channel-major input: block = 32 consecutive j of one row i.
 template <typename T>
 __global__ void __launch_bounds__(256) ln_fwd_cm_k(const T *x, int64_t pitch, const float *gamma, const float *beta,
@@ -349,11 +618,28 @@ __global__ void __launch_bounds__(256) ln_bwd_cm_k(const T *dy, const T *x, int6
   }
 }
 
+template <typename T, int C>
+void launch_ln_fwd_v8(const T *x, const float *gamma, const float *beta, T *y, int64_t M, cudaStream_t s) {
+  constexpr int U = 4, RPW = 32 / (C / 8);
+  const int64_t steps = (M + RPW * U - 1) / (RPW * U);  // warp-steps
+  const int64_t blocks = std::min<int64_t>((steps + 7) / 8, (int64_t)152 * 4);  // one resident wave
+  launch_k(ln_fwd_rows_v8<T, C, U>, (unsigned)std::max<int64_t>(blocks, 1), 256, 0, s, x, gamma, beta, y, M);
+}
+
 template <typename T>
 cudaError_t ln_fwd_t(const void *x, const float *gamma, const float *beta, void *y, int64_t M, int C, cudaStream_t s) {
   const dim3 grid((unsigned)((M + 7) / 8));
   const T *xx = (const T *)x;
   T *yy = (T *)y;
+  auto a16 = [](const void *p) { return ((uintptr_t)p & 15u) == 0; };
+  if (a16(x) && a16(y) && a16(gamma) && a16(beta)) {
+    switch (C) {
+      case 64: launch_ln_fwd_v8<T, 64>(xx, gamma, beta, yy, M, s); return cudaGetLastError();
+      case 128: launch_ln_fwd_v8<T, 128>(xx, gamma, beta, yy, M, s); return cudaGetLastError();
+      case 256: launch_ln_fwd_v8<T, 256>(xx, gamma, beta, yy, M, s); return cudaGetLastError();
+      default: break;
+    }
+  }
   switch (C) {
     case 64: launch_k(ln_fwd_rows_vec<T, 1>, grid, 256, 0, s, xx, gamma, beta, yy, M); break;
     case 128: launch_k(ln_fwd_rows_vec<T, 2>, grid, 256, 0, s, xx, gamma, beta, yy, M); break;
@@ -383,6 +669,20 @@ cudaError_t ln_fwd_cm(const void *x, int64_t pitch, const float *gamma, const fl
   if (R <= 0) return cudaSuccess;
   Prof p("ln_fwd_cm", s, 0, (use_bf16 ? 4.0 : 8.0) * R * (double)R * C);
   dim3 grid((R + 31) / 32, R);
+  auto a16 = [](const void *q) { return ((uintptr_t)q & 15u) == 0; };
+  if (pitch % 8 == 0 && C % 8 == 0 && a16(x) && a16(y)) {
+    const size_t smv = (size_t)(C * 33 + 8 * 32 + 64) * 4 + (size_t)32 * (C + 8) * (use_bf16 ? 2 : 4);
+    if (smv > 48 * 1024) {
+      cudaError_t e = use_bf16 ? cudaFuncSetAttribute(ln_fwd_cm_v<bf16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smv)
+                               : cudaFuncSetAttribute(ln_fwd_cm_v<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smv);
+      if (e != cudaSuccess) return e;
+    }
+    if (use_bf16)
+      launch_k(ln_fwd_cm_v<bf16>, grid, 256, smv, s, (const bf16 *)x, pitch, gamma, beta, (bf16 *)y, R, C);
+    else
+      launch_k(ln_fwd_cm_v<float>, grid, 256, smv, s, (const float *)x, pitch, gamma, beta, (float *)y, R, C);
+    return cudaGetLastError();
+  }
   const size_t sm = (size_t)C * 33 * sizeof(float);
   if (use_bf16)
     launch_k(ln_fwd_cm_k<bf16>, grid, 256, sm, s, (const bf16 *)x, pitch, gamma, beta, (bf16 *)y, R, C);
@@ -426,6 +726,22 @@ cudaError_t ln_bwd_cm(const void *dy, const void *x, int64_t pitch, const float 
   if (R <= 0) return cudaSuccess;
   Prof p("ln_bwd_cm", s, 0, (use_bf16 ? 6.0 : 12.0) * R * (double)R * C);
   dim3 grid((R + 31) / 32, R);
+  auto a16 = [](const void *q) { return ((uintptr_t)q & 15u) == 0; };
+  if (pitch % 8 == 0 && C % 8 == 0 && a16(x) && a16(dy) && a16(dx)) {
+    const size_t smv = (size_t)(C * 33 + 8 * 32 + 128 + 32 * (C + 1)) * 4;
+    if (smv > 48 * 1024) {
+      cudaError_t e = use_bf16 ? cudaFuncSetAttribute(ln_bwd_cm_v<bf16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smv)
+                               : cudaFuncSetAttribute(ln_bwd_cm_v<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smv);
+      if (e != cudaSuccess) return e;
+    }
+    if (use_bf16)
+      launch_k(ln_bwd_cm_v<bf16>, grid, 256, smv, s, (const bf16 *)dy, (const bf16 *)x, pitch, gamma, (bf16 *)dx, R, C,
+               dgamma, dbeta);
+    else
+      launch_k(ln_bwd_cm_v<float>, grid, 256, smv, s, (const float *)dy, (const float *)x, pitch, gamma, (float *)dx, R,
+               C, dgamma, dbeta);
+    return cudaGetLastError();
+  }
   const size_t sm = ((size_t)2 * C * 33 + (size_t)8 * 2 * C) * sizeof(float);
   if (sm > 48 * 1024) {
     cudaError_t e = use_bf16 ? cudaFuncSetAttribute(ln_bwd_cm_k<bf16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)

@@ -6,10 +6,11 @@
 // the 152 SMs), and, for a product whose epilogue adds into an fp32
 // destination with atomics (the weight gradients), the number of K ranges the
 // contraction is split into.  Between evo_tune_begin and evo_tune_end every
-// GEMM launch of the library is keyed by its shape and epilogue; the k-th
-// launch of a key runs candidate k mod n of that key's list, bracketed by a
-// CUDA event pair.  evo_tune_end takes, per key, the candidate with the lowest
-// mean time; later launches of that key use it (graph captures included).
+// GEMM launch of the library is keyed by its shape and epilogue; each run of
+// n consecutive launches of a key tries each of the key's n candidates once
+// (in a shuffled order), every launch bracketed by a CUDA event pair.
+// evo_tune_end takes, per key, the candidate with the lowest median time;
+// later launches of that key use it (graph captures included).
 // While a stream is capturing a graph nothing is timed.
 #include <algorithm>
 #include <array>
@@ -166,6 +167,24 @@ void load_cache_once() {
   if (cache_path()) load_table(cache_path());
 }
 
+// Candidate of the k-th launch of a key: every n consecutive launches run
+// each of the n candidates once, in an order that changes from one group to
+// the next, so that a candidate is not tied to one call site of a workload
+// that launches the key several times per pass.
+int cand_of_call(uint64_t k, uint32_t n) {
+  const uint64_t group = k / n;
+  uint32_t perm[16];
+  for (uint32_t i = 0; i < n; ++i) perm[i] = i;
+  uint64_t x = group * 0x9E3779B97F4A7C15ull + 0x2545F4914F6CDD1Dull;
+  for (uint32_t i = n - 1; i > 0; --i) {  // Fisher-Yates with a xorshift stream
+    x ^= x << 13, x ^= x >> 7, x ^= x << 17;
+    const uint32_t j = (uint32_t)(x % (i + 1));
+    const uint32_t t = perm[i];
+    perm[i] = perm[j], perm[j] = t;
+  }
+  return (int)perm[k % n];
+}
+
 cudaEvent_t pool_event() {
   if (g_next == g_pool.size()) {
     cudaEvent_t e;
@@ -198,7 +217,7 @@ TuneChoice tune_choose(const GemmOp &g, int default_bn, cudaStream_t s) {
     it->second.cands = candidates(g, default_bn);
   }
   Entry &e = it->second;
-  const int ci = (int)(e.calls++ % e.cands.size());
+  const int ci = cand_of_call(e.calls++, (uint32_t)e.cands.size());
   c.bn = e.cands[ci].bn;
   c.splits = e.cands[ci].splits;
   c.a = pool_event();
@@ -238,23 +257,28 @@ int evo_tune_end(evo_stream_t stream) {
   int tuned = 0;
   for (auto &kv : g_table) {
     Entry &e = kv.second;
-    std::vector<double> sum(e.cands.size(), 0.0);
-    std::vector<int> n(e.cands.size(), 0);
+    std::vector<std::vector<float>> ms(e.cands.size());
     for (const Trial &t : e.trials) {
-      float ms = 0.f;
-      if (cudaEventElapsedTime(&ms, t.a, t.b) != cudaSuccess) return EVO_ERR_CUDA;
-      sum[t.cand] += ms;
-      n[t.cand] += 1;
+      float x = 0.f;
+      if (cudaEventElapsedTime(&x, t.a, t.b) != cudaSuccess) return EVO_ERR_CUDA;
+      ms[t.cand].push_back(x);
     }
     e.trials.clear();
-    // a candidate that never ran cannot win; the default (index 0) stays
+    // the median time per candidate (robust to a cold first launch); a
+    // candidate that never ran cannot win, and the default (index 0) stays
     // unless every candidate ran
+    std::vector<float> med(e.cands.size(), 0.f);
     bool all = true;
-    for (size_t i = 0; i < n.size(); ++i) all = all && n[i] > 0;
+    for (size_t i = 0; i < ms.size(); ++i) {
+      all = all && !ms[i].empty();
+      if (ms[i].empty()) continue;
+      std::sort(ms[i].begin(), ms[i].end());
+      med[i] = ms[i][ms[i].size() / 2];
+    }
     e.best = 0;
     if (all) {
-      for (size_t i = 1; i < n.size(); ++i)
-        if (sum[i] / n[i] < sum[e.best] / n[e.best]) e.best = (int)i;
+      for (size_t i = 1; i < med.size(); ++i)
+        if (med[i] < med[e.best]) e.best = (int)i;
     }
     ++tuned;
   }
