@@ -459,8 +459,9 @@ struct Drv {
     ln(zin, pre + ".ln_in", B(b.xz), Mz, (int)Cz);
     GemmOp g = mk(Mz, ABG, Cz, B(b.xz), Cz, 0, W(pre + ".w_abg"), Cz, 0, B(b.abg), ABG);
     g.e.bias = P(pre + ".b_abg");
+    g.e.act = ACT_SIGMOID, g.e.act_n0 = (int)(4 * cmul);  // the output gate g
     gemm(g);
-    ck(trimul_gate_fwd(B(b.abg), ABG, pm, B(b.A), B(b.B), Rp, (int)R, (int)cmul, (int)Cz, t, bf, s));
+    ck(trimul_gate_fwd(B(b.abg), ABG, pm, B(b.A), B(b.B), Rp, (int)R, (int)cmul, t, bf, s));
     // X_c = A_c B_c^T per channel c (incoming stores A, B transposed, so the product is the same)
     GemmOp x = mk(R, R, R, B(b.A), Rp, 0, B(b.B), Rp, 0, B(b.X), Rp);
     x.batch = (int)cmul, x.a_bs = R * Rp, x.b_bs = R * Rp, x.e.c_bstride = R * Rp;

@@ -152,11 +152,12 @@ cudaError_t head_proj_fwd(const void *x, const float *w, void *out, int R, int C
 cudaError_t head_proj_bwd(const float *dbias, const void *x, const float *w, void *dx, int accumulate,
                           int R, int C, int H, int transpose, int use_bf16, cudaStream_t s, float *dw);
 
-// Triangle multiplication gating: abg[P, ld] raw projections [ap|ag|bp|bg|g];
-// a,b written channel-major [c][R][pitch] (incoming: transposed positions);
-// g columns replaced by sigmoid(g) in place.
-cudaError_t trimul_gate_fwd(void *abg, int64_t ld, const float *mask, void *A, void *B, int64_t pitch,
-                            int R, int cm, int cz, int incoming, int use_bf16, cudaStream_t s);
+// Triangle multiplication gating: abg[P, ld] projections [ap|ag|bp|bg|g] (the
+// output gate g already through its sigmoid, by the projection's epilogue);
+// a = mask ap sigmoid(ag), b = mask bp sigmoid(bg) written channel-major
+// [c][R][pitch] (incoming: transposed positions).
+cudaError_t trimul_gate_fwd(const void *abg, int64_t ld, const float *mask, void *A, void *B, int64_t pitch,
+                            int R, int cm, int incoming, int use_bf16, cudaStream_t s);
 cudaError_t trimul_gate_bwd(const void *dA, const void *dB, int64_t pitch, const void *abg, int64_t ld,
                             const float *mask, void *dabg, int R, int cm, int incoming, int use_bf16,
                             cudaStream_t s);

@@ -222,6 +222,208 @@ __global__ void __launch_bounds__(256) head_proj_bwd_k(const float *dbias, const
 }
 
 
+// CPL consecutive bf16 channels per lane as floats (CPL = 4 or 8).
+template <int CPL>
+__device__ __forceinline__ void ldc(const bf16 *p, float (&v)[CPL]) {
+  if constexpr (CPL == 8) {
+    ld8(p, v);
+  } else {
+    const uint2 w = *reinterpret_cast<const uint2 *>(p);
+    const float2 a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&w.x));
+    const float2 b = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&w.y));
+    v[0] = a.x, v[1] = a.y, v[2] = b.x, v[3] = b.y;
+  }
+}
+template <int CPL>
+__device__ __forceinline__ void stc(bf16 *p, const float (&v)[CPL]) {
+  if constexpr (CPL == 8) {
+    st8(p, v);
+  } else {
+    uint2 w;
+    *reinterpret_cast<__nv_bfloat162 *>(&w.x) = __floats2bfloat162_rn(v[0], v[1]);
+    *reinterpret_cast<__nv_bfloat162 *>(&w.y) = __floats2bfloat162_rn(v[2], v[3]);
+    *reinterpret_cast<uint2 *>(p) = w;
+  }
+}
+
+// Sum of H per-lane values over the TPR lanes of a position group (aligned
+// groups of TPR lanes), by halving exchanges: at the step with offset o the
+// lane with bit o set keeps the upper half of its remaining heads and sends
+// the lower half.  Lane l ends with the full sum of head head_of_lane(l).
+template <int H, int TPR>
+__device__ __forceinline__ float head_reduce(float (&a)[H], int lane) {
+  int n = H;
+#pragma unroll
+  for (int o = TPR / 2; o >= 1; o >>= 1) {
+    if (n > 1) {
+      const int half = n / 2;
+      const bool up = (lane & o) != 0;
+#pragma unroll
+      for (int i = 0; i < H / 2; ++i) {
+        if (i < half) {
+          const float send = up ? a[i] : a[i + half];
+          const float keep = up ? a[i + half] : a[i];
+          a[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+        }
+      }
+      n = half;
+    } else {
+      a[0] += __shfl_xor_sync(0xffffffffu, a[0], o);
+    }
+  }
+  return a[0];
+}
+// the head whose sum lane l holds after head_reduce, and whether l is the
+// lowest lane holding it
+template <int H, int TPR>
+__device__ __forceinline__ int head_of_lane(int lane, bool &writer) {
+  int h = 0, n = H, low = 0;
+#pragma unroll
+  for (int o = TPR / 2; o >= 1; o >>= 1) {
+    if (n > 1) {
+      n /= 2;
+      if (lane & o) h += n;
+    } else {
+      low |= lane & o;
+    }
+  }
+  writer = low == 0;
+  return h;
+}
+
+// Pair-bias projection, BF16: a position's C channels are spread over
+// TPR = C / CPL lanes with CPL channels each, so the lane's slice of w stays
+// in registers; U warp-steps of loads are in flight before the products are
+// reduced over the group (head_reduce).  Grid-stride over warp-steps.
+template <int H, int C, int CPL, int U>
+__global__ void __launch_bounds__(256) head_proj_fwd_w(const bf16 *x, const float *w, bf16 *out, int R,
+                                                       int transpose) {
+  pdl_entry();
+  constexpr int TPR = C / CPL, PPW = 32 / TPR;
+  const int lane = threadIdx.x & 31;
+  const int sub = lane % TPR, pw = lane / TPR;
+  float wl[H][CPL];
+#pragma unroll
+  for (int h = 0; h < H; ++h)
+#pragma unroll
+    for (int k = 0; k < CPL; ++k) wl[h][k] = w[h * C + sub * CPL + k];
+  bool writer;
+  const int hsel = head_of_lane<H, TPR>(lane, writer);
+  const int64_t P = (int64_t)R * R;
+  const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  const int64_t w0 = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  for (int64_t base = w0 * (PPW * U); base < P; base += nwarps * (PPW * U)) {
+    float v[U][CPL];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t p = base + u * PPW + pw;
+      if (p < P) {
+        ldc<CPL>(x + p * C + sub * CPL, v[u]);
+      } else {
+#pragma unroll
+        for (int k = 0; k < CPL; ++k) v[u][k] = 0.f;
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      float acc[H];
+#pragma unroll
+      for (int h = 0; h < H; ++h) {
+        acc[h] = 0.f;
+#pragma unroll
+        for (int k = 0; k < CPL; ++k) acc[h] = fmaf(v[u][k], wl[h][k], acc[h]);
+      }
+      const float r = head_reduce<H, TPR>(acc, lane);
+      const int64_t p = base + u * PPW + pw;
+      if (writer && p < P) {
+        int64_t i;
+        int j;
+        divmod(p, R, i, j);
+        const int64_t pp = transpose ? (int64_t)j * R + i : p;
+        out[hsel * P + pp] = __float2bfloat16_rn(r);
+      }
+    }
+  }
+}
+
+// Backward: dx (+)= sum_h dbias[h][pos'] w[h] over the lane's CPL channels,
+// and the lane's slice of dw accumulates in registers (one atomic add per
+// element and block at the end).
+template <int H, int C, int CPL, int U>
+__global__ void __launch_bounds__(256) head_proj_bwd_w(const float *dbias, const bf16 *x, const float *w, bf16 *dx,
+                                                       int accumulate, int R, int transpose, float *dw) {
+  pdl_entry();
+  constexpr int TPR = C / CPL, PPW = 32 / TPR;
+  __shared__ float red[8][H * C];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int sub = lane % TPR, pw = lane / TPR;
+  float wl[H][CPL], aw[H][CPL];
+#pragma unroll
+  for (int h = 0; h < H; ++h)
+#pragma unroll
+    for (int k = 0; k < CPL; ++k) wl[h][k] = w[h * C + sub * CPL + k], aw[h][k] = 0.f;
+  const int64_t P = (int64_t)R * R;
+  const int64_t nwarps = (int64_t)gridDim.x * 8;
+  const int64_t w0 = (int64_t)blockIdx.x * 8 + warp;
+  for (int64_t base = w0 * (PPW * U); base < P; base += nwarps * (PPW * U)) {
+    float v[U][CPL], d[U][CPL], g[U][H];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t p = base + u * PPW + pw;
+      if (p < P) {
+        int64_t i;
+        int j;
+        divmod(p, R, i, j);
+        const int64_t pp = transpose ? (int64_t)j * R + i : p;
+#pragma unroll
+        for (int h = 0; h < H; ++h) g[u][h] = dbias[h * P + pp];
+        ldc<CPL>(x + p * C + sub * CPL, v[u]);
+        if (accumulate) {
+          ldc<CPL>(dx + p * C + sub * CPL, d[u]);
+        } else {
+#pragma unroll
+          for (int k = 0; k < CPL; ++k) d[u][k] = 0.f;
+        }
+      } else {
+#pragma unroll
+        for (int h = 0; h < H; ++h) g[u][h] = 0.f;
+#pragma unroll
+        for (int k = 0; k < CPL; ++k) v[u][k] = d[u][k] = 0.f;
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+#pragma unroll
+      for (int h = 0; h < H; ++h)
+#pragma unroll
+        for (int k = 0; k < CPL; ++k) {
+          d[u][k] = fmaf(g[u][h], wl[h][k], d[u][k]);
+          aw[h][k] = fmaf(g[u][h], v[u][k], aw[h][k]);
+        }
+      const int64_t p = base + u * PPW + pw;
+      if (p < P) stc<CPL>(dx + p * C + sub * CPL, d[u]);
+    }
+  }
+  // dw: lanes of the same sub hold the same channels; sum over the warp's
+  // position groups, then over the block's warps
+#pragma unroll
+  for (int h = 0; h < H; ++h)
+#pragma unroll
+    for (int k = 0; k < CPL; ++k) {
+      float t = aw[h][k];
+#pragma unroll
+      for (int o = TPR; o < 32; o <<= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+      if (pw == 0) red[warp][h * C + sub * CPL + k] = t;
+    }
+  __syncthreads();
+  for (int k = threadIdx.x; k < H * C; k += blockDim.x) {
+    float t = 0.f;
+#pragma unroll
+    for (int ww = 0; ww < 8; ++ww) t += red[ww][k];
+    atomicAdd(dw + k, t);
+  }
+}
+
 // Pair-bias projection, BF16 fast path: one thread per position, the
 // position's C channels read as 16-byte vectors, w staged in shared memory.
 template <int H, typename OT>
@@ -405,8 +607,8 @@ __global__ void __launch_bounds__(256) trimul_gate_bwd_k(const T *dA, const T *d
 // 8 channels; each position's 8 channels of a_proj, a_gate, b_proj, b_gate
 // arrive as four 16-byte loads; the sigmoid of the g columns is folded in
 // (block z handles g columns z*8.., z*8 + 8).
-__global__ void __launch_bounds__(256) trimul_gate_fwd_v8(bf16 *abg, int64_t ld, const float *mask, bf16 *A, bf16 *B,
-                                                          int64_t pitch, int R, int cm, int cz, int incoming) {
+__global__ void __launch_bounds__(256) trimul_gate_fwd_v8(const bf16 *abg, int64_t ld, const float *mask, bf16 *A,
+                                                          bf16 *B, int64_t pitch, int R, int cm, int incoming) {
   pdl_entry();
   __shared__ bf16 as[8][32][34], bs[8][32][34];
   const int q0 = blockIdx.x * 32, r0 = blockIdx.y * 32, c0 = blockIdx.z * 8;
@@ -416,7 +618,7 @@ __global__ void __launch_bounds__(256) trimul_gate_fwd_v8(bf16 *abg, int64_t ld,
     float av[8] = {}, bv[8] = {};
     if (orow < R && ocol < R) {
       const int64_t p = incoming ? (int64_t)ocol * R + orow : (int64_t)orow * R + ocol;
-      bf16 *row = abg + p * ld;
+      const bf16 *row = abg + p * ld;
       const float mk = mask[p];
       float ap[8], ag[8], bp[8], bg[8];
       ld8(row + c0, ap);
@@ -427,13 +629,6 @@ __global__ void __launch_bounds__(256) trimul_gate_fwd_v8(bf16 *abg, int64_t ld,
       for (int k = 0; k < 8; ++k) {
         av[k] = mk * __fdividef(ap[k], 1.f + __expf(-ag[k]));
         bv[k] = mk * __fdividef(bp[k], 1.f + __expf(-bg[k]));
-      }
-      for (int gc = c0; gc < cz; gc += gridDim.z * 8) {  // sigmoid of this block's share of the g columns
-        float g[8];
-        ld8(row + 4 * cm + gc, g);
-#pragma unroll
-        for (int k = 0; k < 8; ++k) g[k] = __fdividef(1.f, 1.f + __expf(-g[k]));
-        st8(row + 4 * cm + gc, g);
       }
     }
 #pragma unroll
@@ -526,50 +721,48 @@ __global__ void __launch_bounds__(256) trimul_gate_bwd_v8(const bf16 *dA, const 
 // channel pitch, so both the channel-wise and the column-wise accesses are
 // free of bank conflicts).  Position of (row, col): row * R + col (outgoing)
 // or col * R + row (incoming).
-constexpr int TG_ROWS = 2, TG_COLS = 64, TG_CH = 64, TG_LDC = TG_CH + 1;
+constexpr int TG_ROWS = 2, TG_COLS = 64, TG_CH = 64, TG_LDC = TG_CH + 1, TG_U = 4;
 
 __device__ __forceinline__ float sigm(float x) { return __fdividef(1.f, 1.f + __expf(-x)); }
 
-__global__ void __launch_bounds__(256) trimul_gate_fwd_t(bf16 *abg, int64_t ld, const float *mask, bf16 *A, bf16 *B,
-                                                         int64_t pitch, int R, int cm, int cz, int incoming) {
+__global__ void __launch_bounds__(256) trimul_gate_fwd_t(const bf16 *abg, int64_t ld, const float *mask, bf16 *A,
+                                                         bf16 *B, int64_t pitch, int R, int cm, int incoming) {
   pdl_entry();
   __shared__ bf16 as[TG_ROWS][TG_COLS][TG_LDC];
   __shared__ bf16 bs[TG_ROWS][TG_COLS][TG_LDC];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int q0 = blockIdx.x * TG_COLS, r0 = blockIdx.y * TG_ROWS, c0 = blockIdx.z * TG_CH;
   const int seg = lane >> 3, sub = lane & 7;  // segment (ap, ag, bp, bg) and its 8-channel piece
-  const int gz = (cz + TG_CH - 1) / TG_CH;    // z-blocks that also take a share of the g columns
-  for (int pi = warp; pi < TG_ROWS * TG_COLS; pi += 8) {
-    const int orl = pi / TG_COLS, ocl = pi % TG_COLS;
-    const int orow = r0 + orl, ocol = q0 + ocl;
-    float v[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    float mk = 0.f;
-    int64_t p = 0;
-    const bool in = orow < R && ocol < R;
-    if (in) {
-      p = incoming ? (int64_t)ocol * R + orow : (int64_t)orow * R + ocol;
-      mk = mask[p];
-      ld8(abg + p * ld + seg * cm + c0 + sub * 8, v);
+  // a warp takes positions warp + 8u + 32k; the loads of TG_U positions are
+  // issued before any of them is used
+  for (int pb = warp; pb < TG_ROWS * TG_COLS; pb += 8 * TG_U) {
+    float v[TG_U][8], mk[TG_U];
+#pragma unroll
+    for (int u = 0; u < TG_U; ++u) {
+      const int pi = pb + 8 * u;
+      const int orow = r0 + pi / TG_COLS, ocol = q0 + pi % TG_COLS;
+      mk[u] = 0.f;
+      if (orow < R && ocol < R) {
+        const int64_t p = incoming ? (int64_t)ocol * R + orow : (int64_t)orow * R + ocol;
+        mk[u] = mask[p];
+        ld8(abg + p * ld + seg * cm + c0 + sub * 8, v[u]);
+      } else {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) v[u][k] = 0.f;
+      }
     }
-    // lanes 0-7 (ap) take ag from lanes 8-15; lanes 16-23 (bp) take bg from 24-31
-    float gv[8];
 #pragma unroll
-    for (int k = 0; k < 8; ++k) gv[k] = __shfl_down_sync(0xffffffffu, v[k], 8);
-    if ((seg & 1) == 0) {
-      bf16 *dst = seg == 0 ? &as[orl][ocl][sub * 8] : &bs[orl][ocl][sub * 8];
+    for (int u = 0; u < TG_U; ++u) {
+      const int pi = pb + 8 * u;
+      const int orl = pi / TG_COLS, ocl = pi % TG_COLS;
+      // lanes 0-7 (ap) take ag from lanes 8-15; lanes 16-23 (bp) take bg from 24-31
+      float gv[8];
 #pragma unroll
-      for (int k = 0; k < 8; ++k) dst[k] = __float2bfloat16_rn(mk * v[k] * sigm(gv[k]));
-    }
-    // sigmoid of this block's share of the output-gate columns, in place
-    if (in && blockIdx.z < gz && lane < 8) {
-      const int gc = blockIdx.z * TG_CH + sub * 8;
-      if (gc < cz) {
-        float g[8];
-        bf16 *gp = abg + p * ld + 4 * cm + gc;
-        ld8(gp, g);
+      for (int k = 0; k < 8; ++k) gv[k] = __shfl_down_sync(0xffffffffu, v[u][k], 8);
+      if ((seg & 1) == 0) {
+        bf16 *dst = seg == 0 ? &as[orl][ocl][sub * 8] : &bs[orl][ocl][sub * 8];
 #pragma unroll
-        for (int k = 0; k < 8; ++k) g[k] = sigm(g[k]);
-        st8(gp, g);
+        for (int k = 0; k < 8; ++k) dst[k] = __float2bfloat16_rn(mk[u] * v[u][k] * sigm(gv[k]));
       }
     }
   }
@@ -604,68 +797,84 @@ __global__ void __launch_bounds__(256) trimul_gate_bwd_t(const bf16 *dA, const b
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int q0 = blockIdx.x * TG_COLS, r0 = blockIdx.y * TG_ROWS, c0 = blockIdx.z * TG_CH;
   const int64_t plane = (int64_t)R * pitch;
-  // channel-major gradient rows in (128 B per warp instruction)
-  for (int t = warp; t < 2 * TG_CH * TG_ROWS; t += 8) {
-    const int which = t / (TG_CH * TG_ROWS), rem = t % (TG_CH * TG_ROWS);
-    const int ch = rem / TG_ROWS, orl = rem % TG_ROWS;
-    const int c = c0 + ch, orow = r0 + orl, ocol = q0 + 2 * lane;
-    bf16 (*dst)[TG_COLS][TG_LDC] = which ? bs : as;
-    bf16 v0 = __float2bfloat16_rn(0.f), v1 = v0;
-    if (c < cm && orow < R && ocol < R) {
-      const bf16 *src = (which ? dB : dA) + (int64_t)c * plane + (int64_t)orow * pitch + ocol;
-      if (ocol + 1 < R && ((((uintptr_t)src) & 3u) == 0)) {
-        const __nv_bfloat162 w = *reinterpret_cast<const __nv_bfloat162 *>(src);
-        v0 = w.x, v1 = w.y;
-      } else {
-        v0 = src[0];
-        if (ocol + 1 < R) v1 = src[1];
+  // channel-major gradient rows in (128 B per warp instruction), eight rows
+  // of a warp in flight together
+  constexpr int NROW = 2 * TG_CH * TG_ROWS, RU = 8;
+  for (int tb = warp; tb < NROW; tb += 8 * RU) {
+    __nv_bfloat162 w[RU];
+#pragma unroll
+    for (int u = 0; u < RU; ++u) {
+      const int t = tb + 8 * u;
+      const int which = t / (TG_CH * TG_ROWS), rem = t % (TG_CH * TG_ROWS);
+      const int ch = rem / TG_ROWS, orl = rem % TG_ROWS;
+      const int c = c0 + ch, orow = r0 + orl, ocol = q0 + 2 * lane;
+      w[u].x = w[u].y = __float2bfloat16_rn(0.f);
+      if (c < cm && orow < R && ocol < R) {
+        const bf16 *src = (which ? dB : dA) + (int64_t)c * plane + (int64_t)orow * pitch + ocol;
+        if (ocol + 1 < R && ((((uintptr_t)src) & 3u) == 0)) {
+          w[u] = *reinterpret_cast<const __nv_bfloat162 *>(src);
+        } else {
+          w[u].x = src[0];
+          if (ocol + 1 < R) w[u].y = src[1];
+        }
       }
     }
-    dst[orl][2 * lane][ch] = v0;
-    dst[orl][2 * lane + 1][ch] = v1;
+#pragma unroll
+    for (int u = 0; u < RU; ++u) {
+      const int t = tb + 8 * u;
+      const int which = t / (TG_CH * TG_ROWS), rem = t % (TG_CH * TG_ROWS);
+      const int ch = rem / TG_ROWS, orl = rem % TG_ROWS;
+      bf16 (*dst)[TG_COLS][TG_LDC] = which ? bs : as;
+      dst[orl][2 * lane][ch] = w[u].x;
+      dst[orl][2 * lane + 1][ch] = w[u].y;
+    }
   }
   __syncthreads();
   const int seg = lane >> 3, sub = lane & 7;
-  for (int pi = warp; pi < TG_ROWS * TG_COLS; pi += 8) {
-    const int orl = pi / TG_COLS, ocl = pi % TG_COLS;
-    const int orow = r0 + orl, ocol = q0 + ocl;
-    if (orow >= R || ocol >= R) continue;  // warp-uniform
-    const int64_t p = incoming ? (int64_t)ocol * R + orow : (int64_t)orow * R + ocol;
-    const float mk = mask[p];
-    float v[8];
-    ld8(abg + p * ld + seg * cm + c0 + sub * 8, v);
-    float gv[8], pv[8];
+  for (int pb = warp; pb < TG_ROWS * TG_COLS; pb += 8 * TG_U) {
+    float v[TG_U][8], mk[TG_U];
+    int64_t pp[TG_U];
 #pragma unroll
-    for (int k = 0; k < 8; ++k) {
-      gv[k] = __shfl_down_sync(0xffffffffu, v[k], 8);  // the gate pre-activation, for lanes of ap / bp
-      pv[k] = __shfl_up_sync(0xffffffffu, v[k], 8);    // the projection, for lanes of ag / bg
-    }
-    const bf16 *src = seg < 2 ? &as[orl][ocl][sub * 8] : &bs[orl][ocl][sub * 8];
-    float out[8];
-#pragma unroll
-    for (int k = 0; k < 8; ++k) {
-      const float d = __bfloat162float(src[k]) * mk;
-      if ((seg & 1) == 0) {
-        out[k] = d * sigm(gv[k]);  // d proj = d * sigmoid(gate)
+    for (int u = 0; u < TG_U; ++u) {
+      const int pi = pb + 8 * u;
+      const int orow = r0 + pi / TG_COLS, ocol = q0 + pi % TG_COLS;
+      mk[u] = 0.f;
+      pp[u] = -1;
+      if (orow < R && ocol < R) {
+        pp[u] = incoming ? (int64_t)ocol * R + orow : (int64_t)orow * R + ocol;
+        mk[u] = mask[pp[u]];
+        ld8(abg + pp[u] * ld + seg * cm + c0 + sub * 8, v[u]);
       } else {
-        const float sg = sigm(v[k]);
-        out[k] = d * pv[k] * sg * (1.f - sg);  // d gate = d * proj * sigmoid'(gate)
+#pragma unroll
+        for (int k = 0; k < 8; ++k) v[u][k] = 0.f;
       }
     }
-    st8(dabg + p * ld + seg * cm + c0 + sub * 8, out);
+#pragma unroll
+    for (int u = 0; u < TG_U; ++u) {
+      const int pi = pb + 8 * u;
+      const int orl = pi / TG_COLS, ocl = pi % TG_COLS;
+      float gv[8], pv[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        gv[k] = __shfl_down_sync(0xffffffffu, v[u][k], 8);  // the gate pre-activation, for lanes of ap / bp
+        pv[k] = __shfl_up_sync(0xffffffffu, v[u][k], 8);    // the projection, for lanes of ag / bg
+      }
+      if (pp[u] < 0) continue;  // warp-uniform
+      const bf16 *src = seg < 2 ? &as[orl][ocl][sub * 8] : &bs[orl][ocl][sub * 8];
+      float out[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        const float d = __bfloat162float(src[k]) * mk[u];
+        if ((seg & 1) == 0) {
+          out[k] = d * sigm(gv[k]);  // d proj = d * sigmoid(gate)
+        } else {
+          const float sg = sigm(v[u][k]);
+          out[k] = d * pv[k] * sg * (1.f - sg);  // d gate = d * proj * sigmoid'(gate)
+        }
+      }
+      st8(dabg + pp[u] * ld + seg * cm + c0 + sub * 8, out);
+    }
   }
-}
-
-template <typename T>
-__global__ void sigmoid_cols_k(T *x, int64_t ld, int col0, int ncols, int64_t P) {
-  pdl_entry();
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= P * ncols) return;
-  int64_t p;
-  int c;
-  divmod(i, ncols, p, c);
-  T *e = x + p * ld + col0 + c;
-  stf(e, sigmoidf_(ldf(e)));
 }
 
 template <typename T>
@@ -820,7 +1029,13 @@ cudaError_t head_proj_fwd(const void *x, const float *w, void *out, int R, int C
   Prof prof("head_proj_fwd", s, 2.0 * R * (double)R * C * H, (use_bf16 ? 2.0 : 4.0) * R * (double)R * C + 4.0 * H * R * (double)R, 1);
   if (H > 8) return cudaErrorInvalidValue;
   const int64_t P = (int64_t)R * R;
-  if (use_bf16 && C % 8 == 0 && (((uintptr_t)x) & 15u) == 0 && (H == 4 || H == 8)) {
+  if (use_bf16 && C == 128 && (((uintptr_t)x) & 15u) == 0 && (H == 4 || H == 8)) {
+    constexpr int U = 4;
+    const int64_t steps = (P + 2 * U - 1) / (2 * U);  // warp-steps (two positions each)
+    const unsigned blocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>((steps + 7) / 8, 152 * 3));
+    if (H == 4) launch_k(head_proj_fwd_w<4, 128, 8, U>, blocks, 256, 0, s, (const bf16 *)x, w, (bf16 *)out, R, transpose);
+    else launch_k(head_proj_fwd_w<8, 128, 8, U>, blocks, 256, 0, s, (const bf16 *)x, w, (bf16 *)out, R, transpose);
+  } else if (use_bf16 && C % 8 == 0 && (((uintptr_t)x) & 15u) == 0 && (H == 4 || H == 8)) {
     const size_t sm = (size_t)H * C * sizeof(float);
     if (H == 4) launch_k(head_proj_fwd_v8<4, bf16>, nblk(P, 128), 128, sm, s, (const bf16 *)x, w, (bf16 *)out, R, C, transpose);
     else launch_k(head_proj_fwd_v8<8, bf16>, nblk(P, 128), 128, sm, s, (const bf16 *)x, w, (bf16 *)out, R, C, transpose);
@@ -844,7 +1059,21 @@ cudaError_t head_proj_bwd(const float *dbias, const void *x, const float *w, voi
   const int64_t ppb = ((int64_t)R * R + nb - 1) / nb;
   const size_t sm = (size_t)8 * H * C * sizeof(float);
   if (sm > 48 * 1024) return cudaErrorInvalidValue;
-  if (use_bf16 && C == 128 && (H == 4 || H == 8) && (((uintptr_t)x) & 3u) == 0 && (((uintptr_t)dx) & 3u) == 0) {
+  if (use_bf16 && C == 128 && (H == 4 || H == 8) && (((uintptr_t)x) & 15u) == 0 && (((uintptr_t)dx) & 15u) == 0) {
+    // H = 4: eight channels per lane (16 positions' worth of w and dw in
+    // registers); H = 8: four channels per lane
+    constexpr int U = 4;
+    const int64_t P = (int64_t)R * R;
+    const int64_t ppw = H == 4 ? 2 : 1;
+    const int64_t steps = (P + ppw * U - 1) / (ppw * U);
+    const unsigned blocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>((steps + 7) / 8, 152 * 2));
+    if (H == 4)
+      launch_k(head_proj_bwd_w<4, 128, 8, U>, blocks, 256, 0, s, dbias, (const bf16 *)x, w, (bf16 *)dx, accumulate, R,
+               transpose, dw);
+    else
+      launch_k(head_proj_bwd_w<8, 128, 4, U>, blocks, 256, 0, s, dbias, (const bf16 *)x, w, (bf16 *)dx, accumulate, R,
+               transpose, dw);
+  } else if (use_bf16 && C == 128 && (H == 4 || H == 8) && (((uintptr_t)x) & 3u) == 0 && (((uintptr_t)dx) & 3u) == 0) {
     if (H == 4)
       launch_k(head_proj_bwd_v8<4, 2>, nb, 256, 0, s, dbias, (const bf16 *)x, w, (bf16 *)dx, accumulate, R, transpose,
                                                 ppb, dw);
@@ -860,26 +1089,25 @@ cudaError_t head_proj_bwd(const float *dbias, const void *x, const float *w, voi
   return cudaGetLastError();
 }
 
-cudaError_t trimul_gate_fwd(void *abg, int64_t ld, const float *mask, void *A, void *B, int64_t pitch, int R, int cm,
-                            int cz, int incoming, int use_bf16, cudaStream_t s) {
-  Prof prof("trimul_gate_fwd", s, 0, (use_bf16 ? 2.0 : 4.0) * R * (double)R * (6.0 * cm + 2.0 * cz), use_bf16 ? 1 : 2);
+cudaError_t trimul_gate_fwd(const void *abg, int64_t ld, const float *mask, void *A, void *B, int64_t pitch, int R,
+                            int cm, int incoming, int use_bf16, cudaStream_t s) {
+  Prof prof("trimul_gate_fwd", s, 0, (use_bf16 ? 2.0 : 4.0) * R * (double)R * 6.0 * cm, 1);
   dim3 grid((R + 31) / 32, (R + 31) / 32, (cm + 3) / 4);
-  const int64_t P = (int64_t)R * R;
-  const bool v8 = cm % 8 == 0 && cz % 8 == 0 && ld % 8 == 0 && (((uintptr_t)abg) & 15u) == 0;
-  if (use_bf16 && v8 && cm % TG_CH == 0 && (cz + TG_CH - 1) / TG_CH <= cm / TG_CH) {
+  const bool v8 = cm % 8 == 0 && ld % 8 == 0 && (((uintptr_t)abg) & 15u) == 0;
+  if (use_bf16 && v8 && cm % TG_CH == 0) {
     dim3 gt((R + TG_COLS - 1) / TG_COLS, (R + TG_ROWS - 1) / TG_ROWS, cm / TG_CH);
-    launch_k(trimul_gate_fwd_t, gt, 256, 0, s, (bf16 *)abg, ld, mask, (bf16 *)A, (bf16 *)B, pitch, R, cm, cz, incoming);
+    launch_k(trimul_gate_fwd_t, gt, 256, 0, s, (const bf16 *)abg, ld, mask, (bf16 *)A, (bf16 *)B, pitch, R, cm,
+             incoming);
   } else if (use_bf16 && v8) {
     dim3 g8((R + 31) / 32, (R + 31) / 32, cm / 8);
-    launch_k(trimul_gate_fwd_v8, g8, 256, 0, s, (bf16 *)abg, ld, mask, (bf16 *)A, (bf16 *)B, pitch, R, cm, cz, incoming);
+    launch_k(trimul_gate_fwd_v8, g8, 256, 0, s, (const bf16 *)abg, ld, mask, (bf16 *)A, (bf16 *)B, pitch, R, cm,
+             incoming);
   } else if (use_bf16) {
     launch_k(trimul_gate_fwd_k<bf16>, grid, 256, 0, s, (const bf16 *)abg, ld, mask, (bf16 *)A, (bf16 *)B, pitch, R, cm,
-                                                 incoming);
-    launch_k(sigmoid_cols_k<bf16>, nblk(P * cz), 256, 0, s, (bf16 *)abg, ld, 4 * cm, cz, P);
+             incoming);
   } else {
     launch_k(trimul_gate_fwd_k<float>, grid, 256, 0, s, (const float *)abg, ld, mask, (float *)A, (float *)B, pitch, R,
-                                                  cm, incoming);
-    launch_k(sigmoid_cols_k<float>, nblk(P * cz), 256, 0, s, (float *)abg, ld, 4 * cm, cz, P);
+             cm, incoming);
   }
   return cudaGetLastError();
 }
