@@ -102,7 +102,18 @@ __global__ void __launch_bounds__(256) colsum_v8_k(const bf16 *x, int64_t ld, in
   float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
   const int64_t r0 = (int64_t)blockIdx.x * rows_per_blk, r1 = min(M, r0 + rows_per_blk);
   if (r_in < rpi) {
-    for (int64_t r = r0 + r_in; r < r1; r += rpi) {
+    // four rows of loads in flight per thread
+    int64_t r = r0 + r_in;
+    for (; r + 3 * rpi < r1; r += 4 * rpi) {
+      float v[4][8];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) ld8(x + (r + u * rpi) * ld + c8, v[u]);
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int k = 0; k < 8; ++k) acc[k] += v[u][k];
+    }
+    for (; r < r1; r += rpi) {
       float v[8];
       ld8(x + r * ld + c8, v);
 #pragma unroll
@@ -934,17 +945,65 @@ __global__ void attn_dq_store_k(AttnArgs a, T *dq) {
 }
 
 // ------------------------------------------------------------ OPM, scaling
-__global__ void opm_inv_norm_k(const float *mask, float *inv, int S, int R, float eps) {
+// inv[i*R + j] = 1 / (eps + sum_s mask[s,i] mask[s,j]): a 32 x 32 tile of
+// (i, j) per block, the mask columns of the tile staged in shared memory 64
+// rows s at a time, 2 x 2 outputs per thread.
+__global__ void __launch_bounds__(256) opm_inv_norm_k(const float *mask, float *inv, int S, int R, float eps) {
   pdl_entry();
-  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= (int64_t)R * R) return;
-  int64_t i64;
-  int j;
-  divmod(idx, R, i64, j);
-  const int i = (int)i64;
-  float n = 0.f;
-  for (int s = 0; s < S; ++s) n += mask[(int64_t)s * R + i] * mask[(int64_t)s * R + j];
-  inv[idx] = 1.f / (eps + n);
+  __shared__ float mi[64][32], mj[64][32];
+  const int i0 = blockIdx.y * 32, j0 = blockIdx.x * 32;
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;  // outputs (i0 + 2ty + a, j0 + 2tx + b)
+  float n00 = 0.f, n01 = 0.f, n10 = 0.f, n11 = 0.f;
+  for (int s0 = 0; s0 < S; s0 += 64) {
+    for (int idx = threadIdx.x; idx < 64 * 32; idx += blockDim.x) {
+      const int ss = idx >> 5, c = idx & 31, srow = s0 + ss;
+      mi[ss][c] = srow < S && i0 + c < R ? mask[(int64_t)srow * R + i0 + c] : 0.f;
+      mj[ss][c] = srow < S && j0 + c < R ? mask[(int64_t)srow * R + j0 + c] : 0.f;
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int ss = 0; ss < 64; ++ss) {
+      const float a0 = mi[ss][2 * ty], a1 = mi[ss][2 * ty + 1];
+      const float b0 = mj[ss][2 * tx], b1 = mj[ss][2 * tx + 1];
+      n00 = fmaf(a0, b0, n00), n01 = fmaf(a0, b1, n01);
+      n10 = fmaf(a1, b0, n10), n11 = fmaf(a1, b1, n11);
+    }
+    __syncthreads();
+  }
+  const int i = i0 + 2 * ty, j = j0 + 2 * tx;
+  if (i < R && j < R) inv[(int64_t)i * R + j] = 1.f / (eps + n00);
+  if (i < R && j + 1 < R) inv[(int64_t)i * R + j + 1] = 1.f / (eps + n01);
+  if (i + 1 < R && j < R) inv[(int64_t)(i + 1) * R + j] = 1.f / (eps + n10);
+  if (i + 1 < R && j + 1 < R) inv[(int64_t)(i + 1) * R + j + 1] = 1.f / (eps + n11);
+}
+
+// bf16 rows of C = 8k channels, 16 bytes per access, two in flight per thread
+__global__ void __launch_bounds__(256) row_scale_v8(const bf16 *x, const float *scale, bf16 *y, int64_t M, int C) {
+  pdl_entry();
+  const int cq = C / 8;
+  const int64_t n = M * cq;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += 2 * stride) {
+    float v[2][8];
+    float sc[2];
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const int64_t e = i + u * stride;
+      if (e < n) {
+        ld8(x + e * 8, v[u]);
+        sc[u] = scale[e / cq];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const int64_t e = i + u * stride;
+      if (e < n) {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) v[u][k] *= sc[u];
+        st8(y + e * 8, v[u]);
+      }
+    }
+  }
 }
 
 template <typename T>
@@ -1169,13 +1228,17 @@ cudaError_t attn_dq_store(const AttnArgs &a, void *dq, int use_bf16, cudaStream_
 
 cudaError_t opm_inv_norm(const float *mask, float *inv, int S, int R, float eps, cudaStream_t s) {
   Prof prof("opm_inv_norm", s, 0, 8.0 * S * (double)R + 4.0 * R * (double)R, 1);
-  launch_k(opm_inv_norm_k, nblk((int64_t)R * R), 256, 0, s, mask, inv, S, R, eps);
+  launch_k(opm_inv_norm_k, dim3((R + 31) / 32, (R + 31) / 32), 256, 0, s, mask, inv, S, R, eps);
   return cudaGetLastError();
 }
 
 cudaError_t row_scale(const void *x, const float *scale, void *y, int64_t M, int C, int use_bf16, cudaStream_t s) {
   Prof prof("row_scale", s, 0, (use_bf16 ? 4.0 : 8.0) * M * (double)C, 1);
-  if (use_bf16) launch_k(row_scale_k<bf16>, nblk(M * C), 256, 0, s, (const bf16 *)x, scale, (bf16 *)y, M, C);
+  if (use_bf16 && C % 8 == 0 && (((uintptr_t)x | (uintptr_t)y) & 15u) == 0) {
+    const int64_t n = M * (C / 8);
+    const unsigned blocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 511) / 512, 152 * 8));
+    launch_k(row_scale_v8, blocks, 256, 0, s, (const bf16 *)x, scale, (bf16 *)y, M, C);
+  } else if (use_bf16) launch_k(row_scale_k<bf16>, nblk(M * C), 256, 0, s, (const bf16 *)x, scale, (bf16 *)y, M, C);
   else launch_k(row_scale_k<float>, nblk(M * C), 256, 0, s, (const float *)x, scale, (float *)y, M, C);
   return cudaGetLastError();
 }
