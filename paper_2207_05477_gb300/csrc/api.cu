@@ -106,10 +106,11 @@ int evo_stack_fwd(const evo_dims *d, int n_blocks, const float *params, const vo
 
 int evo_get_error(evo_stream_t stream) {
   if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) return EVO_ERR_CUDA;
-  int h = 0, h2 = 0;
+  int h = 0, h2 = 0, h3 = 0;
   if (error_word_read_clear(&h) != cudaSuccess) return EVO_ERR_CUDA;
   if (attn_tc_error_read_clear(&h2) != cudaSuccess) return EVO_ERR_CUDA;
-  return h != EVO_OK ? h : h2;
+  if (trimul_tc_error_read_clear(&h3) != cudaSuccess) return EVO_ERR_CUDA;
+  return h != EVO_OK ? h : h2 != EVO_OK ? h2 : h3;
 }
 
 int evo_debug_wait_timeout(long long limit_ns, evo_stream_t stream) {

@@ -158,6 +158,17 @@ cudaError_t head_proj_bwd(const float *dbias, const void *x, const float *w, voi
 // [c][R][pitch] (incoming: transposed positions).
 cudaError_t trimul_gate_fwd(const void *abg, int64_t ld, const float *mask, void *A, void *B, int64_t pitch,
                             int R, int cm, int incoming, int use_bf16, cudaStream_t s);
+// TMA-tiled BF16 versions (cm a multiple of 64, 16-byte aligned rows); they
+// return cudaErrorNotSupported (nothing launched) when a tensor map cannot
+// describe the buffers.
+bool trimul_gate_tma_supported(const void *abg, int64_t ld, const void *A, const void *B, int64_t pitch, int R,
+                               int cm);
+cudaError_t trimul_gate_fwd_tma_launch(const void *abg, int64_t ld, const float *mask, void *A, void *B, int64_t pitch,
+                                       int R, int cm, int incoming, cudaStream_t s);
+cudaError_t trimul_gate_bwd_tma_launch(const void *dA, const void *dB, int64_t pitch, const void *abg, int64_t ld,
+                                       const float *mask, void *dabg, int R, int cm, int incoming, cudaStream_t s);
+// Reads and clears the error word of the TMA gate kernels; synchronous.
+cudaError_t trimul_tc_error_read_clear(int *out);
 cudaError_t trimul_gate_bwd(const void *dA, const void *dB, int64_t pitch, const void *abg, int64_t ld,
                             const float *mask, void *dabg, int R, int cm, int incoming, int use_bf16,
                             cudaStream_t s);

@@ -1151,6 +1151,10 @@ cudaError_t head_proj_bwd(const float *dbias, const void *x, const float *w, voi
 cudaError_t trimul_gate_fwd(const void *abg, int64_t ld, const float *mask, void *A, void *B, int64_t pitch, int R,
                             int cm, int incoming, int use_bf16, cudaStream_t s) {
   Prof prof("trimul_gate_fwd", s, 0, (use_bf16 ? 2.0 : 4.0) * R * (double)R * 6.0 * cm, 1);
+  if (use_bf16 && trimul_gate_tma_supported(abg, ld, A, B, pitch, R, cm)) {
+    const cudaError_t e = trimul_gate_fwd_tma_launch(abg, ld, mask, A, B, pitch, R, cm, incoming, s);
+    if (e != cudaErrorNotSupported) return e;
+  }
   dim3 grid((R + 31) / 32, (R + 31) / 32, (cm + 3) / 4);
   const bool v8 = cm % 8 == 0 && ld % 8 == 0 && (((uintptr_t)abg) & 15u) == 0;
   if (use_bf16 && v8 && cm % TG_CH == 0) {
@@ -1174,6 +1178,10 @@ cudaError_t trimul_gate_fwd(const void *abg, int64_t ld, const float *mask, void
 cudaError_t trimul_gate_bwd(const void *dA, const void *dB, int64_t pitch, const void *abg, int64_t ld,
                             const float *mask, void *dabg, int R, int cm, int incoming, int use_bf16, cudaStream_t s) {
   Prof prof("trimul_gate_bwd", s, 0, (use_bf16 ? 2.0 : 4.0) * R * (double)R * 10.0 * cm, 1);
+  if (use_bf16 && trimul_gate_tma_supported(abg, ld, dA, dB, pitch, R, cm) && (((uintptr_t)dabg) & 15u) == 0) {
+    const cudaError_t e = trimul_gate_bwd_tma_launch(dA, dB, pitch, abg, ld, mask, dabg, R, cm, incoming, s);
+    if (e != cudaErrorNotSupported) return e;
+  }
   dim3 grid((R + 31) / 32, (R + 31) / 32, (cm + 3) / 4);
   const bool v8 = cm % 8 == 0 && ld % 8 == 0 && (((uintptr_t)abg) & 15u) == 0 && (((uintptr_t)dabg) & 15u) == 0;
   if (use_bf16 && v8 && cm % TG_CH == 0) {

@@ -1,0 +1,278 @@
+// Triangle-multiplication gating (Alg. 11 and 12, the gated projections a and
+// b) as TMA-tiled BF16 kernels.
+//
+// The projection output abg is row-major over positions p (columns
+// [ap | ag | bp | bg | g], cm channels each for the first four); the batched
+// per-channel products want a and b channel-major, A[c][i][j] with a row
+// pitch.  One CTA moves a tile of 64 positions (64 consecutive ocol of one
+// orow) x 64 channels: TMA brings the four 8 KB source tiles (128-byte
+// swizzled rows of 64 channels) in at once, the threads gate and transpose
+// through shared memory, and TMA stores the two channel-major 8 KB tiles
+// (rows of 64 positions).  The backward reads dA, dB in the same tiles and
+// writes the gradients of the four projections in place of their tiles.
+// Position of (orow, ocol): orow R + ocol (outgoing) or ocol R + orow
+// (incoming); the tensor maps order their dimensions by stride, so both
+// cases give the same shared-memory tile, rows indexed by ocol.
+#include "tc.cuh"
+
+namespace evo {
+using namespace tc;
+namespace {
+
+constexpr int TT_C = 64;                 // channels per tile
+constexpr int TT_Q = 64;                 // positions per tile
+constexpr int TT_TILE = TT_C * TT_Q * 2;  // bytes of one bf16 tile
+
+__device__ __forceinline__ void tma_store_3d(const CUtensorMap *tm, uint32_t src, int c0, int c1, int c2) {
+  asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.tile.bulk_group [%0, {%2, %3, %4}], [%1];" ::"l"(
+                   (uint64_t)tm),
+               "r"(src), "r"(c0), "r"(c1), "r"(c2)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read_all() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+
+// byte offset of 16-byte chunk q of row r in a tile of 128-byte rows written
+// by TMA with the 128-byte swizzle (tile base 1024-byte aligned)
+__device__ __forceinline__ uint32_t sw128(int r, int q) { return (uint32_t)(r * 128 + ((q ^ (r & 7)) << 4)); }
+
+__device__ __forceinline__ float sigm_tc(float x) { return __fdividef(1.f, 1.f + __expf(-x)); }
+
+__device__ __forceinline__ void lds8(uint32_t addr, float (&v)[8]) {
+  uint32_t w0, w1, w2, w3;
+  asm volatile("ld.shared.v4.b32 {%0, %1, %2, %3}, [%4];" : "=r"(w0), "=r"(w1), "=r"(w2), "=r"(w3) : "r"(addr));
+  // bf16 to fp32 is exact: the bf16 bits are the top half of the fp32 word
+  v[0] = __uint_as_float(w0 << 16), v[1] = __uint_as_float(w0 & 0xffff0000u);
+  v[2] = __uint_as_float(w1 << 16), v[3] = __uint_as_float(w1 & 0xffff0000u);
+  v[4] = __uint_as_float(w2 << 16), v[5] = __uint_as_float(w2 & 0xffff0000u);
+  v[6] = __uint_as_float(w3 << 16), v[7] = __uint_as_float(w3 & 0xffff0000u);
+}
+__device__ __forceinline__ void sts8(uint32_t addr, const float (&v)[8]) {
+  uint32_t w[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k)
+    w[k] = (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(v[2 * k])) |
+           ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(v[2 * k + 1])) << 16);
+  asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(w[0]), "r"(w[1]), "r"(w[2]), "r"(w[3])
+               : "memory");
+}
+__device__ __forceinline__ void sts16(uint32_t addr, float v) {
+  asm volatile("st.shared.b16 [%0], %1;" ::"r"(addr), "h"(__bfloat16_as_ushort(__float2bfloat16_rn(v))) : "memory");
+}
+__device__ __forceinline__ float lds16(uint32_t addr) {
+  unsigned short u;
+  asm volatile("ld.shared.b16 %0, [%1];" : "=h"(u) : "r"(addr));
+  return __uint_as_float((uint32_t)u << 16);
+}
+
+// mask of the positions this thread gates: ocol = q0 + 32 half + lane
+__device__ __forceinline__ void load_mask(const float *mask, int R, int orow, int q0, int incoming, float (&mk)[2]) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int half = 0; half < 2; ++half) {
+    const int ocol = q0 + 32 * half + lane;
+    mk[half] = 0.f;
+    if (ocol < R) mk[half] = mask[incoming ? (int64_t)ocol * R + orow : (int64_t)orow * R + ocol];
+  }
+}
+
+__device__ __forceinline__ void load_abg(const CUtensorMap *tm, uint32_t tiles, int cm, int c0, int q0, int orow,
+                                         int incoming, uint64_t *bar) {
+#pragma unroll
+  for (int s = 0; s < 4; ++s) {
+    if (incoming) tma_load_3d(tiles + s * TT_TILE, tm, s * cm + c0, orow, q0, bar);
+    else tma_load_3d(tiles + s * TT_TILE, tm, s * cm + c0, q0, orow, bar);
+  }
+}
+
+// grid (ceil(R / 64), R, cm / 64): tile of ocol q0 .. q0 + 63 of row orow,
+// channels c0 .. c0 + 63
+__global__ void __launch_bounds__(256) trimul_gate_fwd_tma(const __grid_constant__ CUtensorMap tm_abg,
+                                                           const __grid_constant__ CUtensorMap tm_A,
+                                                           const __grid_constant__ CUtensorMap tm_B,
+                                                           const float *mask, int R, int cm, int incoming) {
+  extern __shared__ uint8_t dsm[];
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ volatile int s_abort;
+  const uint32_t base = (smem_u32(dsm) + 1023u) & ~1023u;
+  const uint32_t in = base, outA = base + 4 * TT_TILE, outB = outA + TT_TILE;
+  const int q0 = blockIdx.x * TT_Q, orow = blockIdx.y, c0 = blockIdx.z * TT_C;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    s_abort = 0;
+    fence_mbar_init();
+  }
+  __syncthreads();
+  pdl_entry();  // abg is the previous kernel's output
+  if (threadIdx.x == 0) {
+    mbar_arrive_expect_tx(&bar, 4 * TT_TILE);
+    load_abg(&tm_abg, in, cm, c0, q0, orow, incoming, &bar);
+  }
+  float mk[2];
+  load_mask(mask, R, orow, q0, incoming, mk);
+  const bool ok = __syncthreads_and(mbar_wait(&bar, 0, &s_abort));
+  if (!ok) {
+    if (threadIdx.x == 0) mbar_drain(&bar, 0);
+    return;
+  }
+  // items: (a or b, half, 8-channel chunk); a warp takes four
+#pragma unroll
+  for (int it = 0; it < 4; ++it) {
+    const int item = warp + 8 * it;
+    const int ab = item >> 4, half = (item >> 3) & 1, chunk = item & 7;
+    const int r = 32 * half + lane;
+    float p[8], g[8];
+    lds8(in + (2 * ab) * TT_TILE + sw128(r, chunk), p);
+    lds8(in + (2 * ab + 1) * TT_TILE + sw128(r, chunk), g);
+    const uint32_t out = ab ? outB : outA;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const int c = chunk * 8 + k;
+      sts16(out + sw128(c, r >> 3) + (r & 7) * 2, mk[half] * p[k] * sigm_tc(g[k]));
+    }
+  }
+  fence_proxy_async();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    tma_store_3d(&tm_A, outA, q0, orow, c0);
+    tma_store_3d(&tm_B, outB, q0, orow, c0);
+    bulk_commit();
+    bulk_wait_read_all();
+  }
+}
+
+// Backward: d ap = dA mask sigmoid(ag); d ag = dA mask ap sigmoid'(ag) (and b
+// likewise), written over the abg tiles and stored to dabg.
+__global__ void __launch_bounds__(256) trimul_gate_bwd_tma(const __grid_constant__ CUtensorMap tm_abg,
+                                                           const __grid_constant__ CUtensorMap tm_dA,
+                                                           const __grid_constant__ CUtensorMap tm_dB,
+                                                           const __grid_constant__ CUtensorMap tm_dabg,
+                                                           const float *mask, int R, int cm, int incoming) {
+  extern __shared__ uint8_t dsm[];
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ volatile int s_abort;
+  const uint32_t base = (smem_u32(dsm) + 1023u) & ~1023u;
+  const uint32_t in = base, dAt = base + 4 * TT_TILE, dBt = dAt + TT_TILE;
+  const int q0 = blockIdx.x * TT_Q, orow = blockIdx.y, c0 = blockIdx.z * TT_C;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    s_abort = 0;
+    fence_mbar_init();
+  }
+  __syncthreads();
+  pdl_entry();
+  if (threadIdx.x == 0) {
+    mbar_arrive_expect_tx(&bar, 6 * TT_TILE);
+    load_abg(&tm_abg, in, cm, c0, q0, orow, incoming, &bar);
+    tma_load_3d(dAt, &tm_dA, q0, orow, c0, &bar);
+    tma_load_3d(dBt, &tm_dB, q0, orow, c0, &bar);
+  }
+  float mk[2];
+  load_mask(mask, R, orow, q0, incoming, mk);
+  const bool ok = __syncthreads_and(mbar_wait(&bar, 0, &s_abort));
+  if (!ok) {
+    if (threadIdx.x == 0) mbar_drain(&bar, 0);
+    return;
+  }
+#pragma unroll
+  for (int it = 0; it < 4; ++it) {
+    const int item = warp + 8 * it;
+    const int ab = item >> 4, half = (item >> 3) & 1, chunk = item & 7;
+    const int r = 32 * half + lane;
+    const uint32_t pa = in + (2 * ab) * TT_TILE + sw128(r, chunk), ga = in + (2 * ab + 1) * TT_TILE + sw128(r, chunk);
+    float p[8], g[8], dp[8], dg[8];
+    lds8(pa, p);
+    lds8(ga, g);
+    const uint32_t dt = ab ? dBt : dAt;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const int c = chunk * 8 + k;
+      const float d = lds16(dt + sw128(c, r >> 3) + (r & 7) * 2) * mk[half];
+      const float sg = sigm_tc(g[k]);
+      dp[k] = d * sg;
+      dg[k] = d * p[k] * sg * (1.f - sg);
+    }
+    sts8(pa, dp);
+    sts8(ga, dg);
+  }
+  fence_proxy_async();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+      if (incoming) tma_store_3d(&tm_dabg, in + s * TT_TILE, s * cm + c0, orow, q0);
+      else tma_store_3d(&tm_dabg, in + s * TT_TILE, s * cm + c0, q0, orow);
+    }
+    bulk_commit();
+    bulk_wait_read_all();
+  }
+}
+
+// abg-like map: channels [0, 4 cm) of rows of ld elements, positions in
+// stride order (outgoing: ocol then orow; incoming: orow then ocol)
+bool map_abg(CUtensorMap *tm, const void *p, int64_t ld, int R, int cm, int incoming) {
+  const uint64_t dims[3] = {(uint64_t)4 * cm, (uint64_t)R, (uint64_t)R};
+  const uint64_t st[2] = {(uint64_t)ld * 2, (uint64_t)R * ld * 2};
+  const uint32_t box[3] = {TT_C, incoming ? 1u : (uint32_t)TT_Q, incoming ? (uint32_t)TT_Q : 1u};
+  return make_tmap_nd(tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, p, dims, st, box, CU_TENSOR_MAP_SWIZZLE_128B);
+}
+// channel-major map: [c][orow][ocol] with row pitch, ocol clipped at R
+bool map_cm(CUtensorMap *tm, const void *p, int64_t pitch, int R, int cm) {
+  const uint64_t dims[3] = {(uint64_t)R, (uint64_t)R, (uint64_t)cm};
+  const uint64_t st[2] = {(uint64_t)pitch * 2, (uint64_t)R * pitch * 2};
+  const uint32_t box[3] = {TT_Q, 1, TT_C};
+  return make_tmap_nd(tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, p, dims, st, box, CU_TENSOR_MAP_SWIZZLE_128B);
+}
+
+bool a16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
+
+}  // namespace
+
+bool trimul_gate_tma_supported(const void *abg, int64_t ld, const void *A, const void *B, int64_t pitch, int R,
+                               int cm) {
+  return R > 0 && cm % TT_C == 0 && ld % 8 == 0 && pitch % 8 == 0 && a16(abg) && a16(A) && a16(B);
+}
+
+cudaError_t trimul_gate_fwd_tma_launch(const void *abg, int64_t ld, const float *mask, void *A, void *B, int64_t pitch,
+                                       int R, int cm, int incoming, cudaStream_t s) {
+  CUtensorMap ta, tA, tB;
+  if (!map_abg(&ta, abg, ld, R, cm, incoming) || !map_cm(&tA, A, pitch, R, cm) || !map_cm(&tB, B, pitch, R, cm))
+    return cudaErrorNotSupported;
+  const int smem = 6 * TT_TILE + 1024;
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(trimul_gate_fwd_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  const dim3 grid((R + TT_Q - 1) / TT_Q, R, cm / TT_C);
+  return launch_k(trimul_gate_fwd_tma, grid, 256, smem, s, ta, tA, tB, mask, R, cm, incoming);
+}
+
+cudaError_t trimul_gate_bwd_tma_launch(const void *dA, const void *dB, int64_t pitch, const void *abg, int64_t ld,
+                                       const float *mask, void *dabg, int R, int cm, int incoming, cudaStream_t s) {
+  CUtensorMap ta, tdA, tdB, tdabg;
+  if (!map_abg(&ta, abg, ld, R, cm, incoming) || !map_cm(&tdA, dA, pitch, R, cm) ||
+      !map_cm(&tdB, dB, pitch, R, cm) || !map_abg(&tdabg, dabg, ld, R, cm, incoming))
+    return cudaErrorNotSupported;
+  const int smem = 6 * TT_TILE + 1024;
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(trimul_gate_bwd_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  const dim3 grid((R + TT_Q - 1) / TT_Q, R, cm / TT_C);
+  return launch_k(trimul_gate_bwd_tma, grid, 256, smem, s, ta, tdA, tdB, tdabg, mask, R, cm, incoming);
+}
+
+cudaError_t trimul_tc_error_read_clear(int *out) {
+  int zero = 0;
+  cudaError_t e = cudaMemcpyFromSymbol(out, tc_error_word, sizeof(int));
+  if (e != cudaSuccess) return e;
+  return cudaMemcpyToSymbol(tc_error_word, &zero, sizeof(int));
+}
+
+}  // namespace evo
