@@ -668,6 +668,10 @@ cudaError_t ln_fwd_cm(const void *x, int64_t pitch, const float *gamma, const fl
                       int use_bf16, cudaStream_t s) {
   if (R <= 0) return cudaSuccess;
   Prof p("ln_fwd_cm", s, 0, (use_bf16 ? 4.0 : 8.0) * R * (double)R * C);
+  if (use_bf16 && ln_cm_tma_supported(x, pitch, y, R, C)) {
+    const cudaError_t e = ln_fwd_cm_tma_launch(x, pitch, gamma, beta, y, R, C, s);
+    if (e != cudaErrorNotSupported) return e;
+  }
   dim3 grid((R + 31) / 32, R);
   auto a16 = [](const void *q) { return ((uintptr_t)q & 15u) == 0; };
   if (pitch % 8 == 0 && C % 8 == 0 && a16(x) && a16(y)) {
@@ -725,6 +729,10 @@ cudaError_t ln_bwd_cm(const void *dy, const void *x, int64_t pitch, const float 
                       int C, int use_bf16, cudaStream_t s, float *dgamma, float *dbeta) {
   if (R <= 0) return cudaSuccess;
   Prof p("ln_bwd_cm", s, 0, (use_bf16 ? 6.0 : 12.0) * R * (double)R * C);
+  if (use_bf16 && ln_cm_tma_supported(x, pitch, dx, R, C) && (((uintptr_t)dy) & 15u) == 0) {
+    const cudaError_t e = ln_bwd_cm_tma_launch(dy, x, pitch, gamma, dx, R, C, dgamma, dbeta, s);
+    if (e != cudaErrorNotSupported) return e;
+  }
   dim3 grid((R + 31) / 32, R);
   auto a16 = [](const void *q) { return ((uintptr_t)q & 15u) == 0; };
   if (pitch % 8 == 0 && C % 8 == 0 && a16(x) && a16(dy) && a16(dx)) {

@@ -902,6 +902,46 @@ __global__ void gate_out_bwd_k(const T *dz, const T *g, int64_t g_ld, const T *y
   stf(dgpre + p * dg_ld + c, d * yv * gv * (1.f - gv));
 }
 
+// bf16, C = 8k: eight channels per thread with 16-byte accesses, two groups
+// of loads in flight per thread
+__global__ void __launch_bounds__(256) gate_out_bwd_v8(const bf16 *dz, const bf16 *g, int64_t g_ld, const bf16 *y,
+                                                       bf16 *dy, bf16 *dgpre, int64_t dg_ld, int64_t P, int C) {
+  pdl_entry();
+  const int cq = C / 8;
+  const int64_t n = P * cq;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += 2 * stride) {
+    float d[2][8], gv[2][8], yv[2][8];
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const int64_t e = i + u * stride;
+      if (e < n) {
+        const int64_t p = e / cq;
+        const int c = (int)(e - p * cq) * 8;
+        ld8(dz + p * C + c, d[u]);
+        ld8(g + p * g_ld + c, gv[u]);
+        ld8(y + p * C + c, yv[u]);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const int64_t e = i + u * stride;
+      if (e < n) {
+        const int64_t p = e / cq;
+        const int c = (int)(e - p * cq) * 8;
+        float a[8], b[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          a[k] = d[u][k] * gv[u][k];
+          b[k] = d[u][k] * yv[u][k] * gv[u][k] * (1.f - gv[u][k]);
+        }
+        st8(dy + p * C + c, a);
+        st8(dgpre + p * dg_ld + c, b);
+      }
+    }
+  }
+}
+
 // ------------------------------------------------------------ attention gate
 template <typename T>
 __global__ void attn_gate_bwd_k(AttnArgs a, const T *dog, T *dgpre, int64_t sGb_d, int64_t sGx_d, T *do_att,
@@ -1204,7 +1244,14 @@ cudaError_t trimul_gate_bwd(const void *dA, const void *dB, int64_t pitch, const
 cudaError_t gate_out_bwd(const void *dz, const void *g, int64_t g_ld, const void *y, void *dy, void *dgpre,
                          int64_t dg_ld, int64_t P, int C, int use_bf16, cudaStream_t s) {
   Prof prof("gate_out_bwd", s, 0, (use_bf16 ? 2.0 : 4.0) * (double)P * C * 5, 1);
-  if (use_bf16)
+  auto a16 = [](const void *q) { return ((uintptr_t)q & 15u) == 0; };
+  if (use_bf16 && C % 8 == 0 && g_ld % 8 == 0 && dg_ld % 8 == 0 && a16(dz) && a16(g) && a16(y) && a16(dy) &&
+      a16(dgpre)) {
+    const int64_t n = P * (C / 8);
+    const unsigned blocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 511) / 512, 152 * 8));
+    launch_k(gate_out_bwd_v8, blocks, 256, 0, s, (const bf16 *)dz, (const bf16 *)g, g_ld, (const bf16 *)y, (bf16 *)dy,
+             (bf16 *)dgpre, dg_ld, P, C);
+  } else if (use_bf16)
     launch_k(gate_out_bwd_k<bf16>, nblk(P * C), 256, 0, s, (const bf16 *)dz, (const bf16 *)g, g_ld, (const bf16 *)y,
                                                      (bf16 *)dy, (bf16 *)dgpre, dg_ld, P, C);
   else

@@ -210,6 +210,189 @@ __global__ void __launch_bounds__(256) trimul_gate_bwd_tma(const __grid_constant
   }
 }
 
+// ---------------------------------------------------------------------------
+// LayerNorm of the triangle-multiplication product (Alg. 11 and 12, the
+// LayerNorm before the output projection), channel-major in, row-major out:
+// one CTA per 64 positions j of a row i, all C channels (C / 64 tiles of
+// [64 c][64 j] in, [64 j][64 c] out, each 8 KB, 128-byte swizzled).
+constexpr int LN_MAXC = 256;
+constexpr float LNC_EPS = 1e-5f;
+
+// mean and rstd of the 64 positions of the channel-major tiles (256 threads:
+// position t % 64, channel quarter t / 64); red holds 4 x 64 floats
+__device__ __forceinline__ void cm_tile_stats(uint32_t xin, int C, float *red, float *mu, float *rs) {
+  const int t = threadIdx.x, j = t & 63, qt = t >> 6, cpq = C / 4;
+  float sum = 0.f;
+  for (int c = qt * cpq; c < (qt + 1) * cpq; ++c) sum += lds16(xin + (c >> 6) * TT_TILE + sw128(c & 63, j >> 3) + (j & 7) * 2);
+  red[qt * 64 + j] = sum;
+  __syncthreads();
+  if (t < 64) mu[t] = (red[t] + red[64 + t] + red[128 + t] + red[192 + t]) / C;
+  __syncthreads();
+  const float m = mu[j];
+  float q = 0.f;
+  for (int c = qt * cpq; c < (qt + 1) * cpq; ++c) {
+    const float d = lds16(xin + (c >> 6) * TT_TILE + sw128(c & 63, j >> 3) + (j & 7) * 2) - m;
+    q += d * d;
+  }
+  red[qt * 64 + j] = q;
+  __syncthreads();
+  if (t < 64) rs[t] = rsqrtf((red[t] + red[64 + t] + red[128 + t] + red[192 + t]) / C + LNC_EPS);
+  __syncthreads();
+}
+
+// grid (ceil(R / 64), R)
+__global__ void __launch_bounds__(256) ln_fwd_cm_tma(const __grid_constant__ CUtensorMap tm_x,
+                                                     const __grid_constant__ CUtensorMap tm_y, const float *gamma,
+                                                     const float *beta, int C) {
+  extern __shared__ uint8_t dsm[];
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ volatile int s_abort;
+  __shared__ float red[256], mu[64], rs[64], gs[LN_MAXC], bs[LN_MAXC];
+  const uint32_t base = (smem_u32(dsm) + 1023u) & ~1023u;
+  const int nt = C / 64;
+  const uint32_t xin = base, yout = base + nt * TT_TILE;
+  const int j0 = blockIdx.x * 64, i = blockIdx.y;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    s_abort = 0;
+    fence_mbar_init();
+  }
+  __syncthreads();
+  pdl_entry();
+  if (threadIdx.x == 0) {
+    mbar_arrive_expect_tx(&bar, nt * TT_TILE);
+    for (int c = 0; c < nt; ++c) tma_load_3d(xin + c * TT_TILE, &tm_x, j0, i, 64 * c, &bar);
+  }
+  for (int c = threadIdx.x; c < C; c += blockDim.x) gs[c] = gamma[c], bs[c] = beta[c];
+  const bool ok = __syncthreads_and(mbar_wait(&bar, 0, &s_abort));
+  if (!ok) {
+    if (threadIdx.x == 0) mbar_drain(&bar, 0);
+    return;
+  }
+  cm_tile_stats(xin, C, red, mu, rs);
+  // item (position j, 8-channel chunk q): lanes take consecutive j
+  for (int item = threadIdx.x; item < 64 * (C / 8); item += blockDim.x) {
+    const int j = item & 63, q = item >> 6;
+    float o[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const int c = q * 8 + k;
+      const float x = lds16(xin + (c >> 6) * TT_TILE + sw128(c & 63, j >> 3) + (j & 7) * 2);
+      o[k] = (x - mu[j]) * rs[j] * gs[c] + bs[c];
+    }
+    sts8(yout + (q >> 3) * TT_TILE + sw128(j, q & 7), o);
+  }
+  fence_proxy_async();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int c = 0; c < nt; ++c) tma_store_3d(&tm_y, yout + c * TT_TILE, 64 * c, j0, i);
+    bulk_commit();
+    bulk_wait_read_all();
+  }
+}
+
+// Backward: dy row-major tiles [64 j][64 c], x channel-major; dx channel-major
+// (written over the x tiles), gamma / beta gradients by fp32 atomics.
+__global__ void __launch_bounds__(256) ln_bwd_cm_tma(const __grid_constant__ CUtensorMap tm_x,
+                                                     const __grid_constant__ CUtensorMap tm_dy,
+                                                     const __grid_constant__ CUtensorMap tm_dx, const float *gamma,
+                                                     int C, float *dgamma, float *dbeta) {
+  extern __shared__ uint8_t dsm[];
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ volatile int s_abort;
+  __shared__ float red[256], red2[512], mu[64], rs[64], a1[64], a2[64], gs[LN_MAXC];
+  const uint32_t base = (smem_u32(dsm) + 1023u) & ~1023u;
+  const int nt = C / 64;
+  const uint32_t xin = base, dyin = base + nt * TT_TILE;
+  const int j0 = blockIdx.x * 64, i = blockIdx.y;
+  const int t = threadIdx.x, j = t & 63, qt = t >> 6, cpq = C / 4;
+  if (t == 0) {
+    mbar_init(&bar, 1);
+    s_abort = 0;
+    fence_mbar_init();
+  }
+  __syncthreads();
+  pdl_entry();
+  if (t == 0) {
+    mbar_arrive_expect_tx(&bar, 2 * nt * TT_TILE);
+    for (int c = 0; c < nt; ++c) {
+      tma_load_3d(xin + c * TT_TILE, &tm_x, j0, i, 64 * c, &bar);
+      tma_load_3d(dyin + c * TT_TILE, &tm_dy, 64 * c, j0, i, &bar);
+    }
+  }
+  for (int c = t; c < C; c += blockDim.x) gs[c] = gamma[c];
+  const bool ok = __syncthreads_and(mbar_wait(&bar, 0, &s_abort));
+  if (!ok) {
+    if (t == 0) mbar_drain(&bar, 0);
+    return;
+  }
+  cm_tile_stats(xin, C, red, mu, rs);
+  auto xat = [&](int c, int jj) { return lds16(xin + (c >> 6) * TT_TILE + sw128(c & 63, jj >> 3) + (jj & 7) * 2); };
+  auto dyat = [&](int c, int jj) {
+    return lds16(dyin + (c >> 6) * TT_TILE + sw128(jj, (c & 63) >> 3) + (c & 7) * 2);
+  };
+  // a1 = mean_c(dy gamma), a2 = mean_c(dy gamma xhat) per position
+  {
+    const float m = mu[j], r = rs[j];
+    float s1 = 0.f, s2 = 0.f;
+    for (int c = qt * cpq; c < (qt + 1) * cpq; ++c) {
+      const float gd = dyat(c, j) * gs[c];
+      s1 += gd;
+      s2 += gd * (xat(c, j) - m) * r;
+    }
+    red[qt * 64 + j] = s1;
+    __syncthreads();
+    if (t < 64) a1[t] = (red[t] + red[64 + t] + red[128 + t] + red[192 + t]) / C;
+    __syncthreads();
+    red[qt * 64 + j] = s2;
+    __syncthreads();
+    if (t < 64) a2[t] = (red[t] + red[64 + t] + red[128 + t] + red[192 + t]) / C;
+    __syncthreads();
+  }
+  // gamma / beta gradients: 256 / C threads per channel, each over a slice of
+  // the tile's positions, combined in shared memory (red2: 2 x 256 floats)
+  {
+    const int tpc = 256 / C, c = t % C, part = t / C, per = 64 / tpc;
+    float sg = 0.f, sb = 0.f;
+    for (int jj = part * per; jj < (part + 1) * per; ++jj) {
+      const float d = dyat(c, jj);
+      sg += d * (xat(c, jj) - mu[jj]) * rs[jj];
+      sb += d;
+    }
+    red2[t] = sg;
+    red2[256 + t] = sb;
+    __syncthreads();
+    if (t < C) {
+      float g = 0.f, b = 0.f;
+      for (int k = 0; k < tpc; ++k) g += red2[k * C + t], b += red2[256 + k * C + t];
+      atomicAdd(dgamma + t, g);
+      atomicAdd(dbeta + t, b);
+    }
+  }
+  __syncthreads();  // every read of x is done before dx overwrites it
+  for (int e = t; e < 64 * C; e += blockDim.x) {
+    const int jj = e & 63, c = e >> 6;
+    const uint32_t a = xin + (c >> 6) * TT_TILE + sw128(c & 63, jj >> 3) + (jj & 7) * 2;
+    const float xh = (lds16(a) - mu[jj]) * rs[jj];
+    sts16(a, rs[jj] * (dyat(c, jj) * gs[c] - a1[jj] - xh * a2[jj]));
+  }
+  fence_proxy_async();
+  __syncthreads();
+  if (t == 0) {
+    for (int c = 0; c < nt; ++c) tma_store_3d(&tm_dx, xin + c * TT_TILE, j0, i, 64 * c);
+    bulk_commit();
+    bulk_wait_read_all();
+  }
+}
+
+// row-major [R][R][C] map, boxes of 64 channels x 64 positions j
+bool map_rows(CUtensorMap *tm, const void *p, int R, int C) {
+  const uint64_t dims[3] = {(uint64_t)C, (uint64_t)R, (uint64_t)R};
+  const uint64_t st[2] = {(uint64_t)C * 2, (uint64_t)R * C * 2};
+  const uint32_t box[3] = {64, 64, 1};
+  return make_tmap_nd(tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, p, dims, st, box, CU_TENSOR_MAP_SWIZZLE_128B);
+}
+
 // abg-like map: channels [0, 4 cm) of rows of ld elements, positions in
 // stride order (outgoing: ocol then orow; incoming: orow then ocol)
 bool map_abg(CUtensorMap *tm, const void *p, int64_t ld, int R, int cm, int incoming) {
@@ -266,6 +449,39 @@ cudaError_t trimul_gate_bwd_tma_launch(const void *dA, const void *dB, int64_t p
   }
   const dim3 grid((R + TT_Q - 1) / TT_Q, R, cm / TT_C);
   return launch_k(trimul_gate_bwd_tma, grid, 256, smem, s, ta, tdA, tdB, tdabg, mask, R, cm, incoming);
+}
+
+bool ln_cm_tma_supported(const void *x, int64_t pitch, const void *y, int R, int C) {
+  return R > 0 && C % 64 == 0 && C <= LN_MAXC && pitch % 8 == 0 && a16(x) && a16(y);
+}
+
+cudaError_t ln_fwd_cm_tma_launch(const void *x, int64_t pitch, const float *gamma, const float *beta, void *y, int R,
+                                 int C, cudaStream_t s) {
+  CUtensorMap tx, ty;
+  if (!map_cm(&tx, x, pitch, R, C) || !map_rows(&ty, y, R, C)) return cudaErrorNotSupported;
+  const int smem = 2 * (C / 64) * TT_TILE + 1024;
+  static int attr = 0;
+  if (attr < smem) {
+    cudaError_t e = cudaFuncSetAttribute(ln_fwd_cm_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    attr = smem;
+  }
+  return launch_k(ln_fwd_cm_tma, dim3((R + 63) / 64, R), 256, smem, s, tx, ty, gamma, beta, C);
+}
+
+cudaError_t ln_bwd_cm_tma_launch(const void *dy, const void *x, int64_t pitch, const float *gamma, void *dx, int R,
+                                 int C, float *dgamma, float *dbeta, cudaStream_t s) {
+  CUtensorMap tx, tdy, tdx;
+  if (!map_cm(&tx, x, pitch, R, C) || !map_rows(&tdy, dy, R, C) || !map_cm(&tdx, dx, pitch, R, C))
+    return cudaErrorNotSupported;
+  const int smem = 2 * (C / 64) * TT_TILE + 1024;
+  static int attr = 0;
+  if (attr < smem) {
+    cudaError_t e = cudaFuncSetAttribute(ln_bwd_cm_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    attr = smem;
+  }
+  return launch_k(ln_bwd_cm_tma, dim3((R + 63) / 64, R), 256, smem, s, tx, tdy, tdx, gamma, C, dgamma, dbeta);
 }
 
 cudaError_t trimul_tc_error_read_clear(int *out) {
