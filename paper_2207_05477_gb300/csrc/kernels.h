@@ -167,8 +167,8 @@ cudaError_t trimul_gate_fwd_tma_launch(const void *abg, int64_t ld, const float 
                                        int R, int cm, int incoming, cudaStream_t s);
 cudaError_t trimul_gate_bwd_tma_launch(const void *dA, const void *dB, int64_t pitch, const void *abg, int64_t ld,
                                        const float *mask, void *dabg, int R, int cm, int incoming, cudaStream_t s);
-// TMA-tiled BF16 versions of ln_fwd_cm / ln_bwd_cm (C a multiple of 64, at
-// most 256); cudaErrorNotSupported (nothing launched) as above.
+// TMA-tiled BF16 versions of ln_fwd_cm / ln_bwd_cm (C = 64, 128 or 256);
+// cudaErrorNotSupported (nothing launched) as above.
 bool ln_cm_tma_supported(const void *x, int64_t pitch, const void *y, int R, int C);
 cudaError_t ln_fwd_cm_tma_launch(const void *x, int64_t pitch, const float *gamma, const float *beta, void *y, int R,
                                  int C, cudaStream_t s);

@@ -452,7 +452,7 @@ cudaError_t trimul_gate_bwd_tma_launch(const void *dA, const void *dB, int64_t p
 }
 
 bool ln_cm_tma_supported(const void *x, int64_t pitch, const void *y, int R, int C) {
-  return R > 0 && C % 64 == 0 && C <= LN_MAXC && pitch % 8 == 0 && a16(x) && a16(y);
+  return R > 0 && (C == 64 || C == 128 || C == 256) && pitch % 8 == 0 && a16(x) && a16(y);
 }
 
 cudaError_t ln_fwd_cm_tma_launch(const void *x, int64_t pitch, const float *gamma, const float *beta, void *y, int R,
