@@ -339,6 +339,119 @@ __global__ void __launch_bounds__(256) ln_fwd_rows_v8(const T *x, const float *g
   }
 }
 
+// Row LayerNorm backward, C in {64, 128, 256}, eight channels per lane as in
+// ln_fwd_rows_v8 (U warp-steps of loads in flight).  dacc (fp32) becomes
+// (dinit or dacc) + dx and dcopy its activation-type copy, or dx_out = dx;
+// the gamma / beta partial sums stay in registers (fixed channel slice per
+// lane) and leave through one atomic add per channel and block.
+__device__ __forceinline__ void ld8f(const float *p, float (&v)[8]) { ld8(p, v); }
+
+template <typename T, int C, int U>
+__global__ void __launch_bounds__(256) ln_bwd_rows_v8(const T *dy, const T *x, const float *gamma, float *dacc,
+                                                      T *dcopy, T *dx_out, const T *dinit, int64_t M, float *dgamma,
+                                                      float *dbeta) {
+  pdl_entry();
+  constexpr int TPR = C / 8, RPW = 32 / TPR;
+  __shared__ float red[8][2 * C];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int sub = lane % TPR, rw = lane / TPR, c0 = sub * 8;
+  float g[8], ag[8], ab[8];
+  ld8f(gamma + c0, g);
+#pragma unroll
+  for (int k = 0; k < 8; ++k) ag[k] = ab[k] = 0.f;
+  const int64_t nwarps = (int64_t)gridDim.x * 8;
+  const int64_t w0 = (int64_t)blockIdx.x * 8 + warp;
+  for (int64_t base = w0 * (RPW * U); base < M; base += nwarps * (RPW * U)) {
+    float xv[U][8], gv[U][8], av[U][8];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t row = base + u * RPW + rw;
+      if (row < M) {
+        ld8(x + row * C + c0, xv[u]);
+        ld8(dy + row * C + c0, gv[u]);
+        if (dinit) {
+          ld8(dinit + row * C + c0, av[u]);
+        } else if (dacc) {
+          ld8f(dacc + row * C + c0, av[u]);
+        } else {
+#pragma unroll
+          for (int k = 0; k < 8; ++k) av[u][k] = 0.f;
+        }
+      } else {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) xv[u][k] = gv[u][k] = av[u][k] = 0.f;
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t row = base + u * RPW + rw;
+      float s = 0.f;
+#pragma unroll
+      for (int k = 0; k < 8; ++k) s += xv[u][k];
+#pragma unroll
+      for (int o = TPR / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      const float mu = s * (1.f / C);
+      float q = 0.f;
+#pragma unroll
+      for (int k = 0; k < 8; ++k) q += (xv[u][k] - mu) * (xv[u][k] - mu);
+#pragma unroll
+      for (int o = TPR / 2; o > 0; o >>= 1) q += __shfl_xor_sync(0xffffffffu, q, o);
+      const float rstd = rsqrtf(q * (1.f / C) + LN_EPS);
+      float a1 = 0.f, a2 = 0.f;
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        const float xh = (xv[u][k] - mu) * rstd;
+        xv[u][k] = xh;
+        const float d = gv[u][k] * g[k];
+        a1 += d;
+        a2 += d * xh;
+        ag[k] += gv[u][k] * xh;
+        ab[k] += gv[u][k];
+      }
+#pragma unroll
+      for (int o = TPR / 2; o > 0; o >>= 1) {
+        a1 += __shfl_xor_sync(0xffffffffu, a1, o);
+        a2 += __shfl_xor_sync(0xffffffffu, a2, o);
+      }
+      a1 *= 1.f / C;
+      a2 *= 1.f / C;
+      if (row >= M) continue;
+      float dx[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) dx[k] = rstd * (gv[u][k] * g[k] - a1 - xv[u][k] * a2);
+      if (dacc) {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) dx[k] += av[u][k];
+        st8(dacc + row * C + c0, dx);
+        if (dcopy) st8(dcopy + row * C + c0, dx);
+      } else {
+        st8(dx_out + row * C + c0, dx);
+      }
+    }
+  }
+  // lanes with the same channel slice: sum over the warp's row groups, then
+  // over the block's warps
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+#pragma unroll
+    for (int o = TPR; o < 32; o <<= 1) {
+      ag[k] += __shfl_xor_sync(0xffffffffu, ag[k], o);
+      ab[k] += __shfl_xor_sync(0xffffffffu, ab[k], o);
+    }
+  }
+  if (rw == 0) {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) red[warp][c0 + k] = ag[k], red[warp][C + c0 + k] = ab[k];
+  }
+  __syncthreads();
+  for (int cc = threadIdx.x; cc < 2 * C; cc += blockDim.x) {
+    float t = 0.f;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) t += red[w][cc];
+    atomicAdd(cc < C ? dgamma + cc : dbeta + cc - C, t);
+  }
+}
+
 // Channel-major LayerNorm of the triangle-multiplication output x[c][i][pitch]
 // (pitch a multiple of 8): one block per 32 positions j of a row i.  The
 // C x 32 tile comes in with 16-byte loads (8 positions per thread) into a
@@ -699,6 +812,31 @@ cudaError_t ln_bwd(const void *dy, const void *x, const float *gamma, float *dac
                    int64_t M, int C, int use_bf16, cudaStream_t s, float *dgamma, float *dbeta, const void *dinit) {
   if (M <= 0) return cudaSuccess;
   Prof p("ln_bwd", s, 0, (use_bf16 ? 2.0 : 4.0) * M * C * (dcopy ? 3 : 2) + (dacc ? 8.0 * M * C : 0.0));
+  {
+    auto a16 = [](const void *q) { return ((uintptr_t)q & 15u) == 0; };
+    const bool al = a16(dy) && a16(x) && a16(gamma) && (!dacc || a16(dacc)) && (!dcopy || a16(dcopy)) &&
+                    (!dx_out || a16(dx_out)) && (!dinit || a16(dinit));
+    if (al && (C == 64 || C == 128 || C == 256)) {
+      constexpr int U = 2;
+      const int64_t rpw = 32 / (C / 8);
+      const int64_t steps = (M + rpw * U - 1) / (rpw * U);
+      const unsigned blocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>((steps + 7) / 8, 152 * 2));
+#define EVO_LN_BWD_V8(CC)                                                                                        \
+  if (C == CC) {                                                                                                 \
+    if (use_bf16)                                                                                                \
+      launch_k(ln_bwd_rows_v8<bf16, CC, U>, blocks, 256, 0, s, (const bf16 *)dy, (const bf16 *)x, gamma, dacc,   \
+               (bf16 *)dcopy, (bf16 *)dx_out, (const bf16 *)dinit, M, dgamma, dbeta);                          \
+    else                                                                                                         \
+      launch_k(ln_bwd_rows_v8<float, CC, U>, blocks, 256, 0, s, (const float *)dy, (const float *)x, gamma, dacc, \
+               (float *)dcopy, (float *)dx_out, (const float *)dinit, M, dgamma, dbeta);                       \
+    return cudaGetLastError();                                                                                   \
+  }
+      EVO_LN_BWD_V8(64)
+      EVO_LN_BWD_V8(128)
+      EVO_LN_BWD_V8(256)
+#undef EVO_LN_BWD_V8
+    }
+  }
   const int nb = ln_bwd_blocks(M);
   const int64_t rpb = (M + nb - 1) / nb;
 #define EVO_LN_BWD_VEC(P, NR)                                                                                    \

@@ -22,6 +22,9 @@ where those cannot hold, from the arithmetic:
     independent roundings add in quadrature (amplitude x4) and the flip error
     grows as the square root of the amplitude: x2.
 """
+import json
+import os
+
 import pytest
 
 from helpers import gpu_run, oracle_bf16_floor, oracle_fwd, oracle_fwd_bwd, param_grad_errors, rel_l2
@@ -136,7 +139,15 @@ def test_extra_msa_bf16_fwd_bwd(built_lib):
 
 @pytest.mark.slow
 def test_extra_msa_bf16_full_size(built_lib):
-    """The paper's initial-training extra-MSA block: N_extra_seq=1024, N_res=256, c_e=64."""
+    """The paper's initial-training extra-MSA block: N_extra_seq=1024, N_res=256, c_e=64.
+
+    The oracle's own BF16 input-rounding floor is about 3 % here for the
+    gradients that pass through the global column attention (col.w_qkvg
+    3.05 %, tests/golden/bf16_floor_extra_msa.json, written by
+    tests/golden/make_bf16_floor.py from the oracle alone), so these bounds
+    take the same floor rule as the small problems."""
     d = synth.DIMS_EXTRA_MSA
     out = gpu_run(d, evo.EVO_BF16, pad_frac=0.05)
-    _check(out, oracle_fwd_bwd(d, pad_frac=0.05), BF16_TOL, BF16_GRAD_TOL, d, RELU_MASKED_TOL)
+    with open(os.path.join(os.path.dirname(__file__), "golden", "bf16_floor_extra_msa.json")) as f:
+        floor = json.load(f)
+    _check(out, oracle_fwd_bwd(d, pad_frac=0.05), BF16_TOL, BF16_GRAD_TOL, d, RELU_MASKED_TOL, floor)
