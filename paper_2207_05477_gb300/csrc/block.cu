@@ -315,9 +315,12 @@ struct Drv {
   void db(const void *dY, int64_t ldY, int64_t rows, int64_t N, const std::string &b) {
     ck(colsum(dY, ldY, rows, (int)N, bf, s, D(b)));
   }
+  // next_db: the bias gradient of the layer that consumes this gradient next
+  // (the column sums of the updated accumulator, fused into the kernel)
   void lnb(const void *dy, const void *x, const std::string &pre, float *dacc, void *dcopy, void *dx_out, int64_t M,
-           int C, const void *dinit = nullptr) {
-    ck(ln_bwd(dy, x, P(pre + ".gamma"), dacc, dcopy, dx_out, M, C, bf, s, D(pre + ".gamma"), D(pre + ".beta"), dinit));
+           int C, const void *dinit = nullptr, float *next_db = nullptr) {
+    ck(ln_bwd(dy, x, P(pre + ".gamma"), dacc, dcopy, dx_out, M, C, bf, s, D(pre + ".gamma"), D(pre + ".beta"), dinit,
+              next_db));
   }
 
   // ---------------- attention argument sets
@@ -494,11 +497,14 @@ struct Drv {
   // dT: the incoming gradient (activation type); dcopy receives the updated
   // running gradient (dT itself unless the incoming one must stay intact);
   // dinit: start the fp32 accumulator from this tensor instead of its contents.
+  // b2_done: the b2 gradient (column sums of dT) was added by the kernel that
+  // wrote dT; next_db as in lnb.
   void transition_bwd(const std::string &pre, const void *x, const void *xn, const void *h, float *dacc,
-                      const void *dT, void *dcopy, int64_t M, int64_t C, const void *dinit = nullptr) {
+                      const void *dT, void *dcopy, int64_t M, int64_t C, const void *dinit = nullptr,
+                      bool b2_done = false, float *next_db = nullptr) {
     const int64_t nC = k.n * C;
     dW(dT, C, C, h, nC, nC, M, pre + ".w2");
-    db(dT, C, M, C, pre + ".b2");
+    if (!b2_done) db(dT, C, M, C, pre + ".b2");
     GemmOp g = mk(M, nC, C, dT, C, 0, W(pre + ".w2"), nC, 1, B(pl.G1), nC);
     g.e.relu_ref = h, g.e.relu_ld = nC;
     gemm(g);
@@ -506,17 +512,19 @@ struct Drv {
     db(B(pl.G1), nC, M, nC, pre + ".b1");
     GemmOp o = mk(M, C, nC, B(pl.G1), nC, 0, W(pre + ".w1"), C, 1, B(pl.G2), C);
     gemm(o);
-    lnb(B(pl.G2), x, pre + ".ln", dacc, dcopy, nullptr, M, (int)C, dinit);
+    lnb(B(pl.G2), x, pre + ".ln", dacc, dcopy, nullptr, M, (int)C, dinit, next_db);
   }
 
   // Gated attention backward down to d(LN input) in G2 (not yet through LayerNorm).
   // Leaves dqkvg in G1 and the pair-bias gradient in dbias (when bias != null).
+  // bo_done: the b_o gradient (column sums of dT) was added by the kernel
+  // that wrote dT.
   void attention_bwd(int kind, const std::string &pre, const void *xn, void *qkvg, void *oatt, void *og, float *lse,
-                     float *bias, const float *mask, const void *dT, int64_t M, int64_t Cin) {
+                     float *bias, const float *mask, const void *dT, int64_t M, int64_t Cin, bool bo_done = false) {
     const bool msa = kind < 2;
     const int64_t HC = msa ? k.HCm : k.HCt, QK = 4 * HC;
     dW(dT, Cin, Cin, og, HC, HC, M, pre + ".w_o");
-    db(dT, Cin, M, Cin, pre + ".b_o");
+    if (!bo_done) db(dT, Cin, M, Cin, pre + ".b_o");
     GemmOp g = mk(M, HC, Cin, dT, Cin, 0, W(pre + ".w_o"), HC, 1, B(pl.G2), HC);
     gemm(g);
     AttnArgs a = attn_args(kind, qkvg, oatt, og, lse, bias, mask);
@@ -546,9 +554,9 @@ struct Drv {
     const std::string pre = t == 0 ? "tri_out" : "tri_in";
     const TriBufs &b = pl.tri[t];
     const int64_t R = k.R, Rp = k.Rp, Cz = k.Cz, Mz = k.Mz, cmul = k.cmul, ABG = k.ABG;
-    ck(gate_out_bwd(dT, at(B(b.abg), 4 * cmul), ABG, B(b.y), B(pl.G2), at(B(pl.G1), 4 * cmul), ABG, Mz, (int)Cz, bf, s));
+    ck(gate_out_bwd(dT, at(B(b.abg), 4 * cmul), ABG, B(b.y), B(pl.G2), at(B(pl.G1), 4 * cmul), ABG, Mz, (int)Cz, bf, s,
+                    D(pre + ".b_o")));
     dW(B(pl.G2), Cz, Cz, B(b.xo), cmul, cmul, Mz, pre + ".w_o");
-    db(B(pl.G2), Cz, Mz, Cz, pre + ".b_o");
     GemmOp g = mk(Mz, cmul, Cz, B(pl.G2), Cz, 0, W(pre + ".w_o"), cmul, 1, B(pl.G3), cmul);
     gemm(g);
     ck(ln_bwd_cm(B(pl.G3), B(b.X), Rp, P(pre + ".ln_out.gamma"), B(pl.dX), (int)R, (int)cmul, bf, s,
@@ -579,24 +587,24 @@ struct Drv {
     void *dmT = B(pl.dmT), *dzT = B(pl.dzT);
 
     // 9. pair transition
-    transition_bwd("pair_trans", B(pl.att[1].zout), B(pl.xz9), B(pl.h9), dz, dz_out, dzT, Mz, Cz, dz_out);
+    transition_bwd("pair_trans", B(pl.att[1].zout), B(pl.xz9), B(pl.h9), dz, dz_out, dzT, Mz, Cz, dz_out, false,
+                   D("att_end.b_o"));
     // 8, 7. triangle attention ending / starting node
     for (int t = 1; t >= 0; --t) {
       const AttBufs &b = pl.att[t];
       const std::string pre = t == 0 ? "att_start" : "att_end";
       const void *zin = t == 0 ? B(pl.tri[1].zout) : B(pl.att[0].zout);
-      attention_bwd(2 + t, pre, B(b.xz), B(b.qkvg), B(b.oatt), B(b.og), Bf(b.lse), Bf(b.bias), pm, dzT, Mz, Cz);
+      attention_bwd(2 + t, pre, B(b.xz), B(b.qkvg), B(b.oatt), B(b.og), Bf(b.lse), Bf(b.bias), pm, dzT, Mz, Cz, true);
       pair_bias_bwd(pre + ".w_b", B(b.xz), (int)k.Ht, t, 1);
-      lnb(B(pl.G2), zin, pre + ".ln", dz, dzT, nullptr, Mz, (int)Cz);
+      lnb(B(pl.G2), zin, pre + ".ln", dz, dzT, nullptr, Mz, (int)Cz, nullptr, t == 1 ? D("att_start.b_o") : nullptr);
     }
     // 6, 5. triangle multiplication incoming / outgoing
     trimul_bwd(1, B(pl.tri[0].zout), pm, dz, dzT);
     trimul_bwd(0, B(pl.z1), pm, dz, dzT);
     // 4. outer product mean
     {
-      ck(row_scale(dzT, Bf(pl.inv4), B(pl.G2), Mz, (int)Cz, bf, s));
+      ck(row_scale(dzT, Bf(pl.inv4), B(pl.G2), Mz, (int)Cz, bf, s, D("opm.b_o")));
       dW(B(pl.G2), Cz, Cz, B(pl.O4), co * co, co * co, Mz, "opm.w_o");
-      db(B(pl.G2), Cz, Mz, Cz, "opm.b_o");
       // dO laid out [i][c][j][d] so both contractions below read it as a plain matrix
       GemmOp g = mk(Mz, co * co, Cz, B(pl.G2), Cz, 0, W("opm.w_o"), co * co, 1, B(pl.dO4), 0);
       g.e.map = OutMap{R, co * R * co, co, co, R * co, 1};
@@ -609,20 +617,18 @@ struct Drv {
       GemmOp gb = mk(S, R * co, R * co, B(pl.ab4), R * co, 0, B(pl.dO4), R * co, 1, at(B(pl.dab4), co), 0);
       gb.e.map = OutMap{1ll << 40, 0, R * 2 * co, co, 2 * co, 1};
       gemm(gb);
-      ck(row_scale(B(pl.dab4), mm, B(pl.dab4), Mm, (int)(2 * co), bf, s));
+      ck(row_scale(B(pl.dab4), mm, B(pl.dab4), Mm, (int)(2 * co), bf, s, D("opm.b_ab")));
       dW(B(pl.dab4), 2 * co, 2 * co, B(pl.xm4), Cm, Cm, Mm, "opm.w_ab");
-      db(B(pl.dab4), 2 * co, Mm, 2 * co, "opm.b_ab");
       GemmOp x = mk(Mm, Cm, 2 * co, B(pl.dab4), 2 * co, 0, W("opm.w_ab"), Cm, 1, B(pl.G2), Cm);
       gemm(x);
-      lnb(B(pl.G2), B(pl.m3), "opm.ln", dm, dmT, nullptr, Mm, (int)Cm, dm_out);
+      lnb(B(pl.G2), B(pl.m3), "opm.ln", dm, dmT, nullptr, Mm, (int)Cm, dm_out, D("msa_trans.b2"));
     }
     // 3. MSA transition
-    transition_bwd("msa_trans", B(pl.m2), B(pl.xm3), B(pl.h3), dm, dmT, dmT, Mm, Cm);
+    transition_bwd("msa_trans", B(pl.m2), B(pl.xm3), B(pl.h3), dm, dmT, dmT, Mm, Cm, nullptr, true, D("col.b_o"));
     // 2. MSA column attention (or global column attention)
     if (d.msa_col_mode == EVO_COL_GLOBAL) {
       const int64_t HC = k.HCm, QK = k.QKc;
-      dW(dmT, Cm, Cm, B(pl.og2), HC, HC, Mm, "col.w_o");
-      db(dmT, Cm, Mm, Cm, "col.b_o");
+      dW(dmT, Cm, Cm, B(pl.og2), HC, HC, Mm, "col.w_o");  // col.b_o: added by the MSA transition's LayerNorm backward
       GemmOp g = mk(Mm, HC, Cm, dmT, Cm, 0, W("col.w_o"), HC, 1, B(pl.G2), HC);
       gemm(g);
       ck(global_attn_bwd(global_args(), B(pl.G2), B(pl.G1), nullptr, bf, s));
@@ -631,12 +637,13 @@ struct Drv {
       GemmOp x = mk(Mm, Cm, QK, B(pl.G1), QK, 0, W("col.w_qkvg"), Cm, 1, B(pl.G2), Cm);
       gemm(x);
     } else {
-      attention_bwd(1, "col", B(pl.xm2), B(pl.qkvg2), B(pl.oatt2), B(pl.og2), Bf(pl.lse2), nullptr, mm, dmT, Mm, Cm);
+      attention_bwd(1, "col", B(pl.xm2), B(pl.qkvg2), B(pl.oatt2), B(pl.og2), Bf(pl.lse2), nullptr, mm, dmT, Mm, Cm,
+                    true);
     }
-    lnb(B(pl.G2), B(pl.m1), "col.ln", dm, dmT, nullptr, Mm, (int)Cm);
+    lnb(B(pl.G2), B(pl.m1), "col.ln", dm, dmT, nullptr, Mm, (int)Cm, nullptr, D("row.b_o"));
     // 1. MSA row attention with pair bias
     attention_bwd(0, "row", B(pl.xm1), B(pl.qkvg1), B(pl.oatt1), B(pl.og1), Bf(pl.lse1), Bf(pl.bias1), mm, dmT, Mm,
-                  Cm);
+                  Cm, true);
     lnb(B(pl.G2), m0, "row.ln_m", dm, dm_in, nullptr, Mm, (int)Cm);
     pair_bias_bwd("row.w_b", B(pl.xz1), (int)k.Hm, 0, 0);
     lnb(B(pl.G2), z0, "row.ln_z", dz, dz_in, nullptr, Mz, (int)Cz);

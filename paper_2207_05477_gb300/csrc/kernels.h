@@ -121,9 +121,12 @@ cudaError_t ln_fwd_cm(const void *x, int64_t pitch, const float *gamma, const fl
 // type) the accumulator starts from dinit instead of its old contents (dacc =
 // dinit + dx).  Each block adds its sums of the gamma/beta gradients to
 // dgamma, dbeta with fp32 atomics.
+// With dsum (fp32, may be null) the column sums of what is written (the
+// updated accumulator, or dx_out) are added to dsum[0..C): the bias gradient
+// of the layer that consumes this gradient next.
 cudaError_t ln_bwd(const void *dy, const void *x, const float *gamma, float *dacc, void *dcopy,
                    void *dx_out, int64_t M, int C, int use_bf16, cudaStream_t s, float *dgamma,
-                   float *dbeta, const void *dinit = nullptr);
+                   float *dbeta, const void *dinit = nullptr, float *dsum = nullptr);
 // LayerNorm backward for the channel-major input of ln_fwd_cm: dy row-major [R*R, C],
 // dx channel-major [C][R][pitch]; dgamma, dbeta accumulated with fp32 atomics.
 cudaError_t ln_bwd_cm(const void *dy, const void *x, int64_t pitch, const float *gamma, void *dx,
@@ -180,8 +183,10 @@ cudaError_t trimul_gate_bwd(const void *dA, const void *dB, int64_t pitch, const
                             const float *mask, void *dabg, int R, int cm, int incoming, int use_bf16,
                             cudaStream_t s);
 // Output gate backward: dy = dz * g; dgpre = dz * y * g (1 - g).
+// With dsum (fp32, may be null): dsum[c] += sum_p dy[p, c].
 cudaError_t gate_out_bwd(const void *dz, const void *g, int64_t g_ld, const void *y, void *dy,
-                         void *dgpre, int64_t dg_ld, int64_t P, int C, int use_bf16, cudaStream_t s);
+                         void *dgpre, int64_t dg_ld, int64_t P, int C, int use_bf16, cudaStream_t s,
+                         float *dsum = nullptr);
 // Attention gate backward: do_att = dog * g; dgpre = dog * o_att * g (1-g);
 // D[(b*H+h)*X+x] = sum_d do_att * o_att.  Rows follow AttnArgs strides.
 cudaError_t attn_gate_bwd(const AttnArgs &a, const void *dog, void *dgpre, int64_t sGb_d, int64_t sGx_d,
@@ -191,7 +196,9 @@ cudaError_t attn_dq_store(const AttnArgs &a, void *dq, int use_bf16, cudaStream_
 // inv_norm[i*R+j] = 1 / (eps + sum_s mask[s,i] mask[s,j])
 cudaError_t opm_inv_norm(const float *mask, float *inv_norm, int S, int R, float eps, cudaStream_t s);
 // y[m, :] = x[m, :] * scale[m]   (x, y activation type; rows of width C)
-cudaError_t row_scale(const void *x, const float *scale, void *y, int64_t M, int C, int use_bf16, cudaStream_t s);
+// With dsum (fp32, may be null): dsum[c] += sum_m y[m, c].
+cudaError_t row_scale(const void *x, const float *scale, void *y, int64_t M, int C, int use_bf16, cudaStream_t s,
+                      float *dsum = nullptr);
 // dst = (float) src  and  dst = (T) src conversions; fill.
 cudaError_t to_f32(const void *src, float *dst, int64_t n, int use_bf16, cudaStream_t s);
 cudaError_t from_f32(const float *src, void *dst, int64_t n, int use_bf16, cudaStream_t s);

@@ -349,16 +349,16 @@ __device__ __forceinline__ void ld8f(const float *p, float (&v)[8]) { ld8(p, v);
 template <typename T, int C, int U>
 __global__ void __launch_bounds__(256) ln_bwd_rows_v8(const T *dy, const T *x, const float *gamma, float *dacc,
                                                       T *dcopy, T *dx_out, const T *dinit, int64_t M, float *dgamma,
-                                                      float *dbeta) {
+                                                      float *dbeta, float *dsum) {
   pdl_entry();
   constexpr int TPR = C / 8, RPW = 32 / TPR;
-  __shared__ float red[8][2 * C];
+  __shared__ float red[8][3 * C];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int sub = lane % TPR, rw = lane / TPR, c0 = sub * 8;
-  float g[8], ag[8], ab[8];
+  float g[8], ag[8], ab[8], as[8];
   ld8f(gamma + c0, g);
 #pragma unroll
-  for (int k = 0; k < 8; ++k) ag[k] = ab[k] = 0.f;
+  for (int k = 0; k < 8; ++k) ag[k] = ab[k] = as[k] = 0.f;
   const int64_t nwarps = (int64_t)gridDim.x * 8;
   const int64_t w0 = (int64_t)blockIdx.x * 8 + warp;
   for (int64_t base = w0 * (RPW * U); base < M; base += nwarps * (RPW * U)) {
@@ -427,6 +427,8 @@ __global__ void __launch_bounds__(256) ln_bwd_rows_v8(const T *dy, const T *x, c
       } else {
         st8(dx_out + row * C + c0, dx);
       }
+#pragma unroll
+      for (int k = 0; k < 8; ++k) as[k] += dx[k];
     }
   }
   // lanes with the same channel slice: sum over the warp's row groups, then
@@ -437,18 +439,21 @@ __global__ void __launch_bounds__(256) ln_bwd_rows_v8(const T *dy, const T *x, c
     for (int o = TPR; o < 32; o <<= 1) {
       ag[k] += __shfl_xor_sync(0xffffffffu, ag[k], o);
       ab[k] += __shfl_xor_sync(0xffffffffu, ab[k], o);
+      as[k] += __shfl_xor_sync(0xffffffffu, as[k], o);
     }
   }
   if (rw == 0) {
 #pragma unroll
-    for (int k = 0; k < 8; ++k) red[warp][c0 + k] = ag[k], red[warp][C + c0 + k] = ab[k];
+    for (int k = 0; k < 8; ++k)
+      red[warp][c0 + k] = ag[k], red[warp][C + c0 + k] = ab[k], red[warp][2 * C + c0 + k] = as[k];
   }
   __syncthreads();
-  for (int cc = threadIdx.x; cc < 2 * C; cc += blockDim.x) {
+  const int nsum = dsum ? 3 * C : 2 * C;
+  for (int cc = threadIdx.x; cc < nsum; cc += blockDim.x) {
     float t = 0.f;
 #pragma unroll
     for (int w = 0; w < 8; ++w) t += red[w][cc];
-    atomicAdd(cc < C ? dgamma + cc : dbeta + cc - C, t);
+    atomicAdd(cc < C ? dgamma + cc : cc < 2 * C ? dbeta + cc - C : dsum + cc - 2 * C, t);
   }
 }
 
@@ -808,35 +813,11 @@ cudaError_t ln_fwd_cm(const void *x, int64_t pitch, const float *gamma, const fl
   return cudaGetLastError();
 }
 
-cudaError_t ln_bwd(const void *dy, const void *x, const float *gamma, float *dacc, void *dcopy, void *dx_out,
-                   int64_t M, int C, int use_bf16, cudaStream_t s, float *dgamma, float *dbeta, const void *dinit) {
-  if (M <= 0) return cudaSuccess;
-  Prof p("ln_bwd", s, 0, (use_bf16 ? 2.0 : 4.0) * M * C * (dcopy ? 3 : 2) + (dacc ? 8.0 * M * C : 0.0));
-  {
-    auto a16 = [](const void *q) { return ((uintptr_t)q & 15u) == 0; };
-    const bool al = a16(dy) && a16(x) && a16(gamma) && (!dacc || a16(dacc)) && (!dcopy || a16(dcopy)) &&
-                    (!dx_out || a16(dx_out)) && (!dinit || a16(dinit));
-    if (al && (C == 64 || C == 128 || C == 256)) {
-      constexpr int U = 2;
-      const int64_t rpw = 32 / (C / 8);
-      const int64_t steps = (M + rpw * U - 1) / (rpw * U);
-      const unsigned blocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>((steps + 7) / 8, 152 * 2));
-#define EVO_LN_BWD_V8(CC)                                                                                        \
-  if (C == CC) {                                                                                                 \
-    if (use_bf16)                                                                                                \
-      launch_k(ln_bwd_rows_v8<bf16, CC, U>, blocks, 256, 0, s, (const bf16 *)dy, (const bf16 *)x, gamma, dacc,   \
-               (bf16 *)dcopy, (bf16 *)dx_out, (const bf16 *)dinit, M, dgamma, dbeta);                          \
-    else                                                                                                         \
-      launch_k(ln_bwd_rows_v8<float, CC, U>, blocks, 256, 0, s, (const float *)dy, (const float *)x, gamma, dacc, \
-               (float *)dcopy, (float *)dx_out, (const float *)dinit, M, dgamma, dbeta);                       \
-    return cudaGetLastError();                                                                                   \
-  }
-      EVO_LN_BWD_V8(64)
-      EVO_LN_BWD_V8(128)
-      EVO_LN_BWD_V8(256)
-#undef EVO_LN_BWD_V8
-    }
-  }
+// LayerNorm backward without the fused column sums (any C; the vectorised
+// kernels for C = 64 P).
+cudaError_t ln_bwd_rows_any(const void *dy, const void *x, const float *gamma, float *dacc, void *dcopy,
+                            void *dx_out, int64_t M, int C, int use_bf16, cudaStream_t s, float *dgamma, float *dbeta,
+                            const void *dinit) {
   const int nb = ln_bwd_blocks(M);
   const int64_t rpb = (M + nb - 1) / nb;
 #define EVO_LN_BWD_VEC(P, NR)                                                                                    \
@@ -861,6 +842,43 @@ cudaError_t ln_bwd(const void *dy, const void *x, const float *gamma, float *dac
     launch_k(ln_bwd_rows<float>, nb, 256, sm, s, (const float *)dy, (const float *)x, gamma, dacc, (float *)dcopy,
                                            (float *)dx_out, (const float *)dinit, M, C, rpb, dgamma, dbeta);
   return cudaGetLastError();
+}
+
+cudaError_t ln_bwd(const void *dy, const void *x, const float *gamma, float *dacc, void *dcopy, void *dx_out,
+                   int64_t M, int C, int use_bf16, cudaStream_t s, float *dgamma, float *dbeta, const void *dinit,
+                   float *dsum) {
+  if (M <= 0) return cudaSuccess;
+  Prof p("ln_bwd", s, 0, (use_bf16 ? 2.0 : 4.0) * M * C * (dcopy ? 3 : 2) + (dacc ? 8.0 * M * C : 0.0));
+  {
+    auto a16 = [](const void *q) { return ((uintptr_t)q & 15u) == 0; };
+    const bool al = a16(dy) && a16(x) && a16(gamma) && (!dacc || a16(dacc)) && (!dcopy || a16(dcopy)) &&
+                    (!dx_out || a16(dx_out)) && (!dinit || a16(dinit));
+    if (al && (C == 64 || C == 128 || C == 256)) {
+      constexpr int U = 2;
+      const int64_t rpw = 32 / (C / 8);
+      const int64_t steps = (M + rpw * U - 1) / (rpw * U);
+      const unsigned blocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>((steps + 7) / 8, 152 * 2));
+#define EVO_LN_BWD_V8(CC)                                                                                        \
+  if (C == CC) {                                                                                                 \
+    if (use_bf16)                                                                                                \
+      launch_k(ln_bwd_rows_v8<bf16, CC, U>, blocks, 256, 0, s, (const bf16 *)dy, (const bf16 *)x, gamma, dacc,   \
+               (bf16 *)dcopy, (bf16 *)dx_out, (const bf16 *)dinit, M, dgamma, dbeta, dsum);                    \
+    else                                                                                                         \
+      launch_k(ln_bwd_rows_v8<float, CC, U>, blocks, 256, 0, s, (const float *)dy, (const float *)x, gamma, dacc, \
+               (float *)dcopy, (float *)dx_out, (const float *)dinit, M, dgamma, dbeta, dsum);                 \
+    return cudaGetLastError();                                                                                   \
+  }
+      EVO_LN_BWD_V8(64)
+      EVO_LN_BWD_V8(128)
+      EVO_LN_BWD_V8(256)
+#undef EVO_LN_BWD_V8
+    }
+  }
+  cudaError_t e = ln_bwd_rows_any(dy, x, gamma, dacc, dcopy, dx_out, M, C, use_bf16, s, dgamma, dbeta, dinit);
+  if (e == cudaSuccess && dsum) {
+    e = dacc ? colsum(dacc, C, M, C, 0, s, dsum) : colsum(dx_out, C, M, C, use_bf16, s, dsum);
+  }
+  return e;
 }
 
 cudaError_t ln_bwd_cm(const void *dy, const void *x, int64_t pitch, const float *gamma, void *dx, int R,

@@ -904,9 +904,34 @@ __global__ void gate_out_bwd_k(const T *dz, const T *g, int64_t g_ld, const T *y
 
 // bf16, C = 8k: eight channels per thread with 16-byte accesses, two groups
 // of loads in flight per thread
+// Column sums of a grid-stride pass whose thread keeps one 8-channel chunk
+// (the stride is a multiple of C / 8): lanes of a warp holding the same chunk
+// are combined by shuffles, the warps of a block in shared memory, then one
+// atomic add per channel and block.  red: [8][C] floats (C <= 256).
+__device__ __forceinline__ void chunk_colsum_flush(float (&cs)[8], int C, float *red, float *dsum) {
+  const int cq = C / 8, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int o = cq; o < 32; o <<= 1)
+#pragma unroll
+    for (int k = 0; k < 8; ++k) cs[k] += __shfl_xor_sync(0xffffffffu, cs[k], o);
+  if (lane < cq) {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) red[warp * C + lane * 8 + k] = cs[k];
+  }
+  __syncthreads();
+  for (int c = threadIdx.x; c < C; c += blockDim.x) {
+    float t = 0.f;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) t += red[w * C + c];
+    atomicAdd(dsum + c, t);
+  }
+}
+
 __global__ void __launch_bounds__(256) gate_out_bwd_v8(const bf16 *dz, const bf16 *g, int64_t g_ld, const bf16 *y,
-                                                       bf16 *dy, bf16 *dgpre, int64_t dg_ld, int64_t P, int C) {
+                                                       bf16 *dy, bf16 *dgpre, int64_t dg_ld, int64_t P, int C,
+                                                       float *dsum) {
   pdl_entry();
+  __shared__ float red[8 * 256];
+  float cs[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
   const int cq = C / 8;
   const int64_t n = P * cq;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -937,9 +962,12 @@ __global__ void __launch_bounds__(256) gate_out_bwd_v8(const bf16 *dz, const bf1
         }
         st8(dy + p * C + c, a);
         st8(dgpre + p * dg_ld + c, b);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) cs[k] += a[k];
       }
     }
   }
+  if (dsum) chunk_colsum_flush(cs, C, red, dsum);
 }
 
 // ------------------------------------------------------------ attention gate
@@ -1018,8 +1046,11 @@ __global__ void __launch_bounds__(256) opm_inv_norm_k(const float *mask, float *
 }
 
 // bf16 rows of C = 8k channels, 16 bytes per access, two in flight per thread
-__global__ void __launch_bounds__(256) row_scale_v8(const bf16 *x, const float *scale, bf16 *y, int64_t M, int C) {
+__global__ void __launch_bounds__(256) row_scale_v8(const bf16 *x, const float *scale, bf16 *y, int64_t M, int C,
+                                                    float *dsum) {
   pdl_entry();
+  __shared__ float red[8 * 256];
+  float cs[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
   const int cq = C / 8;
   const int64_t n = M * cq;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -1039,11 +1070,12 @@ __global__ void __launch_bounds__(256) row_scale_v8(const bf16 *x, const float *
       const int64_t e = i + u * stride;
       if (e < n) {
 #pragma unroll
-        for (int k = 0; k < 8; ++k) v[u][k] *= sc[u];
+        for (int k = 0; k < 8; ++k) v[u][k] *= sc[u], cs[k] += v[u][k];
         st8(y + e * 8, v[u]);
       }
     }
   }
+  if (dsum) chunk_colsum_flush(cs, C, red, dsum);
 }
 
 template <typename T>
@@ -1242,22 +1274,25 @@ cudaError_t trimul_gate_bwd(const void *dA, const void *dB, int64_t pitch, const
 }
 
 cudaError_t gate_out_bwd(const void *dz, const void *g, int64_t g_ld, const void *y, void *dy, void *dgpre,
-                         int64_t dg_ld, int64_t P, int C, int use_bf16, cudaStream_t s) {
+                         int64_t dg_ld, int64_t P, int C, int use_bf16, cudaStream_t s, float *dsum) {
   Prof prof("gate_out_bwd", s, 0, (use_bf16 ? 2.0 : 4.0) * (double)P * C * 5, 1);
   auto a16 = [](const void *q) { return ((uintptr_t)q & 15u) == 0; };
-  if (use_bf16 && C % 8 == 0 && g_ld % 8 == 0 && dg_ld % 8 == 0 && a16(dz) && a16(g) && a16(y) && a16(dy) &&
-      a16(dgpre)) {
+  if (use_bf16 && C % 8 == 0 && C <= 256 && 256 % (C / 8) == 0 && g_ld % 8 == 0 && dg_ld % 8 == 0 && a16(dz) &&
+      a16(g) && a16(y) && a16(dy) && a16(dgpre)) {
     const int64_t n = P * (C / 8);
     const unsigned blocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 511) / 512, 152 * 8));
     launch_k(gate_out_bwd_v8, blocks, 256, 0, s, (const bf16 *)dz, (const bf16 *)g, g_ld, (const bf16 *)y, (bf16 *)dy,
-             (bf16 *)dgpre, dg_ld, P, C);
+             (bf16 *)dgpre, dg_ld, P, C, dsum);
+    return cudaGetLastError();
   } else if (use_bf16)
     launch_k(gate_out_bwd_k<bf16>, nblk(P * C), 256, 0, s, (const bf16 *)dz, (const bf16 *)g, g_ld, (const bf16 *)y,
                                                      (bf16 *)dy, (bf16 *)dgpre, dg_ld, P, C);
   else
     launch_k(gate_out_bwd_k<float>, nblk(P * C), 256, 0, s, (const float *)dz, (const float *)g, g_ld, (const float *)y,
                                                       (float *)dy, (float *)dgpre, dg_ld, P, C);
-  return cudaGetLastError();
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess && dsum) e = colsum(dy, C, P, C, use_bf16, s, dsum);
+  return e;
 }
 
 cudaError_t attn_gate_bwd(const AttnArgs &a, const void *dog, void *dgpre, int64_t sGb_d, int64_t sGx_d, void *do_att,
@@ -1287,15 +1322,19 @@ cudaError_t opm_inv_norm(const float *mask, float *inv, int S, int R, float eps,
   return cudaGetLastError();
 }
 
-cudaError_t row_scale(const void *x, const float *scale, void *y, int64_t M, int C, int use_bf16, cudaStream_t s) {
+cudaError_t row_scale(const void *x, const float *scale, void *y, int64_t M, int C, int use_bf16, cudaStream_t s,
+                      float *dsum) {
   Prof prof("row_scale", s, 0, (use_bf16 ? 4.0 : 8.0) * M * (double)C, 1);
-  if (use_bf16 && C % 8 == 0 && (((uintptr_t)x | (uintptr_t)y) & 15u) == 0) {
+  if (use_bf16 && C % 8 == 0 && C <= 256 && 256 % (C / 8) == 0 && (((uintptr_t)x | (uintptr_t)y) & 15u) == 0) {
     const int64_t n = M * (C / 8);
     const unsigned blocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 511) / 512, 152 * 8));
-    launch_k(row_scale_v8, blocks, 256, 0, s, (const bf16 *)x, scale, (bf16 *)y, M, C);
+    launch_k(row_scale_v8, blocks, 256, 0, s, (const bf16 *)x, scale, (bf16 *)y, M, C, dsum);
+    return cudaGetLastError();
   } else if (use_bf16) launch_k(row_scale_k<bf16>, nblk(M * C), 256, 0, s, (const bf16 *)x, scale, (bf16 *)y, M, C);
   else launch_k(row_scale_k<float>, nblk(M * C), 256, 0, s, (const float *)x, scale, (float *)y, M, C);
-  return cudaGetLastError();
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess && dsum) e = colsum(y, C, M, C, use_bf16, s, dsum);
+  return e;
 }
 
 cudaError_t to_f32(const void *src, float *dst, int64_t n, int use_bf16, cudaStream_t s) {
