@@ -259,6 +259,32 @@ __device__ __forceinline__ TileCoord decode_tile(const GemmOp &g, int t, int bn)
 __device__ __forceinline__ void epi_chunk(const GemmOp &g, const float *mine, int lane, int mrow0, int nbase, int b,
                                           int split) {
   const Epi &e = g.e;
+  if (e.atomic && e.map.mdiv >= (1ll << 31) && e.map.ndiv >= (1ll << 31) && e.map.s_n0 == 1 &&
+      e.map.s_m0 % 4 == 0 && e.c_bstride % 4 == 0 && (((uintptr_t)e.C) & 15u) == 0) {
+    // split-K partial products added into a row-major fp32 output with
+    // 16-byte vector reductions: lane = (row r0 + lane / 8 + 4 i, columns
+    // 4 (lane % 8) .. + 3), a quarter of the reduction requests of one per
+    // element
+    const int rq = lane >> 3, cq = lane & 7;
+    const int n0 = nbase + 4 * cq;
+    float *cbase = (float *)e.C + (int64_t)b * e.c_bstride;
+    for (int i = 0; i < 8; ++i) {
+      const int rr = rq + 4 * i, m = mrow0 + rr;
+      if (m >= g.M) break;
+      const float *src = mine + rr * 33 + 4 * cq;
+      const float v0 = src[0] * e.alpha, v1 = src[1] * e.alpha, v2 = src[2] * e.alpha, v3 = src[3] * e.alpha;
+      float *dst = cbase + (int64_t)m * e.map.s_m0 + n0;
+      if (n0 + 3 < g.N) {
+        asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(dst), "f"(v0), "f"(v1), "f"(v2), "f"(v3)
+                     : "memory");
+      } else {
+        if (n0 < g.N) atomicAdd(dst, v0);
+        if (n0 + 1 < g.N) atomicAdd(dst + 1, v1);
+        if (n0 + 2 < g.N) atomicAdd(dst + 2, v2);
+      }
+    }
+    return;
+  }
   const int n = nbase + lane;
   if (n >= g.N) return;
   for (int rr = 0; rr < 32; ++rr) {
