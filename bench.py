@@ -309,7 +309,10 @@ def ours_arm(args):
     if world > 1:
         torch.distributed.barrier()
     clk = clocks.stop()
-    dev_ms = sum(a.elapsed_time(b) for a, b in ev)
+    step_ms = sorted(a.elapsed_time(b) for a, b in ev)
+    dev_ms = sum(step_ms)
+    pick = lambda q: step_ms[min(len(step_ms) - 1, int(q * (len(step_ms) - 1) + 0.5))]
+    step_stats = {"p10": pick(0.1), "median": pick(0.5), "p90": pick(0.9)}
     if evo.get_error() != evo.EVO_OK:
         raise RuntimeError("device error word set during the timed steps")
     t = torch.tensor([dev_ms], device=dev, dtype=torch.float64)
@@ -441,7 +444,7 @@ def ours_arm(args):
                        "l2": "flushed between timed steps (258 MB write outside the step events)",
                        "parallelism": f"replicas x{world}", "cuda_graph": bool(args.graph),
                        "gemm_tiles": ("autotuned before the warm-up: " + json.dumps(tuned)) if tuned else "built-in"},
-            "clocks": clk, "gpu_launches": launches,
+            "clocks": clk, "gpu_launches": launches, "step_ms": step_stats,
             "e2e": {"value": e2e_value, "unit": "TFLOP/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "ms_per_step": float(te.item())},
             "roofline": roof, "cpu_baseline": cpu, "fp32_plain": fp32, "kernels": kernels,
