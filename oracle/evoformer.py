@@ -18,7 +18,9 @@ module, in plain tensor algebra: no blocking, no fusion, no reordering.
 Readings where the paper is silent (each is listed with its reason in the
 design notes of the repository):
   * sub-module order is the sequential Algorithm 6 order;
-  * dropout is off (evaluation semantics);
+  * dropout is off (evaluation semantics) unless its scales are given
+    (training mode: the random draw is an input, AF2 row-wise / column-wise
+    sharing);
   * a masked key is excluded from the softmax exactly; a query with no valid
     key gets an attention output of 0;
   * LayerNorm: biased variance, eps = 1e-5;
@@ -261,25 +263,48 @@ def triangle_attention_ending_node(z, pair_mask, p, h, c, prefix="att_end",
 
 # --------------------------------------------------------------------- block
 
-def evoformer_block(m, z, msa_mask, pair_mask, p, dims):
+def dropout_rowwise(update, scale):
+    """AF2 DropoutRowwise with the random draw given: one scale per (column,
+    channel), shared by every row of the [rows, columns, channels] update."""
+    return update * scale[None, :, :]
+
+
+def dropout_columnwise(update, scale):
+    """AF2 DropoutColumnwise: one scale per (row, channel), shared by every
+    column."""
+    return update * scale[:, None, :]
+
+
+def evoformer_block(m, z, msa_mask, pair_mask, p, dims, dropout=None):
     """One Evoformer block in AF2 Algorithm 6 order, each step seeing the last.
 
     ``dims`` carries h_msa, c_msa, h_tri, c_tri, c_mul, c_opm, msa_col_mode.
     With msa_col_mode = 1 the column step is global column attention (the
-    extra-MSA block of AF2 Alg. 18).
+    extra-MSA block of AF2 Alg. 18).  ``dropout`` (training mode) maps the
+    sites msa_row, tri_out, tri_in, att_start (row-wise) and att_end
+    (column-wise) to their scales (0 or 1/(1-rate), the random draw being an
+    input); a missing site is not dropped.
     """
     hm, cm, ht, ct = dims.h_msa, dims.c_msa, dims.h_tri, dims.c_tri
-    m = m + msa_row_attention_with_pair_bias(m, z, msa_mask, p, hm, cm)
+    dr = dropout or {}
+
+    def rowwise(name, u):
+        return dropout_rowwise(u, dr[name]) if name in dr else u
+
+    def colwise(name, u):
+        return dropout_columnwise(u, dr[name]) if name in dr else u
+
+    m = m + rowwise("msa_row", msa_row_attention_with_pair_bias(m, z, msa_mask, p, hm, cm))
     if dims.msa_col_mode == 0:
         m = m + msa_column_attention(m, msa_mask, p, hm, cm)
     else:
         m = m + msa_global_column_attention(m, msa_mask, p, hm, cm)
     m = m + transition(m, p, "msa_trans")
     z = z + outer_product_mean(m, msa_mask, p, dims.c_opm)
-    z = z + triangle_multiplication_outgoing(z, pair_mask, p, dims.c_mul)
-    z = z + triangle_multiplication_incoming(z, pair_mask, p, dims.c_mul)
-    z = z + triangle_attention_starting_node(z, pair_mask, p, ht, ct)
-    z = z + triangle_attention_ending_node(z, pair_mask, p, ht, ct)
+    z = z + rowwise("tri_out", triangle_multiplication_outgoing(z, pair_mask, p, dims.c_mul))
+    z = z + rowwise("tri_in", triangle_multiplication_incoming(z, pair_mask, p, dims.c_mul))
+    z = z + rowwise("att_start", triangle_attention_starting_node(z, pair_mask, p, ht, ct))
+    z = z + colwise("att_end", triangle_attention_ending_node(z, pair_mask, p, ht, ct))
     z = z + transition(z, p, "pair_trans")
     return m, z
 
@@ -341,16 +366,20 @@ def to_f64(params: dict, requires_grad=False):
 
 # ---------------------------------------------------------- fwd / bwd entry
 
-def block_forward(m, z, msa_mask, pair_mask, params: dict, dims):
+def _dropout_f64(dropout):
+    return None if dropout is None else {k: torch.as_tensor(v).to(DT) for k, v in dropout.items()}
+
+
+def block_forward(m, z, msa_mask, pair_mask, params: dict, dims, dropout=None):
     """FP64 forward. Inputs may be numpy or torch; returns (m_out, z_out)."""
     with torch.no_grad():
         p = to_f64(params)
         return evoformer_block(torch.as_tensor(m).to(DT), torch.as_tensor(z).to(DT),
                                torch.as_tensor(msa_mask).to(DT),
-                               torch.as_tensor(pair_mask).to(DT), p, dims)
+                               torch.as_tensor(pair_mask).to(DT), p, dims, _dropout_f64(dropout))
 
 
-def block_forward_backward(m, z, msa_mask, pair_mask, params: dict, dims, gm, gz):
+def block_forward_backward(m, z, msa_mask, pair_mask, params: dict, dims, gm, gz, dropout=None):
     """FP64 forward and the gradient of <m_out, gm> + <z_out, gz>.
 
     Returns (m_out, z_out, dm_in, dz_in, dparams: dict name -> tensor).
@@ -359,7 +388,7 @@ def block_forward_backward(m, z, msa_mask, pair_mask, params: dict, dims, gm, gz
     m0 = torch.as_tensor(m).to(DT).clone().requires_grad_(True)
     z0 = torch.as_tensor(z).to(DT).clone().requires_grad_(True)
     mo, zo = evoformer_block(m0, z0, torch.as_tensor(msa_mask).to(DT),
-                             torch.as_tensor(pair_mask).to(DT), p, dims)
+                             torch.as_tensor(pair_mask).to(DT), p, dims, _dropout_f64(dropout))
     loss = (mo * torch.as_tensor(gm).to(DT)).sum() + (zo * torch.as_tensor(gz).to(DT)).sum()
     names = list(p.keys())
     grads = torch.autograd.grad(loss, [m0, z0] + [p[n] for n in names])

@@ -27,6 +27,7 @@ _M1 = np.uint64(0xBF58476D1CE4E5B9)
 _M2 = np.uint64(0x94D049BB133111EB)
 
 TAG_M, TAG_Z, TAG_PARAMS, TAG_MASK, TAG_COT_M, TAG_COT_Z = 1, 2, 3, 4, 5, 6
+TAG_DROPOUT = 7  # + index of the dropout site
 
 
 def _mix(z: np.ndarray) -> np.ndarray:
@@ -267,3 +268,32 @@ def make_problem(d: Dims, seed: int = 32, pad_frac: float = 0.0, trailing: bool 
     params = make_params(d, seed)
     gm, gz = make_cotangents(d, seed, msa_mask, pair_mask)
     return dict(m=m, z=z, msa_mask=msa_mask, pair_mask=pair_mask, params=params, gm=gm, gz=gz)
+
+
+# Training-mode dropout sites of the Evoformer block (AF2 Alg. 6): the update
+# each one scales, its rate, its shape and which axis of the updated tensor
+# shares one draw ("row": the same scale for every row, i.e. every MSA
+# sequence or every pair row i; "col": every pair column j).
+DROPOUT_SITES = (
+    ("msa_row", 0.15, "row"),    # MSA row attention with pair bias, [N_res, c_m]
+    ("tri_out", 0.25, "row"),    # triangle multiplication outgoing, [N_res, c_z]
+    ("tri_in", 0.25, "row"),     # triangle multiplication incoming
+    ("att_start", 0.25, "row"),  # triangle attention starting node
+    ("att_end", 0.25, "col"),    # triangle attention ending node, [N_res (i), c_z]
+)
+
+
+def make_dropout(d: Dims, seed: int = 32, scale_rates: float = 1.0) -> dict:
+    """Seeded dropout scales: for each site an FP32 array of shape
+    [N_res, channels] holding 0 (dropped, probability rate) or 1 / (1 - rate).
+    The random draws are inputs of the block, so the CUDA path and the oracle
+    apply the same scales.  ``scale_rates`` multiplies every rate (0 gives
+    all-ones scales)."""
+    out = {}
+    for k, (name, rate, _) in enumerate(DROPOUT_SITES):
+        rate = rate * scale_rates
+        C = d.c_m if name == "msa_row" else d.c_z
+        u = uniforms(stream_key(seed, TAG_DROPOUT + k), d.n_res * C).reshape(d.n_res, C)
+        keep = (u >= rate).astype(np.float64)
+        out[name] = (keep / (1.0 - rate)).astype(np.float32)
+    return out
