@@ -106,6 +106,23 @@ int evo_block_fwd(const evo_dims *d, const float *params, const void *params_bf1
                   const float *msa_mask, const float *pair_mask,
                   void *workspace, size_t ws_bytes, evo_stream_t stream);
 
+/* Training-mode dropout of the block (AF2 Alg. 6): each non-null pointer is
+ * the scale of one site's residual update, fp32 on the device, 256-byte
+ * aligned, entries 0 (dropped) or 1 / (1 - rate), drawn by the caller (the
+ * random draw is an input).  Row-wise sites share one draw over the rows of
+ * the update: msa_row [n_res, c_m] (MSA row attention, same for every
+ * sequence), tri_out, tri_in, att_start [n_res, c_z] (indexed by the pair
+ * column j, same for every row i); the column-wise site att_end [n_res, c_z]
+ * is indexed by the pair row i, same for every column j.  A null site is
+ * not dropped; a null evo_dropout pointer is evaluation mode. */
+typedef struct evo_dropout {
+  const float *msa_row;
+  const float *tri_out;
+  const float *tri_in;
+  const float *att_start;
+  const float *att_end;
+} evo_dropout;
+
 /* Backward of one block with per-block recompute (Sec. 3.4.1): recomputes
  * the forward from (m_in, z_in) inside the workspace, then propagates the
  * cotangents dm_out [n_seq,n_res,c_m] and dz_out [n_res,n_res,c_z]
@@ -117,6 +134,20 @@ int evo_block_bwd(const evo_dims *d, const float *params, const void *params_bf1
                   const void *dm_out, const void *dz_out,
                   void *dm_in, void *dz_in, float *dparams,
                   void *workspace, size_t ws_bytes, evo_stream_t stream);
+
+/* evo_block_fwd / evo_block_bwd with training-mode dropout (see
+ * evo_dropout; NULL gives exactly the plain calls).  The backward recomputes
+ * the forward with the same scales, which must be unchanged between the two
+ * calls. */
+int evo_block_fwd_dropout(const evo_dims *d, const float *params, const void *params_bf16,
+                          const void *m_in, const void *z_in, void *m_out, void *z_out,
+                          const float *msa_mask, const float *pair_mask, const evo_dropout *dropout,
+                          void *workspace, size_t ws_bytes, evo_stream_t stream);
+int evo_block_bwd_dropout(const evo_dims *d, const float *params, const void *params_bf16,
+                          const void *m_in, const void *z_in, const float *msa_mask,
+                          const float *pair_mask, const evo_dropout *dropout,
+                          const void *dm_out, const void *dz_out, void *dm_in, void *dz_in,
+                          float *dparams, void *workspace, size_t ws_bytes, evo_stream_t stream);
 
 /* Forward through n_blocks consecutive blocks (the EvoformerStack, Fig. 1),
  * updating m and z in place.  Block b reads params + b*param_stride and

@@ -54,9 +54,34 @@ int evo_workspace_size(const evo_dims *d, int mode, size_t *bytes) {
   return EVO_OK;
 }
 
+namespace {
+
+int dropout_ok(const evo_dropout *dr) {
+  if (!dr) return EVO_OK;
+  for (const float *q : {dr->msa_row, dr->tri_out, dr->tri_in, dr->att_start, dr->att_end})
+    if (q && !aligned256(q)) return EVO_ERR_ALIGNMENT;
+  return EVO_OK;
+}
+
+}  // namespace
+
 int evo_block_fwd(const evo_dims *d, const float *params, const void *params_bf16, const void *m_in, const void *z_in,
                   void *m_out, void *z_out, const float *msa_mask, const float *pair_mask, void *workspace,
                   size_t ws_bytes, evo_stream_t stream) {
+  return evo_block_fwd_dropout(d, params, params_bf16, m_in, z_in, m_out, z_out, msa_mask, pair_mask, nullptr,
+                               workspace, ws_bytes, stream);
+}
+
+int evo_block_bwd(const evo_dims *d, const float *params, const void *params_bf16, const void *m_in, const void *z_in,
+                  const float *msa_mask, const float *pair_mask, const void *dm_out, const void *dz_out, void *dm_in,
+                  void *dz_in, float *dparams, void *workspace, size_t ws_bytes, evo_stream_t stream) {
+  return evo_block_bwd_dropout(d, params, params_bf16, m_in, z_in, msa_mask, pair_mask, nullptr, dm_out, dz_out,
+                               dm_in, dz_in, dparams, workspace, ws_bytes, stream);
+}
+
+int evo_block_fwd_dropout(const evo_dims *d, const float *params, const void *params_bf16, const void *m_in,
+                          const void *z_in, void *m_out, void *z_out, const float *msa_mask, const float *pair_mask,
+                          const evo_dropout *dropout, void *workspace, size_t ws_bytes, evo_stream_t stream) {
   const int v = validate_dims(d);
   if (v != EVO_OK) return v;
   const bool bf = d->act_dtype == EVO_BF16;
@@ -66,13 +91,15 @@ int evo_block_fwd(const evo_dims *d, const float *params, const void *params_bf1
                         (const void *)msa_mask, (const void *)pair_mask, (const void *)workspace})
     if (!aligned256(p)) return EVO_ERR_ALIGNMENT;
   if (bf && !aligned256(params_bf16)) return EVO_ERR_ALIGNMENT;
+  if (dropout_ok(dropout) != EVO_OK) return EVO_ERR_ALIGNMENT;
   return block_forward(*d, params, (const bf16 *)params_bf16, m_in, z_in, m_out, z_out, msa_mask, pair_mask,
-                       workspace, ws_bytes, (cudaStream_t)stream);
+                       workspace, ws_bytes, (cudaStream_t)stream, dropout);
 }
 
-int evo_block_bwd(const evo_dims *d, const float *params, const void *params_bf16, const void *m_in, const void *z_in,
-                  const float *msa_mask, const float *pair_mask, const void *dm_out, const void *dz_out, void *dm_in,
-                  void *dz_in, float *dparams, void *workspace, size_t ws_bytes, evo_stream_t stream) {
+int evo_block_bwd_dropout(const evo_dims *d, const float *params, const void *params_bf16, const void *m_in,
+                          const void *z_in, const float *msa_mask, const float *pair_mask, const evo_dropout *dropout,
+                          const void *dm_out, const void *dz_out, void *dm_in, void *dz_in, float *dparams,
+                          void *workspace, size_t ws_bytes, evo_stream_t stream) {
   const int v = validate_dims(d);
   if (v != EVO_OK) return v;
   const bool bf = d->act_dtype == EVO_BF16;
@@ -84,8 +111,9 @@ int evo_block_bwd(const evo_dims *d, const float *params, const void *params_bf1
                         (const void *)workspace})
     if (!aligned256(p)) return EVO_ERR_ALIGNMENT;
   if (bf && !aligned256(params_bf16)) return EVO_ERR_ALIGNMENT;
+  if (dropout_ok(dropout) != EVO_OK) return EVO_ERR_ALIGNMENT;
   return block_backward(*d, params, (const bf16 *)params_bf16, m_in, z_in, msa_mask, pair_mask, dm_out, dz_out, dm_in,
-                        dz_in, dparams, workspace, ws_bytes, (cudaStream_t)stream);
+                        dz_in, dparams, workspace, ws_bytes, (cudaStream_t)stream, dropout);
 }
 
 int evo_stack_fwd(const evo_dims *d, int n_blocks, const float *params, const void *params_bf16, size_t param_stride,

@@ -129,6 +129,7 @@ struct Plan {
   AttBufs att[2];
   size_t xz9, h9, z6;
   size_t dm_acc, dmT, dz_acc, dzT, G1, G2, G3, dO4, dA, dB, dX, dq_acc, dbias, Dsum, dab4, split;
+  size_t drop_u;  // training-mode dropout: the update before its scale (forward), the scaled gradient (backward)
   int64_t wmax = 0;  // split holds MAXSPLIT * wmax floats
   size_t total;
 };
@@ -179,6 +180,7 @@ size_t make_plan(const evo_dims &d, int mode, Plan &p) {
     b.og = T(k.Mz * k.HCt), b.lse = F(k.R * k.Ht * k.R), b.zout = T(k.Mz * k.Cz);
   }
   p.xz9 = T(k.Mz * k.Cz), p.h9 = T(k.Mz * k.n * k.Cz), p.z6 = T(k.Mz * k.Cz);
+  p.drop_u = T(std::max(k.Mm * k.Cm, k.Mz * k.Cz));
   if (mode == EVO_MODE_BWD) {
     p.dm_acc = F(k.Mm * k.Cm), p.dmT = T(k.Mm * k.Cm), p.dz_acc = F(k.Mz * k.Cz), p.dzT = T(k.Mz * k.Cz);
     int64_t g1 = std::max<int64_t>({k.Mm * k.n * k.Cm, k.Mz * k.n * k.Cz, k.Mm * k.QKm, k.Mm * k.QKc, k.Mz * 4 * k.HCt,
@@ -228,6 +230,7 @@ struct Drv {
   char *ws;
   Plan pl;
   float *dparams = nullptr;
+  const evo_dropout *drop = nullptr;  // training-mode dropout scales (null: evaluation mode)
   cudaError_t err = cudaSuccess;
 
   Drv(const evo_dims &d_, const float *p32_, const bf16 *p16_, void *ws_, int mode, cudaStream_t s_)
@@ -239,6 +242,18 @@ struct Drv {
   }
   void ck(cudaError_t e) {
     if (err == cudaSuccess && e != cudaSuccess) err = e;
+  }
+  // dropout scale of a site (null when the block runs in evaluation mode or
+  // the site is not dropped)
+  const float *dsc(int site) const {
+    if (!drop) return nullptr;
+    switch (site) {
+      case 0: return drop->msa_row;
+      case 1: return drop->tri_out;
+      case 2: return drop->tri_in;
+      case 3: return drop->att_start;
+      default: return drop->att_end;
+    }
   }
   void *B(size_t o) { return ws + o; }
   float *Bf(size_t o) { return (float *)(ws + o); }
@@ -392,9 +407,11 @@ struct Drv {
       gemm(g);
       AttnArgs a = attn_args(0, B(pl.qkvg1), B(pl.oatt1), B(pl.og1), Bf(pl.lse1), Bf(pl.bias1), mm);
       ck(attn_fwd(a, bf, s));
-      GemmOp o = mk(Mm, Cm, HCm, B(pl.og1), HCm, 0, W("row.w_o"), HCm, 0, B(pl.m1), Cm);
-      o.e.bias = P("row.b_o"), o.e.residual = m0;
+      const float *sc = dsc(0);
+      GemmOp o = mk(Mm, Cm, HCm, B(pl.og1), HCm, 0, W("row.w_o"), HCm, 0, B(sc ? pl.drop_u : pl.m1), Cm);
+      o.e.bias = P("row.b_o"), o.e.residual = sc ? nullptr : m0;
       gemm(o);
+      if (sc) ck(dropout_apply(B(pl.drop_u), sc, m0, B(pl.m1), Mm, (int)Cm, (int)R, 0, bf, s));
     }
     // 2. MSA column attention (AF2 Alg. 8), or global column attention (AF2 Alg. 19)
     ln(B(pl.m1), "col.ln", B(pl.xm2), Mm, (int)Cm);
@@ -470,10 +487,12 @@ struct Drv {
     x.batch = (int)cmul, x.a_bs = R * Rp, x.b_bs = R * Rp, x.e.c_bstride = R * Rp;
     gemm(x);
     ck(ln_fwd_cm(B(b.X), Rp, P(pre + ".ln_out.gamma"), P(pre + ".ln_out.beta"), B(b.xo), (int)R, (int)cmul, bf, s));
-    GemmOp o = mk(Mz, Cz, cmul, B(b.xo), cmul, 0, W(pre + ".w_o"), cmul, 0, B(b.zout), Cz);
+    const float *sc = dsc(1 + t);
+    GemmOp o = mk(Mz, Cz, cmul, B(b.xo), cmul, 0, W(pre + ".w_o"), cmul, 0, B(sc ? pl.drop_u : b.zout), Cz);
     o.e.bias = P(pre + ".b_o"), o.e.aux = B(b.y), o.e.aux_ld = Cz;
-    o.e.gate = at(B(b.abg), 4 * cmul), o.e.gate_ld = ABG, o.e.residual = zin;
+    o.e.gate = at(B(b.abg), 4 * cmul), o.e.gate_ld = ABG, o.e.residual = sc ? nullptr : zin;
     gemm(o);
+    if (sc) ck(dropout_apply(B(pl.drop_u), sc, zin, B(b.zout), Mz, (int)Cz, (int)R, 0, bf, s));
   }
 
   void triatt_fwd(int t, const void *zin, const float *pm) {
@@ -487,9 +506,11 @@ struct Drv {
     gemm(g);
     AttnArgs a = attn_args(2 + t, B(b.qkvg), B(b.oatt), B(b.og), Bf(b.lse), Bf(b.bias), pm);
     ck(attn_fwd(a, bf, s));
-    GemmOp o = mk(Mz, Cz, HCt, B(b.og), HCt, 0, W(pre + ".w_o"), HCt, 0, B(b.zout), Cz);
-    o.e.bias = P(pre + ".b_o"), o.e.residual = zin;
+    const float *sc = dsc(3 + t);
+    GemmOp o = mk(Mz, Cz, HCt, B(b.og), HCt, 0, W(pre + ".w_o"), HCt, 0, B(sc ? pl.drop_u : b.zout), Cz);
+    o.e.bias = P(pre + ".b_o"), o.e.residual = sc ? nullptr : zin;
     gemm(o);
+    if (sc) ck(dropout_apply(B(pl.drop_u), sc, zin, B(b.zout), Mz, (int)Cz, (int)R, t, bf, s));
   }
 
   // ================================================================ backward
@@ -554,8 +575,10 @@ struct Drv {
     const std::string pre = t == 0 ? "tri_out" : "tri_in";
     const TriBufs &b = pl.tri[t];
     const int64_t R = k.R, Rp = k.Rp, Cz = k.Cz, Mz = k.Mz, cmul = k.cmul, ABG = k.ABG;
-    ck(gate_out_bwd(dT, at(B(b.abg), 4 * cmul), ABG, B(b.y), B(pl.G2), at(B(pl.G1), 4 * cmul), ABG, Mz, (int)Cz, bf, s,
-                    D(pre + ".b_o")));
+    const float *sc = dsc(1 + t);
+    if (sc) ck(dropout_apply(dT, sc, nullptr, B(pl.drop_u), Mz, (int)Cz, (int)R, 0, bf, s));
+    ck(gate_out_bwd(sc ? B(pl.drop_u) : dT, at(B(b.abg), 4 * cmul), ABG, B(b.y), B(pl.G2), at(B(pl.G1), 4 * cmul), ABG,
+                    Mz, (int)Cz, bf, s, D(pre + ".b_o")));
     dW(B(pl.G2), Cz, Cz, B(b.xo), cmul, cmul, Mz, pre + ".w_o");
     GemmOp g = mk(Mz, cmul, Cz, B(pl.G2), Cz, 0, W(pre + ".w_o"), cmul, 1, B(pl.G3), cmul);
     gemm(g);
@@ -588,15 +611,20 @@ struct Drv {
 
     // 9. pair transition
     transition_bwd("pair_trans", B(pl.att[1].zout), B(pl.xz9), B(pl.h9), dz, dz_out, dzT, Mz, Cz, dz_out, false,
-                   D("att_end.b_o"));
+                   dsc(4) ? nullptr : D("att_end.b_o"));
     // 8, 7. triangle attention ending / starting node
     for (int t = 1; t >= 0; --t) {
       const AttBufs &b = pl.att[t];
       const std::string pre = t == 0 ? "att_start" : "att_end";
       const void *zin = t == 0 ? B(pl.tri[1].zout) : B(pl.att[0].zout);
-      attention_bwd(2 + t, pre, B(b.xz), B(b.qkvg), B(b.oatt), B(b.og), Bf(b.lse), Bf(b.bias), pm, dzT, Mz, Cz, true);
+      // with dropout the update's gradient is dz scaled by the site's draw
+      const float *sc = dsc(3 + t);
+      if (sc) ck(dropout_apply(dzT, sc, nullptr, B(pl.drop_u), Mz, (int)Cz, (int)R, t, bf, s));
+      attention_bwd(2 + t, pre, B(b.xz), B(b.qkvg), B(b.oatt), B(b.og), Bf(b.lse), Bf(b.bias), pm,
+                    sc ? B(pl.drop_u) : dzT, Mz, Cz, sc == nullptr);
       pair_bias_bwd(pre + ".w_b", B(b.xz), (int)k.Ht, t, 1);
-      lnb(B(pl.G2), zin, pre + ".ln", dz, dzT, nullptr, Mz, (int)Cz, nullptr, t == 1 ? D("att_start.b_o") : nullptr);
+      lnb(B(pl.G2), zin, pre + ".ln", dz, dzT, nullptr, Mz, (int)Cz, nullptr,
+          t == 1 && !dsc(3) ? D("att_start.b_o") : nullptr);
     }
     // 6, 5. triangle multiplication incoming / outgoing
     trimul_bwd(1, B(pl.tri[0].zout), pm, dz, dzT);
@@ -640,10 +668,14 @@ struct Drv {
       attention_bwd(1, "col", B(pl.xm2), B(pl.qkvg2), B(pl.oatt2), B(pl.og2), Bf(pl.lse2), nullptr, mm, dmT, Mm, Cm,
                     true);
     }
-    lnb(B(pl.G2), B(pl.m1), "col.ln", dm, dmT, nullptr, Mm, (int)Cm, nullptr, D("row.b_o"));
+    lnb(B(pl.G2), B(pl.m1), "col.ln", dm, dmT, nullptr, Mm, (int)Cm, nullptr, dsc(0) ? nullptr : D("row.b_o"));
     // 1. MSA row attention with pair bias
-    attention_bwd(0, "row", B(pl.xm1), B(pl.qkvg1), B(pl.oatt1), B(pl.og1), Bf(pl.lse1), Bf(pl.bias1), mm, dmT, Mm,
-                  Cm, true);
+    {
+      const float *sc = dsc(0);
+      if (sc) ck(dropout_apply(dmT, sc, nullptr, B(pl.drop_u), Mm, (int)Cm, (int)k.R, 0, bf, s));
+      attention_bwd(0, "row", B(pl.xm1), B(pl.qkvg1), B(pl.oatt1), B(pl.og1), Bf(pl.lse1), Bf(pl.bias1), mm,
+                    sc ? B(pl.drop_u) : dmT, Mm, Cm, sc == nullptr);
+    }
     lnb(B(pl.G2), m0, "row.ln_m", dm, dm_in, nullptr, Mm, (int)Cm);
     pair_bias_bwd("row.w_b", B(pl.xz1), (int)k.Hm, 0, 0);
     lnb(B(pl.G2), z0, "row.ln_z", dz, dz_in, nullptr, Mz, (int)Cz);
@@ -659,8 +691,9 @@ size_t workspace_bytes(const evo_dims &d, int mode) {
 
 int block_forward(const evo_dims &d, const float *p32, const bf16 *p16, const void *m_in, const void *z_in,
                   void *m_out, void *z_out, const float *msa_mask, const float *pair_mask, void *ws, size_t ws_bytes,
-                  cudaStream_t s) {
+                  cudaStream_t s, const evo_dropout *dropout) {
   Drv drv(d, p32, p16, ws, EVO_MODE_FWD, s);
+  drv.drop = dropout;
   if (ws_bytes < drv.pl.total) return EVO_ERR_WORKSPACE;
   drv.forward(m_in, z_in, m_out, z_out, msa_mask, pair_mask);
   return drv.err == cudaSuccess ? EVO_OK : EVO_ERR_CUDA;
@@ -668,8 +701,9 @@ int block_forward(const evo_dims &d, const float *p32, const bf16 *p16, const vo
 
 int block_backward(const evo_dims &d, const float *p32, const bf16 *p16, const void *m_in, const void *z_in,
                    const float *msa_mask, const float *pair_mask, const void *dm_out, const void *dz_out, void *dm_in,
-                   void *dz_in, float *dparams, void *ws, size_t ws_bytes, cudaStream_t s) {
+                   void *dz_in, float *dparams, void *ws, size_t ws_bytes, cudaStream_t s, const evo_dropout *dropout) {
   Drv drv(d, p32, p16, ws, EVO_MODE_BWD, s);
+  drv.drop = dropout;
   if (ws_bytes < drv.pl.total) return EVO_ERR_WORKSPACE;
   drv.dparams = dparams;
   drv.forward(m_in, z_in, nullptr, nullptr, msa_mask, pair_mask);

@@ -27,10 +27,11 @@ size_t workspace_bytes(const evo_dims &d, int mode);
 
 int block_forward(const evo_dims &d, const float *p32, const bf16 *p16, const void *m_in, const void *z_in,
                   void *m_out, void *z_out, const float *msa_mask, const float *pair_mask, void *ws, size_t ws_bytes,
-                  cudaStream_t s);
+                  cudaStream_t s, const evo_dropout *dropout = nullptr);
 
 int block_backward(const evo_dims &d, const float *p32, const bf16 *p16, const void *m_in, const void *z_in,
                    const float *msa_mask, const float *pair_mask, const void *dm_out, const void *dz_out, void *dm_in,
-                   void *dz_in, float *dparams, void *ws, size_t ws_bytes, cudaStream_t s);
+                   void *dz_in, float *dparams, void *ws, size_t ws_bytes, cudaStream_t s,
+                   const evo_dropout *dropout = nullptr);
 
 }  // namespace evo

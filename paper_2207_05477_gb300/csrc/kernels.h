@@ -191,6 +191,11 @@ cudaError_t gate_out_bwd(const void *dz, const void *g, int64_t g_ld, const void
 // D[(b*H+h)*X+x] = sum_d do_att * o_att.  Rows follow AttnArgs strides.
 cudaError_t attn_gate_bwd(const AttnArgs &a, const void *dog, void *dgpre, int64_t sGb_d, int64_t sGx_d,
                           void *do_att, float *D, int use_bf16, cudaStream_t s);
+// Training-mode dropout of a residual update: out[p, c] = (res ? res[p, c] : 0)
+// + upd[p, c] * scale[q, c] with q = p % R (row-wise) or p / R (column-wise);
+// rows of C channels, activation type; scale fp32 [R, C].
+cudaError_t dropout_apply(const void *upd, const float *scale, const void *res, void *out, int64_t P, int C, int R,
+                          int colwise, int use_bf16, cudaStream_t s);
 // dq (activation type, q strides of dst) = scale * dq_acc
 cudaError_t attn_dq_store(const AttnArgs &a, void *dq, int use_bf16, cudaStream_t s);
 // inv_norm[i*R+j] = 1 / (eps + sum_s mask[s,i] mask[s,j])

@@ -970,6 +970,50 @@ __global__ void __launch_bounds__(256) gate_out_bwd_v8(const bf16 *dz, const bf1
   if (dsum) chunk_colsum_flush(cs, C, red, dsum);
 }
 
+// ------------------------------------------------------------------ dropout
+// out[p, c] = (res ? res[p, c] : 0) + upd[p, c] * scale[q(p), c], q(p) = p % R
+// (row-wise: one draw per column, shared by every row) or p / R (column-wise).
+template <typename T>
+__global__ void dropout_apply_k(const T *upd, const float *scale, const T *res, T *out, int64_t P, int C, int R,
+                                int colwise) {
+  pdl_entry();
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= P * C) return;
+  int64_t p;
+  int c;
+  divmod(i, C, p, c);
+  const int64_t q = colwise ? p / R : p % R;
+  const float v = ldf(upd + i) * scale[q * C + c];
+  stf(out + i, res ? ldf(res + i) + v : v);
+}
+
+__global__ void __launch_bounds__(256) dropout_apply_v8(const bf16 *upd, const float *scale, const bf16 *res,
+                                                        bf16 *out, int64_t P, int C, int R, int colwise) {
+  pdl_entry();
+  const int cq = C / 8;
+  const int64_t n = P * cq;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += stride) {
+    const int64_t p = e / cq;
+    const int c = (int)(e - p * cq) * 8;
+    const int64_t q = colwise ? p / R : p % R;
+    float u[8], r[8];
+    ld8(upd + p * C + c, u);
+    const float4 s0 = reinterpret_cast<const float4 *>(scale + q * C + c)[0];
+    const float4 s1 = reinterpret_cast<const float4 *>(scale + q * C + c)[1];
+    const float sc[8] = {s0.x, s0.y, s0.z, s0.w, s1.x, s1.y, s1.z, s1.w};
+    if (res) {
+      ld8(res + p * C + c, r);
+    } else {
+#pragma unroll
+      for (int k = 0; k < 8; ++k) r[k] = 0.f;
+    }
+#pragma unroll
+    for (int k = 0; k < 8; ++k) r[k] += u[k] * sc[k];
+    st8(out + p * C + c, r);
+  }
+}
+
 // ------------------------------------------------------------ attention gate
 template <typename T>
 __global__ void attn_gate_bwd_k(AttnArgs a, const T *dog, T *dgpre, int64_t sGb_d, int64_t sGx_d, T *do_att,
@@ -1352,6 +1396,30 @@ cudaError_t from_f32(const float *src, void *dst, int64_t n, int use_bf16, cudaS
 cudaError_t f32_to_bf16(const float *src, bf16 *dst, int64_t n, cudaStream_t s) {
   Prof prof("convert", s, 0, 6.0 * n, 1);
   launch_k(from_f32_k<bf16>, nblk(n), 256, 0, s, src, dst, n);
+  return cudaGetLastError();
+}
+
+}  // namespace evo
+
+namespace evo {
+
+cudaError_t dropout_apply(const void *upd, const float *scale, const void *res, void *out, int64_t P, int C, int R,
+                          int colwise, int use_bf16, cudaStream_t s) {
+  if (P <= 0) return cudaSuccess;
+  Prof prof("dropout", s, 0, (use_bf16 ? 2.0 : 4.0) * (double)P * C * (res ? 3 : 2), 1);
+  auto a16 = [](const void *q) { return ((uintptr_t)q & 15u) == 0; };
+  if (use_bf16 && C % 8 == 0 && a16(upd) && a16(scale) && a16(out) && (!res || a16(res))) {
+    const int64_t n = P * (C / 8);
+    const unsigned blocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 152 * 8));
+    launch_k(dropout_apply_v8, blocks, 256, 0, s, (const bf16 *)upd, scale, (const bf16 *)res, (bf16 *)out, P, C, R,
+             colwise);
+  } else if (use_bf16) {
+    launch_k(dropout_apply_k<bf16>, nblk(P * C), 256, 0, s, (const bf16 *)upd, scale, (const bf16 *)res, (bf16 *)out,
+             P, C, R, colwise);
+  } else {
+    launch_k(dropout_apply_k<float>, nblk(P * C), 256, 0, s, (const float *)upd, scale, (const float *)res,
+             (float *)out, P, C, R, colwise);
+  }
   return cudaGetLastError();
 }
 

@@ -45,6 +45,10 @@ class CParamEntry(ctypes.Structure):
                 ("shape", ctypes.c_int64 * 4)]
 
 
+class CDropout(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_void_p) for n in ("msa_row", "tri_out", "tri_in", "att_start", "att_end")]
+
+
 class CTuneEntry(ctypes.Structure):
     _fields_ = [("M", ctypes.c_int64), ("N", ctypes.c_int64), ("K", ctypes.c_int64), ("batch", ctypes.c_int64),
                 ("default_bn", ctypes.c_int32), ("default_splits", ctypes.c_int32), ("bn", ctypes.c_int32),
@@ -72,6 +76,10 @@ def lib():
         L.evo_block_fwd.argtypes = [P(CDims), _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _sz, _vp]
         L.evo_block_bwd.argtypes = [P(CDims), _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _sz,
                                     _vp]
+        L.evo_block_fwd_dropout.argtypes = [P(CDims), _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, P(CDropout), _vp, _sz,
+                                            _vp]
+        L.evo_block_bwd_dropout.argtypes = [P(CDims), _vp, _vp, _vp, _vp, _vp, _vp, P(CDropout), _vp, _vp, _vp, _vp,
+                                            _vp, _vp, _sz, _vp]
         L.evo_block_fwd_noalloc.argtypes = [P(CDims), _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]
         L.evo_stack_fwd.argtypes = [P(CDims), ctypes.c_int, _vp, _vp, _sz, _vp, _vp, _vp, _vp, _vp, _sz, _vp]
         L.evo_get_error.argtypes = [_vp]
@@ -156,6 +164,36 @@ def block_fwd(cd, params, params_bf16, m, z, m_out, z_out, msa_mask, pair_mask, 
     _check(lib().evo_block_fwd(ctypes.byref(cd), _ptr(params), _ptr(params_bf16), _ptr(m), _ptr(z), _ptr(m_out),
                                _ptr(z_out), _ptr(msa_mask), _ptr(pair_mask), _ptr(ws), ws.numel() * ws.element_size(),
                                _stream(stream)), "evo_block_fwd")
+
+
+def _dropout_struct(dropout):
+    """CDropout of a dict site -> fp32 device tensor [n_res, channels] (None: no dropout)."""
+    if dropout is None:
+        return None
+    c = CDropout()
+    for name, _ in CDropout._fields_:
+        t = dropout.get(name)
+        setattr(c, name, None if t is None else t.data_ptr())
+    return c
+
+
+def block_fwd_dropout(cd, params, params_bf16, m, z, m_out, z_out, msa_mask, pair_mask, dropout, ws, stream=None):
+    """Training-mode block forward: dropout maps site names (msa_row, tri_out, tri_in,
+    att_start, att_end) to fp32 scale tensors on the device."""
+    c = _dropout_struct(dropout)
+    _check(lib().evo_block_fwd_dropout(ctypes.byref(cd), _ptr(params), _ptr(params_bf16), _ptr(m), _ptr(z),
+                                       _ptr(m_out), _ptr(z_out), _ptr(msa_mask), _ptr(pair_mask),
+                                       ctypes.byref(c) if c is not None else None, _ptr(ws),
+                                       ws.numel() * ws.element_size(), _stream(stream)), "evo_block_fwd_dropout")
+
+
+def block_bwd_dropout(cd, params, params_bf16, m, z, msa_mask, pair_mask, dropout, dm_out, dz_out, dm_in, dz_in,
+                      dparams, ws, stream=None):
+    c = _dropout_struct(dropout)
+    _check(lib().evo_block_bwd_dropout(ctypes.byref(cd), _ptr(params), _ptr(params_bf16), _ptr(m), _ptr(z),
+                                       _ptr(msa_mask), _ptr(pair_mask), ctypes.byref(c) if c is not None else None,
+                                       _ptr(dm_out), _ptr(dz_out), _ptr(dm_in), _ptr(dz_in), _ptr(dparams), _ptr(ws),
+                                       ws.numel() * ws.element_size(), _stream(stream)), "evo_block_bwd_dropout")
 
 
 def block_fwd_noalloc(cd, params, params_bf16, m, z, m_out, z_out, msa_mask, pair_mask, stream=None):

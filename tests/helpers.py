@@ -27,11 +27,13 @@ def problem(d, seed=32, pad_frac=0.0, trailing=False):
 
 
 @functools.lru_cache(maxsize=3)
-def oracle_fwd_bwd(d, seed=32, pad_frac=0.0, trailing=False):
+def oracle_fwd_bwd(d, seed=32, pad_frac=0.0, trailing=False, dropout=False):
+    """dropout: apply the seeded training-mode dropout scales (synth.make_dropout)."""
     prob = problem(d, seed, pad_frac, trailing)
     p = synth.unpack_params(d, prob["params"])
+    dr = synth.make_dropout(d, seed) if dropout else None
     mo, zo, dm, dz, dp = O.block_forward_backward(prob["m"], prob["z"], prob["msa_mask"], prob["pair_mask"], p, d,
-                                                  prob["gm"], prob["gz"])
+                                                  prob["gm"], prob["gz"], dropout=dr)
     return mo, zo, dm, dz, dp
 
 
@@ -48,7 +50,7 @@ def _to_bf16_grid(x):
 
 
 @functools.lru_cache(maxsize=3)
-def oracle_bf16_floor(d, seed=32, pad_frac=0.0, trailing=False):
+def oracle_bf16_floor(d, seed=32, pad_frac=0.0, trailing=False, dropout=False):
     """Relative L2 change of each oracle output when only the block's inputs
     (m, z, every parameter and the cotangents gm, gz) are rounded to BF16 and
     everything else stays FP64.  A BF16 path must round these inputs, so no
@@ -56,10 +58,11 @@ def oracle_bf16_floor(d, seed=32, pad_frac=0.0, trailing=False):
     Returns {"dm": .., "dz": .., <parameter name>: ..}."""
     prob = problem(d, seed, pad_frac, trailing)
     p = synth.unpack_params(d, _to_bf16_grid(prob["params"]))
+    dr = synth.make_dropout(d, seed) if dropout else None
     _, _, dm, dz, dp = O.block_forward_backward(_to_bf16_grid(prob["m"]), _to_bf16_grid(prob["z"]), prob["msa_mask"],
                                                 prob["pair_mask"], p, d, _to_bf16_grid(prob["gm"]),
-                                                _to_bf16_grid(prob["gz"]))
-    ref = oracle_fwd_bwd(d, seed, pad_frac, trailing)
+                                                _to_bf16_grid(prob["gz"]), dropout=dr)
+    ref = oracle_fwd_bwd(d, seed, pad_frac, trailing, dropout)
     lay, _ = synth.param_layout(d)
     packed = np.zeros(max(o + int(np.prod(s)) for _, o, s, _ in lay))
     for name, off, shape, _ in lay:
@@ -69,8 +72,9 @@ def oracle_bf16_floor(d, seed=32, pad_frac=0.0, trailing=False):
     return errs
 
 
-def gpu_run(d, act_dtype, seed=32, pad_frac=0.0, trailing=False, backward=True):
-    """Block forward (and backward) through the C ABI on cuda:0; results on the CPU in fp64."""
+def gpu_run(d, act_dtype, seed=32, pad_frac=0.0, trailing=False, backward=True, dropout=False):
+    """Block forward (and backward) through the C ABI on cuda:0; results on the CPU in fp64.
+    dropout: training mode with the seeded scales of synth.make_dropout."""
     prob = problem(d, seed, pad_frac, trailing)
     dev = torch.device("cuda:0")
     dt = torch.bfloat16 if act_dtype == evo.EVO_BF16 else torch.float32
@@ -83,7 +87,11 @@ def gpu_run(d, act_dtype, seed=32, pad_frac=0.0, trailing=False, backward=True):
     pm = torch.tensor(prob["pair_mask"], device=dev)
     m_out, z_out = torch.empty_like(m), torch.empty_like(z)
     ws = evo.workspace(cd, evo.EVO_MODE_FWD, dev)
-    evo.block_fwd(cd, params, p16, m, z, m_out, z_out, mm, pm, ws)
+    dr = {k: torch.tensor(v, device=dev) for k, v in synth.make_dropout(d, seed).items()} if dropout else None
+    if dropout:
+        evo.block_fwd_dropout(cd, params, p16, m, z, m_out, z_out, mm, pm, dr, ws)
+    else:
+        evo.block_fwd(cd, params, p16, m, z, m_out, z_out, mm, pm, ws)
     out = {"m": m_out.double().cpu(), "z": z_out.double().cpu()}
     if backward:
         gm = torch.tensor(prob["gm"], device=dev).to(dt)
@@ -91,7 +99,10 @@ def gpu_run(d, act_dtype, seed=32, pad_frac=0.0, trailing=False, backward=True):
         dm, dz = torch.empty_like(m), torch.empty_like(z)
         dp = torch.zeros_like(params)
         wsb = evo.workspace(cd, evo.EVO_MODE_BWD, dev)
-        evo.block_bwd(cd, params, p16, m, z, mm, pm, gm, gz, dm, dz, dp, wsb)
+        if dropout:
+            evo.block_bwd_dropout(cd, params, p16, m, z, mm, pm, dr, gm, gz, dm, dz, dp, wsb)
+        else:
+            evo.block_bwd(cd, params, p16, m, z, mm, pm, gm, gz, dm, dz, dp, wsb)
         out.update(dm=dm.double().cpu(), dz=dz.double().cpu(), dparams=dp.double().cpu())
     torch.cuda.synchronize()
     assert evo.get_error() == evo.EVO_OK

@@ -151,3 +151,26 @@ def test_extra_msa_bf16_full_size(built_lib):
     with open(os.path.join(os.path.dirname(__file__), "golden", "bf16_floor_extra_msa.json")) as f:
         floor = json.load(f)
     _check(out, oracle_fwd_bwd(d, pad_frac=0.05), BF16_TOL, BF16_GRAD_TOL, d, RELU_MASKED_TOL, floor)
+
+
+# ------------------------------------------------------- training-mode dropout
+# The seeded scales of synth.make_dropout (rates 0.15 / 0.25, AF2 row-wise and
+# column-wise sharing) go to the oracle and, through evo_block_*_dropout, to
+# the kernels; the bounds are those of evaluation mode.
+
+def test_fp32_fwd_bwd_dropout_ragged_padded(built_lib):
+    out = gpu_run(RAGGED, evo.EVO_F32, pad_frac=0.1, dropout=True)
+    _check(out, oracle_fwd_bwd(RAGGED, pad_frac=0.1, dropout=True), FP32_TOL, FP32_GRAD_TOL, RAGGED)
+
+
+def test_bf16_fwd_bwd_dropout_ragged_padded(built_lib):
+    out = gpu_run(RAGGED, evo.EVO_BF16, pad_frac=0.1, dropout=True)
+    _check(out, oracle_fwd_bwd(RAGGED, pad_frac=0.1, dropout=True), BF16_TOL, BF16_GRAD_TOL, RAGGED, RELU_MASKED_TOL,
+           oracle_bf16_floor(RAGGED, pad_frac=0.1, dropout=True))
+
+
+@pytest.mark.slow
+def test_bf16_fwd_bwd_dropout_training_crop(built_lib):
+    d = synth.DIMS_TRAIN_CROP
+    out = gpu_run(d, evo.EVO_BF16, pad_frac=0.05, dropout=True)
+    _check(out, oracle_fwd_bwd(d, pad_frac=0.05, dropout=True), BF16_TOL, BF16_GRAD_TOL, d, RELU_MASKED_TOL)
