@@ -229,11 +229,19 @@ def ours_arm(args):
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
 
+    # training-mode dropout (--dropout): the seeded scales of the five AF2
+    # sites, device-resident like the other inputs
+    drop = {k: torch.tensor(v, device=dev) for k, v in synth.make_dropout(d, seed).items()} if args.dropout else None
+
     def step(mi, zi, mmi, pmi, gmi, gzi, prm):
         if p16 is not None:
             evo.params_to_bf16(cd, prm, p16)
-        evo.block_fwd(cd, prm, p16, mi, zi, m_out, z_out, mmi, pmi, ws_f)
-        evo.block_bwd(cd, prm, p16, mi, zi, mmi, pmi, gmi, gzi, dm, dz, dparams, ws_b)
+        if drop is None:
+            evo.block_fwd(cd, prm, p16, mi, zi, m_out, z_out, mmi, pmi, ws_f)
+            evo.block_bwd(cd, prm, p16, mi, zi, mmi, pmi, gmi, gzi, dm, dz, dparams, ws_b)
+        else:
+            evo.block_fwd_dropout(cd, prm, p16, mi, zi, m_out, z_out, mmi, pmi, drop, ws_f)
+            evo.block_bwd_dropout(cd, prm, p16, mi, zi, mmi, pmi, drop, gmi, gzi, dm, dz, dparams, ws_b)
 
     tuned = autotune(evo, lambda: step(m, z, mm, pm, gm, gz, params), TUNE_PASSES) \
         if act == evo.EVO_BF16 and not args.no_tune else None
@@ -324,9 +332,10 @@ def ours_arm(args):
     # ---- end to end through the C ABI with host buffers: H2D of the step's inputs, D2H of its results
     host = {k: torch.tensor(prob[k]).to(tdt if k in ("m", "z", "gm", "gz") else torch.float32).pin_memory()
             for k in ("m", "z", "msa_mask", "pair_mask", "gm", "gz", "params")}
+    host_drop = {k: v.cpu().pin_memory() for k, v in drop.items()} if drop is not None else {}
     out_host = {k: torch.empty(v.shape, dtype=v.dtype).pin_memory() for k, v in
                 (("dm", dm), ("dz", dz), ("dparams", dparams))}
-    h2d = sum(v.numel() * v.element_size() for v in host.values())
+    h2d = sum(v.numel() * v.element_size() for v in list(host.values()) + list(host_drop.values()))
     d2h = sum(v.numel() * v.element_size() for v in out_host.values())
     dbuf = {k: torch.empty(v.shape, dtype=v.dtype, device=dev) for k, v in host.items()}
     e2e_steps = max(1, min(args.steps, 50))
@@ -338,6 +347,8 @@ def ours_arm(args):
     for _ in range(e2e_steps):
         for k in host:
             dbuf[k].copy_(host[k], non_blocking=True)
+        for k in host_drop:  # the dropout draw of the step is an input too
+            drop[k].copy_(host_drop[k], non_blocking=True)
         if graph is None:
             step(dbuf["m"], dbuf["z"], dbuf["msa_mask"], dbuf["pair_mask"], dbuf["gm"], dbuf["gz"], dbuf["params"])
         else:
@@ -364,8 +375,12 @@ def ours_arm(args):
         dp32 = torch.zeros_like(params)
 
         def step32():
-            evo.block_fwd(cd32, params, None, m32, z32, mo32, zo32, mm, pm, w32f)
-            evo.block_bwd(cd32, params, None, m32, z32, mm, pm, g32m, g32z, dm32, dz32, dp32, w32b)
+            if drop is None:
+                evo.block_fwd(cd32, params, None, m32, z32, mo32, zo32, mm, pm, w32f)
+                evo.block_bwd(cd32, params, None, m32, z32, mm, pm, g32m, g32z, dm32, dz32, dp32, w32b)
+            else:
+                evo.block_fwd_dropout(cd32, params, None, m32, z32, mo32, zo32, mm, pm, drop, w32f)
+                evo.block_bwd_dropout(cd32, params, None, m32, z32, mm, pm, drop, g32m, g32z, dm32, dz32, dp32, w32b)
 
         step32()
         torch.cuda.synchronize()
@@ -443,6 +458,8 @@ def ours_arm(args):
                        "n_seq": d.n_seq, "n_res": d.n_res, "flops_per_step": step_flops(d),
                        "l2": "flushed between timed steps (258 MB write outside the step events)",
                        "parallelism": f"replicas x{world}", "cuda_graph": bool(args.graph),
+                       "dropout": "training mode, AF2 rates (0.15 MSA row, 0.25 pair), seeded draws as inputs"
+                       if args.dropout else "evaluation mode (none)",
                        "gemm_tiles": ("autotuned before the warm-up: " + json.dumps(tuned)) if tuned else "built-in"},
             "clocks": clk, "gpu_launches": launches, "step_ms": step_stats,
             "e2e": {"value": e2e_value, "unit": "TFLOP/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
@@ -658,6 +675,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp32", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="keep the built-in GEMM tile choice")
+    ap.add_argument("--dropout", action="store_true", help="training-mode dropout (AF2 sites and rates)")
     ap.add_argument("--streams", type=int, default=8, help="concurrent CUDA streams of the 16-protein batch")
     ap.add_argument("--graph", action="store_true",
                     help="replay the step as one captured CUDA graph (the default; kept for older command lines)")
