@@ -312,14 +312,18 @@ def _autograd_fn():
         """One Evoformer block; backward recomputes the block (only m, z saved)."""
 
         @staticmethod
-        def forward(ctx, m, z, params, msa_mask, pair_mask, cd):
+        def forward(ctx, m, z, params, msa_mask, pair_mask, cd, dropout=None):
             m, z = m.contiguous(), z.contiguous()
             p16 = bf16_params(cd, params)
             m_out, z_out = torch.empty_like(m), torch.empty_like(z)
             ws = workspace(cd, EVO_MODE_FWD, m.device)
-            block_fwd(cd, params, p16, m, z, m_out, z_out, msa_mask, pair_mask, ws)
+            if dropout is None:
+                block_fwd(cd, params, p16, m, z, m_out, z_out, msa_mask, pair_mask, ws)
+            else:
+                block_fwd_dropout(cd, params, p16, m, z, m_out, z_out, msa_mask, pair_mask, dropout, ws)
             ctx.save_for_backward(m, z, params, msa_mask, pair_mask)
             ctx.cd = cd
+            ctx.dropout = dropout  # the same draw must be replayed by the recompute
             ctx.mark_non_differentiable(msa_mask, pair_mask)
             return m_out, z_out
 
@@ -334,8 +338,12 @@ def _autograd_fn():
             dm_in, dz_in = torch.empty_like(m), torch.empty_like(z)
             dparams = torch.zeros_like(params)
             ws = workspace(cd, EVO_MODE_BWD, m.device)
-            block_bwd(cd, params, p16, m, z, msa_mask, pair_mask, dm, dz, dm_in, dz_in, dparams, ws)
-            return dm_in, dz_in, dparams, None, None, None
+            if ctx.dropout is None:
+                block_bwd(cd, params, p16, m, z, msa_mask, pair_mask, dm, dz, dm_in, dz_in, dparams, ws)
+            else:
+                block_bwd_dropout(cd, params, p16, m, z, msa_mask, pair_mask, ctx.dropout, dm, dz, dm_in, dz_in,
+                                  dparams, ws)
+            return dm_in, dz_in, dparams, None, None, None, None
 
     return EvoBlockFn
 
@@ -343,16 +351,19 @@ def _autograd_fn():
 _EvoBlockFn = None
 
 
-def evoformer_block(m, z, params, msa_mask, pair_mask, cd):
-    """Differentiable Evoformer block through libevo (forward and backward kernels)."""
+def evoformer_block(m, z, params, msa_mask, pair_mask, cd, dropout=None):
+    """Differentiable Evoformer block through libevo (forward and backward kernels).
+    dropout: None (evaluation mode) or a dict of the site scales (training mode,
+    see block_fwd_dropout); the backward replays the same draw."""
     global _EvoBlockFn
     if _EvoBlockFn is None:
         _EvoBlockFn = _autograd_fn()
-    return _EvoBlockFn.apply(m, z, params, msa_mask, pair_mask, cd)
+    return _EvoBlockFn.apply(m, z, params, msa_mask, pair_mask, cd, dropout)
 
 
-def evoformer_stack(m, z, params_list, msa_mask, pair_mask, cd):
-    """Stack of blocks; each block recomputes itself in backward (per-block recompute)."""
-    for p in params_list:
-        m, z = evoformer_block(m, z, p, msa_mask, pair_mask, cd)
+def evoformer_stack(m, z, params_list, msa_mask, pair_mask, cd, dropouts=None):
+    """Stack of blocks; each block recomputes itself in backward (per-block recompute).
+    dropouts: None or one dropout dict per block."""
+    for i, p in enumerate(params_list):
+        m, z = evoformer_block(m, z, p, msa_mask, pair_mask, cd, None if dropouts is None else dropouts[i])
     return m, z
