@@ -309,6 +309,48 @@ def evoformer_block(m, z, msa_mask, pair_mask, p, dims, dropout=None):
     return m, z
 
 
+def pair_stack_block(z, pair_mask, p, dims, dropout=None):
+    """One template pair stack block (AF2 Alg. 16): the pair half of the
+    Evoformer block -- triangle multiplications, triangle attentions, pair
+    transition, with the same dropout sites -- on the template pair
+    representation alone (no MSA, no outer product mean)."""
+    ht, ct = dims.h_tri, dims.c_tri
+    dr = dropout or {}
+
+    def rowwise(name, u):
+        return dropout_rowwise(u, dr[name]) if name in dr else u
+
+    def colwise(name, u):
+        return dropout_columnwise(u, dr[name]) if name in dr else u
+
+    z = z + rowwise("tri_out", triangle_multiplication_outgoing(z, pair_mask, p, dims.c_mul))
+    z = z + rowwise("tri_in", triangle_multiplication_incoming(z, pair_mask, p, dims.c_mul))
+    z = z + rowwise("att_start", triangle_attention_starting_node(z, pair_mask, p, ht, ct))
+    z = z + colwise("att_end", triangle_attention_ending_node(z, pair_mask, p, ht, ct))
+    z = z + transition(z, p, "pair_trans")
+    return z
+
+
+def pair_block_forward(z, pair_mask, params: dict, dims, dropout=None):
+    """FP64 template pair block forward; returns z_out."""
+    with torch.no_grad():
+        return pair_stack_block(torch.as_tensor(z).to(DT), torch.as_tensor(pair_mask).to(DT), to_f64(params), dims,
+                                _dropout_f64(dropout))
+
+
+def pair_block_forward_backward(z, pair_mask, params: dict, dims, gz, dropout=None):
+    """FP64 template pair block forward and the gradient of <z_out, gz>.
+
+    Returns (z_out, dz_in, dparams: dict name -> tensor)."""
+    p = to_f64(params, requires_grad=True)
+    z0 = torch.as_tensor(z).to(DT).clone().requires_grad_(True)
+    zo = pair_stack_block(z0, torch.as_tensor(pair_mask).to(DT), p, dims, _dropout_f64(dropout))
+    loss = (zo * torch.as_tensor(gz).to(DT)).sum()
+    names = list(p.keys())
+    grads = torch.autograd.grad(loss, [z0] + [p[n] for n in names])
+    return zo.detach(), grads[0], {n: g for n, g in zip(names, grads[1:])}
+
+
 # -------------------------------------------------------------- param table
 
 def expected_param_shapes(dims):
@@ -338,6 +380,8 @@ def expected_param_shapes(dims):
         "pair_trans.w1": (dims.trans_n * Z, Z), "pair_trans.b1": (dims.trans_n * Z,),
         "pair_trans.w2": (Z, dims.trans_n * Z), "pair_trans.b2": (Z,),
     }
+    if getattr(dims, "pair_only", 0):
+        s = {k: v for k, v in s.items() if k.startswith("pair_trans.")}
     for t in ("tri_out", "tri_in"):
         s.update({
             t + ".ln_in.gamma": (Z,), t + ".ln_in.beta": (Z,),

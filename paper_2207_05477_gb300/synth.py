@@ -81,6 +81,7 @@ class Dims:
     c_opm: int = 32
     trans_n: int = 4
     msa_col_mode: int = 0  # 0 column attention, 1 global column attention
+    pair_only: int = 0     # 1: a template pair stack block (pair half only, AF2 Alg. 16)
 
     def replace(self, **kw) -> "Dims":
         d = dict(self.__dict__)
@@ -96,6 +97,10 @@ DIMS_TRAIN_CROP = Dims(n_seq=128, n_res=256)
 DIMS_EXTRA_MSA = Dims(n_seq=1024, n_res=256, c_m=64, h_msa=8, c_msa=8, msa_col_mode=1)
 DIMS_TINY = Dims(n_seq=3, n_res=5, c_m=8, c_z=4, h_msa=2, c_msa=4, h_tri=2, c_tri=4,
                  c_mul=4, c_opm=2, trans_n=2)
+# Template pair stack block (AF2 Alg. 16, published template dims): c_t = 64,
+# triangle multiplication 64 channels, triangle attention 4 heads of 16,
+# pair transition factor 2.  The MSA fields are unused (n_seq = 1).
+DIMS_TEMPLATE = Dims(n_seq=1, n_res=256, c_z=64, h_tri=4, c_tri=16, c_mul=64, trans_n=2, pair_only=1)
 
 
 def param_entries(d: Dims):
@@ -112,6 +117,9 @@ def param_entries(d: Dims):
         e.append((prefix + ".gamma", (c,), "gamma"))
         e.append((prefix + ".beta", (c,), "beta"))
 
+    if d.pair_only:
+        _pair_entries(d, e, ln)
+        return e
     ln("row.ln_m", d.c_m)
     ln("row.ln_z", d.c_z)
     e.append(("row.w_b", (hm, d.c_z), "weight"))
@@ -137,6 +145,14 @@ def param_entries(d: Dims):
     e.append(("opm.b_ab", (2 * d.c_opm,), "bias"))
     e.append(("opm.w_o", (d.c_z, d.c_opm * d.c_opm), "weight"))
     e.append(("opm.b_o", (d.c_z,), "bias"))
+    _pair_entries(d, e, ln)
+    return e
+
+
+def _pair_entries(d: Dims, e: list, ln):
+    """The pair-stack tensors (triangle multiplications, triangle attentions,
+    pair transition), shared by the Evoformer and the template pair block."""
+    ht, ct = d.h_tri, d.c_tri
     for t in ("tri_out", "tri_in"):
         ln(t + ".ln_in", d.c_z)
         e.append((t + ".w_abg", (4 * d.c_mul + d.c_z, d.c_z), "weight"))
@@ -156,7 +172,6 @@ def param_entries(d: Dims):
     e.append(("pair_trans.b1", (d.trans_n * d.c_z,), "bias"))
     e.append(("pair_trans.w2", (d.c_z, d.trans_n * d.c_z), "weight"))
     e.append(("pair_trans.b2", (d.c_z,), "bias"))
-    return e
 
 
 ALIGN_FLOATS = 64  # 256 bytes
