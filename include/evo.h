@@ -180,6 +180,29 @@ int evo_block_fwd_noalloc(const evo_dims *d, const float *params, const void *pa
                           const void *m_in, const void *z_in, void *m_out, void *z_out,
                           const float *msa_mask, const float *pair_mask, evo_stream_t stream);
 
+/* Template pair stack block (AF2 Alg. 16; SURVEY next row): the pair half of
+ * the block -- triangle multiplication outgoing and incoming, triangle
+ * attention starting and ending node, pair transition, with the same
+ * dropout sites (msa_row ignored) -- on z alone.  Only the pair fields of
+ * evo_dims are read (n_res, c_z, h_tri, c_tri, c_mul, trans_n, act_dtype);
+ * the template dims are c_z 64, c_mul 64, h_tri 4, c_tri 16, trans_n 2.
+ * Its flat parameter buffer holds the pair-stack tensors only
+ * (evo_pair_param_count / evo_pair_param_layout, same names and 256-byte
+ * alignment as the block's); evo_pair_workspace_size sizes its scratch.
+ * The backward recomputes the forward, writes dz_in and adds the parameter
+ * gradient to dparams; errors as for the block. */
+size_t evo_pair_param_count(const evo_dims *d);
+int evo_pair_param_layout(const evo_dims *d, evo_param_entry *out, int cap);
+int evo_pair_workspace_size(const evo_dims *d, int mode, size_t *bytes);
+int evo_pair_params_to_bf16(const evo_dims *d, const float *params, void *params_bf16, evo_stream_t stream);
+int evo_pair_block_fwd(const evo_dims *d, const float *params, const void *params_bf16,
+                       const void *z_in, void *z_out, const float *pair_mask, const evo_dropout *dropout,
+                       void *workspace, size_t ws_bytes, evo_stream_t stream);
+int evo_pair_block_bwd(const evo_dims *d, const float *params, const void *params_bf16,
+                       const void *z_in, const float *pair_mask, const evo_dropout *dropout,
+                       const void *dz_out, void *dz_in, float *dparams,
+                       void *workspace, size_t ws_bytes, evo_stream_t stream);
+
 /* Waits for the stream, then returns and clears the device error word:
  * EVO_OK, or EVO_ERR_TIMEOUT if a bounded in-kernel wait gave up since the
  * last call. */

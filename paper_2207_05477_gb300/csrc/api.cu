@@ -162,3 +162,75 @@ const char *evo_strerror(int code) {
 const char *evo_version(void) { return "libevo 0.1 sm_103a"; }
 
 }  // extern "C"
+
+extern "C" {
+
+size_t evo_pair_param_count(const evo_dims *d) {
+  if (!d) return 0;
+  std::vector<PEntry> t;
+  return (size_t)build_param_table(*d, t, true);
+}
+
+int evo_pair_param_layout(const evo_dims *d, evo_param_entry *out, int cap) {
+  if (!d) return EVO_ERR_INVALID_ARG;
+  std::vector<PEntry> t;
+  build_param_table(*d, t, true);
+  for (int i = 0; i < (int)t.size() && i < cap && out; ++i) {
+    std::memset(&out[i], 0, sizeof(evo_param_entry));
+    std::strncpy(out[i].name, t[i].name.c_str(), sizeof(out[i].name) - 1);
+    out[i].offset = t[i].offset;
+    out[i].ndim = t[i].ndim;
+    for (int k = 0; k < 4; ++k) out[i].shape[k] = t[i].shape[k];
+  }
+  return (int)t.size();
+}
+
+int evo_pair_workspace_size(const evo_dims *d, int mode, size_t *bytes) {
+  if (!bytes || (mode != EVO_MODE_FWD && mode != EVO_MODE_BWD)) return EVO_ERR_INVALID_ARG;
+  const int v = validate_pair_dims(d);
+  if (v != EVO_OK) return v;
+  *bytes = workspace_bytes(*d, mode, true);
+  return EVO_OK;
+}
+
+int evo_pair_params_to_bf16(const evo_dims *d, const float *params, void *params_bf16, evo_stream_t stream) {
+  if (!d || !params || !params_bf16) return EVO_ERR_INVALID_ARG;
+  if (!aligned256(params) || !aligned256(params_bf16)) return EVO_ERR_ALIGNMENT;
+  const int64_t n = (int64_t)evo_pair_param_count(d);
+  return f32_to_bf16(params, (bf16 *)params_bf16, n, (cudaStream_t)stream) == cudaSuccess ? EVO_OK : EVO_ERR_CUDA;
+}
+
+int evo_pair_block_fwd(const evo_dims *d, const float *params, const void *params_bf16, const void *z_in,
+                       void *z_out, const float *pair_mask, const evo_dropout *dropout, void *workspace,
+                       size_t ws_bytes, evo_stream_t stream) {
+  const int v = validate_pair_dims(d);
+  if (v != EVO_OK) return v;
+  const bool bf = d->act_dtype == EVO_BF16;
+  if (!params || !z_in || !z_out || !pair_mask || !workspace || (bf && !params_bf16)) return EVO_ERR_INVALID_ARG;
+  for (const void *p : {(const void *)params, z_in, (const void *)z_out, (const void *)pair_mask,
+                        (const void *)workspace})
+    if (!aligned256(p)) return EVO_ERR_ALIGNMENT;
+  if (bf && !aligned256(params_bf16)) return EVO_ERR_ALIGNMENT;
+  if (dropout_ok(dropout) != EVO_OK) return EVO_ERR_ALIGNMENT;
+  return pair_block_forward(*d, params, (const bf16 *)params_bf16, z_in, z_out, pair_mask, workspace, ws_bytes,
+                            (cudaStream_t)stream, dropout);
+}
+
+int evo_pair_block_bwd(const evo_dims *d, const float *params, const void *params_bf16, const void *z_in,
+                       const float *pair_mask, const evo_dropout *dropout, const void *dz_out, void *dz_in,
+                       float *dparams, void *workspace, size_t ws_bytes, evo_stream_t stream) {
+  const int v = validate_pair_dims(d);
+  if (v != EVO_OK) return v;
+  const bool bf = d->act_dtype == EVO_BF16;
+  if (!params || !z_in || !pair_mask || !dz_out || !dz_in || !dparams || !workspace || (bf && !params_bf16))
+    return EVO_ERR_INVALID_ARG;
+  for (const void *p : {(const void *)params, z_in, (const void *)pair_mask, dz_out, (const void *)dz_in,
+                        (const void *)dparams, (const void *)workspace})
+    if (!aligned256(p)) return EVO_ERR_ALIGNMENT;
+  if (bf && !aligned256(params_bf16)) return EVO_ERR_ALIGNMENT;
+  if (dropout_ok(dropout) != EVO_OK) return EVO_ERR_ALIGNMENT;
+  return pair_block_backward(*d, params, (const bf16 *)params_bf16, z_in, pair_mask, dz_out, dz_in, dparams,
+                             workspace, ws_bytes, (cudaStream_t)stream, dropout);
+}
+
+}  // extern "C"

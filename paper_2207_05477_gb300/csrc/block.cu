@@ -18,7 +18,7 @@
 namespace evo {
 
 // ------------------------------------------------------------ param table
-int64_t build_param_table(const evo_dims &d, std::vector<PEntry> &out) {
+int64_t build_param_table(const evo_dims &d, std::vector<PEntry> &out, bool pair_only) {
   out.clear();
   int64_t off = 0;
   auto add = [&](const std::string &name, std::initializer_list<int64_t> shape) {
@@ -41,6 +41,7 @@ int64_t build_param_table(const evo_dims &d, std::vector<PEntry> &out) {
     add(p + ".beta", {c});
   };
   const int64_t C = d.c_m, Z = d.c_z, hm = d.h_msa, cm = d.c_msa, ht = d.h_tri, ct = d.c_tri;
+  if (!pair_only) {
   ln("row.ln_m", C);
   ln("row.ln_z", Z);
   add("row.w_b", {hm, Z});
@@ -64,6 +65,8 @@ int64_t build_param_table(const evo_dims &d, std::vector<PEntry> &out) {
   add("opm.b_ab", {2 * d.c_opm});
   add("opm.w_o", {Z, (int64_t)d.c_opm * d.c_opm});
   add("opm.b_o", {Z});
+  }
+  // the pair stack (shared by the Evoformer and the template pair block)
   for (const char *t : {"tri_out", "tri_in"}) {
     const std::string p(t);
     ln(p + ".ln_in", Z);
@@ -88,6 +91,16 @@ int64_t build_param_table(const evo_dims &d, std::vector<PEntry> &out) {
   add("pair_trans.w2", {Z, d.trans_n * Z});
   add("pair_trans.b2", {Z});
   return off;
+}
+
+int validate_pair_dims(const evo_dims *d) {
+  if (!d) return EVO_ERR_INVALID_ARG;
+  if (d->n_res <= 0 || d->c_z <= 0 || d->h_tri <= 0 || d->c_tri <= 0 || d->c_mul <= 0 || d->trans_n <= 0)
+    return EVO_ERR_INVALID_ARG;
+  if (d->act_dtype != EVO_F32 && d->act_dtype != EVO_BF16) return EVO_ERR_INVALID_ARG;
+  if (d->c_z % 8 || d->c_mul % 8 || d->c_tri % 8) return EVO_ERR_UNSUPPORTED;
+  if (d->h_tri > 8 || d->c_tri > 32 || d->c_z > 1024 || d->c_mul > 256) return EVO_ERR_UNSUPPORTED;
+  return EVO_OK;
 }
 
 int validate_dims(const evo_dims *d) {
@@ -136,8 +149,9 @@ struct Plan {
 
 struct Dims2 {
   int64_t S, R, Cm, Cz, Hm, cm, Ht, ct, cmul, co, n, Mm, Mz, Rp, HCm, HCt, QKm, QKc, ABG;
-  explicit Dims2(const evo_dims &d) {
-    S = d.n_seq, R = d.n_res, Cm = d.c_m, Cz = d.c_z, Hm = d.h_msa, cm = d.c_msa, Ht = d.h_tri, ct = d.c_tri;
+  // pair_only: the template pair block, no MSA (every MSA size 0)
+  explicit Dims2(const evo_dims &d, bool pair_only = false) {
+    S = pair_only ? 0 : d.n_seq, R = d.n_res, Cm = d.c_m, Cz = d.c_z, Hm = d.h_msa, cm = d.c_msa, Ht = d.h_tri, ct = d.c_tri;
     cmul = d.c_mul, co = d.c_opm, n = d.trans_n;
     Mm = S * R, Mz = R * R, Rp = (R + 7) / 8 * 8;
     HCm = Hm * cm, HCt = Ht * ct;
@@ -147,8 +161,8 @@ struct Dims2 {
   }
 };
 
-size_t make_plan(const evo_dims &d, int mode, Plan &p) {
-  const Dims2 k(d);
+size_t make_plan(const evo_dims &d, int mode, Plan &p, bool pair_only = false) {
+  const Dims2 k(d, pair_only);
   const size_t ts = d.act_dtype == EVO_BF16 ? 2 : 4;
   size_t off = 0;
   auto T = [&](int64_t elems) {
@@ -167,8 +181,9 @@ size_t make_plan(const evo_dims &d, int mode, Plan &p) {
   p.lse2 = F(k.R * k.Hm * k.S), p.m2 = T(k.Mm * k.Cm);
   p.gq = F(k.R * k.HCm), p.gob = F(k.R * k.HCm), p.gst = F(k.R * k.Hm * 2);
   p.xm3 = T(k.Mm * k.Cm), p.h3 = T(k.Mm * k.n * k.Cm), p.m3 = T(k.Mm * k.Cm);
-  p.xm4 = T(k.Mm * k.Cm), p.ab4 = T(2 * k.Mm * k.co), p.O4 = T(k.Mz * k.co * k.co), p.inv4 = F(k.Mz);
-  p.z1 = T(k.Mz * k.Cz);
+  const int64_t Mz_opm = pair_only ? 0 : k.Mz;  // the outer product mean's pair buffers
+  p.xm4 = T(k.Mm * k.Cm), p.ab4 = T(2 * k.Mm * k.co), p.O4 = T(Mz_opm * k.co * k.co), p.inv4 = F(Mz_opm);
+  p.z1 = T(Mz_opm * k.Cz);
   for (int t = 0; t < 2; ++t) {
     TriBufs &b = p.tri[t];
     b.xz = T(k.Mz * k.Cz), b.abg = T(k.Mz * k.ABG), b.A = T(k.cmul * k.R * k.Rp), b.B = T(k.cmul * k.R * k.Rp);
@@ -188,7 +203,7 @@ size_t make_plan(const evo_dims &d, int mode, Plan &p) {
     int64_t g2 = std::max<int64_t>({k.Mm * k.Cm, k.Mz * k.Cz, k.Mm * k.HCm, k.Mz * k.HCt, k.Mm * 2 * k.co});
     int64_t g3 = std::max<int64_t>({k.Mm * k.HCm, k.Mz * k.HCt, k.Mz * k.cmul, k.Mz * k.Cz});
     p.G1 = T(g1), p.G2 = T(g2), p.G3 = T(g3);
-    p.dO4 = T(k.Mz * k.co * k.co);
+    p.dO4 = T(Mz_opm * k.co * k.co);
     p.dA = T(k.cmul * k.R * k.Rp), p.dB = T(k.cmul * k.R * k.Rp), p.dX = T(k.cmul * k.R * k.Rp);
     p.dq_acc = F(std::max(k.Mm * k.HCm, k.Mz * k.HCt));
     p.dbias = F(std::max(k.Hm, k.Ht) * k.Mz);
@@ -233,12 +248,14 @@ struct Drv {
   const evo_dropout *drop = nullptr;  // training-mode dropout scales (null: evaluation mode)
   cudaError_t err = cudaSuccess;
 
-  Drv(const evo_dims &d_, const float *p32_, const bf16 *p16_, void *ws_, int mode, cudaStream_t s_)
-      : d(d_), k(d_), bf(d_.act_dtype == EVO_BF16), ts(bf ? 2 : 4), s(s_), p32(p32_), p16(p16_), ws((char *)ws_) {
+  Drv(const evo_dims &d_, const float *p32_, const bf16 *p16_, void *ws_, int mode, cudaStream_t s_,
+      bool pair_only = false)
+      : d(d_), k(d_, pair_only), bf(d_.act_dtype == EVO_BF16), ts(bf ? 2 : 4), s(s_), p32(p32_), p16(p16_),
+        ws((char *)ws_) {
     std::vector<PEntry> t;
-    build_param_table(d, t);
+    build_param_table(d, t, pair_only);
     for (auto &e : t) off[e.name] = e.offset;
-    make_plan(d, mode, pl);
+    make_plan(d, mode, pl, pair_only);
   }
   void ck(cudaError_t e) {
     if (err == cudaSuccess && e != cudaSuccess) err = e;
@@ -449,16 +466,22 @@ struct Drv {
       p.e.bias = P("opm.b_o"), p.e.row_scale = Bf(pl.inv4), p.e.residual = z0;
       gemm(p);
     }
+    pair_forward(B(pl.z1), z_out, pm);
+    (void)HCt;
+  }
+
+  // Steps 5-9 of the block from the pair input zin; also the whole template
+  // pair stack block (AF2 Alg. 16).
+  void pair_forward(const void *zin, void *z_out, const float *pm) {
     // 5, 6. triangle multiplication outgoing / incoming (AF2 Alg. 11, 12)
-    trimul_fwd(0, B(pl.z1), pm);
+    trimul_fwd(0, zin, pm);
     trimul_fwd(1, B(pl.tri[0].zout), pm);
     // 7, 8. triangle attention starting / ending node (AF2 Alg. 13, 14)
     triatt_fwd(0, B(pl.tri[1].zout), pm);
     triatt_fwd(1, B(pl.att[0].zout), pm);
     // 9. pair transition (AF2 Alg. 15)
     void *z6 = z_out ? z_out : B(pl.z6);
-    transition_fwd("pair_trans", B(pl.att[1].zout), B(pl.xz9), B(pl.h9), z6, Mz, Cz);
-    (void)HCt;
+    transition_fwd("pair_trans", B(pl.att[1].zout), B(pl.xz9), B(pl.h9), z6, k.Mz, k.Cz);
   }
 
   void transition_fwd(const std::string &pre, const void *x, void *xn, void *h, void *out, int64_t M, int64_t C) {
@@ -571,7 +594,9 @@ struct Drv {
                      D(wname)));
   }
 
-  void trimul_bwd(int t, const void *zin, const float *pm, float *dacc, void *dT) {
+  // dT: the incoming gradient (activation type); dcopy receives the updated
+  // running gradient (dT itself when null).
+  void trimul_bwd(int t, const void *zin, const float *pm, float *dacc, void *dT, void *dcopy = nullptr) {
     const std::string pre = t == 0 ? "tri_out" : "tri_in";
     const TriBufs &b = pl.tri[t];
     const int64_t R = k.R, Rp = k.Rp, Cz = k.Cz, Mz = k.Mz, cmul = k.cmul, ABG = k.ABG;
@@ -596,7 +621,37 @@ struct Drv {
     db(B(pl.G1), ABG, Mz, ABG, pre + ".b_abg");
     GemmOp x = mk(Mz, Cz, ABG, B(pl.G1), ABG, 0, W(pre + ".w_abg"), Cz, 1, B(pl.G2), Cz);
     gemm(x);
-    lnb(B(pl.G2), zin, pre + ".ln_in", dacc, dT, nullptr, Mz, (int)Cz);
+    lnb(B(pl.G2), zin, pre + ".ln_in", dacc, dcopy ? dcopy : dT, nullptr, Mz, (int)Cz);
+  }
+
+  // Steps 9-5 of the backward (the template pair stack block whole): from the
+  // incoming dz_out to the gradient at the pair input zin, accumulated in the
+  // fp32 dz_acc and copied to dz_last (activation type) by the last LayerNorm
+  // backward.
+  void pair_backward(const void *zin, const float *pm, const void *dz_out, void *dz_last) {
+    const int64_t R = k.R, Cz = k.Cz, Mz = k.Mz;
+    float *dz = Bf(pl.dz_acc);
+    void *dzT = B(pl.dzT);
+    // 9. pair transition
+    transition_bwd("pair_trans", B(pl.att[1].zout), B(pl.xz9), B(pl.h9), dz, dz_out, dzT, Mz, Cz, dz_out, false,
+                   dsc(4) ? nullptr : D("att_end.b_o"));
+    // 8, 7. triangle attention ending / starting node
+    for (int t = 1; t >= 0; --t) {
+      const AttBufs &b = pl.att[t];
+      const std::string pre = t == 0 ? "att_start" : "att_end";
+      const void *zt = t == 0 ? B(pl.tri[1].zout) : B(pl.att[0].zout);
+      // with dropout the update's gradient is dz scaled by the site's draw
+      const float *sc = dsc(3 + t);
+      if (sc) ck(dropout_apply(dzT, sc, nullptr, B(pl.drop_u), Mz, (int)Cz, (int)R, t, bf, s));
+      attention_bwd(2 + t, pre, B(b.xz), B(b.qkvg), B(b.oatt), B(b.og), Bf(b.lse), Bf(b.bias), pm,
+                    sc ? B(pl.drop_u) : dzT, Mz, Cz, sc == nullptr);
+      pair_bias_bwd(pre + ".w_b", B(b.xz), (int)k.Ht, t, 1);
+      lnb(B(pl.G2), zt, pre + ".ln", dz, dzT, nullptr, Mz, (int)Cz, nullptr,
+          t == 1 && !dsc(3) ? D("att_start.b_o") : nullptr);
+    }
+    // 6, 5. triangle multiplication incoming / outgoing
+    trimul_bwd(1, B(pl.tri[0].zout), pm, dz, dzT);
+    trimul_bwd(0, zin, pm, dz, dzT, dz_last);
   }
 
   void backward(const void *m0, const void *z0, const float *mm, const float *pm, const void *dm_out,
@@ -609,26 +664,7 @@ struct Drv {
     float *dm = Bf(pl.dm_acc), *dz = Bf(pl.dz_acc);
     void *dmT = B(pl.dmT), *dzT = B(pl.dzT);
 
-    // 9. pair transition
-    transition_bwd("pair_trans", B(pl.att[1].zout), B(pl.xz9), B(pl.h9), dz, dz_out, dzT, Mz, Cz, dz_out, false,
-                   dsc(4) ? nullptr : D("att_end.b_o"));
-    // 8, 7. triangle attention ending / starting node
-    for (int t = 1; t >= 0; --t) {
-      const AttBufs &b = pl.att[t];
-      const std::string pre = t == 0 ? "att_start" : "att_end";
-      const void *zin = t == 0 ? B(pl.tri[1].zout) : B(pl.att[0].zout);
-      // with dropout the update's gradient is dz scaled by the site's draw
-      const float *sc = dsc(3 + t);
-      if (sc) ck(dropout_apply(dzT, sc, nullptr, B(pl.drop_u), Mz, (int)Cz, (int)R, t, bf, s));
-      attention_bwd(2 + t, pre, B(b.xz), B(b.qkvg), B(b.oatt), B(b.og), Bf(b.lse), Bf(b.bias), pm,
-                    sc ? B(pl.drop_u) : dzT, Mz, Cz, sc == nullptr);
-      pair_bias_bwd(pre + ".w_b", B(b.xz), (int)k.Ht, t, 1);
-      lnb(B(pl.G2), zin, pre + ".ln", dz, dzT, nullptr, Mz, (int)Cz, nullptr,
-          t == 1 && !dsc(3) ? D("att_start.b_o") : nullptr);
-    }
-    // 6, 5. triangle multiplication incoming / outgoing
-    trimul_bwd(1, B(pl.tri[0].zout), pm, dz, dzT);
-    trimul_bwd(0, B(pl.z1), pm, dz, dzT);
+    pair_backward(B(pl.z1), pm, dz_out, dzT);
     // 4. outer product mean
     {
       ck(row_scale(dzT, Bf(pl.inv4), B(pl.G2), Mz, (int)Cz, bf, s, D("opm.b_o")));
@@ -684,9 +720,9 @@ struct Drv {
 
 }  // namespace
 
-size_t workspace_bytes(const evo_dims &d, int mode) {
+size_t workspace_bytes(const evo_dims &d, int mode, bool pair_only) {
   Plan p;
-  return make_plan(d, mode, p);
+  return make_plan(d, mode, p, pair_only);
 }
 
 int block_forward(const evo_dims &d, const float *p32, const bf16 *p16, const void *m_in, const void *z_in,
@@ -696,6 +732,27 @@ int block_forward(const evo_dims &d, const float *p32, const bf16 *p16, const vo
   drv.drop = dropout;
   if (ws_bytes < drv.pl.total) return EVO_ERR_WORKSPACE;
   drv.forward(m_in, z_in, m_out, z_out, msa_mask, pair_mask);
+  return drv.err == cudaSuccess ? EVO_OK : EVO_ERR_CUDA;
+}
+
+int pair_block_forward(const evo_dims &d, const float *p32, const bf16 *p16, const void *z_in, void *z_out,
+                       const float *pair_mask, void *ws, size_t ws_bytes, cudaStream_t s, const evo_dropout *dropout) {
+  Drv drv(d, p32, p16, ws, EVO_MODE_FWD, s, true);
+  if (ws_bytes < drv.pl.total) return EVO_ERR_WORKSPACE;
+  drv.drop = dropout;
+  drv.pair_forward(z_in, z_out, pair_mask);
+  return drv.err == cudaSuccess ? EVO_OK : EVO_ERR_CUDA;
+}
+
+int pair_block_backward(const evo_dims &d, const float *p32, const bf16 *p16, const void *z_in, const float *pair_mask,
+                        const void *dz_out, void *dz_in, float *dparams, void *ws, size_t ws_bytes, cudaStream_t s,
+                        const evo_dropout *dropout) {
+  Drv drv(d, p32, p16, ws, EVO_MODE_BWD, s, true);
+  if (ws_bytes < drv.pl.total) return EVO_ERR_WORKSPACE;
+  drv.drop = dropout;
+  drv.dparams = dparams;
+  drv.pair_forward(z_in, nullptr, pair_mask);
+  drv.pair_backward(z_in, pair_mask, dz_out, dz_in);
   return drv.err == cudaSuccess ? EVO_OK : EVO_ERR_CUDA;
 }
 

@@ -80,6 +80,13 @@ def lib():
                                             _vp]
         L.evo_block_bwd_dropout.argtypes = [P(CDims), _vp, _vp, _vp, _vp, _vp, _vp, P(CDropout), _vp, _vp, _vp, _vp,
                                             _vp, _vp, _sz, _vp]
+        L.evo_pair_param_count.argtypes = [P(CDims)]
+        L.evo_pair_param_count.restype = _sz
+        L.evo_pair_param_layout.argtypes = [P(CDims), P(CParamEntry), ctypes.c_int]
+        L.evo_pair_workspace_size.argtypes = [P(CDims), ctypes.c_int, P(_sz)]
+        L.evo_pair_params_to_bf16.argtypes = [P(CDims), _vp, _vp, _vp]
+        L.evo_pair_block_fwd.argtypes = [P(CDims), _vp, _vp, _vp, _vp, _vp, P(CDropout), _vp, _sz, _vp]
+        L.evo_pair_block_bwd.argtypes = [P(CDims), _vp, _vp, _vp, _vp, P(CDropout), _vp, _vp, _vp, _vp, _sz, _vp]
         L.evo_block_fwd_noalloc.argtypes = [P(CDims), _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]
         L.evo_stack_fwd.argtypes = [P(CDims), ctypes.c_int, _vp, _vp, _sz, _vp, _vp, _vp, _vp, _vp, _sz, _vp]
         L.evo_get_error.argtypes = [_vp]
@@ -194,6 +201,52 @@ def block_bwd_dropout(cd, params, params_bf16, m, z, msa_mask, pair_mask, dropou
                                        _ptr(msa_mask), _ptr(pair_mask), ctypes.byref(c) if c is not None else None,
                                        _ptr(dm_out), _ptr(dz_out), _ptr(dm_in), _ptr(dz_in), _ptr(dparams), _ptr(ws),
                                        ws.numel() * ws.element_size(), _stream(stream)), "evo_block_bwd_dropout")
+
+
+def pair_param_count(cd):
+    return int(lib().evo_pair_param_count(ctypes.byref(cd)))
+
+
+def pair_param_layout(cd):
+    """[(name, offset, shape)] of the template pair block's flat parameter buffer."""
+    n = lib().evo_pair_param_layout(ctypes.byref(cd), None, 0)
+    arr = (CParamEntry * n)()
+    lib().evo_pair_param_layout(ctypes.byref(cd), arr, n)
+    return [(e.name.decode(), e.offset, tuple(e.shape[i] for i in range(e.ndim))) for e in arr]
+
+
+def pair_workspace(cd, mode, device):
+    import torch
+    n = _sz(0)
+    _check(lib().evo_pair_workspace_size(ctypes.byref(cd), mode, ctypes.byref(n)), "evo_pair_workspace_size")
+    return torch.empty(n.value, dtype=torch.uint8, device=device)
+
+
+def pair_bf16_params(cd, params):
+    """BF16 copy of the pair block's flat parameter buffer (None for the FP32 path)."""
+    import torch
+    if cd.act_dtype != EVO_BF16:
+        return None
+    p16 = torch.empty(pair_param_count(cd), dtype=torch.bfloat16, device=params.device)
+    _check(lib().evo_pair_params_to_bf16(ctypes.byref(cd), _ptr(params), _ptr(p16), _stream(None)),
+           "evo_pair_params_to_bf16")
+    return p16
+
+
+def pair_block_fwd(cd, params, params_bf16, z, z_out, pair_mask, ws, dropout=None, stream=None):
+    """Template pair stack block forward (AF2 Alg. 16)."""
+    c = _dropout_struct(dropout)
+    _check(lib().evo_pair_block_fwd(ctypes.byref(cd), _ptr(params), _ptr(params_bf16), _ptr(z), _ptr(z_out),
+                                    _ptr(pair_mask), ctypes.byref(c) if c is not None else None, _ptr(ws),
+                                    ws.numel() * ws.element_size(), _stream(stream)), "evo_pair_block_fwd")
+
+
+def pair_block_bwd(cd, params, params_bf16, z, pair_mask, dz_out, dz_in, dparams, ws, dropout=None, stream=None):
+    c = _dropout_struct(dropout)
+    _check(lib().evo_pair_block_bwd(ctypes.byref(cd), _ptr(params), _ptr(params_bf16), _ptr(z), _ptr(pair_mask),
+                                    ctypes.byref(c) if c is not None else None, _ptr(dz_out), _ptr(dz_in),
+                                    _ptr(dparams), _ptr(ws), ws.numel() * ws.element_size(), _stream(stream)),
+           "evo_pair_block_bwd")
 
 
 def block_fwd_noalloc(cd, params, params_bf16, m, z, m_out, z_out, msa_mask, pair_mask, stream=None):

@@ -61,3 +61,26 @@ def test_null_and_misaligned_pointers_are_rejected_before_any_launch(built_lib):
 def test_strerror_and_version(built_lib):
     assert evo.strerror(evo.EVO_ERR_TIMEOUT) == "bounded device wait timed out"
     assert b"sm_103a" in built_lib.evo_version()
+
+
+@pytest.mark.parametrize("d", [synth.DIMS_TEMPLATE, synth.DIMS_TEMPLATE.replace(n_res=37),
+                               synth.DIMS_TINY.replace(pair_only=1)])
+def test_pair_param_layout_matches_generator_table(built_lib, d):
+    cd = evo.cdims(d, evo.EVO_BF16)
+    lay = evo.pair_param_layout(cd)
+    ref, total = synth.param_layout(d)
+    assert [(n, o, s) for n, o, s, _ in ref] == lay
+    assert evo.pair_param_count(cd) == total
+    assert all(o % 64 == 0 for _, o, _ in lay)
+
+
+def test_pair_workspace_is_the_pair_share_of_the_block(built_lib):
+    d = synth.DIMS_TEMPLATE
+    cd = evo.cdims(d, evo.EVO_BF16)
+    import ctypes
+    n = ctypes.c_size_t(0)
+    assert evo.lib().evo_pair_workspace_size(ctypes.byref(cd), evo.EVO_MODE_BWD, ctypes.byref(n)) == evo.EVO_OK
+    full = ctypes.c_size_t(0)
+    cdf = evo.cdims(d.replace(pair_only=0, n_seq=8), evo.EVO_BF16)
+    assert evo.lib().evo_workspace_size(ctypes.byref(cdf), evo.EVO_MODE_BWD, ctypes.byref(full)) == evo.EVO_OK
+    assert 0 < n.value < full.value
