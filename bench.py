@@ -60,6 +60,16 @@ def block_fwd_flops(d) -> float:
     return float(f)
 
 
+def pair_block_fwd_flops(d) -> float:
+    """Algorithmic forward flops of one template pair stack block (the pair steps alone)."""
+    R, Cz = d.n_res, d.c_z
+    Mz, HCt = R * R, d.h_tri * d.c_tri
+    f = 2 * (2 * Mz * Cz * (4 * d.c_mul + Cz) + 2 * d.c_mul * R ** 3 + 2 * Mz * d.c_mul * Cz)
+    f += 2 * (2 * Mz * Cz * d.h_tri + 2 * Mz * Cz * 4 * HCt + 4 * R * d.h_tri * R * R * d.c_tri + 2 * Mz * HCt * Cz)
+    f += 2 * 2 * Mz * Cz * d.trans_n * Cz
+    return float(f)
+
+
 def step_flops(d) -> float:
     return 3.0 * block_fwd_flops(d)
 
@@ -532,6 +542,36 @@ def other_workload(args):
     torch.cuda.reset_peak_memory_stats()
     w = args.workload
     extra = {}
+    if w == "template_pair":
+        # template pair stack block fwd+bwd (AF2 Alg. 16) at the template dims,
+        # N_res = 256 crop, one template, training-mode dropout
+        d = synth.DIMS_TEMPLATE
+        cd = evo.cdims(d, evo.EVO_BF16)
+        prob = synth.make_problem(d, 32, pad_frac=0.05)
+        params = torch.tensor(prob["params"], device=dev)
+        p16 = evo.pair_bf16_params(cd, params)
+        z = torch.tensor(prob["z"], device=dev).to(torch.bfloat16)
+        pm = torch.tensor(prob["pair_mask"], device=dev)
+        gz = torch.tensor(prob["gz"], device=dev).to(torch.bfloat16)
+        drop = {k: torch.tensor(v, device=dev) for k, v in synth.make_dropout(d, 32).items()}
+        zo, dz, dp = torch.empty_like(z), torch.empty_like(z), torch.zeros_like(params)
+        wsf, wsb = evo.pair_workspace(cd, evo.EVO_MODE_FWD, dev), evo.pair_workspace(cd, evo.EVO_MODE_BWD, dev)
+
+        def fn():
+            evo.pair_block_fwd(cd, params, p16, z, zo, pm, wsf, drop)
+            evo.pair_block_bwd(cd, params, p16, z, pm, gz, dz, dp, wsb, drop)
+
+        if not args.no_tune:
+            extra["gemm_tiles"] = autotune(evo, fn, TUNE_PASSES)
+        ms, clk = timed(fn, args.steps, max(3, args.warmup))
+        flops = 3.0 * pair_block_fwd_flops(d)
+        desc = "template pair stack block fwd+bwd, N_res=256 c_t=64 (4 heads x 16, c_mul 64), BF16, dropout"
+        line = {"workload": w, "metric": desc, "value": flops / (ms / 1e3) / 1e12, "unit": "TFLOP/s",
+                "ms_per_step": ms, "steps": args.steps, "flops_per_step": flops,
+                "peak_mem_gb": torch.cuda.max_memory_allocated() / 1e9, "clocks": clk, "data": "synthetic"}
+        line.update(extra)
+        print(json.dumps(line), flush=True)
+        return 0
     if w in ("small_fp32_fwd", "long2048", "extra_msa"):
         if w == "small_fp32_fwd":
             d, act, bwd = synth.DIMS_SMALL_FP32, evo.EVO_F32, False
@@ -681,7 +721,8 @@ def main():
                     help="replay the step as one captured CUDA graph (the default; kept for older command lines)")
     ap.add_argument("--eager", action="store_true", help="time eager launches instead of a CUDA graph replay")
     ap.add_argument("--workload", default="train_crop",
-                    choices=["train_crop", "small_fp32_fwd", "extra_msa", "stack48", "long2048", "batch16"])
+                    choices=["train_crop", "small_fp32_fwd", "extra_msa", "stack48", "long2048", "batch16",
+                             "template_pair"])
     args = ap.parse_args()
     args.graph = not args.eager
     if args.warmup < 3 and args.impl == "ours":
