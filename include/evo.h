@@ -180,7 +180,7 @@ int evo_block_fwd_noalloc(const evo_dims *d, const float *params, const void *pa
                           const void *m_in, const void *z_in, void *m_out, void *z_out,
                           const float *msa_mask, const float *pair_mask, evo_stream_t stream);
 
-/* Template pair stack block (AF2 Alg. 16; SURVEY next row): the pair half of
+/* Template pair stack block (AF2 Alg. 16): the pair half of
  * the block -- triangle multiplication outgoing and incoming, triangle
  * attention starting and ending node, pair transition, with the same
  * dropout sites (msa_row ignored) -- on z alone.  Only the pair fields of
