@@ -109,3 +109,19 @@ def test_dropout_gradients_match_central_differences():
     fd_check(dz, lambda e: loss(m, z + e, p))
     for name in ("row.w_o", "tri_out.w_o", "att_end.w_o", "att_start.b_o", "tri_in.b_o"):
         fd_check(dp[name], lambda e, n=name: loss(m, z, {**p, n: p[n] + e}))
+
+
+def test_generator_draws_are_seeded_and_have_the_rates():
+    d = synth.Dims(n_seq=2, n_res=256)
+    a, b = synth.make_dropout(d, 5), synth.make_dropout(d, 5)
+    c = synth.make_dropout(d, 6)
+    for name, rate, _ in synth.DROPOUT_SITES:
+        assert np.array_equal(a[name], b[name])
+        assert not np.array_equal(a[name], c[name])
+        keep = 1.0 / (1.0 - rate)
+        vals = np.unique(a[name])
+        assert set(vals.tolist()) <= {0.0, np.float32(keep)}
+        frac = float((a[name] == 0).mean())
+        n = a[name].size
+        # within five standard deviations of the rate
+        assert abs(frac - rate) <= 5 * np.sqrt(rate * (1 - rate) / n), (name, frac)
