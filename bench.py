@@ -133,6 +133,18 @@ def dist_setup():
     return world, rank, local
 
 
+def whole_job_rate(local_ms, world, flops_per_unit, units, device):
+    """Weak-scaling whole-job rate: every rank processed `units` units of
+    `flops_per_unit` in `local_ms`; the job takes the slowest rank's time
+    (max over ranks) and processed world x units.  Returns (max_ms, TFLOP/s)."""
+    import torch
+    t = torch.tensor([local_ms], device=device, dtype=torch.float64)
+    if world > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    max_ms = float(t.item())
+    return max_ms, world * flops_per_unit * units / (max_ms / 1e3) / 1e12
+
+
 def run_oracle_step(d, prob):
     from oracle import evoformer as O
     from paper_2207_05477_gb300 import synth
@@ -333,11 +345,7 @@ def ours_arm(args):
     step_stats = {"p10": pick(0.1), "median": pick(0.5), "p90": pick(0.9)}
     if evo.get_error() != evo.EVO_OK:
         raise RuntimeError("device error word set during the timed steps")
-    t = torch.tensor([dev_ms], device=dev, dtype=torch.float64)
-    if world > 1:
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-    max_ms = float(t.item())
-    value = world * step_flops(d) * args.steps / (max_ms / 1e3) / 1e12
+    max_ms, value = whole_job_rate(dev_ms, world, step_flops(d), args.steps, dev)
 
     # ---- end to end through the C ABI with host buffers: H2D of the step's inputs, D2H of its results
     host = {k: torch.tensor(prob[k]).to(tdt if k in ("m", "z", "gm", "gz") else torch.float32).pin_memory()
@@ -369,10 +377,7 @@ def ours_arm(args):
     e1.record(stream)
     torch.cuda.synchronize()
     e2e_ms = e0.elapsed_time(e1) / e2e_steps
-    te = torch.tensor([e2e_ms], device=dev, dtype=torch.float64)
-    if world > 1:
-        torch.distributed.all_reduce(te, op=torch.distributed.ReduceOp.MAX)
-    e2e_value = world * step_flops(d) / (float(te.item()) / 1e3) / 1e12
+    e2e_max_ms, e2e_value = whole_job_rate(e2e_ms, world, step_flops(d), 1, dev)
 
     # ---- plain FP32 path, same workload (the comparison the target names)
     fp32 = None
@@ -473,7 +478,7 @@ def ours_arm(args):
                        "gemm_tiles": ("autotuned before the warm-up: " + json.dumps(tuned)) if tuned else "built-in"},
             "clocks": clk, "gpu_launches": launches, "step_ms": step_stats,
             "e2e": {"value": e2e_value, "unit": "TFLOP/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                    "ms_per_step": float(te.item())},
+                    "ms_per_step": e2e_max_ms},
             "roofline": roof, "cpu_baseline": cpu, "fp32_plain": fp32, "kernels": kernels,
             "paper_context": {"ms_per_layer_fwd_bwd": 32.47, "hardware": "A100 40G, FP16, PPFold DAP=1 BP=1"},
         }
