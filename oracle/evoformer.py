@@ -27,7 +27,10 @@ design notes of the repository):
   * outer-product-mean: the output bias sits inside the division by
     (1e-3 + number of valid sequence pairs);
   * triangle multiplication: the gate multiplies after the output Linear;
-  * softmax scale 1/sqrt(head dim) on the logits.
+  * softmax scale 1/sqrt(head dim) on the logits;
+  * a template pair stack block (AF2 Alg. 16) is the pair half of Alg. 6 with
+    the same dropout sites; the LayerNorm applied after the whole template
+    stack is not part of a block.
 
 Gradients: the backward of the block is the exact gradient of this forward,
 taken by reverse-mode differentiation of the FP64 graph (``torch.autograd``);
