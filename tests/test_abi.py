@@ -84,3 +84,19 @@ def test_pair_workspace_is_the_pair_share_of_the_block(built_lib):
     cdf = evo.cdims(d.replace(pair_only=0, n_seq=8), evo.EVO_BF16)
     assert evo.lib().evo_workspace_size(ctypes.byref(cdf), evo.EVO_MODE_BWD, ctypes.byref(full)) == evo.EVO_OK
     assert 0 < n.value < full.value
+
+
+def test_stack_stride_and_count_are_checked_before_any_launch(built_lib):
+    cd = evo.cdims(synth.DIMS_SMALL_FP32, evo.EVO_F32)
+    L = built_lib
+    null = ctypes.c_void_p(0)
+    n = evo.param_count(cd)
+    stride = (n + 127) // 128 * 128
+    for nb, st in ((2, stride + 64), (2, stride - 128), (-1, stride)):
+        r = L.evo_stack_fwd(ctypes.byref(cd), nb, null, null, ctypes.c_size_t(st), null, null, null, null, null,
+                            ctypes.c_size_t(0), null)
+        assert r == evo.EVO_ERR_INVALID_ARG, (nb, st)
+    # zero blocks is the identity and launches nothing
+    r = L.evo_stack_fwd(ctypes.byref(cd), 0, null, null, ctypes.c_size_t(stride), null, null, null, null, null,
+                        ctypes.c_size_t(0), null)
+    assert r == evo.EVO_OK
