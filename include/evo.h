@@ -203,6 +203,45 @@ int evo_pair_block_bwd(const evo_dims *d, const float *params, const void *param
                        const void *dz_out, void *dz_in, float *dparams,
                        void *workspace, size_t ws_bytes, evo_stream_t stream);
 
+/* Fused training update over a flat parameter buffer (Sec. 3.2, tensor
+ * fusion: the stages of its table of kernel launches -- gradient clip by
+ * global norm, optimizer update, EMA -- over all parameters at once).  For
+ * every element, with G the L2 norm of the whole of grad:
+ *   g  = grad * (clip_norm > 0 ? clip_norm / max(G, clip_norm) : 1)
+ *   m  = beta1 m + (1 - beta1) g,   v = beta2 v + (1 - beta2) g^2
+ *   w -= lr (m / (1 - beta1^step)) / (sqrt(v / (1 - beta2^step)) + eps)
+ *   e  = ema_decay e + (1 - ema_decay) w          (when ema is given)
+ *   params_bf16 = bf16(w), round to nearest even   (when given)
+ * (Adam as Kingma and Ba 2015, Algorithm 1; AlphaFold2's settings are lr 1e-3,
+ * beta1 0.9, beta2 0.999, eps 1e-6, clip_norm 0.1, ema_decay 0.999.)
+ * Two launches: a deterministic partial sum of squares, then one pass that
+ * clips, updates and averages; the result does not depend on the run.
+ *  - n elements in each buffer (fp32 device buffers params, grad, exp_avg,
+ *    exp_avg_sq, ema; bf16 params_bf16), all caller-owned, 256-byte aligned,
+ *    none overlapping another.  The flat buffer of one or several blocks
+ *    (evo_param_layout, padding included: a zero gradient on the padding
+ *    leaves it at zero) is the intended argument.  grad is not modified.
+ *  - exp_avg and exp_avg_sq start at zero before step 1; ema (may be NULL)
+ *    usually starts as a copy of params; params_bf16 may be NULL.
+ *  - grad_norm (may be NULL): a device float that receives G (before the
+ *    clip), 4-byte aligned.
+ *  - workspace: evo_adam_workspace_size(n) bytes of device scratch.
+ *  - n == 0 is a no-op.  EVO_ERR_INVALID_ARG for a NULL required pointer,
+ *    step < 1, a beta outside [0, 1), eps <= 0, a non-finite lr or eps, a
+ *    NaN clip_norm, or (with ema) a decay outside [0, 1];
+ *    EVO_ERR_ALIGNMENT, EVO_ERR_WORKSPACE as for the block. */
+typedef struct evo_adam {
+  float lr, beta1, beta2, eps;
+  float clip_norm;  /* <= 0: no clipping */
+  float ema_decay;  /* read only when ema is given */
+  int32_t step;     /* Adam step number t, 1 for the first update */
+} evo_adam;
+
+size_t evo_adam_workspace_size(size_t n);
+int evo_adam_step(const evo_adam *h, size_t n, float *params, const float *grad,
+                  float *exp_avg, float *exp_avg_sq, float *ema, void *params_bf16,
+                  float *grad_norm, void *workspace, size_t ws_bytes, evo_stream_t stream);
+
 /* Waits for the stream, then returns and clears the device error word:
  * EVO_OK, or EVO_ERR_TIMEOUT if a bounded in-kernel wait gave up since the
  * last call. */

@@ -55,6 +55,12 @@ class CTuneEntry(ctypes.Structure):
                 ("splits", ctypes.c_int32), ("candidates", ctypes.c_int32)]
 
 
+class CAdam(ctypes.Structure):
+    _fields_ = [("lr", ctypes.c_float), ("beta1", ctypes.c_float), ("beta2", ctypes.c_float),
+                ("eps", ctypes.c_float), ("clip_norm", ctypes.c_float), ("ema_decay", ctypes.c_float),
+                ("step", ctypes.c_int32)]
+
+
 _lib = None
 _vp, _sz = ctypes.c_void_p, ctypes.c_size_t
 
@@ -89,6 +95,9 @@ def lib():
         L.evo_pair_block_bwd.argtypes = [P(CDims), _vp, _vp, _vp, _vp, P(CDropout), _vp, _vp, _vp, _vp, _sz, _vp]
         L.evo_block_fwd_noalloc.argtypes = [P(CDims), _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]
         L.evo_stack_fwd.argtypes = [P(CDims), ctypes.c_int, _vp, _vp, _sz, _vp, _vp, _vp, _vp, _vp, _sz, _vp]
+        L.evo_adam_workspace_size.argtypes = [_sz]
+        L.evo_adam_workspace_size.restype = _sz
+        L.evo_adam_step.argtypes = [P(CAdam), _sz, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _sz, _vp]
         L.evo_get_error.argtypes = [_vp]
         L.evo_debug_wait_timeout.argtypes = [ctypes.c_longlong, _vp]
         L.evo_profile_only.argtypes = [ctypes.c_char_p]
@@ -267,6 +276,22 @@ def stack_fwd(cd, n_blocks, params, params_bf16, param_stride, m, z, msa_mask, p
     _check(lib().evo_stack_fwd(ctypes.byref(cd), n_blocks, _ptr(params), _ptr(params_bf16), param_stride, _ptr(m),
                                _ptr(z), _ptr(msa_mask), _ptr(pair_mask), _ptr(ws), ws.numel() * ws.element_size(),
                                _stream(stream)), "evo_stack_fwd")
+
+
+def adam_hyper(step, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-6, clip_norm=0.1, ema_decay=0.999):
+    """evo_adam for step number `step` (defaults: AlphaFold2's training settings)."""
+    return CAdam(lr, beta1, beta2, eps, clip_norm, ema_decay, step)
+
+
+def adam_workspace_size(n):
+    return int(lib().evo_adam_workspace_size(n))
+
+
+def adam_step(h, params, grad, exp_avg, exp_avg_sq, ws, ema=None, params_bf16=None, grad_norm=None, stream=None):
+    """evo_adam_step over flat buffers of params.numel() elements."""
+    _check(lib().evo_adam_step(ctypes.byref(h), params.numel(), _ptr(params), _ptr(grad), _ptr(exp_avg),
+                               _ptr(exp_avg_sq), _ptr(ema), _ptr(params_bf16), _ptr(grad_norm), _ptr(ws),
+                               ws.numel() * ws.element_size(), _stream(stream)), "evo_adam_step")
 
 
 def get_error(stream=None):

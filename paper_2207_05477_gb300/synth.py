@@ -312,3 +312,38 @@ def make_dropout(d: Dims, seed: int = 32, scale_rates: float = 1.0) -> dict:
         keep = (u >= rate).astype(np.float64)
         out[name] = (keep / (1.0 - rate)).astype(np.float32)
     return out
+
+
+TAG_ADAM = 20  # + index of the tensor in ADAM_TENSORS
+# Buffers of the fused training update and the scale of their values: weights
+# about N(0, 0.05^2), gradients about N(0, 0.01^2), the moments of a run
+# that has taken a few steps.
+ADAM_TENSORS = ("params", "grad", "exp_avg", "exp_avg_sq", "ema")
+
+
+def make_adam_state(n: int, seed: int = 32, fresh: bool = False, base: int = 1 << 20) -> dict:
+    """Seeded FP32 buffers of n elements for the fused training update.
+
+    Arrays longer than ``base`` repeat a ``base``-element draw, each repeat
+    multiplied by its own factor in [0.5, 1.5), so that large buffers are
+    cheap to make and still differ from tile to tile.  ``fresh``: the state
+    before the first step (zero moments, EMA equal to the parameters)."""
+    def draw(k, sd):
+        m = min(n, base)
+        x = normals(stream_key(seed, TAG_ADAM + k), m) * sd
+        if n <= base:
+            return x.astype(np.float32)
+        reps = (n + base - 1) // base
+        f = 0.5 + uniforms(stream_key(seed, TAG_ADAM + 10 + k), reps)
+        return (f.astype(np.float32)[:, None] * x.astype(np.float32)[None, :]).reshape(-1)[:n]
+
+    out = {"params": draw(0, 0.05), "grad": draw(1, 0.01)}
+    if fresh:
+        out["exp_avg"] = np.zeros(n, np.float32)
+        out["exp_avg_sq"] = np.zeros(n, np.float32)
+        out["ema"] = out["params"].copy()
+    else:
+        out["exp_avg"] = draw(2, 1e-3)
+        out["exp_avg_sq"] = np.square(draw(3, 1e-2))
+        out["ema"] = out["params"] + draw(4, 1e-3)
+    return out

@@ -100,3 +100,32 @@ def test_stack_stride_and_count_are_checked_before_any_launch(built_lib):
     r = L.evo_stack_fwd(ctypes.byref(cd), 0, null, null, ctypes.c_size_t(stride), null, null, null, null, null,
                         ctypes.c_size_t(0), null)
     assert r == evo.EVO_OK
+
+
+def test_adam_step_arguments_are_checked_before_any_launch(built_lib):
+    L = built_lib
+    null = ctypes.c_void_p(0)
+    a = ctypes.c_void_p(0x100000)  # 256-byte aligned, never dereferenced
+    odd = ctypes.c_void_p(0x100000 + 16)
+    n = 1000
+    ws = evo.adam_workspace_size(n)
+    assert ws > 0 and evo.adam_workspace_size(0) == 0
+
+    def call(h, n=n, p=a, g=a, m=a, v=a, e=null, pb=null, gn=null, w=a, wsb=ws):
+        return L.evo_adam_step(ctypes.byref(h) if h is not None else None, n, p, g, m, v, e, pb, gn, w,
+                               ctypes.c_size_t(wsb), null)
+
+    assert call(None) == evo.EVO_ERR_INVALID_ARG
+    for bad in (evo.adam_hyper(0), evo.adam_hyper(1, beta1=1.0), evo.adam_hyper(1, beta2=-0.1),
+                evo.adam_hyper(1, eps=0.0), evo.adam_hyper(1, lr=float("inf")),
+                evo.adam_hyper(1, clip_norm=float("nan"))):
+        assert call(bad) == evo.EVO_ERR_INVALID_ARG
+    assert call(evo.adam_hyper(1, ema_decay=1.5), e=a) == evo.EVO_ERR_INVALID_ARG
+    h = evo.adam_hyper(1)
+    assert call(h, n=0, p=null, g=null, m=null, v=null, w=null, wsb=0) == evo.EVO_OK  # empty: nothing to do
+    assert call(h, p=null) == evo.EVO_ERR_INVALID_ARG
+    assert call(h, w=null) == evo.EVO_ERR_INVALID_ARG
+    assert call(h, g=odd) == evo.EVO_ERR_ALIGNMENT
+    assert call(h, e=odd) == evo.EVO_ERR_ALIGNMENT
+    assert call(h, pb=odd) == evo.EVO_ERR_ALIGNMENT
+    assert call(h, wsb=ws - 8) == evo.EVO_ERR_WORKSPACE
