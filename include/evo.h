@@ -55,7 +55,7 @@ enum {
 
 enum { EVO_F32 = 0, EVO_BF16 = 1 };           /* act_dtype */
 enum { EVO_COL_ATTENTION = 0, EVO_COL_GLOBAL = 1 }; /* msa_col_mode */
-enum { EVO_MODE_FWD = 0, EVO_MODE_BWD = 1 };  /* workspace query mode */
+enum { EVO_MODE_FWD = 0, EVO_MODE_BWD = 1, EVO_MODE_INFER = 2 };  /* workspace query mode */
 
 /* Sizes of one block.  Defaults of the paper's Evoformer (Table "model
  * settings", Table "FastFold vs PPFold": C_m=256, C_z=128, 8 heads):
@@ -93,9 +93,10 @@ int evo_params_bf16_size(const evo_dims *d, size_t *bytes);
 int evo_params_to_bf16(const evo_dims *d, const float *params, void *params_bf16,
                        evo_stream_t stream);
 
-/* Workspace bytes for evo_block_fwd (mode EVO_MODE_FWD) or evo_block_bwd
- * (EVO_MODE_BWD).  The workspace is scratch owned by the caller; its
- * content on entry is irrelevant and on exit undefined. */
+/* Workspace bytes for evo_block_fwd (mode EVO_MODE_FWD), evo_block_bwd
+ * (EVO_MODE_BWD) or evo_block_fwd_infer (EVO_MODE_INFER).  The workspace is
+ * scratch owned by the caller; its content on entry is irrelevant and on
+ * exit undefined. */
 int evo_workspace_size(const evo_dims *d, int mode, size_t *bytes);
 
 /* Forward of one block: (m_out, z_out) = Evoformer(m_in, z_in).
@@ -105,6 +106,24 @@ int evo_block_fwd(const evo_dims *d, const float *params, const void *params_bf1
                   const void *m_in, const void *z_in, void *m_out, void *z_out,
                   const float *msa_mask, const float *pair_mask,
                   void *workspace, size_t ws_bytes, evo_stream_t stream);
+
+/* Forward of one block for inference, with the same arguments, layouts,
+ * in-place rules and errors as evo_block_fwd and the same result, bit for
+ * bit, in a workspace about a quarter of EVO_MODE_FWD's: size it with
+ * evo_workspace_size(d, EVO_MODE_INFER, ...).  The sub-modules' scratch
+ * buffers share one region, each dead once its sub-module has written its
+ * output, and the residual streams alternate between two buffers each, so
+ * the workspace is the largest sub-module's scratch plus two m and two z
+ * buffers (about 3.8 KB per pair position at the paper's dims in BF16
+ * instead of 15 KB).  It carries the paper's memory read/write in-place
+ * (Sec. 3.4.3: one allocation reused instead of one per intermediate) across
+ * the block's sub-modules, which lets one GPU run a block on sequences of
+ * several thousand residues without the subbatching of Sec. 3.4.4.
+ * Evaluation mode only. */
+int evo_block_fwd_infer(const evo_dims *d, const float *params, const void *params_bf16,
+                        const void *m_in, const void *z_in, void *m_out, void *z_out,
+                        const float *msa_mask, const float *pair_mask,
+                        void *workspace, size_t ws_bytes, evo_stream_t stream);
 
 /* Training-mode dropout of the block (AF2 Alg. 6): each non-null pointer is
  * the scale of one site's residual update, fp32 on the device, 256-byte

@@ -47,7 +47,7 @@ int evo_params_to_bf16(const evo_dims *d, const float *params, void *params_bf16
 }
 
 int evo_workspace_size(const evo_dims *d, int mode, size_t *bytes) {
-  if (!bytes || (mode != EVO_MODE_FWD && mode != EVO_MODE_BWD)) return EVO_ERR_INVALID_ARG;
+  if (!bytes || (mode != EVO_MODE_FWD && mode != EVO_MODE_BWD && mode != EVO_MODE_INFER)) return EVO_ERR_INVALID_ARG;
   const int v = validate_dims(d);
   if (v != EVO_OK) return v;
   *bytes = workspace_bytes(*d, mode);
@@ -94,6 +94,22 @@ int evo_block_fwd_dropout(const evo_dims *d, const float *params, const void *pa
   if (dropout_ok(dropout) != EVO_OK) return EVO_ERR_ALIGNMENT;
   return block_forward(*d, params, (const bf16 *)params_bf16, m_in, z_in, m_out, z_out, msa_mask, pair_mask,
                        workspace, ws_bytes, (cudaStream_t)stream, dropout);
+}
+
+int evo_block_fwd_infer(const evo_dims *d, const float *params, const void *params_bf16, const void *m_in,
+                        const void *z_in, void *m_out, void *z_out, const float *msa_mask, const float *pair_mask,
+                        void *workspace, size_t ws_bytes, evo_stream_t stream) {
+  const int v = validate_dims(d);
+  if (v != EVO_OK) return v;
+  const bool bf = d->act_dtype == EVO_BF16;
+  if (!params || !m_in || !z_in || !m_out || !z_out || !msa_mask || !pair_mask || !workspace || (bf && !params_bf16))
+    return EVO_ERR_INVALID_ARG;
+  for (const void *p : {(const void *)params, m_in, z_in, (const void *)m_out, (const void *)z_out,
+                        (const void *)msa_mask, (const void *)pair_mask, (const void *)workspace})
+    if (!aligned256(p)) return EVO_ERR_ALIGNMENT;
+  if (bf && !aligned256(params_bf16)) return EVO_ERR_ALIGNMENT;
+  return block_forward_infer(*d, params, (const bf16 *)params_bf16, m_in, z_in, m_out, z_out, msa_mask, pair_mask,
+                             workspace, ws_bytes, (cudaStream_t)stream);
 }
 
 int evo_block_bwd_dropout(const evo_dims *d, const float *params, const void *params_bf16, const void *m_in,

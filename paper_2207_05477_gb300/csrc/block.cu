@@ -161,7 +161,73 @@ struct Dims2 {
   }
 };
 
+// Forward-only plan (inference; no backward reads the intermediates).  Once a
+// sub-module has written its output nothing else of it is read again, so the
+// scratch of every sub-module starts at one common offset, and the residual
+// streams alternate between two buffers each: m1, m2, then m3 over m1; z1 and
+// a second buffer, the five pair updates writing them in turn.  Every buffer
+// keeps the size it has in the full plan.
+size_t make_infer_plan(const evo_dims &d, Plan &p, bool pair_only) {
+  const Dims2 k(d, pair_only);
+  const size_t ts = d.act_dtype == EVO_BF16 ? 2 : 4;
+  p = Plan{};
+  size_t off = 0, top = 0;
+  auto T = [&](int64_t elems) {
+    size_t o = off;
+    off += ((size_t)elems * ts + 255) / 256 * 256;
+    return o;
+  };
+  auto F = [&](int64_t elems) {
+    size_t o = off;
+    off += ((size_t)elems * 4 + 255) / 256 * 256;
+    return o;
+  };
+  p.m1 = T(k.Mm * k.Cm), p.m2 = T(k.Mm * k.Cm), p.m3 = p.m1;
+  p.z1 = T(k.Mz * k.Cz);
+  const size_t zb = T(k.Mz * k.Cz);
+  p.tri[0].zout = zb, p.tri[1].zout = p.z1, p.att[0].zout = zb, p.att[1].zout = p.z1, p.z6 = zb;
+  const size_t scr = off;
+  p.drop_u = scr;  // evaluation only: no dropout
+  auto begin = [&] { off = scr; };
+  auto end = [&] { top = std::max(top, off); };
+  begin();  // 1. MSA row attention
+  p.xm1 = T(k.Mm * k.Cm), p.xz1 = T(k.Mz * k.Cz), p.bias1 = F(k.Hm * k.Mz), p.qkvg1 = T(k.Mm * k.QKm);
+  p.oatt1 = T(k.Mm * k.HCm), p.og1 = T(k.Mm * k.HCm), p.lse1 = F(k.S * k.Hm * k.R);
+  end();
+  begin();  // 2. MSA column attention (or global column attention)
+  p.xm2 = T(k.Mm * k.Cm), p.qkvg2 = T(k.Mm * k.QKc), p.oatt2 = T(k.Mm * k.HCm), p.og2 = T(k.Mm * k.HCm);
+  p.lse2 = F(k.R * k.Hm * k.S), p.gq = F(k.R * k.HCm), p.gob = F(k.R * k.HCm), p.gst = F(k.R * k.Hm * 2);
+  end();
+  begin();  // 3. MSA transition
+  p.xm3 = T(k.Mm * k.Cm), p.h3 = T(k.Mm * k.n * k.Cm);
+  end();
+  const int64_t Mz_opm = pair_only ? 0 : k.Mz;
+  begin();  // 4. outer product mean
+  p.xm4 = T(k.Mm * k.Cm), p.ab4 = T(2 * k.Mm * k.co), p.O4 = T(Mz_opm * k.co * k.co), p.inv4 = F(Mz_opm);
+  end();
+  for (int t = 0; t < 2; ++t) {  // 5, 6. triangle multiplications
+    TriBufs &b = p.tri[t];
+    begin();
+    b.xz = T(k.Mz * k.Cz), b.abg = T(k.Mz * k.ABG), b.A = T(k.cmul * k.R * k.Rp), b.B = T(k.cmul * k.R * k.Rp);
+    b.X = T(k.cmul * k.R * k.Rp), b.xo = T(k.Mz * k.cmul), b.y = T(k.Mz * k.Cz);
+    end();
+  }
+  for (int t = 0; t < 2; ++t) {  // 7, 8. triangle attentions
+    AttBufs &b = p.att[t];
+    begin();
+    b.xz = T(k.Mz * k.Cz), b.bias = F(k.Ht * k.Mz), b.qkvg = T(k.Mz * 4 * k.HCt), b.oatt = T(k.Mz * k.HCt);
+    b.og = T(k.Mz * k.HCt), b.lse = F(k.R * k.Ht * k.R);
+    end();
+  }
+  begin();  // 9. pair transition
+  p.xz9 = T(k.Mz * k.Cz), p.h9 = T(k.Mz * k.n * k.Cz);
+  end();
+  p.total = top;
+  return top;
+}
+
 size_t make_plan(const evo_dims &d, int mode, Plan &p, bool pair_only = false) {
+  if (mode == EVO_MODE_INFER) return make_infer_plan(d, p, pair_only);
   const Dims2 k(d, pair_only);
   const size_t ts = d.act_dtype == EVO_BF16 ? 2 : 4;
   size_t off = 0;
@@ -730,6 +796,15 @@ int block_forward(const evo_dims &d, const float *p32, const bf16 *p16, const vo
                   cudaStream_t s, const evo_dropout *dropout) {
   Drv drv(d, p32, p16, ws, EVO_MODE_FWD, s);
   drv.drop = dropout;
+  if (ws_bytes < drv.pl.total) return EVO_ERR_WORKSPACE;
+  drv.forward(m_in, z_in, m_out, z_out, msa_mask, pair_mask);
+  return drv.err == cudaSuccess ? EVO_OK : EVO_ERR_CUDA;
+}
+
+int block_forward_infer(const evo_dims &d, const float *p32, const bf16 *p16, const void *m_in, const void *z_in,
+                        void *m_out, void *z_out, const float *msa_mask, const float *pair_mask, void *ws,
+                        size_t ws_bytes, cudaStream_t s) {
+  Drv drv(d, p32, p16, ws, EVO_MODE_INFER, s);
   if (ws_bytes < drv.pl.total) return EVO_ERR_WORKSPACE;
   drv.forward(m_in, z_in, m_out, z_out, msa_mask, pair_mask);
   return drv.err == cudaSuccess ? EVO_OK : EVO_ERR_CUDA;

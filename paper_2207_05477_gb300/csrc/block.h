@@ -24,12 +24,18 @@ int64_t build_param_table(const evo_dims &d, std::vector<PEntry> &out, bool pair
 int validate_dims(const evo_dims *d);
 int validate_pair_dims(const evo_dims *d);
 
-// Workspace bytes of forward (save_for_bwd = 0) or backward.
+// Workspace bytes of the forward (EVO_MODE_FWD), the backward (EVO_MODE_BWD)
+// or the forward-only inference plan (EVO_MODE_INFER).
 size_t workspace_bytes(const evo_dims &d, int mode, bool pair_only = false);
 
 int block_forward(const evo_dims &d, const float *p32, const bf16 *p16, const void *m_in, const void *z_in,
                   void *m_out, void *z_out, const float *msa_mask, const float *pair_mask, void *ws, size_t ws_bytes,
                   cudaStream_t s, const evo_dropout *dropout = nullptr);
+
+// Forward in the inference plan: sub-modules share one scratch region.
+int block_forward_infer(const evo_dims &d, const float *p32, const bf16 *p16, const void *m_in, const void *z_in,
+                        void *m_out, void *z_out, const float *msa_mask, const float *pair_mask, void *ws,
+                        size_t ws_bytes, cudaStream_t s);
 
 int block_backward(const evo_dims &d, const float *p32, const bf16 *p16, const void *m_in, const void *z_in,
                    const float *msa_mask, const float *pair_mask, const void *dm_out, const void *dz_out, void *dm_in,

@@ -20,7 +20,7 @@ EVO_OK, EVO_ERR_INVALID_ARG, EVO_ERR_UNSUPPORTED, EVO_ERR_ALIGNMENT = 0, -1, -2,
 EVO_ERR_WORKSPACE, EVO_ERR_CUDA, EVO_ERR_TIMEOUT = -4, -5, -6
 EVO_F32, EVO_BF16 = 0, 1
 EVO_COL_ATTENTION, EVO_COL_GLOBAL = 0, 1
-EVO_MODE_FWD, EVO_MODE_BWD = 0, 1
+EVO_MODE_FWD, EVO_MODE_BWD, EVO_MODE_INFER = 0, 1, 2
 
 
 class EvoError(RuntimeError):
@@ -80,6 +80,7 @@ def lib():
         L.evo_params_to_bf16.argtypes = [P(CDims), _vp, _vp, _vp]
         L.evo_workspace_size.argtypes = [P(CDims), ctypes.c_int, P(_sz)]
         L.evo_block_fwd.argtypes = [P(CDims), _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _sz, _vp]
+        L.evo_block_fwd_infer.argtypes = [P(CDims), _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _sz, _vp]
         L.evo_block_bwd.argtypes = [P(CDims), _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _sz,
                                     _vp]
         L.evo_block_fwd_dropout.argtypes = [P(CDims), _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, P(CDropout), _vp, _sz,
@@ -270,6 +271,13 @@ def block_bwd(cd, params, params_bf16, m, z, msa_mask, pair_mask, dm_out, dz_out
     _check(lib().evo_block_bwd(ctypes.byref(cd), _ptr(params), _ptr(params_bf16), _ptr(m), _ptr(z), _ptr(msa_mask),
                                _ptr(pair_mask), _ptr(dm_out), _ptr(dz_out), _ptr(dm_in), _ptr(dz_in), _ptr(dparams),
                                _ptr(ws), ws.numel() * ws.element_size(), _stream(stream)), "evo_block_bwd")
+
+
+def block_fwd_infer(cd, params, params_bf16, m, z, m_out, z_out, msa_mask, pair_mask, ws, stream=None):
+    """evo_block_fwd_infer: the block forward in the EVO_MODE_INFER workspace."""
+    _check(lib().evo_block_fwd_infer(ctypes.byref(cd), _ptr(params), _ptr(params_bf16), _ptr(m), _ptr(z),
+                                     _ptr(m_out), _ptr(z_out), _ptr(msa_mask), _ptr(pair_mask), _ptr(ws),
+                                     ws.numel() * ws.element_size(), _stream(stream)), "evo_block_fwd_infer")
 
 
 def stack_fwd(cd, n_blocks, params, params_bf16, param_stride, m, z, msa_mask, pair_mask, ws, stream=None):

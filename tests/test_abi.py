@@ -129,3 +129,35 @@ def test_adam_step_arguments_are_checked_before_any_launch(built_lib):
     assert call(h, e=odd) == evo.EVO_ERR_ALIGNMENT
     assert call(h, pb=odd) == evo.EVO_ERR_ALIGNMENT
     assert call(h, wsb=ws - 8) == evo.EVO_ERR_WORKSPACE
+
+
+def test_infer_plan_is_a_fraction_of_the_forward_plan(built_lib):
+    for d in (synth.DIMS_TRAIN_CROP, synth.Dims(n_seq=5, n_res=37), synth.DIMS_EXTRA_MSA):
+        for act in (evo.EVO_BF16, evo.EVO_F32):
+            cd = evo.cdims(d, act)
+            f = evo.workspace_size(cd, evo.EVO_MODE_FWD)
+            i = evo.workspace_size(cd, evo.EVO_MODE_INFER)
+            assert 0 < i < 0.3 * f, (d, act, i, f)
+    # a block at N_res = 8192 (N_seq = 128, BF16): workspace plus m and z
+    # (updated in place) stays within one GPU's memory
+    d = synth.Dims(n_seq=128, n_res=8192)
+    cd = evo.cdims(d, evo.EVO_BF16)
+    io = 2 * (d.n_seq * d.n_res * d.c_m + d.n_res * d.n_res * d.c_z)
+    assert evo.workspace_size(cd, evo.EVO_MODE_INFER) + io < 260e9
+    with pytest.raises(evo.EvoError):
+        evo.workspace_size(cd, 3)
+
+
+def test_infer_arguments_are_checked_before_any_launch(built_lib):
+    cd = evo.cdims(synth.DIMS_SMALL_FP32, evo.EVO_F32)
+    L = built_lib
+    null = ctypes.c_void_p(0)
+    a = ctypes.c_void_p(0x100000)
+    odd = ctypes.c_void_p(0x100000 + 8)
+    need = evo.workspace_size(cd, evo.EVO_MODE_INFER)
+    r = L.evo_block_fwd_infer(ctypes.byref(cd), null, null, a, a, a, a, a, a, a, ctypes.c_size_t(need), null)
+    assert r == evo.EVO_ERR_INVALID_ARG
+    r = L.evo_block_fwd_infer(ctypes.byref(cd), a, null, odd, a, a, a, a, a, a, ctypes.c_size_t(need), null)
+    assert r == evo.EVO_ERR_ALIGNMENT
+    r = L.evo_block_fwd_infer(ctypes.byref(cd), a, null, a, a, a, a, a, a, a, ctypes.c_size_t(need - 256), null)
+    assert r == evo.EVO_ERR_WORKSPACE
