@@ -134,3 +134,21 @@ def test_numpy_inputs_are_accepted():
     z = {k: np.zeros(s, np.float32) for k, s in SHAPES.items()}
     P, M, V, E, G = O.train_update(w, g, z, z, z, 1, h)
     assert all(P[k].dtype == DT for k in P) and G > 0
+
+
+def test_adam_state_generator_is_seeded_and_tiles_differ():
+    from paper_2207_05477_gb300 import synth
+    a, b = synth.make_adam_state(3000, 4), synth.make_adam_state(3000, 4)
+    for k in a:
+        assert a[k].dtype == np.float32 and a[k].shape == (3000,)
+        assert np.array_equal(a[k], b[k]), k
+    assert (a["exp_avg_sq"] >= 0).all()
+    fresh = synth.make_adam_state(3000, 4, fresh=True)
+    assert not fresh["exp_avg"].any() and not fresh["exp_avg_sq"].any()
+    assert np.array_equal(fresh["ema"], fresh["params"]) and np.array_equal(fresh["params"], a["params"])
+    # longer than one draw: repeats of the draw, each with its own factor
+    big = synth.make_adam_state(2500, 4, base=1000)["grad"]
+    r1, r2 = big[1000:2000] / big[:1000], big[2000:] / big[:500]
+    assert np.allclose(r1, r1[0], rtol=1e-6) and np.allclose(r2, r2[0], rtol=1e-6)
+    # ratios of two factors in [0.5, 1.5)
+    assert abs(r1[0] - r2[0]) > 1e-3 and 1 / 3 < r1[0] < 3 and 1 / 3 < r2[0] < 3
