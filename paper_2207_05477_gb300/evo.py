@@ -113,6 +113,7 @@ def lib():
         L.evo_tune_load.argtypes = [ctypes.c_char_p]
         L.evo_strerror.argtypes = [ctypes.c_int]
         L.evo_strerror.restype = ctypes.c_char_p
+        L.evo_version.argtypes = []
         L.evo_version.restype = ctypes.c_char_p
         _lib = L
     return _lib

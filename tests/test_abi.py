@@ -161,3 +161,22 @@ def test_infer_arguments_are_checked_before_any_launch(built_lib):
     assert r == evo.EVO_ERR_ALIGNMENT
     r = L.evo_block_fwd_infer(ctypes.byref(cd), a, null, a, a, a, a, a, a, a, ctypes.c_size_t(need - 256), null)
     assert r == evo.EVO_ERR_WORKSPACE
+
+
+def test_binding_declares_every_signature(built_lib):
+    """Every function of the header has ctypes argument types in the binding,
+    and the ones that return size_t or a string have the matching result
+    type (ctypes would otherwise truncate a 64-bit result to int)."""
+    import re
+    L = built_lib
+    txt = re.sub(r"/\*.*?\*/", "", open(evo.HEADER).read(), flags=re.S)
+    rets = dict((name, ret.strip()) for ret, name in re.findall(r"(size_t|int|const char \*)\s*(evo_[a-z0-9_]+)\s*\(",
+                                                              txt))
+    assert set(rets) == set(evo.header_functions())
+    for name, ret in rets.items():
+        f = getattr(L, name)
+        assert f.argtypes is not None, name
+        if ret == "size_t":
+            assert f.restype is ctypes.c_size_t, name
+        elif ret.startswith("const char"):
+            assert f.restype is ctypes.c_char_p, name
