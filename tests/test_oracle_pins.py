@@ -271,6 +271,61 @@ def test_global_column_attention_special_cases():
     assert torch.allclose(a.sum(-1), torch.ones(R, H, dtype=DT), atol=1e-14)
 
 
+def test_global_column_attention_hand_computed():
+    """Alg. 19 written out scalar by scalar on one residue column: three
+    sequences with distinct query rows, sequence 1 masked, so the mean query
+    is over sequences 0 and 2 only and the softmax has the two valid keys 0
+    and 2.  Each head's output is g * (a_0 v_0 + a_2 v_2) with
+    a_0 = 1 / (1 + exp((l_2 - l_0))) and l_t = qbar . k_t / sqrt(c).  An
+    unmasked mean, a missing 1/sqrt(c) or a mask ignored on the keys each
+    change the result (checked)."""
+    d = synth.Dims(n_seq=3, n_res=1, c_m=8, c_z=4, h_msa=2, c_msa=4, msa_col_mode=1,
+                   h_tri=2, c_tri=4, c_mul=4, c_opm=2, trans_n=2)
+    p = _params(d, seed=11)
+    m, _ = _acts(d, seed=11)
+    S, H, c = d.n_seq, d.h_msa, d.c_msa
+    _expose_output(p, "col", d.c_m)
+    mk = torch.ones(S, 1, dtype=DT)
+    mk[1, 0] = 0
+    out = O.msa_global_column_attention(m, mk, p, H, c)
+
+    x = F.layer_norm(m, (d.c_m,), p["col.ln.gamma"], p["col.ln.beta"], eps=1e-5)[:, 0].tolist()  # [S][c_m]
+    w = p["col.w_qkvg"].tolist()
+    bg = p["col.b_g"].tolist()
+
+    def proj(row, s):  # one output column of the fused projection for sequence s
+        return sum(w[row][t] * x[s][t] for t in range(d.c_m))
+
+    def sig(u):
+        return 1.0 / (1.0 + math.exp(-u))
+
+    q = [[[proj(h * c + e, s) for e in range(c)] for h in range(H)] for s in range(S)]
+    kk = [[proj(H * c + e, s) for e in range(c)] for s in range(S)]
+    vv = [[proj(H * c + c + e, s) for e in range(c)] for s in range(S)]
+    g = [[[sig(proj(H * c + 2 * c + h * c + e, s) + bg[h * c + e]) for e in range(c)] for h in range(H)]
+         for s in range(S)]
+
+    def expected(valid_q, valid_k, scale):
+        res = [[0.0] * (H * c) for _ in range(S)]
+        for h in range(H):
+            qbar = [sum(q[s][h][e] for s in valid_q) / (len(valid_q) + 1e-10) for e in range(c)]
+            logit = {t: scale * sum(qbar[e] * kk[t][e] for e in range(c)) for t in valid_k}
+            mx = max(logit.values())
+            den = sum(math.exp(logit[t] - mx) for t in valid_k)
+            att = {t: math.exp(logit[t] - mx) / den for t in valid_k}
+            for s in range(S):
+                for e in range(c):
+                    res[s][h * c + e] = g[s][h][e] * sum(att[t] * vv[t][e] for t in valid_k)
+        return torch.tensor(res, dtype=DT)[:, None, :]
+
+    ref = expected([0, 2], [0, 2], 1.0 / math.sqrt(c))
+    assert torch.allclose(out, ref, atol=1e-12)
+    for wrong in (expected([0, 1, 2], [0, 2], 1.0 / math.sqrt(c)),   # unmasked mean of q
+                  expected([0, 2], [0, 2], 1.0),                       # no 1/sqrt(c)
+                  expected([0, 2], [0, 1, 2], 1.0 / math.sqrt(c))):    # masked key kept
+        assert (wrong - ref).abs().max() > 1e-4
+
+
 # --------------------------------------------------------------- triangle ops
 
 def _tri_dims():
@@ -329,6 +384,65 @@ def test_triangle_attention_bias_orientation():
             expect = torch.stack([torch.stack([v[inv[i], j] for j in range(R)]) for i in range(R)])
         # selector z changes LN(z) rows, so compare with the bias-selected key
         assert torch.allclose(out, g * expect, atol=1e-5), prefix
+
+
+def _tri_att_sdpa_case(prefix):
+    """Triangle attention with W_b = 0, a saturated gate and W_o = I, with a
+    pair mask that leaves every key row at least one valid key."""
+    d = _tri_dims()
+    p = _params(d)
+    _, z = _acts(d)
+    p[prefix + ".w_b"] = torch.zeros_like(p[prefix + ".w_b"])
+    p[prefix + ".b_g"] = torch.full_like(p[prefix + ".b_g"], 60.0)  # sigmoid(60) = 1 - 9e-27
+    _expose_output(p, prefix, d.c_z)
+    _, pm = _ones_masks(d)
+    pm[0, 3] = 0
+    pm[2, 1] = 0
+    pm[2, 5] = 0
+    pm[4, 0] = 0
+    R, H, c = d.n_res, d.h_tri, d.c_tri
+    x = F.layer_norm(z, (d.c_z,), p[prefix + ".ln.gamma"], p[prefix + ".ln.beta"], eps=1e-5)
+    w = p[prefix + ".w_qkvg"]
+    q, k, v = ((x @ w[t * H * c:(t + 1) * H * c].T).reshape(R, R, H, c) for t in range(3))
+    return d, p, z, pm, q, k, v
+
+
+def test_triangle_attention_starting_node_reduces_to_sdpa_per_row():
+    """Starting node, bias 0 and gate 1: for each pair row i, the queries
+    (i, j) attend over the keys (i, k) of the same row with the library's
+    scaled-dot-product attention, key k excluded where pair_mask[i, k] = 0.
+    This fixes the q.k term: which key a query meets and the 1/sqrt(c) scale."""
+    d, p, z, pm, q, k, v = _tri_att_sdpa_case("att_start")
+    R, H, c = d.n_res, d.h_tri, d.c_tri
+    out = O.triangle_attention_starting_node(z, pm, p, H, c)
+    ref = torch.empty(R, R, H * c, dtype=DT)
+    for i in range(R):
+        qi, ki, vi = (t[i].permute(1, 0, 2) for t in (q, k, v))  # [H, R, c]
+        allowed = (pm[i] > 0)[None, None, :].expand(H, R, R)
+        o = F.scaled_dot_product_attention(qi, ki, vi, attn_mask=allowed)
+        ref[i] = o.permute(1, 0, 2).reshape(R, H * c)
+    assert torch.allclose(out, ref, atol=1e-12)
+
+
+def test_triangle_attention_ending_node_reduces_to_sdpa_per_column():
+    """Ending node, bias 0 and gate 1: for each pair column j, the queries
+    (i, j) attend over the keys (k, j) of the same column, key k excluded
+    where pair_mask[k, j] = 0."""
+    d, p, z, pm, q, k, v = _tri_att_sdpa_case("att_end")
+    R, H, c = d.n_res, d.h_tri, d.c_tri
+    out = O.triangle_attention_ending_node(z, pm, p, H, c)
+    ref = torch.empty(R, R, H * c, dtype=DT)
+    for j in range(R):
+        qj, kj, vj = (t[:, j].permute(1, 0, 2) for t in (q, k, v))  # [H, R, c]
+        allowed = (pm[:, j] > 0)[None, None, :].expand(H, R, R)
+        o = F.scaled_dot_product_attention(qj, kj, vj, attn_mask=allowed)
+        ref[:, j] = o.permute(1, 0, 2).reshape(R, H * c)
+    assert torch.allclose(out, ref, atol=1e-12)
+    # the same inputs through the starting node give a different result (the
+    # two orientations are not interchangeable on this input)
+    pe = {("att_start." + key[len("att_end."):]): val for key, val in p.items() if key.startswith("att_end.")}
+    other = O.triangle_attention_starting_node(z, pm, {**p, **pe}, H, c)
+    assert (other - ref).abs().max() > 1e-3
 
 
 def _swap_ab(p, prefix, c_mul):
