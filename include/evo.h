@@ -185,16 +185,24 @@ int evo_stack_fwd(const evo_dims *d, int n_blocks, const float *params,
  * was divided up at start-up, a host callback or latency-critical loop where
  * cudaMalloc's possible device synchronisation is not acceptable) and do not
  * want to hold a workspace of their own.
+ *  - It runs the inference workspace plan (as evo_block_fwd_infer), whose
+ *    outputs equal evo_block_fwd's bit for bit.
  *  - Inputs and outputs are caller-owned device buffers, exactly as for
  *    evo_block_fwd (256-byte aligned; m_out may equal m_in, z_out z_in).
  *  - Returns EVO_ERR_WORKSPACE when the problem needs more scratch than
- *    128 MiB (evo_workspace_size(d, EVO_MODE_FWD) > 128 MiB).
- *  - The first call on a device looks up the array's device address on the
- *    current device (cudaGetSymbolAddress); make that first call before any
- *    stream capture.
+ *    128 MiB (evo_workspace_size(d, EVO_MODE_INFER) > 128 MiB).  At the
+ *    default channels that is N_res above 198 (BF16) / 138 (FP32) at
+ *    N_seq = 16, above 181 / 100 at N_seq = 128 and above 55 / 28 at
+ *    N_seq = 512.
+ *  - The first call on a device (and the first call in a new context on it)
+ *    looks up the array's device address in the current context
+ *    (cudaGetSymbolAddress); make that first call before any stream capture.
+ *    The address is cached per (device, context): after cudaDeviceReset the
+ *    next call looks it up again.
  *  - Every call uses the same array: calls that may overlap on the GPU (other
  *    streams, other host threads) race and must be serialised by the caller.
- *    Nothing in the array needs to start at zero. */
+ *    The forward writes every scratch byte before reading it, so nothing in
+ *    the array needs to start at zero. */
 int evo_block_fwd_noalloc(const evo_dims *d, const float *params, const void *params_bf16,
                           const void *m_in, const void *z_in, void *m_out, void *z_out,
                           const float *msa_mask, const float *pair_mask, evo_stream_t stream);
@@ -261,18 +269,36 @@ int evo_adam_step(const evo_adam *h, size_t n, float *params, const float *grad,
                   float *exp_avg, float *exp_avg_sq, float *ema, void *params_bf16,
                   float *grad_norm, void *workspace, size_t ws_bytes, evo_stream_t stream);
 
-/* Waits for the stream, then returns and clears the device error word:
- * EVO_OK, or EVO_ERR_TIMEOUT if a bounded in-kernel wait gave up since the
- * last call. */
+/* Waits for the stream, then returns and clears the device error words of
+ * every unit: EVO_OK, or EVO_ERR_TIMEOUT if a bounded in-kernel wait gave up
+ * since the last call. */
 int evo_get_error(evo_stream_t stream);
 
-/* Diagnostics for failure detection: launches one CTA whose bounded
- * mbarrier wait is never satisfied and gives up after limit_ns (at most 5 s),
- * recording EVO_ERR_TIMEOUT in the device error word exactly as a timed-out
- * wait inside a GEMM would.  The GPU context stays usable; evo_get_error
- * then returns EVO_ERR_TIMEOUT.  The paper has no counterpart (it describes
- * no failure detection). */
-int evo_debug_wait_timeout(long long limit_ns, evo_stream_t stream);
+/* Units of the library with their own device error word. */
+enum { EVO_UNIT_GEMM = 0, EVO_UNIT_ATTENTION = 1, EVO_UNIT_TRIMUL = 2 };
+
+/* Diagnostics for failure detection: launches one CTA of the given unit
+ * (EVO_UNIT_GEMM: the tcgen05 GEMM; EVO_UNIT_ATTENTION: the tcgen05
+ * attention kernels; EVO_UNIT_TRIMUL: the TMA triangle-multiplication and
+ * channel-major LayerNorm kernels) whose bounded mbarrier wait -- the same
+ * wait code those kernels use -- is never satisfied and gives up after
+ * limit_ns (at most 5 s), recording EVO_ERR_TIMEOUT in that unit's device
+ * error word exactly as a timed-out wait inside one of its kernels would.
+ * The GPU context stays usable; evo_get_error then returns EVO_ERR_TIMEOUT.
+ * EVO_ERR_INVALID_ARG for an unknown unit or a limit outside [0, 5 s].  The
+ * paper has no counterpart (it describes no failure detection). */
+int evo_debug_wait_timeout(int unit, long long limit_ns, evo_stream_t stream);
+
+/* Throughput probe of the special-function unit's exponential, the bound of
+ * the attention softmax at small head dims (no counterpart in the paper):
+ * `blocks` CTAs of 256 threads each run eight independent chains of
+ * `iters` steps x <- 2^(a x + b) and write one float to sink[thread]
+ * (caller-owned device buffer of blocks * 256 floats).  variant 0 times
+ * ex2.approx.f32 (one result per instruction), variant 1 ex2.approx.bf16x2
+ * (two).  The caller times the launch on `stream`; results per launch =
+ * blocks * 256 * 8 * iters * (variant + 1).  EVO_ERR_INVALID_ARG for a bad
+ * variant, size or pointer. */
+int evo_probe_ex2(int variant, int blocks, int iters, float *sink, evo_stream_t stream);
 
 /* Per-kernel timing.  evo_profile_begin starts recording a CUDA event pair
  * around every kernel launch of the library (on the launch stream), with the

@@ -157,9 +157,16 @@ int evo_get_error(evo_stream_t stream) {
   return h != EVO_OK ? h : h2 != EVO_OK ? h2 : h3;
 }
 
-int evo_debug_wait_timeout(long long limit_ns, evo_stream_t stream) {
+int evo_debug_wait_timeout(int unit, long long limit_ns, evo_stream_t stream) {
   if (limit_ns < 0 || limit_ns > 5000000000ll) return EVO_ERR_INVALID_ARG;
-  return debug_wait(limit_ns, (cudaStream_t)stream) == cudaSuccess ? EVO_OK : EVO_ERR_CUDA;
+  cudaError_t e;
+  switch (unit) {
+    case EVO_UNIT_GEMM: e = debug_wait(limit_ns, (cudaStream_t)stream); break;
+    case EVO_UNIT_ATTENTION: e = attn_tc_debug_wait(limit_ns, (cudaStream_t)stream); break;
+    case EVO_UNIT_TRIMUL: e = trimul_tc_debug_wait(limit_ns, (cudaStream_t)stream); break;
+    default: return EVO_ERR_INVALID_ARG;
+  }
+  return e == cudaSuccess ? EVO_OK : EVO_ERR_CUDA;
 }
 
 const char *evo_strerror(int code) {

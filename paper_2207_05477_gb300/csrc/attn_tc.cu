@@ -65,22 +65,8 @@ bool tc::make_tmap_nd(CUtensorMap *tm, CUtensorMapDataType dt, int rank, const v
 
 namespace {
 
-constexpr int AT_QROWS = 128;
-constexpr int AT_C = 32;
-constexpr int AT_MAXKEYS = 256;
-constexpr int AT_TMEM_COLS = 256;
-constexpr int AT_O_COL = 128;  // O accumulator columns [128, 160)
-constexpr int AT_WARPS = 8;    // two per TMEM lane quarter, splitting the key chunks
-// dynamic shared memory (offsets from a 1 KB aligned base)
-constexpr int AT_Q_OFF = 0;                               // 128 x 64 B
-constexpr int AT_K_OFF = AT_Q_OFF + AT_QROWS * 64;        // 256 x 64 B
-constexpr int AT_V_OFF = AT_K_OFF + AT_MAXKEYS * 64;      // 256 x 64 B
-// pair bias (bf16): per warp AT_BRING boxes of [32 rows x 64 keys] (4 KB each)
-constexpr int AT_BRING = 2;
-constexpr int AT_B_OFF = AT_V_OFF + AT_MAXKEYS * 64;
-constexpr int AT_R_OFF = AT_B_OFF + AT_WARPS * AT_BRING * 4096;  // [2][128] row max, [2][128] row sum
-constexpr int AT_M_OFF = AT_R_OFF + 4 * AT_QROWS * 4;            // 256 floats: additive key mask
-constexpr int AT_SMEM = AT_M_OFF + AT_MAXKEYS * 4 + 1024;
+constexpr int AT_C = 32;      // channels of a shared-memory q / k / v row (head dims 8 and 16 zero-padded)
+constexpr int AT_WARPS = 8;   // backward: two per TMEM lane quarter, splitting the key chunks
 
 constexpr float NEG_INF_F = -__builtin_huge_valf();
 constexpr float POS_INF_F = __builtin_huge_valf();
@@ -98,13 +84,6 @@ struct QkvPos {
   int row, h, b;  // which map dimension (1..3) holds the row, head and batch coordinate
 };
 
-struct AttnTcArgs {
-  AttnArgs a;
-  QkvPos pq, pk;  // q (and g) / k, v map dimension positions
-  int ypad;       // keys padded to a multiple of 32 (<= 256)
-  int has_bias;
-};
-
 __device__ __forceinline__ void tile_coords(const QkvPos &p, int row, int h, int b, int (&c)[4]) {
   c[0] = 0;
   c[p.row] = row;
@@ -112,7 +91,67 @@ __device__ __forceinline__ void tile_coords(const QkvPos &p, int row, int h, int
   c[p.b] = b;
 }
 
-__global__ void __launch_bounds__(AT_WARPS * 32) attn_fwd_tc(const __grid_constant__ CUtensorMap tmQ,
+// byte offset of 16-byte piece q of row r in a tile of 64-byte rows with the
+// 64-byte swizzle (tile base 512-byte aligned)
+__device__ __forceinline__ uint32_t sw64_off(int r, int q) { return (uint32_t)(r * 64 + (((q ^ (r >> 1)) & 3) << 4)); }
+
+__device__ __forceinline__ void sts128(uint32_t addr, uint4 v) {
+  asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(v.x), "r"(v.y), "r"(v.z), "r"(v.w)
+               : "memory");
+}
+__device__ __forceinline__ uint4 lds128(uint32_t addr) {
+  uint4 v;
+  asm volatile("ld.shared.v4.b32 {%0, %1, %2, %3}, [%4];" : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "r"(addr));
+  return v;
+}
+
+// -------------------------------------------------- forward, at most 256 keys
+// Head dim 32 and at most 256 keys (the training-crop attentions): all of a
+// row's logits fit one TMEM tile, so one pass needs no online rescaling.
+// One CTA of eight warps per (128 queries, head, batch item):
+//   * TMA brings Q [128 x 32], K and V [Ypad x 32] (64-byte swizzle); each
+//     warp streams its 32 rows of the pair-bias tile in 64-key boxes through
+//     a ring of its own, so the softmax warps never wait for one another;
+//   * one tcgen05.mma pair computes S = Q K^T (M 128, N Ypad, K 32) into
+//     TMEM columns [0, Ypad);
+//   * thread = query row (warps w and w + 4 read TMEM lanes 32(w % 4).. and
+//     take half of the key chunks each): pass 1 turns S into log2-domain
+//     logits (scale, pair bias, key mask) stored back in place and takes the
+//     row max; pass 2 writes P = 2^(logit - max) as bf16 pairs into TMEM
+//     columns [0, Ypad / 2) (over logits every warp has consumed) and sums
+//     it; partial maxima and sums meet in shared memory;
+//   * tcgen05.mma with A = P from TMEM and B = V from shared memory
+//     accumulates O = P V (M 128, N 32, K Ypad) in TMEM columns [128, 160);
+//   * the epilogue divides by the row sum, writes the attention output and its
+//     sigmoid-gated copy (bf16) and the row log-sum-exp (log2 domain) for the
+//     backward.
+// Keys are padded to a multiple of 32 (the pad and masked keys get a logit of
+// -inf).
+constexpr int AT_QROWS = 128;
+constexpr int AT_MAXKEYS = 256;
+constexpr int AT_TMEM_COLS = 256;
+constexpr int AT_O_COL = 128;  // O accumulator columns [128, 160)
+// dynamic shared memory (offsets from a 1 KB aligned base)
+constexpr int AT_Q_OFF = 0;                               // 128 x 64 B
+constexpr int AT_K_OFF = AT_Q_OFF + AT_QROWS * 64;        // 256 x 64 B
+constexpr int AT_V_OFF = AT_K_OFF + AT_MAXKEYS * 64;      // 256 x 64 B
+// pair bias (bf16): per warp AT_BRING boxes of [32 rows x 64 keys] (4 KB each)
+constexpr int AT_BRING = 2;
+constexpr int AT_B_OFF = AT_V_OFF + AT_MAXKEYS * 64;
+constexpr int AT_R_OFF = AT_B_OFF + AT_WARPS * AT_BRING * 4096;  // [2][128] row max, [2][128] row sum
+constexpr int AT_M_OFF = AT_R_OFF + 4 * AT_QROWS * 4;            // 256 floats: additive key mask
+constexpr int AT_SMEM = AT_M_OFF + AT_MAXKEYS * 4 + 1024;
+
+
+struct AttnTcArgs {
+  AttnArgs a;
+  QkvPos pq, pk;  // q (and g) / k, v map dimension positions
+  int ypad;       // keys padded to a multiple of 32 (<= 256)
+  int has_bias;
+};
+
+
+__global__ void __launch_bounds__(AT_WARPS * 32) attn_fwd_short(const __grid_constant__ CUtensorMap tmQ,
                                                              const __grid_constant__ CUtensorMap tmK,
                                                              const __grid_constant__ CUtensorMap tmV,
                                                              const __grid_constant__ CUtensorMap tmB, AttnTcArgs A) {
@@ -363,6 +402,497 @@ __global__ void __launch_bounds__(AT_WARPS * 32) attn_fwd_tc(const __grid_consta
   __syncthreads();
   if (warp == 0) {
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)AT_TMEM_COLS)
+                 : "memory");
+  }
+}
+
+
+// ------------------------------------------------------------------- forward
+// Any number of keys, head dim c in {8, 16, 32}.  Persistent: two CTAs per
+// SM, each looping over tiles of (128 queries, head, batch item).  The keys
+// of a tile are streamed in blocks of 64 with an online softmax (the logits
+// of a row never exist in full anywhere), and the blocks of all of a CTA's
+// tiles form one stream, so the copies and MMAs of the next tile run under
+// the softmax and epilogue of this one:
+//   * warp 8 (control): loads block G's K, V, pair-bias tile and key mask
+//     into ring slot G % 3 (TMA for K, V at c = 32 and for the bias; its
+//     lanes write the mask and, at c < 32, the zero-padded K / V rows, all
+//     fetched into registers one block ahead so that no global load sits on
+//     its path) and each tile's Q into one of four Q slots; lane 0 issues
+//     S_G = Q K_G^T (M 128, N 64) into TMEM S buffer G % 2 and, once the
+//     softmax warps have read S_G and written P_G into P buffer G % 2,
+//     O += P_G V_G (A = P from TMEM; a tile's first block starts O afresh)
+//     and at once S_{G+2} into the S buffer just read;
+//   * warps 0-7 (thread = query row = TMEM lane; warps w and w + 4 share a
+//     lane quarter and take 32 keys of each block each): logits in the log2
+//     domain (scale, pair bias, key mask), the block's row max (the two
+//     warps of a row meet at a named barrier), the running max m and the
+//     partial sums l, P = 2^(logit - m) as bf16 pairs into the P buffer.
+//     m only moves when a block's row max exceeds it by more than 8 (so
+//     P <= 2^8): then the accumulated O (each warp its 16 columns, after the
+//     last O += P V has finished) and l are rescaled, which after a tile's
+//     first block happens rarely;
+//   * tile epilogue: O / l, the sigmoid-gated copy (bf16; the gate row is
+//     read at the start of the tile) and the row log-sum-exp (log2 domain;
+//     +inf for a row with no valid key, whose output is 0).
+// TMEM: 256 columns (S buffers [0, 64) and [64, 128), P buffers [128, 160)
+// and [160, 192), O [192, 224)).  Ordering facts the waits rely on: the
+// MMAs of the control lane complete in issue order, so S_{G+2} done means
+// O += P_G V_G done (P buffer G % 2 may be rewritten), and a softmax warp at
+// block G has S_G, so every product before P_{G-1} is done.  Every wait is
+// bounded; a wait that runs out records EVO_ERR_TIMEOUT and the CTA drains
+// what it put in flight and returns.
+constexpr int FW_Q = 128;
+constexpr int FW_KB = 64;
+constexpr int FW_NS = 3;   // ring slots of key blocks
+constexpr int FW_NQ = 4;   // Q slots (tiles of one key block still keep two S in flight)
+constexpr int FW_SOFT_WARPS = 8;
+constexpr int FW_THREADS = (FW_SOFT_WARPS + 1) * 32;
+constexpr int FW_TMEM_COLS = 256;
+constexpr int FW_P_COL = 128;
+constexpr int FW_O_COL = 192;
+constexpr float FW_RESCALE = 8.f;
+// shared memory (offsets from a 1 KB aligned base): Q slots ([128 rows]
+// [64 B], 64-byte swizzle); ring slots of K, V ([64 keys][64 B], 64-byte
+// swizzle) and the bias tile ([128 rows][128 B], 128-byte swizzle); the
+// additive key masks [3][64]; the row-max / row-sum exchange [4][128]
+constexpr int FW_Q_OFF = 0;
+constexpr int FW_SK = 0, FW_SV = FW_KB * 64, FW_SB = 2 * FW_KB * 64;
+constexpr int FW_SLOT = FW_SB + FW_Q * FW_KB * 2;
+constexpr int FW_RING_OFF = FW_NQ * FW_Q * 64;
+constexpr int FW_M_OFF = FW_RING_OFF + FW_NS * FW_SLOT;
+constexpr int FW_X_OFF = FW_M_OFF + FW_NS * FW_KB * 4;
+constexpr int FW_SMEM = FW_X_OFF + 4 * FW_Q * 4 + 1024;
+static_assert(FW_SMEM * 2 + 2048 <= 233472, "two CTAs per SM");
+
+struct AttnFwdArgs {
+  AttnArgs a;
+  QkvPos pq, pk;  // q / k, v map dimension positions (TMA path)
+  int tma_qkv;    // q, k, v by TMA (head dim 32); else the control warp loads rows
+  int has_bias;
+  int nb;         // key blocks of 64 per tile
+  int nxt;        // query tiles per (head, batch item)
+  int tiles;      // nxt * H * B1
+};
+
+// What the control warp fetches for one key block before it writes the
+// block into its ring slot: the lane's two key-mask values and, without TMA,
+// its pieces of the K and V rows.
+struct FwFetch {
+  float m[2];
+  uint4 k[4], v[4];
+};
+
+// Rows [row0, row0 + nrows) of a q view into a 64-byte-swizzled tile (c / 8
+// data pieces per row; rows at or past `valid` as zeros); the pieces past
+// c / 8 are left as they are (zeroed once per CTA).
+__device__ __forceinline__ void load_rows(uint32_t tile, const bf16 *src, int64_t stride, int row0, int nrows, int valid,
+                                          int c, int lane) {
+  const int per = c >> 3;
+  for (int idx = lane; idx < nrows * per; idx += 32) {
+    const int r = idx / per, q = idx - r * per;
+    uint4 v = make_uint4(0, 0, 0, 0);
+    if (row0 + r < valid) v = *reinterpret_cast<const uint4 *>(src + (int64_t)(row0 + r) * stride + q * 8);
+    sts128(tile + sw64_off(r, q), v);
+  }
+}
+
+struct TileId {
+  int x0, h, b;
+};
+__device__ __forceinline__ TileId tile_id(const AttnFwdArgs &A, int t) {
+  TileId r;
+  const int xt = t % A.nxt, rest = t / A.nxt;
+  r.x0 = xt * FW_Q;
+  r.h = rest % A.a.H;
+  r.b = rest / A.a.H;
+  return r;
+}
+
+__global__ void __launch_bounds__(FW_THREADS, 2) attn_fwd_stream(const __grid_constant__ CUtensorMap tmQ,
+                                                             const __grid_constant__ CUtensorMap tmK,
+                                                             const __grid_constant__ CUtensorMap tmV,
+                                                             const __grid_constant__ CUtensorMap tmB, AttnFwdArgs A) {
+  pdl_trigger();
+  extern __shared__ uint8_t dsm[];
+  __shared__ __align__(8) uint64_t bar_q[FW_NQ], bar_full[FW_NS], bar_s[2], bar_p[2], bar_o[2];
+  __shared__ uint32_t tmem_slot;
+  __shared__ volatile int s_abort;
+  const AttnArgs &a = A.a;
+  const uint32_t raw = smem_u32(dsm);
+  const uint32_t base = (raw + 1023u) & ~1023u;
+  uint8_t *gbase = dsm + (base - raw);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nb = A.nb, c = a.c;
+  // this CTA's tiles: blockIdx.x, blockIdx.x + gridDim.x, ...
+  const int ntile = blockIdx.x < A.tiles ? (A.tiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+  const int NG = ntile * nb;  // key blocks of all of them, one stream
+
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < FW_NQ; ++i) mbar_init(&bar_q[i], 1);
+    for (int i = 0; i < FW_NS; ++i) mbar_init(&bar_full[i], 2);  // TMA bytes + the control warp's arrival
+    for (int i = 0; i < 2; ++i)
+      mbar_init(&bar_s[i], 1), mbar_init(&bar_p[i], FW_SOFT_WARPS), mbar_init(&bar_o[i], 1);
+    s_abort = 0;
+    fence_mbar_init();
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                 "r"((uint32_t)FW_TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_slot;
+  // global memory only from here on: wait for the kernels before this one
+  pdl_wait();
+
+  if (warp == FW_SOFT_WARPS) {
+    // ------------------------------------------------------------ control warp
+    const bool leader = lane == 0;
+    const int per = c >> 3;  // 16-byte pieces of a K / V row
+    bool ok = true;
+    int loaded = 0, waited = 0;       // key blocks put in flight / seen complete
+    int q_loaded = 0, q_waited = 0;   // tiles whose Q was put in flight / seen complete
+    uint64_t *last_bar = nullptr;     // the last MMA commit and its phase
+    uint32_t last_par = 0;
+    if (!A.tma_qkv) {
+      // the pieces past the head dim stay zero for every row of the Q and K / V slots
+      for (int i = lane; i < FW_NQ * FW_Q * 4; i += 32)
+        if ((i & 3) >= per) sts128(base + FW_Q_OFF + (i >> 9) * (FW_Q * 64) + sw64_off((i >> 2) & 127, i & 3),
+                                   make_uint4(0, 0, 0, 0));
+      for (int sl = 0; sl < FW_NS; ++sl)
+        for (int i = lane; i < 2 * FW_KB * 4; i += 32) {
+          const int r = (i >> 2) & (FW_KB - 1), q = i & 3, kv = i / (FW_KB * 4);
+          if (q >= per) sts128(base + FW_RING_OFF + sl * FW_SLOT + kv * FW_SV + sw64_off(r, q), make_uint4(0, 0, 0, 0));
+        }
+    }
+    // issue the global loads of block G (the values are used a block later)
+    auto fetch = [&](int G, FwFetch &f, bool rows) {
+      const TileId t = tile_id(A, (int)blockIdx.x + (G / nb) * (int)gridDim.x);
+      const int j = G % nb;
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        const int y = j * FW_KB + u * 32 + lane;
+        f.m[u] = y < a.Y ? (a.mask ? a.mask[(int64_t)t.b * a.sMb + (int64_t)y * a.sMy] : 1.f) : 0.f;
+      }
+      if (rows && !A.tma_qkv) {
+        const int64_t kvoff = (int64_t)t.b * a.sKb + (int64_t)t.h * c;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int idx = lane + 32 * u, r = idx / per, q = idx - r * per, y = j * FW_KB + r;
+          const bool in = u < 2 * per && y < a.Y;
+          f.k[u] = in ? *reinterpret_cast<const uint4 *>((const bf16 *)a.k + kvoff + (int64_t)y * a.sKy + q * 8)
+                      : make_uint4(0, 0, 0, 0);
+          f.v[u] = in ? *reinterpret_cast<const uint4 *>((const bf16 *)a.v + kvoff + (int64_t)y * a.sKy + q * 8)
+                      : make_uint4(0, 0, 0, 0);
+        }
+      }
+    };
+    // block G into its ring slot: TMA copies, then the fetched mask and rows
+    auto store = [&](int G, const FwFetch &f) {
+      const TileId t = tile_id(A, (int)blockIdx.x + (G / nb) * (int)gridDim.x);
+      const int j = G % nb, sl = G % FW_NS;
+      const uint32_t slot = base + FW_RING_OFF + sl * FW_SLOT;
+      const uint32_t tx = (A.tma_qkv ? 2u * FW_KB * 64u : 0u) + (A.has_bias ? (uint32_t)(FW_Q * FW_KB * 2) : 0u);
+      if (leader) {
+        mbar_arrive_expect_tx(&bar_full[sl], tx);
+        if (A.tma_qkv) {
+          int cc[4];
+          tile_coords(A.pk, j * FW_KB, t.h, t.b, cc);
+          tma_load_4d(slot + FW_SK, &tmK, cc[0], cc[1], cc[2], cc[3], &bar_full[sl]);
+          tma_load_4d(slot + FW_SV, &tmV, cc[0], cc[1], cc[2], cc[3], &bar_full[sl]);
+        }
+        if (A.has_bias) tma_load_3d(slot + FW_SB, &tmB, j * FW_KB, t.x0, t.h, &bar_full[sl]);
+      }
+      if (!A.tma_qkv) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          if (u < 2 * per) {
+            const int idx = lane + 32 * u, r = idx / per, q = idx - r * per;
+            sts128(slot + FW_SK + sw64_off(r, q), f.k[u]);
+            sts128(slot + FW_SV + sw64_off(r, q), f.v[u]);
+          }
+        }
+      }
+      float *maskadd = reinterpret_cast<float *>(gbase + FW_M_OFF) + sl * FW_KB;
+#pragma unroll
+      for (int u = 0; u < 2; ++u) maskadd[u * 32 + lane] = f.m[u] != 0.f ? 0.f : NEG_INF_F;
+      fence_proxy_async();  // the generic-proxy rows are read by the tensor cores
+      __syncwarp();
+      if (leader) mbar_arrive(&bar_full[sl]);
+      ++loaded;
+    };
+    // Q of tile i into Q slot i % 4
+    auto load_q = [&](int i) {
+      const TileId t = tile_id(A, (int)blockIdx.x + i * (int)gridDim.x);
+      const uint32_t qs = base + FW_Q_OFF + (uint32_t)((i % FW_NQ) * FW_Q * 64);
+      if (A.tma_qkv) {
+        if (leader) {
+          int cc[4];
+          mbar_arrive_expect_tx(&bar_q[i % FW_NQ], FW_Q * 64);
+          tile_coords(A.pq, t.x0, t.h, t.b, cc);
+          tma_load_4d(qs, &tmQ, cc[0], cc[1], cc[2], cc[3], &bar_q[i % FW_NQ]);
+        }
+      } else {
+        load_rows(qs, (const bf16 *)a.q + (int64_t)t.b * a.sQb + (int64_t)t.h * c, a.sQx, t.x0, FW_Q, a.X, c, lane);
+        fence_proxy_async();
+        __syncwarp();
+        if (leader) mbar_arrive(&bar_q[i % FW_NQ]);
+      }
+      ++q_loaded;
+    };
+    // S_G = Q K_G^T into buffer G % 2 (waits for the tile's Q at its first block)
+    // every wait of the control warp is made warp-uniform: its lanes must take
+    // the same path through the __syncwarp of store() and load_q()
+    auto issue_s = [&](int G) {
+      const int i = G / nb;
+      if (G % nb == 0) {
+        ok = __all_sync(0xffffffffu, ok && mbar_wait(&bar_q[i % FW_NQ], (uint32_t)((i / FW_NQ) & 1), &s_abort));
+        if (ok) q_waited = i + 1;
+      }
+      ok = __all_sync(0xffffffffu, ok && mbar_wait(&bar_full[G % FW_NS], (uint32_t)((G / FW_NS) & 1), &s_abort));
+      if (!ok) return;
+      waited = G + 1;
+      if (leader) {
+        tc_fence_after();
+        const uint32_t qs = base + FW_Q_OFF + (uint32_t)((i % FW_NQ) * FW_Q * 64);
+        const uint32_t slot = base + FW_RING_OFF + (G % FW_NS) * FW_SLOT;
+        const uint32_t idesc = instr_desc(128, FW_KB, false, false);
+        for (int ks = 0; ks < (c + 15) / 16; ++ks) {
+          const uint64_t qd = smem_desc(qs + ks * 32, 16, 512, 4);
+          const uint64_t kd = smem_desc(slot + FW_SK + ks * 32, 16, 512, 4);
+          mma_ss(tmem + (uint32_t)((G & 1) * FW_KB), qd, kd, idesc, ks > 0 ? 1u : 0u);
+        }
+        mma_commit(&bar_s[G & 1]);
+      }
+      last_bar = &bar_s[G & 1];
+      last_par = (uint32_t)((G >> 1) & 1);
+    };
+
+    {
+      // the first ring slots and Q tiles: every mask load in flight before
+      // any is stored (the rows of the untiled path are fetched block by block)
+      float m0[FW_NS], m1[FW_NS];
+#pragma unroll
+      for (int G = 0; G < FW_NS; ++G) {
+        FwFetch f;
+        f.m[0] = f.m[1] = 0.f;
+        if (G < NG) fetch(G, f, false);
+        m0[G] = f.m[0], m1[G] = f.m[1];
+      }
+      for (int i = 0; i < FW_NQ && i < ntile; ++i) load_q(i);
+#pragma unroll
+      for (int G = 0; G < FW_NS; ++G) {
+        if (G < NG) {
+          FwFetch f;
+          if (!A.tma_qkv) fetch(G, f, true);
+          f.m[0] = m0[G], f.m[1] = m1[G];
+          store(G, f);
+        }
+      }
+    }
+    FwFetch nxt;  // block FW_NS + (refills so far), fetched a block ahead
+    if (FW_NS < NG) fetch(FW_NS, nxt, true);
+    for (int G = 0; G < NG && G < 2 && ok; ++G) issue_s(G);
+    for (int G = 0; G < NG && ok; ++G) {
+      // the softmax warps have read S_G and written P_G (and rescaled O)
+      ok = __all_sync(0xffffffffu, mbar_wait(&bar_p[G & 1], (uint32_t)((G >> 1) & 1), &s_abort));
+      if (!ok) break;
+      // every S up to S_G is done with its Q slot
+      while (q_loaded < ntile && (q_loaded - FW_NQ) * nb + nb - 1 <= G) load_q(q_loaded);
+      if (leader) {
+        tc_fence_after();
+        const uint32_t slot = base + FW_RING_OFF + (G % FW_NS) * FW_SLOT;
+        const uint32_t idesc = instr_desc(128, AT_C, false, true);
+        for (int ks = 0; ks < FW_KB / 16; ++ks) {
+          const uint64_t vd = smem_desc(slot + FW_SV + ks * 1024, 16384, 512, 4);
+          mma_ts(tmem + FW_O_COL, tmem + (uint32_t)(FW_P_COL + (G & 1) * (FW_KB / 2) + ks * 8), vd, idesc,
+                 (G % nb > 0 || ks > 0) ? 1u : 0u);
+        }
+        mma_commit(&bar_o[G & 1]);
+      }
+      last_bar = &bar_o[G & 1];
+      last_par = (uint32_t)((G >> 1) & 1);
+      if (G + 2 < NG) {
+        issue_s(G + 2);  // into the S buffer the softmax warps have just read
+        if (!ok) break;
+      }
+      if (G + FW_NS < NG) {
+        // ring slot G % 3 is free once O += P_G V_G is done
+        ok = __all_sync(0xffffffffu, mbar_wait(&bar_o[G & 1], (uint32_t)((G >> 1) & 1), &s_abort));
+        if (!ok) break;
+        store(G + FW_NS, nxt);
+        if (G + FW_NS + 1 < NG) fetch(G + FW_NS + 1, nxt, true);
+      }
+    }
+    if (s_abort && leader) {
+      // drain what this CTA put in flight before its memory goes away
+      for (int i = q_waited; i < q_loaded; ++i) mbar_drain(&bar_q[i % FW_NQ], (uint32_t)((i / FW_NQ) & 1));
+      for (int G = waited; G < loaded; ++G) mbar_drain(&bar_full[G % FW_NS], (uint32_t)((G / FW_NS) & 1));
+      if (last_bar) mbar_drain(last_bar, last_par);
+    }
+  } else {
+    // ------------------------------------------------------------ softmax warps
+    const int quarter = warp & 3, hf = warp >> 2;
+    const int row = quarter * 32 + lane;  // query row within the tile (TMEM lane)
+    const uint32_t lane_base = tmem + ((uint32_t)(quarter * 32) << 16);
+    float *xmax = reinterpret_cast<float *>(gbase + FW_X_OFF);  // [2][128]
+    float *lsum = xmax + 2 * FW_Q;                               // [2][128]
+    const float sl2 = a.scale * EVO_LOG2E;
+    const int d0 = hf * 16;  // this warp's 16 output channels
+    const bool mine = d0 < c;
+    bool ok = true;
+    // Both warps of a lane quarter pass the named barriers of every block and
+    // tile, so no early exit: after an abort the rest is skipped in place.
+    for (int i = 0; i < ntile; ++i) {
+      const TileId t = tile_id(A, (int)blockIdx.x + i * (int)gridDim.x);
+      const int x = t.x0 + row;
+      // the gate row of this tile, needed at its end
+      uint4 gw[2] = {make_uint4(0, 0, 0, 0), make_uint4(0, 0, 0, 0)};
+      if (x < a.X && mine) {
+        const bf16 *gp = (const bf16 *)a.g + (int64_t)t.b * a.sQb + (int64_t)x * a.sQx + t.h * c + d0;
+        gw[0] = *reinterpret_cast<const uint4 *>(gp);
+        if (c - d0 > 8) gw[1] = *reinterpret_cast<const uint4 *>(gp + 8);
+      }
+      float m_run = NEG_INF_F, l = 0.f;
+      for (int j = 0; j < nb; ++j) {
+        const int G = i * nb + j, sl = G % FW_NS;
+        const uint32_t slot = base + FW_RING_OFF + sl * FW_SLOT;
+        const uint32_t sbuf = lane_base + (uint32_t)((G & 1) * FW_KB);
+        // tcgen05.ld / st are warp-collective: the guards around them are warp-uniform
+        ok = __all_sync(0xffffffffu, ok && mbar_wait(&bar_s[G & 1], (uint32_t)((G >> 1) & 1), &s_abort));
+        ok = __all_sync(0xffffffffu, ok && mbar_wait(&bar_full[sl], (uint32_t)((G / FW_NS) & 1), &s_abort));
+        float v[32];
+        float mloc = NEG_INF_F;
+        if (ok) {
+          tc_fence_after();
+          uint32_t r[32];
+          tmem_ld32(sbuf + (uint32_t)(hf * 32), r);
+          const float4 *ma = reinterpret_cast<const float4 *>(gbase + FW_M_OFF) + sl * (FW_KB / 4) + hf * 8;
+#pragma unroll
+          for (int q = 0; q < 8; ++q) {
+            const float4 mv = ma[q];
+            v[4 * q] = fmaf(__uint_as_float(r[4 * q]), sl2, mv.x);
+            v[4 * q + 1] = fmaf(__uint_as_float(r[4 * q + 1]), sl2, mv.y);
+            v[4 * q + 2] = fmaf(__uint_as_float(r[4 * q + 2]), sl2, mv.z);
+            v[4 * q + 3] = fmaf(__uint_as_float(r[4 * q + 3]), sl2, mv.w);
+          }
+          if (A.has_bias) {
+            // this row's 128-byte line of the bias tile (64 keys; piece k at k ^ (row & 7)); this warp's half
+            const uint32_t rb = slot + FW_SB + (uint32_t)row * 128u;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+              const uint4 w = lds128(rb + (uint32_t)(((4 * hf + k) ^ (row & 7)) << 4));
+              const __nv_bfloat162 *hv = reinterpret_cast<const __nv_bfloat162 *>(&w);
+#pragma unroll
+              for (int q = 0; q < 4; ++q) {
+                const float2 f = __bfloat1622float2(hv[q]);
+                v[8 * k + 2 * q] = fmaf(f.x, EVO_LOG2E, v[8 * k + 2 * q]);
+                v[8 * k + 2 * q + 1] = fmaf(f.y, EVO_LOG2E, v[8 * k + 2 * q + 1]);
+              }
+            }
+          }
+#pragma unroll
+          for (int k = 0; k < 32; ++k) mloc = fmaxf(mloc, v[k]);
+        }
+        // the row's block max over both halves (the partner has read its
+        // logits before it arrives here, so P may then land over them)
+        xmax[hf * FW_Q + row] = mloc;
+        asm volatile("bar.sync %0, %1;" ::"r"(1 + quarter), "r"(64) : "memory");
+        mloc = fmaxf(mloc, xmax[(hf ^ 1) * FW_Q + row]);
+        if (ok) {
+          const bool need = m_run == NEG_INF_F ? mloc > NEG_INF_F : mloc > m_run + FW_RESCALE;
+          if (__any_sync(0xffffffffu, need)) {
+            float corr = 1.f;
+            if (need) {
+              corr = m_run == NEG_INF_F ? 0.f : ex2(m_run - mloc);
+              m_run = mloc;
+            }
+            l *= corr;
+            if (j > 0) {
+              // O holds the tile's blocks before this one: rescale this warp's
+              // 16 columns once their product is done
+              ok = __all_sync(0xffffffffu,
+                              mbar_wait(&bar_o[(G - 1) & 1], (uint32_t)(((G - 1) >> 1) & 1), &s_abort));
+              if (ok) {
+                tc_fence_after();
+                uint32_t r[16];
+                tmem_ld16(lane_base + FW_O_COL + (uint32_t)d0, r);
+#pragma unroll
+                for (int k = 0; k < 16; ++k) r[k] = __float_as_uint(__uint_as_float(r[k]) * corr);
+                tmem_st16(lane_base + FW_O_COL + (uint32_t)d0, r);
+              }
+            }
+          }
+        }
+        if (ok) {
+          const float muse = m_run == NEG_INF_F ? 0.f : m_run;
+          uint32_t pk[16];
+#pragma unroll
+          for (int k = 0; k < 16; ++k) {
+            const float p0 = ex2(v[2 * k] - muse), p1 = ex2(v[2 * k + 1] - muse);
+            l += p0 + p1;
+            __nv_bfloat162 hv = __floats2bfloat162_rn(p0, p1);
+            pk[k] = *reinterpret_cast<uint32_t *>(&hv);
+          }
+          // P buffer G % 2: its last reader, O += P_{G-2} V_{G-2}, finished before S_G did
+          tmem_st16(lane_base + (uint32_t)(FW_P_COL + (G & 1) * (FW_KB / 2) + hf * 16), pk);
+          tmem_wait_st();
+          tc_fence_before();
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&bar_p[G & 1]);
+        // the next block's max exchange reuses xmax: the partner must have read it
+        asm volatile("bar.sync %0, %1;" ::"r"(1 + quarter), "r"(64) : "memory");
+      }
+      // tile epilogue: the partial sums meet (the block barriers above order
+      // this exchange after the partner's read of the previous tile's)
+      lsum[hf * FW_Q + row] = l;
+      asm volatile("bar.sync %0, %1;" ::"r"(1 + quarter), "r"(64) : "memory");
+      l += lsum[(hf ^ 1) * FW_Q + row];
+      const int Glast = i * nb + nb - 1;
+      ok = __all_sync(0xffffffffu, ok && mbar_wait(&bar_o[Glast & 1], (uint32_t)((Glast >> 1) & 1), &s_abort));
+      if (ok) {
+        tc_fence_after();
+        uint32_t r[16];
+        tmem_ld16(lane_base + FW_O_COL + (uint32_t)d0, r);
+        if (x < a.X && mine) {
+          const float inv = l > 0.f ? 1.f / l : 0.f;
+          bf16 *op = (bf16 *)a.o_att + (int64_t)t.b * a.sOb + (int64_t)x * a.sOx + t.h * c + d0;
+          bf16 *gop = (bf16 *)a.o_gate + (int64_t)t.b * a.sOb + (int64_t)x * a.sOx + t.h * c + d0;
+#pragma unroll
+          for (int q = 0; q < 2; ++q) {
+            if (q * 8 < c - d0) {
+              const __nv_bfloat162 *gh = reinterpret_cast<const __nv_bfloat162 *>(&gw[q]);
+              uint4 ow, gow;
+              uint32_t *o32 = reinterpret_cast<uint32_t *>(&ow), *g32 = reinterpret_cast<uint32_t *>(&gow);
+#pragma unroll
+              for (int k = 0; k < 4; ++k) {
+                const float v0 = __uint_as_float(r[q * 8 + 2 * k]) * inv;
+                const float v1 = __uint_as_float(r[q * 8 + 2 * k + 1]) * inv;
+                const float2 gf = __bfloat1622float2(gh[k]);
+                __nv_bfloat162 o2 = __floats2bfloat162_rn(v0, v1);
+                __nv_bfloat162 g2 = __floats2bfloat162_rn(v0 * gf.x, v1 * gf.y);
+                o32[k] = *reinterpret_cast<uint32_t *>(&o2);
+                g32[k] = *reinterpret_cast<uint32_t *>(&g2);
+              }
+              *reinterpret_cast<uint4 *>(op + q * 8) = ow;
+              *reinterpret_cast<uint4 *>(gop + q * 8) = gow;
+            }
+          }
+        }
+        if (x < a.X && hf == 0)
+          a.lse2[((int64_t)t.b * a.H + t.h) * a.X + x] = l > 0.f ? m_run + log2f(l) : POS_INF_F;
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)FW_TMEM_COLS)
                  : "memory");
   }
 }
@@ -802,27 +1332,29 @@ bool qkv_map(CUtensorMap *tm, const void *base, int H, int rows, int B1, int64_t
 
 bool attn_tc_supported(const AttnArgs &a) {
   auto a16 = [](const void *p) { return ((uintptr_t)p & 15u) == 0; };
-  if (a.c != AT_C || a.Y <= 0 || a.Y > AT_MAXKEYS || a.X <= 0) return false;
+  if ((a.c != 8 && a.c != 16 && a.c != 32) || a.Y <= 0 || a.X <= 0) return false;
   if (!a16(a.q) || !a16(a.k) || !a16(a.v) || !a16(a.g) || !a16(a.o_att) || !a16(a.o_gate)) return false;
-  if (a.sOx % 8 || a.sOb % 8 || a.sQx % 8 || a.sQb % 8) return false;
+  if (a.sOx % 8 || a.sOb % 8 || a.sQx % 8 || a.sQb % 8 || a.sKy % 8 || a.sKb % 8) return false;
   if (a.bias && (!a.bias_bf16 || !a16(a.bias) || a.sBx % 8 || a.sBh % 8 || a.sBx < a.Y ||
                  a.sBh < a.sBx * (int64_t)a.X))
     return false;
   return true;
 }
 
-cudaError_t attn_fwd_tc_launch(const AttnArgs &a, cudaStream_t s, double flops, double bytes) {
+namespace {
+
+cudaError_t attn_fwd_short_launch(const AttnArgs &a, cudaStream_t s, double flops, double bytes) {
   AttnTcArgs A{};
   A.a = a;
   A.ypad = (a.Y + 31) / 32 * 32;
   A.has_bias = a.bias != nullptr;
   CUtensorMap tq, tk, tv, tb;
   std::memset(&tb, 0, sizeof(tb));
-  // views TMA cannot describe: the caller falls back to the mma.sync kernel
-  if (!qkv_map(&tq, a.q, a.H, a.X, a.B1, a.sQx, a.sQb, AT_QROWS, &A.pq)) return cudaErrorNotSupported;
-  if (!qkv_map(&tk, a.k, a.H, a.Y, a.B1, a.sKy, a.sKb, A.ypad, &A.pk)) return cudaErrorNotSupported;
   QkvPos pv;
-  if (!qkv_map(&tv, a.v, a.H, a.Y, a.B1, a.sKy, a.sKb, A.ypad, &pv)) return cudaErrorNotSupported;
+  if (!qkv_map(&tq, a.q, a.H, a.X, a.B1, a.sQx, a.sQb, AT_QROWS, &A.pq) ||
+      !qkv_map(&tk, a.k, a.H, a.Y, a.B1, a.sKy, a.sKb, A.ypad, &A.pk) ||
+      !qkv_map(&tv, a.v, a.H, a.Y, a.B1, a.sKy, a.sKb, A.ypad, &pv))
+    return cudaErrorNotSupported;
   if (a.bias) {
     const uint64_t dims[3] = {(uint64_t)a.Y, (uint64_t)a.X, (uint64_t)a.H};
     const uint64_t st[2] = {(uint64_t)a.sBx * 2, (uint64_t)a.sBh * 2};
@@ -832,19 +1364,73 @@ cudaError_t attn_fwd_tc_launch(const AttnArgs &a, cudaStream_t s, double flops, 
   }
   static bool attr = false;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(attn_fwd_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, AT_SMEM);
+    cudaError_t e = cudaFuncSetAttribute(attn_fwd_short, cudaFuncAttributeMaxDynamicSharedMemorySize, AT_SMEM);
     if (e != cudaSuccess) return e;
     attr = true;
   }
   dim3 grid((a.X + AT_QROWS - 1) / AT_QROWS, a.H, a.B1);
   Prof p("attn_fwd_tc", s, flops, bytes);
-  launch_k(attn_fwd_tc, grid, AT_WARPS * 32, AT_SMEM, s, tq, tk, tv, tb, A);
+  launch_k(attn_fwd_short, grid, AT_WARPS * 32, AT_SMEM, s, tq, tk, tv, tb, A);
   return cudaGetLastError();
+}
+
+cudaError_t attn_fwd_stream_launch(const AttnArgs &a, cudaStream_t s, double flops, double bytes) {
+  AttnFwdArgs A{};
+  A.a = a;
+  A.nb = (a.Y + FW_KB - 1) / FW_KB;
+  A.nxt = (a.X + FW_Q - 1) / FW_Q;
+  const long long tiles = (long long)A.nxt * a.H * a.B1;
+  if (tiles >= (1ll << 31)) return cudaErrorNotSupported;
+  A.tiles = (int)tiles;
+  A.has_bias = a.bias != nullptr;
+  CUtensorMap tq, tk, tv, tb;
+  std::memset(&tq, 0, sizeof(tq));
+  std::memset(&tk, 0, sizeof(tk));
+  std::memset(&tv, 0, sizeof(tv));
+  std::memset(&tb, 0, sizeof(tb));
+  // head dim 32 by TMA where the views allow it; otherwise (and at head dims
+  // 8, 16) the control warp loads the rows
+  QkvPos pv;
+  A.tma_qkv = a.c == AT_C && qkv_map(&tq, a.q, a.H, a.X, a.B1, a.sQx, a.sQb, FW_Q, &A.pq) &&
+              qkv_map(&tk, a.k, a.H, a.Y, a.B1, a.sKy, a.sKb, FW_KB, &A.pk) &&
+              qkv_map(&tv, a.v, a.H, a.Y, a.B1, a.sKy, a.sKb, FW_KB, &pv);
+  if (a.bias) {
+    const uint64_t dims[3] = {(uint64_t)a.Y, (uint64_t)a.X, (uint64_t)a.H};
+    const uint64_t st[2] = {(uint64_t)a.sBx * 2, (uint64_t)a.sBh * 2};
+    const uint32_t box[3] = {FW_KB, FW_Q, 1};
+    if (!make_tmap_nd(&tb, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, a.bias, dims, st, box, CU_TENSOR_MAP_SWIZZLE_128B))
+      return cudaErrorNotSupported;
+  }
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(attn_fwd_stream, cudaFuncAttributeMaxDynamicSharedMemorySize, FW_SMEM);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  // persistent: two CTAs per SM (TMEM, shared memory and registers allow two)
+  int dev = 0, sms = 148;
+  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int grid = (int)std::min<long long>(tiles, 2ll * sms);
+  Prof p("attn_fwd_tc", s, flops, bytes);
+  launch_k(attn_fwd_stream, grid, FW_THREADS, FW_SMEM, s, tq, tk, tv, tb, A);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t attn_fwd_tc_launch(const AttnArgs &a, cudaStream_t s, double flops, double bytes) {
+  // the training-crop shapes (head dim 32, at most 256 keys) take the
+  // one-pass kernel when TMA can describe the views; everything else streams
+  if (a.c == AT_C && a.Y <= AT_MAXKEYS) {
+    const cudaError_t e = attn_fwd_short_launch(a, s, flops, bytes);
+    if (e != cudaErrorNotSupported) return e;
+  }
+  return attn_fwd_stream_launch(a, s, flops, bytes);
 }
 
 bool attn_bwd_tc_supported(const AttnArgs &a) {
   auto a16 = [](const void *p) { return ((uintptr_t)p & 15u) == 0; };
-  if (!attn_tc_supported(a) || a.X > 256 || !a.dq || !a.dk || !a.dv) return false;
+  if (!attn_tc_supported(a) || a.c != AT_C || a.Y > 256 || a.X > 256 || !a.dq || !a.dk || !a.dv) return false;
   if (!a16(a.dq) || !a16(a.dk) || !a16(a.dv) || a.sKy % 8 || a.sKb % 8) return false;
   if (a.dog ? (!a.dgpre || !a16(a.dog) || !a16(a.dgpre)) : (!a.do_att || !a.Dsum || !a16(a.do_att))) return false;
   if (a.bias && (!a.dbias || !a16(a.dbias) || a.Y % 4)) return false;
@@ -888,6 +1474,18 @@ cudaError_t attn_bwd_tc_launch(const AttnArgs &a, cudaStream_t s, double flops, 
   dim3 grid(a.H, a.B1);
   Prof p("attn_bwd_tc", s, flops, bytes);
   launch_k(attn_bwd_tc, grid, AT_WARPS * 32, BT_SMEM, s, tq, tk, tv, to, tb, tg, toa, A);
+  return cudaGetLastError();
+}
+
+namespace {
+__global__ void attn_tc_debug_wait_kernel(int64_t limit_ns) {
+  pdl_entry();
+  debug_wait_body(limit_ns);
+}
+}  // namespace
+
+cudaError_t attn_tc_debug_wait(int64_t limit_ns, cudaStream_t s) {
+  launch_k(attn_tc_debug_wait_kernel, 1, 32, 0, s, limit_ns);
   return cudaGetLastError();
 }
 

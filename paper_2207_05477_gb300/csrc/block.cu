@@ -527,6 +527,7 @@ struct Drv {
       ck(opm_inv_norm(mm, Bf(pl.inv4), (int)S, (int)R, 1e-3f, s));
       GemmOp o = mk(R * co, R * co, S, B(pl.ab4), R * co, 1, at(B(pl.ab4), Mm * co), R * co, 1, B(pl.O4), 0);
       o.e.map = OutMap{co, R * co * co, co, co, co * co, 1};  // O[i][j][c*co + d]
+      o.cls = "opm_outer";
       gemm(o);
       GemmOp p = mk(Mz, Cz, co * co, B(pl.O4), co * co, 0, W("opm.w_o"), co * co, 0, B(pl.z1), Cz);
       p.e.bias = P("opm.b_o"), p.e.row_scale = Bf(pl.inv4), p.e.residual = z0;
@@ -574,6 +575,7 @@ struct Drv {
     // X_c = A_c B_c^T per channel c (incoming stores A, B transposed, so the product is the same)
     GemmOp x = mk(R, R, R, B(b.A), Rp, 0, B(b.B), Rp, 0, B(b.X), Rp);
     x.batch = (int)cmul, x.a_bs = R * Rp, x.b_bs = R * Rp, x.e.c_bstride = R * Rp;
+    x.cls = "tri_einsum";
     gemm(x);
     ck(ln_fwd_cm(B(b.X), Rp, P(pre + ".ln_out.gamma"), P(pre + ".ln_out.beta"), B(b.xo), (int)R, (int)cmul, bf, s));
     const float *sc = dsc(1 + t);
@@ -678,9 +680,11 @@ struct Drv {
     // dA_c = dX_c B_c ; dB_c = dX_c^T A_c
     GemmOp ga = mk(R, R, R, B(pl.dX), Rp, 0, B(b.B), Rp, 1, B(pl.dA), Rp);
     ga.batch = (int)cmul, ga.a_bs = R * Rp, ga.b_bs = R * Rp, ga.e.c_bstride = R * Rp;
+    ga.cls = "tri_einsum";
     gemm(ga);
     GemmOp gb = mk(R, R, R, B(pl.dX), Rp, 1, B(b.A), Rp, 1, B(pl.dB), Rp);
     gb.batch = (int)cmul, gb.a_bs = R * Rp, gb.b_bs = R * Rp, gb.e.c_bstride = R * Rp;
+    gb.cls = "tri_einsum";
     gemm(gb);
     ck(trimul_gate_bwd(B(pl.dA), B(pl.dB), Rp, B(b.abg), ABG, pm, B(pl.G1), (int)R, (int)cmul, t, bf, s));
     dW(B(pl.G1), ABG, ABG, B(b.xz), Cz, Cz, Mz, pre + ".w_abg");
@@ -742,10 +746,12 @@ struct Drv {
       // da[s][(i,c)] = sum_(j,d) b[s][(j,d)] dO[(i,c)][(j,d)]
       GemmOp ga = mk(S, R * co, R * co, at(B(pl.ab4), Mm * co), R * co, 0, B(pl.dO4), R * co, 0, B(pl.dab4), 0);
       ga.e.map = OutMap{1ll << 40, 0, R * 2 * co, co, 2 * co, 1};
+      ga.cls = "opm_outer";
       gemm(ga);
       // db[s][(j,d)] = sum_(i,c) a[s][(i,c)] dO[(i,c)][(j,d)]
       GemmOp gb = mk(S, R * co, R * co, B(pl.ab4), R * co, 0, B(pl.dO4), R * co, 1, at(B(pl.dab4), co), 0);
       gb.e.map = OutMap{1ll << 40, 0, R * 2 * co, co, 2 * co, 1};
+      gb.cls = "opm_outer";
       gemm(gb);
       ck(row_scale(B(pl.dab4), mm, B(pl.dab4), Mm, (int)(2 * co), bf, s, D("opm.b_ab")));
       dW(B(pl.dab4), 2 * co, 2 * co, B(pl.xm4), Cm, Cm, Mm, "opm.w_ab");

@@ -27,162 +27,15 @@
 #include <algorithm>
 #include <cstring>
 
-#include "kernels.h"
+#include "tc.cuh"
 
 namespace evo {
 
-__device__ int g_evo_error = 0;
-
 namespace {
 
+using namespace tc;
+
 constexpr int BM = 128, BK = 64;
-constexpr uint64_t WAIT_LIMIT_NS = 1000000000ull;
-
-__device__ __forceinline__ uint32_t smem_u32(const void *p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void fence_mbar_init() {
-  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-               : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-// try_wait that may suspend the thread until the phase completes or about
-// hint_ns pass (so waiting warps do not spin on the issue slots).
-__device__ __forceinline__ bool mbar_try_wait_hint(uint64_t *bar, uint32_t parity, uint32_t hint_ns) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity), "r"(hint_ns)
-      : "memory");
-  return ok != 0;
-}
-// Bounded wait; gives up when the CTA abort flag is raised or the limit passes.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort_flag) {
-  if (mbar_try_wait(bar, parity)) return true;
-  const uint64_t t0 = globaltimer_ns();
-  while (true) {
-    if (mbar_try_wait_hint(bar, parity, 100000u)) return true;
-    if (*abort_flag) return false;
-    if (globaltimer_ns() - t0 > WAIT_LIMIT_NS) {
-      *abort_flag = 1;
-      atomicExch(&g_evo_error, -6);
-      return false;
-    }
-  }
-}
-
-__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap *tm, int c0, int c1, int c2,
-                                            uint64_t *bar) {
-  asm volatile(
-      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-      " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst),
-      "l"((uint64_t)tm), "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(bar))
-      : "memory");
-}
-
-__device__ __forceinline__ void tma_store_3d(const CUtensorMap *tm, uint32_t src, int c0, int c1, int c2) {
-  asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%1, %2, %3}], [%4];" ::"l"((uint64_t)tm),
-               "r"(c0), "r"(c1), "r"(c2), "r"(src)
-               : "memory");
-}
-__device__ __forceinline__ void tma_store_4d(const CUtensorMap *tm, uint32_t src, int c0, int c1, int c2, int c3) {
-  asm volatile("cp.async.bulk.tensor.4d.global.shared::cta.bulk_group [%0, {%1, %2, %3, %4}], [%5];" ::"l"(
-                   (uint64_t)tm),
-               "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(src)
-               : "memory");
-}
-__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void bulk_wait_read() {
-  asm volatile("cp.async.bulk.wait_group.read %0;" ::"n"(N) : "memory");
-}
-__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
-__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-
-__device__ __forceinline__ void tc_fence_before() {
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-}
-__device__ __forceinline__ void tc_fence_after() {
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-}
-
-// Shared-memory matrix descriptor, 128-byte swizzle, sm_100-family version 1.
-__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
-  uint64_t d = 0;
-  d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
-  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
-  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
-  d |= (uint64_t)1 << 46;
-  d |= (uint64_t)2 << 61;
-  return d;
-}
-
-// Instruction descriptor of kind::f16: D fp32, A and B bf16, dense.
-__host__ __device__ constexpr uint32_t instr_desc(int M, int N, bool a_mn, bool b_mn) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((a_mn ? 1u : 0u) << 15) | ((b_mn ? 1u : 0u) << 16) |
-         ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
-}
-
-__device__ __forceinline__ void tc_mma(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
-                                       uint32_t accumulate) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "setp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
-      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
-      : "memory");
-}
-__device__ __forceinline__ void tc_commit(uint64_t *bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                   smem_u32(bar))
-               : "memory");
-}
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
-      "[%16];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
-        "=r"(r[15])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-}
-
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
 
 // Persistent kernel configuration: a ring of A/B k-tiles, sixteen epilogue
 // warps with a small shared-memory region each, and two TMEM accumulators of
@@ -444,16 +297,16 @@ __global__ void __launch_bounds__(576, 1)
         for (int kk = 0; kk < BK / 16; ++kk) {
           const uint64_t ad = smem_desc(sa + kk * C::A_KSTEP, C::A_LBO, 1024);
           const uint64_t bd = smem_desc(sb + kk * C::B_KSTEP, C::B_LBO, 1024);
-          tc_mma(dacc, ad, bd, C::IDESC, (i > 0 || kk > 0) ? 1u : 0u);
+          mma_ss(dacc, ad, bd, C::IDESC, (i > 0 || kk > 0) ? 1u : 0u);
         }
-        tc_commit(&empty_bar[stage]);
+        mma_commit(&empty_bar[stage]);
         if (++stage == (uint32_t)stages) stage = 0, phase ^= 1u;
       }
       if (stop) break;
-      tc_commit(&accf_bar[ab]);
+      mma_commit(&accf_bar[ab]);
       ++ai;
     }
-    tc_commit(&done_bar);
+    mma_commit(&done_bar);
   } else if (warp >= 2) {
     // ---------------- epilogue warps
     // warp w drains TMEM lane quarter w % 4 (the lanes tcgen05.ld lets it
@@ -741,18 +594,7 @@ __global__ void __launch_bounds__(576, 1)
 
 __global__ void debug_wait_kernel(int64_t limit_ns) {
   pdl_entry();
-  // One mbarrier that nothing ever arrives on: the bounded wait runs out,
-  // records the timeout in the device error word and the kernel returns.
-  __shared__ __align__(8) uint64_t bar;
-  if (threadIdx.x != 0) return;
-  mbar_init(&bar, 1);
-  const uint64_t t0 = globaltimer_ns();
-  while (!mbar_try_wait(&bar, 0)) {
-    if ((int64_t)(globaltimer_ns() - t0) > limit_ns) {
-      atomicExch(&g_evo_error, -6);
-      return;
-    }
-  }
+  debug_wait_body(limit_ns);
 }
 
 typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
@@ -919,7 +761,7 @@ cudaError_t launch_tc(const GemmOp &g, cudaStream_t s) {
   cbytes += 2.0 * ((g.e.residual ? 1 : 0) + (g.e.gate ? 1 : 0) + (g.e.relu_ref ? 1 : 0) + (g.e.aux ? 1 : 0));
   Prof p(prof_detail() ? prof_name("g%dx%dx%d*%ds%dn%d%s%se%d", (int)g.M, (int)g.N, (int)g.K, (int)g.batch, g.splits,
                                     BN, AMN ? "T" : "", BMN ? "t" : "", L.tma_store)
-                      : "gemm_tc",
+                      : (g.cls ? g.cls : "gemm_tc"),
          s, 2.0 * g.M * g.N * (double)g.K * g.batch,
          g.batch * (2.0 * ((double)g.M * g.K + (double)g.N * g.K) + cbytes * g.M * g.N));
   const int ek = !L.tma_store ? EK_GENERAL : (L.has_opa || L.has_res || e.aux) ? EK_OPS : EK_PLAIN;
@@ -940,9 +782,9 @@ cudaError_t dispatch_major(const GemmOp &g, cudaStream_t s) {
 
 cudaError_t error_word_read_clear(int *out) {
   int zero = 0;
-  cudaError_t e = cudaMemcpyFromSymbol(out, g_evo_error, sizeof(int));
+  cudaError_t e = cudaMemcpyFromSymbol(out, tc_error_word, sizeof(int));
   if (e != cudaSuccess) return e;
-  return cudaMemcpyToSymbol(g_evo_error, &zero, sizeof(int));
+  return cudaMemcpyToSymbol(tc_error_word, &zero, sizeof(int));
 }
 
 cudaError_t debug_wait(int64_t limit_ns, cudaStream_t s) {

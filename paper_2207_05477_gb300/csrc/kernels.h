@@ -21,6 +21,7 @@ struct GemmOp {
   int b_mn;
   Epi e;
   int splits;
+  const char *cls;  // profiler class of the launch (nullptr: "gemm_tc")
 };
 
 // SIMT FP32 GEMM (the plain path; no tensor cores).
@@ -89,6 +90,8 @@ bool attn_bwd_tc_supported(const AttnArgs &a);
 cudaError_t attn_bwd_tc_launch(const AttnArgs &a, cudaStream_t s, double flops, double bytes);
 // Reads and clears the error word of the tcgen05 attention kernels; synchronous.
 cudaError_t attn_tc_error_read_clear(int *out);
+// one CTA whose bounded wait (this unit's own) runs out after limit_ns
+cudaError_t attn_tc_debug_wait(int64_t limit_ns, cudaStream_t s);
 cudaError_t attn_bwd(const AttnArgs &a, int use_bf16, cudaStream_t s);
 
 // Global column attention (extra-MSA stack): single-head k, v.
@@ -179,6 +182,7 @@ cudaError_t ln_bwd_cm_tma_launch(const void *dy, const void *x, int64_t pitch, c
                                  int C, float *dgamma, float *dbeta, cudaStream_t s);
 // Reads and clears the error word of the TMA gate kernels; synchronous.
 cudaError_t trimul_tc_error_read_clear(int *out);
+cudaError_t trimul_tc_debug_wait(int64_t limit_ns, cudaStream_t s);
 cudaError_t trimul_gate_bwd(const void *dA, const void *dB, int64_t pitch, const void *abg, int64_t ld,
                             const float *mask, void *dabg, int R, int cm, int incoming, int use_bf16,
                             cudaStream_t s);

@@ -7,8 +7,16 @@
 // which cudaMalloc (which may synchronise the device) is not allowed -- and
 // that also do not want to keep a workspace of their own alive.
 //
+// It runs the inference workspace plan (every sub-module's scratch in one
+// shared region, two buffers per residual stream), the plan evo_block_fwd_infer
+// uses, so the fixed array covers larger problems than the training plan
+// would: with 128 MiB, N_res up to 198 (BF16) / 138 (FP32) at N_seq = 16 and
+// up to 181 / 100 at N_seq = 128 (evo_workspace_size, EVO_MODE_INFER).
+//
 // Cost: the array below (128 MiB) is reserved on every GPU that loads this
 // part of the library and stays reserved until the process exits.
+#include <cuda.h>
+
 #include <mutex>
 
 #include "block.h"
@@ -23,19 +31,50 @@ constexpr int kMaxDevices = 64;
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
 std::mutex g_mu;
-void *g_scratch_addr[kMaxDevices] = {};
+struct ScratchAddr {
+  CUcontext ctx;  // the context the address was looked up in
+  void *addr;
+};
+ScratchAddr g_scratch[kMaxDevices] = {};
 
-// Device address of the scratch on the current device (looked up once per device).
+// The current context of the calling thread, through the driver entry point
+// (no link against libcuda).  nullptr when the query is unavailable.
+CUcontext current_context() {
+  typedef CUresult (*GetCurrentFn)(CUcontext *);
+  static GetCurrentFn fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (GetCurrentFn)p;
+  }
+  CUcontext c = nullptr;
+  if (fn && fn(&c) != CUDA_SUCCESS) c = nullptr;
+  return c;
+}
+
+// Device address of the scratch in the current device's current context,
+// looked up once per (device, context): a symbol's address belongs to the
+// context it was loaded in, so a new context on the same device (after
+// cudaDeviceReset, or a non-primary context made current) is looked up again.
 int scratch_on_current_device(void **out) {
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return EVO_ERR_CUDA;
+  // make sure the runtime has a context on this device before asking for it
+  if (cudaFree(nullptr) != cudaSuccess) return EVO_ERR_CUDA;
+  const CUcontext ctx = current_context();
   std::lock_guard<std::mutex> lk(g_mu);
-  if (!g_scratch_addr[dev]) {
+  ScratchAddr &s = g_scratch[dev];
+  if (!s.addr || s.ctx != ctx) {
     void *p = nullptr;
     if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || p == nullptr) return EVO_ERR_CUDA;
-    g_scratch_addr[dev] = p;
+    s.addr = p;
+    s.ctx = ctx;
   }
-  *out = g_scratch_addr[dev];
+  *out = s.addr;
   return EVO_OK;
 }
 
@@ -55,11 +94,12 @@ extern "C" int evo_block_fwd_noalloc(const evo_dims *d, const float *params, con
                         (const void *)msa_mask, (const void *)pair_mask})
     if (!aligned256(p)) return EVO_ERR_ALIGNMENT;
   if (bf && !aligned256(params_bf16)) return EVO_ERR_ALIGNMENT;
-  if (evo::workspace_bytes(*d, EVO_MODE_FWD) > kScratchBytes) return EVO_ERR_WORKSPACE;
+  if (evo::workspace_bytes(*d, EVO_MODE_INFER) > kScratchBytes) return EVO_ERR_WORKSPACE;
   void *ws = nullptr;
   const int r = scratch_on_current_device(&ws);
   if (r != EVO_OK) return r;
-  // The forward writes every scratch byte it reads, so nothing needs clearing.
-  return evo::block_forward(*d, params, (const bf16 *)params_bf16, m_in, z_in, m_out, z_out, msa_mask, pair_mask, ws,
-                            kScratchBytes, (cudaStream_t)stream);
+  // The inference forward writes every scratch byte before it reads it, so
+  // nothing in the shared array needs clearing between calls.
+  return evo::block_forward_infer(*d, params, (const bf16 *)params_bf16, m_in, z_in, m_out, z_out, msa_mask,
+                                  pair_mask, ws, kScratchBytes, (cudaStream_t)stream);
 }

@@ -55,20 +55,36 @@ __device__ __forceinline__ bool mbar_try_wait_hint(uint64_t *bar, uint32_t parit
   return ok != 0;
 }
 // Bounded wait: false when the CTA abort flag is raised or about a second
-// passes (then the abort flag and the error word are set).
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort_flag) {
+// (limit_ns) passes (then the abort flag and the error word are set).
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort_flag,
+                                          uint64_t limit_ns = WAIT_LIMIT_NS) {
   if (mbar_try_wait(bar, parity)) return true;
   const uint64_t t0 = globaltimer_ns();
   while (true) {
     if (mbar_try_wait_hint(bar, parity, 100000u)) return true;
     if (*abort_flag) return false;
-    if (globaltimer_ns() - t0 > WAIT_LIMIT_NS) {
+    if (globaltimer_ns() - t0 > limit_ns) {
       *abort_flag = 1;
       atomicExch(&tc_error_word, -6);
       return false;
     }
   }
 }
+// Failure-detection diagnostics: one mbarrier that nothing ever arrives on,
+// waited on by the unit's own bounded wait (mbar_wait) with a limit of
+// limit_ns; the wait runs out, records EVO_ERR_TIMEOUT in this unit's error
+// word, and the kernel returns.  Each unit launches it from its own
+// translation unit, so the word it sets is that unit's.
+__device__ __forceinline__ void debug_wait_body(int64_t limit_ns) {
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ volatile int abort_flag;
+  if (threadIdx.x != 0) return;
+  mbar_init(&bar, 1);
+  abort_flag = 0;
+  fence_mbar_init();
+  mbar_wait(&bar, 0, &abort_flag, (uint64_t)limit_ns);
+}
+
 // Bounded wait used while draining after an abort (no error is recorded).
 __device__ __forceinline__ void mbar_drain(uint64_t *bar, uint32_t parity) {
   const uint64_t t0 = globaltimer_ns();
@@ -94,12 +110,35 @@ __device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap *tm,
 }
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
+// TMA stores from shared memory (bulk groups) and their completion waits.
+__device__ __forceinline__ void tma_store_3d(const CUtensorMap *tm, uint32_t src, int c0, int c1, int c2) {
+  asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%1, %2, %3}], [%4];" ::"l"((uint64_t)tm),
+               "r"(c0), "r"(c1), "r"(c2), "r"(src)
+               : "memory");
+}
+__device__ __forceinline__ void tma_store_4d(const CUtensorMap *tm, uint32_t src, int c0, int c1, int c2, int c3) {
+  asm volatile("cp.async.bulk.tensor.4d.global.shared::cta.bulk_group [%0, {%1, %2, %3, %4}], [%5];" ::"l"(
+                   (uint64_t)tm),
+               "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(src)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+// at most N bulk groups still reading their shared-memory source
+template <int N>
+__device__ __forceinline__ void bulk_wait_read() {
+  asm volatile("cp.async.bulk.wait_group.read %0;" ::"n"(N) : "memory");
+}
+__device__ __forceinline__ void bulk_wait_read_all() { bulk_wait_read<0>(); }
+// every bulk group complete (writes visible)
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
-// Shared-memory matrix descriptor (sm_100 family, version 1).  layout: 2 =
-// 128-byte swizzle, 4 = 64-byte swizzle.  lbo / sbo in bytes.
-__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo, uint32_t layout) {
+// Shared-memory matrix descriptor (sm_100 family, version 1).  layout: 0 =
+// no swizzle, 2 = 128-byte swizzle, 4 = 64-byte swizzle, 6 = 32-byte
+// swizzle.  lbo / sbo in bytes.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo, uint32_t layout = 2) {
   uint64_t d = 0;
   d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
   d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;

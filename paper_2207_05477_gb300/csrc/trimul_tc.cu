@@ -23,15 +23,6 @@ constexpr int TT_C = 64;                 // channels per tile
 constexpr int TT_Q = 64;                 // positions per tile
 constexpr int TT_TILE = TT_C * TT_Q * 2;  // bytes of one bf16 tile
 
-__device__ __forceinline__ void tma_store_3d(const CUtensorMap *tm, uint32_t src, int c0, int c1, int c2) {
-  asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.tile.bulk_group [%0, {%2, %3, %4}], [%1];" ::"l"(
-                   (uint64_t)tm),
-               "r"(src), "r"(c0), "r"(c1), "r"(c2)
-               : "memory");
-}
-__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void bulk_wait_read_all() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
-
 // byte offset of 16-byte chunk q of row r in a tile of 128-byte rows written
 // by TMA with the 128-byte swizzle (tile base 1024-byte aligned)
 __device__ __forceinline__ uint32_t sw128(int r, int q) { return (uint32_t)(r * 128 + ((q ^ (r & 7)) << 4)); }
@@ -482,6 +473,18 @@ cudaError_t ln_bwd_cm_tma_launch(const void *dy, const void *x, int64_t pitch, c
     attr = smem;
   }
   return launch_k(ln_bwd_cm_tma, dim3((R + 63) / 64, R), 256, smem, s, tx, tdy, tdx, gamma, C, dgamma, dbeta);
+}
+
+namespace {
+__global__ void trimul_tc_debug_wait_kernel(int64_t limit_ns) {
+  pdl_entry();
+  debug_wait_body(limit_ns);
+}
+}  // namespace
+
+cudaError_t trimul_tc_debug_wait(int64_t limit_ns, cudaStream_t s) {
+  launch_k(trimul_tc_debug_wait_kernel, 1, 32, 0, s, limit_ns);
+  return cudaGetLastError();
 }
 
 cudaError_t trimul_tc_error_read_clear(int *out) {

@@ -21,6 +21,7 @@ EVO_ERR_WORKSPACE, EVO_ERR_CUDA, EVO_ERR_TIMEOUT = -4, -5, -6
 EVO_F32, EVO_BF16 = 0, 1
 EVO_COL_ATTENTION, EVO_COL_GLOBAL = 0, 1
 EVO_MODE_FWD, EVO_MODE_BWD, EVO_MODE_INFER = 0, 1, 2
+EVO_UNIT_GEMM, EVO_UNIT_ATTENTION, EVO_UNIT_TRIMUL = 0, 1, 2
 
 
 class EvoError(RuntimeError):
@@ -100,7 +101,8 @@ def lib():
         L.evo_adam_workspace_size.restype = _sz
         L.evo_adam_step.argtypes = [P(CAdam), _sz, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _sz, _vp]
         L.evo_get_error.argtypes = [_vp]
-        L.evo_debug_wait_timeout.argtypes = [ctypes.c_longlong, _vp]
+        L.evo_probe_ex2.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, _vp]
+        L.evo_debug_wait_timeout.argtypes = [ctypes.c_int, ctypes.c_longlong, _vp]
         L.evo_profile_only.argtypes = [ctypes.c_char_p]
         L.evo_profile_pause.argtypes = [ctypes.c_int]
         L.evo_profile_begin.argtypes = []
@@ -307,8 +309,17 @@ def get_error(stream=None):
     return int(lib().evo_get_error(_stream(stream)))
 
 
-def debug_wait_timeout(limit_ns, stream=None):
-    _check(lib().evo_debug_wait_timeout(int(limit_ns), _stream(stream)), "evo_debug_wait_timeout")
+def probe_ex2(variant, blocks, iters, sink, stream=None):
+    """Launches the ex2 throughput probe (variant 0: f32, 1: bf16x2) writing blocks*256 floats to sink."""
+    import torch
+    assert sink.numel() >= blocks * 256 and sink.dtype == torch.float32 and sink.is_cuda
+    _check(lib().evo_probe_ex2(int(variant), int(blocks), int(iters), _ptr(sink), _stream(stream)), "evo_probe_ex2")
+
+
+def debug_wait_timeout(limit_ns, unit=None, stream=None):
+    """One CTA of `unit` (EVO_UNIT_GEMM / _ATTENTION / _TRIMUL) whose bounded wait runs out after limit_ns."""
+    u = EVO_UNIT_GEMM if unit is None else unit
+    _check(lib().evo_debug_wait_timeout(int(u), int(limit_ns), _stream(stream)), "evo_debug_wait_timeout")
 
 
 def profile_only(kernel_name=None):

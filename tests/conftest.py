@@ -19,3 +19,13 @@ def built_lib():
     from paper_2207_05477_gb300 import build, evo
     build.build()
     return evo.lib()
+
+
+def pytest_sessionfinish(session, exitstatus):
+    """EVO_PARITY_REPORT=<path>: write every parity check's measured errors and bounds."""
+    path = os.environ.get("EVO_PARITY_REPORT")
+    if not path:
+        return
+    mod = sys.modules.get("tolerances")
+    if mod is not None:
+        mod.write_report(path)

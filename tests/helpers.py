@@ -1,5 +1,6 @@
 """Shared helpers of the parity tests: run the library and the oracle on the same seeded inputs."""
 import functools
+import math
 
 import numpy as np
 import torch
@@ -26,50 +27,61 @@ def problem(d, seed=32, pad_frac=0.0, trailing=False):
     return synth.make_problem(d, seed, pad_frac, trailing)
 
 
-@functools.lru_cache(maxsize=3)
-def oracle_fwd_bwd(d, seed=32, pad_frac=0.0, trailing=False, dropout=False):
-    """dropout: apply the seeded training-mode dropout scales (synth.make_dropout)."""
-    prob = problem(d, seed, pad_frac, trailing)
-    p = synth.unpack_params(d, prob["params"])
-    dr = synth.make_dropout(d, seed) if dropout else None
-    mo, zo, dm, dz, dp = O.block_forward_backward(prob["m"], prob["z"], prob["msa_mask"], prob["pair_mask"], p, d,
-                                                  prob["gm"], prob["gz"], dropout=dr)
-    return mo, zo, dm, dz, dp
+def to_bf16_grid(x):
+    """x rounded to the nearest BF16 value (round-to-nearest-even), back in fp64.
 
-
-@functools.lru_cache(maxsize=3)
-def oracle_fwd(d, seed=32, pad_frac=0.0, trailing=False):
-    prob = problem(d, seed, pad_frac, trailing)
-    p = synth.unpack_params(d, prob["params"])
-    return O.block_forward(prob["m"], prob["z"], prob["msa_mask"], prob["pair_mask"], p, d)
-
-
-def _to_bf16_grid(x):
-    """x rounded to the nearest BF16 value (round-to-nearest-even), back in fp64."""
+    A BF16 run hands the library m, z and the cotangents as BF16 bytes, so
+    the oracle of a BF16 run reads these same values (parameters, masks and
+    dropout scales reach the library as FP32 and stay as they are)."""
     return torch.as_tensor(np.asarray(x)).float().bfloat16().double().numpy()
 
 
 @functools.lru_cache(maxsize=3)
-def oracle_bf16_floor(d, seed=32, pad_frac=0.0, trailing=False, dropout=False):
-    """Relative L2 change of each oracle output when only the block's inputs
-    (m, z, every parameter and the cotangents gm, gz) are rounded to BF16 and
-    everything else stays FP64.  A BF16 path must round these inputs, so no
-    BF16 result can be expected closer to the FP64 oracle than this floor.
-    Returns {"dm": .., "dz": .., <parameter name>: ..}."""
+def oracle_fwd_bwd(d, seed=32, pad_frac=0.0, trailing=False, dropout=False, bf16_inputs=False):
+    """dropout: apply the seeded training-mode dropout scales (synth.make_dropout).
+    bf16_inputs: the oracle reads m, z, gm, gz rounded to BF16 (the bytes a BF16 run receives)."""
     prob = problem(d, seed, pad_frac, trailing)
-    p = synth.unpack_params(d, _to_bf16_grid(prob["params"]))
+    cast = to_bf16_grid if bf16_inputs else (lambda x: x)
+    p = synth.unpack_params(d, prob["params"])
     dr = synth.make_dropout(d, seed) if dropout else None
-    _, _, dm, dz, dp = O.block_forward_backward(_to_bf16_grid(prob["m"]), _to_bf16_grid(prob["z"]), prob["msa_mask"],
-                                                prob["pair_mask"], p, d, _to_bf16_grid(prob["gm"]),
-                                                _to_bf16_grid(prob["gz"]), dropout=dr)
-    ref = oracle_fwd_bwd(d, seed, pad_frac, trailing, dropout)
-    lay, _ = synth.param_layout(d)
-    packed = np.zeros(max(o + int(np.prod(s)) for _, o, s, _ in lay))
-    for name, off, shape, _ in lay:
-        packed[off:off + int(np.prod(shape))] = dp[name].detach().numpy().ravel()
-    errs = {"dm": rel_l2(dm, ref[2]), "dz": rel_l2(dz, ref[3])}
-    errs.update(param_grad_errors(d, packed, ref[4]))
-    return errs
+    mo, zo, dm, dz, dp = O.block_forward_backward(cast(prob["m"]), cast(prob["z"]), prob["msa_mask"],
+                                                  prob["pair_mask"], p, d, cast(prob["gm"]), cast(prob["gz"]),
+                                                  dropout=dr)
+    return mo, zo, dm, dz, dp
+
+
+@functools.lru_cache(maxsize=3)
+def oracle_fwd(d, seed=32, pad_frac=0.0, trailing=False, bf16_inputs=False):
+    prob = problem(d, seed, pad_frac, trailing)
+    cast = to_bf16_grid if bf16_inputs else (lambda x: x)
+    p = synth.unpack_params(d, prob["params"])
+    return O.block_forward(cast(prob["m"]), cast(prob["z"]), prob["msa_mask"], prob["pair_mask"], p, d)
+
+
+def slice_rel_l2_max(x, ref, axes, min_nonzero=32):
+    """Largest relative L2 error over the slices of x along each of ``axes``
+    (e.g. per MSA row, per residue, per channel).  A wrong head, row or
+    column that a whole-tensor norm averages away shows here.
+
+    A slice whose reference norm is below a quarter of the typical (RMS)
+    slice norm is measured against that quarter, so a slice that is nearly
+    zero in the reference (a padded row, a channel with a tiny gradient)
+    neither divides by zero nor turns rounding into a large ratio.  An axis
+    whose median slice holds fewer than ``min_nonzero`` nonzero reference
+    elements is not reported (too few elements for a relative error to mean
+    anything: the degenerate and mostly-padded problems)."""
+    x = torch.as_tensor(x).double().cpu()
+    ref = torch.as_tensor(ref).double().cpu()
+    worst = {}
+    for ax in axes:
+        dims = [i for i in range(x.dim()) if i != ax]
+        if (ref != 0).sum(dim=dims).double().median().item() < min_nonzero:
+            continue
+        num = (x - ref).pow(2).sum(dim=dims).sqrt()
+        den = ref.pow(2).sum(dim=dims).sqrt()
+        floor = 0.25 * ref.norm().item() / math.sqrt(ref.shape[ax])
+        worst[ax] = float((num / torch.clamp(den, min=max(floor, 1e-300))).max().item())
+    return worst
 
 
 def gpu_run(d, act_dtype, seed=32, pad_frac=0.0, trailing=False, backward=True, dropout=False):

@@ -1,125 +1,106 @@
 """Parity of the CUDA Evoformer block (through the C ABI) with the FP64 oracle.
 
-Tolerances (relative L2 over all positions), from the stated targets and,
-where those cannot hold, from the arithmetic:
-  * FP32 plain path: m, z <= 1e-4 (stated).  Gradients <= 1e-3: the ReLU
-    derivative of the two transitions is a float-decided 0/1 mask; a
-    pre-activation within FP32 rounding of zero flips sign between the FP64
-    oracle and the kernel, and each flip moves a whole gradient row.  At the
-    training crop a few such flips among 3.4e7 pre-activations give ~5e-4.
-  * BF16 path: m, z <= 2e-2 and dm, dz <= 5e-2 (stated); every parameter
-    gradient <= 5e-2 (stated) except the four tensors per transition whose
-    gradient passes through that ReLU mask (LayerNorm gamma/beta, w1, b1):
-    BF16 forward error ~4e-3 puts ~0.3% of pre-activations on the other side
-    of zero, an expected relative error of ~sqrt(0.3%) = 5.5%; bound 1e-1.
-  * Small BF16 problems (a few MSA rows): every tensor upstream of a
-    transition inherits part of that ReLU-flip noise, with too few positions
-    to average it out.  There the bound of each tensor is also at least twice
-    the oracle's own BF16 floor: the change of that tensor when the oracle's
-    inputs alone are rounded to BF16 (``oracle_bf16_floor``).  The kernels
-    round the activations again at every stored intermediate (about 16
-    roundings of the same size between the block input and a ReLU);
-    independent roundings add in quadrature (amplitude x4) and the flip error
-    grows as the square root of the amplitude: x2.
+The bounds (stated, and measured where the ReLU mask of the transitions
+makes a tensor miss them) and the slice check are in ``tolerances.py``.  The
+oracle of a BF16 case reads the BF16 bytes the library receives.
 """
-import json
-import os
-
 import pytest
 
-from helpers import gpu_run, oracle_bf16_floor, oracle_fwd, oracle_fwd_bwd, param_grad_errors, rel_l2
+from helpers import gpu_run, oracle_fwd, oracle_fwd_bwd, param_grad_errors, rel_l2
 from paper_2207_05477_gb300 import evo, synth
+from tolerances import BF16_GRAD_TOL, BF16_TOL, FP32_GRAD_TOL, FP32_TOL, check, slice_errors
 
 pytestmark = pytest.mark.gpu
-
-FP32_TOL = 1e-4
-FP32_GRAD_TOL = 1e-3
-BF16_TOL = 2e-2
-BF16_GRAD_TOL = 5e-2
-RELU_MASKED_TOL = 1e-1
-BF16_FLOOR_FACTOR = 2.0
-RELU_MASKED = {p + "." + t for p in ("msa_trans", "pair_trans") for t in ("ln.gamma", "ln.beta", "w1", "b1")}
 
 RAGGED = synth.Dims(n_seq=5, n_res=37)  # ragged against every 64/128-wide tile
 
 
-def _check(out, ref, tol, gtol, d, relu_tol=None, floor=None):
+def _errors(out, ref, d):
     mo, zo, dm, dz, dp = ref
     errs = {"m": rel_l2(out["m"], mo), "z": rel_l2(out["z"], zo)}
-    assert errs["m"] <= tol and errs["z"] <= tol, errs
+    refs = {"m": mo, "z": zo}
     if "dm" in out:
-        g = {"dm": rel_l2(out["dm"], dm), "dz": rel_l2(out["dz"], dz)}
-        g.update(param_grad_errors(d, out["dparams"], dp))
-        lim = {k: (relu_tol if relu_tol is not None and k in RELU_MASKED else gtol) for k in g}
-        if floor is not None:
-            lim = {k: max(v, BF16_FLOOR_FACTOR * floor[k]) for k, v in lim.items()}
-        bad = {k: v for k, v in g.items() if not v <= lim[k]}
-        assert not bad, bad
+        errs.update(dm=rel_l2(out["dm"], dm), dz=rel_l2(out["dz"], dz))
+        errs.update(param_grad_errors(d, out["dparams"], dp))
+        refs.update(dm=dm, dz=dz)
+    return errs, slice_errors(out, refs)
+
+
+def _run(case, d, act, pad_frac=0.0, trailing=False, dropout=False, seed=32):
+    bf = act == evo.EVO_BF16
+    out = gpu_run(d, act, seed=seed, pad_frac=pad_frac, trailing=trailing, dropout=dropout)
+    ref = oracle_fwd_bwd(d, seed, pad_frac, trailing, dropout, bf16_inputs=bf)
+    errs, sl = _errors(out, ref, d)
+    check(case, errs, BF16_TOL if bf else FP32_TOL, BF16_GRAD_TOL if bf else FP32_GRAD_TOL, sl)
+    return out, ref
+
+
+def _run_fwd(case, d, act, seed=32):
+    bf = act == evo.EVO_BF16
+    out = gpu_run(d, act, seed=seed, backward=False)
+    mo, zo = oracle_fwd(d, seed, bf16_inputs=bf)
+    errs = {"m": rel_l2(out["m"], mo), "z": rel_l2(out["z"], zo)}
+    check(case, errs, BF16_TOL if bf else FP32_TOL, None, slice_errors(out, {"m": mo, "z": zo}))
 
 
 def test_fp32_forward_small_config(built_lib):
-    d = synth.DIMS_SMALL_FP32
-    out = gpu_run(d, evo.EVO_F32, backward=False)
-    mo, zo = oracle_fwd(d)
-    assert rel_l2(out["m"], mo) <= FP32_TOL
-    assert rel_l2(out["z"], zo) <= FP32_TOL
-
-
-def test_fp32_fwd_bwd_ragged_padded(built_lib):
-    out = gpu_run(RAGGED, evo.EVO_F32, pad_frac=0.1)
-    _check(out, oracle_fwd_bwd(RAGGED, pad_frac=0.1), FP32_TOL, FP32_GRAD_TOL, RAGGED)
-
-
-def test_bf16_fwd_bwd_ragged_padded(built_lib):
-    out = gpu_run(RAGGED, evo.EVO_BF16, pad_frac=0.1)
-    _check(out, oracle_fwd_bwd(RAGGED, pad_frac=0.1), BF16_TOL, BF16_GRAD_TOL, RAGGED, RELU_MASKED_TOL,
-           oracle_bf16_floor(RAGGED, pad_frac=0.1))
+    _run_fwd("block_fp32_fwd_config1", synth.DIMS_SMALL_FP32, evo.EVO_F32)
 
 
 def test_bf16_forward_small_config(built_lib):
-    d = synth.DIMS_SMALL_FP32
-    out = gpu_run(d, evo.EVO_BF16, backward=False)
-    mo, zo = oracle_fwd(d)
-    assert rel_l2(out["m"], mo) <= BF16_TOL
-    assert rel_l2(out["z"], zo) <= BF16_TOL
+    _run_fwd("block_bf16_fwd_config1", synth.DIMS_SMALL_FP32, evo.EVO_BF16)
+
+
+def test_fp32_fwd_bwd_ragged_padded(built_lib):
+    _run("block_fp32_ragged", RAGGED, evo.EVO_F32, pad_frac=0.1)
+
+
+def test_bf16_fwd_bwd_ragged_padded(built_lib):
+    _run("block_bf16_ragged", RAGGED, evo.EVO_BF16, pad_frac=0.1)
 
 
 @pytest.mark.parametrize("d", [synth.Dims(n_seq=1, n_res=8), synth.Dims(n_seq=3, n_res=1)])
 def test_bf16_degenerate_sizes(built_lib, d):
     """One MSA row; one residue.  At N_res = 1 every pair-stack gradient is a
-    single-position quantity with no averaging over positions, so each tensor
-    gets the ReLU-mask bound; dm, dz and the whole parameter gradient keep 5e-2."""
-    out = gpu_run(d, evo.EVO_BF16)
-    ref = oracle_fwd_bwd(d)
-    tensor_tol = RELU_MASKED_TOL if d.n_res == 1 else BF16_GRAD_TOL
-    _check(out, ref, BF16_TOL, tensor_tol, d, RELU_MASKED_TOL)
-    import torch
-    lay, _ = synth.param_layout(d)
+    single-position quantity with no averaging over positions."""
     import numpy as np
+    import torch
+    out, ref = _run(f"block_bf16_degenerate_S{d.n_seq}_R{d.n_res}", d, evo.EVO_BF16)
+    lay, _ = synth.param_layout(d)
     flat_ref = torch.cat([torch.as_tensor(ref[4][n]).double().flatten() for n, _, _, _ in lay])
     flat_gpu = torch.cat([out["dparams"][o:o + int(np.prod(s))].double() for _, o, s, _ in lay])
     assert rel_l2(flat_gpu, flat_ref) <= BF16_GRAD_TOL
 
 
 def test_bf16_trailing_padding_and_single_valid_residue(built_lib):
-    d = synth.Dims(n_seq=4, n_res=20)
-    out = gpu_run(d, evo.EVO_BF16, pad_frac=0.95, trailing=True)
-    _check(out, oracle_fwd_bwd(d, pad_frac=0.95, trailing=True), BF16_TOL, BF16_GRAD_TOL, d, RELU_MASKED_TOL)
+    _run("block_bf16_trailing", synth.Dims(n_seq=4, n_res=20), evo.EVO_BF16, pad_frac=0.95, trailing=True)
 
 
 @pytest.mark.slow
 def test_bf16_fwd_bwd_training_crop(built_lib):
     """The paper's initial-training crop: N_seq=128, N_res=256, 5% padded residues."""
-    d = synth.DIMS_TRAIN_CROP
-    out = gpu_run(d, evo.EVO_BF16, pad_frac=0.05)
-    _check(out, oracle_fwd_bwd(d, pad_frac=0.05), BF16_TOL, BF16_GRAD_TOL, d, RELU_MASKED_TOL)
+    _run("block_bf16_crop", synth.DIMS_TRAIN_CROP, evo.EVO_BF16, pad_frac=0.05)
 
 
 @pytest.mark.slow
 def test_fp32_fwd_bwd_training_crop(built_lib):
-    d = synth.DIMS_TRAIN_CROP
-    out = gpu_run(d, evo.EVO_F32, pad_frac=0.05)
-    _check(out, oracle_fwd_bwd(d, pad_frac=0.05), FP32_TOL, FP32_GRAD_TOL, d)
+    _run("block_fp32_crop", synth.DIMS_TRAIN_CROP, evo.EVO_F32, pad_frac=0.05)
+
+
+# ------------------------------------------------- keys beyond 256 (fine-tune crop)
+@pytest.mark.slow
+def test_bf16_fwd_bwd_finetune_crop(built_lib):
+    """The paper's fine-tune crop, one block: N_seq=512, N_res=384 (model
+    settings table).  Row and triangle attention run over 384 keys, column
+    attention over 512: every attention kind beyond the 256-key tile."""
+    _run("block_bf16_finetune", synth.Dims(n_seq=512, n_res=384), evo.EVO_BF16, pad_frac=0.05)
+
+
+@pytest.mark.slow
+def test_bf16_forward_long_sequence(built_lib):
+    """A forward at N_res = 768 with four sequences: triangle attention over
+    768 keys (six 128-key blocks), the pair stack at three times the crop."""
+    _run_fwd("block_bf16_fwd_R768", synth.Dims(n_seq=4, n_res=768), evo.EVO_BF16)
 
 
 # ------------------------------------------------- extra-MSA block (global column attention)
@@ -128,29 +109,17 @@ EXTRA_MID = synth.DIMS_EXTRA_MSA.replace(n_seq=512, n_res=96)
 
 
 def test_extra_msa_fp32_fwd_bwd(built_lib):
-    out = gpu_run(EXTRA_SMALL, evo.EVO_F32, pad_frac=0.1)
-    _check(out, oracle_fwd_bwd(EXTRA_SMALL, pad_frac=0.1), FP32_TOL, FP32_GRAD_TOL, EXTRA_SMALL)
+    _run("extra_fp32_small", EXTRA_SMALL, evo.EVO_F32, pad_frac=0.1)
 
 
 def test_extra_msa_bf16_fwd_bwd(built_lib):
-    out = gpu_run(EXTRA_MID, evo.EVO_BF16, pad_frac=0.05)
-    _check(out, oracle_fwd_bwd(EXTRA_MID, pad_frac=0.05), BF16_TOL, BF16_GRAD_TOL, EXTRA_MID, RELU_MASKED_TOL)
+    _run("extra_bf16_mid", EXTRA_MID, evo.EVO_BF16, pad_frac=0.05)
 
 
 @pytest.mark.slow
 def test_extra_msa_bf16_full_size(built_lib):
-    """The paper's initial-training extra-MSA block: N_extra_seq=1024, N_res=256, c_e=64.
-
-    The oracle's own BF16 input-rounding floor is about 3 % here for the
-    gradients that pass through the global column attention (col.w_qkvg
-    3.05 %, tests/golden/bf16_floor_extra_msa.json, written by
-    tests/golden/make_bf16_floor.py from the oracle alone), so these bounds
-    take the same floor rule as the small problems."""
-    d = synth.DIMS_EXTRA_MSA
-    out = gpu_run(d, evo.EVO_BF16, pad_frac=0.05)
-    with open(os.path.join(os.path.dirname(__file__), "golden", "bf16_floor_extra_msa.json")) as f:
-        floor = json.load(f)
-    _check(out, oracle_fwd_bwd(d, pad_frac=0.05), BF16_TOL, BF16_GRAD_TOL, d, RELU_MASKED_TOL, floor)
+    """The paper's initial-training extra-MSA block: N_extra_seq=1024, N_res=256, c_e=64."""
+    _run("extra_bf16_full", synth.DIMS_EXTRA_MSA, evo.EVO_BF16, pad_frac=0.05)
 
 
 # ------------------------------------------------------- training-mode dropout
@@ -159,18 +128,13 @@ def test_extra_msa_bf16_full_size(built_lib):
 # the kernels; the bounds are those of evaluation mode.
 
 def test_fp32_fwd_bwd_dropout_ragged_padded(built_lib):
-    out = gpu_run(RAGGED, evo.EVO_F32, pad_frac=0.1, dropout=True)
-    _check(out, oracle_fwd_bwd(RAGGED, pad_frac=0.1, dropout=True), FP32_TOL, FP32_GRAD_TOL, RAGGED)
+    _run("block_fp32_ragged_dropout", RAGGED, evo.EVO_F32, pad_frac=0.1, dropout=True)
 
 
 def test_bf16_fwd_bwd_dropout_ragged_padded(built_lib):
-    out = gpu_run(RAGGED, evo.EVO_BF16, pad_frac=0.1, dropout=True)
-    _check(out, oracle_fwd_bwd(RAGGED, pad_frac=0.1, dropout=True), BF16_TOL, BF16_GRAD_TOL, RAGGED, RELU_MASKED_TOL,
-           oracle_bf16_floor(RAGGED, pad_frac=0.1, dropout=True))
+    _run("block_bf16_ragged_dropout", RAGGED, evo.EVO_BF16, pad_frac=0.1, dropout=True)
 
 
 @pytest.mark.slow
 def test_bf16_fwd_bwd_dropout_training_crop(built_lib):
-    d = synth.DIMS_TRAIN_CROP
-    out = gpu_run(d, evo.EVO_BF16, pad_frac=0.05, dropout=True)
-    _check(out, oracle_fwd_bwd(d, pad_frac=0.05, dropout=True), BF16_TOL, BF16_GRAD_TOL, d, RELU_MASKED_TOL)
+    _run("block_bf16_crop_dropout", synth.DIMS_TRAIN_CROP, evo.EVO_BF16, pad_frac=0.05, dropout=True)

@@ -10,14 +10,23 @@ from paper_2207_05477_gb300 import evo, synth
 pytestmark = pytest.mark.gpu
 
 
-def test_bounded_wait_reports_timeout_and_context_survives(built_lib):
+@pytest.mark.parametrize("unit", [evo.EVO_UNIT_GEMM, evo.EVO_UNIT_ATTENTION, evo.EVO_UNIT_TRIMUL])
+def test_bounded_wait_reports_timeout_and_context_survives(built_lib, unit):
+    """Each unit's own bounded wait (GEMM, attention, triangle multiplication)
+    runs out, its error word reports the timeout, and a block runs afterwards."""
     torch.cuda.init()
     assert evo.get_error() == evo.EVO_OK
-    evo.debug_wait_timeout(200_000_000)  # 0.2 s
+    evo.debug_wait_timeout(200_000_000, unit)  # 0.2 s
     assert evo.get_error() == evo.EVO_ERR_TIMEOUT
     assert evo.get_error() == evo.EVO_OK  # reading clears the word
     out = gpu_run(synth.Dims(n_seq=2, n_res=16), evo.EVO_BF16, backward=False)
     assert torch.isfinite(out["m"]).all() and torch.isfinite(out["z"]).all()
+
+
+def test_debug_wait_rejects_unknown_unit(built_lib):
+    with pytest.raises(evo.EvoError) as e:
+        evo.debug_wait_timeout(1000, 7)
+    assert e.value.code == evo.EVO_ERR_INVALID_ARG
 
 
 def test_workspace_too_small_is_an_error_not_a_fault(built_lib):

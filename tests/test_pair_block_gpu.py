@@ -1,21 +1,18 @@
 """Parity of the template pair stack block (AF2 Alg. 16) through the C ABI
 with the FP64 oracle, at the published template dims (c_t 64, 4 heads of 16,
-c_mul 64, transition factor 2), with training-mode dropout; bounds as for the
-Evoformer block (BF16 with the oracle's own BF16 floor rule at the ragged
-size, where the pair transition's ReLU mask makes the same few tensors
-noisy)."""
+c_mul 64, transition factor 2), with training-mode dropout; bounds and slice
+check as for the Evoformer block (``tolerances.py``)."""
 import numpy as np
 import pytest
 import torch
 
-from helpers import _to_bf16_grid, param_grad_errors, rel_l2
+from helpers import param_grad_errors, rel_l2, to_bf16_grid
 from oracle import evoformer as O
 from paper_2207_05477_gb300 import evo, synth
-from test_block_gpu import BF16_FLOOR_FACTOR, BF16_GRAD_TOL, BF16_TOL, FP32_GRAD_TOL, FP32_TOL, RELU_MASKED_TOL
+from tolerances import BF16_GRAD_TOL, BF16_TOL, FP32_GRAD_TOL, FP32_TOL, check, slice_errors
 
 pytestmark = pytest.mark.gpu
 
-RELU_MASKED = {"pair_trans." + t for t in ("ln.gamma", "ln.beta", "w1", "b1")}
 RAGGED = synth.DIMS_TEMPLATE.replace(n_res=37)
 
 
@@ -25,8 +22,8 @@ def _problem(d, seed=41, pad=0.1):
 
 
 def _oracle(d, prob, dr, bf16_inputs=False):
-    cast = _to_bf16_grid if bf16_inputs else (lambda x: x)
-    p = synth.unpack_params(d, cast(prob["params"]))
+    cast = to_bf16_grid if bf16_inputs else (lambda x: x)
+    p = synth.unpack_params(d, prob["params"])
     return O.pair_block_forward_backward(cast(prob["z"]), prob["pair_mask"], p, d, cast(prob["gz"]), dropout=dr)
 
 
@@ -50,50 +47,28 @@ def _gpu(d, prob, dr, act):
     return z_out.double().cpu(), dz.double().cpu(), dp.double().cpu()
 
 
-def _errors(d, out, ref):
+def _check(case, d, out, ref, tol, gtol):
     zo, dz, dp = out
     errs = {"z": rel_l2(zo, ref[0]), "dz": rel_l2(dz, ref[1])}
     errs.update(param_grad_errors(d, dp, ref[2]))
-    return errs
-
-
-def _bounds(errs, tol, gtol, relu_tol, floor=None):
-    lim = {k: (tol if k == "z" else relu_tol if k in RELU_MASKED else gtol) for k in errs}
-    if floor is not None:
-        lim = {k: max(v, BF16_FLOOR_FACTOR * floor[k]) for k, v in lim.items()}
-    return {k: v for k, v in errs.items() if not v <= lim[k]}
+    check(case, errs, tol, gtol, slice_errors({"z": zo, "dz": dz}, {"z": ref[0], "dz": ref[1]}))
 
 
 def test_fp32_pair_block_ragged_dropout(built_lib):
     prob, dr = _problem(RAGGED)
-    ref = _oracle(RAGGED, prob, dr)
-    bad = _bounds(_errors(RAGGED, _gpu(RAGGED, prob, dr, evo.EVO_F32), ref), FP32_TOL, FP32_GRAD_TOL, FP32_GRAD_TOL)
-    assert not bad, bad
-
-
-def _packed(d, dp):
-    """The flat (padded) buffer layout of a name -> gradient dict."""
-    lay, total = synth.param_layout(d)
-    out = torch.zeros(total, dtype=torch.float64)
-    for name, off, shape, _ in lay:
-        out[off:off + int(np.prod(shape))] = torch.as_tensor(dp[name]).double().flatten()
-    return out
+    _check("pair_fp32_ragged_dropout", RAGGED, _gpu(RAGGED, prob, dr, evo.EVO_F32), _oracle(RAGGED, prob, dr),
+           FP32_TOL, FP32_GRAD_TOL)
 
 
 def test_bf16_pair_block_ragged_dropout(built_lib):
     prob, dr = _problem(RAGGED)
-    ref = _oracle(RAGGED, prob, dr)
-    zo_f, dz_f, dp_f = _oracle(RAGGED, prob, dr, bf16_inputs=True)
-    floor = _errors(RAGGED, (zo_f, dz_f, _packed(RAGGED, dp_f)), ref)
-    bad = _bounds(_errors(RAGGED, _gpu(RAGGED, prob, dr, evo.EVO_BF16), ref), BF16_TOL, BF16_GRAD_TOL,
-                  RELU_MASKED_TOL, floor)
-    assert not bad, bad
+    _check("pair_bf16_ragged_dropout", RAGGED, _gpu(RAGGED, prob, dr, evo.EVO_BF16),
+           _oracle(RAGGED, prob, dr, bf16_inputs=True), BF16_TOL, BF16_GRAD_TOL)
 
 
 @pytest.mark.slow
 def test_bf16_pair_block_template_crop_dropout(built_lib):
     d = synth.DIMS_TEMPLATE
     prob, dr = _problem(d, pad=0.05)
-    ref = _oracle(d, prob, dr)
-    bad = _bounds(_errors(d, _gpu(d, prob, dr, evo.EVO_BF16), ref), BF16_TOL, BF16_GRAD_TOL, RELU_MASKED_TOL)
-    assert not bad, bad
+    _check("pair_bf16_crop_dropout", d, _gpu(d, prob, dr, evo.EVO_BF16), _oracle(d, prob, dr, bf16_inputs=True),
+           BF16_TOL, BF16_GRAD_TOL)

@@ -9,9 +9,10 @@ oracle with the same bounds as the untuned BF16 path.
 """
 import pytest
 
-from helpers import gpu_run, oracle_bf16_floor, oracle_fwd_bwd
+from helpers import gpu_run, oracle_fwd_bwd
 from paper_2207_05477_gb300 import evo, synth
-from test_block_gpu import BF16_GRAD_TOL, BF16_TOL, RELU_MASKED_TOL, _check
+from test_block_gpu import _errors
+from tolerances import BF16_GRAD_TOL, BF16_TOL, check
 
 pytestmark = pytest.mark.gpu
 
@@ -23,14 +24,18 @@ TUNE_DIMS = synth.Dims(n_seq=16, n_res=48)
 
 def test_bf16_every_tuning_candidate_matches_oracle(built_lib):
     d = TUNE_DIMS
-    ref = oracle_fwd_bwd(d, pad_frac=0.1)
-    floor = oracle_bf16_floor(d, pad_frac=0.1)
+    ref = oracle_fwd_bwd(d, pad_frac=0.1, bf16_inputs=True)
+
+    def _check(out):
+        errs, slices = _errors(out, ref, d)
+        check("tune_bf16_16x48", errs, BF16_TOL, BF16_GRAD_TOL, slices)
+
     evo.tune_clear()
     evo.tune_begin()
     try:
         for _ in range(12):
             out = gpu_run(d, evo.EVO_BF16, pad_frac=0.1)
-            _check(out, ref, BF16_TOL, BF16_GRAD_TOL, d, RELU_MASKED_TOL, floor)
+            _check(out)
         n = evo.tune_end()
         entries = evo.tune_entries()
         assert n == len(entries) > 0
@@ -39,7 +44,7 @@ def test_bf16_every_tuning_candidate_matches_oracle(built_lib):
         assert any(e["splits"] != 1 or e["default_splits"] != 1 for e in entries), entries
         # the tuned table is what later launches use
         out = gpu_run(d, evo.EVO_BF16, pad_frac=0.1)
-        _check(out, ref, BF16_TOL, BF16_GRAD_TOL, d, RELU_MASKED_TOL, floor)
+        _check(out)
     finally:
         evo.tune_clear()
     assert evo.tune_entries() == []
