@@ -700,7 +700,13 @@ cudaError_t attn_fwd(const AttnArgs &a, int use_bf16, cudaStream_t s) {
 static cudaError_t attn_bwd_accumulating(const AttnArgs &a, int use_bf16, cudaStream_t s, double flops, double io) {
   cudaError_t e = cudaMemsetAsync(a.dq_acc, 0, (size_t)a.B1 * a.X * a.H * a.c * sizeof(float), s);
   if (e != cudaSuccess) return e;
-  {
+  bool done = false;
+  if (use_bf16 && attn_bwd_stream_supported(a)) {
+    e = attn_bwd_stream_launch(a, s, flops, io);
+    if (e != cudaErrorNotSupported && e != cudaSuccess) return e;
+    done = e == cudaSuccess;
+  }
+  if (!done) {
     Prof p(use_bf16 ? "attn_bwd_mma" : "attn_bwd_simt", s, flops, io, use_bf16 ? 1 : 2);
     if (use_bf16) {
       if (!mma_ok(a)) return cudaErrorInvalidValue;

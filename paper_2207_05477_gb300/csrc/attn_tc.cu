@@ -933,11 +933,14 @@ struct AttnTcBwdArgs {
   int fused_gate;     // dO slots hold dog; g and o tiles are loaded too
 };
 
-// Byte offset of element (mn, k) in a [2 kb][2 mc][64 k][64 mn] bf16 tile
-// with the 128-byte swizzle (the MN-major operand layout, K = 128, MN = 128).
-__device__ __forceinline__ uint32_t mn_major_off(int mn, int k) {
-  const int kb = k >> 6, kr = k & 63, mc = mn >> 6, m = mn & 63;
-  return (uint32_t)(kb * 16384 + mc * 8192 + kr * 128 + ((((m >> 3) ^ (kr & 7)) & 7) << 4) + (m & 7) * 2);
+// Byte offset of element (key, q) in a [2 key chunks][128 q][64 keys] bf16
+// tile with the 128-byte swizzle: rows of 64 keys, one per query.  Read as
+// P^T / dS^T (M = keys, K = queries) it is the MN-major operand of dV and
+// dK (key chunks LBO = 16 KB apart); read as dS (M = queries, K = keys) it is
+// the K-major operand of dQ (a 16-key k-step 32 bytes into a row).
+__device__ __forceinline__ uint32_t ds_off(int key, int q) {
+  const int mc = key >> 6, m = key & 63;
+  return (uint32_t)(mc * 16384 + q * 128 + ((((m >> 3) ^ (q & 7)) & 7) << 4) + (m & 7) * 2);
 }
 
 __global__ void __launch_bounds__(AT_WARPS * 32, 1) attn_bwd_tc(const __grid_constant__ CUtensorMap tmQ,
@@ -1073,45 +1076,54 @@ __global__ void __launch_bounds__(AT_WARPS * 32, 1) attn_bwd_tc(const __grid_con
   const uint32_t bring = base + BT_B_OFF + (uint32_t)warp * 2 * 4096u;
   int bias_issued = 0, bias_done = 0;
 
+  const int nit = nkh * nq;  // sub-tiles
+  // S = Q_qt K_kh^T and dP = dO_qt V_kh^T of sub-tile `it` (thread 0)
+  auto issue_sdp = [&](int it) {
+    const int kh = it / nq, qt = it - kh * nq;
+    tc_fence_after();
+    const uint32_t idesc = instr_desc(128, 128, false, false);
+#pragma unroll
+    for (int ks = 0; ks < AT_C / 16; ++ks) {
+      const uint64_t qd = smem_desc(base + BT_Q_OFF + qt * 8192 + ks * 32, 16, 512, 4);
+      const uint64_t kd = smem_desc(base + BT_K_OFF + kh * 8192 + ks * 32, 16, 512, 4);
+      mma_ss(tmem + BT_S_COL, qd, kd, idesc, ks > 0 ? 1u : 0u);
+    }
+#pragma unroll
+    for (int ks = 0; ks < AT_C / 16; ++ks) {
+      const uint64_t od = smem_desc(base + BT_DO_OFF + qt * 8192 + ks * 32, 16, 512, 4);
+      const uint64_t vd = smem_desc(base + BT_V_OFF + kh * 8192 + ks * 32, 16, 512, 4);
+      mma_ss(tmem + BT_DP_COL, od, vd, idesc, ks > 0 ? 1u : 0u);
+    }
+    mma_commit(&bar_sd);
+    ++nsd;
+  };
+  // this warp's pair-bias box of sub-tile `it` (its 32 query rows x its 64
+  // keys, bf16) into its ring slot it % 2 (lane 0)
+  auto issue_bias = [&](int it) {
+    const int kh = it / nq, qt = it - kh * nq;
+    mbar_arrive_expect_tx(&bar_b[warp][it & 1], 4096);
+    tma_load_3d(bring + (uint32_t)(it & 1) * 4096u, &tmB, kh * 128 + half * 64, qt * 128 + quarter * 32, h,
+                &bar_b[warp][it & 1]);
+    ++bias_issued;
+  };
+  if (a.bias && lane == 0 && ok)
+    for (int it = 0; it < 2 && it < nit; ++it) issue_bias(it);
+  if (tid == 0 && ok && !s_abort) issue_sdp(0);
+
   for (int kh = 0; kh < nkh; ++kh) {
     for (int qt = 0; qt < nq; ++qt) {
       const int it = kh * nq + qt;  // sub-tile counter (barrier phases)
-      // this warp's pair-bias chunks: rows qt*128 + 32 quarter.., keys kh*128 + 64 half + 32 t
-      if (a.bias && lane == 0 && ok) {
-        // one bf16 box: the warp's 32 query rows x its 64 keys
-        mbar_arrive_expect_tx(&bar_b[warp][0], 4096);
-        tma_load_3d(bring, &tmB, kh * 128 + half * 64, qt * 128 + quarter * 32, h, &bar_b[warp][0]);
-        ++bias_issued;
-      }
-      if (tid == 0 && ok && !s_abort) {
-        tc_fence_after();
-        const uint32_t idesc = instr_desc(128, 128, false, false);
-#pragma unroll
-        for (int ks = 0; ks < AT_C / 16; ++ks) {
-          const uint64_t qd = smem_desc(base + BT_Q_OFF + qt * 8192 + ks * 32, 16, 512, 4);
-          const uint64_t kd = smem_desc(base + BT_K_OFF + kh * 8192 + ks * 32, 16, 512, 4);
-          mma_ss(tmem + BT_S_COL, qd, kd, idesc, ks > 0 ? 1u : 0u);
-        }
-#pragma unroll
-        for (int ks = 0; ks < AT_C / 16; ++ks) {
-          const uint64_t od = smem_desc(base + BT_DO_OFF + qt * 8192 + ks * 32, 16, 512, 4);
-          const uint64_t vd = smem_desc(base + BT_V_OFF + kh * 8192 + ks * 32, 16, 512, 4);
-          mma_ss(tmem + BT_DP_COL, od, vd, idesc, ks > 0 ? 1u : 0u);
-        }
-        mma_commit(&bar_sd);
-        ++nsd;
-      }
       ok = __all_sync(0xffffffffu, ok && mbar_wait(&bar_sd, (uint32_t)(it & 1), &s_abort));
       tc_fence_after();
       const int row = quarter * 32 + lane;  // query row in the tile
       const int xq = qt * 128 + row;
       const float lse = lse_s[xq < 256 ? xq : 255], dd = d_s[xq < 256 ? xq : 255];
-      uint32_t pk[2][16];
 #pragma unroll
       for (int t = 0; t < 2; ++t) {
         const int cl = half * 2 + t;           // 32-key chunk within the key half
         const int y0 = kh * 128 + cl * 32;     // first key of the chunk
-        if (a.bias && t == 0) ok = __all_sync(0xffffffffu, ok && mbar_wait(&bar_b[warp][0], (uint32_t)(it & 1), &s_abort));
+        if (a.bias && t == 0)
+          ok = __all_sync(0xffffffffu, ok && mbar_wait(&bar_b[warp][it & 1], (uint32_t)((it >> 1) & 1), &s_abort));
         if (ok && a.bias) bias_done = it + 1;
         if (ok) {
           uint32_t sr[32], pr[32];
@@ -1120,7 +1132,7 @@ __global__ void __launch_bounds__(AT_WARPS * 32, 1) attn_bwd_tc(const __grid_con
           float bv[32];
           if (a.bias) {
             // pieces 4t .. 4t + 3 of this lane's 128-byte (64-key) row, 128-byte swizzle
-            const uint32_t rb = bring + lane * 128u;
+            const uint32_t rb = bring + (uint32_t)(it & 1) * 4096u + lane * 128u;
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
               uint4 w;
@@ -1142,7 +1154,7 @@ __global__ void __launch_bounds__(AT_WARPS * 32, 1) attn_bwd_tc(const __grid_con
             p[k] = ex2(lg - lse);
             ds[k] = p[k] * (__uint_as_float(pr[k]) - dd);
           }
-          // P and dS into the MN-major operand tiles (element (key, query) at mn_major_off)
+          // P and dS into the operand tiles (element (key, query) at ds_off)
 #pragma unroll
           for (int j = 0; j < 4; ++j) {
             uint32_t wp[4], wd[4];
@@ -1153,7 +1165,7 @@ __global__ void __launch_bounds__(AT_WARPS * 32, 1) attn_bwd_tc(const __grid_con
               wp[i] = *reinterpret_cast<uint32_t *>(&a2);
               wd[i] = *reinterpret_cast<uint32_t *>(&d2);
             }
-            const uint32_t off = mn_major_off(cl * 32 + 8 * j, row);
+            const uint32_t off = ds_off(cl * 32 + 8 * j, row);
             asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(base + BT_P_OFF + off), "r"(wp[0]),
                          "r"(wp[1]), "r"(wp[2]), "r"(wp[3])
                          : "memory");
@@ -1161,44 +1173,35 @@ __global__ void __launch_bounds__(AT_WARPS * 32, 1) attn_bwd_tc(const __grid_con
                          "r"(wd[1]), "r"(wd[2]), "r"(wd[3])
                          : "memory");
           }
-#pragma unroll
-          for (int i = 0; i < 16; ++i) {
-            __nv_bfloat162 d2 = __floats2bfloat162_rn(ds[2 * i], ds[2 * i + 1]);
-            pk[t][i] = *reinterpret_cast<uint32_t *>(&d2);
-          }
         }
       }
-      // every warp has read its dP columns: dS pairs may now land over them
-      tc_fence_before();
-      __syncthreads();
-      tc_fence_after();
-      if (ok) {
-        tmem_st16(lane_base + BT_DP_COL + (uint32_t)((half * 2) * 16), pk[0]);
-        tmem_st16(lane_base + BT_DP_COL + (uint32_t)((half * 2 + 1) * 16), pk[1]);
-      }
-      tmem_wait_st();
+      // every warp has read S and dP and written its P / dS rows (read by the
+      // tensor cores: async proxy); the next pair-bias box may reuse the slot
       fence_proxy_async();
       tc_fence_before();
       __syncthreads();
+      if (a.bias && lane == 0 && ok && it + 2 < nit) issue_bias(it + 2);
       if (tid == 0 && ok && !s_abort) {
         tc_fence_after();
         const uint32_t id_kv = instr_desc(128, AT_C, true, true);   // A = P^T / dS^T (MN-major), B = dO / Q (MN-major)
-        const uint32_t id_q = instr_desc(128, AT_C, false, true);   // A = dS (TMEM), B = K (MN-major)
+        const uint32_t id_q = instr_desc(128, AT_C, false, true);   // A = dS (K-major), B = K (MN-major)
         for (int ks = 0; ks < 8; ++ks) {
-          const uint32_t aoff = (uint32_t)((ks >> 2) * 16384 + (ks & 3) * 2048);
-          const uint64_t pd = smem_desc(base + BT_P_OFF + aoff, 8192, 1024, 2);
-          const uint64_t dsd = smem_desc(base + BT_DS_OFF + aoff, 8192, 1024, 2);
+          const uint64_t pd = smem_desc(base + BT_P_OFF + ks * 2048, 16384, 1024, 2);
+          const uint64_t dsd = smem_desc(base + BT_DS_OFF + ks * 2048, 16384, 1024, 2);
+          const uint64_t dsk = smem_desc(base + BT_DS_OFF + (ks >> 2) * 16384 + (ks & 3) * 32, 16, 1024, 2);
           const uint64_t od = smem_desc(base + BT_DO_OFF + qt * 8192 + ks * 1024, 16384, 512, 4);
           const uint64_t qd = smem_desc(base + BT_Q_OFF + qt * 8192 + ks * 1024, 16384, 512, 4);
           const uint64_t kd = smem_desc(base + BT_K_OFF + kh * 8192 + ks * 1024, 16384, 512, 4);
           const uint32_t acc_kv = (qt > 0 || ks > 0) ? 1u : 0u;
           mma_ss(tmem + BT_DV_COL, pd, od, id_kv, acc_kv);
           mma_ss(tmem + BT_DK_COL, dsd, qd, id_kv, acc_kv);
-          mma_ts(tmem + BT_DQ_COL + (uint32_t)(qt * 32), tmem + BT_DP_COL + (uint32_t)(ks * 8), kd, id_q,
-                 (kh > 0 || ks > 0) ? 1u : 0u);
+          mma_ss(tmem + BT_DQ_COL + (uint32_t)(qt * 32), dsk, kd, id_q, (kh > 0 || ks > 0) ? 1u : 0u);
         }
         mma_commit(&bar_mm);
         ++nmm;
+        // the next sub-tile's S and dP (their TMEM columns were read above;
+        // the tensor cores run these after the products just issued)
+        if (it + 1 < nit) issue_sdp(it + 1);
       }
       // pair-bias gradient from the shared dS copy: warp w takes query rows w, w + 8, ..
       if (a.dbias && ok) {
@@ -1206,7 +1209,7 @@ __global__ void __launch_bounds__(AT_WARPS * 32, 1) attn_bwd_tc(const __grid_con
           const int x = qt * 128 + r;
           const int y = kh * 128 + lane * 4;
           if (x >= a.X || y >= a.Y) continue;
-          const uint32_t off = mn_major_off(lane * 4, r);
+          const uint32_t off = ds_off(lane * 4, r);
           uint32_t w0, w1;
           asm volatile("ld.shared.v2.b32 {%0, %1}, [%2];" : "=r"(w0), "=r"(w1) : "r"(base + BT_DS_OFF + off));
           const float2 f0 = __bfloat1622float2(*reinterpret_cast<__nv_bfloat162 *>(&w0));
@@ -1286,12 +1289,417 @@ __global__ void __launch_bounds__(AT_WARPS * 32, 1) attn_bwd_tc(const __grid_con
       for (int i = 0; i < nmm; ++i) mbar_drain(&bar_mm, (uint32_t)(i & 1));
     }
     if (lane == 0)
-      for (int j = bias_done; j < bias_issued; ++j) mbar_drain(&bar_b[warp][0], (uint32_t)(j & 1));
+      for (int j = bias_done; j < bias_issued; ++j) mbar_drain(&bar_b[warp][j & 1], (uint32_t)((j >> 1) & 1));
   }
   tc_fence_before();
   __syncthreads();
   if (warp == 0) {
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)BT_TMEM_COLS)
+                 : "memory");
+  }
+}
+
+// ------------------------------------------------------- backward, any length
+// Any number of queries and keys, head dim c in {8, 16, 32} (rows zero-padded
+// to 32 channels in shared memory).  One CTA of eight warps per (128-key
+// block, head, batch item), looping over the query tiles of 128:
+//   S = Q_t K^T, dP = dO_t V^T                                (TMEM [0,128), [128,256))
+//   P = 2^(logit - lse2), dS = P (dP - D)     thread = query row, two warps
+//                                              per TMEM lane quarter on 64 keys each
+//   P, dS (bf16) -> shared memory (ds_off layout): the MN-major A operands of
+//     dV += P^T dO_t, dK += dS^T Q_t                          (TMEM [256,288), [288,320))
+//   and the K-major A operand of dQ_t = dS K                  (TMEM [320,352))
+//   dQ_t is added into the fp32 dQ accumulator with vector atomics (every key
+//   block of the row adds its share); dbias[h][x][y] += dS likewise.
+// do_att (the gradient of the ungated output) and D = rowsum(do_att * o)
+// come from the gate pass before this kernel.  The next tile's Q, dO (TMA,
+// or at c < 32 rows fetched into registers a tile ahead) and the pair-bias
+// boxes (per warp, two slots) are in flight while a tile is processed.
+constexpr int BS_TMEM_COLS = 512;
+constexpr int BS_S_COL = 0, BS_DP_COL = 128, BS_DK_COL = 256, BS_DV_COL = 288, BS_DQ_COL = 320;
+// dynamic shared memory (1 KB aligned base)
+constexpr int BS_K_OFF = 0;                               // [128 keys][64 B]
+constexpr int BS_V_OFF = 8192;                            // [128 keys][64 B]
+constexpr int BS_Q_OFF = 16384;                           // 2 x [128 q][64 B]
+constexpr int BS_DO_OFF = BS_Q_OFF + 2 * 8192;            // 2 x [128 q][64 B]
+constexpr int BS_P_OFF = BS_DO_OFF + 2 * 8192;            // [2 key chunks][128 q][128 B]
+constexpr int BS_DS_OFF = BS_P_OFF + 32768;               // same layout
+constexpr int BS_B_OFF = BS_DS_OFF + 32768;               // per warp 2 x [32 rows][64 keys] bf16
+constexpr int BS_M_OFF = BS_B_OFF + AT_WARPS * 2 * 4096;  // maskadd [128]
+constexpr int BS_SMEM = BS_M_OFF + 128 * 4 + 1024;
+
+struct AttnBwdStreamArgs {
+  AttnArgs a;
+  QkvPos pq, pk, po;  // q / k, v / do_att map dimension positions (TMA path)
+  int tma;            // q, k, v, do_att by TMA (head dim 32); else rows loaded by the threads
+  int nq;             // query tiles of 128
+  int has_bias;
+};
+
+__global__ void __launch_bounds__(AT_WARPS * 32, 1) attn_bwd_stream(const __grid_constant__ CUtensorMap tmQ,
+                                                                    const __grid_constant__ CUtensorMap tmK,
+                                                                    const __grid_constant__ CUtensorMap tmV,
+                                                                    const __grid_constant__ CUtensorMap tmO,
+                                                                    const __grid_constant__ CUtensorMap tmB,
+                                                                    AttnBwdStreamArgs A) {
+  pdl_trigger();
+  extern __shared__ uint8_t dsm[];
+  __shared__ __align__(8) uint64_t bar_kv, bar_in[2], bar_sd, bar_mm, bar_b[AT_WARPS][2];
+  __shared__ uint32_t tmem_slot;
+  __shared__ volatile int s_abort;
+  const AttnArgs &a = A.a;
+  const uint32_t raw = smem_u32(dsm);
+  const uint32_t base = (raw + 1023u) & ~1023u;
+  uint8_t *gbase = dsm + (base - raw);
+  float *maskadd = reinterpret_cast<float *>(gbase + BS_M_OFF);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, tid = threadIdx.x;
+  const int quarter = warp & 3, half = warp >> 2;
+  const int kb = blockIdx.x, h = blockIdx.y, b = blockIdx.z;
+  const int y0 = kb * 128, nq = A.nq, c = a.c, per = c >> 3;
+
+  if (tid == 0) {
+    mbar_init(&bar_kv, 1);
+    mbar_init(&bar_in[0], 1);
+    mbar_init(&bar_in[1], 1);
+    mbar_init(&bar_sd, 1);
+    mbar_init(&bar_mm, 1);
+    for (int w = 0; w < AT_WARPS; ++w) mbar_init(&bar_b[w][0], 1), mbar_init(&bar_b[w][1], 1);
+    s_abort = 0;
+    fence_mbar_init();
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                 "r"((uint32_t)BS_TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_slot;
+  pdl_wait();
+
+  const int64_t qoff = (int64_t)b * a.sQb + (int64_t)h * c;   // q rows
+  const int64_t ooff = (int64_t)b * a.sOb + (int64_t)h * c;   // do_att rows
+  const int64_t koff = (int64_t)b * a.sKb + (int64_t)h * c;   // k, v rows
+  int in_issued = 0, in_done = 0, bias_issued = 0, bias_done = 0;
+  bool kv_issued = false;
+  int nsd = 0, nmm = 0;
+  // Q_t and dO_t into slot t % 2 (thread 0, TMA)
+  auto issue_in = [&](int t) {
+    int cc[4];
+    mbar_arrive_expect_tx(&bar_in[t & 1], 2 * 8192);
+    tile_coords(A.pq, t * 128, h, b, cc);
+    tma_load_4d(base + BS_Q_OFF + (t & 1) * 8192, &tmQ, cc[0], cc[1], cc[2], cc[3], &bar_in[t & 1]);
+    tile_coords(A.po, t * 128, h, b, cc);
+    tma_load_4d(base + BS_DO_OFF + (t & 1) * 8192, &tmO, cc[0], cc[1], cc[2], cc[3], &bar_in[t & 1]);
+    ++in_issued;
+  };
+  // this warp's pair-bias box of tile t (its 32 query rows x its 64 keys) into slot t % 2 (lane 0)
+  const uint32_t bring = base + BS_B_OFF + (uint32_t)warp * 2 * 4096u;
+  auto issue_bias = [&](int t) {
+    mbar_arrive_expect_tx(&bar_b[warp][t & 1], 4096);
+    tma_load_3d(bring + (uint32_t)(t & 1) * 4096u, &tmB, y0 + half * 64, t * 128 + quarter * 32, h,
+                &bar_b[warp][t & 1]);
+    ++bias_issued;
+  };
+  // rows of the untiled path: thread tid owns pieces tid and tid + 256 of a 128-row tile
+  uint4 pq_reg[2], po_reg[2];
+  auto fetch_in = [&](int t) {
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const int idx = tid + 256 * u, r = idx / per, q = idx - r * per, x = t * 128 + r;
+      const bool in = idx < 128 * per && x < a.X;
+      pq_reg[u] = in ? *reinterpret_cast<const uint4 *>((const bf16 *)a.q + qoff + (int64_t)x * a.sQx + q * 8)
+                     : make_uint4(0, 0, 0, 0);
+      po_reg[u] = in ? *reinterpret_cast<const uint4 *>((const bf16 *)a.do_att + ooff + (int64_t)x * a.sOx + q * 8)
+                     : make_uint4(0, 0, 0, 0);
+    }
+  };
+  auto store_in = [&](int t) {
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const int idx = tid + 256 * u, r = idx / per, q = idx - r * per;
+      if (idx < 128 * per) {
+        sts128(base + BS_Q_OFF + (t & 1) * 8192 + sw64_off(r, q), pq_reg[u]);
+        sts128(base + BS_DO_OFF + (t & 1) * 8192 + sw64_off(r, q), po_reg[u]);
+      }
+    }
+  };
+
+  if (A.tma) {
+    if (tid == 0) {
+      int cc[4];
+      mbar_arrive_expect_tx(&bar_kv, 2 * 8192);
+      tile_coords(A.pk, y0, h, b, cc);
+      tma_load_4d(base + BS_K_OFF, &tmK, cc[0], cc[1], cc[2], cc[3], &bar_kv);
+      tma_load_4d(base + BS_V_OFF, &tmV, cc[0], cc[1], cc[2], cc[3], &bar_kv);
+      kv_issued = true;
+      issue_in(0);
+      if (nq > 1) issue_in(1);
+    }
+  } else {
+    // zero-padded rows: pieces past the head dim stay zero in every tile
+    for (int i = tid; i < 128 * 4; i += blockDim.x) {
+      const int r = i >> 2, q = i & 3;
+      if (q >= per) {
+        const uint4 z = make_uint4(0, 0, 0, 0);
+        sts128(base + BS_K_OFF + sw64_off(r, q), z);
+        sts128(base + BS_V_OFF + sw64_off(r, q), z);
+        for (int sl = 0; sl < 2; ++sl) {
+          sts128(base + BS_Q_OFF + sl * 8192 + sw64_off(r, q), z);
+          sts128(base + BS_DO_OFF + sl * 8192 + sw64_off(r, q), z);
+        }
+      }
+    }
+    for (int idx = tid; idx < 128 * per; idx += blockDim.x) {
+      const int r = idx / per, q = idx - r * per, y = y0 + r;
+      uint4 kv = make_uint4(0, 0, 0, 0), vv = kv;
+      if (y < a.Y) {
+        kv = *reinterpret_cast<const uint4 *>((const bf16 *)a.k + koff + (int64_t)y * a.sKy + q * 8);
+        vv = *reinterpret_cast<const uint4 *>((const bf16 *)a.v + koff + (int64_t)y * a.sKy + q * 8);
+      }
+      sts128(base + BS_K_OFF + sw64_off(r, q), kv);
+      sts128(base + BS_V_OFF + sw64_off(r, q), vv);
+    }
+    fetch_in(0);
+    store_in(0);
+    if (nq > 1) fetch_in(1);
+    fence_proxy_async();
+    if (tid == 0) {
+      mbar_arrive(&bar_kv);
+      mbar_arrive(&bar_in[0]);
+    }
+  }
+  if (a.bias && lane == 0)
+    for (int t = 0; t < 2 && t < nq; ++t) issue_bias(t);
+  // the key mask of the block
+  if (tid < 128) {
+    const int y = y0 + tid;
+    bool valid = y < a.Y;
+    if (valid && a.mask) valid = a.mask[(int64_t)b * a.sMb + (int64_t)y * a.sMy] != 0.f;
+    maskadd[tid] = valid ? 0.f : NEG_INF_F;
+  }
+  __syncthreads();
+  bool ok = __all_sync(0xffffffffu, mbar_wait(&bar_kv, 0, &s_abort));
+
+  const float sl2 = a.scale * EVO_LOG2E;
+  const uint32_t lane_base = tmem + ((uint32_t)(quarter * 32) << 16);
+  const int row = quarter * 32 + lane;  // query row in the tile (TMEM lane)
+  float lse_n = POS_INF_F, d_n = 0.f;   // the row statistics of tile t, read a tile ahead
+  if (row < a.X) {
+    lse_n = a.lse2[((int64_t)b * a.H + h) * a.X + row];
+    d_n = a.Dsum[((int64_t)b * a.H + h) * a.X + row];
+  }
+
+  for (int t = 0; t < nq; ++t) {
+    const float lse = lse_n, dd = d_n;
+    {
+      const int xn = (t + 1) * 128 + row;
+      lse_n = POS_INF_F, d_n = 0.f;
+      if (t + 1 < nq && xn < a.X) {
+        lse_n = a.lse2[((int64_t)b * a.H + h) * a.X + xn];
+        d_n = a.Dsum[((int64_t)b * a.H + h) * a.X + xn];
+      }
+    }
+    if (!A.tma && t > 0) {
+      // this tile's rows, fetched during the last one, into its slot (free:
+      // the last products that read it finished before the last tile ended)
+      store_in(t);
+      fence_proxy_async();
+      __syncthreads();
+      if (t + 1 < nq) fetch_in(t + 1);
+      if (tid == 0) mbar_arrive(&bar_in[t & 1]);
+    }
+    if (tid == 0 && ok && !s_abort) {
+      ok = mbar_wait(&bar_in[t & 1], (uint32_t)((t >> 1) & 1), &s_abort);
+      if (ok) {
+        in_done = t + 1;
+        tc_fence_after();
+        const uint32_t idesc = instr_desc(128, 128, false, false);
+        for (int ks = 0; ks < (c + 15) / 16; ++ks) {
+          const uint64_t qd = smem_desc(base + BS_Q_OFF + (t & 1) * 8192 + ks * 32, 16, 512, 4);
+          const uint64_t kd = smem_desc(base + BS_K_OFF + ks * 32, 16, 512, 4);
+          mma_ss(tmem + BS_S_COL, qd, kd, idesc, ks > 0 ? 1u : 0u);
+        }
+        for (int ks = 0; ks < (c + 15) / 16; ++ks) {
+          const uint64_t od = smem_desc(base + BS_DO_OFF + (t & 1) * 8192 + ks * 32, 16, 512, 4);
+          const uint64_t vd = smem_desc(base + BS_V_OFF + ks * 32, 16, 512, 4);
+          mma_ss(tmem + BS_DP_COL, od, vd, idesc, ks > 0 ? 1u : 0u);
+        }
+        mma_commit(&bar_sd);
+        ++nsd;
+      }
+    }
+    ok = __all_sync(0xffffffffu, ok && mbar_wait(&bar_sd, (uint32_t)(t & 1), &s_abort));
+    tc_fence_after();
+#pragma unroll
+    for (int tt = 0; tt < 2; ++tt) {
+      const int cl = half * 2 + tt;  // 32-key chunk of the block
+      if (a.bias && tt == 0)
+        ok = __all_sync(0xffffffffu, ok && mbar_wait(&bar_b[warp][t & 1], (uint32_t)((t >> 1) & 1), &s_abort));
+      if (ok && a.bias) bias_done = t + 1;
+      if (ok) {
+        uint32_t sr[32], pr[32];
+        tmem_ld32(lane_base + BS_S_COL + (uint32_t)(cl * 32), sr);
+        tmem_ld32(lane_base + BS_DP_COL + (uint32_t)(cl * 32), pr);
+        float bv[32];
+        if (a.bias) {
+          const uint32_t rb = bring + (uint32_t)(t & 1) * 4096u + lane * 128u;
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            const uint4 w = lds128(rb + (uint32_t)(((4 * tt + k) ^ (lane & 7)) << 4));
+            const __nv_bfloat162 *hv = reinterpret_cast<const __nv_bfloat162 *>(&w);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              const float2 f = __bfloat1622float2(hv[q]);
+              bv[8 * k + 2 * q] = f.x, bv[8 * k + 2 * q + 1] = f.y;
+            }
+          }
+        } else {
+#pragma unroll
+          for (int k = 0; k < 32; ++k) bv[k] = 0.f;
+        }
+        float p[32], ds[32];
+#pragma unroll
+        for (int k = 0; k < 32; ++k) {
+          const float lg = fmaf(__uint_as_float(sr[k]), sl2, fmaf(bv[k], EVO_LOG2E, maskadd[cl * 32 + k]));
+          p[k] = ex2(lg - lse);
+          ds[k] = p[k] * (__uint_as_float(pr[k]) - dd);
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          uint4 wp, wd;
+          uint32_t *pp = reinterpret_cast<uint32_t *>(&wp), *pd = reinterpret_cast<uint32_t *>(&wd);
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            __nv_bfloat162 a2 = __floats2bfloat162_rn(p[8 * j + 2 * i], p[8 * j + 2 * i + 1]);
+            __nv_bfloat162 d2 = __floats2bfloat162_rn(ds[8 * j + 2 * i], ds[8 * j + 2 * i + 1]);
+            pp[i] = *reinterpret_cast<uint32_t *>(&a2);
+            pd[i] = *reinterpret_cast<uint32_t *>(&d2);
+          }
+          const uint32_t off = ds_off(cl * 32 + 8 * j, row);
+          sts128(base + BS_P_OFF + off, wp);
+          sts128(base + BS_DS_OFF + off, wd);
+        }
+      }
+    }
+    // every warp has read S and dP and written its P / dS rows (read by the
+    // tensor cores: async proxy); the pair-bias slot of this tile is free
+    fence_proxy_async();
+    tc_fence_before();
+    __syncthreads();
+    if (a.bias && lane == 0 && ok && t + 2 < nq) issue_bias(t + 2);
+    if (tid == 0 && ok && !s_abort) {
+      tc_fence_after();
+      const uint32_t id_kv = instr_desc(128, AT_C, true, true);  // A = P^T / dS^T (MN-major), B = dO / Q (MN-major)
+      const uint32_t id_q = instr_desc(128, AT_C, false, true);  // A = dS (K-major), B = K (MN-major)
+      for (int ks = 0; ks < 8; ++ks) {
+        const uint64_t pd = smem_desc(base + BS_P_OFF + ks * 2048, 16384, 1024, 2);
+        const uint64_t dsd = smem_desc(base + BS_DS_OFF + ks * 2048, 16384, 1024, 2);
+        const uint64_t dsk = smem_desc(base + BS_DS_OFF + (ks >> 2) * 16384 + (ks & 3) * 32, 16, 1024, 2);
+        const uint64_t od = smem_desc(base + BS_DO_OFF + (t & 1) * 8192 + ks * 1024, 16384, 512, 4);
+        const uint64_t qd = smem_desc(base + BS_Q_OFF + (t & 1) * 8192 + ks * 1024, 16384, 512, 4);
+        const uint64_t kd = smem_desc(base + BS_K_OFF + ks * 1024, 16384, 512, 4);
+        const uint32_t acc_kv = (t > 0 || ks > 0) ? 1u : 0u;
+        mma_ss(tmem + BS_DV_COL, pd, od, id_kv, acc_kv);
+        mma_ss(tmem + BS_DK_COL, dsd, qd, id_kv, acc_kv);
+        mma_ss(tmem + BS_DQ_COL, dsk, kd, id_q, ks > 0 ? 1u : 0u);
+      }
+      mma_commit(&bar_mm);
+      ++nmm;
+    }
+    // pair-bias gradient from the shared dS copy: warp w takes query rows w, w + 8, ..
+    if (a.dbias && ok) {
+      const bool vec = (a.Y & 3) == 0;
+      for (int r = warp; r < 128; r += AT_WARPS) {
+        const int x = t * 128 + r, y = y0 + lane * 4;
+        if (x >= a.X || y >= a.Y) continue;
+        uint32_t w0, w1;
+        asm volatile("ld.shared.v2.b32 {%0, %1}, [%2];" : "=r"(w0), "=r"(w1) : "r"(base + BS_DS_OFF + ds_off(lane * 4, r)));
+        const float2 f0 = __bfloat1622float2(*reinterpret_cast<__nv_bfloat162 *>(&w0));
+        const float2 f1 = __bfloat1622float2(*reinterpret_cast<__nv_bfloat162 *>(&w1));
+        float *dst = a.dbias + (int64_t)h * a.sBh + (int64_t)x * a.sBx + y;
+        if (vec) {
+          asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(dst), "f"(f0.x), "f"(f0.y), "f"(f1.x),
+                       "f"(f1.y)
+                       : "memory");
+        } else {
+          const float fv[4] = {f0.x, f0.y, f1.x, f1.y};
+          for (int e = 0; e < 4 && y + e < a.Y; ++e) atomicAdd(dst + e, fv[e]);
+        }
+      }
+    }
+    ok = __all_sync(0xffffffffu, ok && mbar_wait(&bar_mm, (uint32_t)(t & 1), &s_abort));
+    tc_fence_after();
+    // dQ_t into the fp32 accumulator: thread = query row, the two warps of a quarter 16 channels each
+    {
+      const int x = t * 128 + row, d0 = half * 16;
+      uint32_t rq[16];
+      if (ok) tmem_ld16(lane_base + BS_DQ_COL + (uint32_t)d0, rq);
+      if (ok && x < a.X && d0 < c) {
+        float *dst = a.dq_acc + (int64_t)b * a.sOb + (int64_t)x * a.sOx + (int64_t)h * c + d0;
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          if (4 * q < c - d0)
+            asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(dst + 4 * q),
+                         "f"(__uint_as_float(rq[4 * q])), "f"(__uint_as_float(rq[4 * q + 1])),
+                         "f"(__uint_as_float(rq[4 * q + 2])), "f"(__uint_as_float(rq[4 * q + 3]))
+                         : "memory");
+      }
+    }
+    // the next tile rewrites the shared P / dS copies, the TMEM S / dP / dQ
+    // columns and this tile's Q, dO slot
+    tc_fence_before();
+    __syncthreads();
+    if (A.tma && tid == 0 && ok && t + 2 < nq) issue_in(t + 2);
+  }
+  // dK, dV of the block: thread = key row, the two warps of a quarter take 16 channels each
+  {
+    const int y = y0 + quarter * 32 + lane, d0 = half * 16;
+    uint32_t rk[16], rv[16];
+    if (ok) {
+      tmem_ld16(lane_base + BS_DK_COL + (uint32_t)d0, rk);
+      tmem_ld16(lane_base + BS_DV_COL + (uint32_t)d0, rv);
+    }
+    if (ok && y < a.Y && d0 < c) {
+      bf16 *dk = (bf16 *)a.dk + koff + (int64_t)y * a.sKy + d0;
+      bf16 *dv = (bf16 *)a.dv + koff + (int64_t)y * a.sKy + d0;
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        if (8 * q < c - d0) {
+          uint4 wk, wv;
+          uint32_t *k32 = reinterpret_cast<uint32_t *>(&wk), *v32 = reinterpret_cast<uint32_t *>(&wv);
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            __nv_bfloat162 k2 = __floats2bfloat162_rn(__uint_as_float(rk[8 * q + 2 * i]) * a.scale,
+                                                      __uint_as_float(rk[8 * q + 2 * i + 1]) * a.scale);
+            __nv_bfloat162 v2 =
+                __floats2bfloat162_rn(__uint_as_float(rv[8 * q + 2 * i]), __uint_as_float(rv[8 * q + 2 * i + 1]));
+            k32[i] = *reinterpret_cast<uint32_t *>(&k2);
+            v32[i] = *reinterpret_cast<uint32_t *>(&v2);
+          }
+          *reinterpret_cast<uint4 *>(dk + 8 * q) = wk;
+          *reinterpret_cast<uint4 *>(dv + 8 * q) = wv;
+        }
+      }
+    }
+  }
+  // drain (after an abort) anything still in flight before the CTA exits
+  if (s_abort) {
+    if (tid == 0) {
+      if (kv_issued) mbar_drain(&bar_kv, 0);
+      for (int i = in_done; i < in_issued; ++i) mbar_drain(&bar_in[i & 1], (uint32_t)((i >> 1) & 1));
+      if (nmm > 0) mbar_drain(&bar_mm, (uint32_t)((nmm - 1) & 1));
+      if (nsd > 0) mbar_drain(&bar_sd, (uint32_t)((nsd - 1) & 1));
+    }
+    if (lane == 0)
+      for (int j = bias_done; j < bias_issued; ++j) mbar_drain(&bar_b[warp][j & 1], (uint32_t)((j >> 1) & 1));
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)BS_TMEM_COLS)
                  : "memory");
   }
 }
@@ -1486,6 +1894,49 @@ __global__ void attn_tc_debug_wait_kernel(int64_t limit_ns) {
 
 cudaError_t attn_tc_debug_wait(int64_t limit_ns, cudaStream_t s) {
   launch_k(attn_tc_debug_wait_kernel, 1, 32, 0, s, limit_ns);
+  return cudaGetLastError();
+}
+
+bool attn_bwd_stream_supported(const AttnArgs &a) {
+  auto a16 = [](const void *p) { return ((uintptr_t)p & 15u) == 0; };
+  if (!attn_tc_supported(a) || !a.dq_acc || !a.dk || !a.dv || !a.do_att || !a.Dsum) return false;
+  if (!a16(a.dq_acc) || !a16(a.dk) || !a16(a.dv) || !a16(a.do_att)) return false;
+  if (a.bias && !a.dbias) return false;
+  return a.Y <= 65535 * 128;
+}
+
+cudaError_t attn_bwd_stream_launch(const AttnArgs &a, cudaStream_t s, double flops, double bytes) {
+  AttnBwdStreamArgs A{};
+  A.a = a;
+  A.nq = (a.X + 127) / 128;
+  A.has_bias = a.bias != nullptr;
+  CUtensorMap tq, tk, tv, to, tb;
+  std::memset(&tq, 0, sizeof(tq));
+  std::memset(&tk, 0, sizeof(tk));
+  std::memset(&tv, 0, sizeof(tv));
+  std::memset(&to, 0, sizeof(to));
+  std::memset(&tb, 0, sizeof(tb));
+  QkvPos pv;
+  A.tma = a.c == AT_C && qkv_map(&tq, a.q, a.H, a.X, a.B1, a.sQx, a.sQb, 128, &A.pq) &&
+          qkv_map(&tk, a.k, a.H, a.Y, a.B1, a.sKy, a.sKb, 128, &A.pk) &&
+          qkv_map(&tv, a.v, a.H, a.Y, a.B1, a.sKy, a.sKb, 128, &pv) &&
+          qkv_map(&to, a.do_att, a.H, a.X, a.B1, a.sOx, a.sOb, 128, &A.po);
+  if (a.bias) {
+    const uint64_t dims[3] = {(uint64_t)a.Y, (uint64_t)a.X, (uint64_t)a.H};
+    const uint64_t st[2] = {(uint64_t)a.sBx * 2, (uint64_t)a.sBh * 2};
+    const uint32_t box[3] = {64, 32, 1};
+    if (!make_tmap_nd(&tb, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, a.bias, dims, st, box, CU_TENSOR_MAP_SWIZZLE_128B))
+      return cudaErrorNotSupported;
+  }
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(attn_bwd_stream, cudaFuncAttributeMaxDynamicSharedMemorySize, BS_SMEM);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  dim3 grid((a.Y + 127) / 128, a.H, a.B1);
+  Prof p("attn_bwd_tc", s, flops, bytes);
+  launch_k(attn_bwd_stream, grid, AT_WARPS * 32, BS_SMEM, s, tq, tk, tv, to, tb, A);
   return cudaGetLastError();
 }
 

@@ -88,6 +88,12 @@ cudaError_t attn_fwd_tc_launch(const AttnArgs &a, cudaStream_t s, double flops, 
 // the pair-bias gradient; cudaErrorNotSupported (nothing launched) as above.
 bool attn_bwd_tc_supported(const AttnArgs &a);
 cudaError_t attn_bwd_tc_launch(const AttnArgs &a, cudaStream_t s, double flops, double bytes);
+// tcgen05 backward of any length and head dims 8, 16, 32: reads do_att and
+// Dsum (the gate pass), adds the unscaled query gradient into dq_acc (fp32,
+// zeroed by the caller) and the pair-bias gradient into dbias, writes dk, dv;
+// cudaErrorNotSupported (nothing launched) when the views do not fit.
+bool attn_bwd_stream_supported(const AttnArgs &a);
+cudaError_t attn_bwd_stream_launch(const AttnArgs &a, cudaStream_t s, double flops, double bytes);
 // Reads and clears the error word of the tcgen05 attention kernels; synchronous.
 cudaError_t attn_tc_error_read_clear(int *out);
 // one CTA whose bounded wait (this unit's own) runs out after limit_ns
