@@ -560,6 +560,7 @@ def other_workload(args):
     extra_msa       extra-MSA block fwd+bwd (global column attention), N_extra=1024 N_res=256 c_e=64
     stack48         48-block stack fwd+bwd, N_seq=512 N_res=384, per-block recompute (block inputs kept)
     long2048        one block forward at N_res=2048, N_seq=128
+    long4096        one block forward at N_res=4096, N_seq=128 in the inference workspace plan
     batch16         16 proteins (N_res ~ U[64,1024], N_seq ~ U[32,512], seeded), 48-block forward each
     template_pair   template pair stack block fwd+bwd (AF2 Alg. 16), N_res=256, c_t=64, dropout
     adam48          fused training update (global-norm clip, Adam, EMA, BF16 copy) over the flat
@@ -674,22 +675,31 @@ def other_workload(args):
                 "clocks": clk, "data": "synthetic", "l2": "state 1.8 GB > L2, no flush"}
         print(json.dumps(line), flush=True)
         return 0
-    if w in ("small_fp32_fwd", "long2048", "extra_msa"):
+    if w in ("small_fp32_fwd", "long2048", "long4096", "extra_msa"):
+        infer = w == "long4096"
         if w == "small_fp32_fwd":
             d, act, bwd = synth.DIMS_SMALL_FP32, evo.EVO_F32, False
         elif w == "long2048":
             d, act, bwd = synth.Dims(n_seq=128, n_res=2048), evo.EVO_BF16, False
+        elif w == "long4096":
+            d, act, bwd = synth.Dims(n_seq=128, n_res=4096), evo.EVO_BF16, False
         else:
             d, act, bwd = synth.DIMS_EXTRA_MSA, evo.EVO_BF16, True
         B = buffers(d, act, 32)
         cd = B["cd"]
         mo, zo = torch.empty_like(B["m"]), torch.empty_like(B["z"])
-        wsf = evo.workspace(cd, evo.EVO_MODE_FWD, dev)
+        wsf = evo.workspace(cd, evo.EVO_MODE_INFER if infer else evo.EVO_MODE_FWD, dev)
         wsb = evo.workspace(cd, evo.EVO_MODE_BWD, dev) if bwd else None
         dm, dz, dp = torch.empty_like(B["m"]), torch.empty_like(B["z"]), torch.zeros_like(B["params"])
+        if infer:
+            extra["workspace_gb"] = wsf.numel() * wsf.element_size() / 1e9
+            extra["plan"] = "inference workspace plan (evo_block_fwd_infer)"
 
         def fn():
-            evo.block_fwd(cd, B["params"], B["p16"], B["m"], B["z"], mo, zo, B["mm"], B["pm"], wsf)
+            if infer:
+                evo.block_fwd_infer(cd, B["params"], B["p16"], B["m"], B["z"], mo, zo, B["mm"], B["pm"], wsf)
+            else:
+                evo.block_fwd(cd, B["params"], B["p16"], B["m"], B["z"], mo, zo, B["mm"], B["pm"], wsf)
             if bwd:
                 evo.block_bwd(cd, B["params"], B["p16"], B["m"], B["z"], B["mm"], B["pm"], B["gm"], B["gz"], dm, dz,
                               dp, wsb)
@@ -824,7 +834,7 @@ def main():
     ap.add_argument("--eager", action="store_true", help="time eager launches instead of a CUDA graph replay")
     ap.add_argument("--workload", default="train_crop",
                     choices=["train_crop", "small_fp32_fwd", "extra_msa", "stack48", "long2048", "batch16",
-                             "template_pair", "adam48"])
+                             "template_pair", "adam48", "long4096"])
     args = ap.parse_args()
     args.graph = not args.eager
     if args.warmup < 3 and args.impl == "ours":

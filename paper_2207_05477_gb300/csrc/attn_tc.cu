@@ -151,7 +151,7 @@ struct AttnTcArgs {
 };
 
 
-__global__ void __launch_bounds__(AT_WARPS * 32) attn_fwd_short(const __grid_constant__ CUtensorMap tmQ,
+__global__ void __launch_bounds__(AT_WARPS * 32, 2) attn_fwd_short(const __grid_constant__ CUtensorMap tmQ,
                                                              const __grid_constant__ CUtensorMap tmK,
                                                              const __grid_constant__ CUtensorMap tmV,
                                                              const __grid_constant__ CUtensorMap tmB, AttnTcArgs A) {
@@ -251,15 +251,25 @@ __global__ void __launch_bounds__(AT_WARPS * 32) attn_fwd_short(const __grid_con
   bool ok = __all_sync(0xffffffffu, mbar_wait(&bar_s, 0, &s_abort));
   tc_fence_after();
 
-  // pass 1 over this warp's chunks: logits (log2 domain) in place, partial row max
+  // pass 1 over this warp's chunks: logits (log2 domain) in place, partial row
+  // max; the TMEM load of the next chunk is in flight while this one is worked
   float mx = NEG_INF_F;
-  for (int j = c_lo; j < c_hi; ++j) {
-    const int bx = (j - c_lo) >> 1, hh = (j - c_lo) & 1;  // box and its half holding chunk j
-    if (A.has_bias) ok = __all_sync(0xffffffffu, ok && mbar_wait(&bar_b[warp][bx], 0, &s_abort));
+  uint32_t ra[32], rb[32];
+  if (ok && c_lo < c_hi) {
+    tmem_ld32_async(lane_base + (uint32_t)(c_lo * 32), ra);
+    tmem_wait_ld(ra);
+  }
+#pragma unroll
+  for (int t = 0; t < 4; ++t) {
+    const int j = c_lo + t;
+    if (j >= c_hi) break;
+    uint32_t(&r)[32] = (t & 1) ? rb : ra;
+    uint32_t(&nx)[32] = (t & 1) ? ra : rb;
+    const int bx = t >> 1, hh = t & 1;  // box and its half holding chunk j
+    if (A.has_bias && hh == 0) ok = __all_sync(0xffffffffu, ok && mbar_wait(&bar_b[warp][bx], 0, &s_abort));
     if (ok) bias_done = bx + 1;
     if (ok) {
-      uint32_t r[32];
-      tmem_ld32(lane_base + (uint32_t)(j * 32), r);
+      if (j + 1 < c_hi) tmem_ld32_async(lane_base + (uint32_t)((j + 1) * 32), nx);
       float v[32];
       const float4 *ma = reinterpret_cast<const float4 *>(maskadd + j * 32);
 #pragma unroll
@@ -273,26 +283,33 @@ __global__ void __launch_bounds__(AT_WARPS * 32) attn_fwd_short(const __grid_con
       if (A.has_bias) {
         // this lane's 128-byte row of the box (64 keys, 128-byte swizzle: 16-byte
         // piece k at k ^ (lane & 7)); chunk j is pieces 4 hh .. 4 hh + 3
-        const uint32_t rb = bring + bx * 4096u + lane * 128u;
+        const uint32_t rbox = bring + bx * 4096u + lane * 128u;
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
           uint4 w;
           asm volatile("ld.shared.v4.b32 {%0, %1, %2, %3}, [%4];"
                        : "=r"(w.x), "=r"(w.y), "=r"(w.z), "=r"(w.w)
-                       : "r"(rb + (uint32_t)(((4 * hh + k) ^ (lane & 7)) << 4)));
-          const bf16 *hv = reinterpret_cast<const bf16 *>(&w);
+                       : "r"(rbox + (uint32_t)(((4 * hh + k) ^ (lane & 7)) << 4)));
+          const __nv_bfloat162 *hv = reinterpret_cast<const __nv_bfloat162 *>(&w);
 #pragma unroll
-          for (int q = 0; q < 8; ++q) v[8 * k + q] = fmaf(__bfloat162float(hv[q]), EVO_LOG2E, v[8 * k + q]);
+          for (int q = 0; q < 4; ++q) {
+            const float2 f = __bfloat1622float2(hv[q]);
+            v[8 * k + 2 * q] = fmaf(f.x, EVO_LOG2E, v[8 * k + 2 * q]);
+            v[8 * k + 2 * q + 1] = fmaf(f.y, EVO_LOG2E, v[8 * k + 2 * q + 1]);
+          }
         }
       }
+      uint32_t w32[32];
 #pragma unroll
       for (int jj = 0; jj < 32; ++jj) {
         mx = fmaxf(mx, v[jj]);
-        r[jj] = __float_as_uint(v[jj]);
+        w32[jj] = __float_as_uint(v[jj]);
       }
-      tmem_st32(lane_base + (uint32_t)(j * 32), r);
+      tmem_st32(lane_base + (uint32_t)(j * 32), w32);
+      if (j + 1 < c_hi) tmem_wait_ld(nx);
     }
   }
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");  // nothing left in flight after an abort
   red[half * AT_QROWS + row] = mx;
   tmem_wait_st();
   __syncthreads();
@@ -304,12 +321,17 @@ __global__ void __launch_bounds__(AT_WARPS * 32) attn_fwd_short(const __grid_con
   const float muse = mx == NEG_INF_F ? 0.f : mx;
   float l = 0.f;
   uint32_t pk[4][16];
+  if (ok && c_lo < c_hi) {
+    tmem_ld32_async(lane_base + (uint32_t)(c_lo * 32), ra);
+    tmem_wait_ld(ra);
+  }
 #pragma unroll
   for (int t = 0; t < 4; ++t) {
     const int j = c_lo + t;
     if (ok && j < c_hi) {
-      uint32_t r[32];
-      tmem_ld32(lane_base + (uint32_t)(j * 32), r);
+      uint32_t(&r)[32] = (t & 1) ? rb : ra;
+      uint32_t(&nx)[32] = (t & 1) ? ra : rb;
+      if (j + 1 < c_hi) tmem_ld32_async(lane_base + (uint32_t)((j + 1) * 32), nx);
 #pragma unroll
       for (int i = 0; i < 16; ++i) {
         const float p0 = ex2(__uint_as_float(r[2 * i]) - muse);
@@ -318,8 +340,10 @@ __global__ void __launch_bounds__(AT_WARPS * 32) attn_fwd_short(const __grid_con
         __nv_bfloat162 hv = __floats2bfloat162_rn(p0, p1);
         pk[t][i] = *reinterpret_cast<uint32_t *>(&hv);
       }
+      if (j + 1 < c_hi) tmem_wait_ld(nx);
     }
   }
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
   red[2 * AT_QROWS + half * AT_QROWS + row] = l;
   tc_fence_before();
   __syncthreads();
@@ -1118,17 +1142,28 @@ __global__ void __launch_bounds__(AT_WARPS * 32, 1) attn_bwd_tc(const __grid_con
       const int row = quarter * 32 + lane;  // query row in the tile
       const int xq = qt * 128 + row;
       const float lse = lse_s[xq < 256 ? xq : 255], dd = d_s[xq < 256 ? xq : 255];
+      // this warp's two 32-key chunks: the TMEM loads of the second are in
+      // flight while the first is worked
+      uint32_t sa[32], pa[32], sb[32], pb[32];
+      if (a.bias) ok = __all_sync(0xffffffffu, ok && mbar_wait(&bar_b[warp][it & 1], (uint32_t)((it >> 1) & 1), &s_abort));
+      if (ok && a.bias) bias_done = it + 1;
+      if (ok) {
+        tmem_ld32_async(lane_base + BT_S_COL + (uint32_t)(half * 64), sa);
+        tmem_ld32_async(lane_base + BT_DP_COL + (uint32_t)(half * 64), pa);
+        tmem_wait_ld(sa);
+        tmem_wait_ld(pa);
+      }
 #pragma unroll
       for (int t = 0; t < 2; ++t) {
         const int cl = half * 2 + t;           // 32-key chunk within the key half
         const int y0 = kh * 128 + cl * 32;     // first key of the chunk
-        if (a.bias && t == 0)
-          ok = __all_sync(0xffffffffu, ok && mbar_wait(&bar_b[warp][it & 1], (uint32_t)((it >> 1) & 1), &s_abort));
-        if (ok && a.bias) bias_done = it + 1;
         if (ok) {
-          uint32_t sr[32], pr[32];
-          tmem_ld32(lane_base + BT_S_COL + (uint32_t)(cl * 32), sr);
-          tmem_ld32(lane_base + BT_DP_COL + (uint32_t)(cl * 32), pr);
+          uint32_t(&sr)[32] = t ? sb : sa;
+          uint32_t(&pr)[32] = t ? pb : pa;
+          if (t == 0) {
+            tmem_ld32_async(lane_base + BT_S_COL + (uint32_t)(cl * 32 + 32), sb);
+            tmem_ld32_async(lane_base + BT_DP_COL + (uint32_t)(cl * 32 + 32), pb);
+          }
           float bv[32];
           if (a.bias) {
             // pieces 4t .. 4t + 3 of this lane's 128-byte (64-key) row, 128-byte swizzle
@@ -1172,6 +1207,10 @@ __global__ void __launch_bounds__(AT_WARPS * 32, 1) attn_bwd_tc(const __grid_con
             asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(base + BT_DS_OFF + off), "r"(wd[0]),
                          "r"(wd[1]), "r"(wd[2]), "r"(wd[3])
                          : "memory");
+          }
+          if (t == 0) {
+            tmem_wait_ld(sb);
+            tmem_wait_ld(pb);
           }
         }
       }
