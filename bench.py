@@ -771,9 +771,10 @@ def other_workload(args):
                            dtype=torch.uint8, device=dev) for lane in lanes]
         work = {i: (jobs[i][1]["m"].clone(), jobs[i][1]["z"].clone()) for i in range(len(jobs))}
 
-        def fn():
+        def run_lanes(base):
+            # fork from `base` onto the lanes' streams, join back into `base`
             start = torch.cuda.Event()
-            start.record(stream)
+            start.record(base)
             for k, lane in enumerate(lanes):
                 st = streams[k]
                 st.wait_event(start)
@@ -789,7 +790,10 @@ def other_workload(args):
             for st in streams:
                 done = torch.cuda.Event()
                 done.record(st)
-                stream.wait_event(done)
+                base.wait_event(done)
+
+        def fn():
+            run_lanes(torch.cuda.current_stream())
 
         def tune_once():  # each protein's shapes, one protein at a time on one stream
             wst = torch.empty(max(evo.workspace_size(B["cd"], evo.EVO_MODE_FWD) for _, B in jobs),
@@ -802,11 +806,67 @@ def other_workload(args):
         if not args.no_tune:
             tuned = autotune(evo, tune_once, 1)
             extra["gemm_tiles"] = {"shapes": tuned["shapes"], "changed": tuned["changed"]}
-        ms, clk = timed(fn, args.steps, 1)
+
+        def as_graph(body):
+            # the whole batch (all proteins, all blocks, every stream) as one CUDA graph
+            body()  # first run outside capture: lazy kernel set-up
+            torch.cuda.synchronize()
+            g = torch.cuda.CUDAGraph()
+            cap = torch.cuda.Stream()
+            cap.wait_stream(torch.cuda.current_stream())
+            with torch.cuda.graph(g, stream=cap):
+                body()
+            torch.cuda.current_stream().wait_stream(cap)
+            torch.cuda.synchronize()
+            return g.replay
+
+        ms, clk = timed(as_graph(fn) if args.graph else fn, args.steps, 1)
         desc = (f"16 proteins (seeded N_res~U[64,1024], N_seq~U[32,512]), 48-block forward each, BF16, "
-                f"{NSTREAMS} concurrent CUDA streams")
+                f"{NSTREAMS} concurrent CUDA streams{', one CUDA graph replay per step' if args.graph else ''}")
         extra["proteins"] = prot
         extra["streams"] = NSTREAMS
+        extra["cuda_graph"] = bool(args.graph)
+
+        # the same batch through the batched C ABI: one evo_stack_fwd over the
+        # padded [16, Smax, Rmax, c] buffers, proteins one after another on one
+        # stream, each staged at its own sizes (no work on the padding)
+        for i in range(len(jobs)):
+            work[i] = None
+        del wss
+        Smax, Rmax = max(S for S, _ in prot), max(R for _, R in prot)
+        dpad = synth.Dims(n_seq=Smax, n_res=Rmax)
+        cdp = evo.cdims(dpad, evo.EVO_BF16)
+        npar = evo.param_count(cdp)
+        pstride = (npar + 127) // 128 * 128
+        p32 = torch.zeros(nb * pstride, device=dev)
+        p32[:npar] = jobs[0][1]["params"][:npar]
+        p16b = torch.zeros(nb * pstride, dtype=torch.bfloat16, device=dev)
+        p16b[:npar] = jobs[0][1]["p16"][:npar]
+        for k in range(1, nb):  # the first protein's block, repeated (the shapes are what is timed)
+            p32[k * pstride:k * pstride + npar] = p32[:npar]
+            p16b[k * pstride:k * pstride + npar] = p16b[:npar]
+        Bn = len(jobs)
+        m0 = torch.zeros(Bn, Smax, Rmax, dpad.c_m, dtype=torch.bfloat16, device=dev)
+        z0 = torch.zeros(Bn, Rmax, Rmax, dpad.c_z, dtype=torch.bfloat16, device=dev)
+        mm0 = torch.zeros(Bn, Smax, Rmax, device=dev)
+        pm0 = torch.zeros(Bn, Rmax, Rmax, device=dev)
+        for i, (S, R) in enumerate(prot):
+            B = jobs[i][1]
+            m0[i, :S, :R], z0[i, :R, :R] = B["m"], B["z"]
+            mm0[i, :S, :R], pm0[i, :R, :R] = B["mm"], B["pm"]
+        mB, zB = m0.clone(), z0.clone()
+        wsB = evo.workspace(cdp, evo.EVO_MODE_FWD, dev, batch=Bn)
+
+        def fnb():
+            mB.copy_(m0)
+            zB.copy_(z0)
+            evo.stack_fwd(cdp, nb, p32, p16b, pstride, mB, zB, mm0, pm0, wsB,
+                          n_seq_b=[S for S, _ in prot], n_res_b=[R for _, R in prot])
+
+        msb, _ = timed(as_graph(fnb) if args.graph else fnb, args.steps, 1)
+        extra["batched_abi"] = {"ms_per_step": msb, "tflops": flops / (msb / 1e3) / 1e12,
+                                "how": "one evo_stack_fwd over the padded batch, one stream" +
+                                       (", one CUDA graph replay per step" if args.graph else "")}
     line = {"workload": w, "metric": desc, "value": flops / (ms / 1e3) / 1e12, "unit": "TFLOP/s", "ms_per_step": ms,
             "steps": args.steps, "flops_per_step": flops, "frac_of_bf16_peak": flops / (ms / 1e3) / 1e12 / peaks["bf16_sus"],
             "peak_mem_gb": torch.cuda.max_memory_allocated() / 1e9, "clocks": clk, "data": "synthetic"}

@@ -94,10 +94,13 @@ int evo_params_to_bf16(const evo_dims *d, const float *params, void *params_bf16
                        evo_stream_t stream);
 
 /* Workspace bytes for evo_block_fwd (mode EVO_MODE_FWD), evo_block_bwd
- * (EVO_MODE_BWD) or evo_block_fwd_infer (EVO_MODE_INFER).  The workspace is
- * scratch owned by the caller; its content on entry is irrelevant and on
- * exit undefined. */
-int evo_workspace_size(const evo_dims *d, int mode, size_t *bytes);
+ * (EVO_MODE_BWD) or evo_block_fwd_infer (EVO_MODE_INFER), and for
+ * evo_stack_fwd over `batch` proteins padded to d's sizes (EVO_MODE_FWD):
+ * batch 1 is the block's plan; batch > 1 adds the staging of one protein
+ * (its m, z and masks in compact layout, see evo_stack_fwd).  The workspace
+ * is scratch owned by the caller; its content on entry is irrelevant and on
+ * exit undefined.  EVO_ERR_INVALID_ARG for batch < 1 or an unknown mode. */
+int evo_workspace_size(const evo_dims *d, int batch, int mode, size_t *bytes);
 
 /* Forward of one block: (m_out, z_out) = Evoformer(m_in, z_in).
  * m_out may equal m_in and z_out may equal z_in (in-place update).
@@ -168,14 +171,31 @@ int evo_block_bwd_dropout(const evo_dims *d, const float *params, const void *pa
                           const void *dm_out, const void *dz_out, void *dm_in, void *dz_in,
                           float *dparams, void *workspace, size_t ws_bytes, evo_stream_t stream);
 
-/* Forward through n_blocks consecutive blocks (the EvoformerStack, Fig. 1),
- * updating m and z in place.  Block b reads params + b*param_stride and
- * params_bf16 + b*param_stride (bf16 elements).  Workspace as for
- * EVO_MODE_FWD. */
-int evo_stack_fwd(const evo_dims *d, int n_blocks, const float *params,
-                  const void *params_bf16, size_t param_stride,
-                  void *m, void *z, const float *msa_mask, const float *pair_mask,
-                  void *workspace, size_t ws_bytes, evo_stream_t stream);
+/* Forward through n_blocks consecutive blocks (the EvoformerStack, Fig. 1)
+ * of a batch of proteins, updating m and z in place.
+ *  - d holds the padded sizes Smax = d->n_seq, Rmax = d->n_res and the
+ *    channels; protein i has n_seq_b[i] sequences and n_res_b[i] residues
+ *    (host arrays; 1 <= n_seq_b[i] <= Smax, 1 <= n_res_b[i] <= Rmax).  With
+ *    batch 1 they may be NULL and the protein has the padded sizes.
+ *  - Device buffers padded per protein (row-major, channel innermost):
+ *    m [batch][Smax][Rmax][c_m], z [batch][Rmax][Rmax][c_z],
+ *    msa_mask [batch][Smax][Rmax], pair_mask [batch][Rmax][Rmax] (fp32 0/1;
+ *    the masks mark padding inside a protein's own sizes, as for a block).
+ *    Entries outside a protein's sizes are neither read nor written.
+ *  - Block k reads params + k*param_stride and params_bf16 + k*param_stride
+ *    (bf16 elements); every protein runs the same blocks.
+ *  - Workspace: evo_workspace_size(d, batch, EVO_MODE_FWD).  A protein at
+ *    the padded sizes with batch 1 runs in place; in a batch each protein is
+ *    staged into the workspace in compact layout, run through the blocks at
+ *    its own sizes (no work on the padding) and written back.  The proteins
+ *    run one after another on `stream`; results equal those of
+ *    evo_stack_fwd on each protein alone, bit for bit.
+ * Returns EVO_ERR_INVALID_ARG for a bad size or stride, EVO_ERR_WORKSPACE
+ * when ws_bytes is too small. */
+int evo_stack_fwd(const evo_dims *d, int n_blocks, int batch, const int32_t *n_seq_b,
+                  const int32_t *n_res_b, const float *params, const void *params_bf16,
+                  size_t param_stride, void *m, void *z, const float *msa_mask,
+                  const float *pair_mask, void *workspace, size_t ws_bytes, evo_stream_t stream);
 
 /* Forward of one block, as evo_block_fwd, but allocating nothing and taking
  * no workspace: its scratch is a 128 MiB array inside the library, reserved

@@ -46,11 +46,25 @@ int evo_params_to_bf16(const evo_dims *d, const float *params, void *params_bf16
   return f32_to_bf16(params, (bf16 *)params_bf16, n, (cudaStream_t)stream) == cudaSuccess ? EVO_OK : EVO_ERR_CUDA;
 }
 
-int evo_workspace_size(const evo_dims *d, int mode, size_t *bytes) {
-  if (!bytes || (mode != EVO_MODE_FWD && mode != EVO_MODE_BWD && mode != EVO_MODE_INFER)) return EVO_ERR_INVALID_ARG;
+namespace {
+
+size_t al256(size_t x) { return (x + 255) / 256 * 256; }
+
+// Staging of one protein of a padded batch: m, z and both masks in compact layout.
+size_t staging_bytes(const evo_dims &d) {
+  const size_t es = d.act_dtype == EVO_BF16 ? 2 : 4;
+  const size_t S = (size_t)d.n_seq, R = (size_t)d.n_res;
+  return al256(S * R * d.c_m * es) + al256(R * R * d.c_z * es) + al256(S * R * 4) + al256(R * R * 4);
+}
+
+}  // namespace
+
+int evo_workspace_size(const evo_dims *d, int batch, int mode, size_t *bytes) {
+  if (!bytes || batch < 1 || (mode != EVO_MODE_FWD && mode != EVO_MODE_BWD && mode != EVO_MODE_INFER))
+    return EVO_ERR_INVALID_ARG;
   const int v = validate_dims(d);
   if (v != EVO_OK) return v;
-  *bytes = workspace_bytes(*d, mode);
+  *bytes = workspace_bytes(*d, mode) + (batch > 1 ? staging_bytes(*d) : 0);
   return EVO_OK;
 }
 
@@ -132,18 +146,64 @@ int evo_block_bwd_dropout(const evo_dims *d, const float *params, const void *pa
                         dz_in, dparams, workspace, ws_bytes, (cudaStream_t)stream, dropout);
 }
 
-int evo_stack_fwd(const evo_dims *d, int n_blocks, const float *params, const void *params_bf16, size_t param_stride,
-                  void *m, void *z, const float *msa_mask, const float *pair_mask, void *workspace, size_t ws_bytes,
+int evo_stack_fwd(const evo_dims *d, int n_blocks, int batch, const int32_t *n_seq_b, const int32_t *n_res_b,
+                  const float *params, const void *params_bf16, size_t param_stride, void *m, void *z,
+                  const float *msa_mask, const float *pair_mask, void *workspace, size_t ws_bytes,
                   evo_stream_t stream) {
   const int v = validate_dims(d);
   if (v != EVO_OK) return v;
-  if (n_blocks < 0 || param_stride < evo_param_count(d) || param_stride % 128) return EVO_ERR_INVALID_ARG;
+  if (n_blocks < 0 || batch < 1 || param_stride < evo_param_count(d) || param_stride % 128) return EVO_ERR_INVALID_ARG;
+  if (batch > 1 && (!n_seq_b || !n_res_b)) return EVO_ERR_INVALID_ARG;
+  const int Smax = d->n_seq, Rmax = d->n_res;
+  for (int i = 0; i < batch && n_seq_b && n_res_b; ++i)
+    if (n_seq_b[i] < 1 || n_seq_b[i] > Smax || n_res_b[i] < 1 || n_res_b[i] > Rmax) return EVO_ERR_INVALID_ARG;
+  if (batch == 1 && n_seq_b && n_res_b && (n_seq_b[0] != Smax || n_res_b[0] != Rmax)) return EVO_ERR_INVALID_ARG;
+  if (n_blocks == 0) return EVO_OK;  // the identity: nothing to launch
+  if (!params || !m || !z || !msa_mask || !pair_mask || !workspace) return EVO_ERR_INVALID_ARG;
   const bool bf = d->act_dtype == EVO_BF16;
-  for (int b = 0; b < n_blocks; ++b) {
-    const float *p = params + (size_t)b * param_stride;
-    const void *p16 = bf ? (const void *)((const bf16 *)params_bf16 + (size_t)b * param_stride) : nullptr;
-    const int r = evo_block_fwd(d, p, p16, m, z, m, z, msa_mask, pair_mask, workspace, ws_bytes, stream);
+  const cudaStream_t s = (cudaStream_t)stream;
+  auto run = [&](const evo_dims *dd, void *mm, void *zz, const float *ms, const float *ps, void *ws, size_t wb) {
+    for (int k = 0; k < n_blocks; ++k) {
+      const float *p = params + (size_t)k * param_stride;
+      const void *p16 = bf ? (const void *)((const bf16 *)params_bf16 + (size_t)k * param_stride) : nullptr;
+      const int r = evo_block_fwd(dd, p, p16, mm, zz, mm, zz, ms, ps, ws, wb, stream);
+      if (r != EVO_OK) return r;
+    }
+    return (int)EVO_OK;
+  };
+  if (batch == 1) return run(d, m, z, msa_mask, pair_mask, workspace, ws_bytes);
+
+  // a padded batch: each protein staged in compact layout after the block plan
+  const size_t plan = workspace_bytes(*d, EVO_MODE_FWD);
+  if (ws_bytes < plan + staging_bytes(*d)) return EVO_ERR_WORKSPACE;
+  const size_t es = bf ? 2 : 4;
+  char *st = (char *)workspace + al256(plan);
+  if ((uintptr_t)st % 256) return EVO_ERR_ALIGNMENT;
+  char *sm = st;
+  char *sz = sm + al256((size_t)Smax * Rmax * d->c_m * es);
+  char *smm = sz + al256((size_t)Rmax * Rmax * d->c_z * es);
+  char *spm = smm + al256((size_t)Smax * Rmax * 4);
+  const int mw = d->c_m * (int)es / 4, zw = d->c_z * (int)es / 4;  // 32-bit words per row
+  for (int i = 0; i < batch; ++i) {
+    const int S = n_seq_b[i], R = n_res_b[i];
+    evo_dims di = *d;
+    di.n_seq = S, di.n_res = R;
+    char *mi = (char *)m + (size_t)i * Smax * Rmax * d->c_m * es;
+    char *zi = (char *)z + (size_t)i * Rmax * Rmax * d->c_z * es;
+    const float *mmi = msa_mask + (size_t)i * Smax * Rmax;
+    const float *pmi = pair_mask + (size_t)i * Rmax * Rmax;
+    // gather: [S][R][.] of the padded [Smax][Rmax][.] slot into compact rows
+    if (copy_rows_strided(mi, sm, S, R, Rmax, R, mw, s) != cudaSuccess ||
+        copy_rows_strided(zi, sz, R, R, Rmax, R, zw, s) != cudaSuccess ||
+        copy_rows_strided(mmi, smm, S, R, Rmax, R, 1, s) != cudaSuccess ||
+        copy_rows_strided(pmi, spm, R, R, Rmax, R, 1, s) != cudaSuccess)
+      return EVO_ERR_CUDA;
+    const int r = run(&di, sm, sz, (const float *)smm, (const float *)spm, workspace, plan);
     if (r != EVO_OK) return r;
+    // scatter the updated m and z back into the slot
+    if (copy_rows_strided(sm, mi, S, R, R, Rmax, mw, s) != cudaSuccess ||
+        copy_rows_strided(sz, zi, R, R, R, Rmax, zw, s) != cudaSuccess)
+      return EVO_ERR_CUDA;
   }
   return EVO_OK;
 }

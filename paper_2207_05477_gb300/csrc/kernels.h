@@ -218,5 +218,9 @@ cudaError_t row_scale(const void *x, const float *scale, void *y, int64_t M, int
 cudaError_t to_f32(const void *src, float *dst, int64_t n, int use_bf16, cudaStream_t s);
 cudaError_t from_f32(const float *src, void *dst, int64_t n, int use_bf16, cudaStream_t s);
 cudaError_t f32_to_bf16(const float *src, bf16 *dst, int64_t n, cudaStream_t s);
+// Copies A x B rows of W 32-bit words between row-major [.][src_B][W] and
+// [.][dst_B][W] layouts (the staging of a padded protein).
+cudaError_t copy_rows_strided(const void *src, void *dst, int64_t A, int64_t B, int64_t src_B, int64_t dst_B, int W,
+                              cudaStream_t s);
 
 }  // namespace evo

@@ -1393,6 +1393,35 @@ cudaError_t from_f32(const float *src, void *dst, int64_t n, int use_bf16, cudaS
   else launch_k(from_f32_k<float>, nblk(n), 256, 0, s, src, (float *)dst, n);
   return cudaGetLastError();
 }
+namespace {
+// dst[(a * dst_B + b) * W + w] = src[(a * src_B + b) * W + w] for a < A, b < B,
+// w < W (32-bit words): one row (a, b) of W words per warp step.
+__global__ void __launch_bounds__(256) copy_rows_k(const uint32_t *src, uint32_t *dst, int64_t A, int64_t B,
+                                                    int64_t src_B, int64_t dst_B, int W) {
+  pdl_entry();
+  const int64_t rows = A * B;
+  const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  for (int64_t r = wid; r < rows; r += nw) {
+    const int64_t a = r / B, b = r - a * B;
+    const uint32_t *sp = src + (a * src_B + b) * W;
+    uint32_t *dp = dst + (a * dst_B + b) * W;
+    for (int w = lane; w < W; w += 32) dp[w] = sp[w];
+  }
+}
+}  // namespace
+
+cudaError_t copy_rows_strided(const void *src, void *dst, int64_t A, int64_t B, int64_t src_B, int64_t dst_B, int W,
+                              cudaStream_t s) {
+  if (A <= 0 || B <= 0 || W <= 0) return cudaSuccess;
+  Prof prof("copy_rows", s, 0, 8.0 * A * B * W);
+  const int64_t warps = A * B;
+  const unsigned grid = (unsigned)std::min<int64_t>((warps + 7) / 8, 152 * 16);
+  launch_k(copy_rows_k, grid, 256, 0, s, (const uint32_t *)src, (uint32_t *)dst, A, B, src_B, dst_B, W);
+  return cudaGetLastError();
+}
+
 cudaError_t f32_to_bf16(const float *src, bf16 *dst, int64_t n, cudaStream_t s) {
   Prof prof("convert", s, 0, 6.0 * n, 1);
   launch_k(from_f32_k<bf16>, nblk(n), 256, 0, s, src, dst, n);

@@ -79,7 +79,7 @@ def lib():
         L.evo_param_layout.argtypes = [P(CDims), P(CParamEntry), ctypes.c_int]
         L.evo_params_bf16_size.argtypes = [P(CDims), P(_sz)]
         L.evo_params_to_bf16.argtypes = [P(CDims), _vp, _vp, _vp]
-        L.evo_workspace_size.argtypes = [P(CDims), ctypes.c_int, P(_sz)]
+        L.evo_workspace_size.argtypes = [P(CDims), ctypes.c_int, ctypes.c_int, P(_sz)]
         L.evo_block_fwd.argtypes = [P(CDims), _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _sz, _vp]
         L.evo_block_fwd_infer.argtypes = [P(CDims), _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _sz, _vp]
         L.evo_block_bwd.argtypes = [P(CDims), _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _sz,
@@ -96,7 +96,8 @@ def lib():
         L.evo_pair_block_fwd.argtypes = [P(CDims), _vp, _vp, _vp, _vp, _vp, P(CDropout), _vp, _sz, _vp]
         L.evo_pair_block_bwd.argtypes = [P(CDims), _vp, _vp, _vp, _vp, P(CDropout), _vp, _vp, _vp, _vp, _sz, _vp]
         L.evo_block_fwd_noalloc.argtypes = [P(CDims), _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]
-        L.evo_stack_fwd.argtypes = [P(CDims), ctypes.c_int, _vp, _vp, _sz, _vp, _vp, _vp, _vp, _vp, _sz, _vp]
+        L.evo_stack_fwd.argtypes = [P(CDims), ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, _vp, _sz, _vp, _vp, _vp, _vp,
+                                    _vp, _sz, _vp]
         L.evo_adam_workspace_size.argtypes = [_sz]
         L.evo_adam_workspace_size.restype = _sz
         L.evo_adam_step.argtypes = [P(CAdam), _sz, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _sz, _vp]
@@ -159,9 +160,9 @@ def param_layout(cd):
     return [(e.name.decode(), int(e.offset), tuple(int(e.shape[k]) for k in range(e.ndim))) for e in arr]
 
 
-def workspace_size(cd, mode):
+def workspace_size(cd, mode, batch=1):
     out = _sz(0)
-    _check(lib().evo_workspace_size(ctypes.byref(cd), mode, ctypes.byref(out)), "evo_workspace_size")
+    _check(lib().evo_workspace_size(ctypes.byref(cd), int(batch), mode, ctypes.byref(out)), "evo_workspace_size")
     return int(out.value)
 
 
@@ -283,10 +284,19 @@ def block_fwd_infer(cd, params, params_bf16, m, z, m_out, z_out, msa_mask, pair_
                                      ws.numel() * ws.element_size(), _stream(stream)), "evo_block_fwd_infer")
 
 
-def stack_fwd(cd, n_blocks, params, params_bf16, param_stride, m, z, msa_mask, pair_mask, ws, stream=None):
-    _check(lib().evo_stack_fwd(ctypes.byref(cd), n_blocks, _ptr(params), _ptr(params_bf16), param_stride, _ptr(m),
-                               _ptr(z), _ptr(msa_mask), _ptr(pair_mask), _ptr(ws), ws.numel() * ws.element_size(),
-                               _stream(stream)), "evo_stack_fwd")
+def stack_fwd(cd, n_blocks, params, params_bf16, param_stride, m, z, msa_mask, pair_mask, ws, stream=None,
+              n_seq_b=None, n_res_b=None):
+    """n_blocks blocks over m, z in place.  With n_seq_b / n_res_b (lists of
+    per-protein sizes) m, z and the masks are padded batches
+    [batch, Smax, Rmax, ...] with cd's sizes as Smax, Rmax."""
+    batch, sb, rb = 1, None, None
+    if n_seq_b is not None:
+        batch = len(n_seq_b)
+        sb = (ctypes.c_int32 * batch)(*[int(x) for x in n_seq_b])
+        rb = (ctypes.c_int32 * batch)(*[int(x) for x in n_res_b])
+    _check(lib().evo_stack_fwd(ctypes.byref(cd), n_blocks, batch, sb, rb, _ptr(params), _ptr(params_bf16),
+                               param_stride, _ptr(m), _ptr(z), _ptr(msa_mask), _ptr(pair_mask), _ptr(ws),
+                               ws.numel() * ws.element_size(), _stream(stream)), "evo_stack_fwd")
 
 
 def adam_hyper(step, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-6, clip_norm=0.1, ema_decay=0.999):
@@ -388,9 +398,9 @@ def _torch_dtype(act_dtype):
     return torch.bfloat16 if act_dtype == EVO_BF16 else torch.float32
 
 
-def workspace(cd, mode, device):
+def workspace(cd, mode, device, batch=1):
     import torch
-    return torch.empty(workspace_size(cd, mode), dtype=torch.uint8, device=device)
+    return torch.empty(workspace_size(cd, mode, batch), dtype=torch.uint8, device=device)
 
 
 def bf16_params(cd, params):

@@ -82,7 +82,7 @@ def test_pair_workspace_is_the_pair_share_of_the_block(built_lib):
     assert evo.lib().evo_pair_workspace_size(ctypes.byref(cd), evo.EVO_MODE_BWD, ctypes.byref(n)) == evo.EVO_OK
     full = ctypes.c_size_t(0)
     cdf = evo.cdims(d.replace(pair_only=0, n_seq=8), evo.EVO_BF16)
-    assert evo.lib().evo_workspace_size(ctypes.byref(cdf), evo.EVO_MODE_BWD, ctypes.byref(full)) == evo.EVO_OK
+    assert evo.lib().evo_workspace_size(ctypes.byref(cdf), 1, evo.EVO_MODE_BWD, ctypes.byref(full)) == evo.EVO_OK
     assert 0 < n.value < full.value
 
 
@@ -92,14 +92,37 @@ def test_stack_stride_and_count_are_checked_before_any_launch(built_lib):
     null = ctypes.c_void_p(0)
     n = evo.param_count(cd)
     stride = (n + 127) // 128 * 128
+
+    def call(nb, batch, st, sb=None, rb=None, ws=0):
+        return L.evo_stack_fwd(ctypes.byref(cd), nb, batch, sb, rb, null, null, ctypes.c_size_t(st), null, null, null,
+                               null, null, ctypes.c_size_t(ws), null)
+
     for nb, st in ((2, stride + 64), (2, stride - 128), (-1, stride)):
-        r = L.evo_stack_fwd(ctypes.byref(cd), nb, null, null, ctypes.c_size_t(st), null, null, null, null, null,
-                            ctypes.c_size_t(0), null)
-        assert r == evo.EVO_ERR_INVALID_ARG, (nb, st)
+        assert call(nb, 1, st) == evo.EVO_ERR_INVALID_ARG, (nb, st)
     # zero blocks is the identity and launches nothing
-    r = L.evo_stack_fwd(ctypes.byref(cd), 0, null, null, ctypes.c_size_t(stride), null, null, null, null, null,
-                        ctypes.c_size_t(0), null)
-    assert r == evo.EVO_OK
+    assert call(0, 1, stride) == evo.EVO_OK
+    # batch sizes: a batch needs its size arrays; sizes within the padded ones;
+    # a batch of one is the padded protein itself
+    arr = lambda *v: (ctypes.c_int32 * len(v))(*v)
+    assert call(2, 0, stride) == evo.EVO_ERR_INVALID_ARG
+    assert call(2, 2, stride) == evo.EVO_ERR_INVALID_ARG
+    assert call(2, 2, stride, arr(16, 17), arr(64, 64)) == evo.EVO_ERR_INVALID_ARG
+    assert call(2, 2, stride, arr(16, 8), arr(0, 64)) == evo.EVO_ERR_INVALID_ARG
+    assert call(2, 1, stride, arr(8), arr(64)) == evo.EVO_ERR_INVALID_ARG
+
+
+def test_stack_workspace_adds_one_staged_protein_for_a_batch(built_lib):
+    d = synth.DIMS_SMALL_FP32
+    cd = evo.cdims(d, evo.EVO_BF16)
+    one = evo.workspace_size(cd, evo.EVO_MODE_FWD)
+    two = evo.workspace_size(cd, evo.EVO_MODE_FWD, batch=2)
+    assert evo.workspace_size(cd, evo.EVO_MODE_FWD, batch=16) == two
+    al = lambda x: (x + 255) // 256 * 256
+    S, R = d.n_seq, d.n_res
+    staging = al(S * R * d.c_m * 2) + al(R * R * d.c_z * 2) + al(S * R * 4) + al(R * R * 4)
+    assert two == one + staging
+    with pytest.raises(evo.EvoError):
+        evo.workspace_size(cd, evo.EVO_MODE_FWD, batch=0)
 
 
 def test_adam_step_arguments_are_checked_before_any_launch(built_lib):
