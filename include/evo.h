@@ -68,6 +68,17 @@ typedef struct evo_dims {
   int32_t c_mul, c_opm, trans_n;
   int32_t msa_col_mode; /* EVO_COL_ATTENTION | EVO_COL_GLOBAL */
   int32_t act_dtype;    /* EVO_F32 | EVO_BF16: storage of m, z, intermediates */
+  /* i-slab subbatching of the pair stack (Sec. 3.4.4), read by the inference
+   * plan only (evo_block_fwd_infer, evo_block_fwd_noalloc and their
+   * evo_workspace_size): 0 (or >= n_res) runs every pair step on the whole
+   * n_res x n_res grid; 0 < pair_slab < n_res runs it pair_slab rows at a
+   * time, so that the pair-sized scratch shrinks by n_res / pair_slab and
+   * what stays full-size is z (two buffers), its transpose, the b operand of
+   * a triangle product and the pair biases.  The result is the unsliced
+   * forward's, bit for bit.  Requires EVO_BF16, c_z = 128, h_msa and h_tri
+   * 4 or 8 and c_mul 64, 128 or 256 (EVO_ERR_UNSUPPORTED otherwise);
+   * negative: EVO_ERR_INVALID_ARG. */
+  int32_t pair_slab;
 } evo_dims;
 
 typedef struct evo_param_entry {
@@ -121,8 +132,10 @@ int evo_block_fwd(const evo_dims *d, const float *params, const void *params_bf1
  * instead of 15 KB).  It carries the paper's memory read/write in-place
  * (Sec. 3.4.3: one allocation reused instead of one per intermediate) across
  * the block's sub-modules, which lets one GPU run a block on sequences of
- * several thousand residues without the subbatching of Sec. 3.4.4.
- * Evaluation mode only. */
+ * several thousand residues without subbatching; with d->pair_slab set it
+ * also subbatches the pair stack (Sec. 3.4.4), which takes the workspace
+ * from about 3.3 KB to about 1.35 KB per pair position at the paper's dims
+ * (N_seq 128, N_res 4096, slabs of 1/8 of the rows).  Evaluation mode only. */
 int evo_block_fwd_infer(const evo_dims *d, const float *params, const void *params_bf16,
                         const void *m_in, const void *z_in, void *m_out, void *z_out,
                         const float *msa_mask, const float *pair_mask,

@@ -62,7 +62,7 @@ size_t staging_bytes(const evo_dims &d) {
 int evo_workspace_size(const evo_dims *d, int batch, int mode, size_t *bytes) {
   if (!bytes || batch < 1 || (mode != EVO_MODE_FWD && mode != EVO_MODE_BWD && mode != EVO_MODE_INFER))
     return EVO_ERR_INVALID_ARG;
-  const int v = validate_dims(d);
+  const int v = mode == EVO_MODE_INFER ? validate_infer_dims(d) : validate_dims(d);
   if (v != EVO_OK) return v;
   *bytes = workspace_bytes(*d, mode) + (batch > 1 ? staging_bytes(*d) : 0);
   return EVO_OK;
@@ -113,7 +113,7 @@ int evo_block_fwd_dropout(const evo_dims *d, const float *params, const void *pa
 int evo_block_fwd_infer(const evo_dims *d, const float *params, const void *params_bf16, const void *m_in,
                         const void *z_in, void *m_out, void *z_out, const float *msa_mask, const float *pair_mask,
                         void *workspace, size_t ws_bytes, evo_stream_t stream) {
-  const int v = validate_dims(d);
+  const int v = validate_infer_dims(d);
   if (v != EVO_OK) return v;
   const bool bf = d->act_dtype == EVO_BF16;
   if (!params || !m_in || !z_in || !m_out || !z_out || !msa_mask || !pair_mask || !workspace || (bf && !params_bf16))

@@ -117,6 +117,20 @@ int validate_dims(const evo_dims *d) {
   if (d->msa_col_mode == EVO_COL_GLOBAL &&
       (!global_attn_supported(d->h_msa, d->c_msa) || (int64_t)d->n_seq * d->h_msa * 4 > 200 * 1024))
     return EVO_ERR_UNSUPPORTED;
+  if (d->pair_slab < 0) return EVO_ERR_INVALID_ARG;
+  return EVO_OK;
+}
+
+bool pair_slabbed(const evo_dims &d) { return d.pair_slab > 0 && d.pair_slab < d.n_res; }
+
+int validate_infer_dims(const evo_dims *d) {
+  const int v = validate_dims(d);
+  if (v != EVO_OK || !pair_slabbed(*d)) return v;
+  // the slab steps run on the BF16 TMA kernels only (pair bias projection
+  // with c_z = 128 and 4 or 8 heads, channel-major gate and LayerNorm)
+  const bool heads = (d->h_msa == 4 || d->h_msa == 8) && (d->h_tri == 4 || d->h_tri == 8);
+  if (d->act_dtype != EVO_BF16 || d->c_z != 128 || !heads || (d->c_mul != 64 && d->c_mul != 128 && d->c_mul != 256))
+    return EVO_ERR_UNSUPPORTED;
   return EVO_OK;
 }
 
@@ -144,6 +158,18 @@ struct Plan {
   size_t dm_acc, dmT, dz_acc, dzT, G1, G2, G3, dO4, dA, dB, dX, dq_acc, dbias, Dsum, dab4, split;
   size_t drop_u;  // training-mode dropout: the update before its scale (forward), the scaled gradient (backward)
   int64_t wmax = 0;  // split holds MAXSPLIT * wmax floats
+  // i-slab subbatching of the inference plan (d.pair_slab rows per slab)
+  struct Slab {
+    bool on = false;
+    int64_t Ri = 0;                   // pair rows per slab
+    size_t xz1, O4;                   // row-attention pair LayerNorm, outer products (one slab)
+    size_t zT, pmT;                   // full-size: transposed z and pair mask (incoming, ending)
+    size_t Bfull;                     // full-size: channel-major b of a triangle product
+    size_t xz, abg, A, X, xo, y;      // triangle multiplication (one slab)
+    size_t tbias;                     // full-size: triangle attention pair bias
+    size_t axz, qkvg, oatt, og, lse;  // triangle attention (one slab)
+    size_t txz, h;                    // pair transition (one slab)
+  } sl;
   size_t total;
 };
 
@@ -190,6 +216,46 @@ size_t make_infer_plan(const evo_dims &d, Plan &p, bool pair_only) {
   p.drop_u = scr;  // evaluation only: no dropout
   auto begin = [&] { off = scr; };
   auto end = [&] { top = std::max(top, off); };
+  if (!pair_only && pair_slabbed(d)) {
+    // i-slab subbatching (Sec. 3.4.4): every pair-sized intermediate lives for
+    // one slab of Ri pair rows only; what stays full-size is z (two buffers),
+    // the channel-major b of a triangle product, the transposed z and pair
+    // mask of the incoming / ending steps and the pair biases
+    Plan::Slab &sl = p.sl;
+    sl.on = true;
+    sl.Ri = d.pair_slab;
+    const int64_t Ps = sl.Ri * k.R;  // positions of a slab
+    begin();  // 1. MSA row attention (the pair bias from LayerNorm(z) slab by slab)
+    p.xm1 = T(k.Mm * k.Cm), sl.xz1 = T(Ps * k.Cz), p.bias1 = F(k.Hm * k.Mz), p.qkvg1 = T(k.Mm * k.QKm);
+    p.oatt1 = T(k.Mm * k.HCm), p.og1 = T(k.Mm * k.HCm), p.lse1 = F(k.S * k.Hm * k.R);
+    end();
+    begin();  // 2. MSA column attention (or global column attention)
+    p.xm2 = T(k.Mm * k.Cm), p.qkvg2 = T(k.Mm * k.QKc), p.oatt2 = T(k.Mm * k.HCm), p.og2 = T(k.Mm * k.HCm);
+    p.lse2 = F(k.R * k.Hm * k.S), p.gq = F(k.R * k.HCm), p.gob = F(k.R * k.HCm), p.gst = F(k.R * k.Hm * 2);
+    end();
+    begin();  // 3. MSA transition
+    p.xm3 = T(k.Mm * k.Cm), p.h3 = T(k.Mm * k.n * k.Cm);
+    end();
+    begin();  // 4. outer product mean: the outer products of one slab of rows i
+    p.xm4 = T(k.Mm * k.Cm), p.ab4 = T(2 * k.Mm * k.co), p.inv4 = F(k.Mz), sl.O4 = T(Ps * k.co * k.co);
+    end();
+    begin();  // 5-9: the transposed z and mask live through the four triangle steps
+    sl.zT = T(k.Mz * k.Cz), sl.pmT = F(k.Mz);
+    const size_t pair = off;
+    sl.Bfull = T(k.cmul * k.R * k.Rp);  // 5, 6. triangle multiplications
+    sl.xz = T(Ps * k.Cz), sl.abg = T(Ps * k.ABG), sl.A = T(k.cmul * sl.Ri * k.Rp), sl.X = T(k.cmul * sl.Ri * k.Rp);
+    sl.xo = T(Ps * k.cmul), sl.y = T(Ps * k.Cz);
+    end();
+    off = pair;  // 7, 8. triangle attentions
+    sl.tbias = T(k.Ht * k.Mz), sl.axz = T(Ps * k.Cz), sl.qkvg = T(Ps * 4 * k.HCt), sl.oatt = T(Ps * k.HCt);
+    sl.og = T(Ps * k.HCt), sl.lse = F(sl.Ri * k.Ht * k.R);
+    end();
+    begin();  // 9. pair transition
+    sl.txz = T(Ps * k.Cz), sl.h = T(Ps * k.n * k.Cz);
+    end();
+    p.total = top;
+    return top;
+  }
   begin();  // 1. MSA row attention
   p.xm1 = T(k.Mm * k.Cm), p.xz1 = T(k.Mz * k.Cz), p.bias1 = F(k.Hm * k.Mz), p.qkvg1 = T(k.Mm * k.QKm);
   p.oatt1 = T(k.Mm * k.HCm), p.og1 = T(k.Mm * k.HCm), p.lse1 = F(k.S * k.Hm * k.R);
@@ -482,8 +548,17 @@ struct Drv {
     const int64_t S = k.S, R = k.R, Cm = k.Cm, Cz = k.Cz, Mm = k.Mm, Mz = k.Mz, HCm = k.HCm, HCt = k.HCt;
     // 1. MSA row attention with pair bias (AF2 Alg. 7)
     ln(m0, "row.ln_m", B(pl.xm1), Mm, (int)Cm);
-    ln(z0, "row.ln_z", B(pl.xz1), Mz, (int)Cz);
-    ck(head_proj_fwd(B(pl.xz1), P("row.w_b"), Bf(pl.bias1), (int)R, (int)Cz, (int)k.Hm, 0, bf, s));
+    if (pl.sl.on) {
+      // the pair bias of the row attention, one i-slab of LayerNorm(z) at a time
+      slabs([&](int64_t i0, int64_t ri) {
+        ln(at(z0, i0 * R * Cz), "row.ln_z", B(pl.sl.xz1), ri * R, (int)Cz);
+        ck(head_proj_fwd_rows(B(pl.sl.xz1), P("row.w_b"), at(B(pl.bias1), i0 * R), ri * R, Mz, (int)Cz, (int)k.Hm,
+                              s));
+      });
+    } else {
+      ln(z0, "row.ln_z", B(pl.xz1), Mz, (int)Cz);
+      ck(head_proj_fwd(B(pl.xz1), P("row.w_b"), Bf(pl.bias1), (int)R, (int)Cz, (int)k.Hm, 0, bf, s));
+    }
     {
       GemmOp g = mk(Mm, k.QKm, Cm, B(pl.xm1), Cm, 0, W("row.w_qkvg"), Cm, 0, B(pl.qkvg1), k.QKm);
       g.e.bias = P("row.b_g"), g.e.bias_n0 = (int)(3 * HCm), g.e.act = ACT_SIGMOID, g.e.act_n0 = (int)(3 * HCm);
@@ -525,15 +600,23 @@ struct Drv {
       g.e.bias = P("opm.b_ab"), g.e.row_scale = mm;
       gemm(g);
       ck(opm_inv_norm(mm, Bf(pl.inv4), (int)S, (int)R, 1e-3f, s));
-      GemmOp o = mk(R * co, R * co, S, B(pl.ab4), R * co, 1, at(B(pl.ab4), Mm * co), R * co, 1, B(pl.O4), 0);
-      o.e.map = OutMap{co, R * co * co, co, co, co * co, 1};  // O[i][j][c*co + d]
-      o.cls = "opm_outer";
-      gemm(o);
-      GemmOp p = mk(Mz, Cz, co * co, B(pl.O4), co * co, 0, W("opm.w_o"), co * co, 0, B(pl.z1), Cz);
-      p.e.bias = P("opm.b_o"), p.e.row_scale = Bf(pl.inv4), p.e.residual = z0;
-      gemm(p);
+      // the outer products and their projection, for all rows i at once or
+      // one i-slab at a time (the slab's a rows against every b row)
+      auto outer = [&](int64_t i0, int64_t ri, size_t O4) {
+        GemmOp o = mk(ri * co, R * co, S, at(B(pl.ab4), i0 * co), R * co, 1, at(B(pl.ab4), Mm * co), R * co, 1,
+                      B(O4), 0);
+        o.e.map = OutMap{co, R * co * co, co, co, co * co, 1};  // O[i][j][c*co + d]
+        o.cls = "opm_outer";
+        gemm(o);
+        GemmOp p = mk(ri * R, Cz, co * co, B(O4), co * co, 0, W("opm.w_o"), co * co, 0, at(B(pl.z1), i0 * R * Cz), Cz);
+        p.e.bias = P("opm.b_o"), p.e.row_scale = Bf(pl.inv4) + i0 * R, p.e.residual = at(z0, i0 * R * Cz);
+        gemm(p);
+      };
+      if (pl.sl.on) slabs([&](int64_t i0, int64_t ri) { outer(i0, ri, pl.sl.O4); });
+      else outer(0, R, pl.O4);
     }
-    pair_forward(B(pl.z1), z_out, pm);
+    if (pl.sl.on) pair_forward_slabbed(z_out, pm);
+    else pair_forward(B(pl.z1), z_out, pm);
     (void)HCt;
   }
 
@@ -549,6 +632,124 @@ struct Drv {
     // 9. pair transition (AF2 Alg. 15)
     void *z6 = z_out ? z_out : B(pl.z6);
     transition_fwd("pair_trans", B(pl.att[1].zout), B(pl.xz9), B(pl.h9), z6, k.Mz, k.Cz);
+  }
+
+  // ---------------- i-slab subbatching of steps 5-9 (Sec. 3.4.4), inference plan
+  // Every pair step works on Ri rows of the pair grid at a time.  Outgoing
+  // multiplication, starting attention and the transition need, for a row i,
+  // only what is computed from row i plus a full-size operand built in a
+  // first pass over the slabs (the b side of the triangle product, the pair
+  // bias of the attention).  Incoming multiplication and ending attention are
+  // the outgoing / starting forms on the transposed grid: with z'[i][j] =
+  // z[j][i] and the a and b projections swapped, the outgoing product on z'
+  // at (i, j) is the incoming one on z at (j, i), and the starting attention
+  // on z' (mask and bias transposed with it) is the ending attention on z;
+  // their outputs go back through a transposed output map.
+  template <class Fn>
+  void slabs(Fn f) {
+    for (int64_t i0 = 0; i0 < k.R; i0 += pl.sl.Ri) f(i0, std::min(pl.sl.Ri, k.R - i0));
+  }
+  // The output projection of a slab: written in place through the row-major
+  // map, or (transposed grid) into a slab-sized buffer and then put back into
+  // the columns i0 .. i0 + ri of z, so that both take the same epilogue.  The
+  // residual is the source grid's own rows either way (z'[i][j] = z[j][i]).
+  void slab_project(GemmOp o, const void *src, void *out, void *tmp, bool transposed, int64_t i0, int64_t ri) {
+    const int64_t R = k.R, Cz = k.Cz;
+    o.e.residual = at(src, i0 * R * Cz);
+    o.e.C = transposed ? tmp : at(out, i0 * R * Cz);
+    gemm(o);
+    if (transposed) ck(transpose_rows(tmp, at(out, i0 * Cz), ri, R, (int)(Cz * ts / 4), R, s));
+  }
+
+  void pair_forward_slabbed(void *z_out, const float *pm) {
+    const Plan::Slab &sl = pl.sl;
+    const int64_t R = k.R;
+    const int W = (int)(k.Cz * ts / 4);
+    void *za = B(pl.z1), *zb = B(pl.tri[0].zout);
+    // 5. outgoing: z1 -> zb
+    trimul_fwd_slabbed(0, za, pm, zb, false);
+    // 6. incoming, on the transposed grid: zb -> z1
+    ck(transpose_rows(zb, B(sl.zT), R, R, W, R, s));
+    ck(transpose_rows(pm, Bf(sl.pmT), R, R, 1, R, s));
+    trimul_fwd_slabbed(1, B(sl.zT), Bf(sl.pmT), za, true);
+    // 7. starting node: z1 -> zb
+    triatt_fwd_slabbed(0, za, pm, zb, false);
+    // 8. ending node, as starting on the transposed grid: zb -> z1
+    ck(transpose_rows(zb, B(sl.zT), R, R, W, R, s));
+    triatt_fwd_slabbed(1, B(sl.zT), Bf(sl.pmT), za, true);
+    // 9. pair transition: z1 -> z_out (or zb)
+    void *z6 = z_out ? z_out : B(pl.z6);
+    slabs([&](int64_t i0, int64_t ri) {
+      const int64_t o = i0 * R * k.Cz;
+      transition_fwd("pair_trans", at(za, o), B(sl.txz), B(sl.h), at(z6, o), ri * R, k.Cz);
+    });
+  }
+
+  // src: the grid the step reads row by row (z, or its transpose) with its
+  // mask msk; out: the step's output, addressed as z.
+  void trimul_fwd_slabbed(int t, const void *src, const float *msk, void *out, bool transposed) {
+    const std::string pre = t == 0 ? "tri_out" : "tri_in";
+    const Plan::Slab &sl = pl.sl;
+    const int64_t R = k.R, Rp = k.Rp, Cz = k.Cz, cmul = k.cmul, ABG = k.ABG;
+    const int swap = transposed ? 1 : 0;
+    // First pass: the b side of every row into the full-size channel-major
+    // Bfull, from the b half of w_abg alone (columns [2 cmul, 4 cmul); the a
+    // half [0, 2 cmul) when swapped).  The gate kernel also writes an a from
+    // the stale other half of abg into the slab's A: discarded.
+    const int64_t cb = swap ? 0 : 2 * cmul;
+    slabs([&](int64_t i0, int64_t ri) {
+      ln(at(src, i0 * R * Cz), pre + ".ln_in", B(sl.xz), ri * R, (int)Cz);
+      GemmOp g = mk(ri * R, 2 * cmul, Cz, B(sl.xz), Cz, 0, at(W(pre + ".w_abg"), cb * Cz), Cz, 0,
+                    at(B(sl.abg), cb), ABG);
+      g.e.bias = P(pre + ".b_abg") + cb;
+      gemm(g);
+      ck(trimul_gate_fwd_rows(B(sl.abg), ABG, msk + i0 * R, B(sl.A), ri * Rp, at(B(sl.Bfull), i0 * Rp), R * Rp, Rp,
+                              (int)ri, (int)R, (int)cmul, swap, s));
+    });
+    // Second pass: a of the slab (its b goes to the X buffer, overwritten
+    // next), the product against every row of b, LayerNorm, projection.
+    slabs([&](int64_t i0, int64_t ri) {
+      ln(at(src, i0 * R * Cz), pre + ".ln_in", B(sl.xz), ri * R, (int)Cz);
+      GemmOp g = mk(ri * R, ABG, Cz, B(sl.xz), Cz, 0, W(pre + ".w_abg"), Cz, 0, B(sl.abg), ABG);
+      g.e.bias = P(pre + ".b_abg");
+      g.e.act = ACT_SIGMOID, g.e.act_n0 = (int)(4 * cmul);  // the output gate g
+      gemm(g);
+      ck(trimul_gate_fwd_rows(B(sl.abg), ABG, msk + i0 * R, B(sl.A), ri * Rp, B(sl.X), ri * Rp, Rp, (int)ri, (int)R,
+                              (int)cmul, swap, s));
+      GemmOp x = mk(ri, R, R, B(sl.A), Rp, 0, B(sl.Bfull), Rp, 0, B(sl.X), Rp);
+      x.batch = (int)cmul, x.a_bs = ri * Rp, x.b_bs = R * Rp, x.e.c_bstride = ri * Rp;
+      x.cls = "tri_einsum";
+      gemm(x);
+      ck(ln_fwd_cm_rows(B(sl.X), Rp, ri * Rp, P(pre + ".ln_out.gamma"), P(pre + ".ln_out.beta"), B(sl.xo), (int)ri,
+                        (int)R, (int)cmul, s));
+      GemmOp o = mk(ri * R, Cz, cmul, B(sl.xo), cmul, 0, W(pre + ".w_o"), cmul, 0, nullptr, Cz);
+      o.e.bias = P(pre + ".b_o");
+      o.e.gate = at(B(sl.abg), 4 * cmul), o.e.gate_ld = ABG;
+      slab_project(o, src, out, B(sl.y), transposed, i0, ri);
+    });
+  }
+
+  void triatt_fwd_slabbed(int t, const void *src, const float *msk, void *out, bool transposed) {
+    const std::string pre = t == 0 ? "att_start" : "att_end";
+    const Plan::Slab &sl = pl.sl;
+    const int64_t R = k.R, Cz = k.Cz, Mz = k.Mz, HCt = k.HCt;
+    // first pass: the pair bias b[h][j][k] of every row (starting form on src)
+    slabs([&](int64_t i0, int64_t ri) {
+      ln(at(src, i0 * R * Cz), pre + ".ln", B(sl.axz), ri * R, (int)Cz);
+      ck(head_proj_fwd_rows(B(sl.axz), P(pre + ".w_b"), at(B(sl.tbias), i0 * R), ri * R, Mz, (int)Cz, (int)k.Ht, s));
+    });
+    slabs([&](int64_t i0, int64_t ri) {
+      ln(at(src, i0 * R * Cz), pre + ".ln", B(sl.axz), ri * R, (int)Cz);
+      GemmOp g = mk(ri * R, 4 * HCt, Cz, B(sl.axz), Cz, 0, W(pre + ".w_qkvg"), Cz, 0, B(sl.qkvg), 4 * HCt);
+      g.e.bias = P(pre + ".b_g"), g.e.bias_n0 = (int)(3 * HCt), g.e.act = ACT_SIGMOID, g.e.act_n0 = (int)(3 * HCt);
+      gemm(g);
+      AttnArgs a = attn_args(2, B(sl.qkvg), B(sl.oatt), B(sl.og), Bf(sl.lse), Bf(sl.tbias), msk + i0 * R);
+      a.B1 = (int)ri;
+      ck(attn_fwd(a, bf, s));
+      GemmOp o = mk(ri * R, Cz, HCt, B(sl.og), HCt, 0, W(pre + ".w_o"), HCt, 0, nullptr, Cz);
+      o.e.bias = P(pre + ".b_o");
+      slab_project(o, src, out, B(sl.axz), transposed, i0, ri);  // the LayerNorm output is dead here
+    });
   }
 
   void transition_fwd(const std::string &pre, const void *x, void *xn, void *h, void *out, int64_t M, int64_t C) {

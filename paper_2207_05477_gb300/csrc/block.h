@@ -23,6 +23,10 @@ int64_t build_param_table(const evo_dims &d, std::vector<PEntry> &out, bool pair
 // checks only the pair-stack fields).
 int validate_dims(const evo_dims *d);
 int validate_pair_dims(const evo_dims *d);
+// validate_dims plus the requirements of the i-slab inference plan
+// (d->pair_slab set): what evo_block_fwd_infer and its workspace size check.
+int validate_infer_dims(const evo_dims *d);
+bool pair_slabbed(const evo_dims &d);
 
 // Workspace bytes of the forward (EVO_MODE_FWD), the backward (EVO_MODE_BWD)
 // or the forward-only inference plan (EVO_MODE_INFER).

@@ -159,6 +159,11 @@ cudaError_t reduce_splits_map(const float *part, int splits, int M, int N, const
 // attention kernels read the bias as an activation), else fp32.
 cudaError_t head_proj_fwd(const void *x, const float *w, void *out, int R, int C, int H, int transpose,
                           int use_bf16, cudaStream_t s);
+// The pair-bias projection of npos consecutive positions (the rows of an
+// i-slab, not transposed) into out[h * hstride + pos]; BF16, C = 128, H = 4
+// or 8 only (cudaErrorNotSupported otherwise, nothing launched).
+cudaError_t head_proj_fwd_rows(const void *x, const float *w, void *out, int64_t npos, int64_t hstride, int C, int H,
+                               cudaStream_t s);
 // dx[pos] (+)= sum_h dbias[h][pos'] w[h]; dw += sum_pos dbias x (each block adds
 // its sum over a range of positions with fp32 atomics).
 cudaError_t head_proj_bwd(const float *dbias, const void *x, const float *w, void *dx, int accumulate,
@@ -177,6 +182,13 @@ bool trimul_gate_tma_supported(const void *abg, int64_t ld, const void *A, const
                                int cm);
 cudaError_t trimul_gate_fwd_tma_launch(const void *abg, int64_t ld, const float *mask, void *A, void *B, int64_t pitch,
                                        int R, int cm, int incoming, cudaStream_t s);
+// The outgoing gate of `rows` pair rows (an i-slab): abg [rows * R, ld], mask
+// [rows][R] (the slab's rows), A and B channel-major [c][rows][pitch] at
+// channel strides a_cstride / b_cstride (B may be the slab's rows of a full
+// [c][R][pitch] buffer); swap: a from (bp, bg) and b from (ap, ag).  BF16 TMA
+// kernel only (cudaErrorNotSupported when it does not apply).
+cudaError_t trimul_gate_fwd_rows(const void *abg, int64_t ld, const float *mask, void *A, int64_t a_cstride, void *B,
+                                 int64_t b_cstride, int64_t pitch, int rows, int R, int cm, int swap, cudaStream_t s);
 cudaError_t trimul_gate_bwd_tma_launch(const void *dA, const void *dB, int64_t pitch, const void *abg, int64_t ld,
                                        const float *mask, void *dabg, int R, int cm, int incoming, cudaStream_t s);
 // TMA-tiled BF16 versions of ln_fwd_cm / ln_bwd_cm (C = 64, 128 or 256);
@@ -184,6 +196,10 @@ cudaError_t trimul_gate_bwd_tma_launch(const void *dA, const void *dB, int64_t p
 bool ln_cm_tma_supported(const void *x, int64_t pitch, const void *y, int R, int C);
 cudaError_t ln_fwd_cm_tma_launch(const void *x, int64_t pitch, const float *gamma, const float *beta, void *y, int R,
                                  int C, cudaStream_t s);
+// The same for `rows` pair rows of R columns: x [C][rows][pitch] at channel
+// stride cstride, y [rows * R, C] (BF16 TMA kernel only).
+cudaError_t ln_fwd_cm_rows(const void *x, int64_t pitch, int64_t cstride, const float *gamma, const float *beta,
+                           void *y, int rows, int R, int C, cudaStream_t s);
 cudaError_t ln_bwd_cm_tma_launch(const void *dy, const void *x, int64_t pitch, const float *gamma, void *dx, int R,
                                  int C, float *dgamma, float *dbeta, cudaStream_t s);
 // Reads and clears the error word of the TMA gate kernels; synchronous.
@@ -218,6 +234,10 @@ cudaError_t row_scale(const void *x, const float *scale, void *y, int64_t M, int
 cudaError_t to_f32(const void *src, float *dst, int64_t n, int use_bf16, cudaStream_t s);
 cudaError_t from_f32(const float *src, void *dst, int64_t n, int use_bf16, cudaStream_t s);
 cudaError_t f32_to_bf16(const float *src, bf16 *dst, int64_t n, cudaStream_t s);
+// dst[b * dst_ld + a][.] = src[a * Bd + b][.] over an A x Bd grid of rows of
+// W 32-bit words (the pair grid transposed: A = Bd = dst_ld = R; a slab of A
+// rows put back into the columns of an R x R grid: Bd = dst_ld = R).
+cudaError_t transpose_rows(const void *src, void *dst, int64_t A, int64_t Bd, int W, int64_t dst_ld, cudaStream_t s);
 // Copies A x B rows of W 32-bit words between row-major [.][src_B][W] and
 // [.][dst_B][W] layouts (the staging of a padded protein).
 cudaError_t copy_rows_strided(const void *src, void *dst, int64_t A, int64_t B, int64_t src_B, int64_t dst_B, int W,

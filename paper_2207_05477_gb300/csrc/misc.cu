@@ -308,7 +308,7 @@ __device__ __forceinline__ int head_of_lane(int lane, bool &writer) {
 // reduced over the group (head_reduce).  Grid-stride over warp-steps.
 template <int H, int C, int CPL, int U>
 __global__ void __launch_bounds__(256) head_proj_fwd_w(const bf16 *x, const float *w, bf16 *out, int R,
-                                                       int transpose) {
+                                                       int transpose, int64_t P, int64_t hstride) {
   pdl_entry();
   constexpr int TPR = C / CPL, PPW = 32 / TPR;
   const int lane = threadIdx.x & 31;
@@ -320,7 +320,7 @@ __global__ void __launch_bounds__(256) head_proj_fwd_w(const bf16 *x, const floa
     for (int k = 0; k < CPL; ++k) wl[h][k] = w[h * C + sub * CPL + k];
   bool writer;
   const int hsel = head_of_lane<H, TPR>(lane, writer);
-  const int64_t P = (int64_t)R * R;
+  // P positions from x (all R * R, or the rows of an i-slab), head h at out + h * hstride
   const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
   const int64_t w0 = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   for (int64_t base = w0 * (PPW * U); base < P; base += nwarps * (PPW * U)) {
@@ -351,7 +351,7 @@ __global__ void __launch_bounds__(256) head_proj_fwd_w(const bf16 *x, const floa
         int j;
         divmod(p, R, i, j);
         const int64_t pp = transpose ? (int64_t)j * R + i : p;
-        out[hsel * P + pp] = __float2bfloat16_rn(r);
+        out[hsel * hstride + pp] = __float2bfloat16_rn(r);
       }
     }
   }
@@ -1208,8 +1208,8 @@ cudaError_t head_proj_fwd(const void *x, const float *w, void *out, int R, int C
     constexpr int U = 4;
     const int64_t steps = (P + 2 * U - 1) / (2 * U);  // warp-steps (two positions each)
     const unsigned blocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>((steps + 7) / 8, 152 * 3));
-    if (H == 4) launch_k(head_proj_fwd_w<4, 128, 8, U>, blocks, 256, 0, s, (const bf16 *)x, w, (bf16 *)out, R, transpose);
-    else launch_k(head_proj_fwd_w<8, 128, 8, U>, blocks, 256, 0, s, (const bf16 *)x, w, (bf16 *)out, R, transpose);
+    if (H == 4) launch_k(head_proj_fwd_w<4, 128, 8, U>, blocks, 256, 0, s, (const bf16 *)x, w, (bf16 *)out, R, transpose, P, P);
+    else launch_k(head_proj_fwd_w<8, 128, 8, U>, blocks, 256, 0, s, (const bf16 *)x, w, (bf16 *)out, R, transpose, P, P);
   } else if (use_bf16 && C % 8 == 0 && (((uintptr_t)x) & 15u) == 0 && (H == 4 || H == 8)) {
     const size_t sm = (size_t)H * C * sizeof(float);
     if (H == 4) launch_k(head_proj_fwd_v8<4, bf16>, nblk(P, 128), 128, sm, s, (const bf16 *)x, w, (bf16 *)out, R, C, transpose);
@@ -1220,6 +1220,19 @@ cudaError_t head_proj_fwd(const void *x, const float *w, void *out, int R, int C
     launch_k(head_proj_fwd_k<float, float>, nblk(P, 8), 256, 0, s, (const float *)x, w, (float *)out, R, C, H,
              transpose);
   }
+  return cudaGetLastError();
+}
+
+cudaError_t head_proj_fwd_rows(const void *x, const float *w, void *out, int64_t npos, int64_t hstride, int C, int H,
+                               cudaStream_t s) {
+  Prof prof("head_proj_fwd", s, 2.0 * npos * C * H, 2.0 * npos * C + 2.0 * H * npos, 1);
+  if (C != 128 || (H != 4 && H != 8) || (((uintptr_t)x) & 15u)) return cudaErrorNotSupported;
+  if (npos <= 0) return cudaSuccess;
+  constexpr int U = 4;
+  const int64_t steps = (npos + 2 * U - 1) / (2 * U);
+  const unsigned blocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>((steps + 7) / 8, 152 * 3));
+  if (H == 4) launch_k(head_proj_fwd_w<4, 128, 8, U>, blocks, 256, 0, s, (const bf16 *)x, w, (bf16 *)out, 1, 0, npos, hstride);
+  else launch_k(head_proj_fwd_w<8, 128, 8, U>, blocks, 256, 0, s, (const bf16 *)x, w, (bf16 *)out, 1, 0, npos, hstride);
   return cudaGetLastError();
 }
 
@@ -1411,6 +1424,35 @@ __global__ void __launch_bounds__(256) copy_rows_k(const uint32_t *src, uint32_t
   }
 }
 }  // namespace
+
+namespace {
+// dst[(b * dst_ld + a) * W + w] = src[(a * Bd + b) * W + w]: rows of W words
+// on an A x Bd grid, transposed, one row per warp step (a row's reads and its
+// write each one contiguous run of W words).
+__global__ void __launch_bounds__(256) transpose_rows_k(const uint32_t *src, uint32_t *dst, int64_t A, int64_t Bd,
+                                                        int W, int64_t dst_ld) {
+  pdl_entry();
+  const int64_t rows = A * Bd;
+  const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  for (int64_t r = wid; r < rows; r += nw) {
+    const int64_t a = r / Bd, b = r - a * Bd;
+    const uint32_t *sp = src + r * W;
+    uint32_t *dp = dst + (b * dst_ld + a) * W;
+    for (int w = lane; w < W; w += 32) dp[w] = sp[w];
+  }
+}
+}  // namespace
+
+cudaError_t transpose_rows(const void *src, void *dst, int64_t A, int64_t Bd, int W, int64_t dst_ld, cudaStream_t s) {
+  if (A <= 0 || Bd <= 0 || W <= 0) return cudaSuccess;
+  if (dst_ld < A) return cudaErrorInvalidValue;
+  Prof prof("transpose_rows", s, 0, 8.0 * A * Bd * W);
+  const unsigned grid = (unsigned)std::min<int64_t>((A * Bd + 7) / 8, 152 * 16);
+  launch_k(transpose_rows_k, grid, 256, 0, s, (const uint32_t *)src, (uint32_t *)dst, A, Bd, W, dst_ld);
+  return cudaGetLastError();
+}
 
 cudaError_t copy_rows_strided(const void *src, void *dst, int64_t A, int64_t B, int64_t src_B, int64_t dst_B, int W,
                               cudaStream_t s) {

@@ -85,7 +85,7 @@ bool aligned256(const void *p) { return p && ((uintptr_t)p & 255u) == 0; }
 extern "C" int evo_block_fwd_noalloc(const evo_dims *d, const float *params, const void *params_bf16,
                                      const void *m_in, const void *z_in, void *m_out, void *z_out,
                                      const float *msa_mask, const float *pair_mask, evo_stream_t stream) {
-  const int v = evo::validate_dims(d);
+  const int v = evo::validate_infer_dims(d);
   if (v != EVO_OK) return v;
   const bool bf = d->act_dtype == EVO_BF16;
   if (!params || !m_in || !z_in || !m_out || !z_out || !msa_mask || !pair_mask || (bf && !params_bf16))

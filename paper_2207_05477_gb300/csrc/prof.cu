@@ -9,6 +9,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "evo.h"
 #include "prof.h"
 
@@ -35,6 +37,16 @@ size_t g_next = 0;
 }  // namespace
 
 bool prof_on() { return g_on && !g_paused; }
+
+bool prof_nvtx() {
+  static const bool on = [] {
+    const char *v = std::getenv("EVO_NVTX");
+    return v && v[0] == '1';
+  }();
+  return on;
+}
+void prof_nvtx_push(const char *name) { nvtxRangePushA(name); }
+void prof_nvtx_pop() { nvtxRangePop(); }
 
 bool pdl_enabled() {
   static const bool on = [] {

@@ -67,12 +67,14 @@ __device__ __forceinline__ void load_mask(const float *mask, int R, int orow, in
   }
 }
 
+// the four source tiles ap, ag, bp, bg (swap: bp, bg, ap, ag)
 __device__ __forceinline__ void load_abg(const CUtensorMap *tm, uint32_t tiles, int cm, int c0, int q0, int orow,
-                                         int incoming, uint64_t *bar) {
+                                         int incoming, uint64_t *bar, int swap = 0) {
 #pragma unroll
   for (int s = 0; s < 4; ++s) {
-    if (incoming) tma_load_3d(tiles + s * TT_TILE, tm, s * cm + c0, orow, q0, bar);
-    else tma_load_3d(tiles + s * TT_TILE, tm, s * cm + c0, q0, orow, bar);
+    const int src = swap ? (s ^ 2) : s;
+    if (incoming) tma_load_3d(tiles + s * TT_TILE, tm, src * cm + c0, orow, q0, bar);
+    else tma_load_3d(tiles + s * TT_TILE, tm, src * cm + c0, q0, orow, bar);
   }
 }
 
@@ -81,7 +83,7 @@ __device__ __forceinline__ void load_abg(const CUtensorMap *tm, uint32_t tiles, 
 __global__ void __launch_bounds__(256) trimul_gate_fwd_tma(const __grid_constant__ CUtensorMap tm_abg,
                                                            const __grid_constant__ CUtensorMap tm_A,
                                                            const __grid_constant__ CUtensorMap tm_B,
-                                                           const float *mask, int R, int cm, int incoming) {
+                                                           const float *mask, int R, int cm, int incoming, int swap) {
   extern __shared__ uint8_t dsm[];
   __shared__ __align__(8) uint64_t bar;
   __shared__ volatile int s_abort;
@@ -98,7 +100,7 @@ __global__ void __launch_bounds__(256) trimul_gate_fwd_tma(const __grid_constant
   pdl_entry();  // abg is the previous kernel's output
   if (threadIdx.x == 0) {
     mbar_arrive_expect_tx(&bar, 4 * TT_TILE);
-    load_abg(&tm_abg, in, cm, c0, q0, orow, incoming, &bar);
+    load_abg(&tm_abg, in, cm, c0, q0, orow, incoming, &bar, swap);
   }
   float mk[2];
   load_mask(mask, R, orow, q0, incoming, mk);
@@ -377,8 +379,9 @@ __global__ void __launch_bounds__(256) ln_bwd_cm_tma(const __grid_constant__ CUt
 }
 
 // row-major [R][R][C] map, boxes of 64 channels x 64 positions j
-bool map_rows(CUtensorMap *tm, const void *p, int R, int C) {
-  const uint64_t dims[3] = {(uint64_t)C, (uint64_t)R, (uint64_t)R};
+bool map_rows(CUtensorMap *tm, const void *p, int R, int C, int rows = -1) {
+  if (rows < 0) rows = R;
+  const uint64_t dims[3] = {(uint64_t)C, (uint64_t)R, (uint64_t)rows};
   const uint64_t st[2] = {(uint64_t)C * 2, (uint64_t)R * C * 2};
   const uint32_t box[3] = {64, 64, 1};
   return make_tmap_nd(tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, p, dims, st, box, CU_TENSOR_MAP_SWIZZLE_128B);
@@ -386,16 +389,19 @@ bool map_rows(CUtensorMap *tm, const void *p, int R, int C) {
 
 // abg-like map: channels [0, 4 cm) of rows of ld elements, positions in
 // stride order (outgoing: ocol then orow; incoming: orow then ocol)
-bool map_abg(CUtensorMap *tm, const void *p, int64_t ld, int R, int cm, int incoming) {
-  const uint64_t dims[3] = {(uint64_t)4 * cm, (uint64_t)R, (uint64_t)R};
+bool map_abg(CUtensorMap *tm, const void *p, int64_t ld, int R, int cm, int incoming, int rows = -1) {
+  if (rows < 0) rows = R;  // an outgoing i-slab: rows orow of R columns
+  const uint64_t dims[3] = {(uint64_t)4 * cm, (uint64_t)R, (uint64_t)rows};
   const uint64_t st[2] = {(uint64_t)ld * 2, (uint64_t)R * ld * 2};
   const uint32_t box[3] = {TT_C, incoming ? 1u : (uint32_t)TT_Q, incoming ? (uint32_t)TT_Q : 1u};
   return make_tmap_nd(tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, p, dims, st, box, CU_TENSOR_MAP_SWIZZLE_128B);
 }
 // channel-major map: [c][orow][ocol] with row pitch, ocol clipped at R
-bool map_cm(CUtensorMap *tm, const void *p, int64_t pitch, int R, int cm) {
-  const uint64_t dims[3] = {(uint64_t)R, (uint64_t)R, (uint64_t)cm};
-  const uint64_t st[2] = {(uint64_t)pitch * 2, (uint64_t)R * pitch * 2};
+bool map_cm(CUtensorMap *tm, const void *p, int64_t pitch, int R, int cm, int rows = -1, int64_t cstride = -1) {
+  if (rows < 0) rows = R;
+  if (cstride < 0) cstride = (int64_t)R * pitch;
+  const uint64_t dims[3] = {(uint64_t)R, (uint64_t)rows, (uint64_t)cm};
+  const uint64_t st[2] = {(uint64_t)pitch * 2, (uint64_t)cstride * 2};
   const uint32_t box[3] = {TT_Q, 1, TT_C};
   return make_tmap_nd(tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, p, dims, st, box, CU_TENSOR_MAP_SWIZZLE_128B);
 }
@@ -422,7 +428,28 @@ cudaError_t trimul_gate_fwd_tma_launch(const void *abg, int64_t ld, const float 
     attr = true;
   }
   const dim3 grid((R + TT_Q - 1) / TT_Q, R, cm / TT_C);
-  return launch_k(trimul_gate_fwd_tma, grid, 256, smem, s, ta, tA, tB, mask, R, cm, incoming);
+  return launch_k(trimul_gate_fwd_tma, grid, 256, smem, s, ta, tA, tB, mask, R, cm, incoming, 0);
+}
+
+cudaError_t trimul_gate_fwd_rows(const void *abg, int64_t ld, const float *mask, void *A, int64_t a_cstride, void *B,
+                                 int64_t b_cstride, int64_t pitch, int rows, int R, int cm, int swap, cudaStream_t s) {
+  if (rows <= 0) return cudaSuccess;
+  if (!trimul_gate_tma_supported(abg, ld, A, B, pitch, R, cm) || a_cstride % 8 || b_cstride % 8)
+    return cudaErrorNotSupported;
+  Prof prof("trimul_gate_fwd", s, 0, 2.0 * rows * (double)R * 6.0 * cm, 1);
+  CUtensorMap ta, tA, tB;
+  if (!map_abg(&ta, abg, ld, R, cm, 0, rows) || !map_cm(&tA, A, pitch, R, cm, rows, a_cstride) ||
+      !map_cm(&tB, B, pitch, R, cm, rows, b_cstride))
+    return cudaErrorNotSupported;
+  const int smem = 6 * TT_TILE + 1024;
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(trimul_gate_fwd_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  const dim3 grid((R + TT_Q - 1) / TT_Q, rows, cm / TT_C);
+  return launch_k(trimul_gate_fwd_tma, grid, 256, smem, s, ta, tA, tB, mask, R, cm, 0, swap);
 }
 
 cudaError_t trimul_gate_bwd_tma_launch(const void *dA, const void *dB, int64_t pitch, const void *abg, int64_t ld,
@@ -458,6 +485,23 @@ cudaError_t ln_fwd_cm_tma_launch(const void *x, int64_t pitch, const float *gamm
     attr = smem;
   }
   return launch_k(ln_fwd_cm_tma, dim3((R + 63) / 64, R), 256, smem, s, tx, ty, gamma, beta, C);
+}
+
+cudaError_t ln_fwd_cm_rows(const void *x, int64_t pitch, int64_t cstride, const float *gamma, const float *beta,
+                           void *y, int rows, int R, int C, cudaStream_t s) {
+  if (rows <= 0) return cudaSuccess;
+  if (!ln_cm_tma_supported(x, pitch, y, R, C) || cstride % 8) return cudaErrorNotSupported;
+  Prof p("ln_fwd_cm", s, 0, 4.0 * rows * (double)R * C);
+  CUtensorMap tx, ty;
+  if (!map_cm(&tx, x, pitch, R, C, rows, cstride) || !map_rows(&ty, y, R, C, rows)) return cudaErrorNotSupported;
+  const int smem = 2 * (C / 64) * TT_TILE + 1024;
+  static int attr = 0;
+  if (attr < smem) {
+    cudaError_t e = cudaFuncSetAttribute(ln_fwd_cm_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    attr = smem;
+  }
+  return launch_k(ln_fwd_cm_tma, dim3((R + 63) / 64, rows), 256, smem, s, tx, ty, gamma, beta, C);
 }
 
 cudaError_t ln_bwd_cm_tma_launch(const void *dy, const void *x, int64_t pitch, const float *gamma, void *dx, int R,

@@ -33,7 +33,7 @@ class EvoError(RuntimeError):
 class CDims(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int32) for n in (
         "n_seq", "n_res", "c_m", "c_z", "h_msa", "c_msa", "h_tri", "c_tri",
-        "c_mul", "c_opm", "trans_n", "msa_col_mode", "act_dtype")]
+        "c_mul", "c_opm", "trans_n", "msa_col_mode", "act_dtype", "pair_slab")]
 
 
 class CProfileEntry(ctypes.Structure):
@@ -141,10 +141,11 @@ def _check(code, where):
         raise EvoError(code, where)
 
 
-def cdims(d, act_dtype):
-    """ctypes evo_dims from a synth.Dims-like object."""
+def cdims(d, act_dtype, pair_slab=0):
+    """ctypes evo_dims from a synth.Dims-like object; pair_slab > 0 runs the
+    inference plan's pair stack that many rows at a time (Sec. 3.4.4)."""
     return CDims(d.n_seq, d.n_res, d.c_m, d.c_z, d.h_msa, d.c_msa, d.h_tri, d.c_tri, d.c_mul, d.c_opm,
-                 d.trans_n, d.msa_col_mode, act_dtype)
+                 d.trans_n, d.msa_col_mode, act_dtype, pair_slab)
 
 
 def param_count(cd):

@@ -47,6 +47,30 @@ def test_workspace_queries_and_errors(built_lib):
         evo.workspace_size(cd, 7)
 
 
+def test_pair_slab_field(built_lib):
+    """i-slab subbatching (Sec. 3.4.4) shrinks the inference plan's scratch
+    (the pair intermediates of one slab instead of the whole grid); it is read
+    by the inference plan only, needs the BF16 kernels, and a slab of all the
+    rows is the unslabbed plan."""
+    d = synth.DIMS_TRAIN_CROP.replace(n_res=1024)
+    full = evo.workspace_size(evo.cdims(d, evo.EVO_BF16), evo.EVO_MODE_INFER)
+    eighth = evo.workspace_size(evo.cdims(d, evo.EVO_BF16, pair_slab=128), evo.EVO_MODE_INFER)
+    assert eighth < 0.5 * full
+    assert evo.workspace_size(evo.cdims(d, evo.EVO_BF16, pair_slab=1024), evo.EVO_MODE_INFER) == full
+    # the training plans ignore it
+    assert evo.workspace_size(evo.cdims(d, evo.EVO_BF16, pair_slab=128), evo.EVO_MODE_FWD) == \
+        evo.workspace_size(evo.cdims(d, evo.EVO_BF16), evo.EVO_MODE_FWD)
+    with pytest.raises(evo.EvoError) as e:
+        evo.workspace_size(evo.cdims(d, evo.EVO_F32, pair_slab=128), evo.EVO_MODE_INFER)
+    assert e.value.code == evo.EVO_ERR_UNSUPPORTED
+    with pytest.raises(evo.EvoError) as e:
+        evo.workspace_size(evo.cdims(d.replace(c_mul=96), evo.EVO_BF16, pair_slab=128), evo.EVO_MODE_INFER)
+    assert e.value.code == evo.EVO_ERR_UNSUPPORTED
+    with pytest.raises(evo.EvoError) as e:
+        evo.workspace_size(evo.cdims(d, evo.EVO_BF16, pair_slab=-1), evo.EVO_MODE_INFER)
+    assert e.value.code == evo.EVO_ERR_INVALID_ARG
+
+
 def test_null_and_misaligned_pointers_are_rejected_before_any_launch(built_lib):
     cd = evo.cdims(synth.DIMS_SMALL_FP32, evo.EVO_F32)
     L = built_lib

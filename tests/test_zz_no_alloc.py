@@ -24,12 +24,14 @@ from paper_2207_05477_gb300 import evo, synth
 
 pytestmark = pytest.mark.gpu
 
-CASES = [(synth.DIMS_SMALL_FP32, 32), (synth.Dims(n_seq=8, n_res=24), 7), (synth.Dims(n_seq=5, n_res=37), 8)]
+# (dims, seed, pair_slab): the last case also runs the i-slab plan on the
+# BF16 path (rows 12 at a time, a last slab of one row)
+CASES = [(synth.DIMS_SMALL_FP32, 32, 0), (synth.Dims(n_seq=8, n_res=24), 7, 0), (synth.Dims(n_seq=5, n_res=37), 8, 12)]
 
 
-def _inputs(d, act, seed, dev):
+def _inputs(d, act, seed, dev, slab=0):
     dt = torch.bfloat16 if act == evo.EVO_BF16 else torch.float32
-    cd = evo.cdims(d, act)
+    cd = evo.cdims(d, act, pair_slab=slab if act == evo.EVO_BF16 else 0)
     prob = synth.make_problem(d, seed, pad_frac=0.1)
     params = torch.tensor(prob["params"], device=dev)
     p16 = evo.bf16_params(cd, params)
@@ -58,8 +60,8 @@ def _poison_scratch(act, dev):
 def test_noalloc_forward_matches_workspace_forward(built_lib, act):
     dev = torch.device("cuda:0")
     _poison_scratch(act, dev)
-    for d, seed in CASES:
-        cd, params, p16, m, z, mm, pm = _inputs(d, act, seed, dev)
+    for d, seed, slab in CASES:
+        cd, params, p16, m, z, mm, pm = _inputs(d, act, seed, dev, slab)
         ref_m, ref_z = torch.empty_like(m), torch.empty_like(z)
         ws = evo.workspace(cd, evo.EVO_MODE_FWD, dev)
         evo.block_fwd(cd, params, p16, m, z, ref_m, ref_z, mm, pm, ws)
