@@ -35,10 +35,10 @@ def _run(case, d, act, pad_frac=0.0, trailing=False, dropout=False, seed=32):
     return out, ref
 
 
-def _run_fwd(case, d, act, seed=32):
+def _run_fwd(case, d, act, seed=32, pad_frac=0.0):
     bf = act == evo.EVO_BF16
-    out = gpu_run(d, act, seed=seed, backward=False)
-    mo, zo = oracle_fwd(d, seed, bf16_inputs=bf)
+    out = gpu_run(d, act, seed=seed, pad_frac=pad_frac, backward=False)
+    mo, zo = oracle_fwd(d, seed, pad_frac, bf16_inputs=bf)
     errs = {"m": rel_l2(out["m"], mo), "z": rel_l2(out["z"], zo)}
     check(case, errs, BF16_TOL if bf else FP32_TOL, None, slice_errors(out, {"m": mo, "z": zo}))
 
@@ -101,6 +101,22 @@ def test_bf16_forward_long_sequence(built_lib):
     """A forward at N_res = 768 with four sequences: triangle attention over
     768 keys (six 128-key blocks), the pair stack at three times the crop."""
     _run_fwd("block_bf16_fwd_R768", synth.Dims(n_seq=4, n_res=768), evo.EVO_BF16)
+
+
+# The two smallest proteins of the seeded 16-protein batch (N_res ~ U[64, 1024],
+# N_seq ~ U[32, 512], the batched-inference workload), one block forward each
+# at its own sizes, 5 % padded residues.
+def _batch16_smallest(k=2):
+    import numpy as np
+    rng = np.random.default_rng(32)
+    prot = [(int(rng.integers(32, 513)), int(rng.integers(64, 1025))) for _ in range(16)]
+    return sorted(prot, key=lambda p: p[1])[:k]
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("S,R", _batch16_smallest())
+def test_bf16_forward_batch16_smallest_proteins(built_lib, S, R):
+    _run_fwd(f"block_bf16_fwd_S{S}_R{R}", synth.Dims(n_seq=S, n_res=R), evo.EVO_BF16, pad_frac=0.05)
 
 
 # ------------------------------------------------- extra-MSA block (global column attention)
