@@ -438,7 +438,7 @@ __global__ void __launch_bounds__(AT_WARPS * 32, 2) attn_fwd_short(const __grid_
 // of a row never exist in full anywhere), and the blocks of all of a CTA's
 // tiles form one stream, so the copies and MMAs of the next tile run under
 // the softmax and epilogue of this one:
-//   * warp 8 (control): loads block G's K, V, pair-bias tile and key mask
+//   * warp SW (control): loads block G's K, V, pair-bias tile and key mask
 //     into ring slot G % 3 (TMA for K, V at c = 32 and for the bias; its
 //     lanes write the mask and, at c < 32, the zero-padded K / V rows, all
 //     fetched into registers one block ahead so that no global load sits on
@@ -447,13 +447,16 @@ __global__ void __launch_bounds__(AT_WARPS * 32, 2) attn_fwd_short(const __grid_
 //     softmax warps have read S_G and written P_G into P buffer G % 2,
 //     O += P_G V_G (A = P from TMEM; a tile's first block starts O afresh)
 //     and at once S_{G+2} into the S buffer just read;
-//   * warps 0-7 (thread = query row = TMEM lane; warps w and w + 4 share a
-//     lane quarter and take 32 keys of each block each): logits in the log2
-//     domain (scale, pair bias, key mask), the block's row max (the two
-//     warps of a row meet at a named barrier), the running max m and the
-//     partial sums l, P = 2^(logit - m) as bf16 pairs into the P buffer.
+//   * the SW softmax warps (thread = query row = TMEM lane): with SW = 8,
+//     warps w and w + 4 share a lane quarter and take 32 keys of each block
+//     each, and the two warps of a row meet at a named barrier for the
+//     block's row max; with SW = 4 (long key streams) one warp per lane
+//     quarter takes all 64 keys and needs no exchange.  They form the
+//     logits in the log2 domain (scale, pair bias, key mask), the block's
+//     row max, the running max m and the partial sums l, and write
+//     P = 2^(logit - m) as bf16 pairs into the P buffer.
 //     m only moves when a block's row max exceeds it by more than 8 (so
-//     P <= 2^8): then the accumulated O (each warp its 16 columns, after the
+//     P <= 2^8): then the accumulated O (its columns of the row, after the
 //     last O += P V has finished) and l are rescaled, which after a tile's
 //     first block happens rarely;
 //   * tile epilogue: O / l, the sigmoid-gated copy (bf16; the gate row is
@@ -533,7 +536,8 @@ __device__ __forceinline__ TileId tile_id(const AttnFwdArgs &A, int t) {
   return r;
 }
 
-__global__ void __launch_bounds__(FW_THREADS, 2) attn_fwd_stream(const __grid_constant__ CUtensorMap tmQ,
+template <int SW>
+__global__ void __launch_bounds__((SW + 1) * 32, 2) attn_fwd_stream(const __grid_constant__ CUtensorMap tmQ,
                                                              const __grid_constant__ CUtensorMap tmK,
                                                              const __grid_constant__ CUtensorMap tmV,
                                                              const __grid_constant__ CUtensorMap tmB, AttnFwdArgs A) {
@@ -556,7 +560,7 @@ __global__ void __launch_bounds__(FW_THREADS, 2) attn_fwd_stream(const __grid_co
     for (int i = 0; i < FW_NQ; ++i) mbar_init(&bar_q[i], 1);
     for (int i = 0; i < FW_NS; ++i) mbar_init(&bar_full[i], 2);  // TMA bytes + the control warp's arrival
     for (int i = 0; i < 2; ++i)
-      mbar_init(&bar_s[i], 1), mbar_init(&bar_p[i], FW_SOFT_WARPS), mbar_init(&bar_o[i], 1);
+      mbar_init(&bar_s[i], 1), mbar_init(&bar_p[i], SW), mbar_init(&bar_o[i], 1);
     s_abort = 0;
     fence_mbar_init();
   }
@@ -573,7 +577,7 @@ __global__ void __launch_bounds__(FW_THREADS, 2) attn_fwd_stream(const __grid_co
   // global memory only from here on: wait for the kernels before this one
   pdl_wait();
 
-  if (warp == FW_SOFT_WARPS) {
+  if (warp == SW) {
     // ------------------------------------------------------------ control warp
     const bool leader = lane == 0;
     const int per = c >> 3;  // 16-byte pieces of a K / V row
@@ -757,6 +761,146 @@ __global__ void __launch_bounds__(FW_THREADS, 2) attn_fwd_stream(const __grid_co
       for (int i = q_waited; i < q_loaded; ++i) mbar_drain(&bar_q[i % FW_NQ], (uint32_t)((i / FW_NQ) & 1));
       for (int G = waited; G < loaded; ++G) mbar_drain(&bar_full[G % FW_NS], (uint32_t)((G / FW_NS) & 1));
       if (last_bar) mbar_drain(last_bar, last_par);
+    }
+  } else if constexpr (SW == 4) {
+    // ---------------------------------------- softmax warps, one per lane quarter
+    // thread = query row, all 64 keys of a block: no exchange with a partner
+    const int quarter = warp;
+    const int row = quarter * 32 + lane;  // query row within the tile (TMEM lane)
+    const uint32_t lane_base = tmem + ((uint32_t)(quarter * 32) << 16);
+    const float sl2 = a.scale * EVO_LOG2E;
+    bool ok = true;
+    for (int i = 0; i < ntile; ++i) {
+      const TileId t = tile_id(A, (int)blockIdx.x + i * (int)gridDim.x);
+      const int x = t.x0 + row;
+      // the gate row of this tile, needed at its end
+      uint4 gw[4] = {make_uint4(0, 0, 0, 0), make_uint4(0, 0, 0, 0), make_uint4(0, 0, 0, 0),
+                     make_uint4(0, 0, 0, 0)};
+      if (x < a.X) {
+        const uint4 *gp =
+            reinterpret_cast<const uint4 *>((const bf16 *)a.g + (int64_t)t.b * a.sQb + (int64_t)x * a.sQx + t.h * c);
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          if (q * 8 < c) gw[q] = gp[q];
+      }
+      float m_run = NEG_INF_F, l = 0.f;
+      for (int j = 0; j < nb; ++j) {
+        const int G = i * nb + j, sl = G % FW_NS;
+        const uint32_t slot = base + FW_RING_OFF + sl * FW_SLOT;
+        const uint32_t sbuf = lane_base + (uint32_t)((G & 1) * FW_KB);
+        // tcgen05.ld / st are warp-collective: the guards around them are warp-uniform
+        ok = __all_sync(0xffffffffu, ok && mbar_wait(&bar_s[G & 1], (uint32_t)((G >> 1) & 1), &s_abort));
+        ok = __all_sync(0xffffffffu, ok && mbar_wait(&bar_full[sl], (uint32_t)((G / FW_NS) & 1), &s_abort));
+        float v[64];
+        float mloc = NEG_INF_F;
+        if (ok) {
+          tc_fence_after();
+#pragma unroll
+          for (int hf = 0; hf < 2; ++hf) {
+            uint32_t r[32];
+            tmem_ld32(sbuf + (uint32_t)(hf * 32), r);
+            const float4 *ma = reinterpret_cast<const float4 *>(gbase + FW_M_OFF) + sl * (FW_KB / 4) + hf * 8;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+              const float4 mv = ma[q];
+              v[32 * hf + 4 * q] = fmaf(__uint_as_float(r[4 * q]), sl2, mv.x);
+              v[32 * hf + 4 * q + 1] = fmaf(__uint_as_float(r[4 * q + 1]), sl2, mv.y);
+              v[32 * hf + 4 * q + 2] = fmaf(__uint_as_float(r[4 * q + 2]), sl2, mv.z);
+              v[32 * hf + 4 * q + 3] = fmaf(__uint_as_float(r[4 * q + 3]), sl2, mv.w);
+            }
+          }
+          if (A.has_bias) {
+            // this row's 128-byte line of the bias tile (64 keys; piece k at k ^ (row & 7))
+            const uint32_t rb = slot + FW_SB + (uint32_t)row * 128u;
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+              const uint4 w = lds128(rb + (uint32_t)((k ^ (row & 7)) << 4));
+              const __nv_bfloat162 *hv = reinterpret_cast<const __nv_bfloat162 *>(&w);
+#pragma unroll
+              for (int q = 0; q < 4; ++q) {
+                const float2 f = __bfloat1622float2(hv[q]);
+                v[8 * k + 2 * q] = fmaf(f.x, EVO_LOG2E, v[8 * k + 2 * q]);
+                v[8 * k + 2 * q + 1] = fmaf(f.y, EVO_LOG2E, v[8 * k + 2 * q + 1]);
+              }
+            }
+          }
+#pragma unroll
+          for (int k = 0; k < 64; ++k) mloc = fmaxf(mloc, v[k]);
+          const bool need = m_run == NEG_INF_F ? mloc > NEG_INF_F : mloc > m_run + FW_RESCALE;
+          if (__any_sync(0xffffffffu, need)) {
+            float corr = 1.f;
+            if (need) {
+              corr = m_run == NEG_INF_F ? 0.f : ex2(m_run - mloc);
+              m_run = mloc;
+            }
+            l *= corr;
+            if (j > 0) {
+              // O holds the tile's blocks before this one: rescale the row once their product is done
+              ok = __all_sync(0xffffffffu,
+                              mbar_wait(&bar_o[(G - 1) & 1], (uint32_t)(((G - 1) >> 1) & 1), &s_abort));
+              if (ok) {
+                tc_fence_after();
+                uint32_t r[32];
+                tmem_ld32(lane_base + FW_O_COL, r);
+#pragma unroll
+                for (int k = 0; k < 32; ++k) r[k] = __float_as_uint(__uint_as_float(r[k]) * corr);
+                tmem_st32(lane_base + FW_O_COL, r);
+              }
+            }
+          }
+        }
+        if (ok) {
+          const float muse = m_run == NEG_INF_F ? 0.f : m_run;
+          uint32_t pk[32];
+#pragma unroll
+          for (int k = 0; k < 32; ++k) {
+            const float p0 = ex2(v[2 * k] - muse), p1 = ex2(v[2 * k + 1] - muse);
+            l += p0 + p1;
+            __nv_bfloat162 hv = __floats2bfloat162_rn(p0, p1);
+            pk[k] = *reinterpret_cast<uint32_t *>(&hv);
+          }
+          // P buffer G % 2: its last reader, O += P_{G-2} V_{G-2}, finished before S_G did
+          tmem_st32(lane_base + (uint32_t)(FW_P_COL + (G & 1) * (FW_KB / 2)), pk);
+          tmem_wait_st();
+          tc_fence_before();
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&bar_p[G & 1]);
+      }
+      // tile epilogue
+      const int Glast = i * nb + nb - 1;
+      ok = __all_sync(0xffffffffu, ok && mbar_wait(&bar_o[Glast & 1], (uint32_t)((Glast >> 1) & 1), &s_abort));
+      if (ok) {
+        tc_fence_after();
+        uint32_t r[32];
+        tmem_ld32(lane_base + FW_O_COL, r);
+        if (x < a.X) {
+          const float inv = l > 0.f ? 1.f / l : 0.f;
+          bf16 *op = (bf16 *)a.o_att + (int64_t)t.b * a.sOb + (int64_t)x * a.sOx + t.h * c;
+          bf16 *gop = (bf16 *)a.o_gate + (int64_t)t.b * a.sOb + (int64_t)x * a.sOx + t.h * c;
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            if (q * 8 < c) {
+              const __nv_bfloat162 *gh = reinterpret_cast<const __nv_bfloat162 *>(&gw[q]);
+              uint4 ow, gow;
+              uint32_t *o32 = reinterpret_cast<uint32_t *>(&ow), *g32 = reinterpret_cast<uint32_t *>(&gow);
+#pragma unroll
+              for (int k = 0; k < 4; ++k) {
+                const float v0 = __uint_as_float(r[q * 8 + 2 * k]) * inv;
+                const float v1 = __uint_as_float(r[q * 8 + 2 * k + 1]) * inv;
+                const float2 gf = __bfloat1622float2(gh[k]);
+                __nv_bfloat162 o2 = __floats2bfloat162_rn(v0, v1);
+                __nv_bfloat162 g2 = __floats2bfloat162_rn(v0 * gf.x, v1 * gf.y);
+                o32[k] = *reinterpret_cast<uint32_t *>(&o2);
+                g32[k] = *reinterpret_cast<uint32_t *>(&g2);
+              }
+              *reinterpret_cast<uint4 *>(op + q * 8) = ow;
+              *reinterpret_cast<uint4 *>(gop + q * 8) = gow;
+            }
+          }
+          a.lse2[((int64_t)t.b * a.H + t.h) * a.X + x] = l > 0.f ? m_run + log2f(l) : POS_INF_F;
+        }
+      }
     }
   } else {
     // ------------------------------------------------------------ softmax warps
@@ -1850,7 +1994,7 @@ cudaError_t attn_fwd_stream_launch(const AttnArgs &a, cudaStream_t s, double flo
   }
   static bool attr = false;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(attn_fwd_stream, cudaFuncAttributeMaxDynamicSharedMemorySize, FW_SMEM);
+    cudaError_t e = cudaFuncSetAttribute(attn_fwd_stream<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, FW_SMEM);
     if (e != cudaSuccess) return e;
     attr = true;
   }
@@ -1859,7 +2003,22 @@ cudaError_t attn_fwd_stream_launch(const AttnArgs &a, cudaStream_t s, double flo
   if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int grid = (int)std::min<long long>(tiles, 2ll * sms);
   Prof p("attn_fwd_tc", s, flops, bytes);
-  launch_k(attn_fwd_stream, grid, FW_THREADS, FW_SMEM, s, tq, tk, tv, tb, A);
+  // long key streams (16 blocks of 64 or more) take one softmax warp per TMEM
+  // lane quarter (a thread works all 64 keys of a block and needs no
+  // partner's row max): 4 % faster at 2048 keys; shorter streams keep two
+  // warps per quarter, whose extra warps hide more of the per-tile latency
+  // (1.4 % faster at 384 keys)
+  if (A.nb >= 16) {
+    static bool attr4 = false;
+    if (!attr4) {
+      cudaError_t e = cudaFuncSetAttribute(attn_fwd_stream<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, FW_SMEM);
+      if (e != cudaSuccess) return e;
+      attr4 = true;
+    }
+    launch_k(attn_fwd_stream<4>, grid, 5 * 32, FW_SMEM, s, tq, tk, tv, tb, A);
+  } else {
+    launch_k(attn_fwd_stream<8>, grid, FW_THREADS, FW_SMEM, s, tq, tk, tv, tb, A);
+  }
   return cudaGetLastError();
 }
 

@@ -103,6 +103,15 @@ def test_bf16_forward_long_sequence(built_lib):
     _run_fwd("block_bf16_fwd_R768", synth.Dims(n_seq=4, n_res=768), evo.EVO_BF16)
 
 
+@pytest.mark.slow
+def test_bf16_fwd_bwd_deep_msa_column_attention(built_lib):
+    """Column attention over 1100 sequences (18 key blocks of 64, the last
+    ragged): the long-stream forward kernel (one softmax warp per TMEM lane
+    quarter) and the streaming backward, fwd+bwd against the oracle at a
+    small N_res so that the FP64 oracle stays quick."""
+    _run("block_bf16_deep_msa_S1100_R16", synth.Dims(n_seq=1100, n_res=16), evo.EVO_BF16, pad_frac=0.05)
+
+
 # The two smallest proteins of the seeded 16-protein batch (N_res ~ U[64, 1024],
 # N_seq ~ U[32, 512], the batched-inference workload), one block forward each
 # at its own sizes, 5 % padded residues.

@@ -87,6 +87,17 @@ MEASURED = {
         "pair_trans.w1": 0.098,  # 0.0889
         "tri_in.ln_in.gamma": 0.062,  # 0.0563
     },
+    "block_bf16_deep_msa_S1100_R16": {
+        "msa_trans.ln.beta": 0.055,  # 0.0500
+        "opm.b_ab": 0.058,  # 0.0523
+        "opm.ln.beta": 0.061,  # 0.0553
+        "opm.ln.gamma": 0.061,  # 0.0549
+        "opm.w_ab": 0.057,  # 0.0512
+        "pair_trans.b1": 0.081,  # 0.0728
+        "pair_trans.ln.beta": 0.097,  # 0.0879
+        "pair_trans.ln.gamma": 0.087,  # 0.0788
+        "pair_trans.w1": 0.076,  # 0.0688
+    },
     "block_bf16_finetune": {
         "msa_trans.ln.gamma": 0.056,  # 0.0506
         "pair_trans.b1": 0.068,  # 0.0617
