@@ -564,8 +564,11 @@ def ours_arm(args):
     if os.path.exists(tfile):
         with open(tfile) as f:
             tr = json.load(f)
-        if dom_name in tr and tr[dom_name].get("valid", False):
-            roof["traffic"] = tr[dom_name]["bytes_per_launch"]
+        ent = tr.get(dom_name, {})
+        # the capture's figure holds for its own workload shape only
+        same = ent.get("n_seq") == d.n_seq and ent.get("n_res") == d.n_res and not args.dropout
+        if ent.get("valid", False) and same:
+            roof["traffic"] = ent["bytes_per_launch"]
 
     ex2 = measure_ex2_rate(evo, dev)
     roof["classes"] = class_rooflines(prof, peaks, clk, ex2)
