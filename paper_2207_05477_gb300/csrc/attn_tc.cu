@@ -2003,12 +2003,12 @@ cudaError_t attn_fwd_stream_launch(const AttnArgs &a, cudaStream_t s, double flo
   if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int grid = (int)std::min<long long>(tiles, 2ll * sms);
   Prof p("attn_fwd_tc", s, flops, bytes);
-  // long key streams (16 blocks of 64 or more) take one softmax warp per TMEM
+  // long key streams (12 blocks of 64 or more) take one softmax warp per TMEM
   // lane quarter (a thread works all 64 keys of a block and needs no
   // partner's row max): 4 % faster at 2048 keys; shorter streams keep two
   // warps per quarter, whose extra warps hide more of the per-tile latency
   // (1.4 % faster at 384 keys)
-  if (A.nb >= 16) {
+  if (A.nb >= 12) {
     static bool attr4 = false;
     if (!attr4) {
       cudaError_t e = cudaFuncSetAttribute(attn_fwd_stream<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, FW_SMEM);

@@ -98,8 +98,9 @@ def test_bf16_fwd_bwd_finetune_crop(built_lib):
 
 @pytest.mark.slow
 def test_bf16_forward_long_sequence(built_lib):
-    """A forward at N_res = 768 with four sequences: triangle attention over
-    768 keys (six 128-key blocks), the pair stack at three times the crop."""
+    """A forward at N_res = 768 with four sequences: row and triangle
+    attention with pair bias over 768 keys (twelve 64-key blocks: the
+    long-stream forward kernel), the pair stack at three times the crop."""
     _run_fwd("block_bf16_fwd_R768", synth.Dims(n_seq=4, n_res=768), evo.EVO_BF16)
 
 

@@ -23,6 +23,7 @@ CASES = [
     (synth.Dims(n_seq=5, n_res=37), 12, 4),
     (synth.Dims(n_seq=4, n_res=300), 128, 5),
     (synth.DIMS_EXTRA_MSA.replace(n_seq=16, n_res=48), 20, 6),
+    (synth.Dims(n_seq=4, n_res=1024), 256, 7),  # 16 key blocks: the long-stream attention kernel
 ]
 
 
