@@ -106,8 +106,10 @@ __device__ __forceinline__ uint4 lds128(uint32_t addr) {
 }
 
 // -------------------------------------------------- forward, at most 256 keys
-// Head dim 32 and at most 256 keys (the training-crop attentions): all of a
-// row's logits fit one TMEM tile, so one pass needs no online rescaling.
+// At most 256 keys (the training-crop attentions, and the extra-MSA and
+// template rows): all of a row's logits fit one TMEM tile, so one pass needs
+// no online rescaling.  Head dims 8 and 16 arrive zero-padded to 32 channels
+// (the TMA box is 32 channels wide; the copy fills the rest).
 // One CTA of eight warps per (128 queries, head, batch item):
 //   * TMA brings Q [128 x 32], K and V [Ypad x 32] (64-byte swizzle); each
 //     warp streams its 32 rows of the pair-bias tile in 64-key boxes through
@@ -374,12 +376,13 @@ __global__ void __launch_bounds__(AT_WARPS * 32, 2) attn_fwd_short(const __grid_
   // epilogue: the two warps of a quarter take 16 output channels each; the
   // gate row is requested before the wait for O
   const int x = x0 + row;
-  const int d0 = half * 16;
+  const int c = a.c, d0 = half * 16;
+  const bool mine = d0 < c;  // this warp's 16 output channels hold any of the head's c
   uint4 gwv[2] = {make_uint4(0, 0, 0, 0), make_uint4(0, 0, 0, 0)};
-  if (x < a.X) {
-    const bf16 *gp = (const bf16 *)a.g + (int64_t)b * a.sQb + (int64_t)x * a.sQx + h * AT_C + d0;
+  if (x < a.X && mine) {
+    const bf16 *gp = (const bf16 *)a.g + (int64_t)b * a.sQb + (int64_t)x * a.sQx + h * c + d0;
     gwv[0] = *reinterpret_cast<const uint4 *>(gp);
-    gwv[1] = *reinterpret_cast<const uint4 *>(gp + 8);
+    if (c - d0 > 8) gwv[1] = *reinterpret_cast<const uint4 *>(gp + 8);
   }
   __syncthreads();
   ok = __all_sync(0xffffffffu, ok && !s_abort && mbar_wait(&bar_o, 0, &s_abort));
@@ -388,10 +391,11 @@ __global__ void __launch_bounds__(AT_WARPS * 32, 2) attn_fwd_short(const __grid_
   if (ok) tmem_ld16(lane_base + AT_O_COL + (uint32_t)d0, r);
   if (ok && x < a.X) {
     const float inv = l > 0.f ? 1.f / l : 0.f;
-    bf16 *op = (bf16 *)a.o_att + (int64_t)b * a.sOb + (int64_t)x * a.sOx + h * AT_C + d0;
-    bf16 *gop = (bf16 *)a.o_gate + (int64_t)b * a.sOb + (int64_t)x * a.sOx + h * AT_C + d0;
+    bf16 *op = (bf16 *)a.o_att + (int64_t)b * a.sOb + (int64_t)x * a.sOx + h * c + d0;
+    bf16 *gop = (bf16 *)a.o_gate + (int64_t)b * a.sOb + (int64_t)x * a.sOx + h * c + d0;
 #pragma unroll
     for (int q = 0; q < 2; ++q) {
+      if (q * 8 >= c - d0) continue;  // channels past the head dim (none at c = 32)
       const uint4 gw = gwv[q];
       const bf16 *gh = reinterpret_cast<const bf16 *>(&gw);
       uint4 ow, gow;
@@ -1891,12 +1895,14 @@ __global__ void __launch_bounds__(AT_WARPS * 32, 1) attn_bwd_stream(const __grid
 // outer dimensions ordered by stride (TMA takes them in any order; ascending
 // strides keep every dimension's span inside the next stride).
 bool qkv_map(CUtensorMap *tm, const void *base, int H, int rows, int B1, int64_t s_row, int64_t s_b, int box_rows,
-             QkvPos *pos) {
+             QkvPos *pos, int c = AT_C) {
+  // head dim c <= 32: the box is 32 channels wide all the same, so a row
+  // lands as 64 bytes with channels c..31 filled with zeros by the copy
   struct D {
     uint64_t n, stride;
     uint32_t box;
     int which;  // 0 row, 1 h, 2 b
-  } ds[3] = {{(uint64_t)rows, (uint64_t)s_row, (uint32_t)box_rows, 0}, {(uint64_t)H, AT_C, 1, 1},
+  } ds[3] = {{(uint64_t)rows, (uint64_t)s_row, (uint32_t)box_rows, 0}, {(uint64_t)H, (uint64_t)c, 1, 1},
              {(uint64_t)B1, (uint64_t)s_b, 1, 2}};
   // extent-1 dimensions go last (their stride is never stepped); the rest by stride
   std::stable_sort(ds, ds + 3, [](const D &x, const D &y) {
@@ -1905,7 +1911,7 @@ bool qkv_map(CUtensorMap *tm, const void *base, int H, int rows, int B1, int64_t
   });
   for (int i = 1; i < 3; ++i)
     if (ds[i].n == 1) ds[i].stride = std::max<uint64_t>(ds[i].stride, ds[i - 1].stride * ds[i - 1].n);
-  uint64_t dims[4] = {AT_C, ds[0].n, ds[1].n, ds[2].n};
+  uint64_t dims[4] = {(uint64_t)c, ds[0].n, ds[1].n, ds[2].n};
   uint64_t st[3] = {ds[0].stride * 2, ds[1].stride * 2, ds[2].stride * 2};
   uint32_t box[4] = {AT_C, ds[0].box, ds[1].box, ds[2].box};
   for (int i = 0; i < 3; ++i) {
@@ -1915,7 +1921,7 @@ bool qkv_map(CUtensorMap *tm, const void *base, int H, int rows, int B1, int64_t
     else if (ds[i].which == 1) pos->h = i + 1;
     else pos->b = i + 1;
   }
-  if (ds[0].stride < AT_C) return false;
+  if (c <= 0 || c > AT_C || c % 8 || ds[0].stride < (uint64_t)c) return false;
   return make_tmap_nd(tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, base, dims, st, box, CU_TENSOR_MAP_SWIZZLE_64B);
 }
 
@@ -1942,9 +1948,9 @@ cudaError_t attn_fwd_short_launch(const AttnArgs &a, cudaStream_t s, double flop
   CUtensorMap tq, tk, tv, tb;
   std::memset(&tb, 0, sizeof(tb));
   QkvPos pv;
-  if (!qkv_map(&tq, a.q, a.H, a.X, a.B1, a.sQx, a.sQb, AT_QROWS, &A.pq) ||
-      !qkv_map(&tk, a.k, a.H, a.Y, a.B1, a.sKy, a.sKb, A.ypad, &A.pk) ||
-      !qkv_map(&tv, a.v, a.H, a.Y, a.B1, a.sKy, a.sKb, A.ypad, &pv))
+  if (!qkv_map(&tq, a.q, a.H, a.X, a.B1, a.sQx, a.sQb, AT_QROWS, &A.pq, a.c) ||
+      !qkv_map(&tk, a.k, a.H, a.Y, a.B1, a.sKy, a.sKb, A.ypad, &A.pk, a.c) ||
+      !qkv_map(&tv, a.v, a.H, a.Y, a.B1, a.sKy, a.sKb, A.ypad, &pv, a.c))
     return cudaErrorNotSupported;
   if (a.bias) {
     const uint64_t dims[3] = {(uint64_t)a.Y, (uint64_t)a.X, (uint64_t)a.H};
@@ -1979,12 +1985,13 @@ cudaError_t attn_fwd_stream_launch(const AttnArgs &a, cudaStream_t s, double flo
   std::memset(&tk, 0, sizeof(tk));
   std::memset(&tv, 0, sizeof(tv));
   std::memset(&tb, 0, sizeof(tb));
-  // head dim 32 by TMA where the views allow it; otherwise (and at head dims
-  // 8, 16) the control warp loads the rows
+  // q, k, v by TMA where the views allow it (at head dims 8 and 16 the copy
+  // fills channels c..31 of each 64-byte row with zeros); otherwise the
+  // control warp loads the rows
   QkvPos pv;
-  A.tma_qkv = a.c == AT_C && qkv_map(&tq, a.q, a.H, a.X, a.B1, a.sQx, a.sQb, FW_Q, &A.pq) &&
-              qkv_map(&tk, a.k, a.H, a.Y, a.B1, a.sKy, a.sKb, FW_KB, &A.pk) &&
-              qkv_map(&tv, a.v, a.H, a.Y, a.B1, a.sKy, a.sKb, FW_KB, &pv);
+  A.tma_qkv = qkv_map(&tq, a.q, a.H, a.X, a.B1, a.sQx, a.sQb, FW_Q, &A.pq, a.c) &&
+              qkv_map(&tk, a.k, a.H, a.Y, a.B1, a.sKy, a.sKb, FW_KB, &A.pk, a.c) &&
+              qkv_map(&tv, a.v, a.H, a.Y, a.B1, a.sKy, a.sKb, FW_KB, &pv, a.c);
   if (a.bias) {
     const uint64_t dims[3] = {(uint64_t)a.Y, (uint64_t)a.X, (uint64_t)a.H};
     const uint64_t st[2] = {(uint64_t)a.sBx * 2, (uint64_t)a.sBh * 2};
@@ -2027,7 +2034,7 @@ cudaError_t attn_fwd_stream_launch(const AttnArgs &a, cudaStream_t s, double flo
 cudaError_t attn_fwd_tc_launch(const AttnArgs &a, cudaStream_t s, double flops, double bytes) {
   // the training-crop shapes (head dim 32, at most 256 keys) take the
   // one-pass kernel when TMA can describe the views; everything else streams
-  if (a.c == AT_C && a.Y <= AT_MAXKEYS) {
+  if (a.Y <= AT_MAXKEYS) {
     const cudaError_t e = attn_fwd_short_launch(a, s, flops, bytes);
     if (e != cudaErrorNotSupported) return e;
   }
