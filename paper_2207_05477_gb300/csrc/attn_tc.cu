@@ -1071,7 +1071,10 @@ __global__ void __launch_bounds__((SW + 1) * 32, 2) attn_fwd_stream(const __grid
 
 // ------------------------------------------------------------------ backward
 // One CTA of eight warps per (head, batch item), all X <= 256 queries and
-// Y <= 256 keys.  Query tiles of 128 (qt) and key halves of 128 (kh):
+// Y <= 256 keys; head dims 8 and 16 arrive zero-padded to 32 channels (the
+// 32-channel TMA box fills past the head dim) and only the head's channels
+// of the gradients are stored.  Query tiles of 128 (qt) and key halves of
+// 128 (kh):
 //   for kh: for qt:
 //     S = Q_qt K_kh^T, dP = dO_qt V_kh^T                     (TMEM [0,128), [128,256))
 //     P = 2^(logit - lse2), dS = P (dP - D)     thread = query row, two warps
@@ -1234,9 +1237,10 @@ __global__ void __launch_bounds__(AT_WARPS * 32, 1) attn_bwd_tc(const __grid_con
       }
       if (x < a.X) {
         d_s[x] = dsum;
-        bf16 *gp = (bf16 *)a.dgpre + (int64_t)b * a.sQb + (int64_t)x * a.sQx + h * AT_C;
+        bf16 *gp = (bf16 *)a.dgpre + (int64_t)b * a.sQb + (int64_t)x * a.sQx + h * a.c;
 #pragma unroll
-        for (int j = 0; j < 4; ++j) *reinterpret_cast<uint4 *>(gp + 8 * j) = dgw[j];
+        for (int j = 0; j < 4; ++j)
+          if (8 * j < a.c) *reinterpret_cast<uint4 *>(gp + 8 * j) = dgw[j];
       }
     }
     // do_att is read by the tensor cores (async proxy) and D by every row below
@@ -1423,10 +1427,11 @@ __global__ void __launch_bounds__(AT_WARPS * 32, 1) attn_bwd_tc(const __grid_con
         tmem_ld16(lane_base + BT_DV_COL + (uint32_t)(half * 16), rv);
       }
       if (ok && y < a.Y) {
-        bf16 *dk = (bf16 *)a.dk + (int64_t)b * a.sKb + (int64_t)y * a.sKy + h * AT_C + half * 16;
-        bf16 *dv = (bf16 *)a.dv + (int64_t)b * a.sKb + (int64_t)y * a.sKy + h * AT_C + half * 16;
+        bf16 *dk = (bf16 *)a.dk + (int64_t)b * a.sKb + (int64_t)y * a.sKy + h * a.c + half * 16;
+        bf16 *dv = (bf16 *)a.dv + (int64_t)b * a.sKb + (int64_t)y * a.sKy + h * a.c + half * 16;
 #pragma unroll
         for (int q = 0; q < 2; ++q) {
+          if (half * 16 + 8 * q >= a.c) continue;  // channels past the head dim
           uint4 wk, wv;
           uint32_t *k32 = reinterpret_cast<uint32_t *>(&wk), *v32 = reinterpret_cast<uint32_t *>(&wv);
 #pragma unroll
@@ -1453,9 +1458,10 @@ __global__ void __launch_bounds__(AT_WARPS * 32, 1) attn_bwd_tc(const __grid_con
     uint32_t rq[16];
     if (ok) tmem_ld16(lane_base + BT_DQ_COL + (uint32_t)(qt * 32 + half * 16), rq);
     if (ok && x < a.X) {
-      bf16 *dq = (bf16 *)a.dq + (int64_t)b * a.sQb + (int64_t)x * a.sQx + h * AT_C + half * 16;
+      bf16 *dq = (bf16 *)a.dq + (int64_t)b * a.sQb + (int64_t)x * a.sQx + h * a.c + half * 16;
 #pragma unroll
       for (int q = 0; q < 2; ++q) {
+        if (half * 16 + 8 * q >= a.c) continue;  // channels past the head dim
         uint4 w;
         uint32_t *w32 = reinterpret_cast<uint32_t *>(&w);
 #pragma unroll
@@ -2043,7 +2049,7 @@ cudaError_t attn_fwd_tc_launch(const AttnArgs &a, cudaStream_t s, double flops, 
 
 bool attn_bwd_tc_supported(const AttnArgs &a) {
   auto a16 = [](const void *p) { return ((uintptr_t)p & 15u) == 0; };
-  if (!attn_tc_supported(a) || a.c != AT_C || a.Y > 256 || a.X > 256 || !a.dq || !a.dk || !a.dv) return false;
+  if (!attn_tc_supported(a) || a.Y > 256 || a.X > 256 || !a.dq || !a.dk || !a.dv) return false;
   if (!a16(a.dq) || !a16(a.dk) || !a16(a.dv) || a.sKy % 8 || a.sKb % 8) return false;
   if (a.dog ? (!a.dgpre || !a16(a.dog) || !a16(a.dgpre)) : (!a.do_att || !a.Dsum || !a16(a.do_att))) return false;
   if (a.bias && (!a.dbias || !a16(a.dbias) || a.Y % 4)) return false;
@@ -2062,14 +2068,14 @@ cudaError_t attn_bwd_tc_launch(const AttnArgs &a, cudaStream_t s, double flops, 
   std::memset(&toa, 0, sizeof(toa));
   QkvPos pv, px;
   A.fused_gate = a.dog != nullptr;
-  if (!qkv_map(&tq, a.q, a.H, a.X, a.B1, a.sQx, a.sQb, 128, &A.pq)) return cudaErrorNotSupported;
-  if (!qkv_map(&tk, a.k, a.H, a.Y, a.B1, a.sKy, a.sKb, 128, &A.pk)) return cudaErrorNotSupported;
-  if (!qkv_map(&tv, a.v, a.H, a.Y, a.B1, a.sKy, a.sKb, 128, &pv)) return cudaErrorNotSupported;
-  if (!qkv_map(&to, A.fused_gate ? a.dog : a.do_att, a.H, a.X, a.B1, a.sOx, a.sOb, 128, &A.po))
+  if (!qkv_map(&tq, a.q, a.H, a.X, a.B1, a.sQx, a.sQb, 128, &A.pq, a.c)) return cudaErrorNotSupported;
+  if (!qkv_map(&tk, a.k, a.H, a.Y, a.B1, a.sKy, a.sKb, 128, &A.pk, a.c)) return cudaErrorNotSupported;
+  if (!qkv_map(&tv, a.v, a.H, a.Y, a.B1, a.sKy, a.sKb, 128, &pv, a.c)) return cudaErrorNotSupported;
+  if (!qkv_map(&to, A.fused_gate ? a.dog : a.do_att, a.H, a.X, a.B1, a.sOx, a.sOb, 128, &A.po, a.c))
     return cudaErrorNotSupported;
   if (A.fused_gate) {
-    if (!qkv_map(&tg, a.g, a.H, a.X, a.B1, a.sQx, a.sQb, 128, &px)) return cudaErrorNotSupported;
-    if (!qkv_map(&toa, a.o_att, a.H, a.X, a.B1, a.sOx, a.sOb, 128, &px)) return cudaErrorNotSupported;
+    if (!qkv_map(&tg, a.g, a.H, a.X, a.B1, a.sQx, a.sQb, 128, &px, a.c)) return cudaErrorNotSupported;
+    if (!qkv_map(&toa, a.o_att, a.H, a.X, a.B1, a.sOx, a.sOb, 128, &px, a.c)) return cudaErrorNotSupported;
   }
   if (a.bias) {
     const uint64_t dims[3] = {(uint64_t)a.Y, (uint64_t)a.X, (uint64_t)a.H};
