@@ -305,9 +305,12 @@ __device__ __forceinline__ int head_of_lane(int lane, bool &writer) {
 // Pair-bias projection, BF16: a position's C channels are spread over
 // TPR = C / CPL lanes with CPL channels each, so the lane's slice of w stays
 // in registers; U warp-steps of loads are in flight before the products are
-// reduced over the group (head_reduce).  Grid-stride over warp-steps.
+// reduced over the group (head_reduce).  Grid-stride over warp-steps in the
+// order of the output index q; with transpose the input position is the
+// transposed one (i, j) -> (j, i), whose C channels are one contiguous row,
+// so both the reads and the bf16 writes stay coalesced.
 template <int H, int C, int CPL, int U>
-__global__ void __launch_bounds__(256) head_proj_fwd_w(const bf16 *x, const float *w, bf16 *out, int R,
+__global__ void __launch_bounds__(256, H == 4 ? 3 : 2) head_proj_fwd_w(const bf16 *x, const float *w, bf16 *out, int R,
                                                        int transpose, int64_t P, int64_t hstride) {
   pdl_entry();
   constexpr int TPR = C / CPL, PPW = 32 / TPR;
@@ -327,8 +330,15 @@ __global__ void __launch_bounds__(256) head_proj_fwd_w(const bf16 *x, const floa
     float v[U][CPL];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-      const int64_t p = base + u * PPW + pw;
-      if (p < P) {
+      const int64_t q = base + u * PPW + pw;
+      if (q < P) {
+        int64_t p = q;
+        if (transpose) {
+          int64_t i;
+          int j;
+          divmod(q, R, i, j);
+          p = (int64_t)j * R + i;
+        }
         ldc<CPL>(x + p * C + sub * CPL, v[u]);
       } else {
 #pragma unroll
@@ -345,21 +355,17 @@ __global__ void __launch_bounds__(256) head_proj_fwd_w(const bf16 *x, const floa
         for (int k = 0; k < CPL; ++k) acc[h] = fmaf(v[u][k], wl[h][k], acc[h]);
       }
       const float r = head_reduce<H, TPR>(acc, lane);
-      const int64_t p = base + u * PPW + pw;
-      if (writer && p < P) {
-        int64_t i;
-        int j;
-        divmod(p, R, i, j);
-        const int64_t pp = transpose ? (int64_t)j * R + i : p;
-        out[hsel * hstride + pp] = __float2bfloat16_rn(r);
-      }
+      const int64_t q = base + u * PPW + pw;
+      if (writer && q < P) out[hsel * hstride + q] = __float2bfloat16_rn(r);
     }
   }
 }
 
 // Backward: dx (+)= sum_h dbias[h][pos'] w[h] over the lane's CPL channels,
 // and the lane's slice of dw accumulates in registers (one atomic add per
-// element and block at the end).
+// element and block at the end).  Positions are taken in the order of the
+// dbias index q (the input position is the transposed one with transpose),
+// so the dbias loads are coalesced.
 template <int H, int C, int CPL, int U>
 __global__ void __launch_bounds__(256) head_proj_bwd_w(const float *dbias, const bf16 *x, const float *w, bf16 *dx,
                                                        int accumulate, int R, int transpose, float *dw) {
@@ -378,16 +384,22 @@ __global__ void __launch_bounds__(256) head_proj_bwd_w(const float *dbias, const
   const int64_t w0 = (int64_t)blockIdx.x * 8 + warp;
   for (int64_t base = w0 * (PPW * U); base < P; base += nwarps * (PPW * U)) {
     float v[U][CPL], d[U][CPL], g[U][H];
+    int64_t pos[U];  // input / dx position of step u (-1 past the end)
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-      const int64_t p = base + u * PPW + pw;
-      if (p < P) {
-        int64_t i;
-        int j;
-        divmod(p, R, i, j);
-        const int64_t pp = transpose ? (int64_t)j * R + i : p;
+      const int64_t q = base + u * PPW + pw;
+      pos[u] = -1;
+      if (q < P) {
+        int64_t p = q;
+        if (transpose) {
+          int64_t i;
+          int j;
+          divmod(q, R, i, j);
+          p = (int64_t)j * R + i;
+        }
+        pos[u] = p;
 #pragma unroll
-        for (int h = 0; h < H; ++h) g[u][h] = dbias[h * P + pp];
+        for (int h = 0; h < H; ++h) g[u][h] = dbias[h * P + q];
         ldc<CPL>(x + p * C + sub * CPL, v[u]);
         if (accumulate) {
           ldc<CPL>(dx + p * C + sub * CPL, d[u]);
@@ -411,8 +423,7 @@ __global__ void __launch_bounds__(256) head_proj_bwd_w(const float *dbias, const
           d[u][k] = fmaf(g[u][h], wl[h][k], d[u][k]);
           aw[h][k] = fmaf(g[u][h], v[u][k], aw[h][k]);
         }
-      const int64_t p = base + u * PPW + pw;
-      if (p < P) stc<CPL>(dx + p * C + sub * CPL, d[u]);
+      if (pos[u] >= 0) stc<CPL>(dx + pos[u] * C + sub * CPL, d[u]);
     }
   }
   // dw: lanes of the same sub hold the same channels; sum over the warp's
@@ -1199,6 +1210,18 @@ cudaError_t reduce_splits_map(const float *part, int splits, int M, int N, const
   return cudaGetLastError();
 }
 
+// Grid of a grid-stride kernel of 256-thread blocks (no dynamic shared
+// memory): the blocks that fit on all SMs at once, at most `want`; a grid
+// of one whole wave leaves no SM with a partial second round.
+template <typename K>
+unsigned one_wave(K kern, int64_t want) {
+  int per_sm = 0, dev = 0, sms = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, 0) != cudaSuccess || per_sm < 1) per_sm = 1;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    sms = 1;
+  return (unsigned)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)per_sm * sms));
+}
+
 cudaError_t head_proj_fwd(const void *x, const float *w, void *out, int R, int C, int H, int transpose, int use_bf16,
                           cudaStream_t s) {
   Prof prof("head_proj_fwd", s, 2.0 * R * (double)R * C * H, (use_bf16 ? 2.0 : 4.0) * R * (double)R * C + 4.0 * H * R * (double)R, 1);
@@ -1207,9 +1230,12 @@ cudaError_t head_proj_fwd(const void *x, const float *w, void *out, int R, int C
   if (use_bf16 && C == 128 && (((uintptr_t)x) & 15u) == 0 && (H == 4 || H == 8)) {
     constexpr int U = 4;
     const int64_t steps = (P + 2 * U - 1) / (2 * U);  // warp-steps (two positions each)
-    const unsigned blocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>((steps + 7) / 8, 152 * 3));
-    if (H == 4) launch_k(head_proj_fwd_w<4, 128, 8, U>, blocks, 256, 0, s, (const bf16 *)x, w, (bf16 *)out, R, transpose, P, P);
-    else launch_k(head_proj_fwd_w<8, 128, 8, U>, blocks, 256, 0, s, (const bf16 *)x, w, (bf16 *)out, R, transpose, P, P);
+    if (H == 4)
+      launch_k(head_proj_fwd_w<4, 128, 8, U>, one_wave(head_proj_fwd_w<4, 128, 8, U>, (steps + 7) / 8), 256, 0, s,
+               (const bf16 *)x, w, (bf16 *)out, R, transpose, P, P);
+    else
+      launch_k(head_proj_fwd_w<8, 128, 8, U>, one_wave(head_proj_fwd_w<8, 128, 8, U>, (steps + 7) / 8), 256, 0, s,
+               (const bf16 *)x, w, (bf16 *)out, R, transpose, P, P);
   } else if (use_bf16 && C % 8 == 0 && (((uintptr_t)x) & 15u) == 0 && (H == 4 || H == 8)) {
     const size_t sm = (size_t)H * C * sizeof(float);
     if (H == 4) launch_k(head_proj_fwd_v8<4, bf16>, nblk(P, 128), 128, sm, s, (const bf16 *)x, w, (bf16 *)out, R, C, transpose);
@@ -1230,9 +1256,12 @@ cudaError_t head_proj_fwd_rows(const void *x, const float *w, void *out, int64_t
   if (npos <= 0) return cudaSuccess;
   constexpr int U = 4;
   const int64_t steps = (npos + 2 * U - 1) / (2 * U);
-  const unsigned blocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>((steps + 7) / 8, 152 * 3));
-  if (H == 4) launch_k(head_proj_fwd_w<4, 128, 8, U>, blocks, 256, 0, s, (const bf16 *)x, w, (bf16 *)out, 1, 0, npos, hstride);
-  else launch_k(head_proj_fwd_w<8, 128, 8, U>, blocks, 256, 0, s, (const bf16 *)x, w, (bf16 *)out, 1, 0, npos, hstride);
+  if (H == 4)
+    launch_k(head_proj_fwd_w<4, 128, 8, U>, one_wave(head_proj_fwd_w<4, 128, 8, U>, (steps + 7) / 8), 256, 0, s,
+             (const bf16 *)x, w, (bf16 *)out, 1, 0, npos, hstride);
+  else
+    launch_k(head_proj_fwd_w<8, 128, 8, U>, one_wave(head_proj_fwd_w<8, 128, 8, U>, (steps + 7) / 8), 256, 0, s,
+             (const bf16 *)x, w, (bf16 *)out, 1, 0, npos, hstride);
   return cudaGetLastError();
 }
 
@@ -1254,13 +1283,12 @@ cudaError_t head_proj_bwd(const float *dbias, const void *x, const float *w, voi
     const int64_t P = (int64_t)R * R;
     const int64_t ppw = H == 4 ? 2 : 1;
     const int64_t steps = (P + ppw * U - 1) / (ppw * U);
-    const unsigned blocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>((steps + 7) / 8, 152 * 2));
     if (H == 4)
-      launch_k(head_proj_bwd_w<4, 128, 8, U>, blocks, 256, 0, s, dbias, (const bf16 *)x, w, (bf16 *)dx, accumulate, R,
-               transpose, dw);
+      launch_k(head_proj_bwd_w<4, 128, 8, U>, one_wave(head_proj_bwd_w<4, 128, 8, U>, (steps + 7) / 8), 256, 0, s,
+               dbias, (const bf16 *)x, w, (bf16 *)dx, accumulate, R, transpose, dw);
     else
-      launch_k(head_proj_bwd_w<8, 128, 4, U>, blocks, 256, 0, s, dbias, (const bf16 *)x, w, (bf16 *)dx, accumulate, R,
-               transpose, dw);
+      launch_k(head_proj_bwd_w<8, 128, 4, U>, one_wave(head_proj_bwd_w<8, 128, 4, U>, (steps + 7) / 8), 256, 0, s,
+               dbias, (const bf16 *)x, w, (bf16 *)dx, accumulate, R, transpose, dw);
   } else if (use_bf16 && C == 128 && (H == 4 || H == 8) && (((uintptr_t)x) & 3u) == 0 && (((uintptr_t)dx) & 3u) == 0) {
     if (H == 4)
       launch_k(head_proj_bwd_v8<4, 2>, nb, 256, 0, s, dbias, (const bf16 *)x, w, (bf16 *)dx, accumulate, R, transpose,

@@ -205,177 +205,305 @@ __global__ void __launch_bounds__(256) trimul_gate_bwd_tma(const __grid_constant
 
 // ---------------------------------------------------------------------------
 // LayerNorm of the triangle-multiplication product (Alg. 11 and 12, the
-// LayerNorm before the output projection), channel-major in, row-major out:
-// one CTA per 64 positions j of a row i, all C channels (C / 64 tiles of
-// [64 c][64 j] in, [64 j][64 c] out, each 8 KB, 128-byte swizzled).
-constexpr int LN_MAXC = 256;
+// LayerNorm before the output projection), channel-major in, row-major out,
+// and its backward.  The unit of work is a tile of 64 positions j of one row
+// i with all C channels: C / 64 channel-major tiles of [64 c][64 j] (x, dx)
+// and row-major tiles of [64 j][64 c] (y, dy), 8 KB each, 128-byte swizzled.
+//
+// Persistent CTAs of C threads walk the tiles (blockIdx.x, + gridDim.x, ...)
+// with two shared-memory buffers: the next tile's TMA loads are in flight
+// while the current one is worked, and the result is written in place of
+// the input and stored by TMA.  Thread t owns positions 8 pg .. 8 pg + 7 and
+// channels 8 cg .. 8 cg + 7 of a tile, pg = t % 8 and cg = (t / 8 + pg) mod
+// (C / 8): the eight threads of a quarter-warp then read and write eight
+// different 16-byte bank groups both in the channel-major tiles (row c,
+// chunk pg) and in the row-major ones (row j, chunk cg).  Per-position sums
+// over the channels go through shared memory (the C / 8 threads of a
+// position group sit in different warps).
 constexpr float LNC_EPS = 1e-5f;
+constexpr int LNC_RED_LD = 68;  // floats per row of the per-position partials (68 = 4 mod 32: no bank conflicts)
 
-// mean and rstd of the 64 positions of the channel-major tiles (256 threads:
-// position t % 64, channel quarter t / 64); red holds 4 x 64 floats
-__device__ __forceinline__ void cm_tile_stats(uint32_t xin, int C, float *red, float *mu, float *rs) {
-  const int t = threadIdx.x, j = t & 63, qt = t >> 6, cpq = C / 4;
-  float sum = 0.f;
-  for (int c = qt * cpq; c < (qt + 1) * cpq; ++c) sum += lds16(xin + (c >> 6) * TT_TILE + sw128(c & 63, j >> 3) + (j & 7) * 2);
-  red[qt * 64 + j] = sum;
-  __syncthreads();
-  if (t < 64) mu[t] = (red[t] + red[64 + t] + red[128 + t] + red[192 + t]) / C;
-  __syncthreads();
-  const float m = mu[j];
-  float q = 0.f;
-  for (int c = qt * cpq; c < (qt + 1) * cpq; ++c) {
-    const float d = lds16(xin + (c >> 6) * TT_TILE + sw128(c & 63, j >> 3) + (j & 7) * 2) - m;
-    q += d * d;
-  }
-  red[qt * 64 + j] = q;
-  __syncthreads();
-  if (t < 64) rs[t] = rsqrtf((red[t] + red[64 + t] + red[128 + t] + red[192 + t]) / C + LNC_EPS);
-  __syncthreads();
+template <int C>
+struct LnCm {
+  static constexpr int NCG = C / 8, NT = C / 64;
+  static constexpr int BUF = NT * TT_TILE;  // one operand of one tile
+};
+
+// per-position partials v (positions 8 pg ..) of channel group cg into red
+__device__ __forceinline__ void lnc_put(float *red, int cg, int pg, const float (&v)[8]) {
+  float4 *d = reinterpret_cast<float4 *>(red + cg * LNC_RED_LD + 8 * pg);
+  d[0] = make_float4(v[0], v[1], v[2], v[3]);
+  d[1] = make_float4(v[4], v[5], v[6], v[7]);
+}
+// sum over the channel groups of position t (t < 64)
+template <int NCG>
+__device__ __forceinline__ float lnc_sum(const float *red, int t) {
+  float s = 0.f;
+#pragma unroll
+  for (int g = 0; g < NCG; ++g) s += red[g * LNC_RED_LD + t];
+  return s;
+}
+__device__ __forceinline__ void lnc_get8(const float *a, int pg, float (&v)[8]) {
+  const float4 lo = reinterpret_cast<const float4 *>(a + 8 * pg)[0], hi = reinterpret_cast<const float4 *>(a + 8 * pg)[1];
+  v[0] = lo.x, v[1] = lo.y, v[2] = lo.z, v[3] = lo.w, v[4] = hi.x, v[5] = hi.y, v[6] = hi.z, v[7] = hi.w;
 }
 
-// grid (ceil(R / 64), R)
-__global__ void __launch_bounds__(256) ln_fwd_cm_tma(const __grid_constant__ CUtensorMap tm_x,
-                                                     const __grid_constant__ CUtensorMap tm_y, const float *gamma,
-                                                     const float *beta, int C) {
+// Issue the loads of tile `tile` (x channel-major; dy row-major when nsrc is
+// 2) into buffer base `buf`, completing on bar.
+template <int C>
+__device__ __forceinline__ void lnc_load(const CUtensorMap *tm_x, const CUtensorMap *tm_dy, int nsrc, uint32_t buf,
+                                         int tile, int ntj, uint64_t *bar) {
+  using L = LnCm<C>;
+  const int j0 = (tile % ntj) * 64, i = tile / ntj;
+  mbar_arrive_expect_tx(bar, nsrc * L::BUF);
+#pragma unroll
+  for (int c = 0; c < L::NT; ++c) {
+    tma_load_3d(buf + c * TT_TILE, tm_x, j0, i, 64 * c, bar);
+    if (nsrc == 2) tma_load_3d(buf + L::BUF + c * TT_TILE, tm_dy, 64 * c, j0, i, bar);
+  }
+}
+
+// After an abort: wait (bounded) for the loads still in flight into each
+// buffer, and for the stores still reading one.
+__device__ __forceinline__ void lnc_drain(uint64_t *full, const uint32_t (&issued)[2], const uint32_t (&used)[2]) {
+  for (int b = 0; b < 2; ++b)
+    for (uint32_t u = used[b]; u < issued[b]; ++u) mbar_drain(&full[b], u & 1u);
+  bulk_wait_read_all();
+}
+
+// Forward: y = (x - mean) / sqrt(var + eps) gamma + beta over the C channels
+// of each position; ntiles = ceil(R / 64) rows of tiles.
+template <int C>
+__global__ void __launch_bounds__(C) ln_fwd_cm_tma(const __grid_constant__ CUtensorMap tm_x,
+                                                   const __grid_constant__ CUtensorMap tm_y, const float *gamma,
+                                                   const float *beta, int ntj, int ntiles) {
+  using L = LnCm<C>;
   extern __shared__ uint8_t dsm[];
-  __shared__ __align__(8) uint64_t bar;
+  __shared__ __align__(8) uint64_t full[2];
   __shared__ volatile int s_abort;
-  __shared__ float red[256], mu[64], rs[64], gs[LN_MAXC], bs[LN_MAXC];
+  __shared__ __align__(16) float red[L::NCG * LNC_RED_LD];
+  __shared__ __align__(16) float mu[64], rs[64];
   const uint32_t base = (smem_u32(dsm) + 1023u) & ~1023u;
-  const int nt = C / 64;
-  const uint32_t xin = base, yout = base + nt * TT_TILE;
-  const int j0 = blockIdx.x * 64, i = blockIdx.y;
-  if (threadIdx.x == 0) {
-    mbar_init(&bar, 1);
+  const int t = threadIdx.x, pg = t & 7, cg = ((t >> 3) + pg) % L::NCG, cb = cg >> 3, r = cg & 7;
+  uint32_t issued[2] = {0u, 0u}, used[2] = {0u, 0u};
+  if (t == 0) {
+    mbar_init(&full[0], 1);
+    mbar_init(&full[1], 1);
     s_abort = 0;
     fence_mbar_init();
   }
   __syncthreads();
   pdl_entry();
-  if (threadIdx.x == 0) {
-    mbar_arrive_expect_tx(&bar, nt * TT_TILE);
-    for (int c = 0; c < nt; ++c) tma_load_3d(xin + c * TT_TILE, &tm_x, j0, i, 64 * c, &bar);
+  if (t == 0) {
+    for (int k = 0; k < 2; ++k) {
+      const int tile = blockIdx.x + k * gridDim.x;
+      if (tile < ntiles) lnc_load<C>(&tm_x, nullptr, 1, base + k * L::BUF, tile, ntj, &full[k]), ++issued[k];
+    }
   }
-  for (int c = threadIdx.x; c < C; c += blockDim.x) gs[c] = gamma[c], bs[c] = beta[c];
-  const bool ok = __syncthreads_and(mbar_wait(&bar, 0, &s_abort));
-  if (!ok) {
-    if (threadIdx.x == 0) mbar_drain(&bar, 0);
-    return;
+  float gm[8], bt[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) gm[k] = gamma[8 * cg + k], bt[k] = beta[8 * cg + k];
+  for (int tile = blockIdx.x, it = 0; tile < ntiles; tile += gridDim.x, ++it) {
+    const int b = it & 1;
+    const uint32_t buf = base + b * L::BUF;
+    const bool ok = __syncthreads_and(mbar_wait(&full[b], (uint32_t)(it >> 1) & 1u, &s_abort));
+    if (!ok) {
+      if (t == 0) lnc_drain(full, issued, used);
+      return;
+    }
+    ++used[b];
+    // xv[k][p]: channel 8 cg + k, position 8 pg + p
+    float xv[8][8], s[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) lds8(buf + cb * TT_TILE + sw128(8 * r + k, pg), xv[k]);
+#pragma unroll
+    for (int p = 0; p < 8; ++p) {
+      s[p] = 0.f;
+#pragma unroll
+      for (int k = 0; k < 8; ++k) s[p] += xv[k][p];
+    }
+    lnc_put(red, cg, pg, s);
+    __syncthreads();
+    if (t < 64) mu[t] = lnc_sum<L::NCG>(red, t) * (1.f / C);
+    __syncthreads();
+    float m8[8];
+    lnc_get8(mu, pg, m8);
+#pragma unroll
+    for (int p = 0; p < 8; ++p) {
+      s[p] = 0.f;
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        xv[k][p] -= m8[p];
+        s[p] += xv[k][p] * xv[k][p];
+      }
+    }
+    lnc_put(red, cg, pg, s);
+    __syncthreads();
+    if (t < 64) rs[t] = rsqrtf(lnc_sum<L::NCG>(red, t) * (1.f / C) + LNC_EPS);
+    __syncthreads();
+    float r8[8];
+    lnc_get8(rs, pg, r8);
+    // y rows j = 8 pg + p of tile cb, chunk r (the x tile's reads are done)
+#pragma unroll
+    for (int p = 0; p < 8; ++p) {
+      float o[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) o[k] = xv[k][p] * r8[p] * gm[k] + bt[k];
+      sts8(buf + cb * TT_TILE + sw128(8 * pg + p, r), o);
+    }
+    fence_proxy_async();
+    __syncthreads();
+    if (t == 0) {
+      const int j0 = (tile % ntj) * 64, i = tile / ntj;
+      for (int c = 0; c < L::NT; ++c) tma_store_3d(&tm_y, buf + c * TT_TILE, 64 * c, j0, i);
+      bulk_commit();
+      const int next = tile + 2 * gridDim.x;
+      if (next < ntiles) {
+        bulk_wait_read_all();  // the store has read the buffer
+        lnc_load<C>(&tm_x, nullptr, 1, buf, next, ntj, &full[b]);
+        ++issued[b];
+      }
+    }
   }
-  cm_tile_stats(xin, C, red, mu, rs);
-  // item (position j, 8-channel chunk q): lanes take consecutive j
-  for (int item = threadIdx.x; item < 64 * (C / 8); item += blockDim.x) {
-    const int j = item & 63, q = item >> 6;
-    float o[8];
+  if (t == 0) bulk_wait_read_all();
+}
+
+// Backward: dy row-major, x channel-major; dx channel-major (written in place
+// of x); the gamma / beta gradients of the thread's channels accumulate over
+// its tiles and meet in fp32 atomics once per CTA.
+//   dx = rs (dy gamma - mean_c(dy gamma) - xhat mean_c(dy gamma xhat))
+template <int C>
+__global__ void __launch_bounds__(C) ln_bwd_cm_tma(const __grid_constant__ CUtensorMap tm_x,
+                                                   const __grid_constant__ CUtensorMap tm_dy,
+                                                   const __grid_constant__ CUtensorMap tm_dx, const float *gamma,
+                                                   int ntj, int ntiles, float *dgamma, float *dbeta) {
+  using L = LnCm<C>;
+  extern __shared__ uint8_t dsm[];
+  __shared__ __align__(8) uint64_t full[2];
+  __shared__ volatile int s_abort;
+  __shared__ __align__(16) float red[L::NCG * LNC_RED_LD], red2[L::NCG * LNC_RED_LD];
+  __shared__ __align__(16) float mu[64], rs[64], a1[64], a2[64];
+  const uint32_t base = (smem_u32(dsm) + 1023u) & ~1023u;
+  const int t = threadIdx.x, pg = t & 7, cg = ((t >> 3) + pg) % L::NCG, cb = cg >> 3, r = cg & 7;
+  uint32_t issued[2] = {0u, 0u}, used[2] = {0u, 0u};
+  if (t == 0) {
+    mbar_init(&full[0], 1);
+    mbar_init(&full[1], 1);
+    s_abort = 0;
+    fence_mbar_init();
+  }
+  __syncthreads();
+  pdl_entry();
+  if (t == 0) {
+    for (int k = 0; k < 2; ++k) {
+      const int tile = blockIdx.x + k * gridDim.x;
+      if (tile < ntiles) lnc_load<C>(&tm_x, &tm_dy, 2, base + k * 2 * L::BUF, tile, ntj, &full[k]), ++issued[k];
+    }
+  }
+  float gm[8], dg[8], db[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) gm[k] = gamma[8 * cg + k], dg[k] = 0.f, db[k] = 0.f;
+  bool ok = true;
+  for (int tile = blockIdx.x, it = 0; tile < ntiles; tile += gridDim.x, ++it) {
+    const int b = it & 1;
+    const uint32_t xb = base + b * 2 * L::BUF, dyb = xb + L::BUF;
+    ok = __syncthreads_and(mbar_wait(&full[b], (uint32_t)(it >> 1) & 1u, &s_abort));
+    if (!ok) break;
+    ++used[b];
+    // xv[k][p]: channel 8 cg + k, position 8 pg + p; dv[p][k]: the same element of dy
+    float xv[8][8], dv[8][8], s[8], s2[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) lds8(xb + cb * TT_TILE + sw128(8 * r + k, pg), xv[k]);
+#pragma unroll
+    for (int p = 0; p < 8; ++p) lds8(dyb + cb * TT_TILE + sw128(8 * pg + p, r), dv[p]);
+#pragma unroll
+    for (int p = 0; p < 8; ++p) {
+      s[p] = 0.f;
+#pragma unroll
+      for (int k = 0; k < 8; ++k) s[p] += xv[k][p];
+    }
+    lnc_put(red, cg, pg, s);
+    __syncthreads();
+    if (t < 64) mu[t] = lnc_sum<L::NCG>(red, t) * (1.f / C);
+    __syncthreads();
+    float m8[8];
+    lnc_get8(mu, pg, m8);
+#pragma unroll
+    for (int p = 0; p < 8; ++p) {
+      s[p] = 0.f;
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        xv[k][p] -= m8[p];
+        s[p] += xv[k][p] * xv[k][p];
+      }
+    }
+    lnc_put(red, cg, pg, s);
+    __syncthreads();
+    if (t < 64) rs[t] = rsqrtf(lnc_sum<L::NCG>(red, t) * (1.f / C) + LNC_EPS);
+    __syncthreads();
+    float r8[8];
+    lnc_get8(rs, pg, r8);
+    // xhat; the gamma / beta gradients; the per-position sums of dy gamma and
+    // dy gamma xhat
+#pragma unroll
+    for (int p = 0; p < 8; ++p) {
+      s[p] = 0.f, s2[p] = 0.f;
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        xv[k][p] *= r8[p];
+        dg[k] += dv[p][k] * xv[k][p];
+        db[k] += dv[p][k];
+        dv[p][k] *= gm[k];
+        s[p] += dv[p][k];
+        s2[p] += dv[p][k] * xv[k][p];
+      }
+    }
+    lnc_put(red, cg, pg, s);
+    lnc_put(red2, cg, pg, s2);
+    __syncthreads();
+    if (t < 64) a1[t] = lnc_sum<L::NCG>(red, t) * (1.f / C), a2[t] = lnc_sum<L::NCG>(red2, t) * (1.f / C);
+    __syncthreads();
+    float c1[8], c2[8];
+    lnc_get8(a1, pg, c1);
+    lnc_get8(a2, pg, c2);
+    // dx rows c = 8 cg + k of tile cb, chunk pg (in place of x, read above)
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
-      const int c = q * 8 + k;
-      const float x = lds16(xin + (c >> 6) * TT_TILE + sw128(c & 63, j >> 3) + (j & 7) * 2);
-      o[k] = (x - mu[j]) * rs[j] * gs[c] + bs[c];
+      float o[8];
+#pragma unroll
+      for (int p = 0; p < 8; ++p) o[p] = r8[p] * (dv[p][k] - c1[p] - xv[k][p] * c2[p]);
+      sts8(xb + cb * TT_TILE + sw128(8 * r + k, pg), o);
     }
-    sts8(yout + (q >> 3) * TT_TILE + sw128(j, q & 7), o);
-  }
-  fence_proxy_async();
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    for (int c = 0; c < nt; ++c) tma_store_3d(&tm_y, yout + c * TT_TILE, 64 * c, j0, i);
-    bulk_commit();
-    bulk_wait_read_all();
-  }
-}
-
-// Backward: dy row-major tiles [64 j][64 c], x channel-major; dx channel-major
-// (written over the x tiles), gamma / beta gradients by fp32 atomics.
-__global__ void __launch_bounds__(256) ln_bwd_cm_tma(const __grid_constant__ CUtensorMap tm_x,
-                                                     const __grid_constant__ CUtensorMap tm_dy,
-                                                     const __grid_constant__ CUtensorMap tm_dx, const float *gamma,
-                                                     int C, float *dgamma, float *dbeta) {
-  extern __shared__ uint8_t dsm[];
-  __shared__ __align__(8) uint64_t bar;
-  __shared__ volatile int s_abort;
-  __shared__ float red[256], red2[512], mu[64], rs[64], a1[64], a2[64], gs[LN_MAXC];
-  const uint32_t base = (smem_u32(dsm) + 1023u) & ~1023u;
-  const int nt = C / 64;
-  const uint32_t xin = base, dyin = base + nt * TT_TILE;
-  const int j0 = blockIdx.x * 64, i = blockIdx.y;
-  const int t = threadIdx.x, j = t & 63, qt = t >> 6, cpq = C / 4;
-  if (t == 0) {
-    mbar_init(&bar, 1);
-    s_abort = 0;
-    fence_mbar_init();
-  }
-  __syncthreads();
-  pdl_entry();
-  if (t == 0) {
-    mbar_arrive_expect_tx(&bar, 2 * nt * TT_TILE);
-    for (int c = 0; c < nt; ++c) {
-      tma_load_3d(xin + c * TT_TILE, &tm_x, j0, i, 64 * c, &bar);
-      tma_load_3d(dyin + c * TT_TILE, &tm_dy, 64 * c, j0, i, &bar);
+    fence_proxy_async();
+    __syncthreads();
+    if (t == 0) {
+      const int j0 = (tile % ntj) * 64, i = tile / ntj;
+      for (int c = 0; c < L::NT; ++c) tma_store_3d(&tm_dx, xb + c * TT_TILE, j0, i, 64 * c);
+      bulk_commit();
+      const int next = tile + 2 * gridDim.x;
+      if (next < ntiles) {
+        bulk_wait_read_all();  // the store has read the buffer
+        lnc_load<C>(&tm_x, &tm_dy, 2, xb, next, ntj, &full[b]);
+        ++issued[b];
+      }
     }
   }
-  for (int c = t; c < C; c += blockDim.x) gs[c] = gamma[c];
-  const bool ok = __syncthreads_and(mbar_wait(&bar, 0, &s_abort));
   if (!ok) {
-    if (t == 0) mbar_drain(&bar, 0);
+    if (t == 0) lnc_drain(full, issued, used);
     return;
   }
-  cm_tile_stats(xin, C, red, mu, rs);
-  auto xat = [&](int c, int jj) { return lds16(xin + (c >> 6) * TT_TILE + sw128(c & 63, jj >> 3) + (jj & 7) * 2); };
-  auto dyat = [&](int c, int jj) {
-    return lds16(dyin + (c >> 6) * TT_TILE + sw128(jj, (c & 63) >> 3) + (c & 7) * 2);
-  };
-  // a1 = mean_c(dy gamma), a2 = mean_c(dy gamma xhat) per position
-  {
-    const float m = mu[j], r = rs[j];
-    float s1 = 0.f, s2 = 0.f;
-    for (int c = qt * cpq; c < (qt + 1) * cpq; ++c) {
-      const float gd = dyat(c, j) * gs[c];
-      s1 += gd;
-      s2 += gd * (xat(c, j) - m) * r;
-    }
-    red[qt * 64 + j] = s1;
-    __syncthreads();
-    if (t < 64) a1[t] = (red[t] + red[64 + t] + red[128 + t] + red[192 + t]) / C;
-    __syncthreads();
-    red[qt * 64 + j] = s2;
-    __syncthreads();
-    if (t < 64) a2[t] = (red[t] + red[64 + t] + red[128 + t] + red[192 + t]) / C;
-    __syncthreads();
-  }
-  // gamma / beta gradients: 256 / C threads per channel, each over a slice of
-  // the tile's positions, combined in shared memory (red2: 2 x 256 floats)
-  {
-    const int tpc = 256 / C, c = t % C, part = t / C, per = 64 / tpc;
-    float sg = 0.f, sb = 0.f;
-    for (int jj = part * per; jj < (part + 1) * per; ++jj) {
-      const float d = dyat(c, jj);
-      sg += d * (xat(c, jj) - mu[jj]) * rs[jj];
-      sb += d;
-    }
-    red2[t] = sg;
-    red2[256 + t] = sb;
-    __syncthreads();
-    if (t < C) {
-      float g = 0.f, b = 0.f;
-      for (int k = 0; k < tpc; ++k) g += red2[k * C + t], b += red2[256 + k * C + t];
-      atomicAdd(dgamma + t, g);
-      atomicAdd(dbeta + t, b);
-    }
-  }
-  __syncthreads();  // every read of x is done before dx overwrites it
-  for (int e = t; e < 64 * C; e += blockDim.x) {
-    const int jj = e & 63, c = e >> 6;
-    const uint32_t a = xin + (c >> 6) * TT_TILE + sw128(c & 63, jj >> 3) + (jj & 7) * 2;
-    const float xh = (lds16(a) - mu[jj]) * rs[jj];
-    sts16(a, rs[jj] * (dyat(c, jj) * gs[c] - a1[jj] - xh * a2[jj]));
-  }
-  fence_proxy_async();
+  // gamma / beta gradients: the eight threads of a channel group (pg = 0..7)
+  // meet in shared memory (red, red2 reused: 8 x C floats each fit)
   __syncthreads();
-  if (t == 0) {
-    for (int c = 0; c < nt; ++c) tma_store_3d(&tm_dx, xin + c * TT_TILE, j0, i, 64 * c);
-    bulk_commit();
-    bulk_wait_read_all();
-  }
+#pragma unroll
+  for (int k = 0; k < 8; ++k) red[pg * C + 8 * cg + k] = dg[k], red2[pg * C + 8 * cg + k] = db[k];
+  __syncthreads();
+  float g = 0.f, bsum = 0.f;
+#pragma unroll
+  for (int q = 0; q < 8; ++q) g += red[q * C + t], bsum += red2[q * C + t];
+  atomicAdd(dgamma + t, g);
+  atomicAdd(dbeta + t, bsum);
+  if (t == 0) bulk_wait_read_all();
 }
 
 // row-major [R][R][C] map, boxes of 64 channels x 64 positions j
@@ -473,18 +601,61 @@ bool ln_cm_tma_supported(const void *x, int64_t pitch, const void *y, int R, int
   return R > 0 && (C == 64 || C == 128 || C == 256) && pitch % 8 == 0 && a16(x) && a16(y);
 }
 
+namespace {
+// Persistent grid of the channel-major LayerNorm kernels: as many CTAs as
+// fit on the SMs at once (occupancy of the kernel at its shared memory),
+// at most one per tile.
+// (BWD, C) tell the kernels apart: their function types are alike
+template <int BWD, int C, typename K>
+cudaError_t lnc_launch_cfg(K kern, int smem, int threads, int ntiles, int *grid) {
+  static int per_sm = 0, sms = 0;
+  if (per_sm == 0) {
+    int dev = 0;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem);
+    if (e == cudaSuccess) e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  }
+  *grid = std::max(1, std::min(ntiles, per_sm * sms));
+  return cudaSuccess;
+}
+
+template <int C>
+cudaError_t ln_fwd_cm_go(const CUtensorMap &tx, const CUtensorMap &ty, const float *gamma, const float *beta, int R,
+                         int rows, cudaStream_t s) {
+  const int ntj = (R + 63) / 64, ntiles = ntj * rows;
+  const int smem = 2 * LnCm<C>::BUF + 1024;
+  int grid = 0;
+  const cudaError_t e = lnc_launch_cfg<0, C>(ln_fwd_cm_tma<C>, smem, C, ntiles, &grid);
+  if (e != cudaSuccess) return e;
+  return launch_k(ln_fwd_cm_tma<C>, grid, C, smem, s, tx, ty, gamma, beta, ntj, ntiles);
+}
+cudaError_t ln_fwd_cm_dispatch(const CUtensorMap &tx, const CUtensorMap &ty, const float *gamma, const float *beta,
+                               int R, int rows, int C, cudaStream_t s) {
+  if (C == 64) return ln_fwd_cm_go<64>(tx, ty, gamma, beta, R, rows, s);
+  if (C == 128) return ln_fwd_cm_go<128>(tx, ty, gamma, beta, R, rows, s);
+  if (C == 256) return ln_fwd_cm_go<256>(tx, ty, gamma, beta, R, rows, s);
+  return cudaErrorNotSupported;
+}
+template <int C>
+cudaError_t ln_bwd_cm_go(const CUtensorMap &tx, const CUtensorMap &tdy, const CUtensorMap &tdx, const float *gamma,
+                         int R, float *dgamma, float *dbeta, cudaStream_t s) {
+  const int ntj = (R + 63) / 64, ntiles = ntj * R;
+  const int smem = 4 * LnCm<C>::BUF + 1024;
+  int grid = 0;
+  const cudaError_t e = lnc_launch_cfg<1, C>(ln_bwd_cm_tma<C>, smem, C, ntiles, &grid);
+  if (e != cudaSuccess) return e;
+  return launch_k(ln_bwd_cm_tma<C>, grid, C, smem, s, tx, tdy, tdx, gamma, ntj, ntiles, dgamma, dbeta);
+}
+}  // namespace
+
 cudaError_t ln_fwd_cm_tma_launch(const void *x, int64_t pitch, const float *gamma, const float *beta, void *y, int R,
                                  int C, cudaStream_t s) {
   CUtensorMap tx, ty;
   if (!map_cm(&tx, x, pitch, R, C) || !map_rows(&ty, y, R, C)) return cudaErrorNotSupported;
-  const int smem = 2 * (C / 64) * TT_TILE + 1024;
-  static int attr = 0;
-  if (attr < smem) {
-    cudaError_t e = cudaFuncSetAttribute(ln_fwd_cm_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e != cudaSuccess) return e;
-    attr = smem;
-  }
-  return launch_k(ln_fwd_cm_tma, dim3((R + 63) / 64, R), 256, smem, s, tx, ty, gamma, beta, C);
+  return ln_fwd_cm_dispatch(tx, ty, gamma, beta, R, R, C, s);
 }
 
 cudaError_t ln_fwd_cm_rows(const void *x, int64_t pitch, int64_t cstride, const float *gamma, const float *beta,
@@ -494,14 +665,7 @@ cudaError_t ln_fwd_cm_rows(const void *x, int64_t pitch, int64_t cstride, const 
   Prof p("ln_fwd_cm", s, 0, 4.0 * rows * (double)R * C);
   CUtensorMap tx, ty;
   if (!map_cm(&tx, x, pitch, R, C, rows, cstride) || !map_rows(&ty, y, R, C, rows)) return cudaErrorNotSupported;
-  const int smem = 2 * (C / 64) * TT_TILE + 1024;
-  static int attr = 0;
-  if (attr < smem) {
-    cudaError_t e = cudaFuncSetAttribute(ln_fwd_cm_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e != cudaSuccess) return e;
-    attr = smem;
-  }
-  return launch_k(ln_fwd_cm_tma, dim3((R + 63) / 64, rows), 256, smem, s, tx, ty, gamma, beta, C);
+  return ln_fwd_cm_dispatch(tx, ty, gamma, beta, R, rows, C, s);
 }
 
 cudaError_t ln_bwd_cm_tma_launch(const void *dy, const void *x, int64_t pitch, const float *gamma, void *dx, int R,
@@ -509,14 +673,10 @@ cudaError_t ln_bwd_cm_tma_launch(const void *dy, const void *x, int64_t pitch, c
   CUtensorMap tx, tdy, tdx;
   if (!map_cm(&tx, x, pitch, R, C) || !map_rows(&tdy, dy, R, C) || !map_cm(&tdx, dx, pitch, R, C))
     return cudaErrorNotSupported;
-  const int smem = 2 * (C / 64) * TT_TILE + 1024;
-  static int attr = 0;
-  if (attr < smem) {
-    cudaError_t e = cudaFuncSetAttribute(ln_bwd_cm_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e != cudaSuccess) return e;
-    attr = smem;
-  }
-  return launch_k(ln_bwd_cm_tma, dim3((R + 63) / 64, R), 256, smem, s, tx, tdy, tdx, gamma, C, dgamma, dbeta);
+  if (C == 64) return ln_bwd_cm_go<64>(tx, tdy, tdx, gamma, R, dgamma, dbeta, s);
+  if (C == 128) return ln_bwd_cm_go<128>(tx, tdy, tdx, gamma, R, dgamma, dbeta, s);
+  if (C == 256) return ln_bwd_cm_go<256>(tx, tdy, tdx, gamma, R, dgamma, dbeta, s);
+  return cudaErrorNotSupported;
 }
 
 namespace {

@@ -109,6 +109,7 @@ MEASURED = {
         "msa_trans.ln.gamma": 0.068,  # 0.0615
         "msa_trans.w1": 0.061,  # 0.0549
         "pair_trans.b1": 0.071,  # 0.0641
+        "pair_trans.ln.beta": 0.056,  # 0.0504
         "pair_trans.ln.gamma": 0.072,  # 0.0649
         "pair_trans.w1": 0.073,  # 0.0662
     },
