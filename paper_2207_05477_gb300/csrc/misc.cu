@@ -367,7 +367,7 @@ __global__ void __launch_bounds__(256, H == 4 ? 3 : 2) head_proj_fwd_w(const bf1
 // dbias index q (the input position is the transposed one with transpose),
 // so the dbias loads are coalesced.
 template <int H, int C, int CPL, int U>
-__global__ void __launch_bounds__(256) head_proj_bwd_w(const float *dbias, const bf16 *x, const float *w, bf16 *dx,
+__global__ void __launch_bounds__(256, 2) head_proj_bwd_w(const float *dbias, const bf16 *x, const float *w, bf16 *dx,
                                                        int accumulate, int R, int transpose, float *dw) {
   pdl_entry();
   constexpr int TPR = C / CPL, PPW = 32 / TPR;
@@ -1279,7 +1279,7 @@ cudaError_t head_proj_bwd(const float *dbias, const void *x, const float *w, voi
   if (use_bf16 && C == 128 && (H == 4 || H == 8) && (((uintptr_t)x) & 15u) == 0 && (((uintptr_t)dx) & 15u) == 0) {
     // H = 4: eight channels per lane (16 positions' worth of w and dw in
     // registers); H = 8: four channels per lane
-    constexpr int U = 4;
+    constexpr int U = 2;
     const int64_t P = (int64_t)R * R;
     const int64_t ppw = H == 4 ? 2 : 1;
     const int64_t steps = (P + ppw * U - 1) / (ppw * U);
@@ -1412,8 +1412,8 @@ cudaError_t row_scale(const void *x, const float *scale, void *y, int64_t M, int
   Prof prof("row_scale", s, 0, (use_bf16 ? 4.0 : 8.0) * M * (double)C, 1);
   if (use_bf16 && C % 8 == 0 && C <= 256 && 256 % (C / 8) == 0 && (((uintptr_t)x | (uintptr_t)y) & 15u) == 0) {
     const int64_t n = M * (C / 8);
-    const unsigned blocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 511) / 512, 152 * 8));
-    launch_k(row_scale_v8, blocks, 256, 0, s, (const bf16 *)x, scale, (bf16 *)y, M, C, dsum);
+    launch_k(row_scale_v8, one_wave(row_scale_v8, (n + 511) / 512), 256, 0, s, (const bf16 *)x, scale, (bf16 *)y, M, C,
+             dsum);
     return cudaGetLastError();
   } else if (use_bf16) launch_k(row_scale_k<bf16>, nblk(M * C), 256, 0, s, (const bf16 *)x, scale, (bf16 *)y, M, C);
   else launch_k(row_scale_k<float>, nblk(M * C), 256, 0, s, (const float *)x, scale, (float *)y, M, C);
