@@ -937,39 +937,62 @@ __device__ __forceinline__ void chunk_colsum_flush(float (&cs)[8], int C, float 
   }
 }
 
+__device__ __forceinline__ void unpack8(const uint4 &w, float (&v)[8]) {
+  const uint32_t q[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+  for (int k = 0; k < 4; ++k) v[2 * k] = __uint_as_float(q[k] << 16), v[2 * k + 1] = __uint_as_float(q[k] & 0xffff0000u);
+}
+
+// Grid-stride kernels over (position, 8-channel chunk) items with C / 8
+// chunks per position: the grid stride is a multiple of C / 8 (which divides
+// 256), so a thread keeps its eight channels c .. c + 7 (the ones whose
+// column sums it accumulates) and steps over positions.
+struct ChunkWalk {
+  int64_t p0, pstep;
+  int c;
+  __device__ __forceinline__ explicit ChunkWalk(int C) {
+    const int cq = C / 8;
+    const int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    c = (int)(i0 % cq) * 8;
+    p0 = i0 / cq;
+    pstep = (int64_t)gridDim.x * blockDim.x / cq;
+  }
+};
+
+// Output-gate backward: dy = dz g, dgpre = dz y g (1 - g), four positions'
+// 16-byte loads in flight per thread (kept packed).
 __global__ void __launch_bounds__(256) gate_out_bwd_v8(const bf16 *dz, const bf16 *g, int64_t g_ld, const bf16 *y,
                                                        bf16 *dy, bf16 *dgpre, int64_t dg_ld, int64_t P, int C,
                                                        float *dsum) {
   pdl_entry();
+  constexpr int U = 4;
   __shared__ float red[8 * 256];
   float cs[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-  const int cq = C / 8;
-  const int64_t n = P * cq;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += 2 * stride) {
-    float d[2][8], gv[2][8], yv[2][8];
+  const ChunkWalk w(C);
+  const int c = w.c;
+  for (int64_t p0 = w.p0; p0 < P; p0 += U * w.pstep) {
+    uint4 dr[U], gr[U], yr[U];
 #pragma unroll
-    for (int u = 0; u < 2; ++u) {
-      const int64_t e = i + u * stride;
-      if (e < n) {
-        const int64_t p = e / cq;
-        const int c = (int)(e - p * cq) * 8;
-        ld8(dz + p * C + c, d[u]);
-        ld8(g + p * g_ld + c, gv[u]);
-        ld8(y + p * C + c, yv[u]);
+    for (int u = 0; u < U; ++u) {
+      const int64_t p = p0 + u * w.pstep;
+      if (p < P) {
+        dr[u] = *reinterpret_cast<const uint4 *>(dz + p * C + c);
+        gr[u] = *reinterpret_cast<const uint4 *>(g + p * g_ld + c);
+        yr[u] = *reinterpret_cast<const uint4 *>(y + p * C + c);
       }
     }
 #pragma unroll
-    for (int u = 0; u < 2; ++u) {
-      const int64_t e = i + u * stride;
-      if (e < n) {
-        const int64_t p = e / cq;
-        const int c = (int)(e - p * cq) * 8;
-        float a[8], b[8];
+    for (int u = 0; u < U; ++u) {
+      const int64_t p = p0 + u * w.pstep;
+      if (p < P) {
+        float d[8], gv[8], yv[8], a[8], b[8];
+        unpack8(dr[u], d);
+        unpack8(gr[u], gv);
+        unpack8(yr[u], yv);
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
-          a[k] = d[u][k] * gv[u][k];
-          b[k] = d[u][k] * yv[u][k] * gv[u][k] * (1.f - gv[u][k]);
+          a[k] = d[k] * gv[k];
+          b[k] = d[k] * yv[k] * gv[k] * (1.f - gv[k]);
         }
         st8(dy + p * C + c, a);
         st8(dgpre + p * dg_ld + c, b);
@@ -1104,29 +1127,28 @@ __global__ void __launch_bounds__(256) opm_inv_norm_k(const float *mask, float *
 __global__ void __launch_bounds__(256) row_scale_v8(const bf16 *x, const float *scale, bf16 *y, int64_t M, int C,
                                                     float *dsum) {
   pdl_entry();
+  constexpr int U = 4;
   __shared__ float red[8 * 256];
   float cs[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-  const int cq = C / 8;
-  const int64_t n = M * cq;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += 2 * stride) {
-    float v[2][8];
-    float sc[2];
+  const ChunkWalk w(C);
+  const int c = w.c;
+  for (int64_t r0 = w.p0; r0 < M; r0 += U * w.pstep) {
+    uint4 xr[U];
+    float sc[U];
 #pragma unroll
-    for (int u = 0; u < 2; ++u) {
-      const int64_t e = i + u * stride;
-      if (e < n) {
-        ld8(x + e * 8, v[u]);
-        sc[u] = scale[e / cq];
-      }
+    for (int u = 0; u < U; ++u) {
+      const int64_t r = r0 + u * w.pstep;
+      if (r < M) xr[u] = *reinterpret_cast<const uint4 *>(x + r * C + c), sc[u] = scale[r];
     }
 #pragma unroll
-    for (int u = 0; u < 2; ++u) {
-      const int64_t e = i + u * stride;
-      if (e < n) {
+    for (int u = 0; u < U; ++u) {
+      const int64_t r = r0 + u * w.pstep;
+      if (r < M) {
+        float v[8];
+        unpack8(xr[u], v);
 #pragma unroll
-        for (int k = 0; k < 8; ++k) v[u][k] *= sc[u], cs[k] += v[u][k];
-        st8(y + e * 8, v[u]);
+        for (int k = 0; k < 8; ++k) v[k] *= sc[u], cs[k] += v[k];
+        st8(y + r * C + c, v);
       }
     }
   }
@@ -1365,9 +1387,8 @@ cudaError_t gate_out_bwd(const void *dz, const void *g, int64_t g_ld, const void
   if (use_bf16 && C % 8 == 0 && C <= 256 && 256 % (C / 8) == 0 && g_ld % 8 == 0 && dg_ld % 8 == 0 && a16(dz) &&
       a16(g) && a16(y) && a16(dy) && a16(dgpre)) {
     const int64_t n = P * (C / 8);
-    const unsigned blocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 511) / 512, 152 * 8));
-    launch_k(gate_out_bwd_v8, blocks, 256, 0, s, (const bf16 *)dz, (const bf16 *)g, g_ld, (const bf16 *)y, (bf16 *)dy,
-             (bf16 *)dgpre, dg_ld, P, C, dsum);
+    launch_k(gate_out_bwd_v8, one_wave(gate_out_bwd_v8, (n + 1023) / 1024), 256, 0, s, (const bf16 *)dz,
+             (const bf16 *)g, g_ld, (const bf16 *)y, (bf16 *)dy, (bf16 *)dgpre, dg_ld, P, C, dsum);
     return cudaGetLastError();
   } else if (use_bf16)
     launch_k(gate_out_bwd_k<bf16>, nblk(P * C), 256, 0, s, (const bf16 *)dz, (const bf16 *)g, g_ld, (const bf16 *)y,
@@ -1412,8 +1433,8 @@ cudaError_t row_scale(const void *x, const float *scale, void *y, int64_t M, int
   Prof prof("row_scale", s, 0, (use_bf16 ? 4.0 : 8.0) * M * (double)C, 1);
   if (use_bf16 && C % 8 == 0 && C <= 256 && 256 % (C / 8) == 0 && (((uintptr_t)x | (uintptr_t)y) & 15u) == 0) {
     const int64_t n = M * (C / 8);
-    launch_k(row_scale_v8, one_wave(row_scale_v8, (n + 511) / 512), 256, 0, s, (const bf16 *)x, scale, (bf16 *)y, M, C,
-             dsum);
+    launch_k(row_scale_v8, one_wave(row_scale_v8, (n + 1023) / 1024), 256, 0, s, (const bf16 *)x, scale, (bf16 *)y, M,
+             C, dsum);
     return cudaGetLastError();
   } else if (use_bf16) launch_k(row_scale_k<bf16>, nblk(M * C), 256, 0, s, (const bf16 *)x, scale, (bf16 *)y, M, C);
   else launch_k(row_scale_k<float>, nblk(M * C), 256, 0, s, (const float *)x, scale, (float *)y, M, C);
