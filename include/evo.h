@@ -308,13 +308,14 @@ int evo_adam_step(const evo_adam *h, size_t n, float *params, const float *grad,
 int evo_get_error(evo_stream_t stream);
 
 /* Units of the library with their own device error word. */
-enum { EVO_UNIT_GEMM = 0, EVO_UNIT_ATTENTION = 1, EVO_UNIT_TRIMUL = 2 };
+enum { EVO_UNIT_GEMM = 0, EVO_UNIT_ATTENTION = 1, EVO_UNIT_TRIMUL = 2, EVO_UNIT_MLP = 3 };
 
 /* Diagnostics for failure detection: launches one CTA of the given unit
  * (EVO_UNIT_GEMM: the tcgen05 GEMM; EVO_UNIT_ATTENTION: the tcgen05
  * attention kernels; EVO_UNIT_TRIMUL: the TMA triangle-multiplication and
- * channel-major LayerNorm kernels) whose bounded mbarrier wait -- the same
- * wait code those kernels use -- is never satisfied and gives up after
+ * channel-major LayerNorm kernels; EVO_UNIT_MLP: the fused transition MLP)
+ * whose bounded mbarrier wait -- the same wait code those kernels use -- is
+ * never satisfied and gives up after
  * limit_ns (at most 5 s), recording EVO_ERR_TIMEOUT in that unit's device
  * error word exactly as a timed-out wait inside one of its kernels would.
  * The GPU context stays usable; evo_get_error then returns EVO_ERR_TIMEOUT.

@@ -210,11 +210,12 @@ int evo_stack_fwd(const evo_dims *d, int n_blocks, int batch, const int32_t *n_s
 
 int evo_get_error(evo_stream_t stream) {
   if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) return EVO_ERR_CUDA;
-  int h = 0, h2 = 0, h3 = 0;
+  int h = 0, h2 = 0, h3 = 0, h4 = 0;
   if (error_word_read_clear(&h) != cudaSuccess) return EVO_ERR_CUDA;
   if (attn_tc_error_read_clear(&h2) != cudaSuccess) return EVO_ERR_CUDA;
   if (trimul_tc_error_read_clear(&h3) != cudaSuccess) return EVO_ERR_CUDA;
-  return h != EVO_OK ? h : h2 != EVO_OK ? h2 : h3;
+  if (mlp_tc_error_read_clear(&h4) != cudaSuccess) return EVO_ERR_CUDA;
+  return h != EVO_OK ? h : h2 != EVO_OK ? h2 : h3 != EVO_OK ? h3 : h4;
 }
 
 int evo_debug_wait_timeout(int unit, long long limit_ns, evo_stream_t stream) {
@@ -224,6 +225,7 @@ int evo_debug_wait_timeout(int unit, long long limit_ns, evo_stream_t stream) {
     case EVO_UNIT_GEMM: e = debug_wait(limit_ns, (cudaStream_t)stream); break;
     case EVO_UNIT_ATTENTION: e = attn_tc_debug_wait(limit_ns, (cudaStream_t)stream); break;
     case EVO_UNIT_TRIMUL: e = trimul_tc_debug_wait(limit_ns, (cudaStream_t)stream); break;
+    case EVO_UNIT_MLP: e = mlp_tc_debug_wait(limit_ns, (cudaStream_t)stream); break;
     default: return EVO_ERR_INVALID_ARG;
   }
   return e == cudaSuccess ? EVO_OK : EVO_ERR_CUDA;

@@ -378,12 +378,15 @@ struct Drv {
   Plan pl;
   float *dparams = nullptr;
   const evo_dropout *drop = nullptr;  // training-mode dropout scales (null: evaluation mode)
+  // the transitions' hidden layers are written out only for the backward
+  // (its recompute keeps them for dW2 and the ReLU mask)
+  bool keep_hidden = false;
   cudaError_t err = cudaSuccess;
 
   Drv(const evo_dims &d_, const float *p32_, const bf16 *p16_, void *ws_, int mode, cudaStream_t s_,
       bool pair_only = false)
       : d(d_), k(d_, pair_only), bf(d_.act_dtype == EVO_BF16), ts(bf ? 2 : 4), s(s_), p32(p32_), p16(p16_),
-        ws((char *)ws_) {
+        ws((char *)ws_), keep_hidden(mode == EVO_MODE_BWD) {
     std::vector<PEntry> t;
     build_param_table(d, t, pair_only);
     for (auto &e : t) off[e.name] = e.offset;
@@ -755,6 +758,17 @@ struct Drv {
   void transition_fwd(const std::string &pre, const void *x, void *xn, void *h, void *out, int64_t M, int64_t C) {
     ln(x, pre + ".ln", xn, M, (int)C);
     const int64_t nC = k.n * C;
+    // Without the backward the hidden layer is needed by no one: both
+    // products run in one kernel with the hidden layer kept on the SM.  The
+    // backward's recompute keeps h (dW2, the ReLU mask), and there the two
+    // GEMMs, which write h as their intermediate anyway, are faster.
+    if (bf && !keep_hidden &&
+        mlp_fused_supported(M, (int)C, (int)nC, xn, W(pre + ".w1"), P(pre + ".b1"), W(pre + ".w2"), P(pre + ".b2"), x,
+                            out)) {
+      ck(mlp_fused_tc(xn, W(pre + ".w1"), P(pre + ".b1"), W(pre + ".w2"), P(pre + ".b2"), x, out, M, (int)C, (int)nC,
+                      s));
+      return;
+    }
     GemmOp g = mk(M, nC, C, xn, C, 0, W(pre + ".w1"), C, 0, h, nC);
     g.e.bias = P(pre + ".b1"), g.e.act = ACT_RELU;
     gemm(g);

@@ -204,6 +204,17 @@ cudaError_t ln_bwd_cm_tma_launch(const void *dy, const void *x, int64_t pitch, c
                                  int C, float *dgamma, float *dbeta, cudaStream_t s);
 // Reads and clears the error word of the TMA gate kernels; synchronous.
 cudaError_t trimul_tc_error_read_clear(int *out);
+
+// Fused transition MLP (tcgen05, BF16): out = res + b2 + relu(xn W1^T + b1) W2^T
+// over M rows of C channels (C = 128 or 256), the hidden layer (width N1, a
+// multiple of 128) kept on the SM.  W1 is [N1][C], W2 [C][N1] (row-major,
+// BF16); all pointers 16-byte aligned.
+bool mlp_fused_supported(int64_t M, int C, int N1, const void *xn, const void *w1, const float *b1, const void *w2,
+                         const float *b2, const void *res, const void *out);
+cudaError_t mlp_fused_tc(const void *xn, const void *w1, const float *b1, const void *w2, const float *b2,
+                         const void *res, void *out, int64_t M, int C, int N1, cudaStream_t s);
+cudaError_t mlp_tc_error_read_clear(int *out);
+cudaError_t mlp_tc_debug_wait(int64_t limit_ns, cudaStream_t s);
 cudaError_t trimul_tc_debug_wait(int64_t limit_ns, cudaStream_t s);
 cudaError_t trimul_gate_bwd(const void *dA, const void *dB, int64_t pitch, const void *abg, int64_t ld,
                             const float *mask, void *dabg, int R, int cm, int incoming, int use_bf16,

@@ -21,7 +21,7 @@ EVO_ERR_WORKSPACE, EVO_ERR_CUDA, EVO_ERR_TIMEOUT = -4, -5, -6
 EVO_F32, EVO_BF16 = 0, 1
 EVO_COL_ATTENTION, EVO_COL_GLOBAL = 0, 1
 EVO_MODE_FWD, EVO_MODE_BWD, EVO_MODE_INFER = 0, 1, 2
-EVO_UNIT_GEMM, EVO_UNIT_ATTENTION, EVO_UNIT_TRIMUL = 0, 1, 2
+EVO_UNIT_GEMM, EVO_UNIT_ATTENTION, EVO_UNIT_TRIMUL, EVO_UNIT_MLP = 0, 1, 2, 3
 
 
 class EvoError(RuntimeError):
@@ -328,7 +328,7 @@ def probe_ex2(variant, blocks, iters, sink, stream=None):
 
 
 def debug_wait_timeout(limit_ns, unit=None, stream=None):
-    """One CTA of `unit` (EVO_UNIT_GEMM / _ATTENTION / _TRIMUL) whose bounded wait runs out after limit_ns."""
+    """One CTA of `unit` (EVO_UNIT_GEMM / _ATTENTION / _TRIMUL / _MLP) whose bounded wait runs out after limit_ns."""
     u = EVO_UNIT_GEMM if unit is None else unit
     _check(lib().evo_debug_wait_timeout(int(u), int(limit_ns), _stream(stream)), "evo_debug_wait_timeout")
 

@@ -10,7 +10,7 @@ from paper_2207_05477_gb300 import evo, synth
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("unit", [evo.EVO_UNIT_GEMM, evo.EVO_UNIT_ATTENTION, evo.EVO_UNIT_TRIMUL])
+@pytest.mark.parametrize("unit", [evo.EVO_UNIT_GEMM, evo.EVO_UNIT_ATTENTION, evo.EVO_UNIT_TRIMUL, evo.EVO_UNIT_MLP])
 def test_bounded_wait_reports_timeout_and_context_survives(built_lib, unit):
     """Each unit's own bounded wait (GEMM, attention, triangle multiplication)
     runs out, its error word reports the timeout, and a block runs afterwards."""
