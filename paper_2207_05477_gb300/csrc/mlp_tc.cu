@@ -7,10 +7,10 @@
 // for a tile of 128 rows at a time, with the N1-wide hidden layer kept on the
 // SM: it is produced 128 columns (a chunk) at a time into tensor memory by
 // the first product, turned into BF16 (bias, ReLU) by the epilogue warps and
-// written into shared memory in the 128-byte-swizzled K-major layout the
-// tensor core reads, and consumed from there as the A operand of the second
-// product, whose FP32 accumulator O (128 x C) stays in tensor memory across
-// the chunks.  The hidden layer never goes to global memory: the kernel serves
+// written back into the same tensor memory (two BF16 per 32-bit column), and
+// consumed there as the A operand of the second product, whose FP32
+// accumulator O (128 x C) stays in tensor memory across the chunks.  Shared
+// memory holds only the tile's xn rows and a deep ring of weight slices.  The hidden layer never goes to global memory: the kernel serves
 // the paths that do not keep it (the backward's recompute keeps it for dW2
 // and the ReLU mask and runs the two products as separate GEMMs).
 //
@@ -21,11 +21,14 @@
 //   warp 1 lane 0: MMA issuer: GEMM1 of chunk j into hidden buffer j % 2,
 //                  then GEMM2 of chunk j - 1, so that the epilogue of a
 //                  chunk overlaps the next chunk's first product;
-//   warps 2-17:    epilogue: hidden chunks (bias, ReLU, BF16 into shared
-//                  memory), then the tile's output (bias, residual, BF16);
+//   warps 2-17:    epilogue: hidden chunks (bias, ReLU, BF16 back into
+//                  tensor memory), then the tile's output (bias, residual,
+//                  BF16);
 //                  each warp's global operands (biases, residual rows) are
 //                  requested before it waits for the accumulator they meet.
-// Tensor memory: O in columns [0, C), the two hidden buffers at 256 and 384.
+// Tensor memory: O in columns [0, C), the two hidden buffers at 256 and 384
+// (each 128 FP32 columns; the warp that reads hidden columns 32 s .. 32 s + 31
+// writes their BF16 pairs into the first 16 of them).
 // Every mbarrier wait is bounded; a wait that runs out sets this unit's error
 // word and the CTA drains its copies and MMAs, frees its tensor memory and
 // returns.
@@ -41,15 +44,14 @@ constexpr int SLICE = 128 * 64 * 2;      // one [128 rows x 64 k] BF16 operand s
 constexpr int MLP_EPI_WARPS = 16;        // four per TMEM lane quarter
 constexpr int MLP_THREADS = 32 * (2 + MLP_EPI_WARPS);
 constexpr int MLP_SMEM_LIMIT = 232448;   // dynamic shared memory one CTA may use
-constexpr int MLP_MAX_STAGES = 8;
+constexpr int MLP_MAX_STAGES = 12;
 
 template <int C>
 struct MlpCfg {
   static constexpr int KS1 = C / 64;         // k-slices of xn and of a W1 chunk
   static constexpr int W2S = 2 * (C / 128);  // W2 slices of a chunk: C / 128 row halves x 2 k-slices
   static constexpr int A1_BYTES = KS1 * SLICE;
-  static constexpr int HS_BYTES = 2 * SLICE;  // one hidden chunk, 128 rows x 128 k
-  static constexpr int FIXED = A1_BYTES + 2 * HS_BYTES;
+  static constexpr int FIXED = A1_BYTES;
   static constexpr int FIT = (MLP_SMEM_LIMIT - 2048 - FIXED) / SLICE;
   static constexpr int STAGES = FIT > MLP_MAX_STAGES ? MLP_MAX_STAGES : FIT;
   static constexpr int SMEM = FIXED + STAGES * SLICE + 1024;
@@ -73,13 +75,13 @@ __global__ void __launch_bounds__(MLP_THREADS, 1)
   constexpr int STAGES = Cf::STAGES;
   extern __shared__ uint8_t dsmem[];
   __shared__ __align__(8) uint64_t full_bar[STAGES], empty_bar[STAGES];
-  __shared__ __align__(8) uint64_t a1_full, a1_empty, h_full[2], h_empty[2], hs_full[2], hs_empty[2];
+  __shared__ __align__(8) uint64_t a1_full, a1_empty, h_full[2], hs_full[2], hs_empty[2];
   __shared__ __align__(8) uint64_t o_full, o_empty, done_bar;
   __shared__ uint32_t tmem_slot;
   __shared__ volatile int s_abort;
 
   const uint32_t raw = smem_u32(dsmem);
-  const uint32_t sA1 = (raw + 1023u) & ~1023u, sHs = sA1 + Cf::A1_BYTES, sRing = sHs + 2 * Cf::HS_BYTES;
+  const uint32_t sA1 = (raw + 1023u) & ~1023u, sRing = sA1 + Cf::A1_BYTES;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int ntiles = (M + MB - 1) / MB, NCH = N1 / NH;
 
@@ -92,7 +94,6 @@ __global__ void __launch_bounds__(MLP_THREADS, 1)
     mbar_init(&a1_empty, 1);
     for (int b = 0; b < 2; ++b) {
       mbar_init(&h_full[b], 1);
-      mbar_init(&h_empty[b], MLP_EPI_WARPS);
       mbar_init(&hs_full[b], MLP_EPI_WARPS);
       mbar_init(&hs_empty[b], 1);
     }
@@ -165,9 +166,10 @@ __global__ void __launch_bounds__(MLP_THREADS, 1)
       tc_fence_after();
       for (int j = 0; j <= NCH && !stop; ++j) {
         if (j < NCH) {
-          // GEMM1 of chunk j: H[hb] = xn W1_j^T (the buffer's previous chunk read out)
+          // GEMM1 of chunk j: H[hb] = xn W1_j^T, once GEMM2 of the buffer's
+          // previous chunk (gj - 2) has read its BF16 pairs
           const uint32_t gj = g + j, hb = gj & 1u, u = gj >> 1;
-          if (gj >= 2 && !mbar_wait(&h_empty[hb], (u - 1) & 1u, &s_abort)) {
+          if (gj >= 2 && !mbar_wait(&hs_empty[hb], (u - 1) & 1u, &s_abort)) {
             stop = true;
             break;
           }
@@ -191,7 +193,7 @@ __global__ void __launch_bounds__(MLP_THREADS, 1)
           if (j == NCH - 1) mma_commit(&a1_empty);
         }
         if (j >= 1) {
-          // GEMM2 of chunk j - 1: O += Hs[pb] W2_{j-1}^T
+          // GEMM2 of chunk j - 1: O += H[pb] (BF16 in tensor memory) W2_{j-1}^T
           const uint32_t gp = g + j - 1, pb = gp & 1u, up = gp >> 1;
           if (j == 1 && ti >= 1 && !mbar_wait(&o_empty, (ti - 1) & 1u, &s_abort)) {
             stop = true;
@@ -202,7 +204,7 @@ __global__ void __launch_bounds__(MLP_THREADS, 1)
             break;
           }
           tc_fence_after();
-          const uint32_t aH = sHs + pb * Cf::HS_BYTES;
+          const uint32_t aH = tmem + Cf::TM_H + pb * NH;
           for (int q = 0; q < Cf::W2S; ++q) {
             uint32_t b;
             if (!take(b)) {
@@ -210,9 +212,12 @@ __global__ void __launch_bounds__(MLP_THREADS, 1)
               break;
             }
             const int s = q & 1, half = q >> 1;
+            // k step 4 s + kk (hidden columns 64 s + 16 kk ..): the BF16 pairs
+            // the warp of slot (4 s + kk) / 2 wrote, 8 columns from the start
+            // of its 32-column region for odd steps
 #pragma unroll
             for (int kk = 0; kk < 4; ++kk)
-              mma_ss(tmem + Cf::TM_O + 128 * half, smem_desc(aH + s * SLICE + kk * 32, 16, 1024),
+              mma_ts(tmem + Cf::TM_O + 128 * half, aH + (uint32_t)(64 * s + 32 * (kk >> 1) + 8 * (kk & 1)),
                      smem_desc(b + kk * 32, 16, 1024), Cf::IDESC, (j > 1 || s > 0 || kk > 0) ? 1u : 0u);
             release();
           }
@@ -246,35 +251,20 @@ __global__ void __launch_bounds__(MLP_THREADS, 1)
         if (!ok) break;
         tc_fence_after();
         uint32_t v[32];
-        tmem_ld32(lane_base + Cf::TM_H + hb * NH + 32 * slot, v);
+        const uint32_t hcol = lane_base + Cf::TM_H + hb * NH + 32 * slot;
+        tmem_ld32(hcol, v);
+        // hidden columns 32 slot + 2 i, + 1: bias, ReLU, a BF16 pair into
+        // column 32 slot + i of the same buffer (this warp's own columns)
+        uint32_t pk[16];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+          const float4 bb = bq[i >> 1];
+          const float b0 = (i & 1) ? bb.z : bb.x, b1v = (i & 1) ? bb.w : bb.y;
+          pk[i] = pack_bf16x2(fmaxf(__uint_as_float(v[2 * i]) + b0, 0.f), fmaxf(__uint_as_float(v[2 * i + 1]) + b1v, 0.f));
+        }
+        tmem_st16(hcol, pk);
+        tmem_wait_st();
         tc_fence_before();
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&h_empty[hb]);  // TMEM buffer hb free for chunk gj + 2
-        // the shared-memory buffer hb was last read by GEMM2 of chunk gj - 2
-        if (gj >= 2) {
-          ok = __all_sync(0xffffffffu, mbar_wait(&hs_empty[hb], (u - 1) & 1u, &s_abort));
-          if (!ok) break;
-        }
-        // hidden columns 32 slot + 8 q .. + 7: bias, ReLU, BF16 into row r of
-        // k-slice slot / 2, 16-byte chunk 4 (slot % 2) + q at that index
-        // XOR r % 8 (the 128-byte swizzle)
-        const uint32_t dst = sHs + hb * Cf::HS_BYTES + (slot >> 1) * SLICE + r * 128;
-        uint4 w[4];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const float bv[8] = {bq[2 * q].x,     bq[2 * q].y,     bq[2 * q].z,     bq[2 * q].w,
-                               bq[2 * q + 1].x, bq[2 * q + 1].y, bq[2 * q + 1].z, bq[2 * q + 1].w};
-          float f[8];
-#pragma unroll
-          for (int e = 0; e < 8; ++e) f[e] = fmaxf(__uint_as_float(v[8 * q + e]) + bv[e], 0.f);
-          w[q] = make_uint4(pack_bf16x2(f[0], f[1]), pack_bf16x2(f[2], f[3]), pack_bf16x2(f[4], f[5]),
-                            pack_bf16x2(f[6], f[7]));
-          const uint32_t qc = (uint32_t)((((slot & 1) * 4 + q) ^ (r & 7)) << 4);
-          asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(dst + qc), "r"(w[q].x), "r"(w[q].y),
-                       "r"(w[q].z), "r"(w[q].w)
-                       : "memory");
-        }
-        fence_proxy_async();  // the generic-proxy writes, seen by the tensor core
         __syncwarp();
         if (lane == 0) mbar_arrive(&hs_full[hb]);
       }
