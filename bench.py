@@ -230,7 +230,8 @@ def measure_ex2_rate(evo, dev):
 def class_rooflines(prof, peaks, clk, ex2_rate=None):
     """Per kernel class of the step: achieved TFLOP/s and fraction of the
     sustained BF16 tensor peak for the contractions (attention forward and
-    backward, triangle einsum, outer-product contraction, every other GEMM),
+    backward, triangle einsum, outer-product contraction, the fused
+    transition MLP, every other GEMM),
     and for the attention forward also against the exponential bound: one
     ex2 per (query, key) pair and 4 c flops per pair at head dim c = 32, so
     its flops / 128 exponentials at 16 per clock per SM."""
@@ -238,7 +239,7 @@ def class_rooflines(prof, peaks, clk, ex2_rate=None):
     nominal = SFU_EX2_PER_CLK_SM * N_SM * mhz * 1e6
     rate = (ex2_rate or {}).get("f32") or nominal
     out = {}
-    for name in ("gemm_tc", "attn_fwd_tc", "attn_bwd_tc", "tri_einsum", "opm_outer"):
+    for name in ("gemm_tc", "attn_fwd_tc", "attn_bwd_tc", "tri_einsum", "opm_outer", "mlp_fused"):
         v = prof.get(name)
         if not v or not v["flops"] or not v["ms"]:
             continue

@@ -54,3 +54,22 @@ def test_reference_arm_runs_on_rank_zero_only():
                         "--warmup", "0"], cwd=ROOT, env=env, capture_output=True, text=True, timeout=300)
     assert r.returncode == 0, r.stderr
     assert r.stdout.strip() == ""
+
+
+def test_class_rooflines_cover_every_contraction_class():
+    """The bench line's per-class rooflines: each contraction class present in
+    the profile gets TFLOP/s against the sustained peak; absent ones are left
+    out; the attention forward also gets its exponential bound."""
+    import bench
+    prof = {n: {"flops": 2e12, "ms": 10.0, "bytes": 1e9, "launches": 4}
+            for n in ("gemm_tc", "attn_fwd_tc", "attn_bwd_tc", "tri_einsum", "opm_outer", "mlp_fused")}
+    prof["ln_fwd"] = {"flops": 0.0, "ms": 1.0, "bytes": 1e9, "launches": 2}
+    peaks = {"bf16_sus": 1000.0, "hbm": 5000.0}
+    out = bench.class_rooflines(prof, peaks, {"sm_mhz": 2000.0}, {"f32": 1e13})
+    assert set(out) == {"gemm_tc", "attn_fwd_tc", "attn_bwd_tc", "tri_einsum", "opm_outer", "mlp_fused"}
+    for e in out.values():
+        assert abs(e["tflops"] - 200.0) < 1e-9 and abs(e["tensor_frac"] - 0.2) < 1e-12
+        assert abs(e["hbm_frac_of_operand_bytes"] - 0.02) < 1e-12
+    assert abs(out["attn_fwd_tc"]["exp_bound_ms"] - 1e3 * 2e12 / 128.0 / 1e13) < 1e-9
+    del prof["mlp_fused"]
+    assert "mlp_fused" not in bench.class_rooflines(prof, peaks, None, None)
